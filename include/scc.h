@@ -1,0 +1,166 @@
+/*
+ * scc.h -- C ABI of the GB300 (sm_103a) strongly-connected-components library.
+ *
+ * Method: the BGSS reachability-based SCC algorithm as engineered in Wang, Dong,
+ * Gu, Sun, "Parallel Strong Connectivity Based on Faster Reachability"
+ * (SIGMOD 2023): trimming (Sec. 4.1), a first SCC from one pivot by forward and
+ * backward single-reachability (Sec. 4.2), then forward and backward
+ * multi-reachability searches over prefix-doubling batches of random pivots
+ * (Alg. 1; Sec. 4.3), labelling/partitioning by reachability signature
+ * (Alg. 1; Sec. 4.4). Every reachability search uses vertical granularity control
+ * (bounded multi-hop local searches, Sec. 3.1-3.2) and a hash-bag frontier
+ * (Sec. 3.3). All of it runs in hand-written CUDA kernels on one GPU.
+ *
+ * Conventions shared by every entry point:
+ *  - Graphs are int32 CSR: row v of targets is targets[offsets[v] .. offsets[v+1]),
+ *    the out-neighbours of v; 0 <= targets[e] < n, offsets[0] = 0,
+ *    offsets[n] = m, offsets non-decreasing; m <= INT32_MAX. Self-loops and
+ *    duplicate arcs are accepted (they never change an SCC).
+ *  - Pointers marked "host or device" may point to either; the library asks the
+ *    driver (cudaPointerGetAttributes) which one it is. Pointers marked "device"
+ *    must be device (or managed) memory of the current CUDA device.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *    stream). Work is stream-ordered on it. Calls return after enqueueing, except
+ *    where a call says it synchronises `stream`.
+ *  - Every call returns SCC_OK (0) or a negative SCC_ERR_* code and never
+ *    throws. On failure, outputs are undefined. A handle is not thread-safe: one
+ *    host thread at a time per handle.
+ *  - Memory: the library allocates its device buffers stream-ordered
+ *    (cudaMallocAsync) from the device's default memory pool and frees them in
+ *    scc_graph_destroy.
+ */
+#ifndef SCC_GB300_SCC_H
+#define SCC_GB300_SCC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define SCC_API __attribute__((visibility("default")))
+#else
+#define SCC_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- errors ---- */
+#define SCC_OK 0
+#define SCC_ERR_INVALID_ARG (-1) /* bad size, CSR not well formed, id out of range, bad k/dir */
+#define SCC_ERR_OOM (-2)         /* a device allocation failed */
+#define SCC_ERR_CUDA (-3)        /* a CUDA runtime call or kernel launch failed */
+#define SCC_ERR_TIMEOUT (-4)     /* a bounded device-side wait gave up (kernel returned early) */
+#define SCC_ERR_CAPACITY (-5)    /* an internal table/bag could not grow far enough */
+#define SCC_ERR_INTERNAL (-6)    /* a self-check of the library failed */
+
+/* Static string describing an error code (never NULL). */
+SCC_API const char* scc_error_string(int code);
+
+/* ---------------------------------------------------------------- config ---- */
+/*
+ * Tunables. None of them changes any result: labels and reachability masks are
+ * identical for every valid configuration and seed.
+ *   tau         VGC edge budget of one local search (Sec. 3.2 "Control of
+ *               Granularity"): a warp task stops expanding after visiting about
+ *               tau arcs; vertices with more than tau out-arcs are expanded by
+ *               many warps in parallel instead. Default 512 (the paper's 2^9).
+ *   beta        prefix-doubling multiplier, > 1 (Sec. 2; the paper uses 1.5).
+ *   lambda      first hash-bag chunk size in slots, a power of two >= 1024
+ *               (Sec. 3.3; chunks grow lambda, 2*lambda, ...). Default 16384.
+ *   sigma       hash-bag samples per chunk before it is declared full (Sec. 3.3,
+ *               default 50).
+ *   block       threads per block of the search kernels (256; other values are
+ *               rejected with SCC_ERR_INVALID_ARG).
+ *   seeds       frontier items one warp takes per task, 1..32 (default 32).
+ *   dense       1: the first-SCC single-reachability may switch to the dense
+ *               (bottom-up) mode of Sec. 4.2 on large frontiers; 0: never.
+ *   seed        seed of the pivot permutation.
+ */
+typedef struct scc_config {
+    int32_t tau;
+    double beta;
+    int32_t lambda;
+    int32_t sigma;
+    int32_t block;
+    int32_t seeds;
+    int32_t dense;
+    uint64_t seed;
+} scc_config;
+
+/* Fill *cfg with the defaults listed above. */
+SCC_API int scc_config_default(scc_config* cfg);
+
+/* ----------------------------------------------------------------- graphs ---- */
+typedef struct scc_graph* scc_handle; /* opaque, owned by the library */
+
+/*
+ * Copy a CSR graph to the device and build what every later call needs: the
+ * self-loop-free forward CSR and its transpose G^T (Sec. 2: a backward search is a
+ * forward search on G^T), built with an in-degree histogram, an exclusive scan and
+ * a scatter.
+ *   n        number of vertices, 0 <= n < 2^31 - 1.
+ *   m        number of arcs, 0 <= m <= INT32_MAX.
+ *   offsets  host or device int32[n+1]; targets host or device int32[m]. Both are
+ *            only read; the caller keeps ownership and may free them when the
+ *            call returns.
+ *   out      receives the handle.
+ * Synchronises `stream` (it validates the CSR and returns SCC_ERR_INVALID_ARG if
+ * it is not well formed).
+ */
+SCC_API int scc_graph_create(int32_t n, int64_t m, const int32_t* offsets, const int32_t* targets,
+                     void* stream, scc_handle* out);
+
+/* Release every buffer of h (stream-ordered on the stream of the last call). NULL is ok. */
+SCC_API int scc_graph_destroy(scc_handle h);
+
+/* Replace the configuration of h (validated; SCC_ERR_INVALID_ARG if out of range). */
+SCC_API int scc_set_config(scc_handle h, const scc_config* cfg);
+
+/* ------------------------------------------------------------------- SCC ---- */
+/*
+ * Strongly connected components (Sec. 1 problem statement, computed by Alg. 1):
+ * labels_out[v] = the smallest vertex id u with u ~> v and v ~> u. The result is
+ * deterministic and independent of the configuration and seed.
+ *   labels_out  host or device int32[n], written.
+ * Host-driven rounds: the call synchronises `stream` a few times per round and
+ * before returning.
+ */
+SCC_API int scc_run(scc_handle h, int32_t* labels_out, void* stream);
+
+/* -------------------------------------------------------------- reach ---- */
+/*
+ * Multi-source reachability (Sec. 2 "Reachability Search"): for j < k,
+ * bit j of out[v] is 1 iff sources[j] ~> v (dir = 0, forward on G) or
+ * v ~> sources[j] (dir = 1, backward: forward on G^T). Plain reachability: no
+ * label classes. Duplicate sources are allowed; bit j always refers to
+ * sources[j].
+ *   sources  host or device int32[k], 1 <= k <= 64, each in [0, n).
+ *   out      host or device uint64[n], written.
+ * Synchronises `stream` before returning.
+ */
+SCC_API int reach_multi(scc_handle h, const int32_t* sources, int32_t k, int32_t dir, uint64_t* out,
+                void* stream);
+
+/* ------------------------------------------------------------ statistics ---- */
+/*
+ * Counters of the last scc_run on h, in the paper's cost categories (Sec. 4,
+ * Fig. 8): times in milliseconds measured with CUDA events on the run's stream.
+ */
+typedef struct scc_stats {
+    int32_t n_trimmed;         /* vertices removed by trimming */
+    int32_t first_scc_size;    /* size of the SCC found from the first pivot */
+    int32_t batches;           /* prefix-doubling batches run (including the first) */
+    int32_t search_rounds;     /* reachability rounds (frontier swaps), all searches */
+    int64_t pairs;             /* reachability pairs inserted by multi-reachability */
+    int32_t table_resizes;     /* pair-table regrowths */
+    int32_t reserved;
+    double ms_trim, ms_first_scc, ms_multi_search, ms_resize, ms_label;
+} scc_stats;
+
+SCC_API int scc_get_stats(scc_handle h, scc_stats* out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SCC_GB300_SCC_H */

@@ -1,0 +1,97 @@
+/*
+ * scc_debug.h -- step-level entry points of the SCC library, for parity tests.
+ *
+ * Each call runs ONE step of the hot path in the same kernels scc_run uses, so a
+ * test can compare that step's output with a CPU restatement. Conventions
+ * (errors, streams, host-or-device pointers) are those of scc.h. Every call here
+ * synchronises `stream` before returning.
+ */
+#ifndef SCC_GB300_SCC_DEBUG_H
+#define SCC_GB300_SCC_DEBUG_H
+
+#include "scc.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* n, m of the input and m_t = arcs of the self-loop-free graph (= arcs of G^T). */
+SCC_API int scc_graph_info(scc_handle h, int32_t* n, int64_t* m, int64_t* m_t);
+
+/*
+ * Copy the library's self-loop-free CSR of G (which = 0) or of G^T (which = 1)
+ * (Sec. 2; G^T row v lists the in-neighbours of v, one entry per arc, in an
+ * unspecified order).
+ *   off  host or device int32[n+1]; adj host or device int32[m_t].
+ */
+SCC_API int scc_debug_csr(scc_handle h, int32_t which, int32_t* off, int32_t* adj, void* stream);
+
+/*
+ * Trimming (Sec. 4.1): flags[v] = 1 iff v has no arc to or no arc from another
+ * vertex. flags: host or device uint8[n].
+ */
+SCC_API int scc_debug_trim(scc_handle h, uint8_t* flags, void* stream);
+
+/*
+ * Pivot order (Alg. 1 random batches; Sec. 2 prefix doubling): order[p] =
+ * act[pi(p)], act the increasing list of untrimmed vertices and pi the seeded
+ * Feistel bijection of [0, N) with cycle walking (Black & Rogaway, CT-RSA 2002)
+ * under h's config seed. order: host or device int32[n] (first N entries
+ * written); *n_active (host) receives N.
+ */
+SCC_API int scc_debug_pivot_order(scc_handle h, int32_t* order, int32_t* n_active, void* stream);
+
+/*
+ * Single-reachability with the first-SCC engine (Alg. 3 with VGC, Sec. 3;
+ * dense mode per config, Sec. 4.2): visited[v] = 1 iff s reaches v over arcs
+ * whose endpoints both carry label[s] (labels NULL: one class).
+ *   labels  host or device int32[n] or NULL; a negative label means finished.
+ *   dir     0 forward on G, 1 backward on G^T.
+ *   visited host or device uint8[n].
+ */
+SCC_API int scc_debug_single_reach(scc_handle h, const int32_t* labels, int32_t s, int32_t dir,
+                           uint8_t* visited, void* stream);
+
+/*
+ * Multi-reachability (Alg. 1 MultiReach with VGC and a hash-bag frontier,
+ * Sec. 3, and the pair table of Sec. 4.3/4.5): the set of pairs
+ * (v, s), s in sources, s ~> v (dir 0) or v ~> s (dir 1) inside s's label class.
+ *   labels   host or device int32[n] (negative = finished: no pairs).
+ *   sources  host or device int32[k], k >= 1.
+ *   pairs    host or device uint64[cap]; receives v << 32 | s, unordered, when
+ *            the total fits.
+ *   *npairs  (host) total number of pairs (may exceed cap).
+ *   table_cap  initial pair-table capacity (power of two >= 1024, or 0 = by the
+ *            paper's sizing heuristic); small values exercise regrowth.
+ */
+SCC_API int scc_debug_multi_reach(scc_handle h, const int32_t* labels, const int32_t* sources, int32_t k,
+                          int32_t dir, uint64_t* pairs, int64_t cap, int64_t* npairs,
+                          int64_t table_cap, void* stream);
+
+/*
+ * Hash bag (Sec. 3.3, Fig. 5): insert items[0..count) from many warps
+ * concurrently (each warp claims random 32-slot segments of the current chunk by
+ * CAS, with sampled chunk advance), then ExtractAll by warp-aggregated
+ * compaction. out receives the extracted multiset (unordered), *nout (host) its
+ * size, *chunks (host, may be NULL) the number of chunks in use at extraction.
+ *   items  host or device int32[count], each in [0, 2^31 - 1).
+ *   out    host or device int32[count].
+ */
+SCC_API int scc_debug_hashbag(const int32_t* items, int64_t count, int32_t lambda, int32_t sigma,
+                      int32_t* out, int64_t* nout, int32_t* chunks, void* stream);
+
+/*
+ * Pair table (Sec. 4.3 phase-concurrent table, with the regrowth of Sec. 4.5):
+ * insert keys[0..count) (duplicates allowed) into a table of initial capacity
+ * init_cap; out receives the distinct keys (unordered), *nout (host) their number,
+ * *resizes (host, may be NULL) how often the table grew.
+ *   keys  host or device uint64[count], each != UINT64_MAX.
+ *   out   host or device uint64[count].
+ */
+SCC_API int scc_debug_pair_table(const uint64_t* keys, int64_t count, int64_t init_cap, uint64_t* out,
+                         int64_t* nout, int32_t* resizes, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SCC_GB300_SCC_DEBUG_H */

@@ -1,0 +1,790 @@
+// C ABI (include/scc.h, include/scc_debug.h): graph handles, the SCC round
+// driver (Alg. 1 with the paper's Sec. 4 engineering), multi-source
+// reachability and the step-level test hooks.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/scc.h"
+#include "../../include/scc_debug.h"
+#include "common.cuh"
+#include "engine.cuh"
+#include "internal.h"
+
+using namespace scc;
+
+struct scc_graph {
+    DeviceInfo di;
+    int32_t n = 0;
+    int64_t m_in = 0;      // arcs of the input
+    int64_t mt = 0;        // arcs without self-loops (= arcs of G^T)
+    int32_t* off = nullptr;
+    int32_t* adj = nullptr;
+    int32_t* toff = nullptr;
+    int32_t* tadj = nullptr;
+    scc_config cfg;
+    cudaStream_t last = nullptr;
+    // run state (allocated on first use, reused)
+    int32_t* label = nullptr;
+    int32_t* rep = nullptr;
+    int32_t* act = nullptr;
+    int32_t* tmp_a = nullptr;  // n+1
+    int32_t* tmp_b = nullptr;  // n+1
+    void* scan_tmp = nullptr;
+    int32_t* sources = nullptr;
+    unsigned long long* fmax = nullptr;
+    unsigned long long* bmax = nullptr;
+    unsigned long long* hit = nullptr;
+    uint32_t* bits_f = nullptr;
+    uint32_t* bits_b = nullptr;
+    unsigned long long* counters = nullptr;  // [0] nact [1] ndone [2] scratch
+    int* flags = nullptr;                    // [0] k [1] bad [2] overflow
+    unsigned long long* tab[2] = {nullptr, nullptr};
+    int64_t tab_alloc[2] = {0, 0};
+    EngineBuf eb32, eb64;
+    scc_stats stats;
+};
+
+namespace scc {
+
+int dalloc(void** p, size_t bytes, cudaStream_t s) {
+    *p = nullptr;
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMallocAsync(p, bytes, s);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return e == cudaErrorMemoryAllocation ? SCC_ERR_OOM : SCC_ERR_CUDA;
+    }
+    return SCC_OK;
+}
+void dfree(void* p, cudaStream_t s) {
+    if (p) cudaFreeAsync(p, s);
+}
+bool is_device_ptr(const void* p) {
+    if (!p) return false;
+    cudaPointerAttributes a;
+    cudaError_t e = cudaPointerGetAttributes(&a, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+int device_info(DeviceInfo* out) {
+    SCC_CUDA(cudaGetDevice(&out->dev));
+    SCC_CUDA(cudaDeviceGetAttribute(&out->num_sms, cudaDevAttrMultiProcessorCount, out->dev));
+    return SCC_OK;
+}
+
+}  // namespace scc
+
+namespace {
+
+int64_t pow2ceil(int64_t x) {
+    int64_t p = 1;
+    while (p < x) p <<= 1;
+    return p;
+}
+
+// Copy count elements from a host-or-device pointer into device memory dst.
+int to_device(void* dst, const void* src, size_t bytes, cudaStream_t s) {
+    if (bytes == 0) return SCC_OK;
+    cudaMemcpyKind kind = is_device_ptr(src) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    SCC_CUDA(cudaMemcpyAsync(dst, src, bytes, kind, s));
+    return SCC_OK;
+}
+int from_device(void* dst, const void* src, size_t bytes, cudaStream_t s) {
+    if (bytes == 0) return SCC_OK;
+    cudaMemcpyKind kind = is_device_ptr(dst) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    SCC_CUDA(cudaMemcpyAsync(dst, src, bytes, kind, s));
+    return SCC_OK;
+}
+
+EngineOpts opts_of(const scc_graph* h) {
+    EngineOpts o;
+    o.tau = h->cfg.tau;
+    o.seeds = h->cfg.seeds;
+    o.sigma = h->cfg.sigma;
+    o.block = h->cfg.block;
+    o.num_sms = h->di.num_sms;
+    return o;
+}
+
+int valid_config(const scc_config* c) {
+    if (!c) return SCC_ERR_INVALID_ARG;
+    if (c->tau < 1 || c->tau > (1 << 20)) return SCC_ERR_INVALID_ARG;
+    if (!(c->beta > 1.0 && c->beta <= 64.0)) return SCC_ERR_INVALID_ARG;
+    if (c->lambda < 1024 || c->lambda > (1 << 24) || (c->lambda & (c->lambda - 1))) return SCC_ERR_INVALID_ARG;
+    if (c->sigma < 1 || c->sigma > (1 << 20)) return SCC_ERR_INVALID_ARG;
+    if (c->block != 256) return SCC_ERR_INVALID_ARG;
+    if (c->seeds < 1 || c->seeds > 32) return SCC_ERR_INVALID_ARG;
+    if (c->dense != 0 && c->dense != 1) return SCC_ERR_INVALID_ARG;
+    return SCC_OK;
+}
+
+int reserve_run_state(scc_graph* h, cudaStream_t s) {
+    if (h->label) return SCC_OK;
+    const int64_t n = h->n;
+    const int64_t nw = (n + 31) / 32;
+    SCC_TRY(dalloc_t(&h->label, n, s));
+    SCC_TRY(dalloc_t(&h->rep, n, s));
+    SCC_TRY(dalloc_t(&h->act, n, s));
+    SCC_TRY(dalloc_t(&h->tmp_a, n + 1, s));
+    SCC_TRY(dalloc_t(&h->tmp_b, n + 1, s));
+    SCC_TRY(dalloc(&h->scan_tmp, scan_tmp_bytes(n), s));
+    SCC_TRY(dalloc_t(&h->sources, std::max<int64_t>(n, 64), s));
+    SCC_TRY(dalloc_t(&h->fmax, n, s));
+    SCC_TRY(dalloc_t(&h->bmax, n, s));
+    SCC_TRY(dalloc_t(&h->hit, n, s));
+    SCC_TRY(dalloc_t(&h->bits_f, nw, s));
+    SCC_TRY(dalloc_t(&h->bits_b, nw, s));
+    SCC_TRY(dalloc_t(&h->counters, 4, s));
+    SCC_TRY(dalloc_t(&h->flags, 4, s));
+    return SCC_OK;
+}
+
+int reserve_table(scc_graph* h, int d, int64_t cap, cudaStream_t s) {
+    if (h->tab_alloc[d] >= cap) return SCC_OK;
+    dfree(h->tab[d], s);
+    h->tab[d] = nullptr;
+    h->tab_alloc[d] = 0;
+    SCC_TRY(dalloc_t(&h->tab[d], (size_t)cap, s));
+    h->tab_alloc[d] = cap;
+    return SCC_OK;
+}
+
+struct EvTimer {
+    cudaEvent_t a = nullptr, b = nullptr;
+    cudaStream_t s;
+    explicit EvTimer(cudaStream_t st) : s(st) {
+        cudaEventCreate(&a);
+        cudaEventCreate(&b);
+    }
+    ~EvTimer() {
+        if (a) cudaEventDestroy(a);
+        if (b) cudaEventDestroy(b);
+    }
+    void start() { cudaEventRecord(a, s); }
+    double stop() {
+        cudaEventRecord(b, s);
+        cudaEventSynchronize(b);
+        float ms = 0;
+        cudaEventElapsedTime(&ms, a, b);
+        return ms;
+    }
+};
+
+// Forward and backward multi-reachability of one batch into tables tab[0], tab[1]
+// with the paper's sizing heuristic (Sec. 4.5): capacity pow2ceil(max(0.3 b,
+// 1.5 a)), a = pairs of the previous round in the same direction, b = active
+// vertices; an insertion that probes too far (or a load above 0.6) regrows the
+// table to twice the capacity and reruns that direction.
+int multi_search(scc_graph* h, int32_t k, int64_t b_active, int64_t a_prev[2], int64_t cap_out[2],
+                 int64_t pairs_out[2], cudaStream_t s, double* ms_search, double* ms_resize, int* rounds) {
+    EngineOpts o = opts_of(h);
+    for (int d = 0; d < 2; ++d) {
+        int64_t want = std::max<int64_t>((int64_t)std::ceil(0.3 * (double)b_active), (int64_t)std::ceil(1.5 * a_prev[d]));
+        want = std::max<int64_t>(want, 2 * (int64_t)k);
+        int64_t cap = std::max<int64_t>(pow2ceil(want), 1024);
+        const int32_t* off = d == 0 ? h->off : h->toff;
+        const int32_t* adj = d == 0 ? h->adj : h->tadj;
+        for (int attempt = 0;; ++attempt) {
+            if (attempt > 40) return SCC_ERR_CAPACITY;
+            EvTimer t(s);
+            t.start();
+            SCC_TRY(reserve_table(h, d, cap, s));
+            SCC_CUDA(cudaMemsetAsync(h->tab[d], 0xff, (size_t)cap * 8, s));
+            long long max_ins = (long long)(0.6 * (double)cap);
+            SCC_TRY(engine_reserve(&h->eb64, 8, max_ins + (1 << 20), h->cfg.lambda, h->mt, s));
+            EngineRun r;
+            int rc = run_pairs(off, adj, h->n, h->label, h->sources, k, h->tab[d], cap, max_ins, &h->eb64, o, &r, s);
+            double ms = t.stop();
+            *rounds += r.rounds;
+            if (rc == SCC_ERR_CAPACITY || r.overflow) {
+                *ms_resize += ms;
+                h->stats.table_resizes++;
+                cap *= 2;
+                continue;
+            }
+            SCC_TRY(rc);
+            *ms_search += ms;
+            cap_out[d] = cap;
+            pairs_out[d] = (int64_t)r.inserted;
+            break;
+        }
+    }
+    return SCC_OK;
+}
+
+}  // namespace
+
+// ==================================================================== ABI ====
+extern "C" {
+
+const char* scc_error_string(int code) {
+    switch (code) {
+        case SCC_OK: return "ok";
+        case SCC_ERR_INVALID_ARG: return "invalid argument";
+        case SCC_ERR_OOM: return "out of device memory";
+        case SCC_ERR_CUDA: return "CUDA error";
+        case SCC_ERR_TIMEOUT: return "bounded device wait timed out";
+        case SCC_ERR_CAPACITY: return "internal capacity exceeded";
+        case SCC_ERR_INTERNAL: return "internal self-check failed";
+        default: return "unknown error";
+    }
+}
+
+int scc_config_default(scc_config* cfg) {
+    if (!cfg) return SCC_ERR_INVALID_ARG;
+    cfg->tau = 512;
+    cfg->beta = 1.5;
+    cfg->lambda = 1 << 14;
+    cfg->sigma = 50;
+    cfg->block = 256;
+    cfg->seeds = 32;
+    cfg->dense = 1;
+    cfg->seed = 0x5CC00ull;
+    return SCC_OK;
+}
+
+static int graph_create_impl(scc_graph* h, int32_t n, int64_t m, const int32_t* offsets, const int32_t* targets,
+                             cudaStream_t s) {
+    SCC_TRY(device_info(&h->di));
+    h->n = n;
+    h->m_in = m;
+    int32_t *off_in = nullptr, *adj_in = nullptr;
+    SCC_TRY(dalloc_t(&off_in, (size_t)n + 1, s));
+    SCC_TRY(dalloc_t(&adj_in, (size_t)m, s));
+    h->off = off_in;
+    h->adj = adj_in;
+    SCC_TRY(to_device(off_in, offsets, sizeof(int32_t) * ((size_t)n + 1), s));
+    SCC_TRY(to_device(adj_in, targets, sizeof(int32_t) * (size_t)m, s));
+    // validate before any kernel indexes with these arrays
+    int* bad = nullptr;
+    SCC_TRY(dalloc_t(&bad, 1, s));
+    SCC_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), s));
+    SCC_TRY(launch_validate(off_in, adj_in, n, m, bad, s));
+    int hbad = 0;
+    SCC_CUDA(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
+    SCC_CUDA(cudaStreamSynchronize(s));
+    dfree(bad, s);
+    if (hbad) return SCC_ERR_INVALID_ARG;
+    // in-degrees and self-loops
+    int32_t *indeg = nullptr, *selfrow = nullptr, *toff = nullptr;
+    unsigned long long* nself = nullptr;
+    void* stmp = nullptr;
+    SCC_TRY(dalloc_t(&indeg, (size_t)n + 1, s));
+    SCC_TRY(dalloc_t(&selfrow, (size_t)n + 1, s));
+    SCC_TRY(dalloc_t(&nself, 1, s));
+    SCC_TRY(dalloc(&stmp, scan_tmp_bytes(n), s));
+    SCC_CUDA(cudaMemsetAsync(indeg, 0, sizeof(int32_t) * ((size_t)n + 1), s));
+    SCC_CUDA(cudaMemsetAsync(selfrow, 0, sizeof(int32_t) * ((size_t)n + 1), s));
+    SCC_CUDA(cudaMemsetAsync(nself, 0, sizeof(unsigned long long), s));
+    SCC_TRY(launch_count_arcs(off_in, adj_in, n, m, indeg, selfrow, nself, s));
+    unsigned long long hself = 0;
+    SCC_CUDA(cudaMemcpyAsync(&hself, nself, sizeof(hself), cudaMemcpyDeviceToHost, s));
+    SCC_CUDA(cudaStreamSynchronize(s));
+    h->mt = m - (int64_t)hself;
+    if (hself > 0) {
+        // forward CSR without self-loops
+        int32_t *cnt = nullptr, *off2 = nullptr, *adj2 = nullptr;
+        SCC_TRY(dalloc_t(&cnt, (size_t)n + 1, s));
+        SCC_TRY(dalloc_t(&off2, (size_t)n + 1, s));
+        SCC_TRY(dalloc_t(&adj2, (size_t)h->mt, s));
+        SCC_TRY(launch_row_nonself(off_in, selfrow, n, cnt, s));
+        SCC_TRY(launch_scan(cnt, off2, n, stmp, s));
+        SCC_TRY(launch_drop_self_loops(off_in, adj_in, n, m, selfrow, off2, adj2, s));
+        dfree(cnt, s);
+        dfree(off_in, s);
+        dfree(adj_in, s);
+        h->off = off2;
+        h->adj = adj2;
+    }
+    // G^T: exclusive scan of in-degrees, then scatter
+    SCC_TRY(dalloc_t(&toff, (size_t)n + 1, s));
+    SCC_TRY(dalloc_t(&h->tadj, (size_t)h->mt, s));
+    SCC_TRY(launch_scan(indeg, toff, n, stmp, s));
+    SCC_CUDA(cudaMemcpyAsync(indeg, toff, sizeof(int32_t) * (size_t)n, cudaMemcpyDeviceToDevice, s));
+    SCC_TRY(launch_transpose_scatter(h->off, h->adj, n, h->mt, indeg, h->tadj, s));
+    h->toff = toff;
+    dfree(indeg, s);
+    dfree(selfrow, s);
+    dfree(nself, s);
+    dfree(stmp, s);
+    SCC_CUDA(cudaStreamSynchronize(s));
+    return SCC_OK;
+}
+
+static void graph_free(scc_graph* h, cudaStream_t s) {
+    dfree(h->off, s);
+    dfree(h->adj, s);
+    dfree(h->toff, s);
+    dfree(h->tadj, s);
+    dfree(h->label, s);
+    dfree(h->rep, s);
+    dfree(h->act, s);
+    dfree(h->tmp_a, s);
+    dfree(h->tmp_b, s);
+    dfree(h->scan_tmp, s);
+    dfree(h->sources, s);
+    dfree(h->fmax, s);
+    dfree(h->bmax, s);
+    dfree(h->hit, s);
+    dfree(h->bits_f, s);
+    dfree(h->bits_b, s);
+    dfree(h->counters, s);
+    dfree(h->flags, s);
+    dfree(h->tab[0], s);
+    dfree(h->tab[1], s);
+    engine_release(&h->eb32, s);
+    engine_release(&h->eb64, s);
+}
+
+int scc_graph_create(int32_t n, int64_t m, const int32_t* offsets, const int32_t* targets, void* stream,
+                     scc_handle* out) {
+    if (!out) return SCC_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (n < 0 || n >= INT32_MAX || m < 0 || m > INT32_MAX || !offsets || (m > 0 && !targets))
+        return SCC_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    scc_graph* h = new (std::nothrow) scc_graph();
+    if (!h) return SCC_ERR_OOM;
+    scc_config_default(&h->cfg);
+    memset(&h->stats, 0, sizeof(h->stats));
+    h->last = s;
+    int rc = graph_create_impl(h, n, m, offsets, targets, s);
+    if (rc != SCC_OK) {
+        graph_free(h, s);
+        cudaStreamSynchronize(s);
+        delete h;
+        return rc;
+    }
+    *out = h;
+    return SCC_OK;
+}
+
+int scc_graph_destroy(scc_handle h) {
+    if (!h) return SCC_OK;
+    graph_free(h, h->last);
+    cudaError_t e = cudaStreamSynchronize(h->last);
+    delete h;
+    return cuda_err(e);
+}
+
+int scc_set_config(scc_handle h, const scc_config* cfg) {
+    if (!h) return SCC_ERR_INVALID_ARG;
+    SCC_TRY(valid_config(cfg));
+    h->cfg = *cfg;
+    return SCC_OK;
+}
+
+int scc_get_stats(scc_handle h, scc_stats* out) {
+    if (!h || !out) return SCC_ERR_INVALID_ARG;
+    *out = h->stats;
+    return SCC_OK;
+}
+
+int scc_graph_info(scc_handle h, int32_t* n, int64_t* m, int64_t* m_t) {
+    if (!h) return SCC_ERR_INVALID_ARG;
+    if (n) *n = h->n;
+    if (m) *m = h->m_in;
+    if (m_t) *m_t = h->mt;
+    return SCC_OK;
+}
+
+static int scc_run_impl(scc_graph* h, int32_t* labels_out, cudaStream_t s) {
+    const int32_t n = h->n;
+    scc_stats& st = h->stats;
+    memset(&st, 0, sizeof(st));
+    if (n == 0) return SCC_OK;
+    SCC_TRY(reserve_run_state(h, s));
+    EngineOpts o = opts_of(h);
+
+    // ---- trimming (Sec. 4.1) and the active list
+    EvTimer t(s);
+    t.start();
+    SCC_CUDA(cudaMemsetAsync(h->counters, 0, 4 * sizeof(unsigned long long), s));
+    SCC_CUDA(cudaMemsetAsync(h->fmax, 0, (size_t)n * 8, s));
+    SCC_CUDA(cudaMemsetAsync(h->bmax, 0, (size_t)n * 8, s));
+    SCC_CUDA(cudaMemsetAsync(h->hit, 0, (size_t)n * 8, s));
+    SCC_TRY(launch_init_labels(h->off, h->toff, n, h->label, h->rep, &h->counters[0], s));
+    SCC_TRY(launch_compact_active(h->label, n, h->tmp_a, h->tmp_b, h->scan_tmp, h->act, s));
+    unsigned long long hc[4];
+    SCC_CUDA(cudaMemcpyAsync(hc, h->counters, sizeof(hc), cudaMemcpyDeviceToHost, s));
+    st.ms_trim = t.stop();
+    const int64_t N = (int64_t)hc[0];
+    st.n_trimmed = (int32_t)(n - N);
+
+    if (N > 0) {
+        // ---- prefix-doubling batches over the seeded pivot order (Alg. 1)
+        std::vector<int64_t> bounds{0};
+        {
+            double x = 1.0;
+            int64_t pos = 0;
+            while (pos < N) {
+                int64_t sz;
+                if (x >= (double)N) sz = N;
+                else {
+                    sz = (int64_t)x;
+                    if ((double)sz < x) ++sz;
+                }
+                if (sz < 1) sz = 1;
+                pos = (N - pos < sz) ? N : pos + sz;
+                bounds.push_back(pos);
+                x *= h->cfg.beta;
+            }
+        }
+        const int nb = (int)bounds.size() - 1;
+
+        // ---- first SCC: single-reachability both ways from the first pivot (Sec. 4.2)
+        t.start();
+        int64_t p0 = feistel_perm_host(0, N, h->cfg.seed);
+        int32_t s0 = 0;
+        SCC_CUDA(cudaMemcpyAsync(&s0, h->act + p0, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        SCC_CUDA(cudaStreamSynchronize(s));
+        SCC_TRY(engine_reserve(&h->eb32, 4, N + 1024, h->cfg.lambda, h->mt, s));
+        SCC_TRY(launch_prefill_bits(h->label, 0, n, h->bits_f, s));
+        SCC_TRY(launch_prefill_bits(h->label, 0, n, h->bits_b, s));
+        EngineRun r0, r1;
+        SCC_TRY(run_single(h->off, h->adj, n, s0, h->bits_f, &h->eb32, o, &r0, s));
+        SCC_TRY(run_single(h->toff, h->tadj, n, s0, h->bits_b, &h->eb32, o, &r1, s));
+        SCC_TRY(launch_label_first(h->bits_f, h->bits_b, n, s0, h->label, h->rep, &h->counters[1], s));
+        SCC_CUDA(cudaMemcpyAsync(hc, h->counters, sizeof(hc), cudaMemcpyDeviceToHost, s));
+        st.ms_first_scc = t.stop();
+        st.first_scc_size = (int32_t)hc[1];
+        st.search_rounds += r0.rounds + r1.rounds;
+        st.batches = 1;
+
+        // ---- multi-reachability batches (Alg. 1; Sec. 4.3-4.5)
+        int64_t a_prev[2] = {0, 0};
+        for (int i = 1; i < nb; ++i) {
+            const int64_t done = (int64_t)hc[1];
+            const int64_t b_active = N - done;
+            if (b_active <= 0) break;
+            SCC_CUDA(cudaMemsetAsync(h->flags, 0, sizeof(int), s));
+            SCC_TRY(launch_batch_sources(h->act, N, h->cfg.seed, bounds[i], bounds[i + 1], h->label, h->sources,
+                                         &h->flags[0], s));
+            int k = 0;
+            SCC_CUDA(cudaMemcpyAsync(&k, h->flags, sizeof(int), cudaMemcpyDeviceToHost, s));
+            SCC_CUDA(cudaStreamSynchronize(s));
+            if (k == 0) continue;
+            st.batches++;
+            int64_t cap[2], pairs[2];
+            SCC_TRY(multi_search(h, k, b_active, a_prev, cap, pairs, s, &st.ms_multi_search, &st.ms_resize,
+                                 &st.search_rounds));
+            st.pairs += pairs[0] + pairs[1];
+            a_prev[0] = pairs[0];
+            a_prev[1] = pairs[1];
+            t.start();
+            SCC_TRY(launch_label_pairs(h->tab[0], cap[0], h->tab[1], cap[1], (uint32_t)i, h->fmax, h->bmax, h->hit,
+                                       h->label, h->rep, &h->counters[1], s));
+            SCC_CUDA(cudaMemcpyAsync(hc, h->counters, sizeof(hc), cudaMemcpyDeviceToHost, s));
+            st.ms_label += t.stop();
+        }
+        if ((int64_t)hc[1] != N) return SCC_ERR_INTERNAL;  // every active vertex must be finished
+    }
+
+    // ---- canonical minimum labels
+    t.start();
+    int32_t* dst = labels_out;
+    bool host_out = !is_device_ptr(labels_out);
+    if (host_out) dst = h->tmp_a;
+    SCC_CUDA(cudaMemsetAsync(h->flags + 1, 0, sizeof(int), s));
+    SCC_TRY(launch_canonicalize(h->rep, n, h->tmp_b, dst, h->flags + 1, s));
+    if (host_out) SCC_CUDA(cudaMemcpyAsync(labels_out, dst, sizeof(int32_t) * (size_t)n, cudaMemcpyDeviceToHost, s));
+    int bad = 0;
+    SCC_CUDA(cudaMemcpyAsync(&bad, h->flags + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
+    st.ms_label += t.stop();
+    if (bad) return SCC_ERR_INTERNAL;
+    return SCC_OK;
+}
+
+int scc_run(scc_handle h, int32_t* labels_out, void* stream) {
+    if (!h || (h->n > 0 && !labels_out)) return SCC_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    h->last = s;
+    return scc_run_impl(h, labels_out, s);
+}
+
+int reach_multi(scc_handle h, const int32_t* sources, int32_t k, int32_t dir, uint64_t* out, void* stream) {
+    if (!h || !sources || !out || k < 1 || k > 64 || (dir != 0 && dir != 1)) return SCC_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    h->last = s;
+    const int32_t n = h->n;
+    if (!is_device_ptr(sources)) {
+        for (int j = 0; j < k; ++j)
+            if (sources[j] < 0 || sources[j] >= n) return SCC_ERR_INVALID_ARG;
+    }
+    SCC_TRY(reserve_run_state(h, s));
+    int32_t* dsrc = h->sources;
+    SCC_TRY(to_device(dsrc, sources, sizeof(int32_t) * (size_t)k, s));
+    bool dev_out = is_device_ptr(out);
+    unsigned long long* mask = dev_out ? reinterpret_cast<unsigned long long*>(out) : h->fmax;
+    // A vertex re-enters the frontier each time it gains source bits, so a round
+    // can hold more than n items; if the bag runs out of room the search restarts
+    // from the sources with twice the buffers.
+    for (int attempt = 0;; ++attempt) {
+        if (attempt > 8) return SCC_ERR_CAPACITY;
+        SCC_CUDA(cudaMemsetAsync(mask, 0, (size_t)n * 8, s));
+        SCC_CUDA(cudaMemsetAsync(h->flags + 1, 0, sizeof(int), s));
+        SCC_TRY(launch_mask_init(dsrc, k, n, mask, h->flags + 1, s));
+        int bad = 0;
+        SCC_CUDA(cudaMemcpyAsync(&bad, h->flags + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
+        SCC_CUDA(cudaStreamSynchronize(s));
+        if (bad) return SCC_ERR_INVALID_ARG;
+        SCC_TRY(engine_reserve(&h->eb32, 4, ((long long)n + 1024) << attempt, h->cfg.lambda, h->mt, s));
+        EngineRun r;
+        int rc = run_mask(dir == 0 ? h->off : h->toff, dir == 0 ? h->adj : h->tadj, n, dsrc, k, mask, &h->eb32,
+                          opts_of(h), &r, s);
+        if (rc == SCC_ERR_CAPACITY) continue;
+        SCC_TRY(rc);
+        break;
+    }
+    if (!dev_out) SCC_TRY(from_device(out, mask, (size_t)n * 8, s));
+    SCC_CUDA(cudaStreamSynchronize(s));
+    // mask mode uses fmax as scratch: the next scc_run clears it
+    return SCC_OK;
+}
+
+// ------------------------------------------------------------ debug hooks --
+int scc_debug_csr(scc_handle h, int32_t which, int32_t* off, int32_t* adj, void* stream) {
+    if (!h || !off || (h->mt > 0 && !adj) || (which != 0 && which != 1)) return SCC_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    h->last = s;
+    SCC_TRY(from_device(off, which ? h->toff : h->off, sizeof(int32_t) * ((size_t)h->n + 1), s));
+    SCC_TRY(from_device(adj, which ? h->tadj : h->adj, sizeof(int32_t) * (size_t)h->mt, s));
+    SCC_CUDA(cudaStreamSynchronize(s));
+    return SCC_OK;
+}
+
+int scc_debug_trim(scc_handle h, uint8_t* flags, void* stream) {
+    if (!h || (h->n > 0 && !flags)) return SCC_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    h->last = s;
+    if (h->n == 0) return SCC_OK;
+    uint8_t* d = nullptr;
+    SCC_TRY(dalloc_t(&d, (size_t)h->n, s));
+    int rc = launch_trim(h->off, h->toff, h->n, d, s);
+    if (rc == SCC_OK) rc = from_device(flags, d, (size_t)h->n, s);
+    if (rc == SCC_OK) rc = cuda_err(cudaStreamSynchronize(s));
+    dfree(d, s);
+    return rc;
+}
+
+int scc_debug_pivot_order(scc_handle h, int32_t* order, int32_t* n_active, void* stream) {
+    if (!h || !n_active || (h->n > 0 && !order)) return SCC_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    h->last = s;
+    *n_active = 0;
+    if (h->n == 0) return SCC_OK;
+    SCC_TRY(reserve_run_state(h, s));
+    SCC_CUDA(cudaMemsetAsync(h->counters, 0, 4 * sizeof(unsigned long long), s));
+    SCC_TRY(launch_init_labels(h->off, h->toff, h->n, h->label, h->rep, &h->counters[0], s));
+    SCC_TRY(launch_compact_active(h->label, h->n, h->tmp_a, h->tmp_b, h->scan_tmp, h->act, s));
+    unsigned long long N = 0;
+    SCC_CUDA(cudaMemcpyAsync(&N, h->counters, sizeof(N), cudaMemcpyDeviceToHost, s));
+    SCC_CUDA(cudaStreamSynchronize(s));
+    SCC_TRY(launch_pivot_order(h->act, (int64_t)N, h->cfg.seed, h->sources, s));
+    SCC_TRY(from_device(order, h->sources, sizeof(int32_t) * N, s));
+    SCC_CUDA(cudaStreamSynchronize(s));
+    *n_active = (int32_t)N;
+    return SCC_OK;
+}
+
+int scc_debug_single_reach(scc_handle h, const int32_t* labels, int32_t src, int32_t dir, uint8_t* visited,
+                           void* stream) {
+    if (!h || !visited || src < 0 || src >= h->n || (dir != 0 && dir != 1)) return SCC_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    h->last = s;
+    SCC_TRY(reserve_run_state(h, s));
+    const int32_t n = h->n;
+    int32_t L = 0;
+    const int32_t* dl = nullptr;
+    if (labels) {
+        SCC_TRY(to_device(h->label, labels, sizeof(int32_t) * (size_t)n, s));
+        dl = h->label;
+        SCC_CUDA(cudaMemcpyAsync(&L, h->label + src, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        SCC_CUDA(cudaStreamSynchronize(s));
+    }
+    uint8_t* d = nullptr;
+    SCC_TRY(dalloc_t(&d, (size_t)n, s));
+    int rc = SCC_OK;
+    if (labels && L < 0) {
+        rc = cuda_err(cudaMemsetAsync(d, 0, (size_t)n, s));  // a finished source reaches nothing
+    } else {
+        rc = launch_prefill_bits(dl, L, n, h->bits_f, s);
+        if (rc == SCC_OK) rc = engine_reserve(&h->eb32, 4, (long long)n + 1024, h->cfg.lambda, h->mt, s);
+        EngineRun r;
+        if (rc == SCC_OK)
+            rc = run_single(dir == 0 ? h->off : h->toff, dir == 0 ? h->adj : h->tadj, n, src, h->bits_f, &h->eb32,
+                            opts_of(h), &r, s);
+        if (rc == SCC_OK) rc = launch_bits_to_bytes(h->bits_f, dl, L, n, d, s);
+    }
+    if (rc == SCC_OK) rc = from_device(visited, d, (size_t)n, s);
+    if (rc == SCC_OK) rc = cuda_err(cudaStreamSynchronize(s));
+    dfree(d, s);
+    return rc;
+}
+
+int scc_debug_multi_reach(scc_handle h, const int32_t* labels, const int32_t* sources, int32_t k, int32_t dir,
+                          uint64_t* pairs, int64_t cap, int64_t* npairs, int64_t table_cap, void* stream) {
+    if (!h || !labels || !sources || k < 1 || k > h->n || (dir != 0 && dir != 1) || !npairs || cap < 0 ||
+        (cap > 0 && !pairs))
+        return SCC_ERR_INVALID_ARG;
+    if (table_cap != 0 && (table_cap < 1024 || (table_cap & (table_cap - 1)))) return SCC_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    h->last = s;
+    const int32_t n = h->n;
+    SCC_TRY(reserve_run_state(h, s));
+    SCC_TRY(to_device(h->label, labels, sizeof(int32_t) * (size_t)n, s));
+    SCC_TRY(to_device(h->tmp_a, sources, sizeof(int32_t) * (size_t)k, s));
+    // keep only distinct sources in [0,n) whose label is active (finished
+    // sources reach nothing); the engine wants valid ids
+    SCC_CUDA(cudaMemsetAsync(h->flags, 0, 2 * sizeof(int), s));
+    SCC_TRY(launch_filter_sources(h->tmp_a, k, n, h->label, h->sources, &h->flags[0], &h->flags[1], s));
+    int hf[2];
+    SCC_CUDA(cudaMemcpyAsync(hf, h->flags, sizeof(hf), cudaMemcpyDeviceToHost, s));
+    SCC_CUDA(cudaStreamSynchronize(s));
+    if (hf[1]) return SCC_ERR_INVALID_ARG;
+    const int kk = hf[0];
+    *npairs = 0;
+    if (kk == 0) return SCC_OK;
+    EngineOpts o = opts_of(h);
+    int64_t tcap = table_cap ? table_cap : std::max<int64_t>(1024, pow2ceil(std::max<int64_t>((int64_t)(0.3 * n), 2 * kk)));
+    const int d = dir;
+    int resizes = 0;
+    for (int attempt = 0;; ++attempt) {
+        if (attempt > 40) return SCC_ERR_CAPACITY;
+        SCC_TRY(reserve_table(h, d, tcap, s));
+        SCC_CUDA(cudaMemsetAsync(h->tab[d], 0xff, (size_t)tcap * 8, s));
+        long long max_ins = (long long)(0.6 * (double)tcap);
+        SCC_TRY(engine_reserve(&h->eb64, 8, max_ins + (1 << 20), h->cfg.lambda, h->mt, s));
+        EngineRun r;
+        int rc = run_pairs(d == 0 ? h->off : h->toff, d == 0 ? h->adj : h->tadj, n, h->label, h->sources, kk,
+                           h->tab[d], tcap, max_ins, &h->eb64, o, &r, s);
+        if (rc == SCC_ERR_CAPACITY || r.overflow) {
+            tcap *= 2;
+            ++resizes;
+            continue;
+        }
+        SCC_TRY(rc);
+        break;
+    }
+    h->stats.table_resizes = resizes;
+    // gather the table
+    unsigned long long* dout = nullptr;
+    bool dev_out = is_device_ptr(pairs);
+    SCC_CUDA(cudaMemsetAsync(h->counters + 2, 0, sizeof(unsigned long long), s));
+    if (dev_out) {
+        SCC_TRY(launch_table_gather(h->tab[d], tcap, reinterpret_cast<unsigned long long*>(pairs), cap, h->counters + 2, s));
+    } else {
+        SCC_TRY(dalloc_t(&dout, (size_t)std::max<int64_t>(cap, 1), s));
+        SCC_TRY(launch_table_gather(h->tab[d], tcap, dout, cap, h->counters + 2, s));
+    }
+    unsigned long long tot = 0;
+    SCC_CUDA(cudaMemcpyAsync(&tot, h->counters + 2, sizeof(tot), cudaMemcpyDeviceToHost, s));
+    SCC_CUDA(cudaStreamSynchronize(s));
+    if (!dev_out) {
+        int64_t c = std::min<int64_t>((int64_t)tot, cap);
+        int rc = cuda_err(cudaMemcpyAsync(pairs, dout, sizeof(uint64_t) * (size_t)c, cudaMemcpyDeviceToHost, s));
+        if (rc == SCC_OK) rc = cuda_err(cudaStreamSynchronize(s));
+        dfree(dout, s);
+        SCC_TRY(rc);
+    }
+    *npairs = (int64_t)tot;
+    return SCC_OK;
+}
+
+int scc_debug_hashbag(const int32_t* items, int64_t count, int32_t lambda, int32_t sigma, int32_t* out, int64_t* nout,
+                      int32_t* chunks, void* stream) {
+    if (!items || !out || !nout || count < 1 || lambda < 1024 || (lambda & (lambda - 1)) || sigma < 1)
+        return SCC_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    int32_t *din = nullptr, *dout = nullptr;
+    SCC_TRY(dalloc_t(&din, (size_t)count, s));
+    SCC_TRY(dalloc_t(&dout, (size_t)count, s));
+    int rc = to_device(din, items, sizeof(int32_t) * (size_t)count, s);
+    int64_t got = 0;
+    int ch = 0;
+    if (rc == SCC_OK) rc = run_bag_only(din, count, lambda, sigma, dout, &got, &ch, s);
+    if (rc == SCC_OK && got > count) rc = SCC_ERR_INTERNAL;
+    if (rc == SCC_OK) rc = from_device(out, dout, sizeof(int32_t) * (size_t)got, s);
+    if (rc == SCC_OK) rc = cuda_err(cudaStreamSynchronize(s));
+    dfree(din, s);
+    dfree(dout, s);
+    cudaStreamSynchronize(s);
+    SCC_TRY(rc);
+    *nout = got;
+    if (chunks) *chunks = ch;
+    return SCC_OK;
+}
+
+int scc_debug_pair_table(const uint64_t* keys, int64_t count, int64_t init_cap, uint64_t* out, int64_t* nout,
+                         int32_t* resizes, void* stream) {
+    if (!keys || !out || !nout || count < 1 || init_cap < 1024 || (init_cap & (init_cap - 1)))
+        return SCC_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    unsigned long long *dk = nullptr, *tab = nullptr, *cnt = nullptr, *dout = nullptr;
+    int* ovf = nullptr;
+    SCC_TRY(dalloc_t(&dk, (size_t)count, s));
+    SCC_TRY(dalloc_t(&cnt, 2, s));
+    SCC_TRY(dalloc_t(&ovf, 1, s));
+    SCC_TRY(dalloc_t(&dout, (size_t)count, s));
+    SCC_TRY(to_device(dk, keys, sizeof(uint64_t) * (size_t)count, s));
+    // insert in slices; when a slice pushes the load over 1/2 (or a probe runs
+    // too far) the table doubles and every key is rehashed (Sec. 4.5 regrowth)
+    int64_t cap = init_cap;
+    SCC_TRY(dalloc_t(&tab, (size_t)cap, s));
+    SCC_CUDA(cudaMemsetAsync(tab, 0xff, (size_t)cap * 8, s));
+    SCC_CUDA(cudaMemsetAsync(cnt, 0, 16, s));
+    int nres = 0;
+    const int64_t slice = 4096;
+    for (int64_t b = 0; b < count;) {
+        int64_t c = std::min(slice, count - b);
+        SCC_CUDA(cudaMemsetAsync(ovf, 0, sizeof(int), s));
+        SCC_TRY(launch_table_insert(dk + b, c, tab, cap, ovf, cnt, s));
+        unsigned long long hc = 0;
+        int hov = 0;
+        SCC_CUDA(cudaMemcpyAsync(&hc, cnt, 8, cudaMemcpyDeviceToHost, s));
+        SCC_CUDA(cudaMemcpyAsync(&hov, ovf, 4, cudaMemcpyDeviceToHost, s));
+        SCC_CUDA(cudaStreamSynchronize(s));
+        if (hov || 2 * (int64_t)hc > cap) {
+            unsigned long long* t2 = nullptr;
+            SCC_TRY(dalloc_t(&t2, (size_t)cap * 2, s));
+            SCC_CUDA(cudaMemsetAsync(t2, 0xff, (size_t)cap * 16, s));
+            SCC_CUDA(cudaMemsetAsync(ovf, 0, sizeof(int), s));
+            SCC_TRY(launch_table_rehash(tab, cap, t2, cap * 2, ovf, s));
+            dfree(tab, s);
+            tab = t2;
+            cap *= 2;
+            ++nres;
+            if (hov) {  // keys of the slice may be missing: insert the slice again
+                SCC_CUDA(cudaMemsetAsync(cnt, 0, 8, s));
+                continue;
+            }
+        }
+        b += c;
+    }
+    SCC_CUDA(cudaMemsetAsync(cnt + 1, 0, 8, s));
+    SCC_TRY(launch_table_gather(tab, cap, dout, count, cnt + 1, s));
+    unsigned long long tot = 0;
+    SCC_CUDA(cudaMemcpyAsync(&tot, cnt + 1, 8, cudaMemcpyDeviceToHost, s));
+    SCC_CUDA(cudaStreamSynchronize(s));
+    int rc = (int64_t)tot <= count ? from_device(out, dout, sizeof(uint64_t) * (size_t)tot, s) : SCC_ERR_INTERNAL;
+    if (rc == SCC_OK) rc = cuda_err(cudaStreamSynchronize(s));
+    dfree(dk, s);
+    dfree(tab, s);
+    dfree(cnt, s);
+    dfree(ovf, s);
+    dfree(dout, s);
+    cudaStreamSynchronize(s);
+    SCC_TRY(rc);
+    *nout = (int64_t)tot;
+    if (resizes) *resizes = nres;
+    return SCC_OK;
+}
+
+}  // extern "C"

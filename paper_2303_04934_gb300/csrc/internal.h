@@ -1,0 +1,173 @@
+// Host-side declarations shared by the library's translation units.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/scc.h"
+
+namespace scc {
+
+struct EngineCtl;
+
+// ------------------------------------------------------------------ errors --
+inline int cuda_err(cudaError_t e) {
+    if (e == cudaSuccess) return SCC_OK;
+    if (e == cudaErrorMemoryAllocation) return SCC_ERR_OOM;
+    return SCC_ERR_CUDA;
+}
+#define SCC_TRY(expr)                         \
+    do {                                      \
+        int _rc = (expr);                     \
+        if (_rc != SCC_OK) return _rc;        \
+    } while (0)
+#define SCC_CUDA(expr) SCC_TRY(::scc::cuda_err(expr))
+#define SCC_LAUNCH() SCC_TRY(::scc::cuda_err(cudaGetLastError()))
+
+// Stream-ordered device allocation from the default pool.
+int dalloc(void** p, size_t bytes, cudaStream_t s);
+void dfree(void* p, cudaStream_t s);
+template <class T>
+inline int dalloc_t(T** p, size_t count, cudaStream_t s) {
+    return dalloc(reinterpret_cast<void**>(p), count * sizeof(T), s);
+}
+
+// True when p is device (or managed) memory.
+bool is_device_ptr(const void* p);
+
+struct DeviceInfo {
+    int dev = -1;
+    int num_sms = 0;
+};
+int device_info(DeviceInfo* out);
+
+// --------------------------------------------------------- graph building --
+// Validate a CSR on the device; *bad (device int) becomes nonzero if malformed.
+int launch_validate(const int32_t* off, const int32_t* adj, int32_t n, int64_t m, int* bad, cudaStream_t s);
+// indeg[v] += number of arcs u->v with u != v; selfrow[u] += self-loops of u.
+int launch_count_arcs(const int32_t* off, const int32_t* adj, int32_t n, int64_t m, int32_t* indeg,
+                      int32_t* selfrow, unsigned long long* nself, cudaStream_t s);
+// Exclusive scan of int32 counts: out[0..n] with out[n] = total. tmp: scan_tmp_bytes(n).
+size_t scan_tmp_bytes(int64_t n);
+int launch_scan(const int32_t* in, int32_t* out, int64_t n, void* tmp, cudaStream_t s);
+// Copy G without self-loops: off2 already scanned from per-row non-self counts.
+int launch_drop_self_loops(const int32_t* off, const int32_t* adj, int32_t n, int64_t m, const int32_t* selfrow,
+                           const int32_t* off2, int32_t* adj2, cudaStream_t s);
+// cnt[u] = out-arcs of u that are not self-loops.
+int launch_row_nonself(const int32_t* off, const int32_t* selfrow, int32_t n, int32_t* cnt, cudaStream_t s);
+// Scatter every non-self arc (u,v) to row v of G^T; cursor[v] starts at toff[v].
+int launch_transpose_scatter(const int32_t* off, const int32_t* adj, int32_t n, int64_t m, int32_t* cursor,
+                             int32_t* tadj, cudaStream_t s);
+
+// ------------------------------------------------------------- SCC steps --
+// trimmed flags from the self-loop-free CSRs (Sec. 4.1).
+int launch_trim(const int32_t* off, const int32_t* toff, int32_t n, uint8_t* flags, cudaStream_t s);
+// label[v] = trimmed ? kDone : 0, rep[v] = trimmed ? v : -1; counts active into *nact.
+int launch_init_labels(const int32_t* off, const int32_t* toff, int32_t n, int32_t* label, int32_t* rep,
+                       unsigned long long* nact, cudaStream_t s);
+// act = increasing list of v with label[v] >= 0 (scan-based, order preserving).
+int launch_compact_active(const int32_t* label, int32_t n, int32_t* flags_tmp, int32_t* pos_tmp, void* scan_tmp,
+                          int32_t* act, cudaStream_t s);
+// sources = { act[pi(p)] : p in [p0, p1), label >= 0 }, *k = count (device).
+int launch_batch_sources(const int32_t* act, int64_t N, uint64_t seed, int64_t p0, int64_t p1, const int32_t* label,
+                         int32_t* sources, int* k, cudaStream_t s);
+// order[p] = act[pi(p)] for p < N (debug hook).
+int launch_pivot_order(const int32_t* act, int64_t N, uint64_t seed, int32_t* order, cudaStream_t s);
+
+// Host copy of the Feistel permutation, for the first pivot (identical definition).
+int64_t feistel_perm_host(int64_t p, int64_t N, uint64_t seed);
+
+// bitmap bit v = (label == NULL ? done-free : label[v] != L)  (pre-set "not in class")
+int launch_prefill_bits(const int32_t* label, int32_t L, int32_t n, uint32_t* bits, cudaStream_t s);
+// visited[v] = bit v of bits AND label[v] == L (undo the prefill) -> uint8
+int launch_bits_to_bytes(const uint32_t* bits, const int32_t* label, int32_t L, int32_t n, uint8_t* out,
+                         cudaStream_t s);
+
+// Round-0 labelling from the two visited bitmaps of pivot s (Alg. 1 label step
+// with one source). Adds the number of finished vertices to *ndone.
+int launch_label_first(const uint32_t* bf, const uint32_t* bb, int32_t n, int32_t s, int32_t* label, int32_t* rep,
+                       unsigned long long* ndone, cudaStream_t s_);
+
+// Labelling after a multi-reachability round (Alg. 1; Sec. 4.4).
+int launch_label_pairs(const unsigned long long* tf, int64_t capf, const unsigned long long* tb, int64_t capb,
+                       uint32_t round_tag, unsigned long long* fmax, unsigned long long* bmax,
+                       unsigned long long* hit, int32_t* label, int32_t* rep, unsigned long long* ndone,
+                       cudaStream_t s);
+
+// labels_out[v] = min{u : rep[u] == rep[v]} (canonical minimum).
+int launch_canonicalize(const int32_t* rep, int32_t n, int32_t* minid, int32_t* labels_out, int* bad,
+                        cudaStream_t s);
+
+// mask[sources[j]] |= 1 << j; *bad = 1 if a source is outside [0, n).
+int launch_mask_init(const int32_t* sources, int32_t k, int32_t n, unsigned long long* mask, int* bad,
+                     cudaStream_t s);
+// out = the sources with label >= 0 (count in *cnt); *bad = 1 if one is outside [0, n).
+int launch_filter_sources(const int32_t* in, int32_t k, int32_t n, const int32_t* label, int32_t* out, int* cnt,
+                          int* bad, cudaStream_t s);
+
+// Gather pair-table contents (non-empty keys) into out; *count (device) total.
+int launch_table_gather(const unsigned long long* tab, int64_t cap, unsigned long long* out, int64_t out_cap,
+                        unsigned long long* count, cudaStream_t s);
+// Rehash every key of src (capacity src_cap) into dst (capacity dst_cap, empty).
+int launch_table_rehash(const unsigned long long* src, int64_t src_cap, unsigned long long* dst, int64_t dst_cap,
+                        int* overflow, cudaStream_t s);
+// Insert keys (debug): dst table capacity cap.
+int launch_table_insert(const unsigned long long* keys, int64_t count, unsigned long long* tab, int64_t cap,
+                        int* overflow, unsigned long long* inserted, cudaStream_t s);
+
+// ---------------------------------------------------------------- engine --
+// Buffers of one engine instance (item type = 4 or 8 bytes).
+struct EngineBuf {
+    int item_bytes = 0;
+    void* slots = nullptr;
+    long long nslots = 0;
+    void* front = nullptr;
+    long long front_cap = 0;
+    void* hub_item = nullptr;
+    int32_t* hub_beg = nullptr;
+    int32_t* hub_deg = nullptr;
+    long long* hub_segbase = nullptr;
+    int hub_cap = 0;
+    int32_t* segmap = nullptr;
+    long long segmap_cap = 0;
+    EngineCtl* ctl = nullptr;
+    int lambda = 0;
+    void* init = nullptr;      // staging of the initial items
+    size_t init_bytes = 0;
+};
+// Allocate (or keep, if large enough) buffers for at most `items` items per round.
+int engine_reserve(EngineBuf* b, int item_bytes, long long items, int lambda, int64_t m, cudaStream_t s);
+void engine_release(EngineBuf* b, cudaStream_t s);
+
+struct EngineRun {
+    int err = 0;
+    int overflow = 0;
+    int rounds = 0;
+    int max_chunk = 0;
+    unsigned long long edges = 0;
+    unsigned long long inserted = 0;
+};
+
+struct EngineOpts {
+    int tau = 512;
+    int seeds = 32;
+    int sigma = 50;
+    int block = 256;
+    int num_sms = 0;
+};
+
+// Single reachability from `s` over (off, adj) with the bitmap (already prefilled).
+int run_single(const int32_t* off, const int32_t* adj, int32_t n, int32_t s, uint32_t* bits, EngineBuf* b,
+               const EngineOpts& o, EngineRun* out, cudaStream_t st);
+// Multi reachability: init pairs (s,s) from sources (device int32[k]); pairs into table.
+int run_pairs(const int32_t* off, const int32_t* adj, int32_t n, const int32_t* label, const int32_t* sources,
+              int32_t k, unsigned long long* table, int64_t cap, long long max_inserted, EngineBuf* b,
+              const EngineOpts& o, EngineRun* out, cudaStream_t st);
+// Mask reachability: mask already holds the source bits; init = sources.
+int run_mask(const int32_t* off, const int32_t* adj, int32_t n, const int32_t* sources, int32_t k,
+             unsigned long long* mask, EngineBuf* b, const EngineOpts& o, EngineRun* out, cudaStream_t st);
+
+// Debug: hash bag alone (vertex items).
+int run_bag_only(const int32_t* items, int64_t count, int lambda, int sigma, int32_t* out, int64_t* nout,
+                 int* chunks, cudaStream_t st);
+
+}  // namespace scc

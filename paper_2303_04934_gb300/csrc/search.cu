@@ -1,0 +1,271 @@
+// Reachability searches: instantiation and cooperative launch of the VGC /
+// hash-bag engine (engine.cuh) for single-reachability (first SCC, Sec. 4.2),
+// multi-reachability (Alg. 1; Sec. 4.3) and plain multi-source masks.
+#include <algorithm>
+#include <cstring>
+
+#include "common.cuh"
+#include "engine.cuh"
+#include "internal.h"
+
+namespace scc {
+
+namespace {
+
+constexpr int kEngineBlock = 256;
+
+__global__ void k_pairs_from_sources(const int32_t* __restrict__ src, int32_t k, uint64_t* out) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < k; i += gridDim.x * blockDim.x) {
+        uint32_t s = (uint32_t)src[i];
+        out[i] = ((uint64_t)s << 32) | s;
+    }
+}
+
+template <class Pol>
+int coop_grid(int num_sms, int* grid) {
+    static int cached = -1;
+    if (cached < 0) {
+        int per_sm = 0;
+        SCC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, engine_kernel<Pol>, kEngineBlock, 0));
+        if (per_sm < 1) return SCC_ERR_CUDA;
+        cached = per_sm;
+    }
+    *grid = cached * num_sms;
+    return SCC_OK;
+}
+
+template <class Pol>
+int launch_engine(EngineParams<typename Pol::Item>& P, Pol& pol, const EngineOpts& o, EngineRun* out,
+                  cudaStream_t st) {
+    int grid = 0;
+    SCC_TRY(coop_grid<Pol>(o.num_sms, &grid));
+    SCC_CUDA(cudaMemsetAsync(P.ctl, 0, sizeof(EngineCtl), st));
+    void* args[] = {(void*)&P, (void*)&pol};
+    SCC_CUDA(cudaLaunchCooperativeKernel((const void*)engine_kernel<Pol>, dim3(grid), dim3(kEngineBlock), args, 0, st));
+    EngineCtl h;
+    SCC_CUDA(cudaMemcpyAsync(&h, P.ctl, sizeof(EngineCtl), cudaMemcpyDeviceToHost, st));
+    SCC_CUDA(cudaStreamSynchronize(st));
+    out->err = h.err;
+    out->overflow = h.overflow;
+    out->rounds = h.rounds;
+    out->max_chunk = h.max_chunk;
+    out->edges = h.edges;
+    out->inserted = h.inserted;
+    if (h.err != 0 && h.err != SCC_ERR_CAPACITY) return h.err;
+    return SCC_OK;
+}
+
+template <class Item>
+EngineParams<Item> make_params(const int32_t* off, const int32_t* adj, int32_t n, EngineBuf* b,
+                               const EngineOpts& o) {
+    EngineParams<Item> P;
+    memset(&P, 0, sizeof(P));
+    P.off = off;
+    P.adj = adj;
+    P.n = n;
+    P.tau = o.tau;
+    P.hub_thr = o.tau;
+    P.seeds = o.seeds;
+    P.slots = (Item*)b->slots;
+    P.nslots = b->nslots;
+    P.lambda = b->lambda;
+    P.sigma = o.sigma;
+    P.front = (Item*)b->front;
+    P.front_cap = b->front_cap;
+    P.hub_item = (Item*)b->hub_item;
+    P.hub_beg = b->hub_beg;
+    P.hub_deg = b->hub_deg;
+    P.hub_segbase = b->hub_segbase;
+    P.hub_cap = b->hub_cap;
+    P.segmap = b->segmap;
+    P.segmap_cap = b->segmap_cap;
+    P.ctl = b->ctl;
+    return P;
+}
+
+int reserve_init(EngineBuf* b, size_t bytes, cudaStream_t st) {
+    if (b->init && b->init_bytes >= bytes) return SCC_OK;
+    dfree(b->init, st);
+    b->init = nullptr;
+    size_t want = std::max<size_t>(bytes, 1 << 16);
+    SCC_TRY(dalloc(&b->init, want, st));
+    b->init_bytes = want;
+    return SCC_OK;
+}
+
+// Restore an all-empty bag after a run that stopped early (error or overflow).
+int reset_slots(EngineBuf* b, cudaStream_t st) {
+    SCC_CUDA(cudaMemsetAsync(b->slots, 0xff, (size_t)b->nslots * b->item_bytes, st));
+    return SCC_OK;
+}
+
+}  // namespace
+
+int engine_reserve(EngineBuf* b, int item_bytes, long long items, int lambda, int64_t m, cudaStream_t s) {
+    if (items < 1) items = 1;
+    long long need_slots = std::max<long long>(4 * items, 4ll * lambda);
+    if (b->slots && b->item_bytes == item_bytes && b->nslots >= need_slots && b->lambda == lambda &&
+        b->front_cap >= items)
+        return SCC_OK;
+    engine_release(b, s);
+    b->item_bytes = item_bytes;
+    b->lambda = lambda;
+    b->nslots = need_slots;
+    b->front_cap = items;
+    b->hub_cap = (int)std::min<long long>(items, 1ll << 22);
+    b->segmap_cap = 2 * (m / kHubSeg) + b->hub_cap + 1024;
+    SCC_TRY(dalloc(&b->slots, (size_t)b->nslots * item_bytes, s));
+    SCC_TRY(dalloc(&b->front, (size_t)b->front_cap * item_bytes, s));
+    SCC_TRY(dalloc(&b->hub_item, (size_t)b->hub_cap * item_bytes, s));
+    SCC_TRY(dalloc_t(&b->hub_beg, b->hub_cap, s));
+    SCC_TRY(dalloc_t(&b->hub_deg, b->hub_cap, s));
+    SCC_TRY(dalloc_t(&b->hub_segbase, b->hub_cap, s));
+    SCC_TRY(dalloc_t(&b->segmap, b->segmap_cap, s));
+    SCC_TRY(dalloc(reinterpret_cast<void**>(&b->ctl), sizeof(EngineCtl), s));
+    SCC_CUDA(cudaMemsetAsync(b->slots, 0xff, (size_t)b->nslots * item_bytes, s));
+    return SCC_OK;
+}
+
+void engine_release(EngineBuf* b, cudaStream_t s) {
+    dfree(b->slots, s);
+    dfree(b->front, s);
+    dfree(b->hub_item, s);
+    dfree(b->hub_beg, s);
+    dfree(b->hub_deg, s);
+    dfree(b->hub_segbase, s);
+    dfree(b->segmap, s);
+    dfree(b->ctl, s);
+    dfree(b->init, s);
+    *b = EngineBuf();
+}
+
+int run_single(const int32_t* off, const int32_t* adj, int32_t n, int32_t s, uint32_t* bits, EngineBuf* b,
+               const EngineOpts& o, EngineRun* out, cudaStream_t st) {
+    auto P = make_params<uint32_t>(off, adj, n, b, o);
+    SCC_TRY(reserve_init(b, sizeof(uint32_t), st));
+    SCC_CUDA(cudaMemcpyAsync(b->init, &s, sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    P.init = reinterpret_cast<const uint32_t*>(b->init);
+    P.ninit = 1;
+    PolSingle pol{bits};
+    int rc = launch_engine(P, pol, o, out, st);
+    if (rc != SCC_OK || out->err) SCC_TRY(reset_slots(b, st));
+    SCC_TRY(rc);
+    return out->err ? out->err : SCC_OK;
+}
+
+int run_pairs(const int32_t* off, const int32_t* adj, int32_t n, const int32_t* label, const int32_t* sources,
+              int32_t k, unsigned long long* table, int64_t cap, long long max_inserted, EngineBuf* b,
+              const EngineOpts& o, EngineRun* out, cudaStream_t st) {
+    auto P = make_params<uint64_t>(off, adj, n, b, o);
+    SCC_TRY(reserve_init(b, (size_t)k * sizeof(uint64_t), st));
+    uint64_t* init = reinterpret_cast<uint64_t*>(b->init);
+    k_pairs_from_sources<<<std::max(1, std::min(1024, (k + 255) / 256)), 256, 0, st>>>(sources, k, init);
+    SCC_LAUNCH();
+    P.init = init;
+    P.ninit = k;
+    P.max_inserted = max_inserted;
+    PolPair pol;
+    pol.label = label;
+    pol.tab.keys = table;
+    pol.tab.mask = (unsigned long long)(cap - 1);
+    pol.tab.overflow = &b->ctl->overflow;
+    pol.ins = 0;
+    int rc = launch_engine(P, pol, o, out, st);
+    if (rc != SCC_OK || out->err || out->overflow) {
+        int r2 = reset_slots(b, st);
+        if (rc == SCC_OK) rc = r2;
+    }
+    SCC_TRY(rc);
+    return out->err ? out->err : SCC_OK;
+}
+
+int run_mask(const int32_t* off, const int32_t* adj, int32_t n, const int32_t* sources, int32_t k,
+             unsigned long long* mask, EngineBuf* b, const EngineOpts& o, EngineRun* out, cudaStream_t st) {
+    auto P = make_params<uint32_t>(off, adj, n, b, o);
+    P.init = reinterpret_cast<const uint32_t*>(sources);
+    P.ninit = k;
+    PolMask pol{mask};
+    int rc = launch_engine(P, pol, o, out, st);
+    if (rc != SCC_OK || out->err) SCC_TRY(reset_slots(b, st));
+    SCC_TRY(rc);
+    return out->err ? out->err : SCC_OK;
+}
+
+// ---------------------------------------------------------- hash bag test --
+namespace {
+
+struct BagOnlyParams {
+    uint32_t* slots;
+    long long nslots;
+    int lambda;
+    int sigma;
+    EngineCtl* ctl;
+};
+
+__global__ void __launch_bounds__(256) k_bag_only(BagOnlyParams P, const int32_t* __restrict__ items, long long count,
+                                                  int32_t* out) {
+    const int lane = lane_id();
+    const uint32_t wid = (uint32_t)(blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5));
+    const uint32_t nwarps = (uint32_t)(gridDim.x * (blockDim.x >> 5));
+    SegState st{-1, 0, wid * 2654435761u};
+    // every warp pushes a strided share, a few items at a time, as spills do
+    for (long long b = (long long)wid * 32; b < count; b += (long long)nwarps * 32) {
+        long long i = b + lane;
+        bool has = i < count;
+        uint32_t it = has ? (uint32_t)items[i] : 0u;
+        // split each group of 32 into two pushes to exercise partial segments
+        bag_push<uint32_t>(P, &P.ctl->bag[0], st, has && lane < 13, it, wid, 0);
+        bag_push<uint32_t>(P, &P.ctl->bag[0], st, has && lane >= 13, it, wid, 0);
+    }
+    if (!grid_sync(&P.ctl->bar, &P.ctl->err)) return;
+    // ExtractAll: warp-aggregated compaction of the used prefix
+    const int r = ld_volatile(&P.ctl->bag[0].r);
+    const long long end = chunk_end(P.lambda, r, P.nslots);
+    for (long long b = (long long)wid * 32; b < end; b += (long long)nwarps * 32) {
+        long long i = b + lane;
+        uint32_t x = i < end ? P.slots[i] : Sent<uint32_t>::empty;
+        bool valid = x != Sent<uint32_t>::empty && x != Sent<uint32_t>::claimed;
+        if (i < end && x != Sent<uint32_t>::empty) P.slots[i] = Sent<uint32_t>::empty;
+        uint32_t msk = __ballot_sync(kFull, valid);
+        long long base = 0;
+        if (lane == 0 && msk)
+            base = (long long)atomicAdd((unsigned long long*)&P.ctl->fsize[0], (unsigned long long)__popc(msk));
+        base = __shfl_sync(kFull, base, 0);
+        if (valid) out[base + __popc(msk & lanemask_lt())] = (int32_t)x;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) P.ctl->rounds = r;
+}
+
+}  // namespace
+
+int run_bag_only(const int32_t* items, int64_t count, int lambda, int sigma, int32_t* out, int64_t* nout,
+                 int* chunks, cudaStream_t st) {
+    DeviceInfo di;
+    SCC_TRY(device_info(&di));
+    BagOnlyParams P;
+    P.lambda = lambda;
+    P.sigma = sigma;
+    P.nslots = std::max<long long>(4 * count, 4ll * lambda);
+    SCC_TRY(dalloc(reinterpret_cast<void**>(&P.slots), (size_t)P.nslots * 4, st));
+    SCC_TRY(dalloc(reinterpret_cast<void**>(&P.ctl), sizeof(EngineCtl), st));
+    SCC_CUDA(cudaMemsetAsync(P.slots, 0xff, (size_t)P.nslots * 4, st));
+    SCC_CUDA(cudaMemsetAsync(P.ctl, 0, sizeof(EngineCtl), st));
+    int per_sm = 0;
+    SCC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bag_only, 256, 0));
+    int grid = std::max(1, per_sm) * di.num_sms;
+    void* args[] = {(void*)&P, (void*)&items, (void*)&count, (void*)&out};
+    int rc = cuda_err(cudaLaunchCooperativeKernel((const void*)k_bag_only, dim3(grid), dim3(256), args, 0, st));
+    EngineCtl h;
+    memset(&h, 0, sizeof(h));
+    if (rc == SCC_OK) rc = cuda_err(cudaMemcpyAsync(&h, P.ctl, sizeof(EngineCtl), cudaMemcpyDeviceToHost, st));
+    if (rc == SCC_OK) rc = cuda_err(cudaStreamSynchronize(st));
+    dfree(P.slots, st);
+    dfree(P.ctl, st);
+    SCC_TRY(rc);
+    if (h.err) return h.err;
+    *nout = h.fsize[0];
+    if (chunks) *chunks = h.rounds + 1;
+    return SCC_OK;
+}
+
+}  // namespace scc

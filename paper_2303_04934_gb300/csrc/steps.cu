@@ -1,0 +1,708 @@
+// SCC steps other than the reachability searches (sm_103a):
+//  - CSR validation, transposed-CSR construction (histogram, scan, scatter);
+//  - trimming (Sec. 4.1);
+//  - pivot permutation and prefix-doubling batches (Alg. 1; Sec. 2);
+//  - labelling/partition after the first SCC and after each multi-search round
+//    (Alg. 1; Sec. 4.4);
+//  - canonical minimum labels.
+// Paper: Wang, Dong, Gu, Sun, "Parallel Strong Connectivity Based on Faster
+// Reachability", SIGMOD 2023.
+#include <climits>
+
+#include "common.cuh"
+#include "engine.cuh"
+#include "internal.h"
+
+namespace scc {
+
+namespace {
+
+constexpr int kBlk = 256;
+constexpr int kEdgeTile = kBlk * 8;  // arcs per block tile in the CSR passes
+
+inline int grid_for(int64_t work, int per_block, int cap = 152 * 32) {
+    int64_t g = (work + per_block - 1) / per_block;
+    if (g < 1) g = 1;
+    if (g > cap) g = cap;
+    return (int)g;
+}
+
+// Largest r in [lo, hi] with off[r] <= e (off non-decreasing, off[lo] <= e).
+__device__ __forceinline__ int row_of(const int32_t* __restrict__ off, int lo, int hi, int64_t e) {
+    while (lo < hi) {
+        int mid = lo + ((hi - lo + 1) >> 1);
+        if ((int64_t)__ldg(&off[mid]) <= e) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Row range of the arcs [e0, e1) of a tile, found once per block.
+__device__ __forceinline__ void tile_rows(const int32_t* off, int32_t n, int64_t e0, int64_t e1, int* r0, int* r1) {
+    __shared__ int s_r[2];
+    if (threadIdx.x == 0) {
+        s_r[0] = row_of(off, 0, n - 1, e0);
+        s_r[1] = row_of(off, s_r[0], n - 1, e1 - 1);
+    }
+    __syncthreads();
+    *r0 = s_r[0];
+    *r1 = s_r[1];
+    __syncthreads();
+}
+
+// ---------------------------------------------------------------- validate --
+__global__ void k_validate(const int32_t* __restrict__ off, const int32_t* __restrict__ adj, int32_t n, int64_t m,
+                           int* bad) {
+    int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    if (tid == 0 && (off[0] != 0 || (int64_t)off[n] != m)) atomicExch(bad, 1);
+    for (int64_t i = tid; i < n; i += stride)
+        if (off[i] > off[i + 1]) atomicExch(bad, 1);
+    for (int64_t e = tid; e < m; e += stride) {
+        int32_t t = adj[e];
+        if (t < 0 || t >= n) atomicExch(bad, 1);
+    }
+}
+
+// -------------------------------------------------------------- arc counts --
+// Per arc (u, v): u != v -> indeg[v]++ (warp-aggregated over equal v with
+// __match_any_sync, which turns hub in-degrees into one atomic per warp);
+// u == v -> selfrow[u]++.
+__global__ void __launch_bounds__(kBlk) k_count_arcs(const int32_t* __restrict__ off, const int32_t* __restrict__ adj,
+                                                     int32_t n, int64_t m, int32_t* indeg, int32_t* selfrow,
+                                                     unsigned long long* nself) {
+    unsigned long long my_self = 0;
+    for (int64_t t0 = (int64_t)blockIdx.x * kEdgeTile; t0 < m; t0 += (int64_t)gridDim.x * kEdgeTile) {
+        int64_t t1 = t0 + kEdgeTile < m ? t0 + kEdgeTile : m;
+        int r0, r1;
+        tile_rows(off, n, t0, t1, &r0, &r1);
+        for (int64_t e = t0 + threadIdx.x; e - threadIdx.x < t1; e += blockDim.x) {
+            int key = -1;
+            if (e < t1) {
+                int u = row_of(off, r0, r1, e);
+                int v = __ldg(&adj[e]);
+                if (u == v) {
+                    atomicAdd(&selfrow[u], 1);
+                    ++my_self;
+                } else {
+                    key = v;
+                }
+            }
+            uint32_t peers = __match_any_sync(kFull, key);
+            int leader = __ffs(peers) - 1;
+            if (key >= 0 && lane_id() == leader) atomicAdd(&indeg[key], __popc(peers));
+        }
+    }
+    if (my_self) atomicAdd(nself, my_self);
+}
+
+// G^T scatter: row v gets u for every arc (u, v), u != v; one atomic per group
+// of lanes with equal v.
+__global__ void __launch_bounds__(kBlk) k_transpose_scatter(const int32_t* __restrict__ off,
+                                                            const int32_t* __restrict__ adj, int32_t n, int64_t m,
+                                                            int32_t* cursor, int32_t* tadj) {
+    for (int64_t t0 = (int64_t)blockIdx.x * kEdgeTile; t0 < m; t0 += (int64_t)gridDim.x * kEdgeTile) {
+        int64_t t1 = t0 + kEdgeTile < m ? t0 + kEdgeTile : m;
+        int r0, r1;
+        tile_rows(off, n, t0, t1, &r0, &r1);
+        for (int64_t e = t0 + threadIdx.x; e - threadIdx.x < t1; e += blockDim.x) {
+            int key = -1, u = -1;
+            if (e < t1) {
+                u = row_of(off, r0, r1, e);
+                int v = __ldg(&adj[e]);
+                if (u != v) key = v;
+            }
+            uint32_t peers = __match_any_sync(kFull, key);
+            int leader = __ffs(peers) - 1;
+            int base = 0;
+            if (key >= 0 && lane_id() == leader) base = atomicAdd(&cursor[key], __popc(peers));
+            base = __shfl_sync(kFull, base, leader);
+            if (key >= 0) tadj[base + __popc(peers & lanemask_lt())] = u;
+        }
+    }
+}
+
+// Forward CSR without self-loops. Rows without self-loops are copied arc-parallel;
+// rows with self-loops (rare) are copied by one thread each.
+__global__ void __launch_bounds__(kBlk) k_drop_self_arcs(const int32_t* __restrict__ off,
+                                                         const int32_t* __restrict__ adj, int32_t n, int64_t m,
+                                                         const int32_t* __restrict__ selfrow,
+                                                         const int32_t* __restrict__ off2, int32_t* adj2) {
+    for (int64_t t0 = (int64_t)blockIdx.x * kEdgeTile; t0 < m; t0 += (int64_t)gridDim.x * kEdgeTile) {
+        int64_t t1 = t0 + kEdgeTile < m ? t0 + kEdgeTile : m;
+        int r0, r1;
+        tile_rows(off, n, t0, t1, &r0, &r1);
+        for (int64_t e = t0 + threadIdx.x; e < t1; e += blockDim.x) {
+            int u = row_of(off, r0, r1, e);
+            if (selfrow[u] == 0) adj2[off2[u] + (e - off[u])] = adj[e];
+        }
+    }
+}
+__global__ void k_drop_self_rows(const int32_t* __restrict__ off, const int32_t* __restrict__ adj, int32_t n,
+                                 const int32_t* __restrict__ selfrow, const int32_t* __restrict__ off2,
+                                 int32_t* adj2) {
+    for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n; u += (int64_t)gridDim.x * blockDim.x) {
+        if (selfrow[u] == 0) continue;
+        int o = off2[u];
+        for (int e = off[u]; e < off[u + 1]; ++e)
+            if (adj[e] != u) adj2[o++] = adj[e];
+    }
+}
+__global__ void k_sub(const int32_t* __restrict__ off, const int32_t* __restrict__ selfrow, int32_t n, int32_t* out) {
+    for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n; u += (int64_t)gridDim.x * blockDim.x)
+        out[u] = off[u + 1] - off[u] - selfrow[u];
+}
+
+// ------------------------------------------------------------------- scan --
+constexpr int kScanItems = 8;
+constexpr int kScanTile = kBlk * kScanItems;
+
+__device__ __forceinline__ long long block_excl_scan(long long x, long long* total) {
+    __shared__ long long s_w[kBlk / 32];
+    const int lane = lane_id(), w = threadIdx.x >> 5;
+    long long incl = x;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        long long y = __shfl_up_sync(kFull, incl, d);
+        if (lane >= d) incl += y;
+    }
+    if (lane == 31) s_w[w] = incl;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        long long s = 0;
+        for (int i = 0; i < kBlk / 32; ++i) {
+            long long c = s_w[i];
+            s_w[i] = s;
+            s += c;
+        }
+        *total = s;
+    }
+    __syncthreads();
+    long long r = s_w[w] + incl - x;
+    __syncthreads();
+    return r;
+}
+
+__global__ void __launch_bounds__(kBlk) k_scan_reduce(const int32_t* __restrict__ in, int64_t n, long long* sums) {
+    int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+    long long s = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k)
+        if (base + k < n) s += in[base + k];
+    __shared__ long long tot;
+    block_excl_scan(s, &tot);
+    if (threadIdx.x == 0) sums[blockIdx.x] = tot;
+}
+__global__ void __launch_bounds__(1024) k_scan_sums(long long* sums, int64_t nb, long long* total) {
+    // one block: each thread owns a contiguous run of block sums
+    __shared__ long long s_part[1024];
+    int64_t per = (nb + 1023) / 1024;
+    int64_t b0 = (int64_t)threadIdx.x * per, b1 = b0 + per < nb ? b0 + per : nb;
+    long long s = 0;
+    for (int64_t i = b0; i < b1; ++i) s += sums[i];
+    s_part[threadIdx.x] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        long long a = 0;
+        for (int i = 0; i < 1024; ++i) {
+            long long c = s_part[i];
+            s_part[i] = a;
+            a += c;
+        }
+        *total = a;
+    }
+    __syncthreads();
+    long long a = s_part[threadIdx.x];
+    for (int64_t i = b0; i < b1; ++i) {
+        long long c = sums[i];
+        sums[i] = a;
+        a += c;
+    }
+}
+__global__ void __launch_bounds__(kBlk) k_scan_down(const int32_t* __restrict__ in, int32_t* out, int64_t n,
+                                                   const long long* __restrict__ sums, const long long* total) {
+    int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+    int32_t v[kScanItems];
+    long long s = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        v[k] = base + k < n ? in[base + k] : 0;
+        s += v[k];
+    }
+    __shared__ long long tot;
+    long long pre = block_excl_scan(s, &tot) + sums[blockIdx.x];
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        if (base + k < n) out[base + k] = (int32_t)pre;
+        pre += v[k];
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) out[n] = (int32_t)*total;
+}
+
+// ------------------------------------------------------------------- trim --
+__global__ void k_trim(const int32_t* __restrict__ off, const int32_t* __restrict__ toff, int32_t n, uint8_t* flags) {
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
+        flags[v] = (off[v + 1] == off[v]) || (toff[v + 1] == toff[v]);
+}
+
+__global__ void k_init_labels(const int32_t* __restrict__ off, const int32_t* __restrict__ toff, int32_t n,
+                              int32_t* label, int32_t* rep, unsigned long long* nact) {
+    unsigned long long c = 0;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+        bool tr = (off[v + 1] == off[v]) || (toff[v + 1] == toff[v]);
+        label[v] = tr ? kDone : 0;
+        rep[v] = tr ? (int32_t)v : -1;
+        c += !tr;
+    }
+    for (int d = 16; d >= 1; d >>= 1) c += __shfl_xor_sync(kFull, c, d);
+    if (lane_id() == 0 && c) atomicAdd(nact, c);
+}
+
+// ----------------------------------------------------------------- pivots --
+// Seeded bijection of [0, N): 4-round balanced Feistel network on the smallest
+// even bit width b >= 2 with 2^b >= N, round function low(b/2) bits of
+// mix64(key_r ^ R), key_r = mix64(seed + (r + 1) * golden), then cycle walking
+// into [0, N) (Black & Rogaway, CT-RSA 2002).
+struct Feistel {
+    uint64_t key[4];
+    int half;
+    uint64_t mask;
+    __host__ __device__ void init(uint64_t seed, uint64_t N) {
+        for (int r = 0; r < 4; ++r) key[r] = mix64(seed + (uint64_t)(r + 1) * 0x9E3779B97F4A7C15ull);
+        int b = 2;
+        while (b < 62 && (1ull << b) < N) b += 2;
+        half = b / 2;
+        mask = (1ull << half) - 1;
+    }
+    __host__ __device__ uint64_t once(uint64_t x) const {
+        uint64_t L = x >> half, R = x & mask;
+        for (int r = 0; r < 4; ++r) {
+            uint64_t F = mix64(key[r] ^ R) & mask;
+            uint64_t t = L ^ F;
+            L = R;
+            R = t;
+        }
+        return (L << half) | R;
+    }
+    __host__ __device__ uint64_t perm(uint64_t p, uint64_t N) const {
+        uint64_t y = once(p);
+        while (y >= N) y = once(y);
+        return y;
+    }
+};
+
+__global__ void k_pivot_order(const int32_t* __restrict__ act, int64_t N, Feistel f, int32_t* order) {
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < N; p += (int64_t)gridDim.x * blockDim.x)
+        order[p] = act[f.perm((uint64_t)p, (uint64_t)N)];
+}
+
+__global__ void k_batch_sources(const int32_t* __restrict__ act, int64_t N, Feistel f, int64_t p0, int64_t p1,
+                                const int32_t* __restrict__ label, int32_t* sources, int* k) {
+    for (int64_t b = p0 + (int64_t)blockIdx.x * blockDim.x; b < p1; b += (int64_t)gridDim.x * blockDim.x) {
+        int64_t p = b + threadIdx.x;
+        int v = -1;
+        if (p < p1) {
+            v = act[f.perm((uint64_t)p, (uint64_t)N)];
+            if (label[v] < 0) v = -1;
+        }
+        uint32_t msk = __ballot_sync(kFull, v >= 0);
+        int base = 0;
+        if (lane_id() == 0 && msk) base = atomicAdd(k, __popc(msk));
+        base = __shfl_sync(kFull, base, 0);
+        if (v >= 0) sources[base + __popc(msk & lanemask_lt())] = v;
+    }
+}
+
+__global__ void k_active_flags(const int32_t* __restrict__ label, int32_t n, int32_t* flags) {
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
+        flags[v] = label[v] >= 0;
+}
+__global__ void k_scatter_active(const int32_t* __restrict__ flags, const int32_t* __restrict__ pos, int32_t n,
+                                 int32_t* act) {
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
+        if (flags[v]) act[pos[v]] = (int32_t)v;
+}
+
+// --------------------------------------------------------------- bitmaps --
+__global__ void k_prefill_bits(const int32_t* __restrict__ label, int32_t L, int32_t n, uint32_t* bits) {
+    int64_t nw = (n + 31) / 32;
+    for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < nw; w += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t b = 0;
+        for (int i = 0; i < 32; ++i) {
+            int64_t v = w * 32 + i;
+            bool out = v >= n || (label != nullptr && label[v] != L);
+            b |= (uint32_t)out << i;
+        }
+        bits[w] = b;
+    }
+}
+__global__ void k_bits_to_bytes(const uint32_t* __restrict__ bits, const int32_t* __restrict__ label, int32_t L,
+                                int32_t n, uint8_t* out) {
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+        bool in = label == nullptr || label[v] == L;
+        out[v] = in && ((bits[v >> 5] >> (v & 31)) & 1u);
+    }
+}
+
+// ---------------------------------------------------------------- labels --
+// After the first SCC (one pivot s, class L = label[s]): a vertex of class L
+// reached both ways is finished with representative s; otherwise its class
+// becomes hash(L, s if reached from s, s if it reaches s) (Alg. 1 label step).
+__global__ void k_label_first(const uint32_t* __restrict__ bf, const uint32_t* __restrict__ bb, int32_t n, int32_t s,
+                              int32_t L, int32_t* label, int32_t* rep, unsigned long long* ndone) {
+    unsigned long long c = 0;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+        if (label[v] != L) continue;
+        bool f = (bf[v >> 5] >> (v & 31)) & 1u, b = (bb[v >> 5] >> (v & 31)) & 1u;
+        if (f && b) {
+            label[v] = kDone;
+            rep[v] = s;
+            ++c;
+        } else if (f || b) {
+            label[v] = class_hash(L, f ? s : -1, b ? s : -1);
+        }
+    }
+    for (int d = 16; d >= 1; d >>= 1) c += __shfl_xor_sync(kFull, c, d);
+    if (lane_id() == 0 && c) atomicAdd(ndone, c);
+}
+
+// Pass 1 over T_out: per vertex the largest source reaching it (round-tagged
+// 64-bit max, so no reset between rounds) and, if the pair is also in T_in, the
+// largest source in R1 n R2.
+__global__ void k_label_scan_fwd(const unsigned long long* __restrict__ tf, int64_t capf, PairTable tb,
+                                 unsigned long long tag, unsigned long long* fmax, unsigned long long* hit) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < capf; i += (int64_t)gridDim.x * blockDim.x) {
+        unsigned long long key = tf[i];
+        if (key == ~0ull) continue;
+        uint32_t v = (uint32_t)(key >> 32), s = (uint32_t)key;
+        atomicMax(&fmax[v], tag | s);
+        if (tb.contains(key)) atomicMax(&hit[v], tag | s);
+    }
+}
+__global__ void k_label_scan_bwd(const unsigned long long* __restrict__ tb, int64_t capb, unsigned long long tag,
+                                 unsigned long long* bmax) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < capb; i += (int64_t)gridDim.x * blockDim.x) {
+        unsigned long long key = tb[i];
+        if (key == ~0ull) continue;
+        atomicMax(&bmax[(uint32_t)(key >> 32)], tag | (uint32_t)key);
+    }
+}
+// Pass 2: exactly one table entry per touched vertex (the one carrying its
+// maximum) rewrites its label: finished (rep = max of R1 n R2) or the hash of its
+// old class and its two maxima.
+__device__ __forceinline__ void finalize_vertex(uint32_t v, unsigned long long tag, const unsigned long long* fmax,
+                                                const unsigned long long* bmax, const unsigned long long* hit,
+                                                int32_t* label, int32_t* rep, unsigned long long& c) {
+    unsigned long long h = hit[v], f = fmax[v], b = bmax[v];
+    if ((h & 0xffffffff00000000ull) == tag) {
+        label[v] = kDone;
+        rep[v] = (int32_t)(uint32_t)h;
+        ++c;
+    } else {
+        int32_t a = (f & 0xffffffff00000000ull) == tag ? (int32_t)(uint32_t)f : -1;
+        int32_t bb = (b & 0xffffffff00000000ull) == tag ? (int32_t)(uint32_t)b : -1;
+        label[v] = class_hash(label[v], a, bb);
+    }
+}
+__global__ void k_label_finalize(const unsigned long long* __restrict__ tf, int64_t capf,
+                                 const unsigned long long* __restrict__ tb, int64_t capb, unsigned long long tag,
+                                 const unsigned long long* fmax, const unsigned long long* bmax,
+                                 const unsigned long long* hit, int32_t* label, int32_t* rep,
+                                 unsigned long long* ndone) {
+    unsigned long long c = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < capf + capb;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        bool fw = i < capf;
+        unsigned long long key = fw ? tf[i] : tb[i - capf];
+        if (key == ~0ull) continue;
+        uint32_t v = (uint32_t)(key >> 32), s = (uint32_t)key;
+        unsigned long long f = fmax[v];
+        bool owner;
+        if (fw) owner = f == (tag | s);
+        else owner = (f & 0xffffffff00000000ull) != tag && bmax[v] == (tag | s);
+        if (owner) finalize_vertex(v, tag, fmax, bmax, hit, label, rep, c);
+    }
+    for (int d = 16; d >= 1; d >>= 1) c += __shfl_xor_sync(kFull, c, d);
+    if (lane_id() == 0 && c) atomicAdd(ndone, c);
+}
+
+// ---------------------------------------------------------- canonicalise --
+__global__ void k_fill_i32(int32_t* p, int64_t n, int32_t v) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        p[i] = v;
+}
+__global__ void k_min_of_rep(const int32_t* __restrict__ rep, int32_t n, int32_t* minid, int* bad) {
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+        int r = rep[v];
+        if (r < 0 || r >= n) {
+            atomicExch(bad, 1);
+            continue;
+        }
+        atomicMin(&minid[r], (int32_t)v);
+    }
+}
+__global__ void k_write_labels(const int32_t* __restrict__ rep, int32_t n, const int32_t* __restrict__ minid,
+                               int32_t* out) {
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+        int r = rep[v];
+        out[v] = (r >= 0 && r < n) ? minid[r] : -1;
+    }
+}
+
+// ------------------------------------------------------------- pair table --
+__global__ void k_table_gather(const unsigned long long* __restrict__ tab, int64_t cap, unsigned long long* out,
+                               int64_t out_cap, unsigned long long* count) {
+    for (int64_t b = (int64_t)blockIdx.x * blockDim.x; b < cap; b += (int64_t)gridDim.x * blockDim.x) {
+        int64_t i = b + threadIdx.x;
+        unsigned long long k = i < cap ? tab[i] : ~0ull;
+        uint32_t msk = __ballot_sync(kFull, k != ~0ull);
+        unsigned long long base = 0;
+        if (lane_id() == 0 && msk) base = atomicAdd(count, (unsigned long long)__popc(msk));
+        base = __shfl_sync(kFull, base, 0);
+        unsigned long long pos = base + __popc(msk & lanemask_lt());
+        if (k != ~0ull && (int64_t)pos < out_cap) out[pos] = k;
+    }
+}
+__global__ void k_table_insert(const unsigned long long* __restrict__ keys, int64_t count, PairTable t,
+                               unsigned long long* inserted) {
+    unsigned long long c = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x)
+        c += t.insert(keys[i]);
+    for (int d = 16; d >= 1; d >>= 1) c += __shfl_xor_sync(kFull, c, d);
+    if (lane_id() == 0 && c && inserted) atomicAdd(inserted, c);
+}
+
+}  // namespace
+
+// ================================================================ launchers ==
+int launch_validate(const int32_t* off, const int32_t* adj, int32_t n, int64_t m, int* bad, cudaStream_t s) {
+    k_validate<<<grid_for(n > m ? n : m, kBlk * 4), kBlk, 0, s>>>(off, adj, n, m, bad);
+    SCC_LAUNCH();
+    return SCC_OK;
+}
+
+int launch_count_arcs(const int32_t* off, const int32_t* adj, int32_t n, int64_t m, int32_t* indeg,
+                      int32_t* selfrow, unsigned long long* nself, cudaStream_t s) {
+    if (m == 0 || n == 0) return SCC_OK;
+    k_count_arcs<<<grid_for(m, kEdgeTile, 152 * 16), kBlk, 0, s>>>(off, adj, n, m, indeg, selfrow, nself);
+    SCC_LAUNCH();
+    return SCC_OK;
+}
+
+size_t scan_tmp_bytes(int64_t n) { return (size_t)(ceil_div(n + 1, kScanTile) + 2) * sizeof(long long); }
+
+int launch_scan(const int32_t* in, int32_t* out, int64_t n, void* tmp, cudaStream_t s) {
+    int64_t nb = ceil_div(n > 0 ? n : 1, kScanTile);
+    long long* sums = (long long*)tmp;
+    long long* total = sums + nb;
+    k_scan_reduce<<<(unsigned)nb, kBlk, 0, s>>>(in, n, sums);
+    SCC_LAUNCH();
+    k_scan_sums<<<1, 1024, 0, s>>>(sums, nb, total);
+    SCC_LAUNCH();
+    k_scan_down<<<(unsigned)nb, kBlk, 0, s>>>(in, out, n, sums, total);
+    SCC_LAUNCH();
+    return SCC_OK;
+}
+
+int launch_drop_self_loops(const int32_t* off, const int32_t* adj, int32_t n, int64_t m, const int32_t* selfrow,
+                           const int32_t* off2, int32_t* adj2, cudaStream_t s) {
+    if (m > 0) {
+        k_drop_self_arcs<<<grid_for(m, kEdgeTile, 152 * 16), kBlk, 0, s>>>(off, adj, n, m, selfrow, off2, adj2);
+        SCC_LAUNCH();
+    }
+    k_drop_self_rows<<<grid_for(n, kBlk), kBlk, 0, s>>>(off, adj, n, selfrow, off2, adj2);
+    SCC_LAUNCH();
+    return SCC_OK;
+}
+
+int launch_row_nonself(const int32_t* off, const int32_t* selfrow, int32_t n, int32_t* cnt, cudaStream_t s) {
+    if (n == 0) return SCC_OK;
+    k_sub<<<grid_for(n, kBlk), kBlk, 0, s>>>(off, selfrow, n, cnt);
+    SCC_LAUNCH();
+    return SCC_OK;
+}
+
+namespace {
+__global__ void k_mask_init(const int32_t* __restrict__ src, int32_t k, int32_t n, unsigned long long* mask, int* bad) {
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= k) return;
+    int v = src[j];
+    if (v < 0 || v >= n) {
+        atomicExch(bad, 1);
+        return;
+    }
+    atomicOr(&mask[v], 1ull << j);
+}
+__global__ void k_filter_sources(const int32_t* __restrict__ in, int32_t k, int32_t n,
+                                 const int32_t* __restrict__ label, int32_t* out, int* cnt, int* bad) {
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < k; j += gridDim.x * blockDim.x) {
+        int v = in[j];
+        if (v < 0 || v >= n) {
+            atomicExch(bad, 1);
+            continue;
+        }
+        if (label[v] >= 0) out[atomicAdd(cnt, 1)] = v;
+    }
+}
+}  // namespace
+
+int launch_mask_init(const int32_t* sources, int32_t k, int32_t n, unsigned long long* mask, int* bad,
+                     cudaStream_t s) {
+    k_mask_init<<<1, 64, 0, s>>>(sources, k, n, mask, bad);
+    SCC_LAUNCH();
+    return SCC_OK;
+}
+
+int launch_filter_sources(const int32_t* in, int32_t k, int32_t n, const int32_t* label, int32_t* out, int* cnt,
+                          int* bad, cudaStream_t s) {
+    k_filter_sources<<<grid_for(k, kBlk), kBlk, 0, s>>>(in, k, n, label, out, cnt, bad);
+    SCC_LAUNCH();
+    return SCC_OK;
+}
+
+int launch_transpose_scatter(const int32_t* off, const int32_t* adj, int32_t n, int64_t m, int32_t* cursor,
+                             int32_t* tadj, cudaStream_t s) {
+    if (m == 0 || n == 0) return SCC_OK;
+    k_transpose_scatter<<<grid_for(m, kEdgeTile, 152 * 16), kBlk, 0, s>>>(off, adj, n, m, cursor, tadj);
+    SCC_LAUNCH();
+    return SCC_OK;
+}
+
+int launch_trim(const int32_t* off, const int32_t* toff, int32_t n, uint8_t* flags, cudaStream_t s) {
+    if (n == 0) return SCC_OK;
+    k_trim<<<grid_for(n, kBlk), kBlk, 0, s>>>(off, toff, n, flags);
+    SCC_LAUNCH();
+    return SCC_OK;
+}
+
+int launch_init_labels(const int32_t* off, const int32_t* toff, int32_t n, int32_t* label, int32_t* rep,
+                       unsigned long long* nact, cudaStream_t s) {
+    if (n == 0) return SCC_OK;
+    k_init_labels<<<grid_for(n, kBlk), kBlk, 0, s>>>(off, toff, n, label, rep, nact);
+    SCC_LAUNCH();
+    return SCC_OK;
+}
+
+int launch_compact_active(const int32_t* label, int32_t n, int32_t* flags_tmp, int32_t* pos_tmp, void* scan_tmp,
+                          int32_t* act, cudaStream_t s) {
+    if (n == 0) return SCC_OK;
+    k_active_flags<<<grid_for(n, kBlk), kBlk, 0, s>>>(label, n, flags_tmp);
+    SCC_LAUNCH();
+    SCC_TRY(launch_scan(flags_tmp, pos_tmp, n, scan_tmp, s));
+    k_scatter_active<<<grid_for(n, kBlk), kBlk, 0, s>>>(flags_tmp, pos_tmp, n, act);
+    SCC_LAUNCH();
+    return SCC_OK;
+}
+
+int64_t feistel_perm_host(int64_t p, int64_t N, uint64_t seed) {
+    Feistel f;
+    f.init(seed, (uint64_t)N);
+    return (int64_t)f.perm((uint64_t)p, (uint64_t)N);
+}
+
+int launch_batch_sources(const int32_t* act, int64_t N, uint64_t seed, int64_t p0, int64_t p1, const int32_t* label,
+                         int32_t* sources, int* k, cudaStream_t s) {
+    if (p1 <= p0) return SCC_OK;
+    Feistel f;
+    f.init(seed, (uint64_t)N);
+    k_batch_sources<<<grid_for(p1 - p0, kBlk), kBlk, 0, s>>>(act, N, f, p0, p1, label, sources, k);
+    SCC_LAUNCH();
+    return SCC_OK;
+}
+
+int launch_pivot_order(const int32_t* act, int64_t N, uint64_t seed, int32_t* order, cudaStream_t s) {
+    if (N == 0) return SCC_OK;
+    Feistel f;
+    f.init(seed, (uint64_t)N);
+    k_pivot_order<<<grid_for(N, kBlk), kBlk, 0, s>>>(act, N, f, order);
+    SCC_LAUNCH();
+    return SCC_OK;
+}
+
+int launch_prefill_bits(const int32_t* label, int32_t L, int32_t n, uint32_t* bits, cudaStream_t s) {
+    int64_t nw = (n + 31) / 32;
+    if (nw == 0) return SCC_OK;
+    k_prefill_bits<<<grid_for(nw, kBlk), kBlk, 0, s>>>(label, L, n, bits);
+    SCC_LAUNCH();
+    return SCC_OK;
+}
+
+int launch_bits_to_bytes(const uint32_t* bits, const int32_t* label, int32_t L, int32_t n, uint8_t* out,
+                         cudaStream_t s) {
+    if (n == 0) return SCC_OK;
+    k_bits_to_bytes<<<grid_for(n, kBlk), kBlk, 0, s>>>(bits, label, L, n, out);
+    SCC_LAUNCH();
+    return SCC_OK;
+}
+
+int launch_label_first(const uint32_t* bf, const uint32_t* bb, int32_t n, int32_t s, int32_t* label, int32_t* rep,
+                       unsigned long long* ndone, cudaStream_t st) {
+    if (n == 0) return SCC_OK;
+    // the class of the pivot is 0 in the first round (every untrimmed vertex)
+    k_label_first<<<grid_for(n, kBlk), kBlk, 0, st>>>(bf, bb, n, s, 0, label, rep, ndone);
+    SCC_LAUNCH();
+    return SCC_OK;
+}
+
+int launch_label_pairs(const unsigned long long* tf, int64_t capf, const unsigned long long* tb, int64_t capb,
+                       uint32_t round_tag, unsigned long long* fmax, unsigned long long* bmax,
+                       unsigned long long* hit, int32_t* label, int32_t* rep, unsigned long long* ndone,
+                       cudaStream_t s) {
+    unsigned long long tag = (unsigned long long)round_tag << 32;
+    PairTable tbt{const_cast<unsigned long long*>(tb), (unsigned long long)(capb - 1), nullptr};
+    k_label_scan_fwd<<<grid_for(capf, kBlk), kBlk, 0, s>>>(tf, capf, tbt, tag, fmax, hit);
+    SCC_LAUNCH();
+    k_label_scan_bwd<<<grid_for(capb, kBlk), kBlk, 0, s>>>(tb, capb, tag, bmax);
+    SCC_LAUNCH();
+    k_label_finalize<<<grid_for(capf + capb, kBlk), kBlk, 0, s>>>(tf, capf, tb, capb, tag, fmax, bmax, hit, label,
+                                                                    rep, ndone);
+    SCC_LAUNCH();
+    return SCC_OK;
+}
+
+int launch_canonicalize(const int32_t* rep, int32_t n, int32_t* minid, int32_t* labels_out, int* bad,
+                        cudaStream_t s) {
+    if (n == 0) return SCC_OK;
+    k_fill_i32<<<grid_for(n, kBlk), kBlk, 0, s>>>(minid, n, INT_MAX);
+    SCC_LAUNCH();
+    k_min_of_rep<<<grid_for(n, kBlk), kBlk, 0, s>>>(rep, n, minid, bad);
+    SCC_LAUNCH();
+    k_write_labels<<<grid_for(n, kBlk), kBlk, 0, s>>>(rep, n, minid, labels_out);
+    SCC_LAUNCH();
+    return SCC_OK;
+}
+
+int launch_table_gather(const unsigned long long* tab, int64_t cap, unsigned long long* out, int64_t out_cap,
+                        unsigned long long* count, cudaStream_t s) {
+    k_table_gather<<<grid_for(cap, kBlk), kBlk, 0, s>>>(tab, cap, out, out_cap, count);
+    SCC_LAUNCH();
+    return SCC_OK;
+}
+
+namespace {
+__global__ void k_table_rehash(const unsigned long long* __restrict__ src, int64_t src_cap, PairTable dst) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < src_cap; i += (int64_t)gridDim.x * blockDim.x) {
+        unsigned long long k = src[i];
+        if (k != ~0ull) dst.insert(k);
+    }
+}
+}  // namespace
+
+int launch_table_rehash(const unsigned long long* src, int64_t src_cap, unsigned long long* dst, int64_t dst_cap,
+                        int* overflow, cudaStream_t s) {
+    PairTable t{dst, (unsigned long long)(dst_cap - 1), overflow};
+    k_table_rehash<<<grid_for(src_cap, kBlk), kBlk, 0, s>>>(src, src_cap, t);
+    SCC_LAUNCH();
+    return SCC_OK;
+}
+
+int launch_table_insert(const unsigned long long* keys, int64_t count, unsigned long long* tab, int64_t cap,
+                        int* overflow, unsigned long long* inserted, cudaStream_t s) {
+    if (count == 0) return SCC_OK;
+    PairTable t{tab, (unsigned long long)(cap - 1), overflow};
+    k_table_insert<<<grid_for(count, kBlk), kBlk, 0, s>>>(keys, count, t, inserted);
+    SCC_LAUNCH();
+    return SCC_OK;
+}
+
+}  // namespace scc

@@ -1,0 +1,271 @@
+"""Thin Python binding of the C ABI in ``include/scc.h`` / ``include/scc_debug.h``.
+
+Argument marshalling only: every step runs in the CUDA library
+``_lib/libscc_gb300.so``. Arrays may be CUDA torch tensors (device pointers are
+passed) or numpy arrays / CPU tensors (host pointers are passed; the library
+copies). Streams are ``torch.cuda.Stream`` objects or None (torch's current
+stream). There is no CPU fallback: if the library is missing, loading fails.
+
+The function names are those of the C ABI.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+SCC_OK = 0
+SCC_ERR_INVALID_ARG = -1
+SCC_ERR_OOM = -2
+SCC_ERR_CUDA = -3
+SCC_ERR_TIMEOUT = -4
+SCC_ERR_CAPACITY = -5
+SCC_ERR_INTERNAL = -6
+
+#: every symbol the headers declare (checked by tests/test_abi_symbols.py)
+EXPORTED = [
+    "scc_error_string", "scc_config_default", "scc_graph_create", "scc_graph_destroy", "scc_set_config",
+    "scc_run", "reach_multi", "scc_get_stats",
+    "scc_graph_info", "scc_debug_csr", "scc_debug_trim", "scc_debug_pivot_order", "scc_debug_single_reach",
+    "scc_debug_multi_reach", "scc_debug_hashbag", "scc_debug_pair_table",
+]
+
+
+class scc_config(ctypes.Structure):
+    _fields_ = [("tau", ctypes.c_int32), ("beta", ctypes.c_double), ("lambda_", ctypes.c_int32),
+                ("sigma", ctypes.c_int32), ("block", ctypes.c_int32), ("seeds", ctypes.c_int32),
+                ("dense", ctypes.c_int32), ("seed", ctypes.c_uint64)]
+
+
+class scc_stats(ctypes.Structure):
+    _fields_ = [("n_trimmed", ctypes.c_int32), ("first_scc_size", ctypes.c_int32), ("batches", ctypes.c_int32),
+                ("search_rounds", ctypes.c_int32), ("pairs", ctypes.c_int64), ("table_resizes", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("ms_trim", ctypes.c_double), ("ms_first_scc", ctypes.c_double),
+                ("ms_multi_search", ctypes.c_double), ("ms_resize", ctypes.c_double), ("ms_label", ctypes.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
+
+
+class SccError(RuntimeError):
+    def __init__(self, code, what):
+        super().__init__(f"{what}: {error_string(code)} ({code})")
+        self.code = code
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.SO_PATH
+
+
+def load() -> ctypes.CDLL:
+    """Load the CUDA library (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.SO_PATH
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library {path} is missing: run __graft_entry__.build() "
+                           "(or python -m paper_2303_04934_gb300.build) first")
+    lib = ctypes.CDLL(path)
+    vp, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+    P = ctypes.POINTER
+    sig = {
+        "scc_error_string": ([ctypes.c_int], ctypes.c_char_p),
+        "scc_config_default": ([P(scc_config)], ctypes.c_int),
+        "scc_graph_create": ([i32, i64, vp, vp, vp, P(vp)], ctypes.c_int),
+        "scc_graph_destroy": ([vp], ctypes.c_int),
+        "scc_set_config": ([vp, P(scc_config)], ctypes.c_int),
+        "scc_run": ([vp, vp, vp], ctypes.c_int),
+        "reach_multi": ([vp, vp, i32, i32, vp, vp], ctypes.c_int),
+        "scc_get_stats": ([vp, P(scc_stats)], ctypes.c_int),
+        "scc_graph_info": ([vp, P(i32), P(i64), P(i64)], ctypes.c_int),
+        "scc_debug_csr": ([vp, i32, vp, vp, vp], ctypes.c_int),
+        "scc_debug_trim": ([vp, vp, vp], ctypes.c_int),
+        "scc_debug_pivot_order": ([vp, vp, P(i32), vp], ctypes.c_int),
+        "scc_debug_single_reach": ([vp, vp, i32, i32, vp, vp], ctypes.c_int),
+        "scc_debug_multi_reach": ([vp, vp, vp, i32, i32, vp, i64, P(i64), i64, vp], ctypes.c_int),
+        "scc_debug_hashbag": ([vp, i64, i32, i32, vp, P(i64), P(i32), vp], ctypes.c_int),
+        "scc_debug_pair_table": ([vp, i64, i64, vp, P(i64), P(i32), vp], ctypes.c_int),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = lib
+    return lib
+
+
+def error_string(code: int) -> str:
+    try:
+        return load().scc_error_string(code).decode()
+    except Exception:  # pragma: no cover - only when the library cannot load
+        return f"error {code}"
+
+
+def _check(rc: int, what: str):
+    if rc != SCC_OK:
+        raise SccError(rc, what)
+
+
+def _ptr(a):
+    """Raw pointer of a torch tensor (device or host) or a numpy array."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return a.ctypes.data
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return a.data_ptr()
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        if not torch.cuda.is_available():
+            return None
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if hasattr(stream, "cuda_stream"):
+        return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+# ------------------------------------------------------------------- config --
+def scc_config_default() -> scc_config:
+    c = scc_config()
+    _check(load().scc_config_default(ctypes.byref(c)), "scc_config_default")
+    return c
+
+
+# ------------------------------------------------------------------- graphs --
+def scc_graph_create(n: int, m: int, offsets, targets, stream=None) -> int:
+    h = ctypes.c_void_p()
+    _check(load().scc_graph_create(n, m, _ptr(offsets), _ptr(targets), _stream(stream), ctypes.byref(h)),
+           "scc_graph_create")
+    return h.value
+
+
+def scc_graph_destroy(h) -> None:
+    _check(load().scc_graph_destroy(h), "scc_graph_destroy")
+
+
+def scc_set_config(h, cfg: scc_config) -> None:
+    _check(load().scc_set_config(h, ctypes.byref(cfg)), "scc_set_config")
+
+
+def scc_run(h, labels_out, stream=None) -> None:
+    _check(load().scc_run(h, _ptr(labels_out), _stream(stream)), "scc_run")
+
+
+def reach_multi(h, sources, k: int, dir: int, out, stream=None) -> None:
+    _check(load().reach_multi(h, _ptr(sources), k, dir, _ptr(out), _stream(stream)), "reach_multi")
+
+
+def scc_get_stats(h) -> dict:
+    s = scc_stats()
+    _check(load().scc_get_stats(h, ctypes.byref(s)), "scc_get_stats")
+    return s.as_dict()
+
+
+# -------------------------------------------------------------- debug hooks --
+def scc_graph_info(h):
+    n, m, mt = ctypes.c_int32(), ctypes.c_int64(), ctypes.c_int64()
+    _check(load().scc_graph_info(h, ctypes.byref(n), ctypes.byref(m), ctypes.byref(mt)), "scc_graph_info")
+    return n.value, m.value, mt.value
+
+
+def scc_debug_csr(h, which: int, off, adj, stream=None) -> None:
+    _check(load().scc_debug_csr(h, which, _ptr(off), _ptr(adj), _stream(stream)), "scc_debug_csr")
+
+
+def scc_debug_trim(h, flags, stream=None) -> None:
+    _check(load().scc_debug_trim(h, _ptr(flags), _stream(stream)), "scc_debug_trim")
+
+
+def scc_debug_pivot_order(h, order, stream=None) -> int:
+    na = ctypes.c_int32()
+    _check(load().scc_debug_pivot_order(h, _ptr(order), ctypes.byref(na), _stream(stream)), "scc_debug_pivot_order")
+    return na.value
+
+
+def scc_debug_single_reach(h, labels, s: int, dir: int, visited, stream=None) -> None:
+    _check(load().scc_debug_single_reach(h, _ptr(labels), s, dir, _ptr(visited), _stream(stream)),
+           "scc_debug_single_reach")
+
+
+def scc_debug_multi_reach(h, labels, sources, k: int, dir: int, pairs, cap: int, table_cap: int = 0,
+                          stream=None) -> int:
+    npairs = ctypes.c_int64()
+    _check(load().scc_debug_multi_reach(h, _ptr(labels), _ptr(sources), k, dir, _ptr(pairs), cap,
+                                        ctypes.byref(npairs), table_cap, _stream(stream)), "scc_debug_multi_reach")
+    return npairs.value
+
+
+def scc_debug_hashbag(items, count: int, lam: int, sigma: int, out, stream=None):
+    nout, chunks = ctypes.c_int64(), ctypes.c_int32()
+    _check(load().scc_debug_hashbag(_ptr(items), count, lam, sigma, _ptr(out), ctypes.byref(nout),
+                                    ctypes.byref(chunks), _stream(stream)), "scc_debug_hashbag")
+    return nout.value, chunks.value
+
+
+def scc_debug_pair_table(keys, count: int, init_cap: int, out, stream=None):
+    nout, res = ctypes.c_int64(), ctypes.c_int32()
+    _check(load().scc_debug_pair_table(_ptr(keys), count, init_cap, _ptr(out), ctypes.byref(nout),
+                                       ctypes.byref(res), _stream(stream)), "scc_debug_pair_table")
+    return nout.value, res.value
+
+
+# ------------------------------------------------------------- convenience --
+class SccGraph:
+    """Owning wrapper of a graph handle: ``SccGraph(n, offsets, targets)``."""
+
+    def __init__(self, n: int, offsets, targets, stream=None, config: scc_config | None = None):
+        self.n = int(n)
+        self.m = int(len(targets))
+        self.h = scc_graph_create(self.n, self.m, offsets, targets, stream)
+        if config is not None:
+            scc_set_config(self.h, config)
+
+    def close(self):
+        if getattr(self, "h", None):
+            scc_graph_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def labels(self, out=None, stream=None):
+        """SCC labels (min vertex id per SCC) into ``out`` (device tensor or host array)."""
+        if out is None:
+            import torch
+            out = torch.empty(self.n, dtype=torch.int32, device="cuda")
+        scc_run(self.h, out, stream)
+        return out
+
+    def reach(self, sources, dir: int = 0, out=None, stream=None):
+        import torch
+        if out is None:
+            out = torch.empty(self.n, dtype=torch.int64, device="cuda")
+        reach_multi(self.h, sources, len(sources), dir, out, stream)
+        return out
+
+    def stats(self) -> dict:
+        return scc_get_stats(self.h)

@@ -1,0 +1,101 @@
+"""GPU scc_run labels are bit-identical to the CPU oracle (iterative Tarjan,
+canonical minimum) on small, edge-case and medium graphs, for every
+configuration (tau, seeds, beta, lambda, pivot seed) and for host or device
+buffers. The labels are canonical, so any scheduling order and configuration
+must give the same bytes."""
+import itertools
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle.invariants import check_scc_labels
+from paper_2303_04934_gb300 import graphgen as gg
+from paper_2303_04934_gb300 import scc
+
+from gpu_util import config, ensure_lib, labels_of, make_graph
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    ensure_lib()
+
+
+def _check(g, cfg=None, host=False):
+    want, _ = oracle.scc_labels(g.n, g.offsets, g.targets)
+    with make_graph(g, cfg, on_device=not host) as G:
+        got = labels_of(G, host=host)
+        stats = G.stats()
+    assert np.array_equal(got, want), g.name
+    return stats
+
+
+def test_edge_cases():
+    _check(gg.from_edges(0, [], name="empty"))
+    _check(gg.from_edges(1, [], name="one"))
+    _check(gg.from_edges(1, [(0, 0)], name="one_self_loop"))
+    _check(gg.from_edges(5, [], name="no_arcs"))
+    _check(gg.from_edges(4, [(i, i) for i in range(4)], name="self_loops_only"))
+    _check(gg.from_edges(6, [(i, (i + 1) % 6) for i in range(6)], name="cycle"))
+    _check(gg.from_edges(6, [(i, i + 1) for i in range(5)], name="chain"))
+    _check(gg.from_edges(7, [(i, j) for i in range(7) for j in range(7) if i != j], name="complete"))
+    _check(gg.from_edges(6, [(0, 1), (1, 2), (2, 0), (3, 4), (4, 5), (5, 3), (2, 3)], name="two_cycles"))
+    _check(gg.from_edges(4, [(0, 1), (0, 1), (1, 0), (1, 0), (2, 3)], name="duplicates"))
+
+
+def test_all_digraphs_with_three_vertices_and_loops():
+    pairs = [(u, v) for u in range(3) for v in range(3)]
+    for mask in range(1 << 9):
+        e = [pairs[i] for i in range(9) if mask >> i & 1]
+        _check(gg.from_edges(3, e, name=f"n3_{mask}"))
+
+
+def test_random_digraphs():
+    for trial in range(120):
+        n = 1 + trial % 90
+        g = gg.gnp(n, [0.01, 0.03, 0.08, 0.2][trial % 4], seed=1000 + trial, allow_self=trial % 5 == 0)
+        _check(g)
+
+
+@pytest.mark.parametrize("make", [
+    lambda: gg.torus(2, 256, 0.5, seed=0x5CC00),          # the 2D 256^2 lattice, p = 0.5
+    lambda: gg.torus(2, 100, 0.75, seed=1),
+    lambda: gg.torus(3, 32, 0.3, seed=2),
+    lambda: gg.torus(3, 24, 0.6, seed=3),
+    lambda: gg.paper_lattice(200, 150, 0, seed=4),
+    lambda: gg.paper_lattice(200, 150, 1, seed=5),
+    lambda: gg.rmat(16, 16, seed=6),
+    lambda: gg.rmat(15, 4, seed=7),
+    lambda: gg.knn(100000, 5, seed=8),
+    lambda: gg.knn(30000, 2, seed=9),
+], ids=["torus2d_256", "torus2d_100_p75", "torus3d_32", "torus3d_24_p6", "REC_model", "RECp_model",
+        "rmat16", "rmat15_ef4", "knn100k", "knn30k_k2"])
+def test_medium_graphs(make):
+    g = make()
+    st = _check(g)
+    assert st["batches"] >= 1
+
+
+@pytest.mark.parametrize("kw", [dict(tau=1), dict(tau=16, seeds=1), dict(tau=4096), dict(beta=2.0),
+                                dict(beta=1.1), dict(lam=1024, sigma=8), dict(seed=12345), dict(seeds=4)])
+def test_configuration_does_not_change_labels(kw):
+    for g in (gg.torus(2, 64, 0.5, seed=31), gg.rmat(13, 8, seed=32), gg.knn(20000, 5, seed=33)):
+        _check(g, config(**kw))
+
+
+def test_host_buffers_and_repeat_runs():
+    g = gg.torus(3, 20, 0.4, seed=41)
+    want, _ = oracle.scc_labels(g.n, g.offsets, g.targets)
+    with make_graph(g, on_device=False) as G:
+        for _ in range(3):
+            assert np.array_equal(labels_of(G, host=True), want)
+            assert np.array_equal(labels_of(G, host=False), want)
+
+
+def test_invariants_hold_on_gpu_output():
+    g = gg.rmat(15, 8, seed=51)
+    with make_graph(g) as G:
+        lab = labels_of(G)
+    check_scc_labels(g.n, g.offsets, g.targets, lab)
