@@ -1,0 +1,338 @@
+#!/usr/bin/env python
+"""SCC throughput benchmark on GB300.
+
+One step = one pass of the whole hot path over one synthetic graph:
+scc_graph_create (device CSR -> self-loop-free CSR + transposed CSR) ->
+scc_run (trim, pivot batches, first-SCC single-reachability both ways,
+multi-reachability batches, labelling, canonical labels) -> scc_graph_destroy.
+Inputs are resident in HBM before the timed region; the CSR (> 1 GB) is larger
+than the 129 MB L2, so no explicit flush is needed between steps.
+
+Workload (default): R-MAT scale 24, edge factor 16 (a, b, c, d = .57, .19, .19,
+.05), self-loops and duplicates removed, ids permuted, seed 0x5CC01.
+
+Prints ONE JSON line (rank 0). `value` is whole-job edges/s: arcs of the input
+times steps times replicas over the max-over-ranks time. `e2e` is the same
+metric through the C ABI with HOST buffers (pinned host CSR in, host labels out,
+copies inside the timed region). `roofline` reports the reachability engine
+kernel (the dominant kernel) against the measured HBM copy bandwidth.
+`cpu_baseline` times the CPU oracle (iterative Tarjan, one thread) on the same
+graph. `--impl reference` times that oracle alone, step by step, on a bounded
+sample of the workload.
+
+Multi-GPU: the workload is one graph, which does not shard; N ranks run N
+independent replicas (no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "SCC edges/s & HBM GB/s vs peak per graph"
+UNIT = "edges/s"
+
+WORKLOADS = {
+    "rmat24": dict(kind="rmat", scale=24, ef=16, seed=0x5CC01),
+    "torus2d256": dict(kind="torus", dims=2, side=256, p=0.5, seed=0x5CC00),
+    "torus3d256": dict(kind="torus", dims=3, side=256, p=0.3, seed=0x5CC02),
+    "knn8m": dict(kind="knn", n=8_000_000, k=5, seed=0x5CC03),
+}
+
+
+def make_graph(spec, scale_override=None):
+    from paper_2303_04934_gb300 import graphgen as gg
+    if spec["kind"] == "rmat":
+        return gg.rmat(scale_override or spec["scale"], spec["ef"], seed=spec["seed"])
+    if spec["kind"] == "torus":
+        return gg.torus(spec["dims"], spec["side"], spec["p"], seed=spec["seed"])
+    if spec["kind"] == "knn":
+        return gg.knn(spec["n"], spec["k"], seed=spec["seed"])
+    raise ValueError(spec)
+
+
+def workload_name(spec, g):
+    if spec["kind"] == "rmat":
+        return f"rmat_s{spec['scale']}_ef{spec['ef']}"
+    if spec["kind"] == "torus":
+        return f"torus{spec['dims']}d_{spec['side']}_p{spec['p']}"
+    return f"knn_n{spec['n']}_k{spec['k']}"
+
+
+# ------------------------------------------------------------------ clocks --
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": []}
+        if self.proc is None:
+            return out
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            p = [x.strip() for x in line.split(",")]
+            if len(p) >= 9:
+                rows.append(p)
+        os.unlink(self.path)
+        if not rows:
+            return out
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in rows:
+            for nm, v in zip(names, r[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        out["sm_mhz"] = statistics.median(sm) if sm else None
+        out["sm_max_mhz"] = max(mx) if mx else None
+        out["reasons"] = sorted(reasons)
+        out["samples"] = len(rows)
+        return out
+
+
+# ------------------------------------------------------------- CPU oracle --
+def time_oracle(g, reps=1):
+    import oracle
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        oracle.scc_labels(g.n, g.offsets, g.targets)
+    return (time.perf_counter() - t0) / reps
+
+
+def run_reference(args, spec):
+    """--impl reference: the CPU oracle (iterative Tarjan, 1 thread) timed per
+    step on a bounded sample of the workload (same generator, smaller scale)."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    sample_spec = dict(spec)
+    if spec["kind"] == "rmat":
+        sample_scale = 20
+        g = make_graph(spec, scale_override=sample_scale)
+        sample = f"rmat_s{sample_scale}_ef{spec['ef']} (same generator and parameters, 1/16 of the vertices)"
+    else:
+        g = make_graph(sample_spec)
+        sample = "the whole workload"
+    for _ in range(args.warmup):
+        time_oracle(g)
+    ts = [time_oracle(g) for _ in range(args.steps)]
+    t = sum(ts)
+    value = g.m * args.steps / t
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+            "data": "synthetic", "config": {"workload": workload_name(spec, g), "sample": sample,
+                                            "n": g.n, "m": g.m},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------- ours --
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="rmat24", choices=sorted(WORKLOADS))
+    ap.add_argument("--tau", type=int, default=None)
+    ap.add_argument("--seeds", type=int, default=None)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--verbose", action="store_true")
+    args = ap.parse_args()
+    spec = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        return run_reference(args, spec)
+
+    import torch
+    from paper_2303_04934_gb300 import build as libbuild
+    from paper_2303_04934_gb300 import scc
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    if not os.path.exists(libbuild.SO_PATH):
+        raise RuntimeError("CUDA library not built: run python -c 'import __graft_entry__ as g; g.build()'")
+    scc.load()
+
+    t_gen = time.perf_counter()
+    g = make_graph(spec)
+    t_gen = time.perf_counter() - t_gen
+    n, m = g.n, g.m
+    stream = torch.cuda.Stream()
+    off_d = torch.from_numpy(g.offsets).to("cuda")
+    adj_d = torch.from_numpy(g.targets).to("cuda")
+    labels_d = torch.empty(n, dtype=torch.int32, device="cuda")
+    cfg = scc.scc_config_default()
+    if args.tau:
+        cfg.tau = args.tau
+    if args.seeds:
+        cfg.seeds = args.seeds
+    torch.cuda.synchronize()
+
+    def step(offp, adjp, labp):
+        h = scc.scc_graph_create(n, m, offp, adjp, stream)
+        try:
+            scc.scc_set_config(h, cfg)
+            scc.scc_run(h, labp, stream)
+            st = scc.scc_get_stats(h)
+        finally:
+            scc.scc_graph_destroy(h)
+        return st
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step(off_d, adj_d, labels_d)
+    torch.cuda.synchronize()
+
+    # ---- timed region: device-resident inputs
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    launches0 = scc.scc_debug_launch_count()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    stats = []
+    barrier()
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        ev0.record(stream)
+        for _ in range(args.steps):
+            stats.append(step(off_d, adj_d, labels_d))
+        ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    launches = scc.scc_debug_launch_count() - launches0
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * m * args.steps / (ms / 1e3)
+
+    # ---- roofline of the dominant kernel (the reachability engine)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    eng_ms = sum(s["ms_engine"] for s in stats)
+    eng_launches = sum(s["engine_launches"] for s in stats)
+    # algorithmic bytes: 4 B target id + 4 B visited/label probe per arc examined,
+    # 8 B row offsets per item expanded, 8 B per newly inserted pair (table word)
+    eng_bytes = sum(8 * s["engine_arcs"] + 8 * s["engine_items"] + 8 * s["engine_inserted"] for s in stats)
+    achieved = eng_bytes / (eng_ms / 1e3) / 1e9 if eng_ms > 0 else 0.0
+    roofline = {"bound": "hbm", "kernel": "engine_kernel (VGC reachability)", "achieved": achieved,
+                "peak": hbm_peak, "peak_source": peak_src, "unit": "GB/s", "frac": achieved / hbm_peak,
+                "traffic": None, "launches_per_step": eng_launches / max(1, len(stats)),
+                "share_of_step": (eng_ms / ms) if ms > 0 else None}
+
+    # ---- end to end through the C ABI with host buffers
+    e2e = None
+    if not args.no_e2e:
+        off_h = torch.from_numpy(g.offsets).pin_memory()
+        adj_h = torch.from_numpy(g.targets).pin_memory()
+        lab_h = torch.empty(n, dtype=torch.int32).pin_memory()
+        k2 = max(1, min(args.steps, 3))
+        with torch.cuda.stream(stream):
+            step(off_h, adj_h, lab_h)
+            torch.cuda.synchronize()
+            barrier()
+            t0 = time.perf_counter()
+            for _ in range(k2):
+                step(off_h, adj_h, lab_h)
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+        barrier()
+        te = t1 - t0
+        if dist is not None:
+            t = torch.tensor([te], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            te = float(t.item())
+        e2e = {"value": world * m * k2 / te, "unit": UNIT, "h2d_bytes_per_step": 4 * (n + 1) + 4 * m,
+               "d2h_bytes_per_step": 4 * n, "steps": k2}
+
+    # ---- CPU oracle on the host cores (rank 0, N = 1 only)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        if m > 400_000_000:
+            sample_scale = 22
+            gs = make_graph(spec, scale_override=sample_scale)
+            sample = f"rmat_s{sample_scale}_ef{spec['ef']} (same generator and parameters, 1/4 of the vertices), 1 run"
+        else:
+            gs, sample = g, "the whole workload, 1 run"
+        tcpu = time_oracle(gs)
+        cpu = {"value": gs.m / tcpu, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
+               "host_cores": os.cpu_count(), "seconds": tcpu}
+
+    last = stats[-1]
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": workload_name(spec, g), "n": n, "m": m, "seed": spec["seed"],
+                       "parallelism": f"replicas{world}", "l2": "inputs larger than L2 (CSR + transpose > 2 GB)",
+                       "tau": cfg.tau, "seeds": cfg.seeds, "beta": cfg.beta, "lambda": cfg.lambda_,
+                       "step": "scc_graph_create + scc_run + scc_graph_destroy"},
+            "e2e": e2e, "roofline": roofline, "cpu_baseline": cpu, "gpu_launches": launches,
+            "clocks": clk}
+    if args.verbose:
+        line["breakdown_last_step"] = last
+        line["gen_seconds"] = t_gen
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

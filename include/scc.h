@@ -154,8 +154,12 @@ typedef struct scc_stats {
     int32_t search_rounds;     /* reachability rounds (frontier swaps), all searches */
     int64_t pairs;             /* reachability pairs inserted by multi-reachability */
     int32_t table_resizes;     /* pair-table regrowths */
-    int32_t reserved;
+    int32_t engine_launches;   /* launches of the reachability engine kernel */
     double ms_trim, ms_first_scc, ms_multi_search, ms_resize, ms_label;
+    double ms_engine;          /* summed duration of the engine launches */
+    int64_t engine_arcs;       /* arcs examined by the engine */
+    int64_t engine_items;      /* frontier/queue items expanded (adjacency rows read) */
+    int64_t engine_inserted;   /* items newly visited (first SCC: vertices; later: pairs) */
 } scc_stats;
 
 SCC_API int scc_get_stats(scc_handle h, scc_stats* out);

@@ -91,6 +91,9 @@ SCC_API int scc_debug_hashbag(const int32_t* items, int64_t count, int32_t lambd
 SCC_API int scc_debug_pair_table(const uint64_t* keys, int64_t count, int64_t init_cap, uint64_t* out,
                          int64_t* nout, int32_t* resizes, void* stream);
 
+/* Number of kernel launches the library has issued since it was loaded. */
+SCC_API int64_t scc_debug_launch_count(void);
+
 #ifdef __cplusplus
 }
 #endif

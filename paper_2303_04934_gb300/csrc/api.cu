@@ -2,7 +2,9 @@
 // driver (Alg. 1 with the paper's Sec. 4 engineering), multi-source
 // reachability and the step-level test hooks.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
+#include <mutex>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -49,10 +51,41 @@ struct scc_graph {
 
 namespace scc {
 
+static std::atomic<long long> g_launches{0};
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+long long launch_count() { return g_launches.load(); }
+
+// The library's stream-ordered allocations come from its own memory pool on the
+// current device, whose release threshold keeps freed memory for reuse: creating
+// and destroying graphs of similar size then costs no new device mappings.
+static cudaMemPool_t library_pool() {
+    static std::mutex mu;
+    static cudaMemPool_t pools[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+    std::lock_guard<std::mutex> lk(mu);
+    if (!pools[dev]) {
+        cudaMemPoolProps props = {};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t p = nullptr;
+        if (cudaMemPoolCreate(&p, &props) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        uint64_t thr = ~0ull;
+        cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &thr);
+        pools[dev] = p;
+    }
+    return pools[dev];
+}
+
 int dalloc(void** p, size_t bytes, cudaStream_t s) {
     *p = nullptr;
     if (bytes == 0) bytes = 16;
-    cudaError_t e = cudaMallocAsync(p, bytes, s);
+    cudaMemPool_t pool = library_pool();
+    cudaError_t e = pool ? cudaMallocFromPoolAsync(p, bytes, pool, s) : cudaMallocAsync(p, bytes, s);
     if (e != cudaSuccess) {
         cudaGetLastError();
         *p = nullptr;
@@ -203,6 +236,11 @@ int multi_search(scc_graph* h, int32_t k, int64_t b_active, int64_t a_prev[2], i
             int rc = run_pairs(off, adj, h->n, h->label, h->sources, k, h->tab[d], cap, max_ins, &h->eb64, o, &r, s);
             double ms = t.stop();
             *rounds += r.rounds;
+            h->stats.engine_launches++;
+            h->stats.ms_engine += r.ms;
+            h->stats.engine_arcs += (int64_t)r.edges;
+            h->stats.engine_items += (int64_t)r.items;
+            h->stats.engine_inserted += (int64_t)r.inserted;
             if (rc == SCC_ERR_CAPACITY || r.overflow) {
                 *ms_resize += ms;
                 h->stats.table_resizes++;
@@ -456,6 +494,12 @@ static int scc_run_impl(scc_graph* h, int32_t* labels_out, cudaStream_t s) {
         st.ms_first_scc = t.stop();
         st.first_scc_size = (int32_t)hc[1];
         st.search_rounds += r0.rounds + r1.rounds;
+        for (const EngineRun* r : {&r0, &r1}) {
+            st.engine_launches++;
+            st.ms_engine += r->ms;
+            st.engine_arcs += (int64_t)r->edges;
+            st.engine_items += (int64_t)r->items;
+        }
         st.batches = 1;
 
         // ---- multi-reachability batches (Alg. 1; Sec. 4.3-4.5)
@@ -697,6 +741,8 @@ int scc_debug_multi_reach(scc_handle h, const int32_t* labels, const int32_t* so
     *npairs = (int64_t)tot;
     return SCC_OK;
 }
+
+int64_t scc_debug_launch_count(void) { return launch_count(); }
 
 int scc_debug_hashbag(const int32_t* items, int64_t count, int32_t lambda, int32_t sigma, int32_t* out, int64_t* nout,
                       int32_t* chunks, void* stream) {

@@ -69,6 +69,7 @@ struct EngineCtl {
     BagCtl bag[2];
     unsigned long long edges;     // arcs examined
     unsigned long long inserted;  // newly visited items (pairs in pair mode)
+    unsigned long long items;     // items expanded (adjacency rows read)
 };
 
 template <class Item>
@@ -198,7 +199,8 @@ template <class Pol>
 __device__ __forceinline__ void expand_batch(const EngineParams<typename Pol::Item>& P, Pol& pol, BagCtl* bc,
                                              SegState& st, uint32_t wid, uint32_t round,
                                              typename Pol::Item* q, uint32_t& qh, uint32_t& qt, int& t,
-                                             bool seeds_phase, unsigned long long& edges) {
+                                             bool seeds_phase, unsigned long long& edges,
+                                             unsigned long long& items) {
     using Item = typename Pol::Item;
     constexpr uint32_t QM = Pol::kQueue - 1;
     const int lane = lane_id();
@@ -264,6 +266,7 @@ __device__ __forceinline__ void expand_batch(const EngineParams<typename Pol::It
     }
     t += total;
     edges += (lane == 0) ? (unsigned long long)total : 0ull;
+    items += (lane == 0) ? (unsigned long long)take : 0ull;
 }
 
 template <class Pol>
@@ -279,7 +282,7 @@ __global__ void __launch_bounds__(256) engine_kernel(EngineParams<typename Pol::
     const uint32_t wid = (uint32_t)(blockIdx.x * (blockDim.x >> 5) + wib);
     const uint32_t nwarps = (uint32_t)(gridDim.x * (blockDim.x >> 5));
     Item* q = sm.q + wib * Pol::kQueue;
-    unsigned long long edges = 0;
+    unsigned long long edges = 0, items = 0;
     long long inserted_acc = 0;
 
     // ---- round -1: the initial items (marked visited) go into bag[1]
@@ -416,6 +419,7 @@ __global__ void __launch_bounds__(256) engine_kernel(EngineParams<typename Pol::
                 bag_push<Item>(P, bc, st, nw, child, wid, iter);
             }
             edges += lane == 0 ? (unsigned long long)len : 0ull;
+            items += (lane == 0 && g == P.hub_segbase[h]) ? 1ull : 0ull;
         }
 
         // ---- phase B: warp tasks over the light frontier (VGC local searches)
@@ -430,9 +434,9 @@ __global__ void __launch_bounds__(256) engine_kernel(EngineParams<typename Pol::
             __syncwarp();
             uint32_t qh = 0, qt = (uint32_t)cnt;
             int t = 0;
-            expand_batch<Pol>(P, pol, bc, st, wid, iter, q, qh, qt, t, true, edges);
+            expand_batch<Pol>(P, pol, bc, st, wid, iter, q, qh, qt, t, true, edges, items);
             while (qt != qh && t < P.tau)
-                expand_batch<Pol>(P, pol, bc, st, wid, iter, q, qh, qt, t, false, edges);
+                expand_batch<Pol>(P, pol, bc, st, wid, iter, q, qh, qt, t, false, edges, items);
             // budget spent: flush what is left in the local queue
             while (qt != qh) {
                 int nrem = (int)min(32u, qt - qh);
@@ -460,6 +464,7 @@ __global__ void __launch_bounds__(256) engine_kernel(EngineParams<typename Pol::
         if (P.max_inserted > 0 && ld_volatile(&ctl->overflow) != 0) break;
     }
     if (lane == 0 && edges) atomicAdd(&ctl->edges, edges);
+    if (lane == 0 && items) atomicAdd(&ctl->items, items);
     if constexpr (Pol::kCountInserts) {
         if (lane == 0 && inserted_acc) atomicAdd(&ctl->inserted, (unsigned long long)inserted_acc);
     }

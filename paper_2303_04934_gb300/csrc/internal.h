@@ -21,7 +21,15 @@ inline int cuda_err(cudaError_t e) {
         if (_rc != SCC_OK) return _rc;        \
     } while (0)
 #define SCC_CUDA(expr) SCC_TRY(::scc::cuda_err(expr))
-#define SCC_LAUNCH() SCC_TRY(::scc::cuda_err(cudaGetLastError()))
+// Kernel launches issued by the library since it was loaded (every launch site
+// goes through SCC_LAUNCH or count_launch).
+void count_launch();
+long long launch_count();
+#define SCC_LAUNCH()                                      \
+    do {                                                  \
+        ::scc::count_launch();                            \
+        SCC_TRY(::scc::cuda_err(cudaGetLastError()));     \
+    } while (0)
 
 // Stream-ordered device allocation from the default pool.
 int dalloc(void** p, size_t bytes, cudaStream_t s);
@@ -139,12 +147,14 @@ int engine_reserve(EngineBuf* b, int item_bytes, long long items, int lambda, in
 void engine_release(EngineBuf* b, cudaStream_t s);
 
 struct EngineRun {
+    float ms = 0;  // kernel duration (CUDA events on the launching stream)
     int err = 0;
     int overflow = 0;
     int rounds = 0;
     int max_chunk = 0;
     unsigned long long edges = 0;
     unsigned long long inserted = 0;
+    unsigned long long items = 0;  // items expanded (adjacency rows read)
 };
 
 struct EngineOpts {

@@ -41,10 +41,26 @@ int launch_engine(EngineParams<typename Pol::Item>& P, Pol& pol, const EngineOpt
     SCC_TRY(coop_grid<Pol>(o.num_sms, &grid));
     SCC_CUDA(cudaMemsetAsync(P.ctl, 0, sizeof(EngineCtl), st));
     void* args[] = {(void*)&P, (void*)&pol};
-    SCC_CUDA(cudaLaunchCooperativeKernel((const void*)engine_kernel<Pol>, dim3(grid), dim3(kEngineBlock), args, 0, st));
+    cudaEvent_t e0, e1;
+    SCC_CUDA(cudaEventCreate(&e0));
+    SCC_CUDA(cudaEventCreate(&e1));
+    cudaEventRecord(e0, st);
+    cudaError_t le =
+        cudaLaunchCooperativeKernel((const void*)engine_kernel<Pol>, dim3(grid), dim3(kEngineBlock), args, 0, st);
+    count_launch();
+    cudaEventRecord(e1, st);
     EngineCtl h;
-    SCC_CUDA(cudaMemcpyAsync(&h, P.ctl, sizeof(EngineCtl), cudaMemcpyDeviceToHost, st));
-    SCC_CUDA(cudaStreamSynchronize(st));
+    cudaError_t ce = cudaMemcpyAsync(&h, P.ctl, sizeof(EngineCtl), cudaMemcpyDeviceToHost, st);
+    cudaError_t se = cudaStreamSynchronize(st);
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    SCC_CUDA(le);
+    SCC_CUDA(ce);
+    SCC_CUDA(se);
+    out->ms = ms;
+    out->items = h.items;
     out->err = h.err;
     out->overflow = h.overflow;
     out->rounds = h.rounds;
@@ -255,6 +271,7 @@ int run_bag_only(const int32_t* items, int64_t count, int lambda, int sigma, int
     int grid = std::max(1, per_sm) * di.num_sms;
     void* args[] = {(void*)&P, (void*)&items, (void*)&count, (void*)&out};
     int rc = cuda_err(cudaLaunchCooperativeKernel((const void*)k_bag_only, dim3(grid), dim3(256), args, 0, st));
+    count_launch();
     EngineCtl h;
     memset(&h, 0, sizeof(h));
     if (rc == SCC_OK) rc = cuda_err(cudaMemcpyAsync(&h, P.ctl, sizeof(EngineCtl), cudaMemcpyDeviceToHost, st));

@@ -30,7 +30,7 @@ EXPORTED = [
     "scc_error_string", "scc_config_default", "scc_graph_create", "scc_graph_destroy", "scc_set_config",
     "scc_run", "reach_multi", "scc_get_stats",
     "scc_graph_info", "scc_debug_csr", "scc_debug_trim", "scc_debug_pivot_order", "scc_debug_single_reach",
-    "scc_debug_multi_reach", "scc_debug_hashbag", "scc_debug_pair_table",
+    "scc_debug_multi_reach", "scc_debug_hashbag", "scc_debug_pair_table", "scc_debug_launch_count",
 ]
 
 
@@ -43,11 +43,13 @@ class scc_config(ctypes.Structure):
 class scc_stats(ctypes.Structure):
     _fields_ = [("n_trimmed", ctypes.c_int32), ("first_scc_size", ctypes.c_int32), ("batches", ctypes.c_int32),
                 ("search_rounds", ctypes.c_int32), ("pairs", ctypes.c_int64), ("table_resizes", ctypes.c_int32),
-                ("reserved", ctypes.c_int32), ("ms_trim", ctypes.c_double), ("ms_first_scc", ctypes.c_double),
-                ("ms_multi_search", ctypes.c_double), ("ms_resize", ctypes.c_double), ("ms_label", ctypes.c_double)]
+                ("engine_launches", ctypes.c_int32), ("ms_trim", ctypes.c_double), ("ms_first_scc", ctypes.c_double),
+                ("ms_multi_search", ctypes.c_double), ("ms_resize", ctypes.c_double), ("ms_label", ctypes.c_double),
+                ("ms_engine", ctypes.c_double), ("engine_arcs", ctypes.c_int64), ("engine_items", ctypes.c_int64),
+                ("engine_inserted", ctypes.c_int64)]
 
     def as_dict(self):
-        return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
+        return {f: getattr(self, f) for f, _ in self._fields_}
 
 
 class SccError(RuntimeError):
@@ -92,6 +94,7 @@ def load() -> ctypes.CDLL:
         "scc_debug_multi_reach": ([vp, vp, vp, i32, i32, vp, i64, P(i64), i64, vp], ctypes.c_int),
         "scc_debug_hashbag": ([vp, i64, i32, i32, vp, P(i64), P(i32), vp], ctypes.c_int),
         "scc_debug_pair_table": ([vp, i64, i64, vp, P(i64), P(i32), vp], ctypes.c_int),
+        "scc_debug_launch_count": ([], ctypes.c_int64),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -222,6 +225,10 @@ def scc_debug_pair_table(keys, count: int, init_cap: int, out, stream=None):
     _check(load().scc_debug_pair_table(_ptr(keys), count, init_cap, _ptr(out), ctypes.byref(nout),
                                        ctypes.byref(res), _stream(stream)), "scc_debug_pair_table")
     return nout.value, res.value
+
+
+def scc_debug_launch_count() -> int:
+    return int(load().scc_debug_launch_count())
 
 
 # ------------------------------------------------------------- convenience --
