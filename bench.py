@@ -327,6 +327,20 @@ def main():
     if args.verbose:
         line["breakdown_last_step"] = last
         line["gen_seconds"] = t_gen
+        # one extra step with the three calls timed separately (outside the timed region)
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        with torch.cuda.stream(stream):
+            evs[0].record(stream)
+            h = scc.scc_graph_create(n, m, off_d, adj_d, stream)
+            evs[1].record(stream)
+            scc.scc_set_config(h, cfg)
+            scc.scc_run(h, labels_d, stream)
+            evs[2].record(stream)
+            scc.scc_graph_destroy(h)
+            evs[3].record(stream)
+        torch.cuda.synchronize()
+        line["split_ms"] = {"create": evs[0].elapsed_time(evs[1]), "run": evs[1].elapsed_time(evs[2]),
+                            "destroy": evs[2].elapsed_time(evs[3])}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:

@@ -310,22 +310,24 @@ static int graph_create_impl(scc_graph* h, int32_t n, int64_t m, const int32_t* 
     SCC_CUDA(cudaStreamSynchronize(s));
     dfree(bad, s);
     if (hbad) return SCC_ERR_INVALID_ARG;
-    // in-degrees and self-loops
-    int32_t *indeg = nullptr, *selfrow = nullptr, *toff = nullptr;
-    unsigned long long* nself = nullptr;
+    // coarse bucket histogram of the arcs (and self-loops)
+    const int shift = bucket_shift(n);
+    const int nb = std::max(1, (int)(((int64_t)n + (1ll << shift) - 1) >> shift));
+    int32_t* selfrow = nullptr;
+    unsigned long long *bcnt = nullptr, *btmp = nullptr;
     void* stmp = nullptr;
-    SCC_TRY(dalloc_t(&indeg, (size_t)n + 1, s));
     SCC_TRY(dalloc_t(&selfrow, (size_t)n + 1, s));
-    SCC_TRY(dalloc_t(&nself, 1, s));
+    SCC_TRY(dalloc_t(&bcnt, (size_t)nb + 2, s));
+    SCC_TRY(dalloc_t(&btmp, 2 * (size_t)nb + 2, s));
     SCC_TRY(dalloc(&stmp, scan_tmp_bytes(n), s));
-    SCC_CUDA(cudaMemsetAsync(indeg, 0, sizeof(int32_t) * ((size_t)n + 1), s));
     SCC_CUDA(cudaMemsetAsync(selfrow, 0, sizeof(int32_t) * ((size_t)n + 1), s));
-    SCC_CUDA(cudaMemsetAsync(nself, 0, sizeof(unsigned long long), s));
-    SCC_TRY(launch_count_arcs(off_in, adj_in, n, m, indeg, selfrow, nself, s));
+    SCC_CUDA(cudaMemsetAsync(bcnt, 0, sizeof(unsigned long long) * ((size_t)nb + 2), s));
+    SCC_TRY(launch_bucket_hist(off_in, adj_in, n, m, shift, bcnt, selfrow, bcnt + nb + 1, h->di.num_sms, s));
     unsigned long long hself = 0;
-    SCC_CUDA(cudaMemcpyAsync(&hself, nself, sizeof(hself), cudaMemcpyDeviceToHost, s));
+    SCC_CUDA(cudaMemcpyAsync(&hself, bcnt + nb + 1, sizeof(hself), cudaMemcpyDeviceToHost, s));
     SCC_CUDA(cudaStreamSynchronize(s));
     h->mt = m - (int64_t)hself;
+    int64_t m_cur = m;
     if (hself > 0) {
         // forward CSR without self-loops
         int32_t *cnt = nullptr, *off2 = nullptr, *adj2 = nullptr;
@@ -340,17 +342,40 @@ static int graph_create_impl(scc_graph* h, int32_t n, int64_t m, const int32_t* 
         dfree(adj_in, s);
         h->off = off2;
         h->adj = adj2;
+        m_cur = h->mt;
     }
-    // G^T: exclusive scan of in-degrees, then scatter
+    // G^T: two-level bucketed counting sort by target (direct atomics when n is huge)
+    int32_t* toff = nullptr;
     SCC_TRY(dalloc_t(&toff, (size_t)n + 1, s));
-    SCC_TRY(dalloc_t(&h->tadj, (size_t)h->mt, s));
-    SCC_TRY(launch_scan(indeg, toff, n, stmp, s));
-    SCC_CUDA(cudaMemcpyAsync(indeg, toff, sizeof(int32_t) * (size_t)n, cudaMemcpyDeviceToDevice, s));
-    SCC_TRY(launch_transpose_scatter(h->off, h->adj, n, h->mt, indeg, h->tadj, s));
     h->toff = toff;
-    dfree(indeg, s);
+    SCC_TRY(dalloc_t(&h->tadj, (size_t)h->mt, s));
+    if (transpose_bucketed(shift)) {
+        int32_t *tmp_u = nullptr, *tmp_v = nullptr, *ord = nullptr;
+        int* terr = nullptr;
+        SCC_TRY(dalloc_t(&tmp_u, (size_t)h->mt, s));
+        SCC_TRY(dalloc_t(&tmp_v, (size_t)h->mt, s));
+        SCC_TRY(dalloc_t(&ord, (size_t)nb, s));
+        SCC_TRY(dalloc_t(&terr, 1, s));
+        SCC_CUDA(cudaMemsetAsync(terr, 0, sizeof(int), s));
+        SCC_TRY(launch_transpose(h->off, h->adj, n, m_cur, h->mt, shift, bcnt, btmp, tmp_u, tmp_v, ord, toff, h->tadj,
+                                 terr, h->di.num_sms, s));
+        int herr = 0;
+        SCC_CUDA(cudaMemcpyAsync(&herr, terr, sizeof(int), cudaMemcpyDeviceToHost, s));
+        SCC_CUDA(cudaStreamSynchronize(s));
+        dfree(tmp_u, s);
+        dfree(tmp_v, s);
+        dfree(ord, s);
+        dfree(terr, s);
+        if (herr) return herr;
+    } else {
+        int32_t* indeg = nullptr;
+        SCC_TRY(dalloc_t(&indeg, (size_t)n + 1, s));
+        SCC_TRY(launch_transpose_direct(h->off, h->adj, n, m_cur, indeg, stmp, toff, h->tadj, h->di.num_sms, s));
+        dfree(indeg, s);
+    }
     dfree(selfrow, s);
-    dfree(nself, s);
+    dfree(bcnt, s);
+    dfree(btmp, s);
     dfree(stmp, s);
     SCC_CUDA(cudaStreamSynchronize(s));
     return SCC_OK;

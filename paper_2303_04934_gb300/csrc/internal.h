@@ -51,9 +51,24 @@ int device_info(DeviceInfo* out);
 // --------------------------------------------------------- graph building --
 // Validate a CSR on the device; *bad (device int) becomes nonzero if malformed.
 int launch_validate(const int32_t* off, const int32_t* adj, int32_t n, int64_t m, int* bad, cudaStream_t s);
-// indeg[v] += number of arcs u->v with u != v; selfrow[u] += self-loops of u.
-int launch_count_arcs(const int32_t* off, const int32_t* adj, int32_t n, int64_t m, int32_t* indeg,
-                      int32_t* selfrow, unsigned long long* nself, cudaStream_t s);
+// Transposed CSR (transpose.cu). bucket_shift(n): vertices per coarse bucket
+// = 2^shift, at most 1024 buckets.
+int bucket_shift(int32_t n);
+// bucket_cnt[b] += non-self arcs into bucket b; selfrow[u] += self-loops of u.
+int launch_bucket_hist(const int32_t* off, const int32_t* adj, int32_t n, int64_t m, int shift,
+                       unsigned long long* bucket_cnt, int32_t* selfrow, unsigned long long* nself, int num_sms,
+                       cudaStream_t s);
+// G^T of the CSR (off, adj) with m arcs of which mt are not self-loops, by the
+// two-level bucketed counting sort (when transpose_bucketed(shift)).
+// bucket_tmp: 2 * nbuckets + 2 words; tmp_u, tmp_v: mt each; order_tmp: nbuckets.
+bool transpose_bucketed(int shift);
+int launch_transpose(const int32_t* off, const int32_t* adj, int32_t n, int64_t m, int64_t mt, int shift,
+                     const unsigned long long* bucket_cnt, unsigned long long* bucket_tmp, int32_t* tmp_u,
+                     int32_t* tmp_v, int32_t* order_tmp, int32_t* toff, int32_t* tadj, int* err, int num_sms,
+                     cudaStream_t s);
+// Direct G^T for very large n: global atomics. indeg: n + 1.
+int launch_transpose_direct(const int32_t* off, const int32_t* adj, int32_t n, int64_t m, int32_t* indeg,
+                            void* scan_tmp, int32_t* toff, int32_t* tadj, int num_sms, cudaStream_t s);
 // Exclusive scan of int32 counts: out[0..n] with out[n] = total. tmp: scan_tmp_bytes(n).
 size_t scan_tmp_bytes(int64_t n);
 int launch_scan(const int32_t* in, int32_t* out, int64_t n, void* tmp, cudaStream_t s);
@@ -62,9 +77,6 @@ int launch_drop_self_loops(const int32_t* off, const int32_t* adj, int32_t n, in
                            const int32_t* off2, int32_t* adj2, cudaStream_t s);
 // cnt[u] = out-arcs of u that are not self-loops.
 int launch_row_nonself(const int32_t* off, const int32_t* selfrow, int32_t n, int32_t* cnt, cudaStream_t s);
-// Scatter every non-self arc (u,v) to row v of G^T; cursor[v] starts at toff[v].
-int launch_transpose_scatter(const int32_t* off, const int32_t* adj, int32_t n, int64_t m, int32_t* cursor,
-                             int32_t* tadj, cudaStream_t s);
 
 // ------------------------------------------------------------- SCC steps --
 // trimmed flags from the self-loop-free CSRs (Sec. 4.1).

@@ -64,64 +64,6 @@ __global__ void k_validate(const int32_t* __restrict__ off, const int32_t* __res
     }
 }
 
-// -------------------------------------------------------------- arc counts --
-// Per arc (u, v): u != v -> indeg[v]++ (warp-aggregated over equal v with
-// __match_any_sync, which turns hub in-degrees into one atomic per warp);
-// u == v -> selfrow[u]++.
-__global__ void __launch_bounds__(kBlk) k_count_arcs(const int32_t* __restrict__ off, const int32_t* __restrict__ adj,
-                                                     int32_t n, int64_t m, int32_t* indeg, int32_t* selfrow,
-                                                     unsigned long long* nself) {
-    unsigned long long my_self = 0;
-    for (int64_t t0 = (int64_t)blockIdx.x * kEdgeTile; t0 < m; t0 += (int64_t)gridDim.x * kEdgeTile) {
-        int64_t t1 = t0 + kEdgeTile < m ? t0 + kEdgeTile : m;
-        int r0, r1;
-        tile_rows(off, n, t0, t1, &r0, &r1);
-        for (int64_t e = t0 + threadIdx.x; e - threadIdx.x < t1; e += blockDim.x) {
-            int key = -1;
-            if (e < t1) {
-                int u = row_of(off, r0, r1, e);
-                int v = __ldg(&adj[e]);
-                if (u == v) {
-                    atomicAdd(&selfrow[u], 1);
-                    ++my_self;
-                } else {
-                    key = v;
-                }
-            }
-            uint32_t peers = __match_any_sync(kFull, key);
-            int leader = __ffs(peers) - 1;
-            if (key >= 0 && lane_id() == leader) atomicAdd(&indeg[key], __popc(peers));
-        }
-    }
-    if (my_self) atomicAdd(nself, my_self);
-}
-
-// G^T scatter: row v gets u for every arc (u, v), u != v; one atomic per group
-// of lanes with equal v.
-__global__ void __launch_bounds__(kBlk) k_transpose_scatter(const int32_t* __restrict__ off,
-                                                            const int32_t* __restrict__ adj, int32_t n, int64_t m,
-                                                            int32_t* cursor, int32_t* tadj) {
-    for (int64_t t0 = (int64_t)blockIdx.x * kEdgeTile; t0 < m; t0 += (int64_t)gridDim.x * kEdgeTile) {
-        int64_t t1 = t0 + kEdgeTile < m ? t0 + kEdgeTile : m;
-        int r0, r1;
-        tile_rows(off, n, t0, t1, &r0, &r1);
-        for (int64_t e = t0 + threadIdx.x; e - threadIdx.x < t1; e += blockDim.x) {
-            int key = -1, u = -1;
-            if (e < t1) {
-                u = row_of(off, r0, r1, e);
-                int v = __ldg(&adj[e]);
-                if (u != v) key = v;
-            }
-            uint32_t peers = __match_any_sync(kFull, key);
-            int leader = __ffs(peers) - 1;
-            int base = 0;
-            if (key >= 0 && lane_id() == leader) base = atomicAdd(&cursor[key], __popc(peers));
-            base = __shfl_sync(kFull, base, leader);
-            if (key >= 0) tadj[base + __popc(peers & lanemask_lt())] = u;
-        }
-    }
-}
-
 // Forward CSR without self-loops. Rows without self-loops are copied arc-parallel;
 // rows with self-loops (rare) are copied by one thread each.
 __global__ void __launch_bounds__(kBlk) k_drop_self_arcs(const int32_t* __restrict__ off,
@@ -431,14 +373,19 @@ __global__ void k_fill_i32(int32_t* p, int64_t n, int32_t v) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         p[i] = v;
 }
+// minid[rep[v]] = min v. Lanes of a warp hold consecutive v, so among lanes with
+// the same rep the lowest lane has the smallest v: one atomic per group, and
+// only when it can still lower the stored minimum (an SCC of millions of
+// vertices then costs a few atomics instead of one per vertex).
 __global__ void k_min_of_rep(const int32_t* __restrict__ rep, int32_t n, int32_t* minid, int* bad) {
-    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
-        int r = rep[v];
-        if (r < 0 || r >= n) {
-            atomicExch(bad, 1);
-            continue;
-        }
-        atomicMin(&minid[r], (int32_t)v);
+    for (int64_t b = (int64_t)blockIdx.x * blockDim.x; b < n; b += (int64_t)gridDim.x * blockDim.x) {
+        int64_t v = b + threadIdx.x;
+        int r = v < n ? rep[v] : -1;
+        bool ok = r >= 0 && r < n;
+        if (v < n && !ok) atomicExch(bad, 1);
+        int key = ok ? r : -1;
+        uint32_t peers = __match_any_sync(kFull, key);
+        if (ok && lane_id() == __ffs(peers) - 1 && ld_volatile(&minid[r]) > (int32_t)v) atomicMin(&minid[r], (int32_t)v);
     }
 }
 __global__ void k_write_labels(const int32_t* __restrict__ rep, int32_t n, const int32_t* __restrict__ minid,
@@ -477,14 +424,6 @@ __global__ void k_table_insert(const unsigned long long* __restrict__ keys, int6
 // ================================================================ launchers ==
 int launch_validate(const int32_t* off, const int32_t* adj, int32_t n, int64_t m, int* bad, cudaStream_t s) {
     k_validate<<<grid_for(n > m ? n : m, kBlk * 4), kBlk, 0, s>>>(off, adj, n, m, bad);
-    SCC_LAUNCH();
-    return SCC_OK;
-}
-
-int launch_count_arcs(const int32_t* off, const int32_t* adj, int32_t n, int64_t m, int32_t* indeg,
-                      int32_t* selfrow, unsigned long long* nself, cudaStream_t s) {
-    if (m == 0 || n == 0) return SCC_OK;
-    k_count_arcs<<<grid_for(m, kEdgeTile, 152 * 16), kBlk, 0, s>>>(off, adj, n, m, indeg, selfrow, nself);
     SCC_LAUNCH();
     return SCC_OK;
 }
@@ -556,14 +495,6 @@ int launch_mask_init(const int32_t* sources, int32_t k, int32_t n, unsigned long
 int launch_filter_sources(const int32_t* in, int32_t k, int32_t n, const int32_t* label, int32_t* out, int* cnt,
                           int* bad, cudaStream_t s) {
     k_filter_sources<<<grid_for(k, kBlk), kBlk, 0, s>>>(in, k, n, label, out, cnt, bad);
-    SCC_LAUNCH();
-    return SCC_OK;
-}
-
-int launch_transpose_scatter(const int32_t* off, const int32_t* adj, int32_t n, int64_t m, int32_t* cursor,
-                             int32_t* tadj, cudaStream_t s) {
-    if (m == 0 || n == 0) return SCC_OK;
-    k_transpose_scatter<<<grid_for(m, kEdgeTile, 152 * 16), kBlk, 0, s>>>(off, adj, n, m, cursor, tadj);
     SCC_LAUNCH();
     return SCC_OK;
 }

@@ -1,0 +1,419 @@
+// Transposed CSR G^T from the CSR of G (sm_103a).
+//
+// Every non-self arc (u, v) of G becomes the entry u of row v of G^T (Sec. 2: a
+// backward reachability search is a forward search on G^T). This is a counting
+// sort of the arcs by target, done in two levels so that every per-arc atomic is
+// a shared-memory atomic:
+//
+//   A. coarse partition by bucket b = v >> shift (at most 512 buckets):
+//      A1 histogram of buckets (per-block shared histogram, one global add per
+//         block and bucket);
+//      A2 partition: a block takes a tile of 8k arcs, counting-sorts it by
+//         bucket in shared memory, reserves one run per non-empty bucket with a
+//         global atomicAdd, and writes the sorted tile out, so consecutive lanes
+//         store consecutive positions of a run.
+//   B. one block per bucket (largest buckets first): per-vertex counts of the
+//      bucket in shared memory, their scan gives the bucket's rows of G^T
+//      (offsets written directly: the bucket's first row starts at the bucket's
+//      start), then the arcs are placed with shared-memory cursors. The rows a
+//      block writes span one bucket, so partial-sector writes merge in L2.
+//
+// Rows of each arc tile are found by one binary search per thread followed by a
+// forward walk over the tile's row offsets staged in shared memory.
+#include <algorithm>
+#include <numeric>
+#include <vector>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace scc {
+namespace {
+
+constexpr int kMaxBuckets = 512;
+constexpr int kBucketLog = 15;          // at most 2^15 vertices per bucket (128 KB of shared counters)
+constexpr int kBlkA = 512;
+static_assert(kMaxBuckets <= kBlkA, "bucket scan uses one thread per bucket");
+constexpr int kChunk = 16;              // consecutive arcs per thread per step
+constexpr int kStep = kBlkA * kChunk;   // arcs per block step (8192) = partition tile
+constexpr int kRowsCap = 4096;          // row offsets of one step staged in shared memory
+constexpr int kBlkB = 1024;
+
+// Largest r in [lo, hi] with off[r] <= e.
+__device__ __forceinline__ int row_search_g(const int32_t* __restrict__ off, int lo, int hi, int64_t e) {
+    while (lo < hi) {
+        int mid = lo + ((hi - lo + 1) >> 1);
+        if ((int64_t)__ldg(&off[mid]) <= e) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Same search by a full warp: 32 probes per round narrow [lo, hi] 32-fold, so a
+// search over 2^24 rows takes 5 dependent rounds instead of 24. The final round
+// probes the (at most 32) remaining candidates lo..hi, one per lane.
+__device__ __forceinline__ int warp_row_search(const int32_t* __restrict__ off, int lo, int hi, int64_t e) {
+    const int lane = threadIdx.x & 31;
+    while (hi - lo >= 32) {
+        const int64_t span = (int64_t)hi - lo;
+        const int pos = lo + (int)(span * lane / 32);  // probe points, lane 0 at lo
+        const bool le = (int64_t)__ldg(&off[pos]) <= e;
+        const uint32_t m = __ballot_sync(0xffffffffu, le);
+        const int last = 31 - __clz(m);  // off[lo] <= e, so lane 0 is always set
+        const int nlo = lo + (int)(span * last / 32);
+        const int nhi = last == 31 ? hi : lo + (int)(span * (last + 1) / 32) - 1;
+        lo = nlo;
+        hi = nhi;
+    }
+    const int pos = min(lo + lane, hi);
+    const uint32_t m = __ballot_sync(0xffffffffu, (int64_t)__ldg(&off[pos]) <= e && lo + lane <= hi);
+    return lo + (31 - __clz(m));
+}
+
+// One step of a block: arcs [s0, s1), thread t owns [s0 + 16 t, s0 + 16 t + 16).
+// Calls f(q, u, v) for its q-th arc (q < 16, a compile-time index after unrolling). Row offsets of the step are staged in
+// shared memory when they fit; each thread binary-searches its first arc's row
+// and walks forward.
+template <class F>
+__device__ __forceinline__ void for_step_arcs(const int32_t* __restrict__ off, const int32_t* __restrict__ adj,
+                                              int32_t n, int64_t s0, int64_t s1, int32_t* s_off, F&& f) {
+    __shared__ int s_r[2];
+    if (threadIdx.x < 32) {
+        int a = warp_row_search(off, 0, n - 1, s0);
+        int b = warp_row_search(off, a, n - 1, s1 - 1);
+        if (threadIdx.x == 0) {
+            s_r[0] = a;
+            s_r[1] = b;
+        }
+    }
+    __syncthreads();
+    const int r0 = s_r[0], r1 = s_r[1];
+    const int cnt = r1 - r0 + 2;  // offsets off[r0 .. r1 + 1]
+    const bool sm = cnt <= kRowsCap;
+    if (sm)
+        for (int i = threadIdx.x; i < cnt; i += blockDim.x) s_off[i] = off[r0 + i];
+    __syncthreads();
+    const int64_t e0 = s0 + (int64_t)threadIdx.x * kChunk;
+    if (e0 < s1) {
+        const int64_t e1 = min(e0 + (int64_t)kChunk, s1);
+        int r;
+        if (sm) {
+            int lo = 0, hi = cnt - 2;
+            while (lo < hi) {
+                int mid = (lo + hi + 1) >> 1;
+                if ((int64_t)s_off[mid] <= e0) lo = mid;
+                else hi = mid - 1;
+            }
+            r = lo;  // relative row
+        } else {
+            r = row_search_g(off, r0, r1, e0) - r0;
+        }
+        int32_t a[kChunk];
+        if (e1 - e0 == kChunk && ((e0 & 3) == 0)) {
+            const int4* p = reinterpret_cast<const int4*>(adj + e0);
+#pragma unroll
+            for (int q = 0; q < kChunk / 4; ++q) {
+                int4 x = __ldg(p + q);
+                a[4 * q] = x.x;
+                a[4 * q + 1] = x.y;
+                a[4 * q + 2] = x.z;
+                a[4 * q + 3] = x.w;
+            }
+        } else {
+#pragma unroll
+            for (int q = 0; q < kChunk; ++q) a[q] = (e0 + q < e1) ? __ldg(&adj[e0 + q]) : 0;
+        }
+#pragma unroll
+        for (int q = 0; q < kChunk; ++q) {
+            const int64_t e = e0 + q;
+            if (e < e1) {
+                // advance to the row containing e
+                // (bounded by the staged rows: r0..r1 always contain e)
+                if (sm) {
+                    while (r + 1 < cnt - 1 && (int64_t)s_off[r + 1] <= e) ++r;
+                } else {
+                    while (r0 + r + 1 <= r1 && (int64_t)__ldg(&off[r0 + r + 1]) <= e) ++r;
+                }
+                f(q, r0 + r, a[q]);
+            }
+        }
+    }
+    __syncthreads();
+}
+
+// A1. bucket histogram of non-self arcs; self-loops counted per row.
+__global__ void __launch_bounds__(kBlkA) k_bucket_hist(const int32_t* __restrict__ off, const int32_t* __restrict__ adj,
+                                                       int32_t n, int64_t m, int shift, int nb,
+                                                       unsigned long long* bucket_cnt, int32_t* selfrow,
+                                                       unsigned long long* nself) {
+    __shared__ int32_t s_off[kRowsCap];
+    __shared__ unsigned int s_hist[kMaxBuckets];
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) s_hist[i] = 0;
+    __syncthreads();
+    unsigned long long my_self = 0;
+    for (int64_t s0 = (int64_t)blockIdx.x * kStep; s0 < m; s0 += (int64_t)gridDim.x * kStep) {
+        const int64_t s1 = min(s0 + (int64_t)kStep, m);
+        for_step_arcs(off, adj, n, s0, s1, s_off, [&](int, int u, int v) {
+            if (u == v) {
+                atomicAdd(&selfrow[u], 1);
+                ++my_self;
+            } else {
+                atomicAdd(&s_hist[v >> shift], 1u);
+            }
+        });
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < nb; i += blockDim.x)
+        if (s_hist[i]) atomicAdd(&bucket_cnt[i], (unsigned long long)s_hist[i]);
+    if (my_self) atomicAdd(nself, my_self);
+}
+
+// exclusive scan of the bucket counts (one block, sequential: nb <= 2048)
+__global__ void k_bucket_scan(const unsigned long long* cnt, int nb, unsigned long long* start,
+                              unsigned long long* cursor) {
+    if (threadIdx.x == 0) {
+        unsigned long long s = 0;
+        for (int i = 0; i < nb; ++i) {
+            start[i] = s;
+            cursor[i] = s;
+            s += cnt[i];
+        }
+        start[nb] = s;
+    }
+}
+
+// A2. partition: per 8k-arc tile, a shared-memory counting sort by bucket,
+// one global reservation per non-empty bucket, then a coalesced write-out.
+__global__ void __launch_bounds__(kBlkA) k_bucket_part(const int32_t* __restrict__ off, const int32_t* __restrict__ adj,
+                                                       int32_t n, int64_t m, int shift, int nb,
+                                                       unsigned long long* cursor, int32_t* out_u, int32_t* out_v,
+                                                       unsigned long long mt, int* err) {
+    __shared__ int32_t s_off[kRowsCap];
+    __shared__ unsigned int s_cnt[kMaxBuckets];
+    __shared__ unsigned int s_start[kMaxBuckets];
+    __shared__ unsigned long long s_gbase[kMaxBuckets];
+    extern __shared__ int32_t s_stage[];  // the sorted tile: u[kStep], v[kStep]
+    int32_t* s_u = s_stage;
+    int32_t* s_v = s_stage + kStep;
+    __shared__ unsigned int s_wsum[kBlkA / 32];
+    __shared__ unsigned int s_total;
+    for (int64_t t0 = (int64_t)blockIdx.x * kStep; t0 < m; t0 += (int64_t)gridDim.x * kStep) {
+        const int64_t t1 = min(t0 + (int64_t)kStep, m);
+        for (int i = threadIdx.x; i < nb; i += blockDim.x) s_cnt[i] = 0;
+        __syncthreads();
+        // ranks within (tile, bucket), kept per thread
+        unsigned int rk[kChunk];
+        int uu[kChunk], vv[kChunk];
+#pragma unroll
+        for (int q = 0; q < kChunk; ++q) vv[q] = -1;
+        for_step_arcs(off, adj, n, t0, t1, s_off, [&](int q, int u, int v) {
+            if (u != v) {
+                uu[q] = u;
+                vv[q] = v;
+                rk[q] = atomicAdd(&s_cnt[v >> shift], 1u);
+            }
+        });
+        // exclusive scan of the bucket counts (nb <= 512 = blockDim)
+        {
+            const int i = threadIdx.x;
+            const unsigned int c = i < nb ? s_cnt[i] : 0u;
+            const int incl = warp_incl_scan((int)c);
+            if (lane_id() == 31) s_wsum[i >> 5] = incl;
+            __syncthreads();
+            if (i < 32) {
+                unsigned int x = i < (int)(blockDim.x >> 5) ? s_wsum[i] : 0u;
+                unsigned int y = (unsigned int)warp_incl_scan((int)x);
+                if (i < (int)(blockDim.x >> 5)) s_wsum[i] = y - x;
+                if (i == 31) s_total = y;
+            }
+            __syncthreads();
+            if (i < nb) {
+                s_start[i] = s_wsum[i >> 5] + incl - c;
+                s_gbase[i] = c ? atomicAdd(&cursor[i], (unsigned long long)c) : 0ull;
+            }
+            __syncthreads();
+        }
+        // stage the tile sorted by bucket
+#pragma unroll
+        for (int q = 0; q < kChunk; ++q)
+            if (vv[q] >= 0) {
+                const unsigned int j = s_start[vv[q] >> shift] + rk[q];
+                s_u[j] = uu[q];
+                s_v[j] = vv[q];
+            }
+        __syncthreads();
+        const unsigned int total = s_total;
+        for (unsigned int j = threadIdx.x; j < total; j += blockDim.x) {
+            const int v = s_v[j];
+            const int b = v >> shift;
+            const unsigned long long pos = s_gbase[b] + (j - s_start[b]);
+            if (pos < mt) {
+                out_u[pos] = s_u[j];
+                out_v[pos] = v;
+            } else {
+                atomicExch(err, SCC_ERR_INTERNAL);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// B. one block per bucket: per-vertex counts in shared memory, row offsets of
+// G^T for the bucket's vertices, placement with shared cursors.
+__global__ void __launch_bounds__(kBlkB) k_bucket_rows(const int32_t* __restrict__ uu, const int32_t* __restrict__ vv,
+                                                       const unsigned long long* __restrict__ start,
+                                                       const int32_t* __restrict__ order, int nb, int shift,
+                                                       int32_t n, int32_t* toff, int32_t* tadj, int* err) {
+    extern __shared__ int s_cnt[];  // 2^shift counters
+    __shared__ int s_wsum[kBlkB / 32];
+    const int W = 1 << shift;
+    for (int oi = blockIdx.x; oi < nb; oi += gridDim.x) {
+        const int b = order[oi];
+        const int v0 = b << shift;
+        const int vw = min(W, n - v0);
+        const long long a0 = (long long)start[b], a1 = (long long)start[b + 1];
+        for (int i = threadIdx.x; i < vw; i += blockDim.x) s_cnt[i] = 0;
+        __syncthreads();
+        for (long long i = a0 + threadIdx.x; i < a1; i += blockDim.x) {
+            const unsigned int lv = (unsigned int)(__ldg(&vv[i]) - v0);
+            if (lv < (unsigned int)vw) atomicAdd(&s_cnt[lv], 1);
+            else atomicExch(err, SCC_ERR_INTERNAL);  // arc outside its bucket: skip it, report
+        }
+        __syncthreads();
+        // exclusive scan of s_cnt[0..vw) in place; each thread owns a contiguous run
+        const int per = (vw + blockDim.x - 1) / blockDim.x;
+        const int c0 = threadIdx.x * per, c1 = min(c0 + per, vw);
+        int sum = 0;
+        for (int i = c0; i < c1; ++i) sum += s_cnt[i];
+        int incl = warp_incl_scan(sum);
+        if (lane_id() == 31) s_wsum[threadIdx.x >> 5] = incl;
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            int x = threadIdx.x < (int)(blockDim.x >> 5) ? s_wsum[threadIdx.x] : 0;
+            int y = warp_incl_scan(x);
+            if (threadIdx.x < (int)(blockDim.x >> 5)) s_wsum[threadIdx.x] = y - x;
+        }
+        __syncthreads();
+        int run = s_wsum[threadIdx.x >> 5] + incl - sum;
+        for (int i = c0; i < c1; ++i) {
+            int c = s_cnt[i];
+            s_cnt[i] = run;
+            toff[v0 + i] = (int32_t)(a0 + run);
+            run += c;
+        }
+        __syncthreads();
+        for (long long i = a0 + threadIdx.x; i < a1; i += blockDim.x) {
+            const unsigned int lv = (unsigned int)(__ldg(&vv[i]) - v0);
+            if (lv >= (unsigned int)vw) continue;
+            const int p = atomicAdd(&s_cnt[lv], 1);
+            if (a0 + p < a1) tadj[a0 + p] = __ldg(&uu[i]);
+            else atomicExch(err, SCC_ERR_INTERNAL);
+        }
+        __syncthreads();
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) toff[n] = (int32_t)start[nb];
+}
+
+// Direct path for graphs too large for shared per-bucket counters: global
+// in-degree atomics, scan, global cursor atomics.
+__global__ void __launch_bounds__(kBlkA) k_direct_count(const int32_t* __restrict__ off,
+                                                        const int32_t* __restrict__ adj, int32_t n, int64_t m,
+                                                        int32_t* indeg) {
+    __shared__ int32_t s_off[kRowsCap];
+    for (int64_t s0 = (int64_t)blockIdx.x * kStep; s0 < m; s0 += (int64_t)gridDim.x * kStep)
+        for_step_arcs(off, adj, n, s0, min(s0 + (int64_t)kStep, m), s_off, [&](int, int u, int v) {
+            if (u != v) atomicAdd(&indeg[v], 1);
+        });
+}
+__global__ void __launch_bounds__(kBlkA) k_direct_place(const int32_t* __restrict__ off,
+                                                        const int32_t* __restrict__ adj, int32_t n, int64_t m,
+                                                        int32_t* cursor, int32_t* tadj) {
+    __shared__ int32_t s_off[kRowsCap];
+    for (int64_t s0 = (int64_t)blockIdx.x * kStep; s0 < m; s0 += (int64_t)gridDim.x * kStep)
+        for_step_arcs(off, adj, n, s0, min(s0 + (int64_t)kStep, m), s_off, [&](int, int u, int v) {
+            if (u != v) tadj[atomicAdd(&cursor[v], 1)] = u;
+        });
+}
+
+int grid_for_arcs(int64_t m, int per_block, int num_sms, int per_sm) {
+    int64_t t = (m + per_block - 1) / per_block;
+    return (int)std::max<int64_t>(1, std::min(t, (int64_t)num_sms * per_sm));
+}
+
+}  // namespace
+
+int bucket_shift(int32_t n) {
+    int shift = 6;
+    while (((int64_t)n + (1ll << shift) - 1) >> shift > kMaxBuckets) ++shift;
+    return shift;
+}
+
+int launch_bucket_hist(const int32_t* off, const int32_t* adj, int32_t n, int64_t m, int shift,
+                       unsigned long long* bucket_cnt, int32_t* selfrow, unsigned long long* nself, int num_sms,
+                       cudaStream_t s) {
+    if (m == 0 || n == 0) return SCC_OK;
+    int nb = (int)(((int64_t)n + (1ll << shift) - 1) >> shift);
+    k_bucket_hist<<<grid_for_arcs(m, kStep, num_sms, 2), kBlkA, 0, s>>>(off, adj, n, m, shift, nb, bucket_cnt,
+                                                                          selfrow, nself);
+    SCC_LAUNCH();
+    return SCC_OK;
+}
+
+int launch_transpose_direct(const int32_t* off, const int32_t* adj, int32_t n, int64_t m, int32_t* indeg,
+                            void* scan_tmp, int32_t* toff, int32_t* tadj, int num_sms, cudaStream_t s) {
+    SCC_CUDA(cudaMemsetAsync(indeg, 0, sizeof(int32_t) * ((size_t)n + 1), s));
+    if (m > 0) {
+        k_direct_count<<<grid_for_arcs(m, kStep, num_sms, 2), kBlkA, 0, s>>>(off, adj, n, m, indeg);
+        SCC_LAUNCH();
+    }
+    SCC_TRY(launch_scan(indeg, toff, n, scan_tmp, s));
+    if (m > 0) {
+        SCC_CUDA(cudaMemcpyAsync(indeg, toff, sizeof(int32_t) * (size_t)n, cudaMemcpyDeviceToDevice, s));
+        k_direct_place<<<grid_for_arcs(m, kStep, num_sms, 2), kBlkA, 0, s>>>(off, adj, n, m, indeg, tadj);
+        SCC_LAUNCH();
+    }
+    return SCC_OK;
+}
+
+bool transpose_bucketed(int shift) { return shift <= kBucketLog; }
+
+int launch_transpose(const int32_t* off, const int32_t* adj, int32_t n, int64_t m, int64_t mt, int shift,
+                     const unsigned long long* bucket_cnt, unsigned long long* bucket_tmp, int32_t* tmp_u,
+                     int32_t* tmp_v, int32_t* order_tmp, int32_t* toff, int32_t* tadj, int* err, int num_sms,
+                     cudaStream_t s) {
+    const int nb = std::max(1, (int)(((int64_t)n + (1ll << shift) - 1) >> shift));
+    unsigned long long* start = bucket_tmp;
+    unsigned long long* cursor = bucket_tmp + nb + 1;
+    if (n == 0) {
+        SCC_CUDA(cudaMemsetAsync(toff, 0, sizeof(int32_t), s));
+        return SCC_OK;
+    }
+    k_bucket_scan<<<1, 32, 0, s>>>(bucket_cnt, nb, start, cursor);
+    SCC_LAUNCH();
+    if (mt > 0) {
+        const int stage = 2 * kStep * (int)sizeof(int32_t);
+        SCC_CUDA(cudaFuncSetAttribute(k_bucket_part, cudaFuncAttributeMaxDynamicSharedMemorySize, stage));
+        k_bucket_part<<<grid_for_arcs(m, kStep, num_sms, 2), kBlkA, stage, s>>>(off, adj, n, m, shift, nb, cursor,
+                                                                                  tmp_u, tmp_v,
+                                                                                  (unsigned long long)mt, err);
+        SCC_LAUNCH();
+    }
+    // buckets by decreasing size (longest first), from the host copy of the counts
+    std::vector<unsigned long long> hc(nb);
+    SCC_CUDA(cudaMemcpyAsync(hc.data(), bucket_cnt, sizeof(unsigned long long) * nb, cudaMemcpyDeviceToHost, s));
+    SCC_CUDA(cudaStreamSynchronize(s));
+    std::vector<int32_t> ord(nb);
+    std::iota(ord.begin(), ord.end(), 0);
+    std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return hc[a] > hc[b]; });
+    SCC_CUDA(cudaMemcpyAsync(order_tmp, ord.data(), sizeof(int32_t) * nb, cudaMemcpyHostToDevice, s));
+    const size_t smem = sizeof(int) << shift;
+    if (smem > 48 * 1024)
+        SCC_CUDA(cudaFuncSetAttribute(k_bucket_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_bucket_rows<<<std::min(nb, num_sms * 2), kBlkB, smem, s>>>(tmp_u, tmp_v, start, order_tmp, nb, shift, n, toff,
+                                                                   tadj, err);
+    SCC_LAUNCH();
+    SCC_CUDA(cudaStreamSynchronize(s));  // ord (host) must outlive the copy
+    return SCC_OK;
+}
+
+}  // namespace scc

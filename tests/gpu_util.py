@@ -54,7 +54,8 @@ def self_loop_free(g):
 
 
 def sorted_rows(off, adj):
-    out = adj.copy()
-    for v in range(len(off) - 1):
-        out[off[v]:off[v + 1]] = np.sort(adj[off[v]:off[v + 1]])
-    return out
+    """adj with every CSR row sorted increasingly."""
+    off = np.asarray(off, dtype=np.int64)
+    row = np.repeat(np.arange(len(off) - 1), np.diff(off))
+    order = np.lexsort((adj, row))
+    return np.asarray(adj)[order]

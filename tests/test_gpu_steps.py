@@ -29,6 +29,7 @@ def _graphs():
     yield gg.torus(3, 12, 0.3, seed=5)
     yield gg.rmat(14, 8, seed=6)
     yield gg.knn(20000, 5, seed=7)
+    yield gg.rmat(20, 16, seed=8)  # ~40% empty rows: row searches end on empty rows
 
 
 @pytest.mark.parametrize("g", list(_graphs()), ids=lambda g: g.name)
@@ -170,3 +171,26 @@ def test_reach_multi_masks(g):
             scc.reach_multi(G.h, np.array([g.n], np.int32), 1, 0, np.empty(g.n, np.uint64))
         with pytest.raises(scc.SccError):
             scc.reach_multi(G.h, np.zeros(65, np.int32), 65, 0, np.empty(g.n, np.uint64))
+
+
+def test_transpose_large_vertex_count_direct_path():
+    """n above 2^26 takes the direct (global-atomic) transpose path."""
+    import torch
+    n = (1 << 26) + 5
+    rng = np.random.default_rng(99)
+    m = 1 << 20
+    src = np.sort(rng.integers(0, n, m))
+    dst = rng.integers(0, n, m).astype(np.int32)
+    off = np.zeros(n + 1, np.int32)
+    np.add.at(off, src + 1, 1)
+    off = np.cumsum(off).astype(np.int32)
+    g = gg.Graph(n, off, dst, "sparse_huge_n")
+    with make_graph(g) as G:
+        _, _, mt = scc.scc_graph_info(G.h)
+        toff = torch.empty(n + 1, dtype=torch.int32, device="cuda")
+        tadj = torch.empty(mt, dtype=torch.int32, device="cuda")
+        scc.scc_debug_csr(G.h, 1, toff, tadj)
+        toff_o, tadj_o = oracle.transpose(g.n, g.offsets, g.targets)
+        toff_h = toff.cpu().numpy()
+        assert np.array_equal(toff_h, toff_o)
+        assert np.array_equal(sorted_rows(toff_h, tadj.cpu().numpy()), tadj_o)
