@@ -41,6 +41,12 @@ struct scc_graph {
     unsigned long long* hit = nullptr;
     uint32_t* bits_f = nullptr;
     uint32_t* bits_b = nullptr;
+    uint32_t* fbits = nullptr;               // dense-round frontier bitmap (kept zero)
+    long long* bounds_d = nullptr;           // batch bounds on the device
+    int32_t* rem_pos = nullptr;              // remaining active pivot positions / vertices
+    int32_t* rem_v = nullptr;
+    int bounds_cap = 0;
+    void* bgss_ctl = nullptr;
     unsigned long long* counters = nullptr;  // [0] nact [1] ndone [2] scratch
     int* flags = nullptr;                    // [0] k [1] bad [2] overflow
     unsigned long long* tab[2] = {nullptr, nullptr};
@@ -176,7 +182,22 @@ int reserve_run_state(scc_graph* h, cudaStream_t s) {
     SCC_TRY(dalloc_t(&h->bits_b, nw, s));
     SCC_TRY(dalloc_t(&h->counters, 4, s));
     SCC_TRY(dalloc_t(&h->flags, 4, s));
+    SCC_TRY(dalloc_t(&h->fbits, nw, s));
+    SCC_CUDA(cudaMemsetAsync(h->fbits, 0, sizeof(uint32_t) * (size_t)std::max<int64_t>(nw, 1), s));
+    SCC_TRY(dalloc(&h->bgss_ctl, bgss_ctl_bytes(), s));
+    SCC_TRY(dalloc_t(&h->rem_pos, n, s));
+    SCC_TRY(dalloc_t(&h->rem_v, n, s));
     return SCC_OK;
+}
+
+DenseOpts dense_opts(const scc_graph* h, int dir, long long n_active) {
+    DenseOpts d;
+    d.roff = dir == 0 ? h->toff : h->off;  // in-arcs of the search direction
+    d.radj = dir == 0 ? h->tadj : h->adj;
+    d.fbits = h->fbits;
+    d.n_active = n_active;
+    d.frac_inv = h->cfg.dense ? 20 : 0;
+    return d;
 }
 
 int reserve_table(scc_graph* h, int d, int64_t cap, cudaStream_t s) {
@@ -209,53 +230,6 @@ struct EvTimer {
         return ms;
     }
 };
-
-// Forward and backward multi-reachability of one batch into tables tab[0], tab[1]
-// with the paper's sizing heuristic (Sec. 4.5): capacity pow2ceil(max(0.3 b,
-// 1.5 a)), a = pairs of the previous round in the same direction, b = active
-// vertices; an insertion that probes too far (or a load above 0.6) regrows the
-// table to twice the capacity and reruns that direction.
-int multi_search(scc_graph* h, int32_t k, int64_t b_active, int64_t a_prev[2], int64_t cap_out[2],
-                 int64_t pairs_out[2], cudaStream_t s, double* ms_search, double* ms_resize, int* rounds) {
-    EngineOpts o = opts_of(h);
-    for (int d = 0; d < 2; ++d) {
-        int64_t want = std::max<int64_t>((int64_t)std::ceil(0.3 * (double)b_active), (int64_t)std::ceil(1.5 * a_prev[d]));
-        want = std::max<int64_t>(want, 2 * (int64_t)k);
-        int64_t cap = std::max<int64_t>(pow2ceil(want), 1024);
-        const int32_t* off = d == 0 ? h->off : h->toff;
-        const int32_t* adj = d == 0 ? h->adj : h->tadj;
-        for (int attempt = 0;; ++attempt) {
-            if (attempt > 40) return SCC_ERR_CAPACITY;
-            EvTimer t(s);
-            t.start();
-            SCC_TRY(reserve_table(h, d, cap, s));
-            SCC_CUDA(cudaMemsetAsync(h->tab[d], 0xff, (size_t)cap * 8, s));
-            long long max_ins = (long long)(0.6 * (double)cap);
-            SCC_TRY(engine_reserve(&h->eb64, 8, max_ins + (1 << 20), h->cfg.lambda, h->mt, s));
-            EngineRun r;
-            int rc = run_pairs(off, adj, h->n, h->label, h->sources, k, h->tab[d], cap, max_ins, &h->eb64, o, &r, s);
-            double ms = t.stop();
-            *rounds += r.rounds;
-            h->stats.engine_launches++;
-            h->stats.ms_engine += r.ms;
-            h->stats.engine_arcs += (int64_t)r.edges;
-            h->stats.engine_items += (int64_t)r.items;
-            h->stats.engine_inserted += (int64_t)r.inserted;
-            if (rc == SCC_ERR_CAPACITY || r.overflow) {
-                *ms_resize += ms;
-                h->stats.table_resizes++;
-                cap *= 2;
-                continue;
-            }
-            SCC_TRY(rc);
-            *ms_search += ms;
-            cap_out[d] = cap;
-            pairs_out[d] = (int64_t)r.inserted;
-            break;
-        }
-    }
-    return SCC_OK;
-}
 
 }  // namespace
 
@@ -402,6 +376,11 @@ static void graph_free(scc_graph* h, cudaStream_t s) {
     dfree(h->flags, s);
     dfree(h->tab[0], s);
     dfree(h->tab[1], s);
+    dfree(h->fbits, s);
+    dfree(h->bounds_d, s);
+    dfree(h->bgss_ctl, s);
+    dfree(h->rem_pos, s);
+    dfree(h->rem_v, s);
     engine_release(&h->eb32, s);
     engine_release(&h->eb64, s);
 }
@@ -512,8 +491,8 @@ static int scc_run_impl(scc_graph* h, int32_t* labels_out, cudaStream_t s) {
         SCC_TRY(launch_prefill_bits(h->label, 0, n, h->bits_f, s));
         SCC_TRY(launch_prefill_bits(h->label, 0, n, h->bits_b, s));
         EngineRun r0, r1;
-        SCC_TRY(run_single(h->off, h->adj, n, s0, h->bits_f, &h->eb32, o, &r0, s));
-        SCC_TRY(run_single(h->toff, h->tadj, n, s0, h->bits_b, &h->eb32, o, &r1, s));
+        SCC_TRY(run_single(h->off, h->adj, n, s0, h->bits_f, dense_opts(h, 0, N), &h->eb32, o, &r0, s));
+        SCC_TRY(run_single(h->toff, h->tadj, n, s0, h->bits_b, dense_opts(h, 1, N), &h->eb32, o, &r1, s));
         SCC_TRY(launch_label_first(h->bits_f, h->bits_b, n, s0, h->label, h->rep, &h->counters[1], s));
         SCC_CUDA(cudaMemcpyAsync(hc, h->counters, sizeof(hc), cudaMemcpyDeviceToHost, s));
         st.ms_first_scc = t.stop();
@@ -527,31 +506,100 @@ static int scc_run_impl(scc_graph* h, int32_t* labels_out, cudaStream_t s) {
         }
         st.batches = 1;
 
-        // ---- multi-reachability batches (Alg. 1; Sec. 4.3-4.5)
-        int64_t a_prev[2] = {0, 0};
-        for (int i = 1; i < nb; ++i) {
-            const int64_t done = (int64_t)hc[1];
-            const int64_t b_active = N - done;
-            if (b_active <= 0) break;
-            SCC_CUDA(cudaMemsetAsync(h->flags, 0, sizeof(int), s));
-            SCC_TRY(launch_batch_sources(h->act, N, h->cfg.seed, bounds[i], bounds[i + 1], h->label, h->sources,
-                                         &h->flags[0], s));
-            int k = 0;
-            SCC_CUDA(cudaMemcpyAsync(&k, h->flags, sizeof(int), cudaMemcpyDeviceToHost, s));
+        // ---- multi-reachability batches (Alg. 1; Sec. 4.3-4.5): one device-side loop
+        if (nb > 1 && (int64_t)hc[1] < N) {
+            if (h->bounds_cap < nb + 1) {
+                dfree(h->bounds_d, s);
+                h->bounds_d = nullptr;
+                h->bounds_cap = 0;
+                SCC_TRY(dalloc_t(&h->bounds_d, (size_t)nb + 1, s));
+                h->bounds_cap = nb + 1;
+            }
+            SCC_CUDA(cudaMemcpyAsync(h->bounds_d, bounds.data(), sizeof(long long) * (size_t)(nb + 1),
+                                     cudaMemcpyHostToDevice, s));
+            long long tab_alloc = std::max<long long>(1 << 14, pow2ceil(4 * (int64_t)std::ceil(0.3 * (double)(N - (int64_t)hc[1]))));
+            BgssArgs a;
+            a.off = h->off;
+            a.adj = h->adj;
+            a.toff = h->toff;
+            a.tadj = h->tadj;
+            a.n = n;
+            a.label = h->label;
+            a.rep = h->rep;
+            a.fmax = h->fmax;
+            a.bmax = h->bmax;
+            a.hit = h->hit;
+            // the pivot positions after the first batch whose vertex is still active
+            SCC_TRY(launch_remaining(h->act, N, h->cfg.seed, bounds[1], h->label, h->tmp_a, h->tmp_b, h->scan_tmp,
+                                     h->rem_pos, h->rem_v, s));
+            int32_t nrem = 0;
+            SCC_CUDA(cudaMemcpyAsync(&nrem, h->tmp_b + (N - bounds[1]), sizeof(int32_t), cudaMemcpyDeviceToHost, s));
             SCC_CUDA(cudaStreamSynchronize(s));
-            if (k == 0) continue;
-            st.batches++;
-            int64_t cap[2], pairs[2];
-            SCC_TRY(multi_search(h, k, b_active, a_prev, cap, pairs, s, &st.ms_multi_search, &st.ms_resize,
-                                 &st.search_rounds));
-            st.pairs += pairs[0] + pairs[1];
-            a_prev[0] = pairs[0];
-            a_prev[1] = pairs[1];
-            t.start();
-            SCC_TRY(launch_label_pairs(h->tab[0], cap[0], h->tab[1], cap[1], (uint32_t)i, h->fmax, h->bmax, h->hit,
-                                       h->label, h->rep, &h->counters[1], s));
-            SCC_CUDA(cudaMemcpyAsync(hc, h->counters, sizeof(hc), cudaMemcpyDeviceToHost, s));
-            st.ms_label += t.stop();
+            a.rem_pos = h->rem_pos;
+            a.rem_v = h->rem_v;
+            a.nrem = nrem;
+            a.N = N;
+            a.bounds = h->bounds_d;
+            a.nb = nb;
+            a.first = 1;
+            a.sources = h->sources;
+            a.bgss_ctl = h->bgss_ctl;
+            a.ndone = hc[1];
+            a.a_prev[0] = a.a_prev[1] = 0;
+            a.o = o;
+            // Grid sized to the active vertices (about 16k per block): small
+            // remainders run on a few blocks, whose barriers cost far less.
+            const int full = bgss_full_grid(h->di.num_sms);
+            auto grid_for_active = [&](long long b) {
+                return (int)std::max<long long>(1, std::min<long long>(full, (b + 16383) / 16384));
+            };
+            auto plan = [&](long long b) {
+                a.grid = grid_for_active(b);
+                // relaunch once the grid could shrink fourfold
+                a.shrink_below = a.grid >= 4 ? (long long)(a.grid / 4) * 16384 : 0;
+            };
+            plan(N - (int64_t)hc[1]);
+            for (int attempt = 0;; ++attempt) {
+                if (attempt > 80) return SCC_ERR_CAPACITY;
+                SCC_TRY(reserve_table(h, 0, tab_alloc, s));
+                SCC_TRY(reserve_table(h, 1, tab_alloc, s));
+                void* old_slots = h->eb64.slots;
+                SCC_TRY(engine_reserve(&h->eb64, 8, (long long)(0.75 * (double)tab_alloc) + (1 << 20), h->cfg.lambda,
+                                       h->mt, s));
+                if (attempt > 0 && h->eb64.slots == old_slots)  // a stopped launch may leave items in the bag
+                    SCC_CUDA(cudaMemsetAsync(h->eb64.slots, 0xff, (size_t)h->eb64.nslots * 8, s));
+                a.tab[0] = h->tab[0];
+                a.tab[1] = h->tab[1];
+                a.tab_alloc = tab_alloc;
+                a.eb = &h->eb64;
+                BgssResult r;
+                SCC_TRY(run_bgss_device(a, &r, s));
+                st.ms_multi_search += r.ms;
+                st.batches += r.batches;
+                st.search_rounds += r.rounds;
+                st.pairs += (int64_t)r.pairs;
+                st.engine_arcs += (int64_t)r.edges;
+                st.engine_items += (int64_t)r.items;
+                st.engine_inserted += (int64_t)r.pairs;
+                hc[1] = r.ndone;
+                if (r.status == 0) break;
+                if (r.status == 2) {
+                    a.first = r.batch;
+                    a.ndone = r.ndone;
+                    a.a_prev[0] = r.a_prev[0];
+                    a.a_prev[1] = r.a_prev[1];
+                    a.first_min_cap = 0;
+                    plan(N - (int64_t)r.ndone);
+                    continue;
+                }
+                st.table_resizes++;
+                tab_alloc = std::max<long long>(tab_alloc, pow2ceil(r.need_cap));
+                a.first = r.batch;
+                a.first_min_cap = r.need_cap;
+                a.ndone = r.ndone;
+                a.a_prev[0] = r.a_prev[0];
+                a.a_prev[1] = r.a_prev[1];
+            }
         }
         if ((int64_t)hc[1] != N) return SCC_ERR_INTERNAL;  // every active vertex must be finished
     }
@@ -688,8 +736,8 @@ int scc_debug_single_reach(scc_handle h, const int32_t* labels, int32_t src, int
         if (rc == SCC_OK) rc = engine_reserve(&h->eb32, 4, (long long)n + 1024, h->cfg.lambda, h->mt, s);
         EngineRun r;
         if (rc == SCC_OK)
-            rc = run_single(dir == 0 ? h->off : h->toff, dir == 0 ? h->adj : h->tadj, n, src, h->bits_f, &h->eb32,
-                            opts_of(h), &r, s);
+            rc = run_single(dir == 0 ? h->off : h->toff, dir == 0 ? h->adj : h->tadj, n, src, h->bits_f,
+                            dense_opts(h, dir, n), &h->eb32, opts_of(h), &r, s);
         if (rc == SCC_OK) rc = launch_bits_to_bytes(h->bits_f, dl, L, n, d, s);
     }
     if (rc == SCC_OK) rc = from_device(visited, d, (size_t)n, s);

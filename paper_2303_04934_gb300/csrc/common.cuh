@@ -79,6 +79,11 @@ struct GridBarrier {
 constexpr uint64_t kBarrierTimeoutNs = 4000000000ull;  // 4 s
 
 __device__ __forceinline__ bool grid_sync(GridBarrier* b, int* err) {
+    if (gridDim.x == 1) {  // a one-block grid needs no global arrival counter
+        __threadfence_block();
+        __syncthreads();
+        return true;
+    }
     __syncthreads();
     __shared__ int s_ok;
     if (threadIdx.x == 0) {
@@ -107,6 +112,39 @@ __device__ __forceinline__ bool grid_sync(GridBarrier* b, int* err) {
     __syncthreads();
     return s_ok != 0;
 }
+
+// ---------------------------------------------------------- pivot order --
+// Seeded bijection of [0, N): 4-round balanced Feistel network on the smallest
+// even bit width b >= 2 with 2^b >= N, round function low(b/2) bits of
+// mix64(key_r ^ R), key_r = mix64(seed + (r + 1) * golden), then cycle walking
+// into [0, N) (Black & Rogaway, CT-RSA 2002).
+struct Feistel {
+    uint64_t key[4];
+    int half;
+    uint64_t mask;
+    __host__ __device__ void init(uint64_t seed, uint64_t N) {
+        for (int r = 0; r < 4; ++r) key[r] = mix64(seed + (uint64_t)(r + 1) * 0x9E3779B97F4A7C15ull);
+        int b = 2;
+        while (b < 62 && (1ull << b) < N) b += 2;
+        half = b / 2;
+        mask = (1ull << half) - 1;
+    }
+    __host__ __device__ uint64_t once(uint64_t x) const {
+        uint64_t L = x >> half, R = x & mask;
+        for (int r = 0; r < 4; ++r) {
+            uint64_t F = mix64(key[r] ^ R) & mask;
+            uint64_t t = L ^ F;
+            L = R;
+            R = t;
+        }
+        return (L << half) | R;
+    }
+    __host__ __device__ uint64_t perm(uint64_t p, uint64_t N) const {
+        uint64_t y = once(p);
+        while (y >= N) y = once(y);
+        return y;
+    }
+};
 
 // ------------------------------------------------------------ misc helpers --
 __host__ __device__ __forceinline__ int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }

@@ -269,39 +269,93 @@ __device__ __forceinline__ void expand_batch(const EngineParams<typename Pol::It
     items += (lane == 0) ? (unsigned long long)take : 0ull;
 }
 
-template <class Pol>
-__global__ void __launch_bounds__(256) engine_kernel(EngineParams<typename Pol::Item> P, Pol pol_in) {
-    Pol pol = pol_in;
+// Dense (bottom-up) rounds of a single-reachability search (Sec. 4.2): every
+// unvisited vertex of the class scans its in-arcs (the reverse CSR) and stops at
+// the first one whose tail is in the current frontier. Used when the frontier
+// holds at least n_active / frac_inv items.
+struct DenseParams {
+    const int32_t* roff;  // reverse CSR (G^T for a forward search, G for a backward one)
+    const int32_t* radj;
+    uint32_t* fbits;      // frontier bitmap scratch, ceil(n/32) words, all zero between rounds
+    long long n_active;   // vertices of the class
+    int frac_inv;         // 0 = never dense
+};
+
+// The initial items of a search: either an explicit list or the pairs (s, s)
+// of a source list.
+template <class Item>
+struct InitList {
+    const Item* items;
+    __device__ __forceinline__ Item operator()(long long i) const { return items[i]; }
+};
+struct InitPairs {
+    const int32_t* sources;
+    __device__ __forceinline__ uint64_t operator()(long long i) const {
+        uint32_t s = (uint32_t)sources[i];
+        return ((uint64_t)s << 32) | s;
+    }
+};
+
+// Per-warp accumulators of a search (folded into the control block at the end).
+struct WarpStats {
+    unsigned long long edges = 0, items = 0;
+};
+
+// One complete reachability search (Alg. 3 rounds) executed by every thread of a
+// cooperative grid. Returns false if a grid barrier timed out (the caller must
+// return at once). On return all blocks have passed the final barrier, so the
+// control block's counters of this search are final.
+template <class Pol, class Init>
+__device__ bool engine_search(EngineParams<typename Pol::Item> P, Pol& pol, Init init, long long ninit,
+                              const DenseParams* dp, typename Pol::Item* q, WarpStats& ws) {
     using Item = typename Pol::Item;
     constexpr uint32_t QM = Pol::kQueue - 1;
-    __shared__ EngineSmem<Pol> sm;
-    __shared__ long long s_tile[2];
+    __shared__ long long s_tile[1];
+    __shared__ int s_wsum[32];
     EngineCtl* ctl = P.ctl;
     const int lane = lane_id();
     const int wib = threadIdx.x >> 5;
     const uint32_t wid = (uint32_t)(blockIdx.x * (blockDim.x >> 5) + wib);
     const uint32_t nwarps = (uint32_t)(gridDim.x * (blockDim.x >> 5));
-    Item* q = sm.q + wib * Pol::kQueue;
-    unsigned long long edges = 0, items = 0;
-    long long inserted_acc = 0;
+
+    // ---- fresh per-search state (the bag slots are already empty)
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        for (int p = 0; p < 2; ++p) {
+            ctl->fsize[p] = 0;
+            ctl->work[p] = 0;
+            ctl->hubseg[p] = 0;
+            ctl->nhub[p] = 0;
+            ctl->bag[p].r = 0;
+            for (int j = 0; j < kMaxChunks; ++j) ctl->bag[p].sample[j] = 0;
+        }
+        ctl->overflow = 0;
+        ctl->inserted = 0;
+        ctl->rounds = 0;
+    }
+    if (!grid_sync(&ctl->bar, &ctl->err)) return false;
 
     // ---- round -1: the initial items (marked visited) go into bag[1]
     {
         SegState st{-1, 0, 0};
-        for (long long b = (long long)wid * 32; b < P.ninit; b += (long long)nwarps * 32) {
+        long long ins = 0;
+        for (long long b = (long long)wid * 32; b < ninit; b += (long long)nwarps * 32) {
             long long i = b + lane;
             bool has = false;
             Item it = Sent<Item>::empty;
-            if (i < P.ninit) {
-                it = P.init[i];
+            if (i < ninit) {
+                it = init(i);
                 has = pol.seed(it);
             }
-            inserted_acc += __popc(__ballot_sync(kFull, has)) * (lane == 0);
+            ins += __popc(__ballot_sync(kFull, has));
             bag_push<Item>(P, &ctl->bag[1], st, has, it, wid, 0xffffu);
         }
+        if constexpr (Pol::kCountInserts) {
+            if (lane == 0 && ins) atomicAdd(&ctl->inserted, (unsigned long long)ins);
+        }
     }
-    if (!grid_sync(&ctl->bar, &ctl->err)) return;
+    if (!grid_sync(&ctl->bar, &ctl->err)) return false;
 
+    bool prev_dense = false;
     for (uint32_t iter = 0;; ++iter) {
         const int p = iter & 1;
         // ---- ExtractAll: pack bag[(iter+1)&1]'s used prefix into the frontier
@@ -356,7 +410,6 @@ __global__ void __launch_bounds__(256) engine_kernel(EngineParams<typename Pol::
 #pragma unroll
                 for (int d = 16; d >= 1; d >>= 1) wsum += __shfl_xor_sync(kFull, wsum, d);
                 int wpre = warp_incl_scan(nl) - nl;
-                __shared__ int s_wsum[32];
                 if (lane == 0) s_wsum[wib] = wsum;
                 __syncthreads();
                 if (threadIdx.x == 0) {
@@ -379,8 +432,17 @@ __global__ void __launch_bounds__(256) engine_kernel(EngineParams<typename Pol::
                     }
                 __syncthreads();
             }
+            // the frontier bitmap of a previous dense round is cleared here
+            if constexpr (Pol::kDense) {
+                if (prev_dense) {
+                    const long long nw = ((long long)P.n + 31) / 32;
+                    for (long long w = (long long)blockIdx.x * blockDim.x + threadIdx.x; w < nw;
+                         w += (long long)gridDim.x * blockDim.x)
+                        if (dp->fbits[w]) dp->fbits[w] = 0;
+                }
+            }
         }
-        if (!grid_sync(&ctl->bar, &ctl->err)) return;
+        if (!grid_sync(&ctl->bar, &ctl->err)) return false;
         if (ld_volatile(&ctl->err) != 0) break;
         const long long fsize = ld_volatile(&ctl->fsize[p]);
         const int nhub = min(ld_volatile(&ctl->nhub[p]), P.hub_cap);
@@ -399,52 +461,103 @@ __global__ void __launch_bounds__(256) engine_kernel(EngineParams<typename Pol::
         SegState st{-1, 0, (uint32_t)(wid * 2654435761u)};
         const bool stop = P.max_inserted > 0 && ld_volatile(&ctl->overflow) != 0;
 
-        // ---- phase A: hub segments, shared by all warps ("in parallel")
-        const long long nseg = min(ld_volatile(&ctl->hubseg[p]), P.segmap_cap);
-        for (long long g = wid; g < nseg && !stop; g += nwarps) {
-            const int h = P.segmap[g];
-            if (h < 0) continue;
-            const Item hit = P.hub_item[h];
-            const long long j0 = (g - P.hub_segbase[h]) * kHubSeg;
-            const int b0 = P.hub_beg[h] + (int)j0;
-            const int len = (int)min((long long)kHubSeg, (long long)P.hub_deg[h] - j0);
-            const uint64_t hctx = pol.ctx(hit);
-            for (int e0 = 0; e0 < len; e0 += 32) {
-                bool nw = false;
-                Item child = Sent<Item>::empty;
-                if (e0 + lane < len) {
-                    int w = __ldg(&P.adj[b0 + e0 + lane]);
-                    nw = pol.visit(hit, hctx, w, child);
-                }
-                bag_push<Item>(P, bc, st, nw, child, wid, iter);
-            }
-            edges += lane == 0 ? (unsigned long long)len : 0ull;
-            items += (lane == 0 && g == P.hub_segbase[h]) ? 1ull : 0ull;
+        bool dense = false;
+        if constexpr (Pol::kDense) {
+            dense = dp != nullptr && dp->frac_inv > 0 &&
+                    (long long)(fsize + nhub) * (long long)dp->frac_inv >= dp->n_active;
         }
-
-        // ---- phase B: warp tasks over the light frontier (VGC local searches)
-        for (;;) {
-            long long b = 0;
-            if (lane == 0) b = (long long)atomicAdd((unsigned long long*)&ctl->work[p], (unsigned long long)P.seeds);
-            b = __shfl_sync(kFull, b, 0);
-            if (b >= fsize) break;
-            if (P.max_inserted > 0 && ld_volatile(&ctl->overflow) != 0) break;
-            int cnt = (int)min((long long)P.seeds, fsize - b);
-            if (lane < cnt) q[lane] = P.front[b + lane];
-            __syncwarp();
-            uint32_t qh = 0, qt = (uint32_t)cnt;
-            int t = 0;
-            expand_batch<Pol>(P, pol, bc, st, wid, iter, q, qh, qt, t, true, edges, items);
-            while (qt != qh && t < P.tau)
-                expand_batch<Pol>(P, pol, bc, st, wid, iter, q, qh, qt, t, false, edges, items);
-            // budget spent: flush what is left in the local queue
-            while (qt != qh) {
-                int nrem = (int)min(32u, qt - qh);
-                Item it = lane < nrem ? q[(qh + lane) & QM] : Sent<Item>::empty;
-                qh += nrem;
-                bag_push<Item>(P, bc, st, lane < nrem, it, wid, iter);
+        prev_dense = dense;
+        if (dense) {
+            if constexpr (Pol::kDense) {
+                // ---- dense round: frontier bitmap, then bottom-up over unvisited vertices
+                for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < fsize + nhub;
+                     i += (long long)gridDim.x * blockDim.x) {
+                    const int v = pol.vertex(i < fsize ? P.front[i] : P.hub_item[i - fsize]);
+                    atomicOr(&dp->fbits[v >> 5], 1u << (v & 31));
+                }
+                if (!grid_sync(&ctl->bar, &ctl->err)) return false;
+                const long long nw = ((long long)P.n + 31) / 32;
+                for (long long w = wid; w < nw; w += nwarps) {
+                    const uint32_t word = pol.bits[w];
+                    const long long v = w * 32 + lane;
+                    bool found = false;
+                    unsigned long long scanned = 0;
+                    if (v < P.n && !((word >> lane) & 1u)) {
+                        const int e0 = __ldg(&dp->roff[v]), e1 = __ldg(&dp->roff[v + 1]);
+                        for (int e = e0; e < e1; ++e) {
+                            const int u = __ldg(&dp->radj[e]);
+                            ++scanned;
+                            if ((ld_volatile(&dp->fbits[u >> 5]) >> (u & 31)) & 1u) {
+                                found = true;
+                                break;
+                            }
+                        }
+                    }
+                    const uint32_t m = __ballot_sync(kFull, found);
+                    if (lane == 0 && m) pol.bits[w] = word | m;  // this warp owns word w in this round
+                    for (int d = 16; d >= 1; d >>= 1) scanned += __shfl_xor_sync(kFull, scanned, d);
+                    if (lane == 0) {
+                        ws.edges += scanned;
+                        ws.items += __popc(m);
+                    }
+                    bag_push<Item>(P, bc, st, found, (Item)v, wid, iter);
+                }
             }
-            __syncwarp();
+        } else {
+            // ---- phase A: hub segments, shared by all warps ("in parallel")
+            const long long nseg = min(ld_volatile(&ctl->hubseg[p]), P.segmap_cap);
+            for (long long g = wid; g < nseg && !stop; g += nwarps) {
+                const int h = P.segmap[g];
+                if (h < 0) continue;
+                const Item hit = P.hub_item[h];
+                const long long j0 = (g - P.hub_segbase[h]) * kHubSeg;
+                const int b0 = P.hub_beg[h] + (int)j0;
+                const int len = (int)min((long long)kHubSeg, (long long)P.hub_deg[h] - j0);
+                const uint64_t hctx = pol.ctx(hit);
+                for (int e0 = 0; e0 < len; e0 += 32) {
+                    bool nw = false;
+                    Item child = Sent<Item>::empty;
+                    if (e0 + lane < len) {
+                        int w = __ldg(&P.adj[b0 + e0 + lane]);
+                        nw = pol.visit(hit, hctx, w, child);
+                    }
+                    bag_push<Item>(P, bc, st, nw, child, wid, iter);
+                }
+                ws.edges += lane == 0 ? (unsigned long long)len : 0ull;
+                ws.items += (lane == 0 && g == P.hub_segbase[h]) ? 1ull : 0ull;
+            }
+
+            // ---- phase B: warp tasks over the light frontier (VGC local searches)
+            for (;;) {
+                long long b = 0;
+                if (lane == 0) b = (long long)atomicAdd((unsigned long long*)&ctl->work[p], (unsigned long long)P.seeds);
+                b = __shfl_sync(kFull, b, 0);
+                if (b >= fsize) break;
+                if (P.max_inserted > 0 && ld_volatile(&ctl->overflow) != 0) break;
+                int cnt = (int)min((long long)P.seeds, fsize - b);
+                if (lane < cnt) q[lane] = P.front[b + lane];
+                __syncwarp();
+                uint32_t qh = 0, qt = (uint32_t)cnt;
+                int t = 0;
+                expand_batch<Pol>(P, pol, bc, st, wid, iter, q, qh, qt, t, true, ws.edges, ws.items);
+                while (qt != qh && t < P.tau)
+                    expand_batch<Pol>(P, pol, bc, st, wid, iter, q, qh, qt, t, false, ws.edges, ws.items);
+                // budget spent: flush what is left in the local queue
+                while (qt != qh) {
+                    int nrem = (int)min(32u, qt - qh);
+                    Item it = lane < nrem ? q[(qh + lane) & QM] : Sent<Item>::empty;
+                    qh += nrem;
+                    bag_push<Item>(P, bc, st, lane < nrem, it, wid, iter);
+                }
+                __syncwarp();
+                if constexpr (Pol::kCountInserts) {
+                    long long c = pol.take_inserted();
+                    if (c && lane == 0) {
+                        unsigned long long tot = atomicAdd(&ctl->inserted, (unsigned long long)c) + c;
+                        if (P.max_inserted > 0 && (long long)tot > P.max_inserted) atomicExch(&ctl->overflow, 1);
+                    }
+                }
+            }
             if constexpr (Pol::kCountInserts) {
                 long long c = pol.take_inserted();
                 if (c && lane == 0) {
@@ -453,21 +566,23 @@ __global__ void __launch_bounds__(256) engine_kernel(EngineParams<typename Pol::
                 }
             }
         }
-        if constexpr (Pol::kCountInserts) {
-            long long c = pol.take_inserted();
-            if (c && lane == 0) {
-                unsigned long long tot = atomicAdd(&ctl->inserted, (unsigned long long)c) + c;
-                if (P.max_inserted > 0 && (long long)tot > P.max_inserted) atomicExch(&ctl->overflow, 1);
-            }
-        }
-        if (!grid_sync(&ctl->bar, &ctl->err)) return;
+        if (!grid_sync(&ctl->bar, &ctl->err)) return false;
         if (P.max_inserted > 0 && ld_volatile(&ctl->overflow) != 0) break;
     }
-    if (lane == 0 && edges) atomicAdd(&ctl->edges, edges);
-    if (lane == 0 && items) atomicAdd(&ctl->items, items);
-    if constexpr (Pol::kCountInserts) {
-        if (lane == 0 && inserted_acc) atomicAdd(&ctl->inserted, (unsigned long long)inserted_acc);
-    }
+    return true;
+}
+
+template <class Pol>
+__global__ void __launch_bounds__(256) engine_kernel(EngineParams<typename Pol::Item> P, Pol pol_in, DenseParams dp) {
+    Pol pol = pol_in;
+    __shared__ EngineSmem<Pol> sm;
+    typename Pol::Item* q = sm.q + (threadIdx.x >> 5) * Pol::kQueue;
+    WarpStats ws;
+    const bool ok = engine_search<Pol>(P, pol, InitList<typename Pol::Item>{P.init}, P.ninit,
+                                       dp.frac_inv > 0 ? &dp : nullptr, q, ws);
+    if (!ok) return;
+    if (lane_id() == 0 && ws.edges) atomicAdd(&P.ctl->edges, ws.edges);
+    if (lane_id() == 0 && ws.items) atomicAdd(&P.ctl->items, ws.items);
 }
 
 // ---------------------------------------------------------------- policies --
@@ -478,6 +593,7 @@ struct PolSingle {
     using Item = uint32_t;
     static constexpr int kQueue = 512;
     static constexpr bool kCountInserts = false;
+    static constexpr bool kDense = true;
     uint32_t* bits;
     __device__ __forceinline__ int vertex(Item it) const { return (int)it; }
     __device__ __forceinline__ uint64_t ctx(Item) const { return 0; }
@@ -535,6 +651,7 @@ struct PolPair {
     using Item = uint64_t;
     static constexpr int kQueue = 256;
     static constexpr bool kCountInserts = true;
+    static constexpr bool kDense = false;
     const int32_t* label;
     PairTable tab;
     long long ins;
@@ -563,6 +680,7 @@ struct PolMask {
     using Item = uint32_t;
     static constexpr int kQueue = 512;
     static constexpr bool kCountInserts = false;
+    static constexpr bool kDense = false;
     unsigned long long* mask;
     __device__ __forceinline__ int vertex(Item it) const { return (int)it; }
     __device__ __forceinline__ uint64_t ctx(Item it) const { return ld_volatile(&mask[it]); }

@@ -90,6 +90,12 @@ int launch_compact_active(const int32_t* label, int32_t n, int32_t* flags_tmp, i
 // sources = { act[pi(p)] : p in [p0, p1), label >= 0 }, *k = count (device).
 int launch_batch_sources(const int32_t* act, int64_t N, uint64_t seed, int64_t p0, int64_t p1, const int32_t* label,
                          int32_t* sources, int* k, cudaStream_t s);
+// Pivot positions p in [p0, N) whose vertex act[pi(p)] is still active, in
+// increasing p: rem_pos[j] = p, rem_v[j] = the vertex; their number is
+// pos_tmp[N - p0] after the call (exclusive scan of the flags).
+int launch_remaining(const int32_t* act, int64_t N, uint64_t seed, int64_t p0, const int32_t* label,
+                     int32_t* flags_tmp, int32_t* pos_tmp, void* scan_tmp, int32_t* rem_pos, int32_t* rem_v,
+                     cudaStream_t s);
 // order[p] = act[pi(p)] for p < N (debug hook).
 int launch_pivot_order(const int32_t* act, int64_t N, uint64_t seed, int32_t* order, cudaStream_t s);
 
@@ -177,9 +183,19 @@ struct EngineOpts {
     int num_sms = 0;
 };
 
+// Dense-round inputs of a single-reachability search (Sec. 4.2 dense mode):
+// the reverse CSR, a zeroed frontier bitmap and the class size; frac_inv = 0
+// disables dense rounds.
+struct DenseOpts {
+    const int32_t* roff = nullptr;
+    const int32_t* radj = nullptr;
+    uint32_t* fbits = nullptr;
+    long long n_active = 0;
+    int frac_inv = 0;
+};
 // Single reachability from `s` over (off, adj) with the bitmap (already prefilled).
-int run_single(const int32_t* off, const int32_t* adj, int32_t n, int32_t s, uint32_t* bits, EngineBuf* b,
-               const EngineOpts& o, EngineRun* out, cudaStream_t st);
+int run_single(const int32_t* off, const int32_t* adj, int32_t n, int32_t s, uint32_t* bits, const DenseOpts& dn,
+               EngineBuf* b, const EngineOpts& o, EngineRun* out, cudaStream_t st);
 // Multi reachability: init pairs (s,s) from sources (device int32[k]); pairs into table.
 int run_pairs(const int32_t* off, const int32_t* adj, int32_t n, const int32_t* label, const int32_t* sources,
               int32_t k, unsigned long long* table, int64_t cap, long long max_inserted, EngineBuf* b,
@@ -187,6 +203,48 @@ int run_pairs(const int32_t* off, const int32_t* adj, int32_t n, const int32_t* 
 // Mask reachability: mask already holds the source bits; init = sources.
 int run_mask(const int32_t* off, const int32_t* adj, int32_t n, const int32_t* sources, int32_t k,
              unsigned long long* mask, EngineBuf* b, const EngineOpts& o, EngineRun* out, cudaStream_t st);
+
+// Device-side loop over the multi-reachability batches (bgss.cu).
+struct BgssArgs {
+    const int32_t *off, *adj, *toff, *tadj;
+    int32_t n;
+    int32_t* label;
+    int32_t* rep;
+    unsigned long long *fmax, *bmax, *hit;
+    const int32_t* rem_pos;   // remaining active pivot positions (increasing) and their vertices
+    const int32_t* rem_v;
+    long long nrem;
+    long long N;              // active vertices after trimming (pivot positions)
+    const long long* bounds;  // device, nb + 1 entries
+    int nb;
+    int first;
+    long long first_min_cap = 0;
+    long long shrink_below = 0;  // return with status 2 once fewer vertices are active
+    int grid = 0;                // blocks of the cooperative launch (0 = all co-resident)
+    int32_t* sources;
+    unsigned long long* tab[2];
+    long long tab_alloc;
+    EngineBuf* eb;
+    void* bgss_ctl;  // device, bgss_ctl_bytes()
+    unsigned long long ndone;
+    unsigned long long a_prev[2];
+    EngineOpts o;
+};
+struct BgssResult {
+    float ms = 0;
+    int status = 0;  // 0 finished; 1 grow to need_cap and resume at batch; 2 resume with a smaller grid
+    int batch = 0;
+    long long need_cap = 0;
+    unsigned long long ndone = 0;
+    unsigned long long a_prev[2] = {0, 0};
+    unsigned long long pairs = 0;
+    int batches = 0;
+    int rounds = 0;
+    unsigned long long edges = 0, items = 0;
+};
+size_t bgss_ctl_bytes();
+int bgss_full_grid(int num_sms);
+int run_bgss_device(const BgssArgs& a, BgssResult* res, cudaStream_t st);
 
 // Debug: hash bag alone (vertex items).
 int run_bag_only(const int32_t* items, int64_t count, int lambda, int sigma, int32_t* out, int64_t* nout,

@@ -36,11 +36,11 @@ int coop_grid(int num_sms, int* grid) {
 
 template <class Pol>
 int launch_engine(EngineParams<typename Pol::Item>& P, Pol& pol, const EngineOpts& o, EngineRun* out,
-                  cudaStream_t st) {
+                  cudaStream_t st, DenseParams dp = DenseParams{nullptr, nullptr, nullptr, 0, 0}) {
     int grid = 0;
     SCC_TRY(coop_grid<Pol>(o.num_sms, &grid));
     SCC_CUDA(cudaMemsetAsync(P.ctl, 0, sizeof(EngineCtl), st));
-    void* args[] = {(void*)&P, (void*)&pol};
+    void* args[] = {(void*)&P, (void*)&pol, (void*)&dp};
     cudaEvent_t e0, e1;
     SCC_CUDA(cudaEventCreate(&e0));
     SCC_CUDA(cudaEventCreate(&e1));
@@ -155,15 +155,16 @@ void engine_release(EngineBuf* b, cudaStream_t s) {
     *b = EngineBuf();
 }
 
-int run_single(const int32_t* off, const int32_t* adj, int32_t n, int32_t s, uint32_t* bits, EngineBuf* b,
-               const EngineOpts& o, EngineRun* out, cudaStream_t st) {
+int run_single(const int32_t* off, const int32_t* adj, int32_t n, int32_t s, uint32_t* bits, const DenseOpts& dn,
+               EngineBuf* b, const EngineOpts& o, EngineRun* out, cudaStream_t st) {
     auto P = make_params<uint32_t>(off, adj, n, b, o);
     SCC_TRY(reserve_init(b, sizeof(uint32_t), st));
     SCC_CUDA(cudaMemcpyAsync(b->init, &s, sizeof(int32_t), cudaMemcpyHostToDevice, st));
     P.init = reinterpret_cast<const uint32_t*>(b->init);
     P.ninit = 1;
     PolSingle pol{bits};
-    int rc = launch_engine(P, pol, o, out, st);
+    DenseParams dp{dn.roff, dn.radj, dn.fbits, dn.n_active, dn.frac_inv};
+    int rc = launch_engine(P, pol, o, out, st, dp);
     if (rc != SCC_OK || out->err) SCC_TRY(reset_slots(b, st));
     SCC_TRY(rc);
     return out->err ? out->err : SCC_OK;

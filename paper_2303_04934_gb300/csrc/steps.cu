@@ -12,6 +12,7 @@
 #include "common.cuh"
 #include "engine.cuh"
 #include "internal.h"
+#include "labels.cuh"
 
 namespace scc {
 
@@ -201,38 +202,6 @@ __global__ void k_init_labels(const int32_t* __restrict__ off, const int32_t* __
 }
 
 // ----------------------------------------------------------------- pivots --
-// Seeded bijection of [0, N): 4-round balanced Feistel network on the smallest
-// even bit width b >= 2 with 2^b >= N, round function low(b/2) bits of
-// mix64(key_r ^ R), key_r = mix64(seed + (r + 1) * golden), then cycle walking
-// into [0, N) (Black & Rogaway, CT-RSA 2002).
-struct Feistel {
-    uint64_t key[4];
-    int half;
-    uint64_t mask;
-    __host__ __device__ void init(uint64_t seed, uint64_t N) {
-        for (int r = 0; r < 4; ++r) key[r] = mix64(seed + (uint64_t)(r + 1) * 0x9E3779B97F4A7C15ull);
-        int b = 2;
-        while (b < 62 && (1ull << b) < N) b += 2;
-        half = b / 2;
-        mask = (1ull << half) - 1;
-    }
-    __host__ __device__ uint64_t once(uint64_t x) const {
-        uint64_t L = x >> half, R = x & mask;
-        for (int r = 0; r < 4; ++r) {
-            uint64_t F = mix64(key[r] ^ R) & mask;
-            uint64_t t = L ^ F;
-            L = R;
-            R = t;
-        }
-        return (L << half) | R;
-    }
-    __host__ __device__ uint64_t perm(uint64_t p, uint64_t N) const {
-        uint64_t y = once(p);
-        while (y >= N) y = once(y);
-        return y;
-    }
-};
-
 __global__ void k_pivot_order(const int32_t* __restrict__ act, int64_t N, Feistel f, int32_t* order) {
     for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < N; p += (int64_t)gridDim.x * blockDim.x)
         order[p] = act[f.perm((uint64_t)p, (uint64_t)N)];
@@ -253,6 +222,23 @@ __global__ void k_batch_sources(const int32_t* __restrict__ act, int64_t N, Feis
         base = __shfl_sync(kFull, base, 0);
         if (v >= 0) sources[base + __popc(msk & lanemask_lt())] = v;
     }
+}
+
+// Remaining pivot positions p >= p0 whose vertex is still active, in order.
+__global__ void k_rem_flags(const int32_t* __restrict__ act, int64_t N, Feistel f, int64_t p0,
+                            const int32_t* __restrict__ label, int32_t* flags) {
+    for (int64_t p = p0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < N; p += (int64_t)gridDim.x * blockDim.x)
+        flags[p - p0] = label[act[f.perm((uint64_t)p, (uint64_t)N)]] >= 0;
+}
+__global__ void k_rem_scatter(const int32_t* __restrict__ act, int64_t N, Feistel f, int64_t p0,
+                              const int32_t* __restrict__ flags, const int32_t* __restrict__ pos, int32_t* rem_pos,
+                              int32_t* rem_v) {
+    for (int64_t p = p0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < N; p += (int64_t)gridDim.x * blockDim.x)
+        if (flags[p - p0]) {
+            const int32_t j = pos[p - p0];
+            rem_pos[j] = (int32_t)p;
+            rem_v[j] = act[f.perm((uint64_t)p, (uint64_t)N)];
+        }
 }
 
 __global__ void k_active_flags(const int32_t* __restrict__ label, int32_t n, int32_t* flags) {
@@ -308,62 +294,19 @@ __global__ void k_label_first(const uint32_t* __restrict__ bf, const uint32_t* _
     if (lane_id() == 0 && c) atomicAdd(ndone, c);
 }
 
-// Pass 1 over T_out: per vertex the largest source reaching it (round-tagged
-// 64-bit max, so no reset between rounds) and, if the pair is also in T_in, the
-// largest source in R1 n R2.
-__global__ void k_label_scan_fwd(const unsigned long long* __restrict__ tf, int64_t capf, PairTable tb,
-                                 unsigned long long tag, unsigned long long* fmax, unsigned long long* hit) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < capf; i += (int64_t)gridDim.x * blockDim.x) {
-        unsigned long long key = tf[i];
-        if (key == ~0ull) continue;
-        uint32_t v = (uint32_t)(key >> 32), s = (uint32_t)key;
-        atomicMax(&fmax[v], tag | s);
-        if (tb.contains(key)) atomicMax(&hit[v], tag | s);
-    }
-}
-__global__ void k_label_scan_bwd(const unsigned long long* __restrict__ tb, int64_t capb, unsigned long long tag,
-                                 unsigned long long* bmax) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < capb; i += (int64_t)gridDim.x * blockDim.x) {
-        unsigned long long key = tb[i];
-        if (key == ~0ull) continue;
-        atomicMax(&bmax[(uint32_t)(key >> 32)], tag | (uint32_t)key);
-    }
-}
-// Pass 2: exactly one table entry per touched vertex (the one carrying its
-// maximum) rewrites its label: finished (rep = max of R1 n R2) or the hash of its
-// old class and its two maxima.
-__device__ __forceinline__ void finalize_vertex(uint32_t v, unsigned long long tag, const unsigned long long* fmax,
-                                                const unsigned long long* bmax, const unsigned long long* hit,
-                                                int32_t* label, int32_t* rep, unsigned long long& c) {
-    unsigned long long h = hit[v], f = fmax[v], b = bmax[v];
-    if ((h & 0xffffffff00000000ull) == tag) {
-        label[v] = kDone;
-        rep[v] = (int32_t)(uint32_t)h;
-        ++c;
-    } else {
-        int32_t a = (f & 0xffffffff00000000ull) == tag ? (int32_t)(uint32_t)f : -1;
-        int32_t bb = (b & 0xffffffff00000000ull) == tag ? (int32_t)(uint32_t)b : -1;
-        label[v] = class_hash(label[v], a, bb);
-    }
+__global__ void k_label_scan(const unsigned long long* __restrict__ tf, int64_t capf, PairTable tb,
+                             unsigned long long tag, unsigned long long* fmax, unsigned long long* bmax,
+                             unsigned long long* hit) {
+    const long long i0 = (long long)blockIdx.x * blockDim.x + threadIdx.x, st = (long long)gridDim.x * blockDim.x;
+    label_scan(i0, st, tf, capf, tb, tag, fmax, bmax, hit);
 }
 __global__ void k_label_finalize(const unsigned long long* __restrict__ tf, int64_t capf,
                                  const unsigned long long* __restrict__ tb, int64_t capb, unsigned long long tag,
                                  const unsigned long long* fmax, const unsigned long long* bmax,
                                  const unsigned long long* hit, int32_t* label, int32_t* rep,
                                  unsigned long long* ndone) {
-    unsigned long long c = 0;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < capf + capb;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        bool fw = i < capf;
-        unsigned long long key = fw ? tf[i] : tb[i - capf];
-        if (key == ~0ull) continue;
-        uint32_t v = (uint32_t)(key >> 32), s = (uint32_t)key;
-        unsigned long long f = fmax[v];
-        bool owner;
-        if (fw) owner = f == (tag | s);
-        else owner = (f & 0xffffffff00000000ull) != tag && bmax[v] == (tag | s);
-        if (owner) finalize_vertex(v, tag, fmax, bmax, hit, label, rep, c);
-    }
+    const long long i0 = (long long)blockIdx.x * blockDim.x + threadIdx.x, st = (long long)gridDim.x * blockDim.x;
+    unsigned long long c = label_finalize(i0, st, tf, capf, tb, capb, tag, fmax, bmax, hit, label, rep);
     for (int d = 16; d >= 1; d >>= 1) c += __shfl_xor_sync(kFull, c, d);
     if (lane_id() == 0 && c) atomicAdd(ndone, c);
 }
@@ -541,6 +484,21 @@ int launch_batch_sources(const int32_t* act, int64_t N, uint64_t seed, int64_t p
     return SCC_OK;
 }
 
+int launch_remaining(const int32_t* act, int64_t N, uint64_t seed, int64_t p0, const int32_t* label,
+                     int32_t* flags_tmp, int32_t* pos_tmp, void* scan_tmp, int32_t* rem_pos, int32_t* rem_v,
+                     cudaStream_t s) {
+    const int64_t cnt = N - p0;
+    if (cnt <= 0) return SCC_OK;
+    Feistel f;
+    f.init(seed, (uint64_t)N);
+    k_rem_flags<<<grid_for(cnt, kBlk), kBlk, 0, s>>>(act, N, f, p0, label, flags_tmp);
+    SCC_LAUNCH();
+    SCC_TRY(launch_scan(flags_tmp, pos_tmp, cnt, scan_tmp, s));
+    k_rem_scatter<<<grid_for(cnt, kBlk), kBlk, 0, s>>>(act, N, f, p0, flags_tmp, pos_tmp, rem_pos, rem_v);
+    SCC_LAUNCH();
+    return SCC_OK;
+}
+
 int launch_pivot_order(const int32_t* act, int64_t N, uint64_t seed, int32_t* order, cudaStream_t s) {
     if (N == 0) return SCC_OK;
     Feistel f;
@@ -581,9 +539,7 @@ int launch_label_pairs(const unsigned long long* tf, int64_t capf, const unsigne
                        cudaStream_t s) {
     unsigned long long tag = (unsigned long long)round_tag << 32;
     PairTable tbt{const_cast<unsigned long long*>(tb), (unsigned long long)(capb - 1), nullptr};
-    k_label_scan_fwd<<<grid_for(capf, kBlk), kBlk, 0, s>>>(tf, capf, tbt, tag, fmax, hit);
-    SCC_LAUNCH();
-    k_label_scan_bwd<<<grid_for(capb, kBlk), kBlk, 0, s>>>(tb, capb, tag, bmax);
+    k_label_scan<<<grid_for(capf + capb, kBlk), kBlk, 0, s>>>(tf, capf, tbt, tag, fmax, bmax, hit);
     SCC_LAUNCH();
     k_label_finalize<<<grid_for(capf + capb, kBlk), kBlk, 0, s>>>(tf, capf, tb, capb, tag, fmax, bmax, hit, label,
                                                                     rep, ndone);
