@@ -172,13 +172,17 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="rmat24", choices=sorted(WORKLOADS))
+    ap.add_argument("--rmat-scale", type=int, default=None,
+                    help="profiling aid: R-MAT scale instead of the workload's (not a bench line)")
     ap.add_argument("--tau", type=int, default=None)
     ap.add_argument("--seeds", type=int, default=None)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--verbose", action="store_true")
     args = ap.parse_args()
-    spec = WORKLOADS[args.workload]
+    spec = dict(WORKLOADS[args.workload])
+    if args.rmat_scale and spec["kind"] == "rmat":
+        spec["scale"] = args.rmat_scale
     if args.impl == "reference":
         return run_reference(args, spec)
 

@@ -182,8 +182,8 @@ int reserve_run_state(scc_graph* h, cudaStream_t s) {
     SCC_TRY(dalloc_t(&h->bits_b, nw, s));
     SCC_TRY(dalloc_t(&h->counters, 4, s));
     SCC_TRY(dalloc_t(&h->flags, 4, s));
-    SCC_TRY(dalloc_t(&h->fbits, nw, s));
-    SCC_CUDA(cudaMemsetAsync(h->fbits, 0, sizeof(uint32_t) * (size_t)std::max<int64_t>(nw, 1), s));
+    SCC_TRY(dalloc_t(&h->fbits, 2 * nw, s));
+    SCC_CUDA(cudaMemsetAsync(h->fbits, 0, sizeof(uint32_t) * (size_t)std::max<int64_t>(2 * nw, 1), s));
     SCC_TRY(dalloc(&h->bgss_ctl, bgss_ctl_bytes(), s));
     SCC_TRY(dalloc_t(&h->rem_pos, n, s));
     SCC_TRY(dalloc_t(&h->rem_v, n, s));
@@ -194,7 +194,9 @@ DenseOpts dense_opts(const scc_graph* h, int dir, long long n_active) {
     DenseOpts d;
     d.roff = dir == 0 ? h->toff : h->off;  // in-arcs of the search direction
     d.radj = dir == 0 ? h->tadj : h->adj;
-    d.fbits = h->fbits;
+    const int64_t nw = ((int64_t)h->n + 31) / 32;
+    d.fbits[0] = h->fbits;
+    d.fbits[1] = h->fbits + nw;
     d.n_active = n_active;
     d.frac_inv = h->cfg.dense ? 20 : 0;
     return d;
@@ -547,27 +549,32 @@ static int scc_run_impl(scc_graph* h, int32_t* labels_out, cudaStream_t s) {
             a.ndone = hc[1];
             a.a_prev[0] = a.a_prev[1] = 0;
             a.o = o;
-            // Grid sized to the active vertices (about 16k per block): small
-            // remainders run on a few blocks, whose barriers cost far less.
+            // Grid sized to the active vertices (about 2k per block, at least 16
+            // blocks): small remainders run on fewer blocks, whose barriers cost
+            // less; the launch stops for a smaller grid once it could shrink 4x.
             const int full = bgss_full_grid(h->di.num_sms);
+            const int min_grid = std::min(16, full);
             auto grid_for_active = [&](long long b) {
-                return (int)std::max<long long>(1, std::min<long long>(full, (b + 16383) / 16384));
+                return (int)std::max<long long>(min_grid, std::min<long long>(full, (b + 2047) / 2048));
             };
             auto plan = [&](long long b) {
                 a.grid = grid_for_active(b);
-                // relaunch once the grid could shrink fourfold
-                a.shrink_below = a.grid >= 4 ? (long long)(a.grid / 4) * 16384 : 0;
+                a.shrink_below = a.grid >= 4 * min_grid ? (long long)(a.grid / 4) * 2048 : 0;
             };
             plan(N - (int64_t)hc[1]);
+            bool fresh = true;  // tables (and bag) must be emptied before the next launch
             for (int attempt = 0;; ++attempt) {
                 if (attempt > 80) return SCC_ERR_CAPACITY;
                 SCC_TRY(reserve_table(h, 0, tab_alloc, s));
                 SCC_TRY(reserve_table(h, 1, tab_alloc, s));
-                void* old_slots = h->eb64.slots;
                 SCC_TRY(engine_reserve(&h->eb64, 8, (long long)(0.75 * (double)tab_alloc) + (1 << 20), h->cfg.lambda,
                                        h->mt, s));
-                if (attempt > 0 && h->eb64.slots == old_slots)  // a stopped launch may leave items in the bag
-                    SCC_CUDA(cudaMemsetAsync(h->eb64.slots, 0xff, (size_t)h->eb64.nslots * 8, s));
+                if (fresh) {  // the kernel keeps both tables empty between batches
+                    SCC_CUDA(cudaMemsetAsync(h->tab[0], 0xff, (size_t)tab_alloc * 8, s));
+                    SCC_CUDA(cudaMemsetAsync(h->tab[1], 0xff, (size_t)tab_alloc * 8, s));
+                    SCC_TRY(engine_reset_slots(&h->eb64, s));
+                    fresh = false;
+                }
                 a.tab[0] = h->tab[0];
                 a.tab[1] = h->tab[1];
                 a.tab_alloc = tab_alloc;
@@ -583,7 +590,7 @@ static int scc_run_impl(scc_graph* h, int32_t* labels_out, cudaStream_t s) {
                 st.engine_inserted += (int64_t)r.pairs;
                 hc[1] = r.ndone;
                 if (r.status == 0) break;
-                if (r.status == 2) {
+                if (r.status == 2) {  // stopped between batches: tables and bag are empty
                     a.first = r.batch;
                     a.ndone = r.ndone;
                     a.a_prev[0] = r.a_prev[0];
@@ -592,6 +599,7 @@ static int scc_run_impl(scc_graph* h, int32_t* labels_out, cudaStream_t s) {
                     plan(N - (int64_t)r.ndone);
                     continue;
                 }
+                fresh = true;  // stopped inside a batch
                 st.table_resizes++;
                 tab_alloc = std::max<long long>(tab_alloc, pow2ceil(r.need_cap));
                 a.first = r.batch;

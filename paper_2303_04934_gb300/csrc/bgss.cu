@@ -19,6 +19,10 @@
 
 namespace scc {
 
+template <class Item>
+EngineParams<Item> make_engine_params(const int32_t* off, const int32_t* adj, int32_t n, const EngineBuf* b,
+                                      const EngineOpts& o);
+
 struct BgssCtl {
     int status;                 // 0 finished, 1 grow tables/bag and resume at `batch`, 2 relaunch smaller
     int batch;
@@ -79,7 +83,7 @@ __device__ __forceinline__ long long pow2ceil_d(long long x) {
     return p;
 }
 
-__global__ void __launch_bounds__(256) bgss_kernel(BgssParams B) {
+__global__ void __launch_bounds__(256, 2) bgss_kernel(BgssParams B) {
     __shared__ EngineSmem<PolPair> sm;
     uint64_t* q = sm.q + (threadIdx.x >> 5) * PolPair::kQueue;
     WarpStats ws;
@@ -90,6 +94,8 @@ __global__ void __launch_bounds__(256) bgss_kernel(BgssParams B) {
     const int lane = lane_id();
     int status = 0, stop_batch = B.nb;
     long long need = 0;
+    uint32_t g = 0;   // global round counter of the engine (same in every block)
+    uint32_t si = 0;  // search index
     for (int i = B.first; i < B.nb; ++i) {
         const int kb = i & 1;
         // ---- sources of batch i: the still-active vertices among its pivot
@@ -137,9 +143,7 @@ __global__ void __launch_bounds__(256) bgss_kernel(BgssParams B) {
             need = max(cap[0], cap[1]);
             break;
         }
-        for (int d = 0; d < 2; ++d)
-            for (long long j = gtid; j < cap[d]; j += gstride) B.tab[d][j] = ~0ull;
-        if (!grid_sync(&ctl->bar, &ctl->err)) return;
+        // (the tables are empty: the previous batch's last pass reset every entry)
         // ---- forward (G) and backward (G^T) multi-reachability
         long long pairs[2];
         bool grow = false;
@@ -152,14 +156,15 @@ __global__ void __launch_bounds__(256) bgss_kernel(BgssParams B) {
             pol.label = B.label;
             pol.tab.keys = B.tab[d];
             pol.tab.mask = (unsigned long long)(cap[d] - 1);
-            pol.tab.overflow = &ctl->overflow;
+            SearchCtl& sc = ctl->search[si % 3];
+            pol.tab.overflow = &sc.overflow;
             pol.ins = 0;
-            if (!engine_search<PolPair>(P, pol, InitPairs{B.sources}, k, nullptr, q, ws)) return;
-            const int ovf = ld_volatile(&ctl->overflow);
+            if (!engine_search<PolPair>(P, pol, InitPairs{B.sources}, k, nullptr, q, ws, g, si)) return;
+            ++si;
+            const int ovf = ld_volatile(&sc.overflow);
             const int err = ld_volatile(&ctl->err);
-            pairs[d] = (long long)ld_volatile(&ctl->inserted);
-            const int rounds = ld_volatile(&ctl->rounds);
-            if (!grid_sync(&ctl->bar, &ctl->err)) return;  // everyone has read the counters
+            pairs[d] = (long long)ld_volatile(&sc.inserted);
+            const int rounds = ld_volatile(&sc.rounds);
             if (err != 0 && err != SCC_ERR_CAPACITY) return;
             if (ovf || err == SCC_ERR_CAPACITY) {
                 grow = true;
@@ -178,7 +183,7 @@ __global__ void __launch_bounds__(256) bgss_kernel(BgssParams B) {
         label_scan(gtid, gstride, B.tab[0], cap[0], tb, tag, B.fmax, B.bmax, B.hit);
         if (!grid_sync(&ctl->bar, &ctl->err)) return;
         unsigned long long c = label_finalize(gtid, gstride, B.tab[0], cap[0], B.tab[1], cap[1], tag, B.fmax,
-                                              B.bmax, B.hit, B.label, B.rep);
+                                              B.bmax, B.hit, B.label, B.rep, true);
         for (int d = 16; d >= 1; d >>= 1) c += __shfl_xor_sync(kFull, c, d);
         if (lane == 0 && c) atomicAdd(&bc->ndone, c);
         if (gtid == 0) {
@@ -227,24 +232,7 @@ int run_bgss_device(const BgssArgs& a, BgssResult* res, cudaStream_t st) {
     B.tab[1] = a.tab[1];
     B.tab_alloc = a.tab_alloc;
     EngineBuf* b = a.eb;
-    B.P.n = a.n;
-    B.P.tau = a.o.tau;
-    B.P.hub_thr = a.o.tau;
-    B.P.seeds = a.o.seeds;
-    B.P.slots = (uint64_t*)b->slots;
-    B.P.nslots = b->nslots;
-    B.P.lambda = b->lambda;
-    B.P.sigma = a.o.sigma;
-    B.P.front = (uint64_t*)b->front;
-    B.P.front_cap = b->front_cap;
-    B.P.hub_item = (uint64_t*)b->hub_item;
-    B.P.hub_beg = b->hub_beg;
-    B.P.hub_deg = b->hub_deg;
-    B.P.hub_segbase = b->hub_segbase;
-    B.P.hub_cap = b->hub_cap;
-    B.P.segmap = b->segmap;
-    B.P.segmap_cap = b->segmap_cap;
-    B.P.ctl = b->ctl;
+    B.P = make_engine_params<uint64_t>(a.off, a.adj, a.n, b, a.o);
     // control block for this launch
     BgssCtl* dbc = reinterpret_cast<BgssCtl*>(a.bgss_ctl);
     BgssCtl h;

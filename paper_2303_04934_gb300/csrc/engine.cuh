@@ -1,9 +1,10 @@
 // Reachability engine: vertical granularity control (VGC) local searches over a
-// hash-bag frontier, in one persistent cooperative kernel (sm_103a).
+// hash-bag frontier, in persistent cooperative kernels (sm_103a).
 //
 // Paper: Wang, Dong, Gu, Sun, SIGMOD 2023.
 //  - Alg. 3 (reachability with a hash bag): rounds; every frontier item is
-//    expanded, newly visited items go to the bag H, F_{i+1} = H.ExtractAll().
+//    expanded and newly visited items go to the bag that forms the next
+//    frontier.
 //  - Sec. 3.1-3.2 (VGC): an item is expanded by a local search that keeps
 //    newly visited items in a local queue and keeps expanding them until about
 //    tau arcs have been examined; what is left in the queue is flushed to the
@@ -12,33 +13,37 @@
 //    of lambda, 2*lambda, ... slots; inserts go to a random position of the
 //    current chunk r with CAS and linear probing; sampled inserts count towards
 //    sigma, at which point r advances by CAS (also after kappa failed probes);
-//    ExtractAll packs the used prefix.
+//    ForAll visits the used prefix and skips empty slots.
+//  - Sec. 4.2: single-reachability may run dense (bottom-up) rounds.
 //
 // GPU mapping (what differs from the 96-core design):
-//  - The unit of a local search is a WARP task, not a thread: a warp takes up to
-//    `seeds` frontier items, keeps its local queue in shared memory and expands
-//    the next batch of queued items cooperatively (one arc per lane: a warp scan
-//    of the batch's degrees and a 5-step shuffle search map lanes to arcs, so
-//    reads of each adjacency row are coalesced). tau bounds the arcs of a task.
-//  - "Expand in parallel" = hub items: an item with more than tau out-arcs
-//    found inside a local search is returned to the bag; at extraction it is
-//    cut into 1024-arc segments that all warps share in the next round.
-//  - The hash bag is claimed in 32-slot segments (one CAS per segment, at a
+//  - The hash bag is claimed in 32-slot segments (one CAS per segment at a
 //    random segment of the current chunk, linear probing over segments), so a
 //    warp writes its spills as full 128/256-byte lines. Sampling and the chunk
-//    advance are as in Fig. 5 but counted per segment claim.
-//  - Rounds are separated by a grid barrier inside one cooperative launch; the
+//    advance are as in Fig. 5, counted per segment claim.
+//  - The next round visits the bag in place (the ForAll operation): one 32-slot
+//    segment is one WARP task. The warp reads the segment, resets its slots,
+//    and runs a local search from the segment's items with its queue in shared
+//    memory, expanding queued items cooperatively (one arc per lane: a warp
+//    scan of the batch's degrees and a 5-step shuffle search map lanes to arcs,
+//    so reads of each adjacency row are coalesced). tau bounds a task's arcs.
+//    Two slot arrays alternate between rounds, so a round needs one grid
+//    barrier and no packing pass.
+//  - "Expand in parallel" = hub items: an item with more than tau out-arcs is
+//    set aside when its segment is read and cut into 1024-arc segments that all
+//    warps share in the next round.
+//  - Rounds are separated by grid barriers inside one cooperative launch; the
 //    host is not involved between rounds.
 #pragma once
 #include "common.cuh"
 
 namespace scc {
 
-constexpr int kSeg = 32;         // slots per hash-bag segment
-constexpr int kHubSeg = 1024;    // arcs of one hub segment
+constexpr int kSeg = 32;          // slots per hash-bag segment = items of one warp task
+constexpr int kHubSeg = 1024;     // arcs of one hub segment
 constexpr int kMaxChunks = 48;
-constexpr int kBagProbe = 16;    // kappa: segment probes before a chunk advance
-constexpr int kTableProbe = 256; // pair-table probe limit (then: overflow, regrow)
+constexpr int kBagProbe = 16;     // kappa: segment probes before a chunk advance
+constexpr int kTableProbe = 256;  // pair-table probe limit (then: overflow, regrow)
 
 template <class Item>
 struct Sent;
@@ -52,24 +57,40 @@ struct Sent<uint64_t> {
 };
 
 struct BagCtl {
-    int r;                     // current chunk
-    int sample[kMaxChunks];    // sampled segment claims per chunk
+    int r;                   // current chunk
+    int sample[kMaxChunks];  // sampled segment claims per chunk
+};
+
+// Per-round state, a ring of three indexed by the global round number g: round
+// g inserts into ring[g % 3] (and slot array g % 2), reads what round g - 1 left
+// in ring[(g + 2) % 3] (slot array (g + 1) % 2), and block 0 clears
+// ring[(g + 1) % 3] for round g + 1 -- nobody touches that entry in round g.
+struct RoundCtl {
+    BagCtl bag;
+    long long items;   // items inserted into this round's bag
+    long long hubseg;  // hub segments reserved this round
+    long long work;    // next warp task of this round (dynamic assignment)
+    int nhub;          // hub items set aside this round (expanded next round)
+    int pad;
+};
+
+// Per-search state, a ring of three indexed by the search index: search s
+// resets entry (s + 1) % 3, last used by search s - 2, whose counters every block
+// read before search s - 1 began.
+struct SearchCtl {
+    int overflow;                 // pair table over its load or probe limit
+    int rounds;                   // rounds executed
+    unsigned long long inserted;  // newly visited items (pairs in pair mode)
 };
 
 struct EngineCtl {
     GridBarrier bar;
     int err;        // first error (SCC_ERR_*)
-    int overflow;   // pair table over its load limit / probe limit
-    int rounds;     // extraction rounds executed
     int max_chunk;  // largest bag chunk used
-    long long fsize[2];
-    long long work[2];
-    long long hubseg[2];
-    int nhub[2];
-    BagCtl bag[2];
-    unsigned long long edges;     // arcs examined
-    unsigned long long inserted;  // newly visited items (pairs in pair mode)
-    unsigned long long items;     // items expanded (adjacency rows read)
+    RoundCtl ring[3];
+    SearchCtl search[3];
+    unsigned long long edges;  // arcs examined
+    unsigned long long items;  // items expanded (adjacency rows read)
 };
 
 template <class Item>
@@ -77,25 +98,23 @@ struct EngineParams {
     const int32_t* off;
     const int32_t* adj;
     int32_t n;
-    int tau;       // VGC arc budget per warp task
-    int hub_thr;   // out-degree above which an item is a hub
-    int seeds;     // frontier items per warp task (<= 32)
-    // hash bag
-    Item* slots;
+    int tau;      // VGC arc budget per warp task
+    int hub_thr;  // out-degree above which an item is a hub
+    int seeds;    // items of a task expanded regardless of the budget (<= 32)
+    // hash bag: two slot arrays, alternating between rounds
+    Item* slots[2];
     long long nslots;
     int lambda;
     int sigma;
-    // frontier and hub lists (one buffer each; counters are double-buffered)
-    Item* front;
-    long long front_cap;
-    Item* hub_item;
-    int32_t* hub_beg;
-    int32_t* hub_deg;
-    long long* hub_segbase;
+    // hub lists, alternating between rounds
+    Item* hub_item[2];
+    int32_t* hub_beg[2];
+    int32_t* hub_deg[2];
+    long long* hub_segbase[2];
     int hub_cap;
-    int32_t* segmap;
+    int32_t* segmap[2];
     long long segmap_cap;
-    // initial items, pushed before round 0
+    // initial items (standalone launches)
     const Item* init;
     long long ninit;
     long long max_inserted;  // pair-mode load limit (0 = none)
@@ -112,6 +131,17 @@ __device__ __forceinline__ long long chunk_end(int lambda, int j, long long nslo
 }
 
 // ------------------------------------------------------------- bag writer --
+template <class Item>
+struct BagRef {
+    Item* slots;
+    long long nslots;
+    int lambda;
+    int sigma;
+    BagCtl* bc;
+    int* err;
+    int* max_chunk;
+};
+
 // Warp-uniform state of the segment a warp is filling.
 struct SegState {
     long long base;  // slot index of the segment, -1 = none
@@ -121,152 +151,181 @@ struct SegState {
 
 // Claim a free segment of the current chunk (lane 0 only). Returns slot index or
 // -1 (bag exhausted: error recorded).
-template <class Item, class P>
-__device__ long long bag_claim(const P& prm, BagCtl* bc, uint32_t wid, uint32_t round, uint32_t& seq) {
+template <class Item>
+__device__ long long bag_claim(const BagRef<Item>& b, uint32_t wid, uint32_t round, uint32_t& seq) {
     for (int attempt = 0; attempt < 4 * kMaxChunks; ++attempt) {
-        int r = ld_volatile(&bc->r);
-        long long cb = chunk_begin(prm.lambda, r);
-        long long ce = chunk_end(prm.lambda, r, prm.nslots);
-        long long nseg = (ce - cb) / kSeg;
+        const int r = ld_volatile(&b.bc->r);
+        const long long cb = chunk_begin(b.lambda, r);
+        const long long ce = chunk_end(b.lambda, r, b.nslots);
+        const long long nseg = (ce - cb) / kSeg;
         if (nseg <= 0) {
-            atomicCAS(&prm.ctl->err, 0, SCC_ERR_CAPACITY);
+            atomicCAS(b.err, 0, SCC_ERR_CAPACITY);
             return -1;
         }
-        uint64_t h = mix64(((uint64_t)wid << 40) ^ ((uint64_t)round << 20) ^ (uint64_t)(seq++) ^ 0x5bd1e995ull);
-        long long pos = (long long)(h % (uint64_t)nseg);
+        const uint64_t h = mix64(((uint64_t)wid << 40) ^ ((uint64_t)round << 20) ^ (uint64_t)(seq++) ^ 0x5bd1e995ull);
+        const long long pos = (long long)(h % (uint64_t)nseg);
         for (int pr = 0; pr < kBagProbe; ++pr) {
-            long long idx = cb + ((pos + pr) % nseg) * kSeg;
-            Item prev = atomicCAS((typename std::conditional<sizeof(Item) == 8, unsigned long long, unsigned int>::type*)&prm.slots[idx],
-                                  Sent<Item>::empty, Sent<Item>::claimed);
+            const long long idx = cb + ((pos + pr) % nseg) * kSeg;
+            using W = typename std::conditional<sizeof(Item) == 8, unsigned long long, unsigned int>::type;
+            const Item prev = atomicCAS(reinterpret_cast<W*>(&b.slots[idx]), (W)Sent<Item>::empty,
+                                        (W)Sent<Item>::claimed);
             if (prev == Sent<Item>::empty) {
                 // sampled claim: rate sigma / (alpha * nseg), alpha = 1/2
-                uint32_t rnd = (uint32_t)(h >> 32);
-                double rate = 2.0 * prm.sigma / (double)nseg;
+                const uint32_t rnd = (uint32_t)(h >> 32);
+                const double rate = 2.0 * b.sigma / (double)nseg;
                 if (rate >= 1.0 || (double)rnd < rate * 4294967296.0) {
-                    int s = atomicAdd(&bc->sample[r], 1) + 1;
-                    if (s >= prm.sigma && ce < prm.nslots) atomicCAS(&bc->r, r, r + 1);
+                    const int s = atomicAdd(&b.bc->sample[r], 1) + 1;
+                    if (s >= b.sigma && ce < b.nslots) atomicCAS(&b.bc->r, r, r + 1);
                 }
-                if (r > ld_volatile(&prm.ctl->max_chunk)) atomicMax(&prm.ctl->max_chunk, r);
+                if (r > ld_volatile(b.max_chunk)) atomicMax(b.max_chunk, r);
                 return idx;
             }
         }
         // kappa probes failed: the chunk is (nearly) full -> try_resize
-        if (ce >= prm.nslots) {
-            atomicCAS(&prm.ctl->err, 0, SCC_ERR_CAPACITY);
+        if (ce >= b.nslots) {
+            atomicCAS(b.err, 0, SCC_ERR_CAPACITY);
             return -1;
         }
-        atomicCAS(&bc->r, r, r + 1);
+        atomicCAS(&b.bc->r, r, r + 1);
     }
-    atomicCAS(&prm.ctl->err, 0, SCC_ERR_CAPACITY);
+    atomicCAS(b.err, 0, SCC_ERR_CAPACITY);
     return -1;
 }
 
 // Warp-cooperative insert of the items of lanes with `has` (all lanes call).
-template <class Item, class P>
-__device__ __forceinline__ void bag_push(const P& prm, BagCtl* bc, SegState& st, bool has, Item it, uint32_t wid,
-                                         uint32_t round) {
-    uint32_t m = __ballot_sync(kFull, has);
+// Returns the number of items inserted by the warp.
+template <class Item>
+__device__ __forceinline__ int bag_push(const BagRef<Item>& b, SegState& st, bool has, Item it, uint32_t wid,
+                                        uint32_t round) {
+    const uint32_t m = __ballot_sync(kFull, has);
     int cnt = __popc(m);
-    if (cnt == 0) return;
+    const int total = cnt;
+    if (cnt == 0) return 0;
     int rank = __popc(m & lanemask_lt());
     while (cnt > 0) {
         if (st.base < 0 || st.fill == kSeg) {
-            long long b = -1;
-            if (lane_id() == 0) b = bag_claim<Item>(prm, bc, wid, round, st.seq);
-            b = __shfl_sync(kFull, b, 0);
+            long long base = -1;
+            if (lane_id() == 0) base = bag_claim<Item>(b, wid, round, st.seq);
+            base = __shfl_sync(kFull, base, 0);
             st.seq = __shfl_sync(kFull, st.seq, 0);
-            if (b < 0) return;  // error recorded
-            st.base = b;
+            if (base < 0) return total;  // error recorded
+            st.base = base;
             st.fill = 0;
         }
-        int space = kSeg - st.fill;
-        if (has && rank >= 0 && rank < space) prm.slots[st.base + st.fill + rank] = it;
-        int used = cnt < space ? cnt : space;
+        const int space = kSeg - st.fill;
+        if (has && rank >= 0 && rank < space) b.slots[st.base + st.fill + rank] = it;
+        const int used = cnt < space ? cnt : space;
         st.fill += used;
         rank -= used;
         cnt -= used;
         if (rank < 0) has = false;
     }
+    return total;
 }
 
-// ------------------------------------------------------------- the kernel --
+// ------------------------------------------------------------ warp tasks --
 template <class Pol>
 struct EngineSmem {
     typename Pol::Item q[8 * Pol::kQueue];  // up to 8 warps per block share this
 };
 
+// Per-warp accumulators (folded into the control block at the end).
+struct WarpStats {
+    unsigned long long edges = 0, items = 0;
+};
+
+// Expand the next batch of queued items (up to 32, or `max_take` in the seeds
+// phase, which ignores the budget and the hub test).
 template <class Pol>
-__device__ __forceinline__ void expand_batch(const EngineParams<typename Pol::Item>& P, Pol& pol, BagCtl* bc,
-                                             SegState& st, uint32_t wid, uint32_t round,
-                                             typename Pol::Item* q, uint32_t& qh, uint32_t& qt, int& t,
-                                             bool seeds_phase, unsigned long long& edges,
-                                             unsigned long long& items) {
+__device__ __forceinline__ void expand_batch(const EngineParams<typename Pol::Item>& P, Pol& pol,
+                                             const BagRef<typename Pol::Item>& out, SegState& st, uint32_t wid,
+                                             uint32_t round, typename Pol::Item* q, uint32_t& qh, uint32_t& qt,
+                                             int& t, bool seeds_phase, int max_take, WarpStats& ws,
+                                             unsigned long long& pushed) {
     using Item = typename Pol::Item;
     constexpr uint32_t QM = Pol::kQueue - 1;
     const int lane = lane_id();
     int avail = (int)min(32u, qt - qh);
+    if (seeds_phase && avail > max_take) avail = max_take;
     Item it = Sent<Item>::empty;
     int beg = 0, deg = 0;
     if (lane < avail) {
         it = q[(qh + lane) & QM];
-        int u = pol.vertex(it);
+        const int u = pol.vertex(it);
         beg = __ldg(&P.off[u]);
         deg = __ldg(&P.off[u + 1]) - beg;
     }
-    // items past the seed batch with more than hub_thr arcs go back to the bag
+    // items past the seeds with more than hub_thr arcs go back to the bag
     bool hub = !seeds_phase && lane < avail && deg > P.hub_thr;
     int d = (lane < avail && !hub) ? deg : 0;
     int pre = warp_incl_scan(d);
     int take = avail;
     if (!seeds_phase) {
-        int remaining = P.tau - t;
-        uint32_t m = __ballot_sync(kFull, lane < avail && (pre - d) < remaining);
+        const int remaining = P.tau - t;
+        const uint32_t m = __ballot_sync(kFull, lane < avail && (pre - d) < remaining);
         take = __popc(m);
         if (take < 1) take = 1;
-        if (lane >= take) { d = 0; hub = false; }
+        if (lane >= take) {
+            d = 0;
+            hub = false;
+        }
         pre = warp_incl_scan(d);
     }
     qh += take;
-    bag_push<Item>(P, bc, st, hub, it, wid, round);
-    uint64_t ctx = (lane < take && !hub) ? pol.ctx(it) : 0;
+    pushed += bag_push<Item>(out, st, hub, it, wid, round);
+    const uint64_t ctx = (lane < take && !hub) ? pol.ctx(it) : 0;
     const int total = __shfl_sync(kFull, pre, 31);
     const int excl = pre - d;
-    for (int base = 0; base < total; base += 32) {
-        const int e = base + lane;
-        // owner lane: number of lanes whose inclusive prefix is <= e
-        int j = 0;
+    // four groups of 32 arcs per step: the adjacency loads and the visit tests of
+    // the groups are independent, so their memory latencies overlap
+    constexpr int U = 4;
+    for (int base = 0; base < total; base += 32 * U) {
+        int w[U];
+        Item jit[U];
+        uint64_t jctx[U];
 #pragma unroll
-        for (int step = 16; step >= 1; step >>= 1) {
-            int v = __shfl_sync(kFull, pre, j + step - 1);
-            if (v <= e) j += step;
+        for (int u = 0; u < U; ++u) {
+            const int e = base + u * 32 + lane;
+            // owner lane: number of lanes whose inclusive prefix is <= e
+            int j = 0;
+#pragma unroll
+            for (int step = 16; step >= 1; step >>= 1) {
+                const int v = __shfl_sync(kFull, pre, j + step - 1);
+                if (v <= e) j += step;
+            }
+            const int jexcl = __shfl_sync(kFull, excl, j);
+            const int jbeg = __shfl_sync(kFull, beg, j);
+            jit[u] = shfl_any(it, j);
+            jctx[u] = shfl_any(ctx, j);
+            w[u] = e < total ? __ldg(&P.adj[jbeg + (e - jexcl)]) : -1;
         }
-        const int jexcl = __shfl_sync(kFull, excl, j);
-        const int jbeg = __shfl_sync(kFull, beg, j);
-        const Item jit = shfl_any(it, j);
-        const uint64_t jctx = shfl_any(ctx, j);
-        bool nw = false;
-        Item child = Sent<Item>::empty;
-        if (e < total) {
-            int w = __ldg(&P.adj[jbeg + (e - jexcl)]);
-            nw = pol.visit(jit, jctx, w, child);
+        bool nw[U];
+        Item child[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            child[u] = Sent<Item>::empty;
+            nw[u] = w[u] >= 0 && pol.visit(jit[u], jctx[u], w[u], child[u]);
         }
-        // new items: local queue while it has room, the bag otherwise
-        uint32_t m = __ballot_sync(kFull, nw);
-        int cnt = __popc(m);
-        if (cnt) {
-            int rank = __popc(m & lanemask_lt());
-            int room = (int)(Pol::kQueue - (qt - qh));
-            bool toq = nw && rank < room;
-            if (toq) q[(qt + rank) & QM] = child;
-            int nq = cnt < room ? cnt : room;
-            bag_push<Item>(P, bc, st, nw && !toq, child, wid, round);
-            qt += nq;
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            // new items: local queue while it has room, the bag otherwise
+            const uint32_t m = __ballot_sync(kFull, nw[u]);
+            const int cnt = __popc(m);
+            if (cnt) {
+                const int rank = __popc(m & lanemask_lt());
+                const int room = (int)(Pol::kQueue - (qt - qh));
+                const bool toq = nw[u] && rank < room;
+                if (toq) q[(qt + rank) & QM] = child[u];
+                const int nq = cnt < room ? cnt : room;
+                pushed += bag_push<Item>(out, st, nw[u] && !toq, child[u], wid, round);
+                qt += nq;
+            }
         }
         __syncwarp();
     }
     t += total;
-    edges += (lane == 0) ? (unsigned long long)total : 0ull;
-    items += (lane == 0) ? (unsigned long long)take : 0ull;
+    ws.edges += (lane == 0) ? (unsigned long long)total : 0ull;
+    ws.items += (lane == 0) ? (unsigned long long)take : 0ull;
 }
 
 // Dense (bottom-up) rounds of a single-reachability search (Sec. 4.2): every
@@ -276,7 +335,7 @@ __device__ __forceinline__ void expand_batch(const EngineParams<typename Pol::It
 struct DenseParams {
     const int32_t* roff;  // reverse CSR (G^T for a forward search, G for a backward one)
     const int32_t* radj;
-    uint32_t* fbits;      // frontier bitmap scratch, ceil(n/32) words, all zero between rounds
+    uint32_t* fbits[2];   // frontier bitmaps (alternating), ceil(n/32) words each, zero between searches
     long long n_active;   // vertices of the class
     int frac_inv;         // 0 = never dense
 };
@@ -291,295 +350,276 @@ struct InitList {
 struct InitPairs {
     const int32_t* sources;
     __device__ __forceinline__ uint64_t operator()(long long i) const {
-        uint32_t s = (uint32_t)sources[i];
+        const uint32_t s = (uint32_t)sources[i];
         return ((uint64_t)s << 32) | s;
     }
 };
 
-// Per-warp accumulators of a search (folded into the control block at the end).
-struct WarpStats {
-    unsigned long long edges = 0, items = 0;
-};
+// Set an item with more than hub_thr arcs aside for the next round, cut into
+// hub segments. Returns false (and reserves nothing usable) when the hub list or
+// the segment map is full; the caller then expands the item itself.
+template <class Item>
+__device__ __forceinline__ bool reserve_hub(const EngineParams<Item>& P, RoundCtl& cur, int par, Item x, int b0,
+                                            int dg) {
+    const int h = atomicAdd(&cur.nhub, 1);
+    if (h >= P.hub_cap) return false;
+    const long long ns = ceil_div(dg, kHubSeg);
+    const long long sb = (long long)atomicAdd((unsigned long long*)&cur.hubseg, (unsigned long long)ns);
+    const long long lim = sb + ns < P.segmap_cap ? sb + ns : P.segmap_cap;
+    if (sb + ns > P.segmap_cap) {
+        for (long long g = sb; g < lim; ++g) P.segmap[par][g] = -1;
+        P.hub_item[par][h] = x;  // listed but without segments: skipped by the next round
+        P.hub_deg[par][h] = 0;
+        P.hub_beg[par][h] = b0;
+        P.hub_segbase[par][h] = sb;
+        return false;
+    }
+    P.hub_item[par][h] = x;
+    P.hub_beg[par][h] = b0;
+    P.hub_deg[par][h] = dg;
+    P.hub_segbase[par][h] = sb;
+    for (long long g = sb; g < lim; ++g) P.segmap[par][g] = h;
+    return true;
+}
 
 // One complete reachability search (Alg. 3 rounds) executed by every thread of a
-// cooperative grid. Returns false if a grid barrier timed out (the caller must
-// return at once). On return all blocks have passed the final barrier, so the
-// control block's counters of this search are final.
+// cooperative grid. `g` is the global round counter (identical in all blocks;
+// advanced past this search's rounds), `si` the search index (selects the
+// per-search control entry). Returns false if a grid barrier timed out (the
+// caller must return at once). On return every block has passed the final
+// barrier, so this search's control entry is final.
 template <class Pol, class Init>
-__device__ bool engine_search(EngineParams<typename Pol::Item> P, Pol& pol, Init init, long long ninit,
-                              const DenseParams* dp, typename Pol::Item* q, WarpStats& ws) {
+__device__ bool engine_search(const EngineParams<typename Pol::Item>& P, Pol& pol, Init init, long long ninit,
+                              const DenseParams* dp, typename Pol::Item* q, WarpStats& ws, uint32_t& g,
+                              uint32_t si) {
     using Item = typename Pol::Item;
     constexpr uint32_t QM = Pol::kQueue - 1;
-    __shared__ long long s_tile[1];
-    __shared__ int s_wsum[32];
     EngineCtl* ctl = P.ctl;
+    SearchCtl& sc = ctl->search[si % 3];
     const int lane = lane_id();
     const int wib = threadIdx.x >> 5;
     const uint32_t wid = (uint32_t)(blockIdx.x * (blockDim.x >> 5) + wib);
     const uint32_t nwarps = (uint32_t)(gridDim.x * (blockDim.x >> 5));
-
-    // ---- fresh per-search state (the bag slots are already empty)
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        for (int p = 0; p < 2; ++p) {
-            ctl->fsize[p] = 0;
-            ctl->work[p] = 0;
-            ctl->hubseg[p] = 0;
-            ctl->nhub[p] = 0;
-            ctl->bag[p].r = 0;
-            for (int j = 0; j < kMaxChunks; ++j) ctl->bag[p].sample[j] = 0;
-        }
-        ctl->overflow = 0;
-        ctl->inserted = 0;
-        ctl->rounds = 0;
-    }
-    if (!grid_sync(&ctl->bar, &ctl->err)) return false;
-
-    // ---- round -1: the initial items (marked visited) go into bag[1]
-    {
-        SegState st{-1, 0, 0};
-        long long ins = 0;
-        for (long long b = (long long)wid * 32; b < ninit; b += (long long)nwarps * 32) {
-            long long i = b + lane;
-            bool has = false;
-            Item it = Sent<Item>::empty;
-            if (i < ninit) {
-                it = init(i);
-                has = pol.seed(it);
-            }
-            ins += __popc(__ballot_sync(kFull, has));
-            bag_push<Item>(P, &ctl->bag[1], st, has, it, wid, 0xffffu);
-        }
-        if constexpr (Pol::kCountInserts) {
-            if (lane == 0 && ins) atomicAdd(&ctl->inserted, (unsigned long long)ins);
-        }
-    }
-    if (!grid_sync(&ctl->bar, &ctl->err)) return false;
-
+    const long long gtid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long gstride = (long long)gridDim.x * blockDim.x;
+    const uint32_t g0 = g;
     bool prev_dense = false;
-    for (uint32_t iter = 0;; ++iter) {
-        const int p = iter & 1;
-        // ---- ExtractAll: pack bag[(iter+1)&1]'s used prefix into the frontier
-        // (light items) and the hub list; every slot read is reset to empty.
-        {
-            BagCtl* rb = &ctl->bag[(iter + 1) & 1];
-            const int r = ld_volatile(&rb->r);
-            const long long end = chunk_end(P.lambda, r, P.nslots);
-            const long long tile = (long long)blockDim.x * 4;
-            for (long long tb = (long long)blockIdx.x * tile; tb < end; tb += (long long)gridDim.x * tile) {
-                Item x[4];
-                bool light[4];
-                int nl = 0;
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    long long i = tb + threadIdx.x + (long long)k * blockDim.x;
-                    x[k] = Sent<Item>::empty;
-                    light[k] = false;
-                    if (i < end) {
-                        x[k] = P.slots[i];
-                        if (x[k] != Sent<Item>::empty) P.slots[i] = Sent<Item>::empty;
-                    }
-                    if (x[k] != Sent<Item>::empty && x[k] != Sent<Item>::claimed) {
-                        int v = pol.vertex(x[k]);
-                        int b0 = __ldg(&P.off[v]);
-                        int dg = __ldg(&P.off[v + 1]) - b0;
-                        bool ok_hub = false;
-                        if (dg > P.hub_thr) {
-                            int h = atomicAdd(&ctl->nhub[p], 1);
-                            if (h < P.hub_cap) {
-                                long long ns = ceil_div(dg, kHubSeg);
-                                long long sb = atomicAdd((unsigned long long*)&ctl->hubseg[p], (unsigned long long)ns);
-                                long long lim = sb + ns < P.segmap_cap ? sb + ns : P.segmap_cap;
-                                if (sb + ns <= P.segmap_cap) {
-                                    P.hub_item[h] = x[k];
-                                    P.hub_beg[h] = b0;
-                                    P.hub_deg[h] = dg;
-                                    P.hub_segbase[h] = sb;
-                                    for (long long g = sb; g < lim; ++g) P.segmap[g] = h;
-                                    ok_hub = true;
-                                } else {
-                                    for (long long g = sb; g < lim; ++g) P.segmap[g] = -1;
-                                }
-                            }
-                        }
-                        light[k] = !ok_hub;
-                        nl += light[k];
-                    }
-                }
-                // block-aggregated reservation in the frontier
-                int wsum = nl;
-#pragma unroll
-                for (int d = 16; d >= 1; d >>= 1) wsum += __shfl_xor_sync(kFull, wsum, d);
-                int wpre = warp_incl_scan(nl) - nl;
-                if (lane == 0) s_wsum[wib] = wsum;
-                __syncthreads();
-                if (threadIdx.x == 0) {
-                    long long tot = 0;
-                    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-                        int c = s_wsum[w];
-                        s_wsum[w] = (int)tot;
-                        tot += c;
-                    }
-                    s_tile[0] = tot ? (long long)atomicAdd((unsigned long long*)&ctl->fsize[p], (unsigned long long)tot) : 0;
-                }
-                __syncthreads();
-                long long pos = s_tile[0] + s_wsum[wib] + wpre;
-#pragma unroll
-                for (int k = 0; k < 4; ++k)
-                    if (light[k]) {
-                        if (pos < P.front_cap) P.front[pos] = x[k];
-                        else atomicCAS(&ctl->err, 0, SCC_ERR_CAPACITY);
-                        ++pos;
-                    }
-                __syncthreads();
-            }
-            // the frontier bitmap of a previous dense round is cleared here
-            if constexpr (Pol::kDense) {
-                if (prev_dense) {
-                    const long long nw = ((long long)P.n + 31) / 32;
-                    for (long long w = (long long)blockIdx.x * blockDim.x + threadIdx.x; w < nw;
-                         w += (long long)gridDim.x * blockDim.x)
-                        if (dp->fbits[w]) dp->fbits[w] = 0;
-                }
-            }
-        }
-        if (!grid_sync(&ctl->bar, &ctl->err)) return false;
-        if (ld_volatile(&ctl->err) != 0) break;
-        const long long fsize = ld_volatile(&ctl->fsize[p]);
-        const int nhub = min(ld_volatile(&ctl->nhub[p]), P.hub_cap);
-        if (fsize == 0 && nhub == 0) break;
+    uint32_t i = 0;
+    for (;; ++i) {
+        const uint32_t gr = g0 + i;
+        const int par = (int)(gr & 1), ipar = par ^ 1;
+        RoundCtl& cur = ctl->ring[gr % 3];
+        RoundCtl& prev = ctl->ring[(gr + 2) % 3];
         if (blockIdx.x == 0 && threadIdx.x == 0) {
-            ctl->fsize[p ^ 1] = 0;
-            ctl->work[p ^ 1] = 0;
-            ctl->hubseg[p ^ 1] = 0;
-            ctl->nhub[p ^ 1] = 0;
-            BagCtl* nb = &ctl->bag[(iter + 1) & 1];
-            nb->r = 0;
-            for (int j = 0; j < kMaxChunks; ++j) nb->sample[j] = 0;
-            ctl->rounds = (int)iter + 1;
+            RoundCtl& nx = ctl->ring[(gr + 1) % 3];
+            nx.bag.r = 0;
+            for (int j = 0; j < kMaxChunks; ++j) nx.bag.sample[j] = 0;
+            nx.items = 0;
+            nx.hubseg = 0;
+            nx.work = 0;
+            nx.nhub = 0;
+            if (i == 0) {
+                SearchCtl& other = ctl->search[(si + 1) % 3];
+                other.overflow = 0;
+                other.rounds = 0;
+                other.inserted = 0;
+            }
         }
-        BagCtl* bc = &ctl->bag[iter & 1];
-        SegState st{-1, 0, (uint32_t)(wid * 2654435761u)};
-        const bool stop = P.max_inserted > 0 && ld_volatile(&ctl->overflow) != 0;
-
+        const BagRef<Item> out{P.slots[par], P.nslots, P.lambda, P.sigma, &cur.bag, &ctl->err, &ctl->max_chunk};
+        Item* const in_slots = P.slots[ipar];
+        SegState st{-1, 0, (uint32_t)(wid * 2654435761u) ^ gr};
+        unsigned long long pushed = 0;
+        const long long in_end = i == 0 ? 0 : chunk_end(P.lambda, ld_volatile(&prev.bag.r), P.nslots);
+        const long long fr_items = i == 0 ? ninit : ld_volatile(&prev.items);
+        const int fr_hubs = i == 0 ? 0 : min(ld_volatile(&prev.nhub), P.hub_cap);
         bool dense = false;
         if constexpr (Pol::kDense) {
-            dense = dp != nullptr && dp->frac_inv > 0 &&
-                    (long long)(fsize + nhub) * (long long)dp->frac_inv >= dp->n_active;
+            dense = i > 0 && dp != nullptr && dp->frac_inv > 0 &&
+                    (long long)(fr_items + fr_hubs) * (long long)dp->frac_inv >= dp->n_active;
+            if (prev_dense) {  // the bitmap of the previous (dense) round
+                uint32_t* old = dp->fbits[ipar];
+                const long long nw = ((long long)P.n + 31) / 32;
+                for (long long w = gtid; w < nw; w += gstride)
+                    if (old[w]) old[w] = 0;
+            }
         }
-        prev_dense = dense;
         if (dense) {
             if constexpr (Pol::kDense) {
-                // ---- dense round: frontier bitmap, then bottom-up over unvisited vertices
-                for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < fsize + nhub;
-                     i += (long long)gridDim.x * blockDim.x) {
-                    const int v = pol.vertex(i < fsize ? P.front[i] : P.hub_item[i - fsize]);
-                    atomicOr(&dp->fbits[v >> 5], 1u << (v & 31));
+                // ---- dense round: frontier bitmap (the input bag, read and reset,
+                // and last round's hubs), then bottom-up over unvisited vertices
+                uint32_t* fb = dp->fbits[par];
+                for (long long j = gtid; j < in_end; j += gstride) {
+                    const Item x = in_slots[j];
+                    if (x == Sent<Item>::empty) continue;
+                    in_slots[j] = Sent<Item>::empty;
+                    if (x == Sent<Item>::claimed) continue;
+                    const int v = pol.vertex(x);
+                    atomicOr(&fb[v >> 5], 1u << (v & 31));
+                }
+                for (long long j = gtid; j < fr_hubs; j += gstride) {
+                    const int v = pol.vertex(P.hub_item[ipar][j]);
+                    atomicOr(&fb[v >> 5], 1u << (v & 31));
                 }
                 if (!grid_sync(&ctl->bar, &ctl->err)) return false;
                 const long long nw = ((long long)P.n + 31) / 32;
-                for (long long w = wid; w < nw; w += nwarps) {
-                    const uint32_t word = pol.bits[w];
-                    const long long v = w * 32 + lane;
-                    bool found = false;
-                    unsigned long long scanned = 0;
-                    if (v < P.n && !((word >> lane) & 1u)) {
-                        const int e0 = __ldg(&dp->roff[v]), e1 = __ldg(&dp->roff[v + 1]);
-                        for (int e = e0; e < e1; ++e) {
-                            const int u = __ldg(&dp->radj[e]);
-                            ++scanned;
-                            if ((ld_volatile(&dp->fbits[u >> 5]) >> (u & 31)) & 1u) {
-                                found = true;
-                                break;
+                // each warp takes 32 consecutive words at a time (one coalesced
+                // load) and works only on words with unvisited vertices
+                for (long long w0 = (long long)wid * 32; w0 < nw; w0 += (long long)nwarps * 32) {
+                    const uint32_t mine = w0 + lane < nw ? ld_volatile(&pol.bits[w0 + lane]) : ~0u;
+                    uint32_t todo = __ballot_sync(kFull, mine != ~0u);
+                    while (todo) {
+                        const int jw = __ffs(todo) - 1;
+                        todo &= todo - 1;
+                        const long long w = w0 + jw;
+                        const uint32_t word = __shfl_sync(kFull, mine, jw);
+                        const long long v = w * 32 + lane;
+                        bool found = false;
+                        unsigned long long scanned = 0;
+                        if (v < P.n && !((word >> lane) & 1u)) {
+                            const int e0 = __ldg(&dp->roff[v]), e1 = __ldg(&dp->roff[v + 1]);
+                            for (int e = e0; e < e1; ++e) {
+                                const int u = __ldg(&dp->radj[e]);
+                                ++scanned;
+                                if ((ld_volatile(&fb[u >> 5]) >> (u & 31)) & 1u) {
+                                    found = true;
+                                    break;
+                                }
                             }
                         }
+                        const uint32_t m = __ballot_sync(kFull, found);
+                        if (lane == 0 && m) pol.bits[w] = word | m;  // this warp owns word w in this round
+                        for (int dd = 16; dd >= 1; dd >>= 1) scanned += __shfl_xor_sync(kFull, scanned, dd);
+                        if (lane == 0) {
+                            ws.edges += scanned;
+                            ws.items += __popc(m);
+                        }
+                        pushed += bag_push<Item>(out, st, found, (Item)v, wid, gr);
                     }
-                    const uint32_t m = __ballot_sync(kFull, found);
-                    if (lane == 0 && m) pol.bits[w] = word | m;  // this warp owns word w in this round
-                    for (int d = 16; d >= 1; d >>= 1) scanned += __shfl_xor_sync(kFull, scanned, d);
-                    if (lane == 0) {
-                        ws.edges += scanned;
-                        ws.items += __popc(m);
-                    }
-                    bag_push<Item>(P, bc, st, found, (Item)v, wid, iter);
                 }
             }
         } else {
-            // ---- phase A: hub segments, shared by all warps ("in parallel")
-            const long long nseg = min(ld_volatile(&ctl->hubseg[p]), P.segmap_cap);
-            for (long long g = wid; g < nseg && !stop; g += nwarps) {
-                const int h = P.segmap[g];
-                if (h < 0) continue;
-                const Item hit = P.hub_item[h];
-                const long long j0 = (g - P.hub_segbase[h]) * kHubSeg;
-                const int b0 = P.hub_beg[h] + (int)j0;
-                const int len = (int)min((long long)kHubSeg, (long long)P.hub_deg[h] - j0);
-                const uint64_t hctx = pol.ctx(hit);
-                for (int e0 = 0; e0 < len; e0 += 32) {
-                    bool nw = false;
-                    Item child = Sent<Item>::empty;
-                    if (e0 + lane < len) {
-                        int w = __ldg(&P.adj[b0 + e0 + lane]);
-                        nw = pol.visit(hit, hctx, w, child);
+            const bool stop = P.max_inserted > 0 && ld_volatile(&sc.overflow) != 0;
+            // ---- phase A: last round's hubs, cut into segments shared by all warps
+            if (i > 0) {
+                const long long nseg = min(ld_volatile(&prev.hubseg), P.segmap_cap);
+                for (long long gs = wid; gs < nseg && !stop; gs += nwarps) {
+                    const int h = P.segmap[ipar][gs];
+                    if (h < 0) continue;
+                    const Item hit = P.hub_item[ipar][h];
+                    const long long j0 = (gs - P.hub_segbase[ipar][h]) * kHubSeg;
+                    const int b0 = P.hub_beg[ipar][h] + (int)j0;
+                    const int len = (int)min((long long)kHubSeg, (long long)P.hub_deg[ipar][h] - j0);
+                    const uint64_t hctx = pol.ctx(hit);
+                    for (int e0 = 0; e0 < len; e0 += 32) {
+                        bool nw = false;
+                        Item child = Sent<Item>::empty;
+                        if (e0 + lane < len) {
+                            const int w = __ldg(&P.adj[b0 + e0 + lane]);
+                            nw = pol.visit(hit, hctx, w, child);
+                        }
+                        pushed += bag_push<Item>(out, st, nw, child, wid, gr);
                     }
-                    bag_push<Item>(P, bc, st, nw, child, wid, iter);
+                    ws.edges += lane == 0 ? (unsigned long long)max(len, 0) : 0ull;
+                    ws.items += (lane == 0 && gs == P.hub_segbase[ipar][h]) ? 1ull : 0ull;
                 }
-                ws.edges += lane == 0 ? (unsigned long long)len : 0ull;
-                ws.items += (lane == 0 && g == P.hub_segbase[h]) ? 1ull : 0ull;
             }
-
-            // ---- phase B: warp tasks over the light frontier (VGC local searches)
+            // ---- phase B: one warp task per input segment (ForAll over the bag),
+            // or per 32 initial items in round 0
+            const long long ntasks = i == 0 ? (ninit + 31) / 32 : in_end / kSeg;
+            long long ins = 0;
             for (;;) {
-                long long b = 0;
-                if (lane == 0) b = (long long)atomicAdd((unsigned long long*)&ctl->work[p], (unsigned long long)P.seeds);
-                b = __shfl_sync(kFull, b, 0);
-                if (b >= fsize) break;
-                if (P.max_inserted > 0 && ld_volatile(&ctl->overflow) != 0) break;
-                int cnt = (int)min((long long)P.seeds, fsize - b);
-                if (lane < cnt) q[lane] = P.front[b + lane];
+                long long tk = 0;
+                if (lane == 0) tk = (long long)atomicAdd((unsigned long long*)&cur.work, 1ull);
+                tk = __shfl_sync(kFull, tk, 0);
+                if (tk >= ntasks || stop) break;
+                const long long idx = tk * 32 + lane;
+                Item it = Sent<Item>::empty;
+                bool has = false;
+                if (i == 0) {
+                    if (idx < ninit) {
+                        it = init(idx);
+                        has = pol.seed(it);
+                        ins += has;
+                    }
+                } else {
+                    it = in_slots[idx];
+                    if (it != Sent<Item>::empty) {
+                        in_slots[idx] = Sent<Item>::empty;
+                        has = it != Sent<Item>::claimed;
+                    }
+                }
+                if (has) {
+                    const int v = pol.vertex(it);
+                    const int b0 = __ldg(&P.off[v]);
+                    const int dg = __ldg(&P.off[v + 1]) - b0;
+                    if (dg > P.hub_thr && reserve_hub(P, cur, par, it, b0, dg)) has = false;
+                }
+                const uint32_t m = __ballot_sync(kFull, has);
+                if (m == 0) continue;
+                if (has) q[__popc(m & lanemask_lt())] = it;
                 __syncwarp();
-                uint32_t qh = 0, qt = (uint32_t)cnt;
+                uint32_t qh = 0, qt = (uint32_t)__popc(m);
                 int t = 0;
-                expand_batch<Pol>(P, pol, bc, st, wid, iter, q, qh, qt, t, true, ws.edges, ws.items);
+                expand_batch<Pol>(P, pol, out, st, wid, gr, q, qh, qt, t, true, P.seeds, ws, pushed);
                 while (qt != qh && t < P.tau)
-                    expand_batch<Pol>(P, pol, bc, st, wid, iter, q, qh, qt, t, false, ws.edges, ws.items);
+                    expand_batch<Pol>(P, pol, out, st, wid, gr, q, qh, qt, t, false, 32, ws, pushed);
                 // budget spent: flush what is left in the local queue
                 while (qt != qh) {
-                    int nrem = (int)min(32u, qt - qh);
-                    Item it = lane < nrem ? q[(qh + lane) & QM] : Sent<Item>::empty;
+                    const int nrem = (int)min(32u, qt - qh);
+                    const Item x = lane < nrem ? q[(qh + lane) & QM] : Sent<Item>::empty;
                     qh += nrem;
-                    bag_push<Item>(P, bc, st, lane < nrem, it, wid, iter);
+                    pushed += bag_push<Item>(out, st, lane < nrem, x, wid, gr);
                 }
                 __syncwarp();
                 if constexpr (Pol::kCountInserts) {
-                    long long c = pol.take_inserted();
+                    const long long c = pol.take_inserted();
                     if (c && lane == 0) {
-                        unsigned long long tot = atomicAdd(&ctl->inserted, (unsigned long long)c) + c;
-                        if (P.max_inserted > 0 && (long long)tot > P.max_inserted) atomicExch(&ctl->overflow, 1);
+                        const unsigned long long tot = atomicAdd(&sc.inserted, (unsigned long long)c) + c;
+                        if (P.max_inserted > 0 && (long long)tot > P.max_inserted) atomicExch(&sc.overflow, 1);
                     }
                 }
             }
             if constexpr (Pol::kCountInserts) {
-                long long c = pol.take_inserted();
+                for (int dd = 16; dd >= 1; dd >>= 1) ins += __shfl_xor_sync(kFull, ins, dd);
+                const long long c = pol.take_inserted() + ins;
                 if (c && lane == 0) {
-                    unsigned long long tot = atomicAdd(&ctl->inserted, (unsigned long long)c) + c;
-                    if (P.max_inserted > 0 && (long long)tot > P.max_inserted) atomicExch(&ctl->overflow, 1);
+                    const unsigned long long tot = atomicAdd(&sc.inserted, (unsigned long long)c) + c;
+                    if (P.max_inserted > 0 && (long long)tot > P.max_inserted) atomicExch(&sc.overflow, 1);
                 }
             }
         }
+        if (lane == 0 && pushed) atomicAdd((unsigned long long*)&cur.items, pushed);
         if (!grid_sync(&ctl->bar, &ctl->err)) return false;
-        if (P.max_inserted > 0 && ld_volatile(&ctl->overflow) != 0) break;
+        prev_dense = dense;
+        if (ld_volatile(&ctl->err) != 0) break;
+        if (P.max_inserted > 0 && ld_volatile(&sc.overflow) != 0) break;
+        if (ld_volatile(&cur.items) == 0 && ld_volatile(&cur.nhub) == 0) break;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) sc.rounds = (int)i + 1;
+    g = g0 + i + 1;
+    if constexpr (Pol::kDense) {
+        // a search that ended on a dense round leaves its bitmap for the next
+        // search's first round... which never clears it: clear it here
+        if (prev_dense && dp != nullptr) {
+            uint32_t* last = dp->fbits[(g0 + i) & 1];
+            const long long nw = ((long long)P.n + 31) / 32;
+            for (long long w = gtid; w < nw; w += gstride)
+                if (last[w]) last[w] = 0;
+            if (!grid_sync(&ctl->bar, &ctl->err)) return false;
+        }
     }
     return true;
 }
 
 template <class Pol>
-__global__ void __launch_bounds__(256) engine_kernel(EngineParams<typename Pol::Item> P, Pol pol_in, DenseParams dp) {
+__global__ void __launch_bounds__(256, 3) engine_kernel(EngineParams<typename Pol::Item> P, Pol pol_in, DenseParams dp) {
     Pol pol = pol_in;
     __shared__ EngineSmem<Pol> sm;
     typename Pol::Item* q = sm.q + (threadIdx.x >> 5) * Pol::kQueue;
     WarpStats ws;
+    uint32_t g = 0;
     const bool ok = engine_search<Pol>(P, pol, InitList<typename Pol::Item>{P.init}, P.ninit,
-                                       dp.frac_inv > 0 ? &dp : nullptr, q, ws);
+                                       dp.frac_inv > 0 ? &dp : nullptr, q, ws, g, 0);
     if (!ok) return;
     if (lane_id() == 0 && ws.edges) atomicAdd(&P.ctl->edges, ws.edges);
     if (lane_id() == 0 && ws.items) atomicAdd(&P.ctl->items, ws.items);

@@ -141,25 +141,27 @@ int launch_table_insert(const unsigned long long* keys, int64_t count, unsigned 
                         int* overflow, unsigned long long* inserted, cudaStream_t s);
 
 // ---------------------------------------------------------------- engine --
-// Buffers of one engine instance (item type = 4 or 8 bytes).
+// Buffers of one engine instance (item type = 4 or 8 bytes): two hash-bag slot
+// arrays and two hub lists, alternating between rounds.
 struct EngineBuf {
     int item_bytes = 0;
-    void* slots = nullptr;
+    void* slots[2] = {nullptr, nullptr};
     long long nslots = 0;
-    void* front = nullptr;
-    long long front_cap = 0;
-    void* hub_item = nullptr;
-    int32_t* hub_beg = nullptr;
-    int32_t* hub_deg = nullptr;
-    long long* hub_segbase = nullptr;
+    long long items = 0;  // items per round the buffers were sized for
+    void* hub_item[2] = {nullptr, nullptr};
+    int32_t* hub_beg[2] = {nullptr, nullptr};
+    int32_t* hub_deg[2] = {nullptr, nullptr};
+    long long* hub_segbase[2] = {nullptr, nullptr};
     int hub_cap = 0;
-    int32_t* segmap = nullptr;
+    int32_t* segmap[2] = {nullptr, nullptr};
     long long segmap_cap = 0;
     EngineCtl* ctl = nullptr;
     int lambda = 0;
-    void* init = nullptr;      // staging of the initial items
+    void* init = nullptr;  // staging of the initial items
     size_t init_bytes = 0;
 };
+// Empty both slot arrays (after a search that stopped early).
+int engine_reset_slots(EngineBuf* b, cudaStream_t s);
 // Allocate (or keep, if large enough) buffers for at most `items` items per round.
 int engine_reserve(EngineBuf* b, int item_bytes, long long items, int lambda, int64_t m, cudaStream_t s);
 void engine_release(EngineBuf* b, cudaStream_t s);
@@ -189,7 +191,7 @@ struct EngineOpts {
 struct DenseOpts {
     const int32_t* roff = nullptr;
     const int32_t* radj = nullptr;
-    uint32_t* fbits = nullptr;
+    uint32_t* fbits[2] = {nullptr, nullptr};
     long long n_active = 0;
     int frac_inv = 0;
 };

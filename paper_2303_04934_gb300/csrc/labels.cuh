@@ -52,19 +52,25 @@ __device__ __forceinline__ void finalize_vertex(uint32_t v, unsigned long long t
     }
 }
 
-// Returns how many vertices this thread finished.
+// Returns how many vertices this thread finished. With `clear`, every entry is
+// reset to empty once used (each entry is read by exactly one thread here), so
+// the tables are empty again for the next batch.
 __device__ __forceinline__ unsigned long long label_finalize(long long i0, long long stride,
-                                                             const unsigned long long* __restrict__ tf, long long capf,
-                                                             const unsigned long long* __restrict__ tb, long long capb,
+                                                             unsigned long long* __restrict__ tf, long long capf,
+                                                             unsigned long long* __restrict__ tb, long long capb,
                                                              unsigned long long tag, const unsigned long long* fmax,
                                                              const unsigned long long* bmax,
                                                              const unsigned long long* hit, int32_t* label,
-                                                             int32_t* rep) {
+                                                             int32_t* rep, bool clear) {
     unsigned long long c = 0;
     for (long long i = i0; i < capf + capb; i += stride) {
         const bool fw = i < capf;
         const unsigned long long key = fw ? tf[i] : tb[i - capf];
         if (key == ~0ull) continue;
+        if (clear) {
+            if (fw) tf[i] = ~0ull;
+            else tb[i - capf] = ~0ull;
+        }
         const uint32_t v = (uint32_t)(key >> 32), s = (uint32_t)key;
         const unsigned long long f = fmax[v];
         const bool owner = fw ? f == (tag | s)

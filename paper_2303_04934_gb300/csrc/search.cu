@@ -36,7 +36,7 @@ int coop_grid(int num_sms, int* grid) {
 
 template <class Pol>
 int launch_engine(EngineParams<typename Pol::Item>& P, Pol& pol, const EngineOpts& o, EngineRun* out,
-                  cudaStream_t st, DenseParams dp = DenseParams{nullptr, nullptr, nullptr, 0, 0}) {
+                  cudaStream_t st, DenseParams dp = DenseParams{nullptr, nullptr, {nullptr, nullptr}, 0, 0}) {
     int grid = 0;
     SCC_TRY(coop_grid<Pol>(o.num_sms, &grid));
     SCC_CUDA(cudaMemsetAsync(P.ctl, 0, sizeof(EngineCtl), st));
@@ -62,18 +62,20 @@ int launch_engine(EngineParams<typename Pol::Item>& P, Pol& pol, const EngineOpt
     out->ms = ms;
     out->items = h.items;
     out->err = h.err;
-    out->overflow = h.overflow;
-    out->rounds = h.rounds;
+    out->overflow = h.search[0].overflow;
+    out->rounds = h.search[0].rounds;
     out->max_chunk = h.max_chunk;
     out->edges = h.edges;
-    out->inserted = h.inserted;
+    out->inserted = h.search[0].inserted;
     if (h.err != 0 && h.err != SCC_ERR_CAPACITY) return h.err;
     return SCC_OK;
 }
 
+}  // namespace
+
 template <class Item>
-EngineParams<Item> make_params(const int32_t* off, const int32_t* adj, int32_t n, EngineBuf* b,
-                               const EngineOpts& o) {
+EngineParams<Item> make_engine_params(const int32_t* off, const int32_t* adj, int32_t n, const EngineBuf* b,
+                                      const EngineOpts& o) {
     EngineParams<Item> P;
     memset(&P, 0, sizeof(P));
     P.off = off;
@@ -82,22 +84,28 @@ EngineParams<Item> make_params(const int32_t* off, const int32_t* adj, int32_t n
     P.tau = o.tau;
     P.hub_thr = o.tau;
     P.seeds = o.seeds;
-    P.slots = (Item*)b->slots;
+    for (int k = 0; k < 2; ++k) {
+        P.slots[k] = (Item*)b->slots[k];
+        P.hub_item[k] = (Item*)b->hub_item[k];
+        P.hub_beg[k] = b->hub_beg[k];
+        P.hub_deg[k] = b->hub_deg[k];
+        P.hub_segbase[k] = b->hub_segbase[k];
+        P.segmap[k] = b->segmap[k];
+    }
     P.nslots = b->nslots;
     P.lambda = b->lambda;
     P.sigma = o.sigma;
-    P.front = (Item*)b->front;
-    P.front_cap = b->front_cap;
-    P.hub_item = (Item*)b->hub_item;
-    P.hub_beg = b->hub_beg;
-    P.hub_deg = b->hub_deg;
-    P.hub_segbase = b->hub_segbase;
     P.hub_cap = b->hub_cap;
-    P.segmap = b->segmap;
     P.segmap_cap = b->segmap_cap;
     P.ctl = b->ctl;
     return P;
 }
+template EngineParams<uint32_t> make_engine_params<uint32_t>(const int32_t*, const int32_t*, int32_t,
+                                                             const EngineBuf*, const EngineOpts&);
+template EngineParams<uint64_t> make_engine_params<uint64_t>(const int32_t*, const int32_t*, int32_t,
+                                                             const EngineBuf*, const EngineOpts&);
+
+namespace {
 
 int reserve_init(EngineBuf* b, size_t bytes, cudaStream_t st) {
     if (b->init && b->init_bytes >= bytes) return SCC_OK;
@@ -109,47 +117,52 @@ int reserve_init(EngineBuf* b, size_t bytes, cudaStream_t st) {
     return SCC_OK;
 }
 
+}  // namespace
+
 // Restore an all-empty bag after a run that stopped early (error or overflow).
-int reset_slots(EngineBuf* b, cudaStream_t st) {
-    SCC_CUDA(cudaMemsetAsync(b->slots, 0xff, (size_t)b->nslots * b->item_bytes, st));
+int engine_reset_slots(EngineBuf* b, cudaStream_t st) {
+    for (int k = 0; k < 2; ++k)
+        if (b->slots[k]) SCC_CUDA(cudaMemsetAsync(b->slots[k], 0xff, (size_t)b->nslots * b->item_bytes, st));
     return SCC_OK;
 }
-
-}  // namespace
 
 int engine_reserve(EngineBuf* b, int item_bytes, long long items, int lambda, int64_t m, cudaStream_t s) {
     if (items < 1) items = 1;
     long long need_slots = std::max<long long>(4 * items, 4ll * lambda);
-    if (b->slots && b->item_bytes == item_bytes && b->nslots >= need_slots && b->lambda == lambda &&
-        b->front_cap >= items)
+    need_slots = (need_slots + kSeg - 1) / kSeg * kSeg;
+    if (b->slots[0] && b->item_bytes == item_bytes && b->nslots >= need_slots && b->lambda == lambda &&
+        b->items >= items)
         return SCC_OK;
     engine_release(b, s);
     b->item_bytes = item_bytes;
     b->lambda = lambda;
     b->nslots = need_slots;
-    b->front_cap = items;
+    b->items = items;
     b->hub_cap = (int)std::min<long long>(items, 1ll << 22);
     b->segmap_cap = 2 * (m / kHubSeg) + b->hub_cap + 1024;
-    SCC_TRY(dalloc(&b->slots, (size_t)b->nslots * item_bytes, s));
-    SCC_TRY(dalloc(&b->front, (size_t)b->front_cap * item_bytes, s));
-    SCC_TRY(dalloc(&b->hub_item, (size_t)b->hub_cap * item_bytes, s));
-    SCC_TRY(dalloc_t(&b->hub_beg, b->hub_cap, s));
-    SCC_TRY(dalloc_t(&b->hub_deg, b->hub_cap, s));
-    SCC_TRY(dalloc_t(&b->hub_segbase, b->hub_cap, s));
-    SCC_TRY(dalloc_t(&b->segmap, b->segmap_cap, s));
+    for (int k = 0; k < 2; ++k) {
+        SCC_TRY(dalloc(&b->slots[k], (size_t)b->nslots * item_bytes, s));
+        SCC_TRY(dalloc(&b->hub_item[k], (size_t)b->hub_cap * item_bytes, s));
+        SCC_TRY(dalloc_t(&b->hub_beg[k], b->hub_cap, s));
+        SCC_TRY(dalloc_t(&b->hub_deg[k], b->hub_cap, s));
+        SCC_TRY(dalloc_t(&b->hub_segbase[k], b->hub_cap, s));
+        SCC_TRY(dalloc_t(&b->segmap[k], b->segmap_cap, s));
+        SCC_CUDA(cudaMemsetAsync(b->slots[k], 0xff, (size_t)b->nslots * item_bytes, s));
+    }
     SCC_TRY(dalloc(reinterpret_cast<void**>(&b->ctl), sizeof(EngineCtl), s));
-    SCC_CUDA(cudaMemsetAsync(b->slots, 0xff, (size_t)b->nslots * item_bytes, s));
+    SCC_CUDA(cudaMemsetAsync(b->ctl, 0, sizeof(EngineCtl), s));
     return SCC_OK;
 }
 
 void engine_release(EngineBuf* b, cudaStream_t s) {
-    dfree(b->slots, s);
-    dfree(b->front, s);
-    dfree(b->hub_item, s);
-    dfree(b->hub_beg, s);
-    dfree(b->hub_deg, s);
-    dfree(b->hub_segbase, s);
-    dfree(b->segmap, s);
+    for (int k = 0; k < 2; ++k) {
+        dfree(b->slots[k], s);
+        dfree(b->hub_item[k], s);
+        dfree(b->hub_beg[k], s);
+        dfree(b->hub_deg[k], s);
+        dfree(b->hub_segbase[k], s);
+        dfree(b->segmap[k], s);
+    }
     dfree(b->ctl, s);
     dfree(b->init, s);
     *b = EngineBuf();
@@ -157,15 +170,15 @@ void engine_release(EngineBuf* b, cudaStream_t s) {
 
 int run_single(const int32_t* off, const int32_t* adj, int32_t n, int32_t s, uint32_t* bits, const DenseOpts& dn,
                EngineBuf* b, const EngineOpts& o, EngineRun* out, cudaStream_t st) {
-    auto P = make_params<uint32_t>(off, adj, n, b, o);
+    auto P = make_engine_params<uint32_t>(off, adj, n, b, o);
     SCC_TRY(reserve_init(b, sizeof(uint32_t), st));
     SCC_CUDA(cudaMemcpyAsync(b->init, &s, sizeof(int32_t), cudaMemcpyHostToDevice, st));
     P.init = reinterpret_cast<const uint32_t*>(b->init);
     P.ninit = 1;
     PolSingle pol{bits};
-    DenseParams dp{dn.roff, dn.radj, dn.fbits, dn.n_active, dn.frac_inv};
+    DenseParams dp{dn.roff, dn.radj, {dn.fbits[0], dn.fbits[1]}, dn.n_active, dn.frac_inv};
     int rc = launch_engine(P, pol, o, out, st, dp);
-    if (rc != SCC_OK || out->err) SCC_TRY(reset_slots(b, st));
+    if (rc != SCC_OK || out->err) SCC_TRY(engine_reset_slots(b, st));
     SCC_TRY(rc);
     return out->err ? out->err : SCC_OK;
 }
@@ -173,7 +186,7 @@ int run_single(const int32_t* off, const int32_t* adj, int32_t n, int32_t s, uin
 int run_pairs(const int32_t* off, const int32_t* adj, int32_t n, const int32_t* label, const int32_t* sources,
               int32_t k, unsigned long long* table, int64_t cap, long long max_inserted, EngineBuf* b,
               const EngineOpts& o, EngineRun* out, cudaStream_t st) {
-    auto P = make_params<uint64_t>(off, adj, n, b, o);
+    auto P = make_engine_params<uint64_t>(off, adj, n, b, o);
     SCC_TRY(reserve_init(b, (size_t)k * sizeof(uint64_t), st));
     uint64_t* init = reinterpret_cast<uint64_t*>(b->init);
     k_pairs_from_sources<<<std::max(1, std::min(1024, (k + 255) / 256)), 256, 0, st>>>(sources, k, init);
@@ -185,11 +198,11 @@ int run_pairs(const int32_t* off, const int32_t* adj, int32_t n, const int32_t* 
     pol.label = label;
     pol.tab.keys = table;
     pol.tab.mask = (unsigned long long)(cap - 1);
-    pol.tab.overflow = &b->ctl->overflow;
+    pol.tab.overflow = &b->ctl->search[0].overflow;  // a standalone launch is search 0
     pol.ins = 0;
     int rc = launch_engine(P, pol, o, out, st);
     if (rc != SCC_OK || out->err || out->overflow) {
-        int r2 = reset_slots(b, st);
+        int r2 = engine_reset_slots(b, st);
         if (rc == SCC_OK) rc = r2;
     }
     SCC_TRY(rc);
@@ -198,12 +211,12 @@ int run_pairs(const int32_t* off, const int32_t* adj, int32_t n, const int32_t* 
 
 int run_mask(const int32_t* off, const int32_t* adj, int32_t n, const int32_t* sources, int32_t k,
              unsigned long long* mask, EngineBuf* b, const EngineOpts& o, EngineRun* out, cudaStream_t st) {
-    auto P = make_params<uint32_t>(off, adj, n, b, o);
+    auto P = make_engine_params<uint32_t>(off, adj, n, b, o);
     P.init = reinterpret_cast<const uint32_t*>(sources);
     P.ninit = k;
     PolMask pol{mask};
     int rc = launch_engine(P, pol, o, out, st);
-    if (rc != SCC_OK || out->err) SCC_TRY(reset_slots(b, st));
+    if (rc != SCC_OK || out->err) SCC_TRY(engine_reset_slots(b, st));
     SCC_TRY(rc);
     return out->err ? out->err : SCC_OK;
 }
@@ -225,18 +238,20 @@ __global__ void __launch_bounds__(256) k_bag_only(BagOnlyParams P, const int32_t
     const uint32_t wid = (uint32_t)(blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5));
     const uint32_t nwarps = (uint32_t)(gridDim.x * (blockDim.x >> 5));
     SegState st{-1, 0, wid * 2654435761u};
+    const BagRef<uint32_t> bag{P.slots, P.nslots, P.lambda, P.sigma, &P.ctl->ring[0].bag, &P.ctl->err,
+                               &P.ctl->max_chunk};
     // every warp pushes a strided share, a few items at a time, as spills do
     for (long long b = (long long)wid * 32; b < count; b += (long long)nwarps * 32) {
         long long i = b + lane;
         bool has = i < count;
         uint32_t it = has ? (uint32_t)items[i] : 0u;
         // split each group of 32 into two pushes to exercise partial segments
-        bag_push<uint32_t>(P, &P.ctl->bag[0], st, has && lane < 13, it, wid, 0);
-        bag_push<uint32_t>(P, &P.ctl->bag[0], st, has && lane >= 13, it, wid, 0);
+        bag_push<uint32_t>(bag, st, has && lane < 13, it, wid, 0);
+        bag_push<uint32_t>(bag, st, has && lane >= 13, it, wid, 0);
     }
     if (!grid_sync(&P.ctl->bar, &P.ctl->err)) return;
     // ExtractAll: warp-aggregated compaction of the used prefix
-    const int r = ld_volatile(&P.ctl->bag[0].r);
+    const int r = ld_volatile(&P.ctl->ring[0].bag.r);
     const long long end = chunk_end(P.lambda, r, P.nslots);
     for (long long b = (long long)wid * 32; b < end; b += (long long)nwarps * 32) {
         long long i = b + lane;
@@ -246,11 +261,11 @@ __global__ void __launch_bounds__(256) k_bag_only(BagOnlyParams P, const int32_t
         uint32_t msk = __ballot_sync(kFull, valid);
         long long base = 0;
         if (lane == 0 && msk)
-            base = (long long)atomicAdd((unsigned long long*)&P.ctl->fsize[0], (unsigned long long)__popc(msk));
+            base = (long long)atomicAdd((unsigned long long*)&P.ctl->ring[1].items, (unsigned long long)__popc(msk));
         base = __shfl_sync(kFull, base, 0);
         if (valid) out[base + __popc(msk & lanemask_lt())] = (int32_t)x;
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) P.ctl->rounds = r;
+    if (blockIdx.x == 0 && threadIdx.x == 0) P.ctl->ring[1].nhub = r;
 }
 
 }  // namespace
@@ -281,8 +296,8 @@ int run_bag_only(const int32_t* items, int64_t count, int lambda, int sigma, int
     dfree(P.ctl, st);
     SCC_TRY(rc);
     if (h.err) return h.err;
-    *nout = h.fsize[0];
-    if (chunks) *chunks = h.rounds + 1;
+    *nout = h.ring[1].items;
+    if (chunks) *chunks = h.ring[1].nhub + 1;
     return SCC_OK;
 }
 

@@ -300,13 +300,13 @@ __global__ void k_label_scan(const unsigned long long* __restrict__ tf, int64_t 
     const long long i0 = (long long)blockIdx.x * blockDim.x + threadIdx.x, st = (long long)gridDim.x * blockDim.x;
     label_scan(i0, st, tf, capf, tb, tag, fmax, bmax, hit);
 }
-__global__ void k_label_finalize(const unsigned long long* __restrict__ tf, int64_t capf,
-                                 const unsigned long long* __restrict__ tb, int64_t capb, unsigned long long tag,
+__global__ void k_label_finalize(unsigned long long* __restrict__ tf, int64_t capf,
+                                 unsigned long long* __restrict__ tb, int64_t capb, unsigned long long tag,
                                  const unsigned long long* fmax, const unsigned long long* bmax,
                                  const unsigned long long* hit, int32_t* label, int32_t* rep,
                                  unsigned long long* ndone) {
     const long long i0 = (long long)blockIdx.x * blockDim.x + threadIdx.x, st = (long long)gridDim.x * blockDim.x;
-    unsigned long long c = label_finalize(i0, st, tf, capf, tb, capb, tag, fmax, bmax, hit, label, rep);
+    unsigned long long c = label_finalize(i0, st, tf, capf, tb, capb, tag, fmax, bmax, hit, label, rep, false);
     for (int d = 16; d >= 1; d >>= 1) c += __shfl_xor_sync(kFull, c, d);
     if (lane_id() == 0 && c) atomicAdd(ndone, c);
 }
@@ -541,7 +541,9 @@ int launch_label_pairs(const unsigned long long* tf, int64_t capf, const unsigne
     PairTable tbt{const_cast<unsigned long long*>(tb), (unsigned long long)(capb - 1), nullptr};
     k_label_scan<<<grid_for(capf + capb, kBlk), kBlk, 0, s>>>(tf, capf, tbt, tag, fmax, bmax, hit);
     SCC_LAUNCH();
-    k_label_finalize<<<grid_for(capf + capb, kBlk), kBlk, 0, s>>>(tf, capf, tb, capb, tag, fmax, bmax, hit, label,
+    k_label_finalize<<<grid_for(capf + capb, kBlk), kBlk, 0, s>>>(const_cast<unsigned long long*>(tf), capf,
+                                                                    const_cast<unsigned long long*>(tb), capb, tag,
+                                                                    fmax, bmax, hit, label,
                                                                     rep, ndone);
     SCC_LAUNCH();
     return SCC_OK;
