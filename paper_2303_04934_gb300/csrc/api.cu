@@ -298,7 +298,10 @@ static int graph_create_impl(scc_graph* h, int32_t n, int64_t m, const int32_t* 
     SCC_TRY(dalloc(&stmp, scan_tmp_bytes(n), s));
     SCC_CUDA(cudaMemsetAsync(selfrow, 0, sizeof(int32_t) * ((size_t)n + 1), s));
     SCC_CUDA(cudaMemsetAsync(bcnt, 0, sizeof(unsigned long long) * ((size_t)nb + 2), s));
-    SCC_TRY(launch_bucket_hist(off_in, adj_in, n, m, shift, bcnt, selfrow, bcnt + nb + 1, h->di.num_sms, s));
+    int32_t* trow = nullptr;
+    SCC_TRY(dalloc_t(&trow, tile_rows_count(m), s));
+    SCC_TRY(launch_tile_rows(off_in, n, m, trow, s));
+    SCC_TRY(launch_bucket_hist(off_in, adj_in, trow, n, m, shift, bcnt, selfrow, bcnt + nb + 1, h->di.num_sms, s));
     unsigned long long hself = 0;
     SCC_CUDA(cudaMemcpyAsync(&hself, bcnt + nb + 1, sizeof(hself), cudaMemcpyDeviceToHost, s));
     SCC_CUDA(cudaStreamSynchronize(s));
@@ -319,6 +322,7 @@ static int graph_create_impl(scc_graph* h, int32_t n, int64_t m, const int32_t* 
         h->off = off2;
         h->adj = adj2;
         m_cur = h->mt;
+        SCC_TRY(launch_tile_rows(h->off, n, m_cur, trow, s));  // rows of the new CSR's tiles
     }
     // G^T: two-level bucketed counting sort by target (direct atomics when n is huge)
     int32_t* toff = nullptr;
@@ -333,8 +337,8 @@ static int graph_create_impl(scc_graph* h, int32_t n, int64_t m, const int32_t* 
         SCC_TRY(dalloc_t(&ord, (size_t)nb, s));
         SCC_TRY(dalloc_t(&terr, 1, s));
         SCC_CUDA(cudaMemsetAsync(terr, 0, sizeof(int), s));
-        SCC_TRY(launch_transpose(h->off, h->adj, n, m_cur, h->mt, shift, bcnt, btmp, tmp_u, tmp_v, ord, toff, h->tadj,
-                                 terr, h->di.num_sms, s));
+        SCC_TRY(launch_transpose(h->off, h->adj, trow, n, m_cur, h->mt, shift, bcnt, btmp, tmp_u, tmp_v, ord, toff,
+                                 h->tadj, terr, h->di.num_sms, s));
         int herr = 0;
         SCC_CUDA(cudaMemcpyAsync(&herr, terr, sizeof(int), cudaMemcpyDeviceToHost, s));
         SCC_CUDA(cudaStreamSynchronize(s));
@@ -346,9 +350,10 @@ static int graph_create_impl(scc_graph* h, int32_t n, int64_t m, const int32_t* 
     } else {
         int32_t* indeg = nullptr;
         SCC_TRY(dalloc_t(&indeg, (size_t)n + 1, s));
-        SCC_TRY(launch_transpose_direct(h->off, h->adj, n, m_cur, indeg, stmp, toff, h->tadj, h->di.num_sms, s));
+        SCC_TRY(launch_transpose_direct(h->off, h->adj, trow, n, m_cur, indeg, stmp, toff, h->tadj, h->di.num_sms, s));
         dfree(indeg, s);
     }
+    dfree(trow, s);
     dfree(selfrow, s);
     dfree(bcnt, s);
     dfree(btmp, s);

@@ -83,6 +83,8 @@ struct SearchCtl {
     unsigned long long inserted;  // newly visited items (pairs in pair mode)
 };
 
+constexpr int kTraceRounds = 64;
+
 struct EngineCtl {
     GridBarrier bar;
     int err;        // first error (SCC_ERR_*)
@@ -91,6 +93,12 @@ struct EngineCtl {
     SearchCtl search[3];
     unsigned long long edges;  // arcs examined
     unsigned long long items;  // items expanded (adjacency rows read)
+    // trace of the first rounds of a standalone search: end time (globaltimer ns),
+    // items of the round's bag, dense flag
+    unsigned long long t0;
+    unsigned long long t_end[kTraceRounds];
+    long long t_items[kTraceRounds];
+    int t_dense[kTraceRounds];
 };
 
 template <class Item>
@@ -240,7 +248,7 @@ template <class Pol>
 __device__ __forceinline__ void expand_batch(const EngineParams<typename Pol::Item>& P, Pol& pol,
                                              const BagRef<typename Pol::Item>& out, SegState& st, uint32_t wid,
                                              uint32_t round, typename Pol::Item* q, uint32_t& qh, uint32_t& qt,
-                                             int& t, bool seeds_phase, int max_take, WarpStats& ws,
+                                             int& t, bool seeds_phase, int max_take, int hub_thr, WarpStats& ws,
                                              unsigned long long& pushed) {
     using Item = typename Pol::Item;
     constexpr uint32_t QM = Pol::kQueue - 1;
@@ -256,7 +264,7 @@ __device__ __forceinline__ void expand_batch(const EngineParams<typename Pol::It
         deg = __ldg(&P.off[u + 1]) - beg;
     }
     // items past the seeds with more than hub_thr arcs go back to the bag
-    bool hub = !seeds_phase && lane < avail && deg > P.hub_thr;
+    bool hub = !seeds_phase && lane < avail && deg > hub_thr;
     int d = (lane < avail && !hub) ? deg : 0;
     int pre = warp_incl_scan(d);
     int take = avail;
@@ -403,6 +411,7 @@ __device__ bool engine_search(const EngineParams<typename Pol::Item>& P, Pol& po
     const long long gtid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long gstride = (long long)gridDim.x * blockDim.x;
     const uint32_t g0 = g;
+    if (si == 0 && blockIdx.x == 0 && threadIdx.x == 0) ctl->t0 = globaltimer_ns();
     bool prev_dense = false;
     uint32_t i = 0;
     for (;; ++i) {
@@ -477,13 +486,20 @@ __device__ bool engine_search(const EngineParams<typename Pol::Item>& P, Pol& po
                         unsigned long long scanned = 0;
                         if (v < P.n && !((word >> lane) & 1u)) {
                             const int e0 = __ldg(&dp->roff[v]), e1 = __ldg(&dp->roff[v + 1]);
-                            for (int e = e0; e < e1; ++e) {
-                                const int u = __ldg(&dp->radj[e]);
-                                ++scanned;
-                                if ((ld_volatile(&fb[u >> 5]) >> (u & 31)) & 1u) {
-                                    found = true;
-                                    break;
-                                }
+                            // in-arcs four at a time: independent loads, early exit per batch
+                            for (int e = e0; e < e1 && !found; e += 4) {
+                                int u[4];
+                                uint32_t fw[4];
+#pragma unroll
+                                for (int k = 0; k < 4; ++k) u[k] = e + k < e1 ? __ldg(&dp->radj[e + k]) : -1;
+#pragma unroll
+                                for (int k = 0; k < 4; ++k) fw[k] = u[k] >= 0 ? ld_volatile(&fb[u[k] >> 5]) : 0u;
+#pragma unroll
+                                for (int k = 0; k < 4; ++k)
+                                    if (!found && u[k] >= 0) {
+                                        ++scanned;
+                                        found = (fw[k] >> (u[k] & 31)) & 1u;
+                                    }
                             }
                         }
                         const uint32_t m = __ballot_sync(kFull, found);
@@ -523,20 +539,29 @@ __device__ bool engine_search(const EngineParams<typename Pol::Item>& P, Pol& po
                     ws.items += (lane == 0 && gs == P.hub_segbase[ipar][h]) ? 1ull : 0ull;
                 }
             }
-            // ---- phase B: one warp task per input segment (ForAll over the bag),
-            // or per 32 initial items in round 0
-            const long long ntasks = i == 0 ? (ninit + 31) / 32 : in_end / kSeg;
+            // ---- phase B: warp tasks over the input (ForAll over the bag, or the
+            // initial items in round 0). A task covers G <= 32 slots, G halved until
+            // every warp gets about two tasks; with a small frontier, items with
+            // more than 64 arcs are also cut into hub segments for the next round,
+            // so that a few heavy items do not serialise the round on a few warps.
+            const long long in_cnt = i == 0 ? ninit : in_end;
+            int G = 32;
+            while (G > 1 && (long long)G * nwarps * 2 > in_cnt) G >>= 1;
+            const int hub_thr = fr_items < (long long)nwarps * 8 ? min(P.hub_thr, 64) : P.hub_thr;
+            const long long ntasks = (in_cnt + G - 1) / G;
             long long ins = 0;
             for (;;) {
                 long long tk = 0;
                 if (lane == 0) tk = (long long)atomicAdd((unsigned long long*)&cur.work, 1ull);
                 tk = __shfl_sync(kFull, tk, 0);
                 if (tk >= ntasks || stop) break;
-                const long long idx = tk * 32 + lane;
+                const long long idx = tk * G + lane;
                 Item it = Sent<Item>::empty;
                 bool has = false;
-                if (i == 0) {
-                    if (idx < ninit) {
+                if (lane >= G || idx >= in_cnt) {
+                    // not part of this task
+                } else if (i == 0) {
+                    {
                         it = init(idx);
                         has = pol.seed(it);
                         ins += has;
@@ -552,7 +577,7 @@ __device__ bool engine_search(const EngineParams<typename Pol::Item>& P, Pol& po
                     const int v = pol.vertex(it);
                     const int b0 = __ldg(&P.off[v]);
                     const int dg = __ldg(&P.off[v + 1]) - b0;
-                    if (dg > P.hub_thr && reserve_hub(P, cur, par, it, b0, dg)) has = false;
+                    if (dg > hub_thr && reserve_hub(P, cur, par, it, b0, dg)) has = false;
                 }
                 const uint32_t m = __ballot_sync(kFull, has);
                 if (m == 0) continue;
@@ -560,9 +585,9 @@ __device__ bool engine_search(const EngineParams<typename Pol::Item>& P, Pol& po
                 __syncwarp();
                 uint32_t qh = 0, qt = (uint32_t)__popc(m);
                 int t = 0;
-                expand_batch<Pol>(P, pol, out, st, wid, gr, q, qh, qt, t, true, P.seeds, ws, pushed);
+                expand_batch<Pol>(P, pol, out, st, wid, gr, q, qh, qt, t, true, P.seeds, hub_thr, ws, pushed);
                 while (qt != qh && t < P.tau)
-                    expand_batch<Pol>(P, pol, out, st, wid, gr, q, qh, qt, t, false, 32, ws, pushed);
+                    expand_batch<Pol>(P, pol, out, st, wid, gr, q, qh, qt, t, false, 32, hub_thr, ws, pushed);
                 // budget spent: flush what is left in the local queue
                 while (qt != qh) {
                     const int nrem = (int)min(32u, qt - qh);
@@ -590,6 +615,11 @@ __device__ bool engine_search(const EngineParams<typename Pol::Item>& P, Pol& po
         }
         if (lane == 0 && pushed) atomicAdd((unsigned long long*)&cur.items, pushed);
         if (!grid_sync(&ctl->bar, &ctl->err)) return false;
+        if (si == 0 && i < (uint32_t)kTraceRounds && blockIdx.x == 0 && threadIdx.x == 0) {
+            ctl->t_end[i] = globaltimer_ns();
+            ctl->t_items[i] = ld_volatile(&cur.items);
+            ctl->t_dense[i] = dense;
+        }
         prev_dense = dense;
         if (ld_volatile(&ctl->err) != 0) break;
         if (P.max_inserted > 0 && ld_volatile(&sc.overflow) != 0) break;
@@ -634,6 +664,7 @@ struct PolSingle {
     static constexpr int kQueue = 512;
     static constexpr bool kCountInserts = false;
     static constexpr bool kDense = true;
+    static constexpr const char* kName = "single-reach";
     uint32_t* bits;
     __device__ __forceinline__ int vertex(Item it) const { return (int)it; }
     __device__ __forceinline__ uint64_t ctx(Item) const { return 0; }
@@ -692,6 +723,7 @@ struct PolPair {
     static constexpr int kQueue = 256;
     static constexpr bool kCountInserts = true;
     static constexpr bool kDense = false;
+    static constexpr const char* kName = "multi-reach";
     const int32_t* label;
     PairTable tab;
     long long ins;
@@ -721,6 +753,7 @@ struct PolMask {
     static constexpr int kQueue = 512;
     static constexpr bool kCountInserts = false;
     static constexpr bool kDense = false;
+    static constexpr const char* kName = "mask-reach";
     unsigned long long* mask;
     __device__ __forceinline__ int vertex(Item it) const { return (int)it; }
     __device__ __forceinline__ uint64_t ctx(Item it) const { return ld_volatile(&mask[it]); }

@@ -54,21 +54,27 @@ int launch_validate(const int32_t* off, const int32_t* adj, int32_t n, int64_t m
 // Transposed CSR (transpose.cu). bucket_shift(n): vertices per coarse bucket
 // = 2^shift, at most 1024 buckets.
 int bucket_shift(int32_t n);
+// trow[t] = row of arc t * step (t < T), trow[T] = row of the last arc; the
+// table has tile_rows_count(m) entries and drives the arc passes below.
+size_t tile_rows_count(int64_t m);
+int launch_tile_rows(const int32_t* off, int32_t n, int64_t m, int32_t* trow, cudaStream_t s);
 // bucket_cnt[b] += non-self arcs into bucket b; selfrow[u] += self-loops of u.
-int launch_bucket_hist(const int32_t* off, const int32_t* adj, int32_t n, int64_t m, int shift,
+int launch_bucket_hist(const int32_t* off, const int32_t* adj, const int32_t* trow, int32_t n, int64_t m, int shift,
                        unsigned long long* bucket_cnt, int32_t* selfrow, unsigned long long* nself, int num_sms,
                        cudaStream_t s);
 // G^T of the CSR (off, adj) with m arcs of which mt are not self-loops, by the
 // two-level bucketed counting sort (when transpose_bucketed(shift)).
 // bucket_tmp: 2 * nbuckets + 2 words; tmp_u, tmp_v: mt each; order_tmp: nbuckets.
 bool transpose_bucketed(int shift);
-int launch_transpose(const int32_t* off, const int32_t* adj, int32_t n, int64_t m, int64_t mt, int shift,
+int launch_transpose(const int32_t* off, const int32_t* adj, const int32_t* trow, int32_t n, int64_t m, int64_t mt,
+                     int shift,
                      const unsigned long long* bucket_cnt, unsigned long long* bucket_tmp, int32_t* tmp_u,
                      int32_t* tmp_v, int32_t* order_tmp, int32_t* toff, int32_t* tadj, int* err, int num_sms,
                      cudaStream_t s);
 // Direct G^T for very large n: global atomics. indeg: n + 1.
-int launch_transpose_direct(const int32_t* off, const int32_t* adj, int32_t n, int64_t m, int32_t* indeg,
-                            void* scan_tmp, int32_t* toff, int32_t* tadj, int num_sms, cudaStream_t s);
+int launch_transpose_direct(const int32_t* off, const int32_t* adj, const int32_t* trow, int32_t n, int64_t m,
+                            int32_t* indeg, void* scan_tmp, int32_t* toff, int32_t* tadj, int num_sms,
+                            cudaStream_t s);
 // Exclusive scan of int32 counts: out[0..n] with out[n] = total. tmp: scan_tmp_bytes(n).
 size_t scan_tmp_bytes(int64_t n);
 int launch_scan(const int32_t* in, int32_t* out, int64_t n, void* tmp, cudaStream_t s);

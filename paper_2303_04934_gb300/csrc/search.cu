@@ -2,6 +2,8 @@
 // hash-bag engine (engine.cuh) for single-reachability (first SCC, Sec. 4.2),
 // multi-reachability (Alg. 1; Sec. 4.3) and plain multi-source masks.
 #include <algorithm>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 
 #include "common.cuh"
@@ -67,6 +69,18 @@ int launch_engine(EngineParams<typename Pol::Item>& P, Pol& pol, const EngineOpt
     out->max_chunk = h.max_chunk;
     out->edges = h.edges;
     out->inserted = h.search[0].inserted;
+    static const bool trace = getenv("SCC_TRACE") != nullptr;
+    if (trace) {  // per-round timeline of this search on stderr
+        const int nr = std::min(h.search[0].rounds, kTraceRounds);
+        fprintf(stderr, "[scc-trace] %s: %d rounds, %.1f us in kernel\n", Pol::kName, h.search[0].rounds,
+                1000.0 * ms);
+        unsigned long long t = h.t0;
+        for (int r = 0; r < nr; ++r) {
+            fprintf(stderr, "[scc-trace]   round %2d %s %9.1f us  items %lld\n", r, h.t_dense[r] ? "dense " : "sparse",
+                    (h.t_end[r] - t) / 1000.0, h.t_items[r]);
+            t = h.t_end[r];
+        }
+    }
     if (h.err != 0 && h.err != SCC_ERR_CAPACITY) return h.err;
     return SCC_OK;
 }

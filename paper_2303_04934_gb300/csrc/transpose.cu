@@ -21,6 +21,7 @@
 // Rows of each arc tile are found by one binary search per thread followed by a
 // forward walk over the tile's row offsets staged in shared memory.
 #include <algorithm>
+#include <climits>
 #include <numeric>
 #include <vector>
 
@@ -49,47 +50,21 @@ __device__ __forceinline__ int row_search_g(const int32_t* __restrict__ off, int
     return lo;
 }
 
-// Same search by a full warp: 32 probes per round narrow [lo, hi] 32-fold, so a
-// search over 2^24 rows takes 5 dependent rounds instead of 24. The final round
-// probes the (at most 32) remaining candidates lo..hi, one per lane.
-__device__ __forceinline__ int warp_row_search(const int32_t* __restrict__ off, int lo, int hi, int64_t e) {
-    const int lane = threadIdx.x & 31;
-    while (hi - lo >= 32) {
-        const int64_t span = (int64_t)hi - lo;
-        const int pos = lo + (int)(span * lane / 32);  // probe points, lane 0 at lo
-        const bool le = (int64_t)__ldg(&off[pos]) <= e;
-        const uint32_t m = __ballot_sync(0xffffffffu, le);
-        const int last = 31 - __clz(m);  // off[lo] <= e, so lane 0 is always set
-        const int nlo = lo + (int)(span * last / 32);
-        const int nhi = last == 31 ? hi : lo + (int)(span * (last + 1) / 32) - 1;
-        lo = nlo;
-        hi = nhi;
-    }
-    const int pos = min(lo + lane, hi);
-    const uint32_t m = __ballot_sync(0xffffffffu, (int64_t)__ldg(&off[pos]) <= e && lo + lane <= hi);
-    return lo + (31 - __clz(m));
-}
-
 // One step of a block: arcs [s0, s1), thread t owns [s0 + 16 t, s0 + 16 t + 16).
 // Calls f(q, u, v) for its q-th arc (q < 16, a compile-time index after unrolling). Row offsets of the step are staged in
 // shared memory when they fit; each thread binary-searches its first arc's row
 // and walks forward.
 template <class F>
 __device__ __forceinline__ void for_step_arcs(const int32_t* __restrict__ off, const int32_t* __restrict__ adj,
-                                              int32_t n, int64_t s0, int64_t s1, int32_t* s_off, F&& f) {
-    __shared__ int s_r[2];
-    if (threadIdx.x < 32) {
-        int a = warp_row_search(off, 0, n - 1, s0);
-        int b = warp_row_search(off, a, n - 1, s1 - 1);
-        if (threadIdx.x == 0) {
-            s_r[0] = a;
-            s_r[1] = b;
-        }
-    }
-    __syncthreads();
-    const int r0 = s_r[0], r1 = s_r[1];
+                                              int32_t n, int64_t s0, int64_t s1, const int32_t* __restrict__ trow,
+                                              int32_t* s_off, F&& f) {
+    // rows of the step: trow[t] holds the row of arc t * kStep, so rows
+    // trow[t] .. trow[t + 1] contain every arc of [s0, s1)
+    const int64_t t = s0 / kStep;
+    const int r0 = __ldg(&trow[t]), r1 = __ldg(&trow[t + 1]);
     const int cnt = r1 - r0 + 2;  // offsets off[r0 .. r1 + 1]
     const bool sm = cnt <= kRowsCap;
+    __syncthreads();  // the previous step's readers of s_off are done
     if (sm)
         for (int i = threadIdx.x; i < cnt; i += blockDim.x) s_off[i] = off[r0 + i];
     __syncthreads();
@@ -141,9 +116,19 @@ __device__ __forceinline__ void for_step_arcs(const int32_t* __restrict__ off, c
     __syncthreads();
 }
 
+// Row of the first arc of every step (trow[t], t < T) and of the last arc
+// (trow[T]): one binary search per step instead of one per block step.
+__global__ void k_tile_rows(const int32_t* __restrict__ off, int32_t n, int64_t m, int64_t T, int32_t* trow) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t <= T; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t e = t < T ? t * kStep : m - 1;
+        trow[t] = row_search_g(off, 0, n - 1, e);
+    }
+}
+
 // A1. bucket histogram of non-self arcs; self-loops counted per row.
 __global__ void __launch_bounds__(kBlkA) k_bucket_hist(const int32_t* __restrict__ off, const int32_t* __restrict__ adj,
-                                                       int32_t n, int64_t m, int shift, int nb,
+                                                       const int32_t* __restrict__ trow, int32_t n, int64_t m,
+                                                       int shift, int nb,
                                                        unsigned long long* bucket_cnt, int32_t* selfrow,
                                                        unsigned long long* nself) {
     __shared__ int32_t s_off[kRowsCap];
@@ -153,7 +138,7 @@ __global__ void __launch_bounds__(kBlkA) k_bucket_hist(const int32_t* __restrict
     unsigned long long my_self = 0;
     for (int64_t s0 = (int64_t)blockIdx.x * kStep; s0 < m; s0 += (int64_t)gridDim.x * kStep) {
         const int64_t s1 = min(s0 + (int64_t)kStep, m);
-        for_step_arcs(off, adj, n, s0, s1, s_off, [&](int, int u, int v) {
+        for_step_arcs(off, adj, n, s0, s1, trow, s_off, [&](int, int u, int v) {
             if (u == v) {
                 atomicAdd(&selfrow[u], 1);
                 ++my_self;
@@ -185,7 +170,8 @@ __global__ void k_bucket_scan(const unsigned long long* cnt, int nb, unsigned lo
 // A2. partition: per 8k-arc tile, a shared-memory counting sort by bucket,
 // one global reservation per non-empty bucket, then a coalesced write-out.
 __global__ void __launch_bounds__(kBlkA) k_bucket_part(const int32_t* __restrict__ off, const int32_t* __restrict__ adj,
-                                                       int32_t n, int64_t m, int shift, int nb,
+                                                       const int32_t* __restrict__ trow, int32_t n, int64_t m,
+                                                       int shift, int nb,
                                                        unsigned long long* cursor, int32_t* out_u, int32_t* out_v,
                                                        unsigned long long mt, int* err) {
     __shared__ int32_t s_off[kRowsCap];
@@ -206,7 +192,7 @@ __global__ void __launch_bounds__(kBlkA) k_bucket_part(const int32_t* __restrict
         int uu[kChunk], vv[kChunk];
 #pragma unroll
         for (int q = 0; q < kChunk; ++q) vv[q] = -1;
-        for_step_arcs(off, adj, n, t0, t1, s_off, [&](int q, int u, int v) {
+        for_step_arcs(off, adj, n, t0, t1, trow, s_off, [&](int q, int u, int v) {
             if (u != v) {
                 uu[q] = u;
                 vv[q] = v;
@@ -274,10 +260,21 @@ __global__ void __launch_bounds__(kBlkB) k_bucket_rows(const int32_t* __restrict
         const long long a0 = (long long)start[b], a1 = (long long)start[b + 1];
         for (int i = threadIdx.x; i < vw; i += blockDim.x) s_cnt[i] = 0;
         __syncthreads();
-        for (long long i = a0 + threadIdx.x; i < a1; i += blockDim.x) {
-            const unsigned int lv = (unsigned int)(__ldg(&vv[i]) - v0);
-            if (lv < (unsigned int)vw) atomicAdd(&s_cnt[lv], 1);
-            else atomicExch(err, SCC_ERR_INTERNAL);  // arc outside its bucket: skip it, report
+        // 8 independent loads in flight per thread
+        for (long long i0 = a0 + threadIdx.x; i0 < a1; i0 += 8ll * blockDim.x) {
+            int x[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const long long i = i0 + (long long)k * blockDim.x;
+                x[k] = i < a1 ? __ldg(&vv[i]) : INT_MIN;
+            }
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                if (x[k] == INT_MIN) continue;
+                const unsigned int lv = (unsigned int)(x[k] - v0);
+                if (lv < (unsigned int)vw) atomicAdd(&s_cnt[lv], 1);
+                else atomicExch(err, SCC_ERR_INTERNAL);  // arc outside its bucket: skip it, report
+            }
         }
         __syncthreads();
         // exclusive scan of s_cnt[0..vw) in place; each thread owns a contiguous run
@@ -302,12 +299,23 @@ __global__ void __launch_bounds__(kBlkB) k_bucket_rows(const int32_t* __restrict
             run += c;
         }
         __syncthreads();
-        for (long long i = a0 + threadIdx.x; i < a1; i += blockDim.x) {
-            const unsigned int lv = (unsigned int)(__ldg(&vv[i]) - v0);
-            if (lv >= (unsigned int)vw) continue;
-            const int p = atomicAdd(&s_cnt[lv], 1);
-            if (a0 + p < a1) tadj[a0 + p] = __ldg(&uu[i]);
-            else atomicExch(err, SCC_ERR_INTERNAL);
+        for (long long i0 = a0 + threadIdx.x; i0 < a1; i0 += 8ll * blockDim.x) {
+            int x[8], y[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const long long i = i0 + (long long)k * blockDim.x;
+                x[k] = i < a1 ? __ldg(&vv[i]) : INT_MIN;
+                y[k] = i < a1 ? __ldg(&uu[i]) : 0;
+            }
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                if (x[k] == INT_MIN) continue;
+                const unsigned int lv = (unsigned int)(x[k] - v0);
+                if (lv >= (unsigned int)vw) continue;
+                const int p = atomicAdd(&s_cnt[lv], 1);
+                if (a0 + p < a1) tadj[a0 + p] = y[k];
+                else atomicExch(err, SCC_ERR_INTERNAL);
+            }
         }
         __syncthreads();
     }
@@ -317,20 +325,22 @@ __global__ void __launch_bounds__(kBlkB) k_bucket_rows(const int32_t* __restrict
 // Direct path for graphs too large for shared per-bucket counters: global
 // in-degree atomics, scan, global cursor atomics.
 __global__ void __launch_bounds__(kBlkA) k_direct_count(const int32_t* __restrict__ off,
-                                                        const int32_t* __restrict__ adj, int32_t n, int64_t m,
+                                                        const int32_t* __restrict__ adj,
+                                                        const int32_t* __restrict__ trow, int32_t n, int64_t m,
                                                         int32_t* indeg) {
     __shared__ int32_t s_off[kRowsCap];
     for (int64_t s0 = (int64_t)blockIdx.x * kStep; s0 < m; s0 += (int64_t)gridDim.x * kStep)
-        for_step_arcs(off, adj, n, s0, min(s0 + (int64_t)kStep, m), s_off, [&](int, int u, int v) {
+        for_step_arcs(off, adj, n, s0, min(s0 + (int64_t)kStep, m), trow, s_off, [&](int, int u, int v) {
             if (u != v) atomicAdd(&indeg[v], 1);
         });
 }
 __global__ void __launch_bounds__(kBlkA) k_direct_place(const int32_t* __restrict__ off,
-                                                        const int32_t* __restrict__ adj, int32_t n, int64_t m,
+                                                        const int32_t* __restrict__ adj,
+                                                        const int32_t* __restrict__ trow, int32_t n, int64_t m,
                                                         int32_t* cursor, int32_t* tadj) {
     __shared__ int32_t s_off[kRowsCap];
     for (int64_t s0 = (int64_t)blockIdx.x * kStep; s0 < m; s0 += (int64_t)gridDim.x * kStep)
-        for_step_arcs(off, adj, n, s0, min(s0 + (int64_t)kStep, m), s_off, [&](int, int u, int v) {
+        for_step_arcs(off, adj, n, s0, min(s0 + (int64_t)kStep, m), trow, s_off, [&](int, int u, int v) {
             if (u != v) tadj[atomicAdd(&cursor[v], 1)] = u;
         });
 }
@@ -348,28 +358,40 @@ int bucket_shift(int32_t n) {
     return shift;
 }
 
-int launch_bucket_hist(const int32_t* off, const int32_t* adj, int32_t n, int64_t m, int shift,
+size_t tile_rows_count(int64_t m) { return (size_t)((m + kStep - 1) / kStep) + 1; }
+
+int launch_tile_rows(const int32_t* off, int32_t n, int64_t m, int32_t* trow, cudaStream_t s) {
+    if (m == 0 || n == 0) return SCC_OK;
+    const int64_t T = (m + kStep - 1) / kStep;
+    k_tile_rows<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>((T + 256) / 256, 4096)), 256, 0, s>>>(off, n, m, T,
+                                                                                                     trow);
+    SCC_LAUNCH();
+    return SCC_OK;
+}
+
+int launch_bucket_hist(const int32_t* off, const int32_t* adj, const int32_t* trow, int32_t n, int64_t m, int shift,
                        unsigned long long* bucket_cnt, int32_t* selfrow, unsigned long long* nself, int num_sms,
                        cudaStream_t s) {
     if (m == 0 || n == 0) return SCC_OK;
     int nb = (int)(((int64_t)n + (1ll << shift) - 1) >> shift);
-    k_bucket_hist<<<grid_for_arcs(m, kStep, num_sms, 2), kBlkA, 0, s>>>(off, adj, n, m, shift, nb, bucket_cnt,
+    k_bucket_hist<<<grid_for_arcs(m, kStep, num_sms, 2), kBlkA, 0, s>>>(off, adj, trow, n, m, shift, nb, bucket_cnt,
                                                                           selfrow, nself);
     SCC_LAUNCH();
     return SCC_OK;
 }
 
-int launch_transpose_direct(const int32_t* off, const int32_t* adj, int32_t n, int64_t m, int32_t* indeg,
-                            void* scan_tmp, int32_t* toff, int32_t* tadj, int num_sms, cudaStream_t s) {
+int launch_transpose_direct(const int32_t* off, const int32_t* adj, const int32_t* trow, int32_t n, int64_t m,
+                            int32_t* indeg, void* scan_tmp, int32_t* toff, int32_t* tadj, int num_sms,
+                            cudaStream_t s) {
     SCC_CUDA(cudaMemsetAsync(indeg, 0, sizeof(int32_t) * ((size_t)n + 1), s));
     if (m > 0) {
-        k_direct_count<<<grid_for_arcs(m, kStep, num_sms, 2), kBlkA, 0, s>>>(off, adj, n, m, indeg);
+        k_direct_count<<<grid_for_arcs(m, kStep, num_sms, 2), kBlkA, 0, s>>>(off, adj, trow, n, m, indeg);
         SCC_LAUNCH();
     }
     SCC_TRY(launch_scan(indeg, toff, n, scan_tmp, s));
     if (m > 0) {
         SCC_CUDA(cudaMemcpyAsync(indeg, toff, sizeof(int32_t) * (size_t)n, cudaMemcpyDeviceToDevice, s));
-        k_direct_place<<<grid_for_arcs(m, kStep, num_sms, 2), kBlkA, 0, s>>>(off, adj, n, m, indeg, tadj);
+        k_direct_place<<<grid_for_arcs(m, kStep, num_sms, 2), kBlkA, 0, s>>>(off, adj, trow, n, m, indeg, tadj);
         SCC_LAUNCH();
     }
     return SCC_OK;
@@ -377,7 +399,8 @@ int launch_transpose_direct(const int32_t* off, const int32_t* adj, int32_t n, i
 
 bool transpose_bucketed(int shift) { return shift <= kBucketLog; }
 
-int launch_transpose(const int32_t* off, const int32_t* adj, int32_t n, int64_t m, int64_t mt, int shift,
+int launch_transpose(const int32_t* off, const int32_t* adj, const int32_t* trow, int32_t n, int64_t m, int64_t mt,
+                     int shift,
                      const unsigned long long* bucket_cnt, unsigned long long* bucket_tmp, int32_t* tmp_u,
                      int32_t* tmp_v, int32_t* order_tmp, int32_t* toff, int32_t* tadj, int* err, int num_sms,
                      cudaStream_t s) {
@@ -393,7 +416,7 @@ int launch_transpose(const int32_t* off, const int32_t* adj, int32_t n, int64_t 
     if (mt > 0) {
         const int stage = 2 * kStep * (int)sizeof(int32_t);
         SCC_CUDA(cudaFuncSetAttribute(k_bucket_part, cudaFuncAttributeMaxDynamicSharedMemorySize, stage));
-        k_bucket_part<<<grid_for_arcs(m, kStep, num_sms, 2), kBlkA, stage, s>>>(off, adj, n, m, shift, nb, cursor,
+        k_bucket_part<<<grid_for_arcs(m, kStep, num_sms, 2), kBlkA, stage, s>>>(off, adj, trow, n, m, shift, nb, cursor,
                                                                                   tmp_u, tmp_v,
                                                                                   (unsigned long long)mt, err);
         SCC_LAUNCH();
