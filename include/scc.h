@@ -145,7 +145,8 @@ SCC_API int reach_multi(scc_handle h, const int32_t* sources, int32_t k, int32_t
 /* ------------------------------------------------------------ statistics ---- */
 /*
  * Counters of the last scc_run on h, in the paper's cost categories (Sec. 4,
- * Fig. 8): times in milliseconds measured with CUDA events on the run's stream.
+ * Fig. 8), and of the handle's construction: times in milliseconds measured
+ * with CUDA events on the stream of the call.
  */
 typedef struct scc_stats {
     int32_t n_trimmed;         /* vertices removed by trimming */
@@ -156,10 +157,13 @@ typedef struct scc_stats {
     int32_t table_resizes;     /* pair-table regrowths */
     int32_t engine_launches;   /* launches of the reachability engine kernel */
     double ms_trim, ms_first_scc, ms_multi_search, ms_resize, ms_label;
-    double ms_engine;          /* summed duration of the engine launches */
-    int64_t engine_arcs;       /* arcs examined by the engine */
-    int64_t engine_items;      /* frontier/queue items expanded (adjacency rows read) */
-    int64_t engine_inserted;   /* items newly visited (first SCC: vertices; later: pairs) */
+    double ms_engine;          /* summed duration of the first-SCC engine launches */
+    int64_t engine_arcs;       /* arcs examined by the first-SCC engine launches */
+    int64_t engine_items;      /* items they expanded (adjacency rows read) */
+    int64_t engine_inserted;   /* reachability pairs inserted by multi-reachability */
+    /* graph construction (scc_graph_create of this handle): total and the three
+       passes of the transposed-CSR build, CUDA events on the creating stream */
+    double ms_create, ms_transpose_hist, ms_transpose_part, ms_transpose_rows;
 } scc_stats;
 
 SCC_API int scc_get_stats(scc_handle h, scc_stats* out);

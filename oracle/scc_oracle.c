@@ -27,7 +27,7 @@
  * Parity pins (tests/test_oracle_*.py): brute-force transitive closure on every
  * digraph with n <= 4 and on random digraphs, closed forms (cycles, chains,
  * complete digraphs, tori with all arcs), invariants (partition, canonical min,
- * acyclic condensation) and the paper's Table 3 statistics for its REC/REC'
+ * acyclic condensation) and the paper's Table 2 statistics for its REC/REC'
  * lattices.
  */
 #include <stdint.h>

@@ -53,6 +53,7 @@ struct scc_graph {
     int64_t tab_alloc[2] = {0, 0};
     EngineBuf eb32, eb64;
     scc_stats stats;
+    double create_ms[4] = {0, 0, 0, 0};  // total, histogram, partition, rows
 };
 
 namespace scc {
@@ -264,9 +265,26 @@ int scc_config_default(scc_config* cfg) {
     return SCC_OK;
 }
 
+struct CreateEvents {
+    cudaEvent_t e[8] = {};
+    CreateEvents() {
+        for (auto& x : e) cudaEventCreate(&x);
+    }
+    ~CreateEvents() {
+        for (auto& x : e)
+            if (x) cudaEventDestroy(x);
+    }
+    double ms(int a, int b) {
+        float t = 0;
+        return cudaEventElapsedTime(&t, e[a], e[b]) == cudaSuccess ? (double)t : 0.0;
+    }
+};
+
 static int graph_create_impl(scc_graph* h, int32_t n, int64_t m, const int32_t* offsets, const int32_t* targets,
                              cudaStream_t s) {
     SCC_TRY(device_info(&h->di));
+    CreateEvents ce;
+    cudaEventRecord(ce.e[0], s);
     h->n = n;
     h->m_in = m;
     int32_t *off_in = nullptr, *adj_in = nullptr;
@@ -301,7 +319,9 @@ static int graph_create_impl(scc_graph* h, int32_t n, int64_t m, const int32_t* 
     int32_t* trow = nullptr;
     SCC_TRY(dalloc_t(&trow, tile_rows_count(m), s));
     SCC_TRY(launch_tile_rows(off_in, n, m, trow, s));
+    cudaEventRecord(ce.e[1], s);
     SCC_TRY(launch_bucket_hist(off_in, adj_in, trow, n, m, shift, bcnt, selfrow, bcnt + nb + 1, h->di.num_sms, s));
+    cudaEventRecord(ce.e[2], s);
     unsigned long long hself = 0;
     SCC_CUDA(cudaMemcpyAsync(&hself, bcnt + nb + 1, sizeof(hself), cudaMemcpyDeviceToHost, s));
     SCC_CUDA(cudaStreamSynchronize(s));
@@ -338,7 +358,7 @@ static int graph_create_impl(scc_graph* h, int32_t n, int64_t m, const int32_t* 
         SCC_TRY(dalloc_t(&terr, 1, s));
         SCC_CUDA(cudaMemsetAsync(terr, 0, sizeof(int), s));
         SCC_TRY(launch_transpose(h->off, h->adj, trow, n, m_cur, h->mt, shift, bcnt, btmp, tmp_u, tmp_v, ord, toff,
-                                 h->tadj, terr, h->di.num_sms, s));
+                                 h->tadj, terr, h->di.num_sms, s, &ce.e[3]));
         int herr = 0;
         SCC_CUDA(cudaMemcpyAsync(&herr, terr, sizeof(int), cudaMemcpyDeviceToHost, s));
         SCC_CUDA(cudaStreamSynchronize(s));
@@ -358,7 +378,14 @@ static int graph_create_impl(scc_graph* h, int32_t n, int64_t m, const int32_t* 
     dfree(bcnt, s);
     dfree(btmp, s);
     dfree(stmp, s);
+    cudaEventRecord(ce.e[7], s);
     SCC_CUDA(cudaStreamSynchronize(s));
+    h->create_ms[0] = ce.ms(0, 7);
+    h->create_ms[1] = ce.ms(1, 2);
+    if (transpose_bucketed(shift) && h->mt > 0) {
+        h->create_ms[2] = ce.ms(3, 4);
+        h->create_ms[3] = ce.ms(5, 6);
+    }
     return SCC_OK;
 }
 
@@ -433,6 +460,10 @@ int scc_set_config(scc_handle h, const scc_config* cfg) {
 int scc_get_stats(scc_handle h, scc_stats* out) {
     if (!h || !out) return SCC_ERR_INVALID_ARG;
     *out = h->stats;
+    out->ms_create = h->create_ms[0];
+    out->ms_transpose_hist = h->create_ms[1];
+    out->ms_transpose_part = h->create_ms[2];
+    out->ms_transpose_rows = h->create_ms[3];
     return SCC_OK;
 }
 
@@ -590,8 +621,6 @@ static int scc_run_impl(scc_graph* h, int32_t* labels_out, cudaStream_t s) {
                 st.batches += r.batches;
                 st.search_rounds += r.rounds;
                 st.pairs += (int64_t)r.pairs;
-                st.engine_arcs += (int64_t)r.edges;
-                st.engine_items += (int64_t)r.items;
                 st.engine_inserted += (int64_t)r.pairs;
                 hc[1] = r.ndone;
                 if (r.status == 0) break;

@@ -70,7 +70,7 @@ int launch_transpose(const int32_t* off, const int32_t* adj, const int32_t* trow
                      int shift,
                      const unsigned long long* bucket_cnt, unsigned long long* bucket_tmp, int32_t* tmp_u,
                      int32_t* tmp_v, int32_t* order_tmp, int32_t* toff, int32_t* tadj, int* err, int num_sms,
-                     cudaStream_t s);
+                     cudaStream_t s, cudaEvent_t* ev = nullptr);  // ev[0..3]: around the partition and the rows pass
 // Direct G^T for very large n: global atomics. indeg: n + 1.
 int launch_transpose_direct(const int32_t* off, const int32_t* adj, const int32_t* trow, int32_t n, int64_t m,
                             int32_t* indeg, void* scan_tmp, int32_t* toff, int32_t* tadj, int num_sms,

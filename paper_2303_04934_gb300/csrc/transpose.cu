@@ -403,7 +403,7 @@ int launch_transpose(const int32_t* off, const int32_t* adj, const int32_t* trow
                      int shift,
                      const unsigned long long* bucket_cnt, unsigned long long* bucket_tmp, int32_t* tmp_u,
                      int32_t* tmp_v, int32_t* order_tmp, int32_t* toff, int32_t* tadj, int* err, int num_sms,
-                     cudaStream_t s) {
+                     cudaStream_t s, cudaEvent_t* ev) {
     const int nb = std::max(1, (int)(((int64_t)n + (1ll << shift) - 1) >> shift));
     unsigned long long* start = bucket_tmp;
     unsigned long long* cursor = bucket_tmp + nb + 1;
@@ -416,10 +416,12 @@ int launch_transpose(const int32_t* off, const int32_t* adj, const int32_t* trow
     if (mt > 0) {
         const int stage = 2 * kStep * (int)sizeof(int32_t);
         SCC_CUDA(cudaFuncSetAttribute(k_bucket_part, cudaFuncAttributeMaxDynamicSharedMemorySize, stage));
+        if (ev) cudaEventRecord(ev[0], s);
         k_bucket_part<<<grid_for_arcs(m, kStep, num_sms, 2), kBlkA, stage, s>>>(off, adj, trow, n, m, shift, nb, cursor,
                                                                                   tmp_u, tmp_v,
                                                                                   (unsigned long long)mt, err);
         SCC_LAUNCH();
+        if (ev) cudaEventRecord(ev[1], s);
     }
     // buckets by decreasing size (longest first), from the host copy of the counts
     std::vector<unsigned long long> hc(nb);
@@ -432,9 +434,11 @@ int launch_transpose(const int32_t* off, const int32_t* adj, const int32_t* trow
     const size_t smem = sizeof(int) << shift;
     if (smem > 48 * 1024)
         SCC_CUDA(cudaFuncSetAttribute(k_bucket_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    if (ev) cudaEventRecord(ev[2], s);
     k_bucket_rows<<<std::min(nb, num_sms * 2), kBlkB, smem, s>>>(tmp_u, tmp_v, start, order_tmp, nb, shift, n, toff,
                                                                    tadj, err);
     SCC_LAUNCH();
+    if (ev) cudaEventRecord(ev[3], s);
     SCC_CUDA(cudaStreamSynchronize(s));  // ord (host) must outlive the copy
     return SCC_OK;
 }

@@ -108,7 +108,7 @@ GG_API int64_t gg_torus(int dims, int64_t X, int64_t Y, int64_t Z, double p, uin
  * model 1 (SQR'/REC'): each of the two arcs u->v and v->u of every adjacent
  *   pair is present independently with probability 0.3. (The paper's wording
  *   lists 0.3 / 0.3 / 0.4 outcomes; the independent reading is the one whose
- *   arc count, m = 0.6 * 2n, and SCC count agree with its Table 3.)
+ *   arc count, m = 0.6 * 2n, and SCC count agree with its table of SCC running times (Table 2).)
  * adj must hold 4*n entries. Returns m.
  */
 GG_API int64_t gg_paper_lattice(int64_t X, int64_t Y, int model, uint64_t seed,
@@ -121,7 +121,7 @@ GG_API int64_t gg_paper_lattice(int64_t X, int64_t Y, int model, uint64_t seed,
     int64_t* cnt = (int64_t*)malloc(sizeof(int64_t) * (size_t)n);
     /* out-arc u->w for neighbour w = nb(u,d), computed locally from the draws
        that concern the pair {u,w}. */
-    #define PAPER_ARC(u, d, res)                                                        \
+    #define LATTICE_ARC(u, d, res)                                                        \
         do {                                                                           \
             int64_t w_ = torus_nb((u), (d), X, Y, 1);                                  \
             int dop_ = (d) ^ 1; /* direction from w back to u */                       \
@@ -138,7 +138,7 @@ GG_API int64_t gg_paper_lattice(int64_t X, int64_t Y, int model, uint64_t seed,
     #pragma omp parallel for schedule(static)
     for (int64_t u = 0; u < n; ++u) {
         int64_t c = 0;
-        for (int d = 0; d < 4; ++d) { int r; PAPER_ARC(u, d, r); c += r; }
+        for (int d = 0; d < 4; ++d) { int r; LATTICE_ARC(u, d, r); c += r; }
         cnt[u] = c;
     }
     int64_t m = scan_counts(cnt, off, n);
@@ -146,11 +146,11 @@ GG_API int64_t gg_paper_lattice(int64_t X, int64_t Y, int model, uint64_t seed,
     for (int64_t u = 0; u < n; ++u) {
         int64_t o = off[u];
         for (int d = 0; d < 4; ++d) {
-            int r; PAPER_ARC(u, d, r);
+            int r; LATTICE_ARC(u, d, r);
             if (r) adj[o++] = (int32_t)torus_nb(u, d, X, Y, 1);
         }
     }
-    #undef PAPER_ARC
+    #undef LATTICE_ARC
     free(cnt);
     return m;
 }

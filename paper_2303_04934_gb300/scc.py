@@ -46,7 +46,9 @@ class scc_stats(ctypes.Structure):
                 ("engine_launches", ctypes.c_int32), ("ms_trim", ctypes.c_double), ("ms_first_scc", ctypes.c_double),
                 ("ms_multi_search", ctypes.c_double), ("ms_resize", ctypes.c_double), ("ms_label", ctypes.c_double),
                 ("ms_engine", ctypes.c_double), ("engine_arcs", ctypes.c_int64), ("engine_items", ctypes.c_int64),
-                ("engine_inserted", ctypes.c_int64)]
+                ("engine_inserted", ctypes.c_int64), ("ms_create", ctypes.c_double),
+                ("ms_transpose_hist", ctypes.c_double), ("ms_transpose_part", ctypes.c_double),
+                ("ms_transpose_rows", ctypes.c_double)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

@@ -1,5 +1,5 @@
 """Oracle output checked against invariants (with planted mistakes that the
-checker must catch) and against the paper's Table 3 statistics for its own
+checker must catch) and against the paper's Table 2 statistics for its own
 lattice models. CPU only."""
 import json
 import os
@@ -11,7 +11,7 @@ import oracle
 from oracle.invariants import check_scc_labels
 from paper_2303_04934_gb300 import graphgen as gg
 
-GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "paper_table3_lattices.json")
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "paper_scc_table_lattices.json")
 
 
 @pytest.mark.parametrize("make", [
@@ -62,8 +62,8 @@ def test_checker_catches_planted_mistakes():
 
 @pytest.mark.slow
 @pytest.mark.parametrize("name", ["REC", "REC'"])
-def test_paper_table3_lattice_statistics(name):
-    """Table 3 prints m, #SCC and |SCC1| for one random instance of each lattice
+def test_paper_table2_lattice_statistics(name):
+    """Table 2 prints m, #SCC and |SCC1| for one random instance of each lattice
     model (Sec. 6 'Setup'); our generator + Tarjan draw another instance.
 
     REC' (independent arcs, p = 0.3 each way) is a pin: #SCC within 1% and the
