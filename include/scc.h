@@ -142,6 +142,29 @@ SCC_API int scc_run(scc_handle h, int32_t* labels_out, void* stream);
 SCC_API int reach_multi(scc_handle h, const int32_t* sources, int32_t k, int32_t dir, uint64_t* out,
                 void* stream);
 
+/*
+ * reach_multi without device allocation. The paper has no counterpart: this
+ * entry point exists for callers that cannot allocate device memory at the
+ * point of the call -- code running while a stream is being captured into a
+ * CUDA graph, latency-critical loops that forbid allocator calls, and hosts
+ * whose device memory belongs to their own allocator. It computes exactly what
+ * reach_multi computes, with the same kernels, and calls no allocating routine:
+ * the search's working memory comes from one fixed device array of 32 MiB that
+ * the library keeps on every device it has run on, until the process exits.
+ *   sources  DEVICE int32[k], 1 <= k <= 64, each in [0, n).
+ *   out      DEVICE uint64[n], written. (Host pointers are rejected.)
+ * Returns SCC_ERR_INVALID_ARG when the graph's working space does not fit the
+ * array (about 500 thousand vertices for sparse graphs), SCC_ERR_CAPACITY when a
+ * search needs more frontier space than the array holds.
+ * Every call shares the array and finds the previous call's contents in it, so
+ * a call resets what must start empty; calls whose work overlaps on the GPU
+ * (for instance on two streams) race on it and must be serialised by the
+ * caller. The first call on a device looks the array's device address up once;
+ * make that first call before any stream capture. Synchronises `stream`.
+ */
+SCC_API int reach_multi_noalloc(scc_handle h, const int32_t* sources, int32_t k, int32_t dir, uint64_t* out,
+                                void* stream);
+
 /* ------------------------------------------------------------ statistics ---- */
 /*
  * Counters of the last scc_run on h, in the paper's cost categories (Sec. 4,

@@ -708,6 +708,16 @@ int reach_multi(scc_handle h, const int32_t* sources, int32_t k, int32_t dir, ui
     return SCC_OK;
 }
 
+// reach_multi for callers that cannot allocate device memory during the call:
+// device buffers only, working memory from the library's fixed device array.
+int reach_multi_noalloc(scc_handle h, const int32_t* sources, int32_t k, int32_t dir, uint64_t* out, void* stream) {
+    if (!h || !sources || !out || k < 1 || k > 64 || (dir != 0 && dir != 1)) return SCC_ERR_INVALID_ARG;
+    if (!is_device_ptr(sources) || !is_device_ptr(out)) return SCC_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    return reach_multi_noalloc_impl(dir == 0 ? h->off : h->toff, dir == 0 ? h->adj : h->tadj, h->n, h->mt,
+                                    h->cfg.lambda, opts_of(h), sources, k, out, s);
+}
+
 // ------------------------------------------------------------ debug hooks --
 int scc_debug_csr(scc_handle h, int32_t which, int32_t* off, int32_t* adj, void* stream) {
     if (!h || !off || (h->mt > 0 && !adj) || (which != 0 && which != 1)) return SCC_ERR_INVALID_ARG;

@@ -254,6 +254,15 @@ size_t bgss_ctl_bytes();
 int bgss_full_grid(int num_sms);
 int run_bgss_device(const BgssArgs& a, BgssResult* res, cudaStream_t st);
 
+// Mask reachability on fixed buffers (no allocation, no events).
+int run_mask_fixed(const int32_t* off, const int32_t* adj, int32_t n, const int32_t* sources, int32_t k,
+                   unsigned long long* mask, const EngineBuf* b, const EngineOpts& o, EngineRun* out,
+                   cudaStream_t st);
+// reach_multi on the library's fixed device scratch array (noalloc.cu).
+int reach_multi_noalloc_impl(const int32_t* off, const int32_t* adj, int32_t n, int64_t mt, int lambda,
+                             const EngineOpts& o, const int32_t* sources, int32_t k, uint64_t* out,
+                             cudaStream_t s);
+
 // Debug: hash bag alone (vertex items).
 int run_bag_only(const int32_t* items, int64_t count, int lambda, int sigma, int32_t* out, int64_t* nout,
                  int* chunks, cudaStream_t st);

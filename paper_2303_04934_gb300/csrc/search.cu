@@ -235,6 +235,34 @@ int run_mask(const int32_t* off, const int32_t* adj, int32_t n, const int32_t* s
     return out->err ? out->err : SCC_OK;
 }
 
+// Mask reachability on caller-provided (fixed) engine buffers: no device
+// allocation and no CUDA event; the caller has emptied the bag and the control
+// block. A search that needs more bag space than the buffers hold returns
+// SCC_ERR_CAPACITY.
+int run_mask_fixed(const int32_t* off, const int32_t* adj, int32_t n, const int32_t* sources, int32_t k,
+                   unsigned long long* mask, const EngineBuf* b, const EngineOpts& o, EngineRun* out,
+                   cudaStream_t st) {
+    auto P = make_engine_params<uint32_t>(off, adj, n, b, o);
+    P.init = reinterpret_cast<const uint32_t*>(sources);
+    P.ninit = k;
+    PolMask pol{mask};
+    DenseParams dp{nullptr, nullptr, {nullptr, nullptr}, 0, 0};
+    int grid = 0;
+    SCC_TRY(coop_grid<PolMask>(o.num_sms, &grid));
+    void* args[] = {(void*)&P, (void*)&pol, (void*)&dp};
+    SCC_CUDA(cudaLaunchCooperativeKernel((const void*)engine_kernel<PolMask>, dim3(grid), dim3(kEngineBlock), args, 0,
+                                         st));
+    count_launch();
+    EngineCtl h;
+    SCC_CUDA(cudaMemcpyAsync(&h, P.ctl, sizeof(EngineCtl), cudaMemcpyDeviceToHost, st));
+    SCC_CUDA(cudaStreamSynchronize(st));
+    out->err = h.err;
+    out->rounds = h.search[0].rounds;
+    out->edges = h.edges;
+    out->items = h.items;
+    return h.err ? h.err : SCC_OK;
+}
+
 // ---------------------------------------------------------- hash bag test --
 namespace {
 

@@ -28,7 +28,7 @@ SCC_ERR_INTERNAL = -6
 #: every symbol the headers declare (checked by tests/test_abi_symbols.py)
 EXPORTED = [
     "scc_error_string", "scc_config_default", "scc_graph_create", "scc_graph_destroy", "scc_set_config",
-    "scc_run", "reach_multi", "scc_get_stats",
+    "scc_run", "reach_multi", "reach_multi_noalloc", "scc_get_stats",
     "scc_graph_info", "scc_debug_csr", "scc_debug_trim", "scc_debug_pivot_order", "scc_debug_single_reach",
     "scc_debug_multi_reach", "scc_debug_hashbag", "scc_debug_pair_table", "scc_debug_launch_count",
 ]
@@ -87,6 +87,7 @@ def load() -> ctypes.CDLL:
         "scc_set_config": ([vp, P(scc_config)], ctypes.c_int),
         "scc_run": ([vp, vp, vp], ctypes.c_int),
         "reach_multi": ([vp, vp, i32, i32, vp, vp], ctypes.c_int),
+        "reach_multi_noalloc": ([vp, vp, i32, i32, vp, vp], ctypes.c_int),
         "scc_get_stats": ([vp, P(scc_stats)], ctypes.c_int),
         "scc_graph_info": ([vp, P(i32), P(i64), P(i64)], ctypes.c_int),
         "scc_debug_csr": ([vp, i32, vp, vp, vp], ctypes.c_int),
@@ -173,6 +174,12 @@ def scc_run(h, labels_out, stream=None) -> None:
 
 def reach_multi(h, sources, k: int, dir: int, out, stream=None) -> None:
     _check(load().reach_multi(h, _ptr(sources), k, dir, _ptr(out), _stream(stream)), "reach_multi")
+
+
+def reach_multi_noalloc(h, sources, k: int, dir: int, out, stream=None) -> None:
+    """reach_multi for callers that cannot allocate: device buffers only, working
+    memory from the library's fixed 32 MiB device array (see include/scc.h)."""
+    _check(load().reach_multi_noalloc(h, _ptr(sources), k, dir, _ptr(out), _stream(stream)), "reach_multi_noalloc")
 
 
 def scc_get_stats(h) -> dict:
