@@ -292,8 +292,20 @@ def main():
     }
     kname, (kms, klaunch, kbytes) = max(cands.items(), key=lambda kv: kv[1][0])
     achieved = kbytes / (kms / 1e3) / 1e9 if kms > 0 else 0.0
+    # measured DRAM bytes per launch of this kernel (profiles/traffic.json, an ncu
+    # capture scaled to this workload), only while the kernel source is unchanged
+    traffic = None
+    try:
+        import hashlib
+        rec = json.load(open(os.path.join(ROOT, "profiles", "traffic.json"))).get(kname)
+        if rec and spec["kind"] == "rmat" and spec["scale"] == 24:
+            cur = hashlib.sha256(open(os.path.join(ROOT, rec["source"]), "rb").read()).hexdigest()
+            if cur == rec["source_sha256"]:
+                traffic = rec["bytes_per_launch"]
+    except Exception:
+        traffic = None
     roofline = {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": hbm_peak,
-                "peak_source": peak_src, "unit": "GB/s", "frac": achieved / hbm_peak, "traffic": None,
+                "peak_source": peak_src, "unit": "GB/s", "frac": achieved / hbm_peak, "traffic": traffic,
                 "algorithmic_bytes_per_launch": kbytes / max(1, klaunch),
                 "ms_per_launch": kms / max(1, klaunch), "share_of_step": (kms / ms) if ms > 0 else None,
                 "others": {k: {"ms_per_step": v[0] / max(1, len(stats)),
