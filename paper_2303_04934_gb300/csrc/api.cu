@@ -603,7 +603,8 @@ static int scc_run_impl(scc_graph* h, int32_t* labels_out, cudaStream_t s) {
                 if (attempt > 80) return SCC_ERR_CAPACITY;
                 SCC_TRY(reserve_table(h, 0, tab_alloc, s));
                 SCC_TRY(reserve_table(h, 1, tab_alloc, s));
-                SCC_TRY(engine_reserve(&h->eb64, 8, (long long)(0.75 * (double)tab_alloc) + (1 << 20), h->cfg.lambda,
+                // a search holds at most 3/4 of each of the two tables
+                SCC_TRY(engine_reserve(&h->eb64, 8, (long long)(1.5 * (double)tab_alloc) + (1 << 20), h->cfg.lambda,
                                        h->mt, s));
                 if (fresh) {  // the kernel keeps both tables empty between batches
                     SCC_CUDA(cudaMemsetAsync(h->tab[0], 0xff, (size_t)tab_alloc * 8, s));

@@ -3,13 +3,15 @@
 // After the first SCC, every remaining prefix-doubling batch runs inside ONE
 // cooperative launch: batch sources (P_i n V'), the pair-table sizing of
 // Sec. 4.5, the forward and the backward multi-reachability searches (VGC +
-// hash bag, engine.cuh) and the labelling passes (labels.cuh), separated by
-// grid barriers. The host is involved only when a table or bag must grow: the
+// hash bag, engine.cuh; the two are independent and share the rounds of one
+// search) and the labelling passes (labels.cuh), separated by grid barriers. The host is involved only when a table or bag must grow: the
 // kernel then stops before labelling that batch and reports it; the host
 // enlarges the buffers and relaunches from that batch (nothing of the batch has
 // been committed, so rerunning it is exact).
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 
 #include "common.cuh"
@@ -85,7 +87,7 @@ __device__ __forceinline__ long long pow2ceil_d(long long x) {
 
 __global__ void __launch_bounds__(256, 2) bgss_kernel(BgssParams B) {
     __shared__ EngineSmem<PolPair> sm;
-    uint64_t* q = sm.q + (threadIdx.x >> 5) * PolPair::kQueue;
+    const LocalQueue<uint64_t> q = warp_queue(sm);
     WarpStats ws;
     EngineCtl* ctl = B.P.ctl;
     BgssCtl* bc = B.bc;
@@ -144,31 +146,38 @@ __global__ void __launch_bounds__(256, 2) bgss_kernel(BgssParams B) {
             break;
         }
         // (the tables are empty: the previous batch's last pass reset every entry)
-        // ---- forward (G) and backward (G^T) multi-reachability
+        // ---- forward (G) and backward (G^T) multi-reachability: independent
+        // searches, run in the same rounds (items carry their direction)
         long long pairs[2];
         bool grow = false;
-        for (int d = 0; d < 2 && !grow; ++d) {
+        {
             EngineParams<uint64_t> P = B.P;
-            P.off = d == 0 ? B.off : B.toff;
-            P.adj = d == 0 ? B.adj : B.tadj;
-            P.max_inserted = (long long)(0.75 * (double)cap[d]);
+            P.off = B.off;
+            P.adj = B.adj;
+            P.off2 = B.toff;
+            P.adj2 = B.tadj;
+            SearchCtl& sc = ctl->search[si % 3];
             PolPair pol;
             pol.label = B.label;
-            pol.tab.keys = B.tab[d];
-            pol.tab.mask = (unsigned long long)(cap[d] - 1);
-            SearchCtl& sc = ctl->search[si % 3];
-            pol.tab.overflow = &sc.overflow;
-            pol.ins = 0;
-            if (!engine_search<PolPair>(P, pol, InitPairs{B.sources}, k, nullptr, q, ws, g, si)) return;
+            for (int d = 0; d < 2; ++d) {
+                pol.keys[d] = B.tab[d];
+                pol.mask[d] = (unsigned long long)(cap[d] - 1);
+                pol.max_ins[d] = (long long)(0.75 * (double)cap[d]);
+            }
+            pol.overflow = &sc.overflow;
+            pol.ins0 = pol.ins1 = 0;
+            if (!engine_search<PolPair>(P, pol, InitPairs{B.sources, k}, 2 * (long long)k, nullptr, q, ws, g, si))
+                return;
             ++si;
             const int ovf = ld_volatile(&sc.overflow);
             const int err = ld_volatile(&ctl->err);
-            pairs[d] = (long long)ld_volatile(&sc.inserted);
+            pairs[0] = (long long)ld_volatile(&sc.inserted[0]);
+            pairs[1] = (long long)ld_volatile(&sc.inserted[1]);
             const int rounds = ld_volatile(&sc.rounds);
             if (err != 0 && err != SCC_ERR_CAPACITY) return;
             if (ovf || err == SCC_ERR_CAPACITY) {
                 grow = true;
-                need = 2 * cap[d];
+                need = 2 * max(cap[0], cap[1]);
             }
             if (gtid == 0) bc->rounds += rounds;
         }
@@ -282,6 +291,18 @@ int run_bgss_device(const BgssArgs& a, BgssResult* res, cudaStream_t st) {
     res->rounds = h.rounds;
     res->edges = h.edges;
     res->items = h.items;
+    static const bool trace = getenv("SCC_TRACE") != nullptr;
+    if (trace) {  // per-round timeline of the batches on stderr
+        fprintf(stderr, "[scc-trace] multi-reach batches %d..%d: %d batches, %d rounds, %.1f us in kernel\n", a.first,
+                h.batch, h.batches, h.rounds, 1000.0 * ms);
+        unsigned long long t = ec.t0;
+        const int nr = std::min(h.rounds, kTraceRounds);
+        for (int r = 0; r < nr; ++r) {
+            fprintf(stderr, "[scc-trace]   round %3d search %3d %s %9.1f us  items %lld\n", r, ec.t_dense[r] >> 1,
+                    (ec.t_dense[r] & 1) ? "dense " : "sparse", (ec.t_end[r] - t) / 1000.0, ec.t_items[r]);
+            t = ec.t_end[r];
+        }
+    }
     if (ec.err != 0 && ec.err != SCC_ERR_CAPACITY) return ec.err;
     return SCC_OK;
 }

@@ -78,12 +78,12 @@ struct RoundCtl {
 // resets entry (s + 1) % 3, last used by search s - 2, whose counters every block
 // read before search s - 1 began.
 struct SearchCtl {
-    int overflow;                 // pair table over its load or probe limit
-    int rounds;                   // rounds executed
-    unsigned long long inserted;  // newly visited items (pairs in pair mode)
+    int overflow;                    // pair table over its load or probe limit
+    int rounds;                      // rounds executed
+    unsigned long long inserted[2];  // newly visited pairs, per direction (pair mode)
 };
 
-constexpr int kTraceRounds = 64;
+constexpr int kTraceRounds = 1024;
 
 struct EngineCtl {
     GridBarrier bar;
@@ -93,8 +93,9 @@ struct EngineCtl {
     SearchCtl search[3];
     unsigned long long edges;  // arcs examined
     unsigned long long items;  // items expanded (adjacency rows read)
-    // trace of the first rounds of a standalone search: end time (globaltimer ns),
-    // items of the round's bag, dense flag
+    // trace of the first kTraceRounds rounds of a launch, indexed by the global
+    // round number: end time (globaltimer ns), items of the round's bag, and
+    // dense flag | search index << 1
     unsigned long long t0;
     unsigned long long t_end[kTraceRounds];
     long long t_items[kTraceRounds];
@@ -105,6 +106,10 @@ template <class Item>
 struct EngineParams {
     const int32_t* off;
     const int32_t* adj;
+    // second graph, for policies whose items carry a direction (kTwoGraphs):
+    // items of direction 1 follow off2/adj2 (the transpose)
+    const int32_t* off2;
+    const int32_t* adj2;
     int32_t n;
     int tau;      // VGC arc budget per warp task
     int hub_thr;  // out-degree above which an item is a hub
@@ -125,9 +130,20 @@ struct EngineParams {
     // initial items (standalone launches)
     const Item* init;
     long long ninit;
-    long long max_inserted;  // pair-mode load limit (0 = none)
     EngineCtl* ctl;
 };
+
+// adjacency arrays of an item's graph
+template <class Pol, class Item>
+__device__ __forceinline__ const int32_t* item_off(const EngineParams<Item>& P, const Pol& pol, Item it) {
+    if constexpr (Pol::kTwoGraphs) return pol.graph(it) ? P.off2 : P.off;
+    else return P.off;
+}
+template <class Pol, class Item>
+__device__ __forceinline__ const int32_t* item_adj(const EngineParams<Item>& P, const Pol& pol, Item it) {
+    if constexpr (Pol::kTwoGraphs) return pol.graph(it) ? P.adj2 : P.adj;
+    else return P.adj;
+}
 
 // ------------------------------------------------------------ chunk geometry --
 __device__ __forceinline__ long long chunk_begin(int lambda, int j) {
@@ -232,10 +248,27 @@ __device__ __forceinline__ int bag_push(const BagRef<Item>& b, SegState& st, boo
 }
 
 // ------------------------------------------------------------ warp tasks --
+// The local queue of a warp's search: a ring of kQueue items, each with its
+// adjacency range (first arc, out-degree), loaded while the item was visited,
+// and, for policies whose arc test needs a per-item value (the class label of a
+// pair's vertex), that value, inherited by the items it visits.
 template <class Pol>
-struct EngineSmem {
-    typename Pol::Item q[8 * Pol::kQueue];  // up to 8 warps per block share this
+struct EngineSmem {  // up to 8 warps per block
+    typename Pol::Item qi[8 * Pol::kQueue];
+    int2 qr[8 * Pol::kQueue];
+    int32_t qc[Pol::kCtxInQueue ? 8 * Pol::kQueue : 1];
 };
+template <class Item>
+struct LocalQueue {
+    Item* it;
+    int2* rg;
+    int32_t* cx;
+};
+template <class Pol>
+__device__ __forceinline__ LocalQueue<typename Pol::Item> warp_queue(EngineSmem<Pol>& sm) {
+    const int w = threadIdx.x >> 5;
+    return {sm.qi + w * Pol::kQueue, sm.qr + w * Pol::kQueue, Pol::kCtxInQueue ? sm.qc + w * Pol::kQueue : sm.qc};
+}
 
 // Per-warp accumulators (folded into the control block at the end).
 struct WarpStats {
@@ -247,7 +280,7 @@ struct WarpStats {
 template <class Pol>
 __device__ __forceinline__ void expand_batch(const EngineParams<typename Pol::Item>& P, Pol& pol,
                                              const BagRef<typename Pol::Item>& out, SegState& st, uint32_t wid,
-                                             uint32_t round, typename Pol::Item* q, uint32_t& qh, uint32_t& qt,
+                                             uint32_t round, const LocalQueue<typename Pol::Item>& q, uint32_t& qh, uint32_t& qt,
                                              int& t, bool seeds_phase, int max_take, int hub_thr, WarpStats& ws,
                                              unsigned long long& pushed) {
     using Item = typename Pol::Item;
@@ -257,11 +290,14 @@ __device__ __forceinline__ void expand_batch(const EngineParams<typename Pol::It
     if (seeds_phase && avail > max_take) avail = max_take;
     Item it = Sent<Item>::empty;
     int beg = 0, deg = 0;
+    uint64_t qctx = 0;
     if (lane < avail) {
-        it = q[(qh + lane) & QM];
-        const int u = pol.vertex(it);
-        beg = __ldg(&P.off[u]);
-        deg = __ldg(&P.off[u + 1]) - beg;
+        const uint32_t k = (qh + lane) & QM;
+        it = q.it[k];
+        const int2 r = q.rg[k];
+        beg = r.x;
+        deg = r.y;
+        if constexpr (Pol::kCtxInQueue) qctx = (uint64_t)(uint32_t)q.cx[k];
     }
     // items past the seeds with more than hub_thr arcs go back to the bag
     bool hub = !seeds_phase && lane < avail && deg > hub_thr;
@@ -281,7 +317,8 @@ __device__ __forceinline__ void expand_batch(const EngineParams<typename Pol::It
     }
     qh += take;
     pushed += bag_push<Item>(out, st, hub, it, wid, round);
-    const uint64_t ctx = (lane < take && !hub) ? pol.ctx(it) : 0;
+    uint64_t ctx = qctx;
+    if constexpr (!Pol::kCtxInQueue) ctx = (lane < take && !hub) ? pol.ctx(it) : 0;
     const int total = __shfl_sync(kFull, pre, 31);
     const int excl = pre - d;
     // four groups of 32 arcs per step: the adjacency loads and the visit tests of
@@ -305,7 +342,17 @@ __device__ __forceinline__ void expand_batch(const EngineParams<typename Pol::It
             const int jbeg = __shfl_sync(kFull, beg, j);
             jit[u] = shfl_any(it, j);
             jctx[u] = shfl_any(ctx, j);
-            w[u] = e < total ? __ldg(&P.adj[jbeg + (e - jexcl)]) : -1;
+            w[u] = e < total ? __ldg(&item_adj(P, pol, jit[u])[jbeg + (e - jexcl)]) : -1;
+        }
+        // the adjacency range of every target is loaded together with its visit
+        // test (not after it), so a newly visited item enters the queue ready to
+        // expand: one dependent memory access less per step of the search
+        int rb[U], re[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int32_t* O = item_off(P, pol, jit[u]);  // a child stays in its parent's graph
+            rb[u] = w[u] >= 0 ? __ldg(&O[w[u]]) : 0;
+            re[u] = w[u] >= 0 ? __ldg(&O[w[u] + 1]) : 0;
         }
         bool nw[U];
         Item child[U];
@@ -323,7 +370,12 @@ __device__ __forceinline__ void expand_batch(const EngineParams<typename Pol::It
                 const int rank = __popc(m & lanemask_lt());
                 const int room = (int)(Pol::kQueue - (qt - qh));
                 const bool toq = nw[u] && rank < room;
-                if (toq) q[(qt + rank) & QM] = child[u];
+                if (toq) {
+                    const uint32_t k = (qt + rank) & QM;
+                    q.it[k] = child[u];
+                    q.rg[k] = make_int2(rb[u], re[u] - rb[u]);
+                    if constexpr (Pol::kCtxInQueue) q.cx[k] = (int32_t)(uint32_t)jctx[u];
+                }
                 const int nq = cnt < room ? cnt : room;
                 pushed += bag_push<Item>(out, st, nw[u] && !toq, child[u], wid, round);
                 qt += nq;
@@ -348,19 +400,12 @@ struct DenseParams {
     int frac_inv;         // 0 = never dense
 };
 
-// The initial items of a search: either an explicit list or the pairs (s, s)
-// of a source list.
+// The initial items of a search: an explicit list (or, for pair searches,
+// InitPairs below).
 template <class Item>
 struct InitList {
     const Item* items;
     __device__ __forceinline__ Item operator()(long long i) const { return items[i]; }
-};
-struct InitPairs {
-    const int32_t* sources;
-    __device__ __forceinline__ uint64_t operator()(long long i) const {
-        const uint32_t s = (uint32_t)sources[i];
-        return ((uint64_t)s << 32) | s;
-    }
 };
 
 // Set an item with more than hub_thr arcs aside for the next round, cut into
@@ -398,7 +443,7 @@ __device__ __forceinline__ bool reserve_hub(const EngineParams<Item>& P, RoundCt
 // barrier, so this search's control entry is final.
 template <class Pol, class Init>
 __device__ bool engine_search(const EngineParams<typename Pol::Item>& P, Pol& pol, Init init, long long ninit,
-                              const DenseParams* dp, typename Pol::Item* q, WarpStats& ws, uint32_t& g,
+                              const DenseParams* dp, const LocalQueue<typename Pol::Item>& q, WarpStats& ws, uint32_t& g,
                               uint32_t si) {
     using Item = typename Pol::Item;
     constexpr uint32_t QM = Pol::kQueue - 1;
@@ -431,7 +476,8 @@ __device__ bool engine_search(const EngineParams<typename Pol::Item>& P, Pol& po
                 SearchCtl& other = ctl->search[(si + 1) % 3];
                 other.overflow = 0;
                 other.rounds = 0;
-                other.inserted = 0;
+                other.inserted[0] = 0;
+                other.inserted[1] = 0;
             }
         }
         const BagRef<Item> out{P.slots[par], P.nslots, P.lambda, P.sigma, &cur.bag, &ctl->err, &ctl->max_chunk};
@@ -514,7 +560,7 @@ __device__ bool engine_search(const EngineParams<typename Pol::Item>& P, Pol& po
                 }
             }
         } else {
-            const bool stop = P.max_inserted > 0 && ld_volatile(&sc.overflow) != 0;
+            const bool stop = Pol::kCountInserts && ld_volatile(&sc.overflow) != 0;
             // ---- phase A: last round's hubs, cut into segments shared by all warps
             if (i > 0) {
                 const long long nseg = min(ld_volatile(&prev.hubseg), P.segmap_cap);
@@ -530,7 +576,7 @@ __device__ bool engine_search(const EngineParams<typename Pol::Item>& P, Pol& po
                         bool nw = false;
                         Item child = Sent<Item>::empty;
                         if (e0 + lane < len) {
-                            const int w = __ldg(&P.adj[b0 + e0 + lane]);
+                            const int w = __ldg(&item_adj(P, pol, hit)[b0 + e0 + lane]);
                             nw = pol.visit(hit, hctx, w, child);
                         }
                         pushed += bag_push<Item>(out, st, nw, child, wid, gr);
@@ -549,7 +595,6 @@ __device__ bool engine_search(const EngineParams<typename Pol::Item>& P, Pol& po
             while (G > 1 && (long long)G * nwarps * 2 > in_cnt) G >>= 1;
             const int hub_thr = fr_items < (long long)nwarps * 8 ? min(P.hub_thr, 64) : P.hub_thr;
             const long long ntasks = (in_cnt + G - 1) / G;
-            long long ins = 0;
             for (;;) {
                 long long tk = 0;
                 if (lane == 0) tk = (long long)atomicAdd((unsigned long long*)&cur.work, 1ull);
@@ -561,11 +606,8 @@ __device__ bool engine_search(const EngineParams<typename Pol::Item>& P, Pol& po
                 if (lane >= G || idx >= in_cnt) {
                     // not part of this task
                 } else if (i == 0) {
-                    {
-                        it = init(idx);
-                        has = pol.seed(it);
-                        ins += has;
-                    }
+                    it = init(idx);
+                    has = pol.seed(it);
                 } else {
                     it = in_slots[idx];
                     if (it != Sent<Item>::empty) {
@@ -573,15 +615,24 @@ __device__ bool engine_search(const EngineParams<typename Pol::Item>& P, Pol& po
                         has = it != Sent<Item>::claimed;
                     }
                 }
+                int b0 = 0, dg = 0;
+                int32_t cx0 = 0;
                 if (has) {
                     const int v = pol.vertex(it);
-                    const int b0 = __ldg(&P.off[v]);
-                    const int dg = __ldg(&P.off[v + 1]) - b0;
+                    const int32_t* O = item_off(P, pol, it);
+                    b0 = __ldg(&O[v]);
+                    dg = __ldg(&O[v + 1]) - b0;
+                    if constexpr (Pol::kCtxInQueue) cx0 = pol.load_ctx(it);
                     if (dg > hub_thr && reserve_hub(P, cur, par, it, b0, dg)) has = false;
                 }
                 const uint32_t m = __ballot_sync(kFull, has);
                 if (m == 0) continue;
-                if (has) q[__popc(m & lanemask_lt())] = it;
+                if (has) {
+                    const int k = __popc(m & lanemask_lt());
+                    q.it[k] = it;
+                    q.rg[k] = make_int2(b0, dg);
+                    if constexpr (Pol::kCtxInQueue) q.cx[k] = cx0;
+                }
                 __syncwarp();
                 uint32_t qh = 0, qt = (uint32_t)__popc(m);
                 int t = 0;
@@ -591,38 +642,25 @@ __device__ bool engine_search(const EngineParams<typename Pol::Item>& P, Pol& po
                 // budget spent: flush what is left in the local queue
                 while (qt != qh) {
                     const int nrem = (int)min(32u, qt - qh);
-                    const Item x = lane < nrem ? q[(qh + lane) & QM] : Sent<Item>::empty;
+                    const Item x = lane < nrem ? q.it[(qh + lane) & QM] : Sent<Item>::empty;
                     qh += nrem;
                     pushed += bag_push<Item>(out, st, lane < nrem, x, wid, gr);
                 }
                 __syncwarp();
-                if constexpr (Pol::kCountInserts) {
-                    const long long c = pol.take_inserted();
-                    if (c && lane == 0) {
-                        const unsigned long long tot = atomicAdd(&sc.inserted, (unsigned long long)c) + c;
-                        if (P.max_inserted > 0 && (long long)tot > P.max_inserted) atomicExch(&sc.overflow, 1);
-                    }
-                }
+                if constexpr (Pol::kCountInserts) pol.flush(sc);
             }
-            if constexpr (Pol::kCountInserts) {
-                for (int dd = 16; dd >= 1; dd >>= 1) ins += __shfl_xor_sync(kFull, ins, dd);
-                const long long c = pol.take_inserted() + ins;
-                if (c && lane == 0) {
-                    const unsigned long long tot = atomicAdd(&sc.inserted, (unsigned long long)c) + c;
-                    if (P.max_inserted > 0 && (long long)tot > P.max_inserted) atomicExch(&sc.overflow, 1);
-                }
-            }
+            if constexpr (Pol::kCountInserts) pol.flush(sc);
         }
         if (lane == 0 && pushed) atomicAdd((unsigned long long*)&cur.items, pushed);
         if (!grid_sync(&ctl->bar, &ctl->err)) return false;
-        if (si == 0 && i < (uint32_t)kTraceRounds && blockIdx.x == 0 && threadIdx.x == 0) {
-            ctl->t_end[i] = globaltimer_ns();
-            ctl->t_items[i] = ld_volatile(&cur.items);
-            ctl->t_dense[i] = dense;
+        if (gr < (uint32_t)kTraceRounds && blockIdx.x == 0 && threadIdx.x == 0) {
+            ctl->t_end[gr] = globaltimer_ns();
+            ctl->t_items[gr] = ld_volatile(&cur.items);
+            ctl->t_dense[gr] = (int)dense | (int)(si << 1);
         }
         prev_dense = dense;
         if (ld_volatile(&ctl->err) != 0) break;
-        if (P.max_inserted > 0 && ld_volatile(&sc.overflow) != 0) break;
+        if (Pol::kCountInserts && ld_volatile(&sc.overflow) != 0) break;
         if (ld_volatile(&cur.items) == 0 && ld_volatile(&cur.nhub) == 0) break;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) sc.rounds = (int)i + 1;
@@ -645,7 +683,7 @@ template <class Pol>
 __global__ void __launch_bounds__(256, 3) engine_kernel(EngineParams<typename Pol::Item> P, Pol pol_in, DenseParams dp) {
     Pol pol = pol_in;
     __shared__ EngineSmem<Pol> sm;
-    typename Pol::Item* q = sm.q + (threadIdx.x >> 5) * Pol::kQueue;
+    const LocalQueue<typename Pol::Item> q = warp_queue(sm);
     WarpStats ws;
     uint32_t g = 0;
     const bool ok = engine_search<Pol>(P, pol, InitList<typename Pol::Item>{P.init}, P.ninit,
@@ -661,9 +699,11 @@ __global__ void __launch_bounds__(256, 3) engine_kernel(EngineParams<typename Po
 // is one bit (Alg. 3 "CAS(visit[u], false, true)").
 struct PolSingle {
     using Item = uint32_t;
-    static constexpr int kQueue = 512;
+    static constexpr int kQueue = 256;
     static constexpr bool kCountInserts = false;
     static constexpr bool kDense = true;
+    static constexpr bool kCtxInQueue = false;
+    static constexpr bool kTwoGraphs = false;
     static constexpr const char* kName = "single-reach";
     uint32_t* bits;
     __device__ __forceinline__ int vertex(Item it) const { return (int)it; }
@@ -678,7 +718,6 @@ struct PolSingle {
         child = (Item)w;
         return (atomicOr(&bits[w >> 5], b) & b) == 0;
     }
-    __device__ __forceinline__ long long take_inserted() { return 0; }
 };
 
 // Pair table (Sec. 4.3 phase-concurrent hash table of reachability pairs):
@@ -688,23 +727,25 @@ struct PairTable {
     unsigned long long mask;  // capacity - 1 (capacity a power of two)
     int* overflow;
     __device__ __forceinline__ static unsigned long long hash(unsigned long long k) { return mix64(k); }
-    __device__ __forceinline__ bool insert(unsigned long long key) const {
+    __device__ __forceinline__ bool insert(unsigned long long key) const { return insert_into(keys, mask, overflow, key); }
+    // the CAS itself is the probe (no read before it): one memory round trip per
+    // slot whether the slot is empty, holds the key or another one
+    __device__ __forceinline__ static bool insert_into(unsigned long long* keys, unsigned long long mask, int* overflow,
+                                                       unsigned long long key) {
         unsigned long long h = hash(key) & mask;
         for (int i = 0; i < kTableProbe; ++i) {
-            unsigned long long cur = ld_volatile(&keys[h]);
-            if (cur == key) return false;
-            if (cur == ~0ull) {
-                unsigned long long prev = atomicCAS(&keys[h], ~0ull, key);
-                if (prev == ~0ull) return true;
-                if (prev == key) return false;
-            }
+            const unsigned long long prev = atomicCAS(&keys[h], ~0ull, key);
+            if (prev == ~0ull) return true;
+            if (prev == key) return false;
             h = (h + 1) & mask;
         }
         atomicExch(overflow, 1);
         return false;
     }
-    __device__ __forceinline__ bool contains(unsigned long long key) const {
-        unsigned long long h = hash(key) & mask;
+    __device__ __forceinline__ bool contains(unsigned long long key) const { return contains_from(hash(key) & mask, key); }
+    // lookup that starts probing at slot h (for callers that read the first
+    // slot themselves)
+    __device__ __forceinline__ bool contains_from(unsigned long long h, unsigned long long key) const {
         for (unsigned long long i = 0; i <= mask; ++i) {
             unsigned long long cur = keys[h];
             if (cur == key) return true;
@@ -715,33 +756,79 @@ struct PairTable {
     }
 };
 
-// Multi-reachability: pair items (v, s); an arc (u, w) is followed only when
-// label[w] == label[u] (Alg. 1: MultiReach skips (u, v) with L(u) != L(v);
-// finished vertices carry kDone < 0 and never match an active class).
+// Multi-reachability: pair items (v, s) plus a direction bit (bit 63). Direction
+// 0 follows G and fills T_out with the pairs s ~> v, direction 1 follows G^T
+// and fills T_in with the pairs v ~> s; the two searches of a batch are
+// independent, so they share the rounds of one search. An arc (u, w) is followed
+// only when label[w] == label[u] (Alg. 1: MultiReach skips (u, v) with
+// L(u) != L(v); finished vertices carry kDone < 0 and never match an active
+// class). Table keys are v << 32 | s without the direction bit; the sentinels
+// (s with bit 31 set) are never items.
 struct PolPair {
     using Item = uint64_t;
     static constexpr int kQueue = 256;
     static constexpr bool kCountInserts = true;
     static constexpr bool kDense = false;
+    static constexpr bool kCtxInQueue = true;
+    static constexpr bool kTwoGraphs = true;
     static constexpr const char* kName = "multi-reach";
+    static constexpr uint64_t kDir = 1ull << 63;
     const int32_t* label;
-    PairTable tab;
-    long long ins;
-    __device__ __forceinline__ int vertex(Item it) const { return (int)(it >> 32); }
-    __device__ __forceinline__ uint64_t ctx(Item it) const { return (uint64_t)(uint32_t)__ldg(&label[it >> 32]); }
-    __device__ __forceinline__ bool seed(Item it) const { return tab.insert(it); }
-    __device__ __forceinline__ bool visit(Item parent, uint64_t c, int w, Item& child) {
-        if (__ldg(&label[w]) != (int32_t)(uint32_t)c) return false;
-        child = ((uint64_t)(uint32_t)w << 32) | (parent & 0xffffffffull);
-        bool ok = tab.insert(child);
-        ins += ok;
+    unsigned long long* keys[2];  // T_out, T_in
+    unsigned long long mask[2];   // capacities - 1 (powers of two)
+    long long max_ins[2];         // load limits (0 = none): over them the search stops
+    int* overflow;                // set on a load or probe-limit overflow
+    long long ins0, ins1;         // this lane's new pairs since the last flush
+    __device__ __forceinline__ int vertex(Item it) const { return (int)((it >> 32) & 0x7fffffffu); }
+    __device__ __forceinline__ int graph(Item it) const { return (int)(it >> 63); }
+    // labels change between the batches of one launch (the labelling passes of
+    // the device-side batch loop), so they are read with coherent loads, never
+    // through the read-only data path
+    __device__ __forceinline__ uint64_t ctx(Item it) const { return (uint64_t)(uint32_t)label[vertex(it)]; }
+    __device__ __forceinline__ int32_t load_ctx(Item it) const { return label[vertex(it)]; }
+    __device__ __forceinline__ bool add(Item it) {
+        const int d = graph(it);
+        const bool ok = PairTable::insert_into(d ? keys[1] : keys[0], d ? mask[1] : mask[0], overflow, it & ~kDir);
+        ins0 += ok && !d;
+        ins1 += ok && d;
         return ok;
     }
-    __device__ __forceinline__ long long take_inserted() {
-        long long c = ins;
-        for (int d = 16; d >= 1; d >>= 1) c += __shfl_xor_sync(kFull, c, d);
-        ins = 0;
-        return c;
+    __device__ __forceinline__ bool seed(Item it) { return add(it); }
+    __device__ __forceinline__ bool visit(Item parent, uint64_t c, int w, Item& child) {
+        if (label[w] != (int32_t)(uint32_t)c) return false;
+        child = (parent & kDir) | ((uint64_t)(uint32_t)w << 32) | (parent & 0xffffffffull);
+        return add(child);
+    }
+    // warp-collective: add the warp's new pairs to the search's counters and
+    // flag an overflow past a load limit
+    __device__ __forceinline__ void flush(SearchCtl& sc) {
+        long long c0 = ins0, c1 = ins1;
+        for (int d = 16; d >= 1; d >>= 1) {
+            c0 += __shfl_xor_sync(kFull, c0, d);
+            c1 += __shfl_xor_sync(kFull, c1, d);
+        }
+        ins0 = ins1 = 0;
+        if (lane_id() != 0) return;
+        if (c0) {
+            const unsigned long long t = atomicAdd(&sc.inserted[0], (unsigned long long)c0) + c0;
+            if (max_ins[0] > 0 && (long long)t > max_ins[0]) atomicExch(&sc.overflow, 1);
+        }
+        if (c1) {
+            const unsigned long long t = atomicAdd(&sc.inserted[1], (unsigned long long)c1) + c1;
+            if (max_ins[1] > 0 && (long long)t > max_ins[1]) atomicExch(&sc.overflow, 1);
+        }
+    }
+};
+
+// Initial items of a pair search: (s, s) for every source, in direction 0
+// (items [0, k)) and, with `both`, in direction 1 as well (items [k, 2k)).
+struct InitPairs {
+    const int32_t* sources;
+    long long k;
+    __device__ __forceinline__ uint64_t operator()(long long i) const {
+        const bool d = i >= k;
+        const uint32_t s = (uint32_t)sources[d ? i - k : i];
+        return (d ? PolPair::kDir : 0ull) | ((uint64_t)s << 32) | s;
     }
 };
 
@@ -750,9 +837,11 @@ struct PolPair {
 // of sources reaching v.
 struct PolMask {
     using Item = uint32_t;
-    static constexpr int kQueue = 512;
+    static constexpr int kQueue = 256;
     static constexpr bool kCountInserts = false;
     static constexpr bool kDense = false;
+    static constexpr bool kCtxInQueue = false;
+    static constexpr bool kTwoGraphs = false;
     static constexpr const char* kName = "mask-reach";
     unsigned long long* mask;
     __device__ __forceinline__ int vertex(Item it) const { return (int)it; }
@@ -764,7 +853,6 @@ struct PolMask {
         child = (Item)w;
         return (mu & ~old) != 0;
     }
-    __device__ __forceinline__ long long take_inserted() { return 0; }
 };
 
 }  // namespace scc

@@ -120,11 +120,6 @@ int launch_label_first(const uint32_t* bf, const uint32_t* bb, int32_t n, int32_
                        unsigned long long* ndone, cudaStream_t s_);
 
 // Labelling after a multi-reachability round (Alg. 1; Sec. 4.4).
-int launch_label_pairs(const unsigned long long* tf, int64_t capf, const unsigned long long* tb, int64_t capb,
-                       uint32_t round_tag, unsigned long long* fmax, unsigned long long* bmax,
-                       unsigned long long* hit, int32_t* label, int32_t* rep, unsigned long long* ndone,
-                       cudaStream_t s);
-
 // labels_out[v] = min{u : rep[u] == rep[v]} (canonical minimum).
 int launch_canonicalize(const int32_t* rep, int32_t n, int32_t* minid, int32_t* labels_out, int* bad,
                         cudaStream_t s);

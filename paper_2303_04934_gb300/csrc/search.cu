@@ -68,7 +68,7 @@ int launch_engine(EngineParams<typename Pol::Item>& P, Pol& pol, const EngineOpt
     out->rounds = h.search[0].rounds;
     out->max_chunk = h.max_chunk;
     out->edges = h.edges;
-    out->inserted = h.search[0].inserted;
+    out->inserted = h.search[0].inserted[0] + h.search[0].inserted[1];
     static const bool trace = getenv("SCC_TRACE") != nullptr;
     if (trace) {  // per-round timeline of this search on stderr
         const int nr = std::min(h.search[0].rounds, kTraceRounds);
@@ -76,7 +76,7 @@ int launch_engine(EngineParams<typename Pol::Item>& P, Pol& pol, const EngineOpt
                 1000.0 * ms);
         unsigned long long t = h.t0;
         for (int r = 0; r < nr; ++r) {
-            fprintf(stderr, "[scc-trace]   round %2d %s %9.1f us  items %lld\n", r, h.t_dense[r] ? "dense " : "sparse",
+            fprintf(stderr, "[scc-trace]   round %2d %s %9.1f us  items %lld\n", r, (h.t_dense[r] & 1) ? "dense " : "sparse",
                     (h.t_end[r] - t) / 1000.0, h.t_items[r]);
             t = h.t_end[r];
         }
@@ -207,13 +207,13 @@ int run_pairs(const int32_t* off, const int32_t* adj, int32_t n, const int32_t* 
     SCC_LAUNCH();
     P.init = init;
     P.ninit = k;
-    P.max_inserted = max_inserted;
-    PolPair pol;
+    PolPair pol;  // every item in direction 0: one table, graph (off, adj)
     pol.label = label;
-    pol.tab.keys = table;
-    pol.tab.mask = (unsigned long long)(cap - 1);
-    pol.tab.overflow = &b->ctl->search[0].overflow;  // a standalone launch is search 0
-    pol.ins = 0;
+    pol.keys[0] = pol.keys[1] = table;
+    pol.mask[0] = pol.mask[1] = (unsigned long long)(cap - 1);
+    pol.max_ins[0] = pol.max_ins[1] = max_inserted;
+    pol.overflow = &b->ctl->search[0].overflow;  // a standalone launch is search 0
+    pol.ins0 = pol.ins1 = 0;
     int rc = launch_engine(P, pol, o, out, st);
     if (rc != SCC_OK || out->err || out->overflow) {
         int r2 = engine_reset_slots(b, st);

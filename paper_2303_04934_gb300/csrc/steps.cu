@@ -12,7 +12,6 @@
 #include "common.cuh"
 #include "engine.cuh"
 #include "internal.h"
-#include "labels.cuh"
 
 namespace scc {
 
@@ -294,23 +293,6 @@ __global__ void k_label_first(const uint32_t* __restrict__ bf, const uint32_t* _
     if (lane_id() == 0 && c) atomicAdd(ndone, c);
 }
 
-__global__ void k_label_scan(const unsigned long long* __restrict__ tf, int64_t capf, PairTable tb,
-                             unsigned long long tag, unsigned long long* fmax, unsigned long long* bmax,
-                             unsigned long long* hit) {
-    const long long i0 = (long long)blockIdx.x * blockDim.x + threadIdx.x, st = (long long)gridDim.x * blockDim.x;
-    label_scan(i0, st, tf, capf, tb, tag, fmax, bmax, hit);
-}
-__global__ void k_label_finalize(unsigned long long* __restrict__ tf, int64_t capf,
-                                 unsigned long long* __restrict__ tb, int64_t capb, unsigned long long tag,
-                                 const unsigned long long* fmax, const unsigned long long* bmax,
-                                 const unsigned long long* hit, int32_t* label, int32_t* rep,
-                                 unsigned long long* ndone) {
-    const long long i0 = (long long)blockIdx.x * blockDim.x + threadIdx.x, st = (long long)gridDim.x * blockDim.x;
-    unsigned long long c = label_finalize(i0, st, tf, capf, tb, capb, tag, fmax, bmax, hit, label, rep, false);
-    for (int d = 16; d >= 1; d >>= 1) c += __shfl_xor_sync(kFull, c, d);
-    if (lane_id() == 0 && c) atomicAdd(ndone, c);
-}
-
 // ---------------------------------------------------------- canonicalise --
 __global__ void k_fill_i32(int32_t* p, int64_t n, int32_t v) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
@@ -529,22 +511,6 @@ int launch_label_first(const uint32_t* bf, const uint32_t* bb, int32_t n, int32_
     if (n == 0) return SCC_OK;
     // the class of the pivot is 0 in the first round (every untrimmed vertex)
     k_label_first<<<grid_for(n, kBlk), kBlk, 0, st>>>(bf, bb, n, s, 0, label, rep, ndone);
-    SCC_LAUNCH();
-    return SCC_OK;
-}
-
-int launch_label_pairs(const unsigned long long* tf, int64_t capf, const unsigned long long* tb, int64_t capb,
-                       uint32_t round_tag, unsigned long long* fmax, unsigned long long* bmax,
-                       unsigned long long* hit, int32_t* label, int32_t* rep, unsigned long long* ndone,
-                       cudaStream_t s) {
-    unsigned long long tag = (unsigned long long)round_tag << 32;
-    PairTable tbt{const_cast<unsigned long long*>(tb), (unsigned long long)(capb - 1), nullptr};
-    k_label_scan<<<grid_for(capf + capb, kBlk), kBlk, 0, s>>>(tf, capf, tbt, tag, fmax, bmax, hit);
-    SCC_LAUNCH();
-    k_label_finalize<<<grid_for(capf + capb, kBlk), kBlk, 0, s>>>(const_cast<unsigned long long*>(tf), capf,
-                                                                    const_cast<unsigned long long*>(tb), capb, tag,
-                                                                    fmax, bmax, hit, label,
-                                                                    rep, ndone);
     SCC_LAUNCH();
     return SCC_OK;
 }
