@@ -187,6 +187,11 @@ typedef struct scc_stats {
     /* graph construction (scc_graph_create of this handle): total and the three
        passes of the transposed-CSR build, CUDA events on the creating stream */
     double ms_create, ms_transpose_hist, ms_transpose_part, ms_transpose_rows;
+    /* trimming inside the classes left by the first SCC: vertices with no arc
+       from or no arc to a vertex of their own class are singleton SCCs */
+    int32_t n_class_trimmed;   /* vertices finished this way */
+    int32_t class_trim_passes; /* passes run */
+    double ms_class_trim;
 } scc_stats;
 
 SCC_API int scc_get_stats(scc_handle h, scc_stats* out);

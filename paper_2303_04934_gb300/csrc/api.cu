@@ -213,6 +213,9 @@ int reserve_table(scc_graph* h, int d, int64_t cap, cudaStream_t s) {
     return SCC_OK;
 }
 
+// at most this many class-trimming passes after the first SCC
+constexpr int kClassTrimPasses = 4;
+
 struct EvTimer {
     cudaEvent_t a = nullptr, b = nullptr;
     cudaStream_t s;
@@ -536,6 +539,25 @@ static int scc_run_impl(scc_graph* h, int32_t* labels_out, cudaStream_t s) {
         st.ms_first_scc = t.stop();
         st.first_scc_size = (int32_t)hc[1];
         st.search_rounds += r0.rounds + r1.rounds;
+
+        // ---- trimming inside the three classes the first SCC leaves: passes
+        // while a pass still finishes at least 1/32 of the active vertices
+        t.start();
+        {
+            unsigned long long before = hc[1];
+            for (int pass = 0; pass < kClassTrimPasses && (int64_t)before < N; ++pass) {
+                SCC_TRY(launch_class_trim(h->act, N, h->off, h->adj, h->toff, h->tadj, h->label, h->rep,
+                                          &h->counters[1], s));
+                SCC_CUDA(cudaMemcpyAsync(hc, h->counters, sizeof(hc), cudaMemcpyDeviceToHost, s));
+                SCC_CUDA(cudaStreamSynchronize(s));
+                st.class_trim_passes++;
+                const unsigned long long got = hc[1] - before;
+                before = hc[1];
+                if ((int64_t)got * 32 < N - (int64_t)hc[1]) break;
+            }
+            st.n_class_trimmed = (int32_t)(hc[1] - (unsigned long long)st.first_scc_size);
+        }
+        st.ms_class_trim = t.stop();
         for (const EngineRun* r : {&r0, &r1}) {
             st.engine_launches++;
             st.ms_engine += r->ms;

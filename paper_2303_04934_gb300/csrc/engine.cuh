@@ -518,44 +518,71 @@ __device__ bool engine_search(const EngineParams<typename Pol::Item>& P, Pol& po
                 if (!grid_sync(&ctl->bar, &ctl->err)) return false;
                 const long long nw = ((long long)P.n + 31) / 32;
                 // each warp takes 32 consecutive words at a time (one coalesced
-                // load) and works only on words with unvisited vertices
+                // load) and works only on words with unvisited vertices, kDW of
+                // them together: lane l scans the in-arcs of vertex l of each of
+                // the kDW words, two arcs per vertex per step, so up to 2 * kDW
+                // independent loads per lane are in flight
+                constexpr int kDW = 4;
                 for (long long w0 = (long long)wid * 32; w0 < nw; w0 += (long long)nwarps * 32) {
                     const uint32_t mine = w0 + lane < nw ? ld_volatile(&pol.bits[w0 + lane]) : ~0u;
                     uint32_t todo = __ballot_sync(kFull, mine != ~0u);
                     while (todo) {
-                        const int jw = __ffs(todo) - 1;
-                        todo &= todo - 1;
-                        const long long w = w0 + jw;
-                        const uint32_t word = __shfl_sync(kFull, mine, jw);
-                        const long long v = w * 32 + lane;
-                        bool found = false;
+                        int jw[kDW];
+                        uint32_t word[kDW];
+                        int e[kDW], e1[kDW];
+                        bool found[kDW];
+#pragma unroll
+                        for (int k = 0; k < kDW; ++k) {
+                            jw[k] = todo ? __ffs(todo) - 1 : -1;  // warp-uniform
+                            if (todo) todo &= todo - 1;
+                            word[k] = jw[k] >= 0 ? __shfl_sync(kFull, mine, jw[k]) : ~0u;
+                            const long long v = (w0 + (jw[k] >= 0 ? jw[k] : 0)) * 32 + lane;
+                            const bool act = jw[k] >= 0 && v < P.n && !((word[k] >> lane) & 1u);
+                            e[k] = act ? __ldg(&dp->roff[v]) : 0;
+                            e1[k] = act ? __ldg(&dp->roff[v + 1]) : 0;
+                            found[k] = false;
+                        }
                         unsigned long long scanned = 0;
-                        if (v < P.n && !((word >> lane) & 1u)) {
-                            const int e0 = __ldg(&dp->roff[v]), e1 = __ldg(&dp->roff[v + 1]);
-                            // in-arcs four at a time: independent loads, early exit per batch
-                            for (int e = e0; e < e1 && !found; e += 4) {
-                                int u[4];
-                                uint32_t fw[4];
+                        for (;;) {
+                            int u[kDW][2];
+                            bool any = false;
 #pragma unroll
-                                for (int k = 0; k < 4; ++k) u[k] = e + k < e1 ? __ldg(&dp->radj[e + k]) : -1;
+                            for (int k = 0; k < kDW; ++k) {
 #pragma unroll
-                                for (int k = 0; k < 4; ++k) fw[k] = u[k] >= 0 ? ld_volatile(&fb[u[k] >> 5]) : 0u;
+                                for (int a = 0; a < 2; ++a) {
+                                    const bool go = !found[k] && e[k] + a < e1[k];
+                                    u[k][a] = go ? __ldg(&dp->radj[e[k] + a]) : -1;
+                                    any |= go;
+                                }
+                            }
+                            if (!any) break;
+                            uint32_t fw[kDW][2];
 #pragma unroll
-                                for (int k = 0; k < 4; ++k)
-                                    if (!found && u[k] >= 0) {
+                            for (int k = 0; k < kDW; ++k)
+#pragma unroll
+                                for (int a = 0; a < 2; ++a) fw[k][a] = u[k][a] >= 0 ? ld_volatile(&fb[u[k][a] >> 5]) : 0u;
+#pragma unroll
+                            for (int k = 0; k < kDW; ++k) {
+#pragma unroll
+                                for (int a = 0; a < 2; ++a)
+                                    if (!found[k] && u[k][a] >= 0) {
                                         ++scanned;
-                                        found = (fw[k] >> (u[k] & 31)) & 1u;
+                                        found[k] = (fw[k][a] >> (u[k][a] & 31)) & 1u;
                                     }
+                                e[k] += 2;
                             }
                         }
-                        const uint32_t m = __ballot_sync(kFull, found);
-                        if (lane == 0 && m) pol.bits[w] = word | m;  // this warp owns word w in this round
                         for (int dd = 16; dd >= 1; dd >>= 1) scanned += __shfl_xor_sync(kFull, scanned, dd);
-                        if (lane == 0) {
-                            ws.edges += scanned;
-                            ws.items += __popc(m);
+                        if (lane == 0) ws.edges += scanned;
+#pragma unroll
+                        for (int k = 0; k < kDW; ++k) {
+                            if (jw[k] < 0) break;  // warp-uniform
+                            const long long w = w0 + jw[k];
+                            const uint32_t m = __ballot_sync(kFull, found[k]);
+                            if (lane == 0 && m) pol.bits[w] = word[k] | m;  // this warp owns word w in this round
+                            if (lane == 0) ws.items += __popc(m);
+                            pushed += bag_push<Item>(out, st, found[k], (Item)(w * 32 + lane), wid, gr);
                         }
-                        pushed += bag_push<Item>(out, st, found, (Item)v, wid, gr);
                     }
                 }
             }

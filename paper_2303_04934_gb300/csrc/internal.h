@@ -116,6 +116,8 @@ int launch_bits_to_bytes(const uint32_t* bits, const int32_t* label, int32_t L, 
 
 // Round-0 labelling from the two visited bitmaps of pivot s (Alg. 1 label step
 // with one source). Adds the number of finished vertices to *ndone.
+int launch_class_trim(const int32_t* act, int64_t N, const int32_t* off, const int32_t* adj, const int32_t* toff,
+                      const int32_t* tadj, int32_t* label, int32_t* rep, unsigned long long* ndone, cudaStream_t s);
 int launch_label_first(const uint32_t* bf, const uint32_t* bb, int32_t n, int32_t s, int32_t* label, int32_t* rep,
                        unsigned long long* ndone, cudaStream_t s_);
 

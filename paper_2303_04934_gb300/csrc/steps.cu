@@ -275,6 +275,46 @@ __global__ void k_bits_to_bytes(const uint32_t* __restrict__ bits, const int32_t
 // After the first SCC (one pivot s, class L = label[s]): a vertex of class L
 // reached both ways is finished with representative s; otherwise its class
 // becomes hash(L, s if reached from s, s if it reaches s) (Alg. 1 label step).
+// Trimming inside classes: an active vertex with no out-arc or no in-arc to an
+// active vertex of its own class cannot share a cycle with any other vertex, so
+// it is a singleton SCC (Sec. 4.1 trimming, applied to the classes of Alg. 1).
+// Arcs to finished vertices (label kDone, never equal to a class) are ignored.
+// A vertex finished concurrently by another thread may or may not be seen as
+// active; either way the decision is exact. Per thread one vertex of the active
+// list, four arcs in flight, early exit at the first arc inside the class.
+__device__ __forceinline__ bool has_class_arc(const int32_t* __restrict__ off, const int32_t* __restrict__ adj,
+                                              const int32_t* label, int32_t v, int32_t L) {
+    const int e1 = off[v + 1];
+    for (int e = off[v]; e < e1; e += 4) {
+        int w[4], lw[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) w[k] = e + k < e1 ? adj[e + k] : -1;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) lw[k] = w[k] >= 0 ? ld_volatile(&label[w[k]]) : kDone;
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            if (lw[k] == L) return true;
+    }
+    return false;
+}
+__global__ void k_class_trim(const int32_t* __restrict__ act, int64_t N, const int32_t* __restrict__ off,
+                             const int32_t* __restrict__ adj, const int32_t* __restrict__ toff,
+                             const int32_t* __restrict__ tadj, int32_t* label, int32_t* rep,
+                             unsigned long long* ndone) {
+    unsigned long long c = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t v = act[i];
+        const int32_t L = ld_volatile(&label[v]);
+        if (L < 0) continue;
+        if (has_class_arc(off, adj, label, v, L) && has_class_arc(toff, tadj, label, v, L)) continue;
+        label[v] = kDone;
+        rep[v] = v;
+        ++c;
+    }
+    for (int d = 16; d >= 1; d >>= 1) c += __shfl_xor_sync(kFull, c, d);
+    if (lane_id() == 0 && c) atomicAdd(ndone, c);
+}
+
 __global__ void k_label_first(const uint32_t* __restrict__ bf, const uint32_t* __restrict__ bb, int32_t n, int32_t s,
                               int32_t L, int32_t* label, int32_t* rep, unsigned long long* ndone) {
     unsigned long long c = 0;
@@ -502,6 +542,14 @@ int launch_bits_to_bytes(const uint32_t* bits, const int32_t* label, int32_t L, 
                          cudaStream_t s) {
     if (n == 0) return SCC_OK;
     k_bits_to_bytes<<<grid_for(n, kBlk), kBlk, 0, s>>>(bits, label, L, n, out);
+    SCC_LAUNCH();
+    return SCC_OK;
+}
+
+int launch_class_trim(const int32_t* act, int64_t N, const int32_t* off, const int32_t* adj, const int32_t* toff,
+                      const int32_t* tadj, int32_t* label, int32_t* rep, unsigned long long* ndone, cudaStream_t s) {
+    if (N <= 0) return SCC_OK;
+    k_class_trim<<<grid_for(N, kBlk), kBlk, 0, s>>>(act, N, off, adj, toff, tadj, label, rep, ndone);
     SCC_LAUNCH();
     return SCC_OK;
 }

@@ -48,7 +48,8 @@ class scc_stats(ctypes.Structure):
                 ("ms_engine", ctypes.c_double), ("engine_arcs", ctypes.c_int64), ("engine_items", ctypes.c_int64),
                 ("engine_inserted", ctypes.c_int64), ("ms_create", ctypes.c_double),
                 ("ms_transpose_hist", ctypes.c_double), ("ms_transpose_part", ctypes.c_double),
-                ("ms_transpose_rows", ctypes.c_double)]
+                ("ms_transpose_rows", ctypes.c_double), ("n_class_trimmed", ctypes.c_int32),
+                ("class_trim_passes", ctypes.c_int32), ("ms_class_trim", ctypes.c_double)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
