@@ -65,7 +65,10 @@ SCC_API const char* scc_error_string(int code);
  *               Granularity"): a warp task stops expanding after visiting about
  *               tau arcs; vertices with more than tau out-arcs are expanded by
  *               many warps in parallel instead. Default 512 (the paper's 2^9).
- *   beta        prefix-doubling multiplier, > 1 (Sec. 2; the paper uses 1.5).
+ *   beta        prefix-doubling multiplier, > 1 (Alg. 1 doubles the batches, the
+ *               experiments use 1.5). Default 2: a batch costs rounds whose
+ *               time on the GPU is set by memory latency more than by the pairs
+ *               they visit, so fewer and larger batches are faster here.
  *   lambda      first hash-bag chunk size in slots, a power of two >= 1024
  *               (Sec. 3.3; chunks grow lambda, 2*lambda, ...). Default 16384.
  *   sigma       hash-bag samples per chunk before it is declared full (Sec. 3.3,

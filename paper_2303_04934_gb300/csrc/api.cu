@@ -258,7 +258,7 @@ const char* scc_error_string(int code) {
 int scc_config_default(scc_config* cfg) {
     if (!cfg) return SCC_ERR_INVALID_ARG;
     cfg->tau = 512;
-    cfg->beta = 1.5;
+    cfg->beta = 2.0;
     cfg->lambda = 1 << 14;
     cfg->sigma = 50;
     cfg->block = 256;
