@@ -270,7 +270,11 @@ def main():
     #     16 B per arc + 4 B per vertex;
     #   transpose partition pass: read the arc, write (u, v): 12 B per arc + 4 B
     #     per vertex (row offsets of the tiles);
-    #   transpose histogram pass: 4 B per arc + 4 B per vertex.
+    #   intake pass (copy + range check + bucket histogram of the targets):
+    #     read and write 4 B per arc;
+    #   multi-reachability batch loop: 8 B per arc examined (target + label),
+    #     8 B row offsets per item expanded, 16 B per pair inserted (table
+    #     slot + bag slot).
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -287,8 +291,11 @@ def main():
             sum(s["ms_transpose_rows"] for s in stats), len(stats), len(stats) * (16 * mt + 4 * n)),
         "k_bucket_part (transpose, bucket partition)": (
             sum(s["ms_transpose_part"] for s in stats), len(stats), len(stats) * (12 * m + 4 * n)),
-        "k_bucket_hist (transpose, bucket histogram)": (
-            sum(s["ms_transpose_hist"] for s in stats), len(stats), len(stats) * (4 * m + 4 * n)),
+        "k_copy_check_hist (intake: copy, range check, bucket histogram)": (
+            sum(s["ms_transpose_hist"] for s in stats), len(stats), len(stats) * (8 * m)),
+        "bgss_kernel (multi-reachability batch loop)": (
+            sum(s["ms_multi_search"] for s in stats), sum(s["multi_launches"] for s in stats),
+            sum(8 * s["multi_arcs"] + 8 * s["multi_items"] + 16 * s["pairs"] for s in stats)),
     }
     kname, (kms, klaunch, kbytes) = max(cands.items(), key=lambda kv: kv[1][0])
     achieved = kbytes / (kms / 1e3) / 1e9 if kms > 0 else 0.0

@@ -187,14 +187,20 @@ typedef struct scc_stats {
     int64_t engine_arcs;       /* arcs examined by the first-SCC engine launches */
     int64_t engine_items;      /* items they expanded (adjacency rows read) */
     int64_t engine_inserted;   /* reachability pairs inserted by multi-reachability */
-    /* graph construction (scc_graph_create of this handle): total and the three
-       passes of the transposed-CSR build, CUDA events on the creating stream */
+    /* graph construction (scc_graph_create of this handle), CUDA events on the
+       creating stream: total; the intake pass (copy and range check of the
+       targets with the bucket histogram of the transpose); the two passes that
+       build the transpose (bucket partition, per-bucket rows) */
     double ms_create, ms_transpose_hist, ms_transpose_part, ms_transpose_rows;
     /* trimming inside the classes left by the first SCC: vertices with no arc
        from or no arc to a vertex of their own class are singleton SCCs */
     int32_t n_class_trimmed;   /* vertices finished this way */
     int32_t class_trim_passes; /* passes run */
     double ms_class_trim;
+    /* the launches of the device-side batch loop (multi-reachability) */
+    int32_t multi_launches;
+    int64_t multi_arcs;        /* arcs examined */
+    int64_t multi_items;       /* items expanded */
 } scc_stats;
 
 SCC_API int scc_get_stats(scc_handle h, scc_stats* out);

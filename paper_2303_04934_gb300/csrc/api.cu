@@ -296,72 +296,92 @@ static int graph_create_impl(scc_graph* h, int32_t n, int64_t m, const int32_t* 
     h->off = off_in;
     h->adj = adj_in;
     SCC_TRY(to_device(off_in, offsets, sizeof(int32_t) * ((size_t)n + 1), s));
-    SCC_TRY(to_device(adj_in, targets, sizeof(int32_t) * (size_t)m, s));
-    // validate before any kernel indexes with these arrays
+    // a device target array is copied by the intake pass itself (one read);
+    // a host one is staged first
+    const int32_t* src = targets;
+    if (m > 0 && !is_device_ptr(targets)) {
+        SCC_TRY(to_device(adj_in, targets, sizeof(int32_t) * (size_t)m, s));
+        src = adj_in;
+    }
+    const int shift = bucket_shift(n);
+    const int nb = std::max(1, (int)(((int64_t)n + (1ll << shift) - 1) >> shift));
     int* bad = nullptr;
+    int32_t* selfrow = nullptr;
+    unsigned long long *bcnt = nullptr, *btmp = nullptr;
+    void* stmp = nullptr;
     SCC_TRY(dalloc_t(&bad, 1, s));
+    SCC_TRY(dalloc_t(&selfrow, (size_t)n + 1, s));
+    SCC_TRY(dalloc_t(&bcnt, (size_t)nb + 2, s));  // [nb + 1]: self-loops found
+    SCC_TRY(dalloc_t(&btmp, 2 * (size_t)nb + 2, s));
+    SCC_TRY(dalloc(&stmp, scan_tmp_bytes(n), s));
     SCC_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), s));
-    SCC_TRY(launch_validate(off_in, adj_in, n, m, bad, s));
+    SCC_CUDA(cudaMemsetAsync(selfrow, 0, sizeof(int32_t) * ((size_t)n + 1), s));
+    SCC_CUDA(cudaMemsetAsync(bcnt, 0, sizeof(unsigned long long) * ((size_t)nb + 2), s));
+    // validation before any kernel indexes with these arrays: the offsets, then
+    // the targets within the intake pass (copy, range check, bucket histogram)
+    SCC_TRY(launch_validate_offsets(off_in, n, m, bad, s));
+    cudaEventRecord(ce.e[1], s);
+    SCC_TRY(launch_copy_check_hist(src, adj_in, n, m, shift, bcnt, bad, h->di.num_sms, s));
+    cudaEventRecord(ce.e[2], s);
     int hbad = 0;
     SCC_CUDA(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
     SCC_CUDA(cudaStreamSynchronize(s));
     dfree(bad, s);
     if (hbad) return SCC_ERR_INVALID_ARG;
-    // coarse bucket histogram of the arcs (and self-loops)
-    const int shift = bucket_shift(n);
-    const int nb = std::max(1, (int)(((int64_t)n + (1ll << shift) - 1) >> shift));
-    int32_t* selfrow = nullptr;
-    unsigned long long *bcnt = nullptr, *btmp = nullptr;
-    void* stmp = nullptr;
-    SCC_TRY(dalloc_t(&selfrow, (size_t)n + 1, s));
-    SCC_TRY(dalloc_t(&bcnt, (size_t)nb + 2, s));
-    SCC_TRY(dalloc_t(&btmp, 2 * (size_t)nb + 2, s));
-    SCC_TRY(dalloc(&stmp, scan_tmp_bytes(n), s));
-    SCC_CUDA(cudaMemsetAsync(selfrow, 0, sizeof(int32_t) * ((size_t)n + 1), s));
-    SCC_CUDA(cudaMemsetAsync(bcnt, 0, sizeof(unsigned long long) * ((size_t)nb + 2), s));
     int32_t* trow = nullptr;
     SCC_TRY(dalloc_t(&trow, tile_rows_count(m), s));
     SCC_TRY(launch_tile_rows(off_in, n, m, trow, s));
-    cudaEventRecord(ce.e[1], s);
-    SCC_TRY(launch_bucket_hist(off_in, adj_in, trow, n, m, shift, bcnt, selfrow, bcnt + nb + 1, h->di.num_sms, s));
-    cudaEventRecord(ce.e[2], s);
-    unsigned long long hself = 0;
-    SCC_CUDA(cudaMemcpyAsync(&hself, bcnt + nb + 1, sizeof(hself), cudaMemcpyDeviceToHost, s));
-    SCC_CUDA(cudaStreamSynchronize(s));
-    h->mt = m - (int64_t)hself;
+    h->mt = m;
     int64_t m_cur = m;
-    if (hself > 0) {
-        // forward CSR without self-loops
+    // forward CSR without its self-loops (selfrow counts them per row)
+    auto drop_self_loops = [&](unsigned long long hself) -> int {
+        h->mt = m - (int64_t)hself;
         int32_t *cnt = nullptr, *off2 = nullptr, *adj2 = nullptr;
         SCC_TRY(dalloc_t(&cnt, (size_t)n + 1, s));
         SCC_TRY(dalloc_t(&off2, (size_t)n + 1, s));
         SCC_TRY(dalloc_t(&adj2, (size_t)h->mt, s));
-        SCC_TRY(launch_row_nonself(off_in, selfrow, n, cnt, s));
+        SCC_TRY(launch_row_nonself(h->off, selfrow, n, cnt, s));
         SCC_TRY(launch_scan(cnt, off2, n, stmp, s));
-        SCC_TRY(launch_drop_self_loops(off_in, adj_in, n, m, selfrow, off2, adj2, s));
+        SCC_TRY(launch_drop_self_loops(h->off, h->adj, n, m, selfrow, off2, adj2, s));
         dfree(cnt, s);
-        dfree(off_in, s);
-        dfree(adj_in, s);
+        dfree(h->off, s);
+        dfree(h->adj, s);
         h->off = off2;
         h->adj = adj2;
         m_cur = h->mt;
         SCC_TRY(launch_tile_rows(h->off, n, m_cur, trow, s));  // rows of the new CSR's tiles
-    }
+        return SCC_OK;
+    };
     // G^T: two-level bucketed counting sort by target (direct atomics when n is huge)
     int32_t* toff = nullptr;
     SCC_TRY(dalloc_t(&toff, (size_t)n + 1, s));
     h->toff = toff;
-    SCC_TRY(dalloc_t(&h->tadj, (size_t)h->mt, s));
+    SCC_TRY(dalloc_t(&h->tadj, (size_t)m, s));
     if (transpose_bucketed(shift)) {
         int32_t *tmp_u = nullptr, *tmp_v = nullptr, *ord = nullptr;
         int* terr = nullptr;
-        SCC_TRY(dalloc_t(&tmp_u, (size_t)h->mt, s));
-        SCC_TRY(dalloc_t(&tmp_v, (size_t)h->mt, s));
+        SCC_TRY(dalloc_t(&tmp_u, (size_t)m, s));
+        SCC_TRY(dalloc_t(&tmp_v, (size_t)m, s));
         SCC_TRY(dalloc_t(&ord, (size_t)nb, s));
         SCC_TRY(dalloc_t(&terr, 1, s));
         SCC_CUDA(cudaMemsetAsync(terr, 0, sizeof(int), s));
-        SCC_TRY(launch_transpose(h->off, h->adj, trow, n, m_cur, h->mt, shift, bcnt, btmp, tmp_u, tmp_v, ord, toff,
-                                 h->tadj, terr, h->di.num_sms, s, &ce.e[3]));
+        for (int attempt = 0;; ++attempt) {
+            bool self_found = false;
+            SCC_TRY(launch_transpose(h->off, h->adj, trow, n, m_cur, m_cur, shift, bcnt, btmp, tmp_u, tmp_v, ord, toff,
+                                     h->tadj, selfrow, bcnt + nb + 1, &self_found, terr, h->di.num_sms, s, &ce.e[3]));
+            if (!self_found) break;
+            if (attempt > 0) return SCC_ERR_INTERNAL;  // the rebuilt CSR has no self-loops
+            // self-loops: rebuild the forward CSR without them and start over
+            unsigned long long hself = 0;
+            SCC_CUDA(cudaMemcpyAsync(&hself, bcnt + nb + 1, sizeof(hself), cudaMemcpyDeviceToHost, s));
+            SCC_CUDA(cudaStreamSynchronize(s));
+            SCC_TRY(drop_self_loops(hself));
+            SCC_CUDA(cudaMemsetAsync(bcnt, 0, sizeof(unsigned long long) * ((size_t)nb + 2), s));
+            int* bad2 = nullptr;
+            SCC_TRY(dalloc_t(&bad2, 1, s));
+            SCC_TRY(launch_copy_check_hist(h->adj, h->adj, n, m_cur, shift, bcnt, bad2, h->di.num_sms, s));
+            dfree(bad2, s);  // nothing to report: the targets were checked above
+        }
         int herr = 0;
         SCC_CUDA(cudaMemcpyAsync(&herr, terr, sizeof(int), cudaMemcpyDeviceToHost, s));
         SCC_CUDA(cudaStreamSynchronize(s));
@@ -371,6 +391,13 @@ static int graph_create_impl(scc_graph* h, int32_t n, int64_t m, const int32_t* 
         dfree(terr, s);
         if (herr) return herr;
     } else {
+        // self-loops from the row-aware histogram pass, then direct placement
+        SCC_CUDA(cudaMemsetAsync(bcnt, 0, sizeof(unsigned long long) * ((size_t)nb + 2), s));
+        SCC_TRY(launch_bucket_hist(h->off, h->adj, trow, n, m, shift, bcnt, selfrow, bcnt + nb + 1, h->di.num_sms, s));
+        unsigned long long hself = 0;
+        SCC_CUDA(cudaMemcpyAsync(&hself, bcnt + nb + 1, sizeof(hself), cudaMemcpyDeviceToHost, s));
+        SCC_CUDA(cudaStreamSynchronize(s));
+        if (hself > 0) SCC_TRY(drop_self_loops(hself));
         int32_t* indeg = nullptr;
         SCC_TRY(dalloc_t(&indeg, (size_t)n + 1, s));
         SCC_TRY(launch_transpose_direct(h->off, h->adj, trow, n, m_cur, indeg, stmp, toff, h->tadj, h->di.num_sms, s));
@@ -645,6 +672,9 @@ static int scc_run_impl(scc_graph* h, int32_t* labels_out, cudaStream_t s) {
                 st.search_rounds += r.rounds;
                 st.pairs += (int64_t)r.pairs;
                 st.engine_inserted += (int64_t)r.pairs;
+                st.multi_launches++;
+                st.multi_arcs += (int64_t)r.edges;
+                st.multi_items += (int64_t)r.items;
                 hc[1] = r.ndone;
                 if (r.status == 0) break;
                 if (r.status == 2) {  // stopped between batches: tables and bag are empty

@@ -49,8 +49,9 @@ struct DeviceInfo {
 int device_info(DeviceInfo* out);
 
 // --------------------------------------------------------- graph building --
-// Validate a CSR on the device; *bad (device int) becomes nonzero if malformed.
-int launch_validate(const int32_t* off, const int32_t* adj, int32_t n, int64_t m, int* bad, cudaStream_t s);
+// Validate CSR offsets on the device (off[0] = 0, off[n] = m, non-decreasing);
+// *bad (device int) becomes nonzero if malformed.
+int launch_validate_offsets(const int32_t* off, int32_t n, int64_t m, int* bad, cudaStream_t s);
 // Transposed CSR (transpose.cu). bucket_shift(n): vertices per coarse bucket
 // = 2^shift, at most 1024 buckets.
 int bucket_shift(int32_t n);
@@ -58,19 +59,27 @@ int bucket_shift(int32_t n);
 // table has tile_rows_count(m) entries and drives the arc passes below.
 size_t tile_rows_count(int64_t m);
 int launch_tile_rows(const int32_t* off, int32_t n, int64_t m, int32_t* trow, cudaStream_t s);
+// Intake of the target array: dst = src (no copy when equal), targets outside
+// [0, n) set *bad, bucket_cnt[b] += arcs into bucket b (self-loops included).
+int launch_copy_check_hist(const int32_t* src, int32_t* dst, int32_t n, int64_t m, int shift,
+                           unsigned long long* bucket_cnt, int* bad, int num_sms, cudaStream_t s);
 // bucket_cnt[b] += non-self arcs into bucket b; selfrow[u] += self-loops of u.
 int launch_bucket_hist(const int32_t* off, const int32_t* adj, const int32_t* trow, int32_t n, int64_t m, int shift,
                        unsigned long long* bucket_cnt, int32_t* selfrow, unsigned long long* nself, int num_sms,
                        cudaStream_t s);
-// G^T of the CSR (off, adj) with m arcs of which mt are not self-loops, by the
-// two-level bucketed counting sort (when transpose_bucketed(shift)).
-// bucket_tmp: 2 * nbuckets + 2 words; tmp_u, tmp_v: mt each; order_tmp: nbuckets.
+// G^T of the CSR (off, adj) with m arcs, by the two-level bucketed counting
+// sort (when transpose_bucketed(shift)); bucket_cnt from launch_copy_check_hist.
+// bucket_tmp: 2 * nbuckets + 2 words; tmp_u, tmp_v: m each; order_tmp: nbuckets.
+// If the CSR has self-loops, nothing is written to toff/tadj: *self_found is
+// set, selfrow[u] (zeroed by the caller) counts u's self-loops and *nself
+// (zeroed by the caller) their total.
 bool transpose_bucketed(int shift);
 int launch_transpose(const int32_t* off, const int32_t* adj, const int32_t* trow, int32_t n, int64_t m, int64_t mt,
                      int shift,
                      const unsigned long long* bucket_cnt, unsigned long long* bucket_tmp, int32_t* tmp_u,
-                     int32_t* tmp_v, int32_t* order_tmp, int32_t* toff, int32_t* tadj, int* err, int num_sms,
-                     cudaStream_t s, cudaEvent_t* ev = nullptr);  // ev[0..3]: around the partition and the rows pass
+                     int32_t* tmp_v, int32_t* order_tmp, int32_t* toff, int32_t* tadj, int32_t* selfrow,
+                     unsigned long long* nself, bool* self_found, int* err, int num_sms, cudaStream_t s,
+                     cudaEvent_t* ev = nullptr);  // ev[0..3]: around the partition and the rows pass
 // Direct G^T for very large n: global atomics. indeg: n + 1.
 int launch_transpose_direct(const int32_t* off, const int32_t* adj, const int32_t* trow, int32_t n, int64_t m,
                             int32_t* indeg, void* scan_tmp, int32_t* toff, int32_t* tadj, int num_sms,

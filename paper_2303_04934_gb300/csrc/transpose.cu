@@ -7,7 +7,9 @@
 //
 //   A. coarse partition by bucket b = v >> shift (at most 512 buckets):
 //      A1 histogram of buckets (per-block shared histogram, one global add per
-//         block and bucket);
+//         block and bucket), fused with the copy and range check of the
+//         targets: it needs no arc sources, so it reads the targets once as a
+//         flat array;
 //      A2 partition: a block takes a tile of 8k arcs, counting-sorts it by
 //         bucket in shared memory, reserves one run per non-empty bucket with a
 //         global atomicAdd, and writes the sorted tile out, so consecutive lanes
@@ -116,6 +118,49 @@ __device__ __forceinline__ void for_step_arcs(const int32_t* __restrict__ off, c
     __syncthreads();
 }
 
+// A1 fused with graph intake: dst[e] = src[e] (unless dst == src), every target
+// checked against [0, n) (*bad set otherwise, the arc skipped), and the bucket
+// histogram of all arcs (self-loops included: the partition pass finds them).
+// 16-byte loads and stores when both arrays are 16-byte aligned.
+__global__ void __launch_bounds__(kBlkA) k_copy_check_hist(const int32_t* __restrict__ src, int32_t* __restrict__ dst,
+                                                           int64_t m, int32_t n, int shift, int nb,
+                                                           unsigned long long* bucket_cnt, int* bad) {
+    __shared__ unsigned int s_hist[kMaxBuckets];
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) s_hist[i] = 0;
+    __syncthreads();
+    const bool copy = src != dst;
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, stride = (int64_t)gridDim.x * blockDim.x;
+    bool badl = false;
+    auto one = [&](int32_t t) {
+        if (t < 0 || t >= n) badl = true;
+        else atomicAdd(&s_hist[t >> shift], 1u);
+    };
+    int64_t done = 0;
+    if ((((uintptr_t)src | (uintptr_t)dst) & 15) == 0) {
+        const int64_t m4 = m / 4;
+        const int4* s4 = reinterpret_cast<const int4*>(src);
+        int4* d4 = reinterpret_cast<int4*>(dst);
+        for (int64_t i = tid; i < m4; i += stride) {
+            const int4 x = __ldg(s4 + i);
+            if (copy) d4[i] = x;
+            one(x.x);
+            one(x.y);
+            one(x.z);
+            one(x.w);
+        }
+        done = m4 * 4;
+    }
+    for (int64_t e = done + tid; e < m; e += stride) {
+        const int32_t t = __ldg(src + e);
+        if (copy) dst[e] = t;
+        one(t);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < nb; i += blockDim.x)
+        if (s_hist[i]) atomicAdd(&bucket_cnt[i], (unsigned long long)s_hist[i]);
+    if (badl) atomicExch(bad, 1);
+}
+
 // Row of the first arc of every step (trow[t], t < T) and of the last arc
 // (trow[T]): one binary search per step instead of one per block step.
 __global__ void k_tile_rows(const int32_t* __restrict__ off, int32_t n, int64_t m, int64_t T, int32_t* trow) {
@@ -173,7 +218,8 @@ __global__ void __launch_bounds__(kBlkA) k_bucket_part(const int32_t* __restrict
                                                        const int32_t* __restrict__ trow, int32_t n, int64_t m,
                                                        int shift, int nb,
                                                        unsigned long long* cursor, int32_t* out_u, int32_t* out_v,
-                                                       unsigned long long mt, int* err) {
+                                                       unsigned long long mt, int32_t* selfrow,
+                                                       unsigned long long* nself, int* err) {
     __shared__ int32_t s_off[kRowsCap];
     __shared__ unsigned int s_cnt[kMaxBuckets];
     __shared__ unsigned int s_start[kMaxBuckets];
@@ -192,11 +238,16 @@ __global__ void __launch_bounds__(kBlkA) k_bucket_part(const int32_t* __restrict
         int uu[kChunk], vv[kChunk];
 #pragma unroll
         for (int q = 0; q < kChunk; ++q) vv[q] = -1;
+        // every arc is placed (the histogram counted self-loops too); a self-loop
+        // is also counted per row, and any self-loop makes the caller rebuild
+        // the CSR without them and start over
         for_step_arcs(off, adj, n, t0, t1, trow, s_off, [&](int q, int u, int v) {
-            if (u != v) {
-                uu[q] = u;
-                vv[q] = v;
-                rk[q] = atomicAdd(&s_cnt[v >> shift], 1u);
+            uu[q] = u;
+            vv[q] = v;
+            rk[q] = atomicAdd(&s_cnt[v >> shift], 1u);
+            if (u == v) {
+                atomicAdd(&selfrow[u], 1);
+                atomicAdd(nself, 1ull);
             }
         });
         // exclusive scan of the bucket counts (nb <= 512 = blockDim)
@@ -360,6 +411,16 @@ int bucket_shift(int32_t n) {
 
 size_t tile_rows_count(int64_t m) { return (size_t)((m + kStep - 1) / kStep) + 1; }
 
+int launch_copy_check_hist(const int32_t* src, int32_t* dst, int32_t n, int64_t m, int shift,
+                           unsigned long long* bucket_cnt, int* bad, int num_sms, cudaStream_t s) {
+    if (m == 0) return SCC_OK;
+    const int nb = std::max(1, (int)(((int64_t)n + (1ll << shift) - 1) >> shift));
+    k_copy_check_hist<<<grid_for_arcs(m, 4 * kBlkA * 4, num_sms, 2), kBlkA, 0, s>>>(src, dst, m, n, shift, nb,
+                                                                                   bucket_cnt, bad);
+    SCC_LAUNCH();
+    return SCC_OK;
+}
+
 int launch_tile_rows(const int32_t* off, int32_t n, int64_t m, int32_t* trow, cudaStream_t s) {
     if (m == 0 || n == 0) return SCC_OK;
     const int64_t T = (m + kStep - 1) / kStep;
@@ -402,8 +463,10 @@ bool transpose_bucketed(int shift) { return shift <= kBucketLog; }
 int launch_transpose(const int32_t* off, const int32_t* adj, const int32_t* trow, int32_t n, int64_t m, int64_t mt,
                      int shift,
                      const unsigned long long* bucket_cnt, unsigned long long* bucket_tmp, int32_t* tmp_u,
-                     int32_t* tmp_v, int32_t* order_tmp, int32_t* toff, int32_t* tadj, int* err, int num_sms,
-                     cudaStream_t s, cudaEvent_t* ev) {
+                     int32_t* tmp_v, int32_t* order_tmp, int32_t* toff, int32_t* tadj, int32_t* selfrow,
+                     unsigned long long* nself, bool* self_found, int* err, int num_sms, cudaStream_t s,
+                     cudaEvent_t* ev) {
+    *self_found = false;
     const int nb = std::max(1, (int)(((int64_t)n + (1ll << shift) - 1) >> shift));
     unsigned long long* start = bucket_tmp;
     unsigned long long* cursor = bucket_tmp + nb + 1;
@@ -419,14 +482,21 @@ int launch_transpose(const int32_t* off, const int32_t* adj, const int32_t* trow
         if (ev) cudaEventRecord(ev[0], s);
         k_bucket_part<<<grid_for_arcs(m, kStep, num_sms, 2), kBlkA, stage, s>>>(off, adj, trow, n, m, shift, nb, cursor,
                                                                                   tmp_u, tmp_v,
-                                                                                  (unsigned long long)mt, err);
+                                                                                  (unsigned long long)mt, selfrow,
+                                                                                  nself, err);
         SCC_LAUNCH();
         if (ev) cudaEventRecord(ev[1], s);
     }
     // buckets by decreasing size (longest first), from the host copy of the counts
     std::vector<unsigned long long> hc(nb);
+    unsigned long long hself = 0;
     SCC_CUDA(cudaMemcpyAsync(hc.data(), bucket_cnt, sizeof(unsigned long long) * nb, cudaMemcpyDeviceToHost, s));
+    SCC_CUDA(cudaMemcpyAsync(&hself, nself, sizeof(hself), cudaMemcpyDeviceToHost, s));
     SCC_CUDA(cudaStreamSynchronize(s));
+    if (hself > 0) {  // the caller drops the self-loops and calls again
+        *self_found = true;
+        return SCC_OK;
+    }
     std::vector<int32_t> ord(nb);
     std::iota(ord.begin(), ord.end(), 0);
     std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return hc[a] > hc[b]; });

@@ -49,7 +49,8 @@ class scc_stats(ctypes.Structure):
                 ("engine_inserted", ctypes.c_int64), ("ms_create", ctypes.c_double),
                 ("ms_transpose_hist", ctypes.c_double), ("ms_transpose_part", ctypes.c_double),
                 ("ms_transpose_rows", ctypes.c_double), ("n_class_trimmed", ctypes.c_int32),
-                ("class_trim_passes", ctypes.c_int32), ("ms_class_trim", ctypes.c_double)]
+                ("class_trim_passes", ctypes.c_int32), ("ms_class_trim", ctypes.c_double),
+                ("multi_launches", ctypes.c_int32), ("multi_arcs", ctypes.c_int64), ("multi_items", ctypes.c_int64)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
