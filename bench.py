@@ -266,10 +266,10 @@ def main():
     # bytes per launch (the data the algorithm must move):
     #   first-SCC engine (2 launches): 4 B arc target + 4 B visited word per arc
     #     examined, 8 B row offsets per item expanded;
-    #   transpose rows pass: read v twice and u once, write u and the row offset:
-    #     16 B per arc + 4 B per vertex;
-    #   transpose partition pass: read the arc, write (u, v): 12 B per arc + 4 B
-    #     per vertex (row offsets of the tiles);
+    #   transpose rows pass: read the 2 B local target twice and the 4 B source
+    #     once, write the source and the row offset: 12 B per arc + 4 B per vertex;
+    #   transpose partition pass: read the arc, write (u, local target): 10 B per
+    #     arc + 4 B per vertex (row offsets of the tiles);
     #   intake pass (copy + range check + bucket histogram of the targets):
     #     read and write 4 B per arc;
     #   multi-reachability batch loop: 8 B per arc examined (target + label),
@@ -288,9 +288,9 @@ def main():
             sum(s["ms_engine"] for s in stats), sum(s["engine_launches"] for s in stats),
             sum(8 * s["engine_arcs"] + 8 * s["engine_items"] for s in stats)),
         "k_bucket_rows (transpose, per-bucket rows)": (
-            sum(s["ms_transpose_rows"] for s in stats), len(stats), len(stats) * (16 * mt + 4 * n)),
+            sum(s["ms_transpose_rows"] for s in stats), len(stats), len(stats) * (12 * mt + 4 * n)),
         "k_bucket_part (transpose, bucket partition)": (
-            sum(s["ms_transpose_part"] for s in stats), len(stats), len(stats) * (12 * m + 4 * n)),
+            sum(s["ms_transpose_part"] for s in stats), len(stats), len(stats) * (10 * m + 4 * n)),
         "k_copy_check_hist (intake: copy, range check, bucket histogram)": (
             sum(s["ms_transpose_hist"] for s in stats), len(stats), len(stats) * (8 * m)),
         "bgss_kernel (multi-reachability batch loop)": (

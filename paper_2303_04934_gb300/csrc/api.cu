@@ -358,16 +358,17 @@ static int graph_create_impl(scc_graph* h, int32_t n, int64_t m, const int32_t* 
     h->toff = toff;
     SCC_TRY(dalloc_t(&h->tadj, (size_t)m, s));
     if (transpose_bucketed(shift)) {
-        int32_t *tmp_u = nullptr, *tmp_v = nullptr, *ord = nullptr;
+        int32_t *tmp_u = nullptr, *ord = nullptr;
+        uint16_t* tmp_lv = nullptr;
         int* terr = nullptr;
-        SCC_TRY(dalloc_t(&tmp_u, (size_t)m, s));
-        SCC_TRY(dalloc_t(&tmp_v, (size_t)m, s));
+        SCC_TRY(dalloc_t(&tmp_u, (size_t)m + 8, s));
+        SCC_TRY(dalloc_t(&tmp_lv, (size_t)m + 8, s));
         SCC_TRY(dalloc_t(&ord, (size_t)nb, s));
         SCC_TRY(dalloc_t(&terr, 1, s));
         SCC_CUDA(cudaMemsetAsync(terr, 0, sizeof(int), s));
         for (int attempt = 0;; ++attempt) {
             bool self_found = false;
-            SCC_TRY(launch_transpose(h->off, h->adj, trow, n, m_cur, m_cur, shift, bcnt, btmp, tmp_u, tmp_v, ord, toff,
+            SCC_TRY(launch_transpose(h->off, h->adj, trow, n, m_cur, m_cur, shift, bcnt, btmp, tmp_u, tmp_lv, ord, toff,
                                      h->tadj, selfrow, bcnt + nb + 1, &self_found, terr, h->di.num_sms, s, &ce.e[3]));
             if (!self_found) break;
             if (attempt > 0) return SCC_ERR_INTERNAL;  // the rebuilt CSR has no self-loops
@@ -386,7 +387,7 @@ static int graph_create_impl(scc_graph* h, int32_t n, int64_t m, const int32_t* 
         SCC_CUDA(cudaMemcpyAsync(&herr, terr, sizeof(int), cudaMemcpyDeviceToHost, s));
         SCC_CUDA(cudaStreamSynchronize(s));
         dfree(tmp_u, s);
-        dfree(tmp_v, s);
+        dfree(tmp_lv, s);
         dfree(ord, s);
         dfree(terr, s);
         if (herr) return herr;

@@ -69,7 +69,8 @@ int launch_bucket_hist(const int32_t* off, const int32_t* adj, const int32_t* tr
                        cudaStream_t s);
 // G^T of the CSR (off, adj) with m arcs, by the two-level bucketed counting
 // sort (when transpose_bucketed(shift)); bucket_cnt from launch_copy_check_hist.
-// bucket_tmp: 2 * nbuckets + 2 words; tmp_u, tmp_v: m each; order_tmp: nbuckets.
+// bucket_tmp: 2 * nbuckets + 2 words; tmp_u: m + 8 entries, tmp_lv: m + 8
+// entries (the padding is read, never used); order_tmp: nbuckets.
 // If the CSR has self-loops, nothing is written to toff/tadj: *self_found is
 // set, selfrow[u] (zeroed by the caller) counts u's self-loops and *nself
 // (zeroed by the caller) their total.
@@ -77,7 +78,7 @@ bool transpose_bucketed(int shift);
 int launch_transpose(const int32_t* off, const int32_t* adj, const int32_t* trow, int32_t n, int64_t m, int64_t mt,
                      int shift,
                      const unsigned long long* bucket_cnt, unsigned long long* bucket_tmp, int32_t* tmp_u,
-                     int32_t* tmp_v, int32_t* order_tmp, int32_t* toff, int32_t* tadj, int32_t* selfrow,
+                     uint16_t* tmp_lv, int32_t* order_tmp, int32_t* toff, int32_t* tadj, int32_t* selfrow,
                      unsigned long long* nself, bool* self_found, int* err, int num_sms, cudaStream_t s,
                      cudaEvent_t* ev = nullptr);  // ev[0..3]: around the partition and the rows pass
 // Direct G^T for very large n: global atomics. indeg: n + 1.

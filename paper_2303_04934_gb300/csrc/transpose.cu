@@ -14,6 +14,8 @@
 //         bucket in shared memory, reserves one run per non-empty bucket with a
 //         global atomicAdd, and writes the sorted tile out, so consecutive lanes
 //         store consecutive positions of a run.
+//      Each arc is written as its source u (4 B) and its target's offset within
+//      the bucket (2 B: buckets hold at most 2^15 vertices).
 //   B. one block per bucket (largest buckets first): per-vertex counts of the
 //      bucket in shared memory, their scan gives the bucket's rows of G^T
 //      (offsets written directly: the bucket's first row starts at the bucket's
@@ -217,7 +219,7 @@ __global__ void k_bucket_scan(const unsigned long long* cnt, int nb, unsigned lo
 __global__ void __launch_bounds__(kBlkA) k_bucket_part(const int32_t* __restrict__ off, const int32_t* __restrict__ adj,
                                                        const int32_t* __restrict__ trow, int32_t n, int64_t m,
                                                        int shift, int nb,
-                                                       unsigned long long* cursor, int32_t* out_u, int32_t* out_v,
+                                                       unsigned long long* cursor, int32_t* out_u, uint16_t* out_lv,
                                                        unsigned long long mt, int32_t* selfrow,
                                                        unsigned long long* nself, int* err) {
     __shared__ int32_t s_off[kRowsCap];
@@ -286,7 +288,7 @@ __global__ void __launch_bounds__(kBlkA) k_bucket_part(const int32_t* __restrict
             const unsigned long long pos = s_gbase[b] + (j - s_start[b]);
             if (pos < mt) {
                 out_u[pos] = s_u[j];
-                out_v[pos] = v;
+                out_lv[pos] = (uint16_t)(v & ((1 << shift) - 1));  // the target within its bucket
             } else {
                 atomicExch(err, SCC_ERR_INTERNAL);
             }
@@ -296,14 +298,28 @@ __global__ void __launch_bounds__(kBlkA) k_bucket_part(const int32_t* __restrict
 }
 
 // B. one block per bucket: per-vertex counts in shared memory, row offsets of
-// G^T for the bucket's vertices, placement with shared cursors.
-__global__ void __launch_bounds__(kBlkB) k_bucket_rows(const int32_t* __restrict__ uu, const int32_t* __restrict__ vv,
+// G^T for the bucket's vertices, placement with shared cursors. The arcs are
+// read in aligned chunks of 8 (one 16-byte load of local targets, two of
+// sources), two chunks per thread per step; the arrays are padded by 8 entries
+// so the last chunk may read past the last arc.
+__device__ __forceinline__ void unpack8(const uint4 r, unsigned int (&lv)[8]) {
+    lv[0] = r.x & 0xffffu;
+    lv[1] = r.x >> 16;
+    lv[2] = r.y & 0xffffu;
+    lv[3] = r.y >> 16;
+    lv[4] = r.z & 0xffffu;
+    lv[5] = r.z >> 16;
+    lv[6] = r.w & 0xffffu;
+    lv[7] = r.w >> 16;
+}
+__global__ void __launch_bounds__(kBlkB) k_bucket_rows(const int32_t* __restrict__ uu, const uint16_t* __restrict__ lvv,
                                                        const unsigned long long* __restrict__ start,
                                                        const int32_t* __restrict__ order, int nb, int shift,
                                                        int32_t n, int32_t* toff, int32_t* tadj, int* err) {
     extern __shared__ int s_cnt[];  // 2^shift counters
     __shared__ int s_wsum[kBlkB / 32];
     const int W = 1 << shift;
+    constexpr int kCh = 2;  // chunks per thread per step
     for (int oi = blockIdx.x; oi < nb; oi += gridDim.x) {
         const int b = order[oi];
         const int v0 = b << shift;
@@ -311,28 +327,34 @@ __global__ void __launch_bounds__(kBlkB) k_bucket_rows(const int32_t* __restrict
         const long long a0 = (long long)start[b], a1 = (long long)start[b + 1];
         for (int i = threadIdx.x; i < vw; i += blockDim.x) s_cnt[i] = 0;
         __syncthreads();
-        // 8 independent loads in flight per thread
-        for (long long i0 = a0 + threadIdx.x; i0 < a1; i0 += 8ll * blockDim.x) {
-            int x[8];
+        const long long c0 = (a0 & ~7ll) + 8ll * threadIdx.x;
+        const long long cstep = 8ll * blockDim.x;
+        for (long long c = c0; c < a1; c += kCh * cstep) {
+            uint4 r[kCh];
 #pragma unroll
-            for (int k = 0; k < 8; ++k) {
-                const long long i = i0 + (long long)k * blockDim.x;
-                x[k] = i < a1 ? __ldg(&vv[i]) : INT_MIN;
+            for (int k = 0; k < kCh; ++k) {
+                const long long cc = c + k * cstep;
+                r[k] = cc < a1 ? __ldg(reinterpret_cast<const uint4*>(lvv + cc)) : make_uint4(0, 0, 0, 0);
             }
 #pragma unroll
-            for (int k = 0; k < 8; ++k) {
-                if (x[k] == INT_MIN) continue;
-                const unsigned int lv = (unsigned int)(x[k] - v0);
-                if (lv < (unsigned int)vw) atomicAdd(&s_cnt[lv], 1);
-                else atomicExch(err, SCC_ERR_INTERNAL);  // arc outside its bucket: skip it, report
+            for (int k = 0; k < kCh; ++k) {
+                const long long cc = c + k * cstep;
+                unsigned int lv[8];
+                unpack8(r[k], lv);
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    if (cc + j < a0 || cc + j >= a1) continue;
+                    if (lv[j] < (unsigned int)vw) atomicAdd(&s_cnt[lv[j]], 1);
+                    else atomicExch(err, SCC_ERR_INTERNAL);  // arc outside its bucket: skip it, report
+                }
             }
         }
         __syncthreads();
         // exclusive scan of s_cnt[0..vw) in place; each thread owns a contiguous run
         const int per = (vw + blockDim.x - 1) / blockDim.x;
-        const int c0 = threadIdx.x * per, c1 = min(c0 + per, vw);
+        const int q0 = threadIdx.x * per, q1 = min(q0 + per, vw);
         int sum = 0;
-        for (int i = c0; i < c1; ++i) sum += s_cnt[i];
+        for (int i = q0; i < q1; ++i) sum += s_cnt[i];
         int incl = warp_incl_scan(sum);
         if (lane_id() == 31) s_wsum[threadIdx.x >> 5] = incl;
         __syncthreads();
@@ -343,29 +365,37 @@ __global__ void __launch_bounds__(kBlkB) k_bucket_rows(const int32_t* __restrict
         }
         __syncthreads();
         int run = s_wsum[threadIdx.x >> 5] + incl - sum;
-        for (int i = c0; i < c1; ++i) {
-            int c = s_cnt[i];
+        for (int i = q0; i < q1; ++i) {
+            int cn = s_cnt[i];
             s_cnt[i] = run;
             toff[v0 + i] = (int32_t)(a0 + run);
-            run += c;
+            run += cn;
         }
         __syncthreads();
-        for (long long i0 = a0 + threadIdx.x; i0 < a1; i0 += 8ll * blockDim.x) {
-            int x[8], y[8];
+        for (long long c = c0; c < a1; c += kCh * cstep) {
+            uint4 r[kCh];
+            int4 ua[kCh], ub[kCh];
 #pragma unroll
-            for (int k = 0; k < 8; ++k) {
-                const long long i = i0 + (long long)k * blockDim.x;
-                x[k] = i < a1 ? __ldg(&vv[i]) : INT_MIN;
-                y[k] = i < a1 ? __ldg(&uu[i]) : 0;
+            for (int k = 0; k < kCh; ++k) {
+                const long long cc = c + k * cstep;
+                const bool in = cc < a1;
+                r[k] = in ? __ldg(reinterpret_cast<const uint4*>(lvv + cc)) : make_uint4(0, 0, 0, 0);
+                ua[k] = in ? __ldg(reinterpret_cast<const int4*>(uu + cc)) : make_int4(0, 0, 0, 0);
+                ub[k] = in ? __ldg(reinterpret_cast<const int4*>(uu + cc + 4)) : make_int4(0, 0, 0, 0);
             }
 #pragma unroll
-            for (int k = 0; k < 8; ++k) {
-                if (x[k] == INT_MIN) continue;
-                const unsigned int lv = (unsigned int)(x[k] - v0);
-                if (lv >= (unsigned int)vw) continue;
-                const int p = atomicAdd(&s_cnt[lv], 1);
-                if (a0 + p < a1) tadj[a0 + p] = y[k];
-                else atomicExch(err, SCC_ERR_INTERNAL);
+            for (int k = 0; k < kCh; ++k) {
+                const long long cc = c + k * cstep;
+                unsigned int lv[8];
+                unpack8(r[k], lv);
+                const int u8[8] = {ua[k].x, ua[k].y, ua[k].z, ua[k].w, ub[k].x, ub[k].y, ub[k].z, ub[k].w};
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    if (cc + j < a0 || cc + j >= a1 || lv[j] >= (unsigned int)vw) continue;
+                    const int p = atomicAdd(&s_cnt[lv[j]], 1);
+                    if (a0 + p < a1) tadj[a0 + p] = u8[j];
+                    else atomicExch(err, SCC_ERR_INTERNAL);
+                }
             }
         }
         __syncthreads();
@@ -463,7 +493,7 @@ bool transpose_bucketed(int shift) { return shift <= kBucketLog; }
 int launch_transpose(const int32_t* off, const int32_t* adj, const int32_t* trow, int32_t n, int64_t m, int64_t mt,
                      int shift,
                      const unsigned long long* bucket_cnt, unsigned long long* bucket_tmp, int32_t* tmp_u,
-                     int32_t* tmp_v, int32_t* order_tmp, int32_t* toff, int32_t* tadj, int32_t* selfrow,
+                     uint16_t* tmp_lv, int32_t* order_tmp, int32_t* toff, int32_t* tadj, int32_t* selfrow,
                      unsigned long long* nself, bool* self_found, int* err, int num_sms, cudaStream_t s,
                      cudaEvent_t* ev) {
     *self_found = false;
@@ -481,7 +511,7 @@ int launch_transpose(const int32_t* off, const int32_t* adj, const int32_t* trow
         SCC_CUDA(cudaFuncSetAttribute(k_bucket_part, cudaFuncAttributeMaxDynamicSharedMemorySize, stage));
         if (ev) cudaEventRecord(ev[0], s);
         k_bucket_part<<<grid_for_arcs(m, kStep, num_sms, 2), kBlkA, stage, s>>>(off, adj, trow, n, m, shift, nb, cursor,
-                                                                                  tmp_u, tmp_v,
+                                                                                  tmp_u, tmp_lv,
                                                                                   (unsigned long long)mt, selfrow,
                                                                                   nself, err);
         SCC_LAUNCH();
@@ -505,7 +535,7 @@ int launch_transpose(const int32_t* off, const int32_t* adj, const int32_t* trow
     if (smem > 48 * 1024)
         SCC_CUDA(cudaFuncSetAttribute(k_bucket_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     if (ev) cudaEventRecord(ev[2], s);
-    k_bucket_rows<<<std::min(nb, num_sms * 2), kBlkB, smem, s>>>(tmp_u, tmp_v, start, order_tmp, nb, shift, n, toff,
+    k_bucket_rows<<<std::min(nb, num_sms * 2), kBlkB, smem, s>>>(tmp_u, tmp_lv, start, order_tmp, nb, shift, n, toff,
                                                                    tadj, err);
     SCC_LAUNCH();
     if (ev) cudaEventRecord(ev[3], s);
