@@ -1,0 +1,1019 @@
+// Batched SCC (sm_103a): many independent graphs in one persistent launch.
+//
+// Each thread block takes the next graph from a device work queue (graphs in
+// decreasing size, so the longest ones start first) and runs the whole method
+// on it alone, with __syncthreads between rounds (CtaScope of engine.cuh):
+//
+//   1. G^T of the graph: in-degree counts, a block scan, placement (Sec. 2: a
+//      backward search is a forward search on G^T).
+//   2. Trimming (Sec. 4.1): vertices without in- or out-arcs are singletons.
+//   3. The pivot order: a seeded Feistel permutation of the active vertices.
+//   4. The first SCC (Sec. 4.2): forward and backward single-reachability from
+//      the first pivot, the VGC engine with vertex items and visited bitmaps.
+//   5. Trimming inside the three classes the first SCC leaves.
+//   6. Prefix-doubling batches (Alg. 1): forward and backward multi-
+//      reachability sharing the rounds of one search (pair items with a
+//      direction bit, Sec. 4.3 pair tables), then the labelling step of Alg. 1
+//      (labels.cuh). A batch whose pairs outgrow its tables is rerun with
+//      larger tables, or -- at the largest size -- with half of its sources.
+//   7. The canonical label: the smallest vertex id of each SCC.
+//
+// The working memory of a block (transpose, labels, tables, hash bag, engine
+// control) is a fixed slice of one device allocation, sized for the largest
+// graph of the batch; nothing is allocated during a run, so the host captures
+// the launch (a reset kernel and the persistent kernel) as a CUDA graph once
+// and replays it.
+#include <algorithm>
+#include <climits>
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "../../include/scc_batch.h"
+#include "common.cuh"
+#include "engine.cuh"
+#include "internal.h"
+#include "labels.cuh"
+
+namespace scc {
+namespace {
+
+constexpr int kBatchMaxBlock = 512;
+constexpr int kBatchTrimPasses = 4;
+constexpr long long kBatchMinTable = 1024;
+
+// ------------------------------------------------------------ working memory --
+// Byte offsets of a block's arrays inside its slice (all 256-byte aligned).
+struct WsLayout {
+    size_t toff, tadj, cnt, label, rep, act, src, fmax, bmax, hit, bits_f, bits_b, tab0, tab1, slots0, slots1,
+        hub_item0, hub_item1, hub_beg0, hub_beg1, hub_deg0, hub_deg1, hub_sb0, hub_sb1, segmap0, segmap1, ctl,
+        tag, bytes;
+};
+
+struct BatchDims {
+    long long n_max, m_max;
+    long long tcap;      // pair-table capacity per direction (power of two)
+    long long nslots;    // hash-bag slots per slot array (64-bit slots)
+    int hub_cap;
+    long long segmap_cap;
+};
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+WsLayout make_layout(const BatchDims& d) {
+    WsLayout L;
+    size_t o = 0;
+    auto take = [&](size_t bytes) {
+        size_t at = o;
+        o = align256(o + bytes);
+        return at;
+    };
+    const size_t n1 = (size_t)d.n_max + 1;
+    const size_t words = (size_t)(d.n_max / 32 + 2);
+    L.toff = take(4 * n1);
+    L.tadj = take(4 * (size_t)std::max<long long>(d.m_max, 1));
+    L.cnt = take(4 * n1);
+    L.label = take(4 * n1);
+    L.rep = take(4 * n1);
+    L.act = take(4 * n1);
+    L.src = take(4 * n1);
+    L.fmax = take(8 * n1);
+    L.bmax = take(8 * n1);
+    L.hit = take(8 * n1);
+    L.bits_f = take(4 * words);
+    L.bits_b = take(4 * words);
+    L.tab0 = take(8 * (size_t)d.tcap);
+    L.tab1 = take(8 * (size_t)d.tcap);
+    L.slots0 = take(8 * (size_t)d.nslots);
+    L.slots1 = take(8 * (size_t)d.nslots);
+    L.hub_item0 = take(8 * (size_t)d.hub_cap);
+    L.hub_item1 = take(8 * (size_t)d.hub_cap);
+    L.hub_beg0 = take(4 * (size_t)d.hub_cap);
+    L.hub_beg1 = take(4 * (size_t)d.hub_cap);
+    L.hub_deg0 = take(4 * (size_t)d.hub_cap);
+    L.hub_deg1 = take(4 * (size_t)d.hub_cap);
+    L.hub_sb0 = take(8 * (size_t)d.hub_cap);
+    L.hub_sb1 = take(8 * (size_t)d.hub_cap);
+    L.segmap0 = take(4 * (size_t)d.segmap_cap);
+    L.segmap1 = take(4 * (size_t)d.segmap_cap);
+    L.ctl = take(sizeof(EngineCtl));
+    L.tag = take(sizeof(uint32_t));
+    L.bytes = o;
+    return L;
+}
+
+struct BatchArgs {
+    int32_t G;
+    const long long* vbase;
+    const long long* ebase;
+    const int32_t* offsets;
+    const int32_t* targets;
+    const int32_t* order;  // graphs in processing order
+    int32_t norder;
+    int32_t* labels;       // output, packed like the vertices
+    int* next;             // work-queue head (zeroed by the reset kernel)
+    int* err;              // first error (SCC_ERR_*), zeroed by the reset kernel
+    unsigned char* ws;
+    size_t ws_stride;
+    WsLayout L;
+    BatchDims D;
+    int tau, seeds, lambda, sigma;
+    double beta;
+    uint64_t seed;
+};
+
+// Per-block pointers into its slice.
+struct Ws {
+    int32_t *toff, *tadj, *cnt, *label, *rep, *act, *src;
+    unsigned long long *fmax, *bmax, *hit;
+    uint32_t *bits_f, *bits_b;
+    unsigned long long *tab0, *tab1;
+    uint32_t* tag;  // the block's labelling-tag counter, kept across launches
+    EngineParams<uint32_t> P32;
+    EngineParams<uint64_t> P64;
+};
+
+template <class T>
+__device__ __forceinline__ T* at(unsigned char* base, size_t off) {
+    return reinterpret_cast<T*>(base + off);
+}
+
+__device__ void bind_ws(const BatchArgs& A, Ws& W) {
+    unsigned char* b = A.ws + A.ws_stride * blockIdx.x;
+    const WsLayout& L = A.L;
+    W.toff = at<int32_t>(b, L.toff);
+    W.tadj = at<int32_t>(b, L.tadj);
+    W.cnt = at<int32_t>(b, L.cnt);
+    W.label = at<int32_t>(b, L.label);
+    W.rep = at<int32_t>(b, L.rep);
+    W.act = at<int32_t>(b, L.act);
+    W.src = at<int32_t>(b, L.src);
+    W.fmax = at<unsigned long long>(b, L.fmax);
+    W.bmax = at<unsigned long long>(b, L.bmax);
+    W.hit = at<unsigned long long>(b, L.hit);
+    W.bits_f = at<uint32_t>(b, L.bits_f);
+    W.bits_b = at<uint32_t>(b, L.bits_b);
+    W.tab0 = at<unsigned long long>(b, L.tab0);
+    W.tab1 = at<unsigned long long>(b, L.tab1);
+    W.tag = at<uint32_t>(b, L.tag);
+    EngineCtl* ctl = at<EngineCtl>(b, L.ctl);
+    auto fill = [&](auto& P, auto* slot0, auto* slot1, auto* hub0, auto* hub1) {
+        memset(&P, 0, sizeof(P));
+        P.tau = A.tau;
+        P.hub_thr = A.tau;
+        P.seeds = A.seeds;
+        P.slots[0] = slot0;
+        P.slots[1] = slot1;
+        P.nslots = A.D.nslots;
+        P.lambda = A.lambda;
+        P.sigma = A.sigma;
+        P.hub_item[0] = hub0;
+        P.hub_item[1] = hub1;
+        P.hub_beg[0] = at<int32_t>(b, L.hub_beg0);
+        P.hub_beg[1] = at<int32_t>(b, L.hub_beg1);
+        P.hub_deg[0] = at<int32_t>(b, L.hub_deg0);
+        P.hub_deg[1] = at<int32_t>(b, L.hub_deg1);
+        P.hub_segbase[0] = at<long long>(b, L.hub_sb0);
+        P.hub_segbase[1] = at<long long>(b, L.hub_sb1);
+        P.hub_cap = A.D.hub_cap;
+        P.segmap[0] = at<int32_t>(b, L.segmap0);
+        P.segmap[1] = at<int32_t>(b, L.segmap1);
+        P.segmap_cap = A.D.segmap_cap;
+        P.ctl = ctl;
+    };
+    // the two hash-bag slot arrays hold 64-bit pair items or, viewed as 32-bit
+    // slots, vertex items (both sentinels are all-ones bytes)
+    fill(W.P32, at<uint32_t>(b, L.slots0), at<uint32_t>(b, L.slots1), at<uint32_t>(b, L.hub_item0),
+         at<uint32_t>(b, L.hub_item1));
+    fill(W.P64, at<uint64_t>(b, L.slots0), at<uint64_t>(b, L.slots1), at<uint64_t>(b, L.hub_item0),
+         at<uint64_t>(b, L.hub_item1));
+}
+
+// ------------------------------------------------------------- block helpers --
+struct BlockShared {
+    int graph;
+    int wsum[kBatchMaxBlock / 32];
+    long long carry;
+    long long count;
+    unsigned long long acc;
+};
+
+// Sum over the block (every thread gets the total).
+__device__ unsigned long long block_sum(unsigned long long x, BlockShared& sh) {
+    for (int d = 16; d >= 1; d >>= 1) x += __shfl_xor_sync(kFull, x, d);
+    __syncthreads();
+    if (threadIdx.x == 0) sh.acc = 0;
+    __syncthreads();
+    if (lane_id() == 0 && x) atomicAdd(&sh.acc, x);
+    __syncthreads();
+    const unsigned long long t = sh.acc;
+    __syncthreads();
+    return t;
+}
+
+// Exclusive scan in place of a[0..n) (int32), a[n] = total: tiles of 4 values
+// per thread, a block scan per tile, a running carry.
+__device__ void block_exclusive_scan(int32_t* a, long long n, BlockShared& sh) {
+    const int nw = blockDim.x >> 5;
+    if (threadIdx.x == 0) sh.carry = 0;
+    __syncthreads();
+    for (long long base = 0; base < n; base += 4ll * blockDim.x) {
+        const long long i0 = base + 4ll * threadIdx.x;
+        int v[4];
+        int s = 0;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            v[j] = i0 + j < n ? a[i0 + j] : 0;
+            s += v[j];
+        }
+        const int incl = warp_incl_scan(s);
+        if (lane_id() == 31) sh.wsum[threadIdx.x >> 5] = incl;
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            const int x = threadIdx.x < nw ? sh.wsum[threadIdx.x] : 0;
+            const int y = warp_incl_scan(x);
+            if (threadIdx.x < nw) sh.wsum[threadIdx.x] = y - x;
+        }
+        __syncthreads();
+        long long run = sh.carry + sh.wsum[threadIdx.x >> 5] + (incl - s);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            if (i0 + j < n) a[i0 + j] = (int32_t)run;
+            run += v[j];
+        }
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1) sh.carry = run;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) a[n] = (int32_t)sh.carry;
+    __syncthreads();
+}
+
+// Largest r in [0, n) with off[r] <= e.
+__device__ __forceinline__ int row_of(const int32_t* off, int n, long long e) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if ((long long)off[mid] <= e) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// ------------------------------------------------------------- initial items --
+struct InitVertex {
+    uint32_t v;
+    __device__ __forceinline__ uint32_t operator()(long long) const { return v; }
+};
+
+// ------------------------------------------------------------ one graph --
+// Returns false after an error (recorded in *A.err): the block stops.
+__device__ bool scc_one_graph(const BatchArgs& A, Ws& W, int g, BlockShared& sh,
+                              const LocalQueue<uint32_t>& q32, const LocalQueue<uint64_t>& q64, uint32_t& gr,
+                              uint32_t& si, uint32_t& tagc) {
+    const long long vb = A.vbase[g];
+    const int n = (int)(A.vbase[g + 1] - vb);
+    const long long eb = A.ebase[g];
+    const long long m = A.ebase[g + 1] - eb;
+    const int32_t* off = A.offsets + vb + g;
+    const int32_t* adj = A.targets + eb;
+    int32_t* out = A.labels + vb;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    if (n == 0) return true;
+
+    // ---- 1. G^T: in-degrees, scan, placement
+    for (int v = tid; v <= n; v += nt) W.cnt[v] = 0;
+    __syncthreads();
+    for (long long e = tid; e < m; e += nt) atomicAdd(&W.cnt[adj[e]], 1);
+    __syncthreads();
+    block_exclusive_scan(W.cnt, n, sh);
+    for (int v = tid; v <= n; v += nt) W.toff[v] = W.cnt[v];
+    __syncthreads();
+    {
+        // 16 consecutive arcs per thread: one row search, then a forward walk
+        constexpr int kC = 16;
+        for (long long e0 = (long long)tid * kC; e0 < m; e0 += (long long)nt * kC) {
+            const long long e1 = min(e0 + kC, m);
+            int u = row_of(off, n, e0);
+            for (long long e = e0; e < e1; ++e) {
+                while ((long long)off[u + 1] <= e) ++u;
+                const int w = adj[e];
+                W.tadj[atomicAdd(&W.cnt[w], 1)] = u;
+            }
+        }
+    }
+    __syncthreads();
+
+    // ---- 2. trimming; 3. active list (ordered) for the pivot permutation
+    unsigned long long na = 0;
+    for (int v = tid; v < n; v += nt) {
+        const bool t = off[v + 1] == off[v] || W.toff[v + 1] == W.toff[v];
+        W.label[v] = t ? kDone : 0;
+        W.rep[v] = v;
+        W.cnt[v] = t ? 0 : 1;
+        na += t ? 0 : 1;
+    }
+    __syncthreads();
+    na = block_sum(na, sh);
+    if (na > 0) {
+        block_exclusive_scan(W.cnt, n, sh);
+        for (int v = tid; v < n; v += nt)
+            if (W.label[v] == 0) W.act[W.cnt[v]] = v;
+    }
+    __syncthreads();
+    long long active = (long long)na;
+    Feistel perm;
+    perm.init(A.seed, (uint64_t)max(na, 1ull));
+
+    // ---- 4. the first SCC from the first pivot
+    if (na > 0) {
+        const int p0 = W.act[perm.perm(0, na)];
+        const int words = (n + 31) / 32;
+        for (int w = tid; w < words; w += nt) {
+            uint32_t m0 = 0;
+            for (int j = 0; j < 32; ++j) {
+                const int v = w * 32 + j;
+                if (v >= n || W.label[v] < 0) m0 |= 1u << j;  // outside the class: pre-visited
+            }
+            W.bits_f[w] = m0;
+            W.bits_b[w] = m0;
+        }
+        __syncthreads();
+        for (int d = 0; d < 2; ++d) {
+            EngineParams<uint32_t> P = W.P32;
+            P.off = d == 0 ? off : W.toff;
+            P.adj = d == 0 ? adj : W.tadj;
+            P.n = n;
+            PolSingle pol{d == 0 ? W.bits_f : W.bits_b};
+            WarpStats ws;
+            int why = 0;
+            if (!engine_search<PolSingle, InitVertex, CtaScope>(P, pol, InitVertex{(uint32_t)p0}, 1, nullptr, q32, ws,
+                                                                  gr, si, why))
+                return false;
+            ++si;
+            if (why != 0) {  // the hash bag is sized so that this never happens
+                if (tid == 0) atomicCAS(A.err, 0, why < 0 ? why : SCC_ERR_INTERNAL);
+                return false;
+            }
+        }
+        unsigned long long c = 0;
+        for (int v = tid; v < n; v += nt) {
+            if (W.label[v] != 0) continue;
+            const bool f = (W.bits_f[v >> 5] >> (v & 31)) & 1u, b = (W.bits_b[v >> 5] >> (v & 31)) & 1u;
+            if (f && b) {
+                W.label[v] = kDone;
+                W.rep[v] = p0;
+                ++c;
+            } else if (f || b) {
+                W.label[v] = class_hash(0, f ? p0 : -1, b ? p0 : -1);
+            }
+        }
+        active -= (long long)block_sum(c, sh);
+    }
+
+    // ---- 5. trimming inside the classes: a vertex with no arc from or no arc
+    // to an active vertex of its own class is a singleton
+    for (int pass = 0; pass < kBatchTrimPasses && active > 0; ++pass) {
+        unsigned long long c = 0;
+        for (int v = tid; v < n; v += nt) {
+            const int32_t L = ld_volatile(&W.label[v]);
+            if (L < 0) continue;
+            bool out_ok = false, in_ok = false;
+            for (int e = off[v]; e < off[v + 1] && !out_ok; ++e) {
+                const int w = adj[e];
+                out_ok = w != v && ld_volatile(&W.label[w]) == L;
+            }
+            if (out_ok)
+                for (int e = W.toff[v]; e < W.toff[v + 1] && !in_ok; ++e) {
+                    const int w = W.tadj[e];
+                    in_ok = w != v && ld_volatile(&W.label[w]) == L;
+                }
+            if (!(out_ok && in_ok)) {
+                W.label[v] = kDone;
+                W.rep[v] = v;
+                ++c;
+            }
+        }
+        const unsigned long long got = block_sum(c, sh);
+        active -= (long long)got;
+        if ((long long)got * 32 < active) break;
+    }
+
+    // ---- 6. prefix-doubling batches over the pivot order
+    long long lo = 1;
+    double width = A.beta;
+    long long a_prev[2] = {0, 0};
+    long long cap_floor = 0;  // table size forced by a retried batch
+    while (lo < (long long)na && active > 0) {
+        long long hi = width >= (double)na ? (long long)na : min((long long)na, lo + (long long)ceil(width));
+        for (;;) {
+            // sources: the still-active vertices at positions [lo, hi)
+            if (tid == 0) sh.count = 0;
+            __syncthreads();
+            for (long long p = lo + tid; p < hi; p += nt) {
+                const int v = W.act[perm.perm((uint64_t)p, na)];
+                if (ld_volatile(&W.label[v]) >= 0) W.src[atomicAdd((unsigned long long*)&sh.count, 1ull)] = v;
+            }
+            __syncthreads();
+            const long long k = sh.count;
+            __syncthreads();
+            if (k == 0) break;
+            // table sizes (Sec. 4.5 heuristic, capped by the slice)
+            long long cap[2];
+            for (int d = 0; d < 2; ++d) {
+                long long want = max((long long)ceil(0.3 * (double)active), (long long)ceil(1.5 * (double)a_prev[d]));
+                want = max(want, k);
+                long long c2 = kBatchMinTable;
+                while (c2 < 2 * want && c2 < A.D.tcap) c2 <<= 1;
+                cap[d] = min(max(c2, cap_floor), A.D.tcap);
+            }
+            EngineParams<uint64_t> P = W.P64;
+            P.off = off;
+            P.adj = adj;
+            P.off2 = W.toff;
+            P.adj2 = W.tadj;
+            P.n = n;
+            SearchCtl& sc = W.P64.ctl->search[si % 3];
+            PolPair pol;
+            pol.label = W.label;
+            pol.keys[0] = W.tab0;
+            pol.keys[1] = W.tab1;
+            for (int d = 0; d < 2; ++d) {
+                pol.mask[d] = (unsigned long long)(cap[d] - 1);
+                pol.max_ins[d] = (long long)(0.75 * (double)cap[d]);
+            }
+            pol.overflow = &sc.overflow;
+            pol.ins0 = pol.ins1 = 0;
+            WarpStats ws;
+            int why = 0;  // 1: a table overflowed; < 0: error (same in every thread)
+            if (!engine_search<PolPair, InitPairs, CtaScope>(P, pol, InitPairs{W.src, k}, 2 * k, nullptr, q64, ws, gr,
+                                                             si, why))
+                return false;
+            ++si;
+            const long long pairs0 = (long long)ld_volatile(&sc.inserted[0]);
+            const long long pairs1 = (long long)ld_volatile(&sc.inserted[1]);
+            __syncthreads();
+            if (why < 0) {  // the hash bag is sized so that this never happens
+                if (tid == 0) atomicCAS(A.err, 0, why);
+                return false;
+            }
+            if (why == 1) {
+                // the search stopped early: empty both tables and the used part of
+                // both hash-bag slot arrays, then grow the tables or, at full
+                // size, halve the batch
+                for (long long i = tid; i < cap[0]; i += nt) W.tab0[i] = ~0ull;
+                for (long long i = tid; i < cap[1]; i += nt) W.tab1[i] = ~0ull;
+                const long long used = chunk_end(A.lambda, ld_volatile(&W.P64.ctl->max_chunk), A.D.nslots);
+                for (long long i = tid; i < used; i += nt) {
+                    W.P64.slots[0][i] = ~0ull;
+                    W.P64.slots[1][i] = ~0ull;
+                }
+                __syncthreads();
+                const long long c = max(cap[0], cap[1]);
+                if (c < A.D.tcap) {
+                    cap_floor = 2 * c;
+                } else if (hi - lo > 1) {
+                    hi = lo + (hi - lo) / 2;
+                } else {
+                    if (tid == 0) atomicCAS(A.err, 0, SCC_ERR_CAPACITY);
+                    return false;
+                }
+                continue;
+            }
+            // labelling (Alg. 1; Sec. 4.4), which also empties both tables
+            ++tagc;
+            const unsigned long long tag = (unsigned long long)tagc << 32;
+            const PairTable tb{W.tab1, (unsigned long long)(cap[1] - 1), nullptr};
+            label_scan(tid, nt, W.tab0, cap[0], tb, tag, W.fmax, W.bmax, W.hit);
+            __syncthreads();
+            const unsigned long long c = label_finalize(tid, nt, W.tab0, cap[0], W.tab1, cap[1], tag, W.fmax, W.bmax,
+                                                        W.hit, W.label, W.rep, true);
+            active -= (long long)block_sum(c, sh);
+            a_prev[0] = pairs0;
+            a_prev[1] = pairs1;
+            cap_floor = 0;
+            break;
+        }
+        if (width < (double)na) width *= A.beta;
+        lo = hi;
+    }
+
+    // ---- 7. canonical labels: the smallest vertex of each SCC (by its rep)
+    for (int v = tid; v < n; v += nt) W.cnt[v] = INT_MAX;
+    __syncthreads();
+    for (int v = tid; v < n; v += nt) atomicMin(&W.cnt[W.rep[v]], v);
+    __syncthreads();
+    for (int v = tid; v < n; v += nt) out[v] = W.cnt[W.rep[v]];
+    __syncthreads();
+    return true;
+}
+
+__global__ void k_batch_reset(int* next, int* err) {
+    *next = 0;
+    *err = 0;
+}
+
+// Dynamic shared memory: the warps' local queues, sized for the larger of the
+// two item kinds (pairs: 8 B item + 8 B range + 4 B label per entry).
+constexpr int kBQ = 256;  // = PolPair::kQueue = PolSingle::kQueue
+static_assert(PolPair::kQueue == kBQ && PolSingle::kQueue == kBQ, "one queue size for both searches");
+size_t batch_smem_bytes(int block) { return (size_t)(block / 32) * kBQ * (8 + 8 + 4); }
+
+__global__ void __launch_bounds__(kBatchMaxBlock, 1) k_batch_scc(BatchArgs A) {
+    extern __shared__ unsigned char dsm[];
+    __shared__ BlockShared sh;
+    const int nw = blockDim.x >> 5, w = threadIdx.x >> 5;
+    // queues of the two searches overlay the same bytes (never live together)
+    LocalQueue<uint64_t> q64{reinterpret_cast<uint64_t*>(dsm) + w * kBQ,
+                             reinterpret_cast<int2*>(dsm + (size_t)nw * kBQ * 8) + w * kBQ,
+                             reinterpret_cast<int32_t*>(dsm + (size_t)nw * kBQ * 16) + w * kBQ};
+    LocalQueue<uint32_t> q32{reinterpret_cast<uint32_t*>(dsm) + w * kBQ,
+                             reinterpret_cast<int2*>(dsm + (size_t)nw * kBQ * 8) + w * kBQ, nullptr};
+    Ws W;
+    bind_ws(A, W);
+    // a fresh engine control block for this launch
+    {
+        uint32_t* c = reinterpret_cast<uint32_t*>(W.P64.ctl);
+        for (size_t i = threadIdx.x; i < sizeof(EngineCtl) / 4; i += blockDim.x) c[i] = 0;
+    }
+    __syncthreads();
+    // labelling tags (the high word of the per-vertex maxima) must never repeat
+    // while a stale maximum could carry them: the counter lives in the slice
+    uint32_t gr = 0, si = 0, tagc = ld_volatile(W.tag);
+    for (;;) {
+        if (threadIdx.x == 0) {
+            const int i = atomicAdd(A.next, 1);
+            sh.graph = (i < A.norder && ld_volatile(A.err) == 0) ? A.order[i] : -1;
+        }
+        __syncthreads();
+        const int g = sh.graph;
+        __syncthreads();
+        if (g < 0) break;
+        if (!scc_one_graph(A, W, g, sh, q32, q64, gr, si, tagc)) break;
+    }
+    if (threadIdx.x == 0) *W.tag = tagc;
+}
+
+// Fresh slices: everything zero except the tables and the hash-bag slot
+// arrays, which start empty (all-ones).
+__global__ void k_batch_init_ws(unsigned char* ws, size_t stride, int blocks, WsLayout L, BatchDims d) {
+    const size_t t0 = (size_t)blockIdx.x * blockDim.x + threadIdx.x, ts = (size_t)gridDim.x * blockDim.x;
+    for (int b = 0; b < blocks; ++b) {
+        unsigned char* base = ws + stride * (size_t)b;
+        unsigned long long* regions[4] = {reinterpret_cast<unsigned long long*>(base + L.tab0),
+                                          reinterpret_cast<unsigned long long*>(base + L.tab1),
+                                          reinterpret_cast<unsigned long long*>(base + L.slots0),
+                                          reinterpret_cast<unsigned long long*>(base + L.slots1)};
+        const size_t len[4] = {(size_t)d.tcap, (size_t)d.tcap, (size_t)d.nslots, (size_t)d.nslots};
+        for (int r = 0; r < 4; ++r)
+            for (size_t i = t0; i < len[r]; i += ts) regions[r][i] = ~0ull;
+    }
+}
+
+}  // namespace
+}  // namespace scc
+
+// ---------------------------------------------------------------- host side --
+using scc::BatchDims;
+using scc::DeviceInfo;
+using scc::WsLayout;
+
+struct scc_batch {
+    DeviceInfo di;
+    int32_t G = 0;
+    long long nv = 0, na = 0;
+    long long n_max = 0, m_max = 0;
+    long long* vbase = nullptr;
+    long long* ebase = nullptr;
+    int32_t* offsets = nullptr;
+    int32_t* targets = nullptr;
+    int32_t* order = nullptr;       // all graphs, largest first
+    std::vector<int32_t> order_h;
+    std::vector<long long> vb_h, eb_h;
+    int* flags = nullptr;           // [0] work-queue head, [1] error
+    int32_t* labels = nullptr;      // internal output (host destinations, tuning)
+    scc_batch_config cfg;
+    // working memory for the current configuration
+    unsigned char* ws = nullptr;
+    size_t ws_bytes = 0;
+    size_t ws_stride = 0;
+    int blocks = 0;
+    WsLayout L;
+    BatchDims D;
+    // captured launch
+    cudaGraphExec_t exec = nullptr;
+    int32_t* exec_out = nullptr;
+    const int32_t* exec_order = nullptr;
+    int exec_norder = -1;
+    bool exec_valid = false;
+    scc_batch_stats st;
+};
+
+namespace scc {
+namespace {
+
+bool valid_config(const scc_batch_config* c) {
+    if (!c) return false;
+    if (c->tau < 1 || c->tau > 65536) return false;
+    if (c->block != 128 && c->block != 256 && c->block != 512) return false;
+    if (c->lambda < 256 || c->lambda > 65536 || (c->lambda & (c->lambda - 1))) return false;
+    if (c->sigma < 1 || c->seeds < 1 || c->seeds > 32) return false;
+    if (!(c->beta > 1.0 && c->beta <= 64.0)) return false;
+    if (c->blocks_per_sm < 0 || c->blocks_per_sm > 16) return false;
+    return true;
+}
+
+void drop_exec(scc_batch* h) {
+    if (h->exec) cudaGraphExecDestroy(h->exec);
+    h->exec = nullptr;
+    h->exec_valid = false;
+}
+
+// Working memory for the current configuration: one slice per block, sized for
+// the largest graph, within a budget of device memory.
+int prepare(scc_batch* h, cudaStream_t s) {
+    BatchDims d;
+    d.n_max = std::max<long long>(h->n_max, 1);
+    d.m_max = std::max<long long>(h->m_max, 1);
+    long long t = kBatchMinTable;
+    while (t < 2 * d.n_max) t <<= 1;  // one source never fills 3/4 of a table
+    d.tcap = t;
+    // the bag holds a round's new items: at most the capacity of each table
+    // (pairs; a round may pass the 3/4 load limit before it stops) or the
+    // vertices (single-reachability); four times that in slots
+    const long long items = 2 * d.tcap + 1024;
+    d.nslots = ((std::max<long long>(4 * items, 4ll * h->cfg.lambda) + kSeg - 1) / kSeg) * kSeg;
+    d.hub_cap = (int)std::min<long long>(items, 8192);
+    d.segmap_cap = 2 * (d.m_max / kHubSeg) + d.hub_cap + 1024;
+    WsLayout L = make_layout(d);
+    int per_sm = 0;
+    const size_t smem = batch_smem_bytes(h->cfg.block);
+    SCC_CUDA(cudaFuncSetAttribute(k_batch_scc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    SCC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_scc, h->cfg.block, smem));
+    if (per_sm < 1) return SCC_ERR_INVALID_ARG;
+    if (h->cfg.blocks_per_sm > 0) per_sm = std::min(per_sm, h->cfg.blocks_per_sm);
+    size_t free_b = 0, total_b = 0;
+    SCC_CUDA(cudaMemGetInfo(&free_b, &total_b));
+    const size_t budget = std::min<size_t>(free_b / 2, (size_t)96 << 30);
+    long long blocks = (long long)per_sm * h->di.num_sms;
+    blocks = std::min<long long>(blocks, std::max<long long>(1, (long long)(budget / L.bytes)));
+    blocks = std::min<long long>(blocks, std::max<int32_t>(h->G, 1));
+    const size_t need = L.bytes * (size_t)blocks;
+    if (h->ws && (h->ws_bytes < need)) {
+        dfree(h->ws, s);
+        h->ws = nullptr;
+        h->ws_bytes = 0;
+    }
+    if (!h->ws) {
+        SCC_TRY(dalloc(reinterpret_cast<void**>(&h->ws), need, s));
+        h->ws_bytes = need;
+    }
+    // every slice starts with empty bags and tables and untagged maxima
+    SCC_CUDA(cudaMemsetAsync(h->ws, 0, need, s));
+    k_batch_init_ws<<<h->di.num_sms * 4, 256, 0, s>>>(h->ws, L.bytes, (int)blocks, L, d);
+    SCC_LAUNCH();
+    h->ws_stride = L.bytes;
+    h->blocks = (int)blocks;
+    h->L = L;
+    h->D = d;
+    h->st.blocks = h->blocks;
+    h->st.workspace_bytes = (int64_t)need;
+    return SCC_OK;
+}
+
+BatchArgs make_args(scc_batch* h, const int32_t* order, int norder, int32_t* out) {
+    BatchArgs A;
+    memset(&A, 0, sizeof(A));
+    A.G = h->G;
+    A.vbase = h->vbase;
+    A.ebase = h->ebase;
+    A.offsets = h->offsets;
+    A.targets = h->targets;
+    A.order = order;
+    A.norder = norder;
+    A.labels = out;
+    A.next = h->flags;
+    A.err = h->flags + 1;
+    A.ws = h->ws;
+    A.ws_stride = h->ws_stride;
+    A.L = h->L;
+    A.D = h->D;
+    A.tau = h->cfg.tau;
+    A.seeds = h->cfg.seeds;
+    A.lambda = h->cfg.lambda;
+    A.sigma = h->cfg.sigma;
+    A.beta = h->cfg.beta;
+    A.seed = h->cfg.seed;
+    return A;
+}
+
+int enqueue(scc_batch* h, const int32_t* order, int norder, int32_t* out, cudaStream_t s) {
+    BatchArgs A = make_args(h, order, norder, out);
+    k_batch_reset<<<1, 1, 0, s>>>(h->flags, h->flags + 1);
+    SCC_LAUNCH();
+    k_batch_scc<<<h->blocks, h->cfg.block, batch_smem_bytes(h->cfg.block), s>>>(A);
+    SCC_LAUNCH();
+    return SCC_OK;
+}
+
+// Capture the reset and the persistent kernel as one CUDA graph.
+int capture(scc_batch* h, const int32_t* order, int norder, int32_t* out) {
+    drop_exec(h);
+    cudaStream_t cs;
+    SCC_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaGraph_t graph = nullptr;
+    int rc = cuda_err(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    if (rc == SCC_OK) {
+        BatchArgs A = make_args(h, order, norder, out);
+        k_batch_reset<<<1, 1, 0, cs>>>(h->flags, h->flags + 1);
+        k_batch_scc<<<h->blocks, h->cfg.block, batch_smem_bytes(h->cfg.block), cs>>>(A);
+        rc = cuda_err(cudaGetLastError());
+        const int rc2 = cuda_err(cudaStreamEndCapture(cs, &graph));
+        if (rc == SCC_OK) rc = rc2;
+    }
+    if (rc == SCC_OK) rc = cuda_err(cudaGraphInstantiate(&h->exec, graph, 0));
+    if (graph) cudaGraphDestroy(graph);
+    cudaStreamDestroy(cs);
+    SCC_TRY(rc);
+    h->exec_out = out;
+    h->exec_order = order;
+    h->exec_norder = norder;
+    h->exec_valid = true;
+    h->st.captures++;
+    return SCC_OK;
+}
+
+// One run over `order` into `out` (device), timed with CUDA events.
+int run_order(scc_batch* h, const int32_t* order, int norder, int32_t* out, cudaStream_t s, double* ms) {
+    if (!h->ws) SCC_TRY(prepare(h, s));
+    cudaStreamCaptureStatus cst = cudaStreamCaptureStatusNone;
+    SCC_CUDA(cudaStreamIsCapturing(s, &cst));
+    if (cst != cudaStreamCaptureStatusNone) {
+        // the caller is capturing: add the launches to the caller's graph
+        return enqueue(h, order, norder, out, s);
+    }
+    if (!h->exec_valid || h->exec_out != out || h->exec_order != order || h->exec_norder != norder)
+        SCC_TRY(capture(h, order, norder, out));
+    cudaEvent_t e0, e1;
+    SCC_CUDA(cudaEventCreate(&e0));
+    SCC_CUDA(cudaEventCreate(&e1));
+    cudaEventRecord(e0, s);
+    cudaError_t le = cudaGraphLaunch(h->exec, s);
+    cudaEventRecord(e1, s);
+    count_launch();  // the reset kernel
+    count_launch();  // the persistent kernel
+    int herr = 0;
+    cudaError_t ce = cudaMemcpyAsync(&herr, h->flags + 1, sizeof(int), cudaMemcpyDeviceToHost, s);
+    cudaError_t se = cudaStreamSynchronize(s);
+    float f = 0;
+    cudaEventElapsedTime(&f, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    SCC_CUDA(le);
+    SCC_CUDA(ce);
+    SCC_CUDA(se);
+    h->st.replays++;
+    h->st.ms_last_run = f;
+    if (ms) *ms = f;
+    return herr ? herr : SCC_OK;
+}
+
+void batch_free(scc_batch* h, cudaStream_t s) {
+    drop_exec(h);
+    dfree(h->ws, s);
+    dfree(h->vbase, s);
+    dfree(h->ebase, s);
+    dfree(h->offsets, s);
+    dfree(h->targets, s);
+    dfree(h->order, s);
+    dfree(h->flags, s);
+    dfree(h->labels, s);
+}
+
+__global__ void k_batch_validate(int32_t G, const long long* vbase, const long long* ebase, const int32_t* off,
+                                 const int32_t* adj, int* bad) {
+    for (int g = blockIdx.x; g < G; g += gridDim.x) {
+        const long long n = vbase[g + 1] - vbase[g];
+        const long long m = ebase[g + 1] - ebase[g];
+        const int32_t* o = off + vbase[g] + g;
+        const int32_t* a = adj + ebase[g];
+        if (threadIdx.x == 0 && (o[0] != 0 || (long long)o[n] != m)) atomicExch(bad, 1);
+        for (long long v = threadIdx.x; v < n; v += blockDim.x)
+            if (o[v] > o[v + 1]) atomicExch(bad, 1);
+        for (long long e = threadIdx.x; e < m; e += blockDim.x)
+            if (a[e] < 0 || (long long)a[e] >= n) atomicExch(bad, 1);
+    }
+}
+
+int batch_create_impl(scc_batch* h, int32_t G, const int64_t* vbase, const int64_t* ebase, const int32_t* offsets,
+                      const int32_t* targets, cudaStream_t s) {
+    SCC_TRY(device_info(&h->di));
+    h->G = G;
+    // bases on the host (sizes, processing order) and on the device
+    h->vb_h.resize((size_t)G + 1);
+    h->eb_h.resize((size_t)G + 1);
+    SCC_CUDA(cudaMemcpyAsync(h->vb_h.data(), vbase, sizeof(long long) * ((size_t)G + 1), cudaMemcpyDefault, s));
+    SCC_CUDA(cudaMemcpyAsync(h->eb_h.data(), ebase, sizeof(long long) * ((size_t)G + 1), cudaMemcpyDefault, s));
+    SCC_CUDA(cudaStreamSynchronize(s));
+    if (h->vb_h[0] != 0 || h->eb_h[0] != 0) return SCC_ERR_INVALID_ARG;
+    for (int32_t g = 0; g < G; ++g) {
+        const long long n = h->vb_h[g + 1] - h->vb_h[g], m = h->eb_h[g + 1] - h->eb_h[g];
+        if (n < 0 || m < 0 || n > (1ll << 30) || m > (long long)INT32_MAX) return SCC_ERR_INVALID_ARG;
+        h->n_max = std::max(h->n_max, n);
+        h->m_max = std::max(h->m_max, m);
+    }
+    h->nv = h->vb_h[G];
+    h->na = h->eb_h[G];
+    SCC_TRY(dalloc_t(&h->vbase, (size_t)G + 1, s));
+    SCC_TRY(dalloc_t(&h->ebase, (size_t)G + 1, s));
+    SCC_TRY(dalloc_t(&h->offsets, (size_t)(h->nv + G) + 1, s));
+    SCC_TRY(dalloc_t(&h->targets, (size_t)h->na + 1, s));
+    SCC_TRY(dalloc_t(&h->flags, 2, s));
+    SCC_TRY(dalloc_t(&h->labels, (size_t)h->nv + 1, s));
+    SCC_CUDA(cudaMemcpyAsync(h->vbase, h->vb_h.data(), sizeof(long long) * ((size_t)G + 1), cudaMemcpyHostToDevice, s));
+    SCC_CUDA(cudaMemcpyAsync(h->ebase, h->eb_h.data(), sizeof(long long) * ((size_t)G + 1), cudaMemcpyHostToDevice, s));
+    if (h->nv + G > 0)
+        SCC_CUDA(cudaMemcpyAsync(h->offsets, offsets, sizeof(int32_t) * (size_t)(h->nv + G), cudaMemcpyDefault, s));
+    if (h->na > 0)
+        SCC_CUDA(cudaMemcpyAsync(h->targets, targets, sizeof(int32_t) * (size_t)h->na, cudaMemcpyDefault, s));
+    int* bad = nullptr;
+    SCC_TRY(dalloc_t(&bad, 1, s));
+    SCC_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), s));
+    if (G > 0) {
+        k_batch_validate<<<std::min<int32_t>(G, 65535), 256, 0, s>>>(G, h->vbase, h->ebase, h->offsets, h->targets,
+                                                                     bad);
+        SCC_LAUNCH();
+    }
+    int hbad = 0;
+    SCC_CUDA(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
+    SCC_CUDA(cudaStreamSynchronize(s));
+    dfree(bad, s);
+    if (hbad) return SCC_ERR_INVALID_ARG;
+    // processing order: decreasing work (arcs + vertices), so long graphs start first
+    h->order_h.resize((size_t)G);
+    for (int32_t g = 0; g < G; ++g) h->order_h[g] = g;
+    std::stable_sort(h->order_h.begin(), h->order_h.end(), [&](int32_t a, int32_t b) {
+        const long long wa = (h->eb_h[a + 1] - h->eb_h[a]) + (h->vb_h[a + 1] - h->vb_h[a]);
+        const long long wb = (h->eb_h[b + 1] - h->eb_h[b]) + (h->vb_h[b + 1] - h->vb_h[b]);
+        return wa > wb;
+    });
+    SCC_TRY(dalloc_t(&h->order, (size_t)G + 1, s));
+    if (G > 0)
+        SCC_CUDA(cudaMemcpyAsync(h->order, h->order_h.data(), sizeof(int32_t) * (size_t)G, cudaMemcpyHostToDevice, s));
+    SCC_CUDA(cudaStreamSynchronize(s));
+    memset(&h->st, 0, sizeof(h->st));
+    h->st.graphs = G;
+    h->st.vertices = h->nv;
+    h->st.arcs = h->na;
+    h->st.max_vertices = (int32_t)h->n_max;
+    h->st.max_arcs = h->m_max;
+    return SCC_OK;
+}
+
+}  // namespace
+}  // namespace scc
+
+using namespace scc;
+
+extern "C" {
+
+SCC_API int scc_batch_config_default(scc_batch_config* cfg) {
+    if (!cfg) return SCC_ERR_INVALID_ARG;
+    cfg->tau = 512;
+    cfg->block = 256;
+    cfg->lambda = 4096;
+    cfg->sigma = 50;
+    cfg->seeds = 32;
+    cfg->beta = 2.0;
+    cfg->blocks_per_sm = 0;
+    cfg->seed = 0x5CC00;
+    return SCC_OK;
+}
+
+SCC_API int scc_batch_create(int32_t G, const int64_t* vbase, const int64_t* ebase, const int32_t* offsets,
+                             const int32_t* targets, cudaStream_t stream, scc_batch_handle* out) {
+    if (!out || G < 0 || !vbase || !ebase) return SCC_ERR_INVALID_ARG;
+    *out = nullptr;
+    scc_batch* h = new (std::nothrow) scc_batch();
+    if (!h) return SCC_ERR_OOM;
+    scc_batch_config_default(&h->cfg);
+    int rc = batch_create_impl(h, G, vbase, ebase, offsets, targets, stream);
+    if (rc == SCC_OK && ((h->nv + G > 0 && !offsets) || (h->na > 0 && !targets))) rc = SCC_ERR_INVALID_ARG;
+    if (rc != SCC_OK) {
+        cudaStreamSynchronize(stream);
+        batch_free(h, stream);
+        cudaStreamSynchronize(stream);
+        delete h;
+        return rc;
+    }
+    *out = h;
+    return SCC_OK;
+}
+
+SCC_API int scc_batch_destroy(scc_batch_handle h) {
+    if (!h) return SCC_ERR_INVALID_ARG;
+    cudaDeviceSynchronize();
+    batch_free(h, 0);
+    cudaDeviceSynchronize();
+    delete h;
+    return SCC_OK;
+}
+
+SCC_API int scc_batch_set_config(scc_batch_handle h, const scc_batch_config* cfg) {
+    if (!h || !valid_config(cfg)) return SCC_ERR_INVALID_ARG;
+    const bool relayout = cfg->block != h->cfg.block || cfg->lambda != h->cfg.lambda ||
+                          cfg->blocks_per_sm != h->cfg.blocks_per_sm;
+    h->cfg = *cfg;
+    drop_exec(h);
+    if (relayout && h->ws) {
+        cudaDeviceSynchronize();
+        dfree(h->ws, 0);
+        cudaDeviceSynchronize();
+        h->ws = nullptr;
+        h->ws_bytes = 0;
+    }
+    return SCC_OK;
+}
+
+SCC_API int scc_batch_get_config(scc_batch_handle h, scc_batch_config* cfg) {
+    if (!h || !cfg) return SCC_ERR_INVALID_ARG;
+    *cfg = h->cfg;
+    return SCC_OK;
+}
+
+SCC_API int scc_batch_run(scc_batch_handle h, int32_t* labels_out, cudaStream_t stream) {
+    if (!h || (!labels_out && h->nv > 0)) return SCC_ERR_INVALID_ARG;
+    if (h->G == 0 || h->nv == 0) return SCC_OK;
+    const bool dev_out = is_device_ptr(labels_out);
+    int32_t* dst = dev_out ? labels_out : h->labels;
+    SCC_TRY(run_order(h, h->order, h->G, dst, stream, nullptr));
+    if (!dev_out) {
+        SCC_CUDA(cudaMemcpyAsync(labels_out, h->labels, sizeof(int32_t) * (size_t)h->nv, cudaMemcpyDeviceToHost, stream));
+        SCC_CUDA(cudaStreamSynchronize(stream));
+    }
+    return SCC_OK;
+}
+
+SCC_API int scc_batch_autotune(scc_batch_handle h, int32_t sample, cudaStream_t stream, scc_batch_config* best,
+                               double* best_ms) {
+    if (!h) return SCC_ERR_INVALID_ARG;
+    const scc_batch_config base = h->cfg;
+    if (h->G == 0) {
+        if (best) *best = base;
+        if (best_ms) *best_ms = 0;
+        return SCC_OK;
+    }
+    // the sample: every k-th graph of the size order, so it spans the size range
+    std::vector<int32_t> sub;
+    const int32_t want = (sample <= 0 || sample >= h->G) ? h->G : sample;
+    const double step = (double)h->G / (double)want;
+    for (int32_t i = 0; i < want; ++i) sub.push_back(h->order_h[(size_t)std::min<double>(h->G - 1, i * step)]);
+    int32_t* dsub = nullptr;
+    SCC_TRY(dalloc_t(&dsub, sub.size(), stream));
+    SCC_CUDA(cudaMemcpyAsync(dsub, sub.data(), sizeof(int32_t) * sub.size(), cudaMemcpyHostToDevice, stream));
+    const int taus[] = {16, 64, 256, 1024, 4096};
+    const int blocks[] = {128, 256, 512};
+    const int lambdas[] = {1024, 4096, 16384, 65536};
+    scc_batch_config bc = base;
+    double bms = 1e300;
+    int rc = SCC_OK;
+    for (int blk : blocks) {
+        for (int lam : lambdas) {
+            for (int tau : taus) {
+                scc_batch_config c = base;
+                c.block = blk;
+                c.lambda = lam;
+                c.tau = tau;
+                rc = scc_batch_set_config(h, &c);
+                if (rc != SCC_OK) break;
+                double ms = 0, ms2 = 0;
+                rc = run_order(h, dsub, (int)sub.size(), h->labels, stream, &ms);  // warm-up (and capture)
+                if (rc == SCC_OK) rc = run_order(h, dsub, (int)sub.size(), h->labels, stream, &ms2);
+                if (rc != SCC_OK) break;
+                if (ms2 < bms) {
+                    bms = ms2;
+                    bc = c;
+                }
+            }
+            if (rc != SCC_OK) break;
+        }
+        if (rc != SCC_OK) break;
+    }
+    dfree(dsub, stream);
+    cudaStreamSynchronize(stream);
+    const int rc2 = scc_batch_set_config(h, rc == SCC_OK ? &bc : &base);
+    if (rc != SCC_OK) return rc;
+    if (rc2 != SCC_OK) return rc2;
+    if (best) *best = bc;
+    if (best_ms) *best_ms = bms;
+    return SCC_OK;
+}
+
+SCC_API int scc_batch_get_stats(scc_batch_handle h, scc_batch_stats* out) {
+    if (!h || !out) return SCC_ERR_INVALID_ARG;
+    *out = h->st;
+    return SCC_OK;
+}
+
+}  // extern "C"

@@ -166,16 +166,16 @@ __global__ void __launch_bounds__(256, 2) bgss_kernel(BgssParams B) {
             }
             pol.overflow = &sc.overflow;
             pol.ins0 = pol.ins1 = 0;
-            if (!engine_search<PolPair>(P, pol, InitPairs{B.sources, k}, 2 * (long long)k, nullptr, q, ws, g, si))
+            int why = 0;  // 1: a table overflowed; < 0: error (same in every block)
+            if (!engine_search<PolPair>(P, pol, InitPairs{B.sources, k}, 2 * (long long)k, nullptr, q, ws, g, si,
+                                        why))
                 return;
             ++si;
-            const int ovf = ld_volatile(&sc.overflow);
-            const int err = ld_volatile(&ctl->err);
             pairs[0] = (long long)ld_volatile(&sc.inserted[0]);
             pairs[1] = (long long)ld_volatile(&sc.inserted[1]);
             const int rounds = ld_volatile(&sc.rounds);
-            if (err != 0 && err != SCC_ERR_CAPACITY) return;
-            if (ovf || err == SCC_ERR_CAPACITY) {
+            if (why < 0 && why != SCC_ERR_CAPACITY) return;
+            if (why == 1 || why == SCC_ERR_CAPACITY) {
                 grow = true;
                 need = 2 * max(cap[0], cap[1]);
             }

@@ -65,12 +65,17 @@ struct BagCtl {
 // g inserts into ring[g % 3] (and slot array g % 2), reads what round g - 1 left
 // in ring[(g + 2) % 3] (slot array (g + 1) % 2), and block 0 clears
 // ring[(g + 1) % 3] for round g + 1 -- nobody touches that entry in round g.
+// The stop flags of a round live here too: a flag raised in round g is read
+// only after round g's barrier, and round g + 1 raises its own, so every block
+// (and every warp) takes the same decision to stop.
 struct RoundCtl {
     BagCtl bag;
     long long items;   // items inserted into this round's bag
     long long hubseg;  // hub segments reserved this round
     long long work;    // next warp task of this round (dynamic assignment)
     int nhub;          // hub items set aside this round (expanded next round)
+    int overflow;      // a pair table went over its load or probe limit
+    int err;           // first error of the round (SCC_ERR_*: the bag is full)
     int pad;
 };
 
@@ -131,6 +136,29 @@ struct EngineParams {
     const Item* init;
     long long ninit;
     EngineCtl* ctl;
+};
+
+// Synchronisation scope of a search. GridScope: every block of a cooperative
+// grid works on one search, rounds end at grid barriers, and the graph arrays
+// (written before the launch) are read through the read-only path. CtaScope:
+// one block runs the search alone (the batched kernel gives each graph to one
+// block), rounds end at __syncthreads, and the graph arrays -- which the block
+// may have written itself earlier in the same launch -- are read with coherent
+// loads.
+struct GridScope {
+    __device__ __forceinline__ static int block() { return blockIdx.x; }
+    __device__ __forceinline__ static int blocks() { return gridDim.x; }
+    __device__ __forceinline__ static bool sync(GridBarrier* b, int* err) { return grid_sync(b, err); }
+    __device__ __forceinline__ static int32_t ld(const int32_t* p) { return __ldg(p); }
+};
+struct CtaScope {
+    __device__ __forceinline__ static int block() { return 0; }
+    __device__ __forceinline__ static int blocks() { return 1; }
+    __device__ __forceinline__ static bool sync(GridBarrier*, int*) {
+        __syncthreads();
+        return true;
+    }
+    __device__ __forceinline__ static int32_t ld(const int32_t* p) { return *p; }
 };
 
 // adjacency arrays of an item's graph
@@ -277,7 +305,7 @@ struct WarpStats {
 
 // Expand the next batch of queued items (up to 32, or `max_take` in the seeds
 // phase, which ignores the budget and the hub test).
-template <class Pol>
+template <class Pol, class S>
 __device__ __forceinline__ void expand_batch(const EngineParams<typename Pol::Item>& P, Pol& pol,
                                              const BagRef<typename Pol::Item>& out, SegState& st, uint32_t wid,
                                              uint32_t round, const LocalQueue<typename Pol::Item>& q, uint32_t& qh, uint32_t& qt,
@@ -342,7 +370,7 @@ __device__ __forceinline__ void expand_batch(const EngineParams<typename Pol::It
             const int jbeg = __shfl_sync(kFull, beg, j);
             jit[u] = shfl_any(it, j);
             jctx[u] = shfl_any(ctx, j);
-            w[u] = e < total ? __ldg(&item_adj(P, pol, jit[u])[jbeg + (e - jexcl)]) : -1;
+            w[u] = e < total ? S::ld(&item_adj(P, pol, jit[u])[jbeg + (e - jexcl)]) : -1;
         }
         // the adjacency range of every target is loaded together with its visit
         // test (not after it), so a newly visited item enters the queue ready to
@@ -351,8 +379,8 @@ __device__ __forceinline__ void expand_batch(const EngineParams<typename Pol::It
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             const int32_t* O = item_off(P, pol, jit[u]);  // a child stays in its parent's graph
-            rb[u] = w[u] >= 0 ? __ldg(&O[w[u]]) : 0;
-            re[u] = w[u] >= 0 ? __ldg(&O[w[u] + 1]) : 0;
+            rb[u] = w[u] >= 0 ? S::ld(&O[w[u]]) : 0;
+            re[u] = w[u] >= 0 ? S::ld(&O[w[u] + 1]) : 0;
         }
         bool nw[U];
         Item child[U];
@@ -441,22 +469,23 @@ __device__ __forceinline__ bool reserve_hub(const EngineParams<Item>& P, RoundCt
 // per-search control entry). Returns false if a grid barrier timed out (the
 // caller must return at once). On return every block has passed the final
 // barrier, so this search's control entry is final.
-template <class Pol, class Init>
+template <class Pol, class Init, class S = GridScope>
 __device__ bool engine_search(const EngineParams<typename Pol::Item>& P, Pol& pol, Init init, long long ninit,
                               const DenseParams* dp, const LocalQueue<typename Pol::Item>& q, WarpStats& ws, uint32_t& g,
-                              uint32_t si) {
+                              uint32_t si, int& why) {
     using Item = typename Pol::Item;
     constexpr uint32_t QM = Pol::kQueue - 1;
     EngineCtl* ctl = P.ctl;
     SearchCtl& sc = ctl->search[si % 3];
     const int lane = lane_id();
     const int wib = threadIdx.x >> 5;
-    const uint32_t wid = (uint32_t)(blockIdx.x * (blockDim.x >> 5) + wib);
-    const uint32_t nwarps = (uint32_t)(gridDim.x * (blockDim.x >> 5));
-    const long long gtid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const long long gstride = (long long)gridDim.x * blockDim.x;
+    const uint32_t wid = (uint32_t)(S::block() * (blockDim.x >> 5) + wib);
+    const uint32_t nwarps = (uint32_t)(S::blocks() * (blockDim.x >> 5));
+    const long long gtid = (long long)S::block() * blockDim.x + threadIdx.x;
+    const long long gstride = (long long)S::blocks() * blockDim.x;
     const uint32_t g0 = g;
-    if (si == 0 && blockIdx.x == 0 && threadIdx.x == 0) ctl->t0 = globaltimer_ns();
+    why = 0;
+    if (si == 0 && S::block() == 0 && threadIdx.x == 0) ctl->t0 = globaltimer_ns();
     bool prev_dense = false;
     uint32_t i = 0;
     for (;; ++i) {
@@ -464,7 +493,7 @@ __device__ bool engine_search(const EngineParams<typename Pol::Item>& P, Pol& po
         const int par = (int)(gr & 1), ipar = par ^ 1;
         RoundCtl& cur = ctl->ring[gr % 3];
         RoundCtl& prev = ctl->ring[(gr + 2) % 3];
-        if (blockIdx.x == 0 && threadIdx.x == 0) {
+        if (S::block() == 0 && threadIdx.x == 0) {
             RoundCtl& nx = ctl->ring[(gr + 1) % 3];
             nx.bag.r = 0;
             for (int j = 0; j < kMaxChunks; ++j) nx.bag.sample[j] = 0;
@@ -472,6 +501,8 @@ __device__ bool engine_search(const EngineParams<typename Pol::Item>& P, Pol& po
             nx.hubseg = 0;
             nx.work = 0;
             nx.nhub = 0;
+            nx.overflow = 0;
+            nx.err = 0;
             if (i == 0) {
                 SearchCtl& other = ctl->search[(si + 1) % 3];
                 other.overflow = 0;
@@ -480,7 +511,8 @@ __device__ bool engine_search(const EngineParams<typename Pol::Item>& P, Pol& po
                 other.inserted[1] = 0;
             }
         }
-        const BagRef<Item> out{P.slots[par], P.nslots, P.lambda, P.sigma, &cur.bag, &ctl->err, &ctl->max_chunk};
+        const BagRef<Item> out{P.slots[par], P.nslots, P.lambda, P.sigma, &cur.bag, &cur.err, &ctl->max_chunk};
+        if constexpr (Pol::kCountInserts) pol.overflow = &cur.overflow;
         Item* const in_slots = P.slots[ipar];
         SegState st{-1, 0, (uint32_t)(wid * 2654435761u) ^ gr};
         unsigned long long pushed = 0;
@@ -515,7 +547,7 @@ __device__ bool engine_search(const EngineParams<typename Pol::Item>& P, Pol& po
                     const int v = pol.vertex(P.hub_item[ipar][j]);
                     atomicOr(&fb[v >> 5], 1u << (v & 31));
                 }
-                if (!grid_sync(&ctl->bar, &ctl->err)) return false;
+                if (!S::sync(&ctl->bar, &ctl->err)) return false;
                 const long long nw = ((long long)P.n + 31) / 32;
                 // each warp takes 32 consecutive words at a time (one coalesced
                 // load) and works only on words with unvisited vertices, kDW of
@@ -538,8 +570,8 @@ __device__ bool engine_search(const EngineParams<typename Pol::Item>& P, Pol& po
                             word[k] = jw[k] >= 0 ? __shfl_sync(kFull, mine, jw[k]) : ~0u;
                             const long long v = (w0 + (jw[k] >= 0 ? jw[k] : 0)) * 32 + lane;
                             const bool act = jw[k] >= 0 && v < P.n && !((word[k] >> lane) & 1u);
-                            e[k] = act ? __ldg(&dp->roff[v]) : 0;
-                            e1[k] = act ? __ldg(&dp->roff[v + 1]) : 0;
+                            e[k] = act ? S::ld(&dp->roff[v]) : 0;
+                            e1[k] = act ? S::ld(&dp->roff[v + 1]) : 0;
                             found[k] = false;
                         }
                         unsigned long long scanned = 0;
@@ -551,7 +583,7 @@ __device__ bool engine_search(const EngineParams<typename Pol::Item>& P, Pol& po
 #pragma unroll
                                 for (int a = 0; a < 2; ++a) {
                                     const bool go = !found[k] && e[k] + a < e1[k];
-                                    u[k][a] = go ? __ldg(&dp->radj[e[k] + a]) : -1;
+                                    u[k][a] = go ? S::ld(&dp->radj[e[k] + a]) : -1;
                                     any |= go;
                                 }
                             }
@@ -587,11 +619,17 @@ __device__ bool engine_search(const EngineParams<typename Pol::Item>& P, Pol& po
                 }
             }
         } else {
-            const bool stop = Pol::kCountInserts && ld_volatile(&sc.overflow) != 0;
+            // once a table overflows the round's work is moot: stop taking work
+            // (lane 0 reads the flag for the warp, so the warp stays converged)
+            auto stop = [&]() {
+                if constexpr (!Pol::kCountInserts) return false;
+                const int f = lane == 0 ? ld_volatile(&cur.overflow) : 0;
+                return __shfl_sync(kFull, f, 0) != 0;
+            };
             // ---- phase A: last round's hubs, cut into segments shared by all warps
             if (i > 0) {
                 const long long nseg = min(ld_volatile(&prev.hubseg), P.segmap_cap);
-                for (long long gs = wid; gs < nseg && !stop; gs += nwarps) {
+                for (long long gs = wid; gs < nseg && !stop(); gs += nwarps) {
                     const int h = P.segmap[ipar][gs];
                     if (h < 0) continue;
                     const Item hit = P.hub_item[ipar][h];
@@ -603,7 +641,7 @@ __device__ bool engine_search(const EngineParams<typename Pol::Item>& P, Pol& po
                         bool nw = false;
                         Item child = Sent<Item>::empty;
                         if (e0 + lane < len) {
-                            const int w = __ldg(&item_adj(P, pol, hit)[b0 + e0 + lane]);
+                            const int w = S::ld(&item_adj(P, pol, hit)[b0 + e0 + lane]);
                             nw = pol.visit(hit, hctx, w, child);
                         }
                         pushed += bag_push<Item>(out, st, nw, child, wid, gr);
@@ -626,7 +664,7 @@ __device__ bool engine_search(const EngineParams<typename Pol::Item>& P, Pol& po
                 long long tk = 0;
                 if (lane == 0) tk = (long long)atomicAdd((unsigned long long*)&cur.work, 1ull);
                 tk = __shfl_sync(kFull, tk, 0);
-                if (tk >= ntasks || stop) break;
+                if (tk >= ntasks || stop()) break;
                 const long long idx = tk * G + lane;
                 Item it = Sent<Item>::empty;
                 bool has = false;
@@ -647,8 +685,8 @@ __device__ bool engine_search(const EngineParams<typename Pol::Item>& P, Pol& po
                 if (has) {
                     const int v = pol.vertex(it);
                     const int32_t* O = item_off(P, pol, it);
-                    b0 = __ldg(&O[v]);
-                    dg = __ldg(&O[v + 1]) - b0;
+                    b0 = S::ld(&O[v]);
+                    dg = S::ld(&O[v + 1]) - b0;
                     if constexpr (Pol::kCtxInQueue) cx0 = pol.load_ctx(it);
                     if (dg > hub_thr && reserve_hub(P, cur, par, it, b0, dg)) has = false;
                 }
@@ -663,9 +701,9 @@ __device__ bool engine_search(const EngineParams<typename Pol::Item>& P, Pol& po
                 __syncwarp();
                 uint32_t qh = 0, qt = (uint32_t)__popc(m);
                 int t = 0;
-                expand_batch<Pol>(P, pol, out, st, wid, gr, q, qh, qt, t, true, P.seeds, hub_thr, ws, pushed);
+                expand_batch<Pol, S>(P, pol, out, st, wid, gr, q, qh, qt, t, true, P.seeds, hub_thr, ws, pushed);
                 while (qt != qh && t < P.tau)
-                    expand_batch<Pol>(P, pol, out, st, wid, gr, q, qh, qt, t, false, 32, hub_thr, ws, pushed);
+                    expand_batch<Pol, S>(P, pol, out, st, wid, gr, q, qh, qt, t, false, 32, hub_thr, ws, pushed);
                 // budget spent: flush what is left in the local queue
                 while (qt != qh) {
                     const int nrem = (int)min(32u, qt - qh);
@@ -679,18 +717,31 @@ __device__ bool engine_search(const EngineParams<typename Pol::Item>& P, Pol& po
             if constexpr (Pol::kCountInserts) pol.flush(sc);
         }
         if (lane == 0 && pushed) atomicAdd((unsigned long long*)&cur.items, pushed);
-        if (!grid_sync(&ctl->bar, &ctl->err)) return false;
-        if (gr < (uint32_t)kTraceRounds && blockIdx.x == 0 && threadIdx.x == 0) {
+        if (!S::sync(&ctl->bar, &ctl->err)) return false;
+        if (gr < (uint32_t)kTraceRounds && S::block() == 0 && threadIdx.x == 0) {
             ctl->t_end[gr] = globaltimer_ns();
             ctl->t_items[gr] = ld_volatile(&cur.items);
             ctl->t_dense[gr] = (int)dense | (int)(si << 1);
         }
         prev_dense = dense;
-        if (ld_volatile(&ctl->err) != 0) break;
-        if (Pol::kCountInserts && ld_volatile(&sc.overflow) != 0) break;
+        // the decision to stop reads only this round's entries, final now
+        const int rerr = ld_volatile(&cur.err);
+        if (rerr != 0) {
+            why = rerr;
+            break;
+        }
+        if (Pol::kCountInserts && ld_volatile(&cur.overflow) != 0) {
+            why = 1;
+            break;
+        }
         if (ld_volatile(&cur.items) == 0 && ld_volatile(&cur.nhub) == 0) break;
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) sc.rounds = (int)i + 1;
+    // for readers after the launch (the caller inside the launch uses `why`)
+    if (S::block() == 0 && threadIdx.x == 0) {
+        sc.rounds = (int)i + 1;
+        if (why == 1) sc.overflow = 1;
+        if (why < 0) atomicCAS(&ctl->err, 0, why);
+    }
     g = g0 + i + 1;
     if constexpr (Pol::kDense) {
         // a search that ended on a dense round leaves its bitmap for the next
@@ -700,7 +751,7 @@ __device__ bool engine_search(const EngineParams<typename Pol::Item>& P, Pol& po
             const long long nw = ((long long)P.n + 31) / 32;
             for (long long w = gtid; w < nw; w += gstride)
                 if (last[w]) last[w] = 0;
-            if (!grid_sync(&ctl->bar, &ctl->err)) return false;
+            if (!S::sync(&ctl->bar, &ctl->err)) return false;
         }
     }
     return true;
@@ -713,8 +764,9 @@ __global__ void __launch_bounds__(256, 3) engine_kernel(EngineParams<typename Po
     const LocalQueue<typename Pol::Item> q = warp_queue(sm);
     WarpStats ws;
     uint32_t g = 0;
+    int why = 0;  // the host reads the outcome from the control block
     const bool ok = engine_search<Pol>(P, pol, InitList<typename Pol::Item>{P.init}, P.ninit,
-                                       dp.frac_inv > 0 ? &dp : nullptr, q, ws, g, 0);
+                                       dp.frac_inv > 0 ? &dp : nullptr, q, ws, g, 0, why);
     if (!ok) return;
     if (lane_id() == 0 && ws.edges) atomicAdd(&P.ctl->edges, ws.edges);
     if (lane_id() == 0 && ws.items) atomicAdd(&P.ctl->items, ws.items);
@@ -804,7 +856,7 @@ struct PolPair {
     unsigned long long* keys[2];  // T_out, T_in
     unsigned long long mask[2];   // capacities - 1 (powers of two)
     long long max_ins[2];         // load limits (0 = none): over them the search stops
-    int* overflow;                // set on a load or probe-limit overflow
+    int* overflow;                // set on a load or probe-limit overflow (per round, by the engine)
     long long ins0, ins1;         // this lane's new pairs since the last flush
     __device__ __forceinline__ int vertex(Item it) const { return (int)((it >> 32) & 0x7fffffffu); }
     __device__ __forceinline__ int graph(Item it) const { return (int)(it >> 63); }
@@ -827,7 +879,8 @@ struct PolPair {
         return add(child);
     }
     // warp-collective: add the warp's new pairs to the search's counters and
-    // flag an overflow past a load limit
+    // flag an overflow past a load limit (in the current round's flag, which
+    // the engine points `overflow` at)
     __device__ __forceinline__ void flush(SearchCtl& sc) {
         long long c0 = ins0, c1 = ins1;
         for (int d = 16; d >= 1; d >>= 1) {
@@ -838,11 +891,11 @@ struct PolPair {
         if (lane_id() != 0) return;
         if (c0) {
             const unsigned long long t = atomicAdd(&sc.inserted[0], (unsigned long long)c0) + c0;
-            if (max_ins[0] > 0 && (long long)t > max_ins[0]) atomicExch(&sc.overflow, 1);
+            if (max_ins[0] > 0 && (long long)t > max_ins[0]) atomicExch(overflow, 1);
         }
         if (c1) {
             const unsigned long long t = atomicAdd(&sc.inserted[1], (unsigned long long)c1) + c1;
-            if (max_ins[1] > 0 && (long long)t > max_ins[1]) atomicExch(&sc.overflow, 1);
+            if (max_ins[1] > 0 && (long long)t > max_ins[1]) atomicExch(overflow, 1);
         }
     }
 };

@@ -158,3 +158,76 @@ def edges_of(g: Graph) -> np.ndarray:
     """(m, 2) int64 array of the arcs of g, row by row."""
     src = np.repeat(np.arange(g.n, dtype=np.int64), np.diff(g.offsets.astype(np.int64)))
     return np.stack([src, g.targets.astype(np.int64)], axis=1)
+
+
+# ------------------------------------------------------------------ batches --
+@dataclass
+class Packed:
+    """Many graphs in one int32 CSR with per-graph int64 bases (the layout of
+    ``include/scc_batch.h``): graph g has ``n_g = vbase[g+1] - vbase[g]``
+    vertices, its ``n_g + 1`` local offsets at ``offsets[vbase[g] + g:]`` and
+    its ``m_g = ebase[g+1] - ebase[g]`` local targets at ``targets[ebase[g]:]``."""
+    G: int
+    vbase: np.ndarray    # int64[G+1]
+    ebase: np.ndarray    # int64[G+1]
+    offsets: np.ndarray  # int32[vbase[G] + G]
+    targets: np.ndarray  # int32[ebase[G]]
+    names: list
+
+    def graph(self, g: int) -> Graph:
+        n = int(self.vbase[g + 1] - self.vbase[g])
+        o0 = int(self.vbase[g]) + g
+        e0, e1 = int(self.ebase[g]), int(self.ebase[g + 1])
+        return Graph(n, self.offsets[o0:o0 + n + 1], self.targets[e0:e1], self.names[g])
+
+    def labels_of(self, labels, g: int):
+        return labels[int(self.vbase[g]):int(self.vbase[g + 1])]
+
+
+def pack(graphs) -> Packed:
+    """Pack a list of :class:`Graph` into one :class:`Packed` batch."""
+    G = len(graphs)
+    vbase = np.zeros(G + 1, np.int64)
+    ebase = np.zeros(G + 1, np.int64)
+    for i, g in enumerate(graphs):
+        vbase[i + 1] = vbase[i] + g.n
+        ebase[i + 1] = ebase[i] + g.m
+    offs = [np.asarray(g.offsets[:g.n + 1], np.int32) for g in graphs]
+    tgts = [np.asarray(g.targets[:g.m], np.int32) for g in graphs]
+    offsets = np.concatenate(offs) if offs else np.zeros(0, np.int32)
+    targets = np.concatenate(tgts) if tgts else np.zeros(0, np.int32)
+    return Packed(G, vbase, ebase, offsets, targets, [g.name for g in graphs])
+
+
+def mixed_batch_spec(G: int, n_lo: int, n_hi: int, seed: int):
+    """(kind, size, seed) of each graph of a mixed batch: vertex counts
+    log-uniform in [n_lo, n_hi]; even entries are 2D tori of side ceil(sqrt(n))
+    with p = 0.5, odd entries R-MAT of scale round(log2 n) with edge factor 8."""
+    rng = np.random.default_rng(seed)
+    ns = np.exp(rng.uniform(np.log(n_lo), np.log(n_hi), G))
+    spec = []
+    for i, n in enumerate(ns):
+        s = (seed * 1000003 + i) & (2**63 - 1)
+        if i % 2 == 0:
+            spec.append(("torus", int(np.ceil(np.sqrt(n))), s))
+        else:
+            spec.append(("rmat", max(1, int(round(np.log2(n)))), s))
+    return spec
+
+
+def make_from_spec(item) -> Graph:
+    kind, size, s = item
+    if kind == "torus":
+        return torus(2, size, 0.5, seed=s, threads=1)
+    return rmat(size, 8, seed=s, threads=1)
+
+
+def mixed_batch(G: int, n_lo: int, n_hi: int, seed: int, workers: int = 0) -> Packed:
+    """A packed batch of :func:`mixed_batch_spec` graphs (generated in parallel)."""
+    import concurrent.futures as cf
+    spec = mixed_batch_spec(G, n_lo, n_hi, seed)
+    workers = workers or (os.cpu_count() or 1)
+    _load()
+    with cf.ThreadPoolExecutor(max_workers=workers) as ex:
+        graphs = list(ex.map(make_from_spec, spec))
+    return pack(graphs)

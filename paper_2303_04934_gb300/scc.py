@@ -1,4 +1,5 @@
-"""Thin Python binding of the C ABI in ``include/scc.h`` / ``include/scc_debug.h``.
+"""Thin Python binding of the C ABI in ``include/scc.h``, ``include/scc_batch.h``
+and ``include/scc_debug.h``.
 
 Argument marshalling only: every step runs in the CUDA library
 ``_lib/libscc_gb300.so``. Arrays may be CUDA torch tensors (device pointers are
@@ -31,6 +32,8 @@ EXPORTED = [
     "scc_run", "reach_multi", "reach_multi_noalloc", "scc_get_stats",
     "scc_graph_info", "scc_debug_csr", "scc_debug_trim", "scc_debug_pivot_order", "scc_debug_single_reach",
     "scc_debug_multi_reach", "scc_debug_hashbag", "scc_debug_pair_table", "scc_debug_launch_count",
+    "scc_batch_config_default", "scc_batch_create", "scc_batch_destroy", "scc_batch_set_config",
+    "scc_batch_get_config", "scc_batch_run", "scc_batch_autotune", "scc_batch_get_stats",
 ]
 
 
@@ -51,6 +54,25 @@ class scc_stats(ctypes.Structure):
                 ("ms_transpose_rows", ctypes.c_double), ("n_class_trimmed", ctypes.c_int32),
                 ("class_trim_passes", ctypes.c_int32), ("ms_class_trim", ctypes.c_double),
                 ("multi_launches", ctypes.c_int32), ("multi_arcs", ctypes.c_int64), ("multi_items", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class scc_batch_config(ctypes.Structure):
+    _fields_ = [("tau", ctypes.c_int32), ("block", ctypes.c_int32), ("lambda_", ctypes.c_int32),
+                ("sigma", ctypes.c_int32), ("seeds", ctypes.c_int32), ("beta", ctypes.c_double),
+                ("blocks_per_sm", ctypes.c_int32), ("seed", ctypes.c_uint64)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class scc_batch_stats(ctypes.Structure):
+    _fields_ = [("graphs", ctypes.c_int32), ("vertices", ctypes.c_int64), ("arcs", ctypes.c_int64),
+                ("max_vertices", ctypes.c_int32), ("max_arcs", ctypes.c_int64), ("blocks", ctypes.c_int32),
+                ("workspace_bytes", ctypes.c_int64), ("ms_last_run", ctypes.c_double), ("captures", ctypes.c_int32),
+                ("replays", ctypes.c_int32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -100,6 +122,14 @@ def load() -> ctypes.CDLL:
         "scc_debug_hashbag": ([vp, i64, i32, i32, vp, P(i64), P(i32), vp], ctypes.c_int),
         "scc_debug_pair_table": ([vp, i64, i64, vp, P(i64), P(i32), vp], ctypes.c_int),
         "scc_debug_launch_count": ([], ctypes.c_int64),
+        "scc_batch_config_default": ([P(scc_batch_config)], ctypes.c_int),
+        "scc_batch_create": ([i32, vp, vp, vp, vp, vp, P(vp)], ctypes.c_int),
+        "scc_batch_destroy": ([vp], ctypes.c_int),
+        "scc_batch_set_config": ([vp, P(scc_batch_config)], ctypes.c_int),
+        "scc_batch_get_config": ([vp, P(scc_batch_config)], ctypes.c_int),
+        "scc_batch_run": ([vp, vp, vp], ctypes.c_int),
+        "scc_batch_autotune": ([vp, i32, vp, P(scc_batch_config), P(ctypes.c_double)], ctypes.c_int),
+        "scc_batch_get_stats": ([vp, P(scc_batch_stats)], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -188,6 +218,90 @@ def scc_get_stats(h) -> dict:
     s = scc_stats()
     _check(load().scc_get_stats(h, ctypes.byref(s)), "scc_get_stats")
     return s.as_dict()
+
+
+# ------------------------------------------------------------------ batches --
+def scc_batch_config_default() -> scc_batch_config:
+    c = scc_batch_config()
+    _check(load().scc_batch_config_default(ctypes.byref(c)), "scc_batch_config_default")
+    return c
+
+
+def scc_batch_create(G: int, vbase, ebase, offsets, targets, stream=None) -> int:
+    h = ctypes.c_void_p()
+    _check(load().scc_batch_create(G, _ptr(vbase), _ptr(ebase), _ptr(offsets), _ptr(targets), _stream(stream),
+                                   ctypes.byref(h)), "scc_batch_create")
+    return h.value
+
+
+def scc_batch_destroy(h) -> None:
+    _check(load().scc_batch_destroy(h), "scc_batch_destroy")
+
+
+def scc_batch_set_config(h, cfg: scc_batch_config) -> None:
+    _check(load().scc_batch_set_config(h, ctypes.byref(cfg)), "scc_batch_set_config")
+
+
+def scc_batch_get_config(h) -> scc_batch_config:
+    c = scc_batch_config()
+    _check(load().scc_batch_get_config(h, ctypes.byref(c)), "scc_batch_get_config")
+    return c
+
+
+def scc_batch_run(h, labels_out, stream=None) -> None:
+    _check(load().scc_batch_run(h, _ptr(labels_out), _stream(stream)), "scc_batch_run")
+
+
+def scc_batch_autotune(h, sample: int = 0, stream=None):
+    best, ms = scc_batch_config(), ctypes.c_double()
+    _check(load().scc_batch_autotune(h, sample, _stream(stream), ctypes.byref(best), ctypes.byref(ms)),
+           "scc_batch_autotune")
+    return best, ms.value
+
+
+def scc_batch_get_stats(h) -> dict:
+    s = scc_batch_stats()
+    _check(load().scc_batch_get_stats(h, ctypes.byref(s)), "scc_batch_get_stats")
+    return s.as_dict()
+
+
+class SccBatch:
+    """Owning wrapper of a batch handle: ``SccBatch(packed)`` for a
+    :class:`graphgen.Packed` batch (or the four packed arrays)."""
+
+    def __init__(self, packed, stream=None, config: scc_batch_config | None = None):
+        self.G = int(packed.G)
+        self.nv = int(packed.vbase[-1])
+        self.h = scc_batch_create(self.G, packed.vbase, packed.ebase, packed.offsets, packed.targets, stream)
+        if config is not None:
+            scc_batch_set_config(self.h, config)
+
+    def close(self):
+        if getattr(self, "h", None):
+            scc_batch_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def labels(self, out=None, stream=None):
+        if out is None:
+            import torch
+            out = torch.empty(max(self.nv, 1), dtype=torch.int32, device="cuda")
+        scc_batch_run(self.h, out, stream)
+        return out
+
+    def stats(self) -> dict:
+        return scc_batch_get_stats(self.h)
 
 
 # -------------------------------------------------------------- debug hooks --
