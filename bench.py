@@ -48,6 +48,11 @@ WORKLOADS = {
     "torus2d256": dict(kind="torus", dims=2, side=256, p=0.5, seed=0x5CC00),
     "torus3d256": dict(kind="torus", dims=3, side=256, p=0.3, seed=0x5CC02),
     "knn8m": dict(kind="knn", n=8_000_000, k=5, seed=0x5CC03),
+    # batched SCC: 4,096 graphs, vertex counts log-uniform in [1e3, 1e6], half 2D
+    # tori (side ceil(sqrt n), p = 0.5), half R-MAT (scale round(log2 n), edge
+    # factor 8); one packed int32 CSR with int64 bases
+    "batch4096": dict(kind="batch", G=4096, n_lo=1000, n_hi=1_000_000, seed=0x5CC04),
+    "batch256": dict(kind="batch", G=256, n_lo=1000, n_hi=100_000, seed=0x5CC05),
 }
 
 
@@ -164,6 +169,249 @@ def run_reference(args, spec):
     return 0
 
 
+# ----------------------------------------------------------------- batches --
+def _stratified(order, k):
+    """k graphs spread evenly over a size order."""
+    k = max(1, min(k, len(order)))
+    return [int(order[int(i * len(order) / k)]) for i in range(k)]
+
+
+def _oracle_all_cores(p, graphs):
+    """Seconds for the CPU oracle on `graphs` of batch p, one graph per thread on
+    every host core (the oracle's C code runs without the interpreter lock)."""
+    import concurrent.futures as cf
+    import oracle
+    cores = os.cpu_count() or 1
+
+    def one(gi):
+        h = p.graph(gi)
+        oracle.scc_labels(h.n, h.offsets, h.targets)
+
+    t0 = time.perf_counter()
+    with cf.ThreadPoolExecutor(max_workers=cores) as ex:
+        list(ex.map(one, graphs))
+    return time.perf_counter() - t0, cores
+
+
+def run_batch(args, spec):
+    """Batched SCC: one step = scc_batch_run over the whole packed batch (the
+    input resident on the device; the per-graph transposes are inside the run).
+    Beside it: the plain per-graph path (scc_graph_create + scc_run + destroy
+    for each graph) timed on a sample of graphs spread over the size range and
+    scaled to the batch, and the CPU oracle on all host cores."""
+    from paper_2303_04934_gb300 import graphgen as gg
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    t_gen = time.perf_counter()
+    p = gg.mixed_batch(spec["G"], spec["n_lo"], spec["n_hi"], seed=spec["seed"])
+    t_gen = time.perf_counter() - t_gen
+    G, nv, na = p.G, int(p.vbase[-1]), int(p.ebase[-1])
+    sizes = np.diff(p.ebase) + np.diff(p.vbase)
+    order = np.argsort(-sizes, kind="stable")
+    wname = f"batch_G{G}_n{spec['n_lo']}-{spec['n_hi']}_torus2d-rmat8"
+    config = {"workload": wname, "graphs": G, "vertices": nv, "arcs": na, "seed": spec["seed"],
+              "parallelism": f"replicas{world}", "l2": "inputs larger than L2 (packed CSR > 4 GB)"}
+
+    if args.impl == "reference":
+        if rank != 0:
+            return 0
+        sample = _stratified(order, max(16, G // 16))
+        ms_ = na_s = 0
+        for _ in range(args.warmup):
+            _oracle_all_cores(p, sample[:8])
+        ts = []
+        for _ in range(args.steps):
+            t, cores = _oracle_all_cores(p, sample)
+            ts.append(t)
+        na_s = int(sum(p.ebase[g + 1] - p.ebase[g] for g in sample))
+        value = na_s * args.steps / sum(ts)
+        smp = f"{len(sample)} of the {G} graphs, spread over the size range, one graph per thread"
+        line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(ts) / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+                "data": "synthetic", "config": {**config, "sample": smp},
+                "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": smp},
+                "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+        return 0
+
+    import torch
+    from paper_2303_04934_gb300 import build as libbuild
+    from paper_2303_04934_gb300 import scc
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    if not os.path.exists(libbuild.SO_PATH):
+        raise RuntimeError("CUDA library not built: run python -c 'import __graft_entry__ as g; g.build()'")
+    scc.load()
+    stream = torch.cuda.Stream()
+    d = [torch.from_numpy(a).to("cuda") for a in (p.vbase, p.ebase, p.offsets, p.targets)]
+    torch.cuda.synchronize()
+    h = scc.scc_batch_create(G, d[0], d[1], d[2], d[3], stream)
+    tuned = None
+    if args.batch_block or args.batch_bps is not None or args.tau:
+        c = scc.scc_batch_get_config(h)
+        if args.batch_block:
+            c.block = args.batch_block
+        if args.batch_bps is not None:
+            c.blocks_per_sm = args.batch_bps
+        if args.tau:
+            c.tau = args.tau
+        scc.scc_batch_set_config(h, c)
+    if args.autotune:
+        best, ms_t = scc.scc_batch_autotune(h, sample=max(32, G // 16), stream=stream)
+        tuned = {"tau": best.tau, "block": best.block, "lambda": best.lambda_, "sample_ms": ms_t}
+    cfg = scc.scc_batch_get_config(h)
+    labels_d = torch.empty(max(nv, 1), dtype=torch.int32, device="cuda")
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            scc.scc_batch_run(h, labels_d, stream)
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    launches0 = scc.scc_debug_launch_count()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        ev0.record(stream)
+        for _ in range(args.steps):
+            scc.scc_batch_run(h, labels_d, stream)
+        ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    launches = scc.scc_debug_launch_count() - launches0
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    st = scc.scc_batch_get_stats(h)
+    per_graph = None
+    if args.verbose:
+        tm = scc.scc_debug_batch_times(h, G).astype(np.int64)
+        dur = (tm[:, 5] - tm[:, 0]) / 1e6
+        span = (tm[:, 5].max() - tm[:, 0].min()) / 1e6
+        busy = np.bincount(tm[:, 6], weights=dur, minlength=st["blocks"])
+        top = np.argsort(-dur)[:8]
+        phase = np.diff(tm[:, :6], axis=1).sum(axis=0) / 1e6
+        names = ["transpose", "trim_and_first_scc", "class_trim", "batches", "labels"]
+        per_graph = {"span_ms": span, "busiest_block_ms": float(busy.max()), "mean_block_ms": float(busy.mean()),
+                     "block_ms_by_phase": {k: float(v) for k, v in zip(names, phase)},
+                     "longest": [{"graph": p.names[i], "n": int(p.vbase[i + 1] - p.vbase[i]),
+                                  "m": int(p.ebase[i + 1] - p.ebase[i]), "ms": float(dur[i]),
+                                  "phases_ms": [float(x) for x in np.diff(tm[i, :6]) / 1e6],
+                                  "rounds_searches_reruns_batches": [int(x) for x in tm[i, 7:11]]} for i in top],
+                     "totals_rounds_searches_reruns_batches": [int(x) for x in tm[:, 7:11].sum(axis=0)]}
+    value = world * na * args.steps / (ms / 1e3)
+    graphs_per_s = world * G * args.steps / (ms / 1e3)
+    # roofline of the persistent kernel (the only kernel of a step besides a
+    # one-thread reset): algorithmic bytes per graph = building G^T (read the
+    # targets twice, write them once, 12 B per arc, + 12 B per vertex of
+    # offsets) + reading G and G^T once and writing the labels (8 B per arc +
+    # 12 B per vertex)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    alg = 20 * na + 24 * nv
+    achieved = alg / (ms / args.steps / 1e3) / 1e9
+    roofline = {"bound": "hbm", "kernel": "k_batch_scc (persistent, one block per graph)", "achieved": achieved,
+                "peak": hbm_peak, "peak_source": "measured" if "hbm_gbs" in peaks else "fallback", "unit": "GB/s",
+                "frac": achieved / hbm_peak, "traffic": None, "algorithmic_bytes_per_launch": alg,
+                "ms_per_launch": ms / args.steps}
+
+    # ---- the plain per-graph path on a sample spread over the sizes, scaled
+    plain = None
+    if not args.no_plain:
+        sample = _stratified(order, 64)
+        tot = 0.0
+        for gi in sample:
+            gph = p.graph(gi)
+            if gph.n == 0:
+                continue
+            od = torch.from_numpy(np.ascontiguousarray(gph.offsets)).to("cuda")
+            ad = torch.from_numpy(np.ascontiguousarray(gph.targets)).to("cuda")
+            lab = torch.empty(gph.n, dtype=torch.int32, device="cuda")
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            with torch.cuda.stream(stream):
+                for rep in range(2):  # the first call warms this size up
+                    if rep == 1:
+                        e0.record(stream)
+                    hh = scc.scc_graph_create(gph.n, gph.m, od, ad, stream)
+                    scc.scc_run(hh, lab, stream)
+                    scc.scc_graph_destroy(hh)
+                e1.record(stream)
+            torch.cuda.synchronize()
+            tot += e0.elapsed_time(e1)
+        est_ms = tot * G / len(sample)
+        plain = {"graphs_per_s": G / (est_ms / 1e3), "edges_per_s": na / (est_ms / 1e3),
+                 "ms_per_batch_est": est_ms, "sample_graphs": len(sample),
+                 "how": "scc_graph_create + scc_run + scc_graph_destroy per graph on a sample spread over the "
+                        "size range, time scaled by G / sample"}
+
+    # ---- end to end: host packed arrays in, host labels out
+    e2e = None
+    if not args.no_e2e:
+        hp = [torch.from_numpy(a).pin_memory() for a in (p.vbase, p.ebase, p.offsets, p.targets)]
+        lab_h = torch.empty(max(nv, 1), dtype=torch.int32).pin_memory()
+        k2 = max(1, min(args.steps, 2))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(k2):
+            hh = scc.scc_batch_create(G, hp[0], hp[1], hp[2], hp[3], stream)
+            scc.scc_batch_set_config(hh, cfg)
+            scc.scc_batch_run(hh, lab_h, stream)
+            scc.scc_batch_destroy(hh)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        h2d = sum(int(a.numel()) * a.element_size() for a in hp)
+        e2e = {"value": world * na * k2 / (t1 - t0), "unit": UNIT, "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": 4 * nv, "steps": k2,
+               "includes": "scc_batch_create (copy + validation) + scc_batch_run + scc_batch_destroy"}
+
+    # ---- the CPU oracle on all host cores, on a sample of the batch
+    cpu = None
+    if not args.no_cpu_baseline and rank == 0:
+        sample = _stratified(order, max(16, G // 16))
+        t, cores = _oracle_all_cores(p, sample)
+        na_s = int(sum(p.ebase[g + 1] - p.ebase[g] for g in sample))
+        cpu = {"value": na_s / t, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"{len(sample)} of the {G} graphs spread over the size range, one graph per thread",
+               "seconds": t}
+    scc.scc_batch_destroy(h)
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+                "config": {**config, "tau": cfg.tau, "block": cfg.block, "lambda": cfg.lambda_,
+                           "beta": cfg.beta, "blocks": st["blocks"], "workspace_gb": st["workspace_bytes"] / 2**30,
+                           "step": "scc_batch_run (CUDA graph replay of the persistent launch)",
+                           "autotuned": tuned},
+                "graphs_per_s": graphs_per_s, "plain_per_graph": plain,
+                "speedup_vs_plain": (graphs_per_s / plain["graphs_per_s"]) if plain else None,
+                "e2e": e2e, "roofline": roofline, "cpu_baseline": cpu, "gpu_launches": launches, "clocks": clk,
+                "gen_seconds": t_gen}
+        if per_graph:
+            line["per_graph"] = per_graph
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
 # ------------------------------------------------------------------- ours --
 def main():
     ap = argparse.ArgumentParser()
@@ -179,8 +427,14 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--verbose", action="store_true")
+    ap.add_argument("--autotune", action="store_true", help="batch workloads: run the autotuner first")
+    ap.add_argument("--no-plain", action="store_true", help="batch workloads: skip the per-graph comparison")
+    ap.add_argument("--batch-block", type=int, default=None, help="batch workloads: threads per block")
+    ap.add_argument("--batch-bps", type=int, default=None, help="batch workloads: blocks per SM (0 = auto)")
     args = ap.parse_args()
     spec = dict(WORKLOADS[args.workload])
+    if spec["kind"] == "batch":
+        return run_batch(args, spec)
     if args.rmat_scale and spec["kind"] == "rmat":
         spec["scale"] = args.rmat_scale
     if args.impl == "reference":

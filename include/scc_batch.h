@@ -49,10 +49,13 @@ extern "C" {
 #endif
 
 /*
- * Tunables of the batched kernel (results never depend on them):
+ * Tunables of the batched kernel (results never depend on them). Defaults:
+ * tau 512, block 512, lambda 256, sigma 50, seeds 32, beta 2, blocks_per_sm 0.
  *   tau     VGC edge budget of a warp's local search (Sec. 3.2), 1..65536.
  *   block   threads per block, 128, 256 or 512 (one block runs one graph).
  *   lambda  first hash-bag chunk, a power of two in [256, 65536] (Sec. 3.3).
+ *           Every round of a search reads at least the first chunk, and one
+ *           block's rounds are short, so the default is the smallest, 256.
  *   sigma   hash-bag samples per chunk (Sec. 3.3), >= 1.
  *   seeds   frontier items one warp takes per task, 1..32.
  *   beta    prefix-doubling multiplier, > 1 (Alg. 1).
@@ -97,7 +100,7 @@ SCC_API int scc_batch_run(scc_batch_handle h, int32_t* labels_out, cudaStream_t 
  * Autotuner: times the batched kernel on a sample of about `sample` graphs
  * (spread over the size range; all graphs when sample <= 0 or >= G) for every
  * configuration of the grid tau in {16, 64, 256, 1024, 4096} x block in
- * {128, 256, 512} x lambda in {1024, 4096, 16384, 65536}, keeps the fastest in
+ * {128, 256, 512} x lambda in {256, 1024, 4096, 16384}, keeps the fastest in
  * the handle and returns it (and its time in milliseconds) when the pointers
  * are not NULL.
  */

@@ -94,6 +94,14 @@ SCC_API int scc_debug_pair_table(const uint64_t* keys, int64_t count, int64_t in
 /* Number of kernel launches the library has issued since it was loaded. */
 SCC_API int64_t scc_debug_launch_count(void);
 
+/* Batched SCC (scc_batch.h): for every graph g of the last scc_batch_run,
+   out[11g .. 11g + 5] = device globaltimer (ns) at its start and at the end of
+   the transpose, the first SCC, the class trimming, the batches and the
+   labels; out[11g + 6] = the block that ran it; out[11g + 7 .. 11g + 10] =
+   engine rounds of its batches, pair searches, pair searches rerun after a
+   table or the bag filled up, batches labelled. out: host uint64[11 * G]. */
+SCC_API int scc_debug_batch_times(struct scc_batch* h, uint64_t* out);
+
 #ifdef __cplusplus
 }
 #endif

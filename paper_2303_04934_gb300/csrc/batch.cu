@@ -42,6 +42,10 @@ namespace {
 constexpr int kBatchMaxBlock = 512;
 constexpr int kBatchTrimPasses = 4;
 constexpr long long kBatchMinTable = 1024;
+// per-graph record: start, transpose done, first SCC done, class trimming done,
+// batches done, end (globaltimer ns); block; engine rounds, pair searches, pair
+// searches rerun (a table or the bag was full), batches labelled
+constexpr int kTimeWords = 11;
 
 // ------------------------------------------------------------ working memory --
 // Byte offsets of a block's arrays inside its slice (all 256-byte aligned).
@@ -114,6 +118,7 @@ struct BatchArgs {
     int32_t* labels;       // output, packed like the vertices
     int* next;             // work-queue head (zeroed by the reset kernel)
     int* err;              // first error (SCC_ERR_*), zeroed by the reset kernel
+    unsigned long long* times;  // per graph (kTimeWords): phase ends (globaltimer ns), block
     unsigned char* ws;
     size_t ws_stride;
     WsLayout L;
@@ -271,7 +276,10 @@ struct InitVertex {
 // Returns false after an error (recorded in *A.err): the block stops.
 __device__ bool scc_one_graph(const BatchArgs& A, Ws& W, int g, BlockShared& sh,
                               const LocalQueue<uint32_t>& q32, const LocalQueue<uint64_t>& q64, uint32_t& gr,
-                              uint32_t& si, uint32_t& tagc) {
+                              uint32_t& si, uint32_t& tagc, unsigned long long* tm) {
+    auto mark = [&](int k) {
+        if (threadIdx.x == 0) tm[k] = globaltimer_ns();
+    };
     const long long vb = A.vbase[g];
     const int n = (int)(A.vbase[g + 1] - vb);
     const long long eb = A.ebase[g];
@@ -280,7 +288,10 @@ __device__ bool scc_one_graph(const BatchArgs& A, Ws& W, int g, BlockShared& sh,
     const int32_t* adj = A.targets + eb;
     int32_t* out = A.labels + vb;
     const int tid = threadIdx.x, nt = blockDim.x;
-    if (n == 0) return true;
+    if (n == 0) {
+        for (int k = 1; k < 5; ++k) mark(k);
+        return true;
+    }
 
     // ---- 1. G^T: in-degrees, scan, placement
     for (int v = tid; v <= n; v += nt) W.cnt[v] = 0;
@@ -305,6 +316,7 @@ __device__ bool scc_one_graph(const BatchArgs& A, Ws& W, int g, BlockShared& sh,
     }
     __syncthreads();
 
+    mark(1);
     // ---- 2. trimming; 3. active list (ordered) for the pivot permutation
     unsigned long long na = 0;
     for (int v = tid; v < n; v += nt) {
@@ -372,6 +384,7 @@ __device__ bool scc_one_graph(const BatchArgs& A, Ws& W, int g, BlockShared& sh,
         active -= (long long)block_sum(c, sh);
     }
 
+    mark(2);
     // ---- 5. trimming inside the classes: a vertex with no arc from or no arc
     // to an active vertex of its own class is a singleton
     for (int pass = 0; pass < kBatchTrimPasses && active > 0; ++pass) {
@@ -400,6 +413,9 @@ __device__ bool scc_one_graph(const BatchArgs& A, Ws& W, int g, BlockShared& sh,
         if ((long long)got * 32 < active) break;
     }
 
+    mark(3);
+    const uint32_t gr_batches = gr;
+    unsigned long long n_search = 0, n_retry = 0, n_batch = 0;
     // ---- 6. prefix-doubling batches over the pivot order
     long long lo = 1;
     double width = A.beta;
@@ -451,14 +467,15 @@ __device__ bool scc_one_graph(const BatchArgs& A, Ws& W, int g, BlockShared& sh,
                                                              si, why))
                 return false;
             ++si;
+            ++n_search;
             const long long pairs0 = (long long)ld_volatile(&sc.inserted[0]);
             const long long pairs1 = (long long)ld_volatile(&sc.inserted[1]);
             __syncthreads();
-            if (why < 0) {  // the hash bag is sized so that this never happens
+            if (why < 0 && why != SCC_ERR_CAPACITY) {
                 if (tid == 0) atomicCAS(A.err, 0, why);
                 return false;
             }
-            if (why == 1) {
+            if (why == 1 || why == SCC_ERR_CAPACITY) {  // a table or the hash bag is full
                 // the search stopped early: empty both tables and the used part of
                 // both hash-bag slot arrays, then grow the tables or, at full
                 // size, halve the batch
@@ -471,7 +488,7 @@ __device__ bool scc_one_graph(const BatchArgs& A, Ws& W, int g, BlockShared& sh,
                 }
                 __syncthreads();
                 const long long c = max(cap[0], cap[1]);
-                if (c < A.D.tcap) {
+                if (why == 1 && c < A.D.tcap) {
                     cap_floor = 2 * c;
                 } else if (hi - lo > 1) {
                     hi = lo + (hi - lo) / 2;
@@ -479,6 +496,7 @@ __device__ bool scc_one_graph(const BatchArgs& A, Ws& W, int g, BlockShared& sh,
                     if (tid == 0) atomicCAS(A.err, 0, SCC_ERR_CAPACITY);
                     return false;
                 }
+                ++n_retry;
                 continue;
             }
             // labelling (Alg. 1; Sec. 4.4), which also empties both tables
@@ -493,12 +511,20 @@ __device__ bool scc_one_graph(const BatchArgs& A, Ws& W, int g, BlockShared& sh,
             a_prev[0] = pairs0;
             a_prev[1] = pairs1;
             cap_floor = 0;
+            ++n_batch;
             break;
         }
         if (width < (double)na) width *= A.beta;
         lo = hi;
     }
 
+    mark(4);
+    if (threadIdx.x == 0) {
+        tm[7] = gr - gr_batches;
+        tm[8] = n_search;
+        tm[9] = n_retry;
+        tm[10] = n_batch;
+    }
     // ---- 7. canonical labels: the smallest vertex of each SCC (by its rep)
     for (int v = tid; v < n; v += nt) W.cnt[v] = INT_MAX;
     __syncthreads();
@@ -520,7 +546,7 @@ constexpr int kBQ = 256;  // = PolPair::kQueue = PolSingle::kQueue
 static_assert(PolPair::kQueue == kBQ && PolSingle::kQueue == kBQ, "one queue size for both searches");
 size_t batch_smem_bytes(int block) { return (size_t)(block / 32) * kBQ * (8 + 8 + 4); }
 
-__global__ void __launch_bounds__(kBatchMaxBlock, 1) k_batch_scc(BatchArgs A) {
+__device__ __forceinline__ void batch_body(const BatchArgs& A) {
     extern __shared__ unsigned char dsm[];
     __shared__ BlockShared sh;
     const int nw = blockDim.x >> 5, w = threadIdx.x >> 5;
@@ -550,10 +576,24 @@ __global__ void __launch_bounds__(kBatchMaxBlock, 1) k_batch_scc(BatchArgs A) {
         const int g = sh.graph;
         __syncthreads();
         if (g < 0) break;
-        if (!scc_one_graph(A, W, g, sh, q32, q64, gr, si, tagc)) break;
+        unsigned long long* tm = A.times + (size_t)kTimeWords * g;
+        if (threadIdx.x == 0) {
+            tm[0] = globaltimer_ns();
+            tm[6] = blockIdx.x;
+            for (int k = 7; k < kTimeWords; ++k) tm[k] = 0;
+        }
+        if (!scc_one_graph(A, W, g, sh, q32, q64, gr, si, tagc, tm)) break;
+        if (threadIdx.x == 0) tm[5] = globaltimer_ns();
     }
     if (threadIdx.x == 0) *W.tag = tagc;
 }
+
+// 128 registers a thread: up to 512 threads per SM (a tighter budget spills
+// and was slower on the mixed batch of tori and R-MAT graphs)
+__global__ void __launch_bounds__(kBatchMaxBlock, 1) k_batch_scc(BatchArgs A) { batch_body(A); }
+
+using BatchKernel = void (*)(BatchArgs);
+BatchKernel batch_kernel_for(const scc_batch_config&) { return k_batch_scc; }
 
 // Fresh slices: everything zero except the tables and the hash-bag slot
 // arrays, which start empty (all-ones).
@@ -592,6 +632,7 @@ struct scc_batch {
     std::vector<int32_t> order_h;
     std::vector<long long> vb_h, eb_h;
     int* flags = nullptr;           // [0] work-queue head, [1] error
+    unsigned long long* times = nullptr;  // per graph: start, end, block (3 words)
     int32_t* labels = nullptr;      // internal output (host destinations, tuning)
     scc_batch_config cfg;
     // working memory for the current configuration
@@ -639,18 +680,20 @@ int prepare(scc_batch* h, cudaStream_t s) {
     long long t = kBatchMinTable;
     while (t < 2 * d.n_max) t <<= 1;  // one source never fills 3/4 of a table
     d.tcap = t;
-    // the bag holds a round's new items: at most the capacity of each table
-    // (pairs; a round may pass the 3/4 load limit before it stops) or the
-    // vertices (single-reachability); four times that in slots
-    const long long items = 2 * d.tcap + 1024;
+    // the bag holds a round's new items, sized for a pair search from one
+    // source (each vertex at most once per direction), four times that in
+    // slots; a pair search from many sources that fills it is rerun with fewer
+    // sources, like one that fills a table
+    const long long items = 2 * d.n_max + 1024;
     d.nslots = ((std::max<long long>(4 * items, 4ll * h->cfg.lambda) + kSeg - 1) / kSeg) * kSeg;
     d.hub_cap = (int)std::min<long long>(items, 8192);
     d.segmap_cap = 2 * (d.m_max / kHubSeg) + d.hub_cap + 1024;
     WsLayout L = make_layout(d);
     int per_sm = 0;
     const size_t smem = batch_smem_bytes(h->cfg.block);
-    SCC_CUDA(cudaFuncSetAttribute(k_batch_scc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    SCC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_scc, h->cfg.block, smem));
+    const BatchKernel kern = batch_kernel_for(h->cfg);
+    SCC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    SCC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, h->cfg.block, smem));
     if (per_sm < 1) return SCC_ERR_INVALID_ARG;
     if (h->cfg.blocks_per_sm > 0) per_sm = std::min(per_sm, h->cfg.blocks_per_sm);
     size_t free_b = 0, total_b = 0;
@@ -695,6 +738,7 @@ BatchArgs make_args(scc_batch* h, const int32_t* order, int norder, int32_t* out
     A.labels = out;
     A.next = h->flags;
     A.err = h->flags + 1;
+    A.times = h->times;
     A.ws = h->ws;
     A.ws_stride = h->ws_stride;
     A.L = h->L;
@@ -712,7 +756,7 @@ int enqueue(scc_batch* h, const int32_t* order, int norder, int32_t* out, cudaSt
     BatchArgs A = make_args(h, order, norder, out);
     k_batch_reset<<<1, 1, 0, s>>>(h->flags, h->flags + 1);
     SCC_LAUNCH();
-    k_batch_scc<<<h->blocks, h->cfg.block, batch_smem_bytes(h->cfg.block), s>>>(A);
+    batch_kernel_for(h->cfg)<<<h->blocks, h->cfg.block, batch_smem_bytes(h->cfg.block), s>>>(A);
     SCC_LAUNCH();
     return SCC_OK;
 }
@@ -727,7 +771,7 @@ int capture(scc_batch* h, const int32_t* order, int norder, int32_t* out) {
     if (rc == SCC_OK) {
         BatchArgs A = make_args(h, order, norder, out);
         k_batch_reset<<<1, 1, 0, cs>>>(h->flags, h->flags + 1);
-        k_batch_scc<<<h->blocks, h->cfg.block, batch_smem_bytes(h->cfg.block), cs>>>(A);
+        batch_kernel_for(h->cfg)<<<h->blocks, h->cfg.block, batch_smem_bytes(h->cfg.block), cs>>>(A);
         rc = cuda_err(cudaGetLastError());
         const int rc2 = cuda_err(cudaStreamEndCapture(cs, &graph));
         if (rc == SCC_OK) rc = rc2;
@@ -788,6 +832,7 @@ void batch_free(scc_batch* h, cudaStream_t s) {
     dfree(h->targets, s);
     dfree(h->order, s);
     dfree(h->flags, s);
+    dfree(h->times, s);
     dfree(h->labels, s);
 }
 
@@ -830,6 +875,7 @@ int batch_create_impl(scc_batch* h, int32_t G, const int64_t* vbase, const int64
     SCC_TRY(dalloc_t(&h->offsets, (size_t)(h->nv + G) + 1, s));
     SCC_TRY(dalloc_t(&h->targets, (size_t)h->na + 1, s));
     SCC_TRY(dalloc_t(&h->flags, 2, s));
+    SCC_TRY(dalloc_t(&h->times, (size_t)kTimeWords * G + 1, s));
     SCC_TRY(dalloc_t(&h->labels, (size_t)h->nv + 1, s));
     SCC_CUDA(cudaMemcpyAsync(h->vbase, h->vb_h.data(), sizeof(long long) * ((size_t)G + 1), cudaMemcpyHostToDevice, s));
     SCC_CUDA(cudaMemcpyAsync(h->ebase, h->eb_h.data(), sizeof(long long) * ((size_t)G + 1), cudaMemcpyHostToDevice, s));
@@ -881,8 +927,8 @@ extern "C" {
 SCC_API int scc_batch_config_default(scc_batch_config* cfg) {
     if (!cfg) return SCC_ERR_INVALID_ARG;
     cfg->tau = 512;
-    cfg->block = 256;
-    cfg->lambda = 4096;
+    cfg->block = 512;
+    cfg->lambda = 256;
     cfg->sigma = 50;
     cfg->seeds = 32;
     cfg->beta = 2.0;
@@ -974,7 +1020,7 @@ SCC_API int scc_batch_autotune(scc_batch_handle h, int32_t sample, cudaStream_t 
     SCC_CUDA(cudaMemcpyAsync(dsub, sub.data(), sizeof(int32_t) * sub.size(), cudaMemcpyHostToDevice, stream));
     const int taus[] = {16, 64, 256, 1024, 4096};
     const int blocks[] = {128, 256, 512};
-    const int lambdas[] = {1024, 4096, 16384, 65536};
+    const int lambdas[] = {256, 1024, 4096, 16384};
     scc_batch_config bc = base;
     double bms = 1e300;
     int rc = SCC_OK;
@@ -1007,6 +1053,13 @@ SCC_API int scc_batch_autotune(scc_batch_handle h, int32_t sample, cudaStream_t 
     if (rc2 != SCC_OK) return rc2;
     if (best) *best = bc;
     if (best_ms) *best_ms = bms;
+    return SCC_OK;
+}
+
+SCC_API int scc_debug_batch_times(scc_batch_handle h, uint64_t* out) {
+    if (!h || (!out && h->G > 0)) return SCC_ERR_INVALID_ARG;
+    if (h->G == 0) return SCC_OK;
+    SCC_CUDA(cudaMemcpy(out, h->times, sizeof(uint64_t) * kTimeWords * (size_t)h->G, cudaMemcpyDeviceToHost));
     return SCC_OK;
 }
 

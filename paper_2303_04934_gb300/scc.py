@@ -34,6 +34,7 @@ EXPORTED = [
     "scc_debug_multi_reach", "scc_debug_hashbag", "scc_debug_pair_table", "scc_debug_launch_count",
     "scc_batch_config_default", "scc_batch_create", "scc_batch_destroy", "scc_batch_set_config",
     "scc_batch_get_config", "scc_batch_run", "scc_batch_autotune", "scc_batch_get_stats",
+    "scc_debug_batch_times",
 ]
 
 
@@ -130,6 +131,7 @@ def load() -> ctypes.CDLL:
         "scc_batch_run": ([vp, vp, vp], ctypes.c_int),
         "scc_batch_autotune": ([vp, i32, vp, P(scc_batch_config), P(ctypes.c_double)], ctypes.c_int),
         "scc_batch_get_stats": ([vp, P(scc_batch_stats)], ctypes.c_int),
+        "scc_debug_batch_times": ([vp, vp], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -263,6 +265,15 @@ def scc_batch_get_stats(h) -> dict:
     s = scc_batch_stats()
     _check(load().scc_batch_get_stats(h, ctypes.byref(s)), "scc_batch_get_stats")
     return s.as_dict()
+
+
+def scc_debug_batch_times(h, G: int) -> np.ndarray:
+    """(G, 11) uint64 per graph of the last run: globaltimer ns at its start and
+    after the transpose, first SCC, class trimming, batches and labels; block;
+    batch rounds, pair searches, reruns, batches."""
+    out = np.zeros(11 * max(G, 1), np.uint64)
+    _check(load().scc_debug_batch_times(h, _ptr(out)), "scc_debug_batch_times")
+    return out[:11 * G].reshape(G, 11)
 
 
 class SccBatch:

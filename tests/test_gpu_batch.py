@@ -110,6 +110,7 @@ def test_batch_mixed_generator_and_autotune():
     with scc.SccBatch(p) as B:
         best, ms = scc.scc_batch_autotune(B.h, sample=6)
         assert ms > 0 and best.block in (128, 256, 512) and best.tau in (16, 64, 256, 1024, 4096)
+        assert best.lambda_ in (256, 1024, 4096, 16384)
         got = scc.scc_batch_get_config(B.h)
         assert (got.tau, got.block, got.lambda_) == (best.tau, best.block, best.lambda_)
         out = B.labels()
