@@ -671,12 +671,14 @@ void drop_exec(scc_batch* h) {
     h->exec_valid = false;
 }
 
-// Working memory for the current configuration: one slice per block, sized for
-// the largest graph, within a budget of device memory.
-int prepare(scc_batch* h, cudaStream_t s) {
+// Working-memory plan for a configuration: one slice per block, sized for the
+// largest graph (n_max, m_max), as many blocks as fit on the device (at most
+// `gcap`, the graphs of one launch) within `budget` bytes.
+int plan_workspace(const DeviceInfo& di, const scc_batch_config& cfg, long long n_max, long long m_max, long long gcap,
+                   size_t budget, WsLayout* Lo, BatchDims* Do, int* blocks_out) {
     BatchDims d;
-    d.n_max = std::max<long long>(h->n_max, 1);
-    d.m_max = std::max<long long>(h->m_max, 1);
+    d.n_max = std::max<long long>(n_max, 1);
+    d.m_max = std::max<long long>(m_max, 1);
     long long t = kBatchMinTable;
     while (t < 2 * d.n_max) t <<= 1;  // one source never fills 3/4 of a table
     d.tcap = t;
@@ -685,23 +687,46 @@ int prepare(scc_batch* h, cudaStream_t s) {
     // slots; a pair search from many sources that fills it is rerun with fewer
     // sources, like one that fills a table
     const long long items = 2 * d.n_max + 1024;
-    d.nslots = ((std::max<long long>(4 * items, 4ll * h->cfg.lambda) + kSeg - 1) / kSeg) * kSeg;
+    d.nslots = ((std::max<long long>(4 * items, 4ll * cfg.lambda) + kSeg - 1) / kSeg) * kSeg;
     d.hub_cap = (int)std::min<long long>(items, 8192);
     d.segmap_cap = 2 * (d.m_max / kHubSeg) + d.hub_cap + 1024;
     WsLayout L = make_layout(d);
     int per_sm = 0;
-    const size_t smem = batch_smem_bytes(h->cfg.block);
-    const BatchKernel kern = batch_kernel_for(h->cfg);
+    const size_t smem = batch_smem_bytes(cfg.block);
+    const BatchKernel kern = batch_kernel_for(cfg);
     SCC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    SCC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, h->cfg.block, smem));
+    SCC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, cfg.block, smem));
     if (per_sm < 1) return SCC_ERR_INVALID_ARG;
-    if (h->cfg.blocks_per_sm > 0) per_sm = std::min(per_sm, h->cfg.blocks_per_sm);
-    size_t free_b = 0, total_b = 0;
-    SCC_CUDA(cudaMemGetInfo(&free_b, &total_b));
-    const size_t budget = std::min<size_t>(free_b / 2, (size_t)96 << 30);
-    long long blocks = (long long)per_sm * h->di.num_sms;
+    if (cfg.blocks_per_sm > 0) per_sm = std::min(per_sm, cfg.blocks_per_sm);
+    long long blocks = (long long)per_sm * di.num_sms;
     blocks = std::min<long long>(blocks, std::max<long long>(1, (long long)(budget / L.bytes)));
-    blocks = std::min<long long>(blocks, std::max<int32_t>(h->G, 1));
+    blocks = std::min<long long>(blocks, std::max<long long>(gcap, 1));
+    *Lo = L;
+    *Do = d;
+    *blocks_out = (int)blocks;
+    return SCC_OK;
+}
+
+// Every slice starts with empty bags and tables and untagged maxima.
+int init_workspace(unsigned char* ws, const WsLayout& L, const BatchDims& d, int blocks, int num_sms, cudaStream_t s) {
+    SCC_CUDA(cudaMemsetAsync(ws, 0, L.bytes * (size_t)blocks, s));
+    k_batch_init_ws<<<num_sms * 4, 256, 0, s>>>(ws, L.bytes, blocks, L, d);
+    SCC_LAUNCH();
+    return SCC_OK;
+}
+
+size_t default_budget() {
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) return 0;
+    return std::min<size_t>(free_b / 2, (size_t)96 << 30);
+}
+
+// Working memory of a batch handle for its current configuration.
+int prepare(scc_batch* h, cudaStream_t s) {
+    WsLayout L;
+    BatchDims d;
+    int blocks = 0;
+    SCC_TRY(plan_workspace(h->di, h->cfg, h->n_max, h->m_max, h->G, default_budget(), &L, &d, &blocks));
     const size_t need = L.bytes * (size_t)blocks;
     if (h->ws && (h->ws_bytes < need)) {
         dfree(h->ws, s);
@@ -712,12 +737,9 @@ int prepare(scc_batch* h, cudaStream_t s) {
         SCC_TRY(dalloc(reinterpret_cast<void**>(&h->ws), need, s));
         h->ws_bytes = need;
     }
-    // every slice starts with empty bags and tables and untagged maxima
-    SCC_CUDA(cudaMemsetAsync(h->ws, 0, need, s));
-    k_batch_init_ws<<<h->di.num_sms * 4, 256, 0, s>>>(h->ws, L.bytes, (int)blocks, L, d);
-    SCC_LAUNCH();
+    SCC_TRY(init_workspace(h->ws, L, d, blocks, h->di.num_sms, s));
     h->ws_stride = L.bytes;
-    h->blocks = (int)blocks;
+    h->blocks = blocks;
     h->L = L;
     h->D = d;
     h->st.blocks = h->blocks;
@@ -725,31 +747,38 @@ int prepare(scc_batch* h, cudaStream_t s) {
     return SCC_OK;
 }
 
-BatchArgs make_args(scc_batch* h, const int32_t* order, int norder, int32_t* out) {
+BatchArgs args_for(const scc_batch_config& cfg, unsigned char* ws, const WsLayout& L, const BatchDims& D, int* flags,
+                   unsigned long long* times, int32_t G, const long long* vbase, const long long* ebase,
+                   const int32_t* offsets, const int32_t* targets, const int32_t* order, int norder, int32_t* out) {
     BatchArgs A;
     memset(&A, 0, sizeof(A));
-    A.G = h->G;
-    A.vbase = h->vbase;
-    A.ebase = h->ebase;
-    A.offsets = h->offsets;
-    A.targets = h->targets;
+    A.G = G;
+    A.vbase = vbase;
+    A.ebase = ebase;
+    A.offsets = offsets;
+    A.targets = targets;
     A.order = order;
     A.norder = norder;
     A.labels = out;
-    A.next = h->flags;
-    A.err = h->flags + 1;
-    A.times = h->times;
-    A.ws = h->ws;
-    A.ws_stride = h->ws_stride;
-    A.L = h->L;
-    A.D = h->D;
-    A.tau = h->cfg.tau;
-    A.seeds = h->cfg.seeds;
-    A.lambda = h->cfg.lambda;
-    A.sigma = h->cfg.sigma;
-    A.beta = h->cfg.beta;
-    A.seed = h->cfg.seed;
+    A.next = flags;
+    A.err = flags + 1;
+    A.times = times;
+    A.ws = ws;
+    A.ws_stride = L.bytes;
+    A.L = L;
+    A.D = D;
+    A.tau = cfg.tau;
+    A.seeds = cfg.seeds;
+    A.lambda = cfg.lambda;
+    A.sigma = cfg.sigma;
+    A.beta = cfg.beta;
+    A.seed = cfg.seed;
     return A;
+}
+
+BatchArgs make_args(scc_batch* h, const int32_t* order, int norder, int32_t* out) {
+    return args_for(h->cfg, h->ws, h->L, h->D, h->flags, h->times, h->G, h->vbase, h->ebase, h->offsets, h->targets,
+                    order, norder, out);
 }
 
 int enqueue(scc_batch* h, const int32_t* order, int norder, int32_t* out, cudaStream_t s) {
@@ -918,6 +947,105 @@ int batch_create_impl(scc_batch* h, int32_t G, const int64_t* vbase, const int64
 }
 
 }  // namespace
+
+// ------------------------------------------------------------ batch runner --
+// The batched kernel on caller-owned packed device arrays, with working memory
+// allocated once (for graphs of up to n_max vertices and m_max arcs, up to
+// gcap graphs per launch): what a serving loop launches over and over.
+struct BatchRunner {
+    DeviceInfo di;
+    scc_batch_config cfg;
+    long long gcap = 0;
+    unsigned char* ws = nullptr;
+    size_t bytes = 0;
+    WsLayout L;
+    BatchDims D;
+    int blocks = 0;
+    int* flags = nullptr;
+    unsigned long long* times = nullptr;
+};
+
+int batch_runner_create(const scc_batch_config* cfg, long long n_max, long long m_max, long long gcap, size_t budget,
+                        cudaStream_t s, BatchRunner** out) {
+    *out = nullptr;
+    BatchRunner* r = new (std::nothrow) BatchRunner();
+    if (!r) return SCC_ERR_OOM;
+    auto fail = [&](int rc) {
+        batch_runner_destroy(r, s);
+        return rc;
+    };
+    r->gcap = std::max<long long>(gcap, 1);
+    if (cfg) r->cfg = *cfg;
+    else scc_batch_config_default(&r->cfg);
+    if (!valid_config(&r->cfg)) return fail(SCC_ERR_INVALID_ARG);
+    int rc = device_info(&r->di);
+    if (rc == SCC_OK) rc = plan_workspace(r->di, r->cfg, n_max, m_max, r->gcap, budget ? budget : default_budget(),
+                                          &r->L, &r->D, &r->blocks);
+    if (rc == SCC_OK) rc = dalloc(reinterpret_cast<void**>(&r->ws), r->L.bytes * (size_t)r->blocks, s);
+    if (rc == SCC_OK) rc = dalloc_t(&r->flags, 2, s);
+    if (rc == SCC_OK) rc = dalloc_t(&r->times, (size_t)kTimeWords * r->gcap, s);
+    if (rc == SCC_OK) rc = init_workspace(r->ws, r->L, r->D, r->blocks, r->di.num_sms, s);
+    if (rc != SCC_OK) return fail(rc);
+    r->bytes = r->L.bytes * (size_t)r->blocks + 8 * (size_t)kTimeWords * r->gcap;
+    *out = r;
+    return SCC_OK;
+}
+
+void batch_runner_destroy(BatchRunner* r, cudaStream_t s) {
+    if (!r) return;
+    dfree(r->ws, s);
+    dfree(r->flags, s);
+    dfree(r->times, s);
+    delete r;
+}
+
+// bad[g] = 1 when graph g of a packed batch is malformed (offsets not starting
+// at 0, decreasing or not ending at m_g; a target outside [0, n_g)), else 0.
+__global__ void k_batch_validate_each(int32_t G, const long long* vbase, const long long* ebase, const int32_t* off,
+                                      const int32_t* adj, int* bad) {
+    for (int g = blockIdx.x; g < G; g += gridDim.x) {
+        const long long n = vbase[g + 1] - vbase[g];
+        const long long m = ebase[g + 1] - ebase[g];
+        const int32_t* o = off + vbase[g] + g;
+        const int32_t* a = adj + ebase[g];
+        __shared__ int s_bad;
+        if (threadIdx.x == 0) s_bad = (o[0] != 0 || (long long)o[n] != m);
+        __syncthreads();
+        bool b = false;
+        for (long long v = threadIdx.x; v < n; v += blockDim.x) b |= o[v] > o[v + 1];
+        for (long long e = threadIdx.x; e < m; e += blockDim.x) b |= a[e] < 0 || (long long)a[e] >= n;
+        if (b) s_bad = 1;
+        __syncthreads();
+        if (threadIdx.x == 0) bad[g] = s_bad;
+        __syncthreads();
+    }
+}
+
+int batch_validate_each(int32_t G, const long long* vbase, const long long* ebase, const int32_t* offsets,
+                        const int32_t* targets, int* bad, cudaStream_t s) {
+    if (G <= 0) return SCC_OK;
+    k_batch_validate_each<<<std::min<int32_t>(G, 65535), 256, 0, s>>>(G, vbase, ebase, offsets, targets, bad);
+    SCC_LAUNCH();
+    return SCC_OK;
+}
+
+bool batch_runner_fits(const BatchRunner* r, long long n, long long m) { return n <= r->D.n_max && m <= r->D.m_max; }
+size_t batch_runner_bytes(const BatchRunner* r) { return r->bytes; }
+const int* batch_runner_err(const BatchRunner* r) { return r->flags + 1; }
+
+int batch_runner_enqueue(BatchRunner* r, int32_t G, const long long* vbase, const long long* ebase,
+                         const int32_t* offsets, const int32_t* targets, const int32_t* order, int32_t norder,
+                         int32_t* out, cudaStream_t s) {
+    if (norder > r->gcap) return SCC_ERR_INVALID_ARG;
+    BatchArgs A = args_for(r->cfg, r->ws, r->L, r->D, r->flags, r->times, G, vbase, ebase, offsets, targets, order,
+                           norder, out);
+    k_batch_reset<<<1, 1, 0, s>>>(r->flags, r->flags + 1);
+    SCC_LAUNCH();
+    batch_kernel_for(r->cfg)<<<r->blocks, r->cfg.block, batch_smem_bytes(r->cfg.block), s>>>(A);
+    SCC_LAUNCH();
+    return SCC_OK;
+}
+
 }  // namespace scc
 
 using namespace scc;

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include "../../include/scc.h"
+#include "../../include/scc_batch.h"
 
 namespace scc {
 
@@ -260,6 +261,23 @@ struct BgssResult {
 size_t bgss_ctl_bytes();
 int bgss_full_grid(int num_sms);
 int run_bgss_device(const BgssArgs& a, BgssResult* res, cudaStream_t st);
+
+// Batched SCC kernel on caller-owned packed device arrays (batch.cu), working
+// memory allocated once: for a serving loop. budget 0: half the free memory,
+// at most 96 GiB.
+struct BatchRunner;
+int batch_runner_create(const scc_batch_config* cfg, long long n_max, long long m_max, long long gcap, size_t budget,
+                        cudaStream_t s, BatchRunner** out);
+void batch_runner_destroy(BatchRunner* r, cudaStream_t s);
+bool batch_runner_fits(const BatchRunner* r, long long n, long long m);
+size_t batch_runner_bytes(const BatchRunner* r);
+const int* batch_runner_err(const BatchRunner* r);  // device error flag of the last launch
+// bad[g] (device int[G]) = 1 when graph g of a packed batch is malformed
+int batch_validate_each(int32_t G, const long long* vbase, const long long* ebase, const int32_t* offsets,
+                        const int32_t* targets, int* bad, cudaStream_t s);
+int batch_runner_enqueue(BatchRunner* r, int32_t G, const long long* vbase, const long long* ebase,
+                         const int32_t* offsets, const int32_t* targets, const int32_t* order, int32_t norder,
+                         int32_t* out, cudaStream_t s);
 
 // Mask reachability on fixed buffers (no allocation, no events).
 int run_mask_fixed(const int32_t* off, const int32_t* adj, int32_t n, const int32_t* sources, int32_t k,

@@ -1,5 +1,5 @@
-"""Thin Python binding of the C ABI in ``include/scc.h``, ``include/scc_batch.h``
-and ``include/scc_debug.h``.
+"""Thin Python binding of the C ABI in ``include/scc.h``, ``include/scc_batch.h``,
+``include/scc_serve.h`` and ``include/scc_debug.h``.
 
 Argument marshalling only: every step runs in the CUDA library
 ``_lib/libscc_gb300.so``. Arrays may be CUDA torch tensors (device pointers are
@@ -35,6 +35,9 @@ EXPORTED = [
     "scc_batch_config_default", "scc_batch_create", "scc_batch_destroy", "scc_batch_set_config",
     "scc_batch_get_config", "scc_batch_run", "scc_batch_autotune", "scc_batch_get_stats",
     "scc_debug_batch_times",
+    "scc_server_config_default", "scc_server_create", "scc_server_destroy", "scc_server_add_graph",
+    "scc_server_remove_graph", "scc_server_submit_scc", "scc_server_submit_reach", "scc_server_wait",
+    "scc_server_drain", "scc_server_get_stats", "scc_server_reset_stats",
 ]
 
 
@@ -74,6 +77,24 @@ class scc_batch_stats(ctypes.Structure):
                 ("max_vertices", ctypes.c_int32), ("max_arcs", ctypes.c_int64), ("blocks", ctypes.c_int32),
                 ("workspace_bytes", ctypes.c_int64), ("ms_last_run", ctypes.c_double), ("captures", ctypes.c_int32),
                 ("replays", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class scc_server_config(ctypes.Structure):
+    _fields_ = [("mem_cap_bytes", ctypes.c_int64), ("batch_vertices", ctypes.c_int32),
+                ("batch_graphs", ctypes.c_int32), ("merge_reach", ctypes.c_int32), ("prefetch", ctypes.c_int32),
+                ("max_bypass_ms", ctypes.c_double)]
+
+
+class scc_server_stats(ctypes.Structure):
+    _fields_ = [(f, ctypes.c_int64) for f in (
+        "submitted", "completed", "failed", "scc_requests", "reach_requests", "units", "batched_launches",
+        "batched_graphs", "plain_scc", "reach_launches", "reach_shared", "mem_in_use", "mem_peak", "mem_cap")] + [
+        ("max_admitted", ctypes.c_int32), ("resident_graphs", ctypes.c_int32)] + [
+        (f, ctypes.c_double) for f in ("p50_ms", "p99_ms", "scc_p50_ms", "scc_p99_ms", "reach_p50_ms",
+                                        "reach_p99_ms")]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -132,6 +153,17 @@ def load() -> ctypes.CDLL:
         "scc_batch_autotune": ([vp, i32, vp, P(scc_batch_config), P(ctypes.c_double)], ctypes.c_int),
         "scc_batch_get_stats": ([vp, P(scc_batch_stats)], ctypes.c_int),
         "scc_debug_batch_times": ([vp, vp], ctypes.c_int),
+        "scc_server_config_default": ([P(scc_server_config)], ctypes.c_int),
+        "scc_server_create": ([P(scc_server_config), P(vp)], ctypes.c_int),
+        "scc_server_destroy": ([vp], ctypes.c_int),
+        "scc_server_add_graph": ([vp, i32, i64, vp, vp, P(i32)], ctypes.c_int),
+        "scc_server_remove_graph": ([vp, i32], ctypes.c_int),
+        "scc_server_submit_scc": ([vp, i32, i64, vp, vp, vp, P(i64)], ctypes.c_int),
+        "scc_server_submit_reach": ([vp, i32, vp, i32, i32, vp, P(i64)], ctypes.c_int),
+        "scc_server_wait": ([vp, i64, P(i32), P(ctypes.c_double)], ctypes.c_int),
+        "scc_server_drain": ([vp], ctypes.c_int),
+        "scc_server_get_stats": ([vp, P(scc_server_stats)], ctypes.c_int),
+        "scc_server_reset_stats": ([vp], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -313,6 +345,87 @@ class SccBatch:
 
     def stats(self) -> dict:
         return scc_batch_get_stats(self.h)
+
+
+# ------------------------------------------------------------------ serving --
+def scc_server_config_default() -> scc_server_config:
+    c = scc_server_config()
+    _check(load().scc_server_config_default(ctypes.byref(c)), "scc_server_config_default")
+    return c
+
+
+class SccServer:
+    """A request server (include/scc_serve.h). Host arrays handed to the submit
+    calls are kept referenced here until their request has been waited for or
+    drained, so the caller may drop them at once."""
+
+    def __init__(self, config: scc_server_config | None = None):
+        h = ctypes.c_void_p()
+        _check(load().scc_server_create(ctypes.byref(config) if config is not None else None, ctypes.byref(h)),
+               "scc_server_create")
+        self.h = h.value
+        self._keep = {}
+
+    def add_graph(self, n: int, offsets, targets) -> int:
+        gid = ctypes.c_int32()
+        _check(load().scc_server_add_graph(self.h, n, len(targets), _ptr(offsets), _ptr(targets), ctypes.byref(gid)),
+               "scc_server_add_graph")
+        return gid.value
+
+    def remove_graph(self, gid: int) -> None:
+        _check(load().scc_server_remove_graph(self.h, gid), "scc_server_remove_graph")
+
+    def submit_scc(self, n: int, offsets, targets, labels_out) -> int:
+        rid = ctypes.c_int64()
+        _check(load().scc_server_submit_scc(self.h, n, len(targets), _ptr(offsets), _ptr(targets), _ptr(labels_out),
+                                            ctypes.byref(rid)), "scc_server_submit_scc")
+        self._keep[rid.value] = (offsets, targets, labels_out)
+        return rid.value
+
+    def submit_reach(self, gid: int, sources, dir: int, out) -> int:
+        rid = ctypes.c_int64()
+        src = np.ascontiguousarray(sources, dtype=np.int32)
+        _check(load().scc_server_submit_reach(self.h, gid, _ptr(src), len(src), dir, _ptr(out), ctypes.byref(rid)),
+               "scc_server_submit_reach")
+        self._keep[rid.value] = (out,)
+        return rid.value
+
+    def wait(self, rid: int):
+        """(status, latency_ms) of a request, after it completed."""
+        st, lat = ctypes.c_int32(), ctypes.c_double()
+        _check(load().scc_server_wait(self.h, rid, ctypes.byref(st), ctypes.byref(lat)), "scc_server_wait")
+        self._keep.pop(rid, None)
+        return st.value, lat.value
+
+    def drain(self) -> None:
+        _check(load().scc_server_drain(self.h), "scc_server_drain")
+        self._keep.clear()
+
+    def stats(self) -> dict:
+        s = scc_server_stats()
+        _check(load().scc_server_get_stats(self.h, ctypes.byref(s)), "scc_server_get_stats")
+        return s.as_dict()
+
+    def reset_stats(self) -> None:
+        _check(load().scc_server_reset_stats(self.h), "scc_server_reset_stats")
+
+    def close(self):
+        if getattr(self, "h", None):
+            _check(load().scc_server_destroy(self.h), "scc_server_destroy")
+            self.h = None
+            self._keep.clear()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 # -------------------------------------------------------------- debug hooks --
