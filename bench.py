@@ -53,6 +53,11 @@ WORKLOADS = {
     # factor 8); one packed int32 CSR with int64 bases
     "batch4096": dict(kind="batch", G=4096, n_lo=1000, n_hi=1_000_000, seed=0x5CC04),
     "batch256": dict(kind="batch", G=256, n_lo=1000, n_hi=100_000, seed=0x5CC05),
+    # served SCC and reachability: Poisson arrivals, SCC requests on graphs
+    # log-uniform in [1e4, 4e6] vertices (R-MAT edge factor 16, 2D tori p = 0.5,
+    # 3D tori p = 0.3) and reach_multi queries of 1-64 sources on resident graphs
+    "serve": dict(kind="serve", rate=2000.0, seconds=4.0, scc_frac=0.25, n_lo=10_000, n_hi=4_000_000, pool=24,
+                  resident=8, cap=120e9, seed=0x5CC06),
 }
 
 
@@ -412,6 +417,148 @@ def run_batch(args, spec):
     return 0
 
 
+# ------------------------------------------------------------------ serving --
+def _serve_pool(count, n_lo, n_hi, seed):
+    """Graphs log-uniform in [n_lo, n_hi] vertices, cycling R-MAT (edge factor
+    16), 2D tori (p = 0.5) and 3D tori (p = 0.3)."""
+    from paper_2303_04934_gb300 import graphgen as gg
+    rng = np.random.default_rng(seed)
+    out = []
+    for i, n in enumerate(np.exp(rng.uniform(np.log(n_lo), np.log(n_hi), count))):
+        s = (seed * 7919 + i) & (2**63 - 1)
+        kind = i % 3
+        if kind == 0:
+            out.append(gg.rmat(max(1, int(round(np.log2(n)))), 16, seed=s))
+        elif kind == 1:
+            out.append(gg.torus(2, int(np.ceil(np.sqrt(n))), 0.5, seed=s))
+        else:
+            out.append(gg.torus(3, int(np.ceil(n ** (1 / 3))), 0.3, seed=s))
+    return out
+
+
+def _serve_trace(spec, pool, resident, seed):
+    rng = np.random.default_rng(seed)
+    t, reqs = 0.0, []
+    while True:
+        t += rng.exponential(1.0 / spec["rate"])
+        if t >= spec["seconds"]:
+            break
+        if rng.random() < spec["scc_frac"]:
+            reqs.append((t, 0, int(rng.integers(0, len(pool))), None, 0))
+        else:
+            r = int(rng.integers(0, len(resident)))
+            k = int(rng.integers(1, 65))
+            reqs.append((t, 1, r, rng.integers(0, resident[r].n, k).astype(np.int32), int(rng.integers(0, 2))))
+    return reqs
+
+
+def _serve_once(scc, cfg, pool_h, res_h, resident, trace):
+    """Replay the trace open-loop against a fresh server; returns its stats and
+    the wall time from the first arrival to the last completion."""
+    srv = scc.SccServer(cfg)
+    try:
+        gids = [srv.add_graph(g.n, off, adj) for g, (off, adj) in zip(resident, res_h)]
+        lab = [np.empty(g.n, np.int32) for g, _ in pool_h]
+        outs = [np.empty(g.n, np.uint64) for g in resident]
+        srv.reset_stats()
+        t0 = time.perf_counter()
+        for (ta, kind, idx, src, d) in trace:
+            while time.perf_counter() - t0 < ta:
+                pass
+            if kind == 0:
+                g, (off, adj) = pool_h[idx]
+                srv.submit_scc(g.n, off, adj, lab[idx])
+            else:
+                srv.submit_reach(gids[idx], src, d, outs[idx])
+        t_sub = time.perf_counter() - t0
+        srv.drain()
+        wall = time.perf_counter() - t0
+        st = srv.stats()
+    finally:
+        srv.close()
+    return st, wall, t_sub
+
+
+def run_serve(args, spec):
+    """Served SCC and reachability (one step = one replay of the arrival trace):
+    the continuous-batching server against the same trace served one request at
+    a time on the plain path (no batching, no merging, no upload ahead)."""
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    import torch
+    from paper_2303_04934_gb300 import scc
+    if args.impl == "reference":
+        if rank == 0:
+            print(json.dumps({"impl": "reference", "metric": METRIC,
+                              "unavailable": "the served workload has no CPU form; the oracle arm covers the graph "
+                                             "workloads"}), flush=True)
+        return 0
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local_rank)
+    scc.load()
+    t_gen = time.perf_counter()
+    pool = _serve_pool(spec["pool"], spec["n_lo"], spec["n_hi"], spec["seed"])
+    resident = _serve_pool(spec["resident"], spec["n_lo"], spec["n_hi"], spec["seed"] + 1)
+    t_gen = time.perf_counter() - t_gen
+    if args.serve_seconds:
+        spec["seconds"] = args.serve_seconds
+    if args.serve_rate:
+        spec["rate"] = args.serve_rate
+    trace = _serve_trace(spec, pool, resident, spec["seed"] + 2)
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
+    pool_h = [(g, (pin(g.offsets), pin(g.targets))) for g in pool]
+    res_h = [(pin(g.offsets), pin(g.targets)) for g in resident]
+    n_scc = sum(1 for r in trace if r[1] == 0)
+    arcs_scc = sum(pool[r[2]].m for r in trace if r[1] == 0)
+    cfg = scc.scc_server_config_default()
+    cfg.mem_cap_bytes = int(spec["cap"])
+    plain_cfg = scc.scc_server_config_default()
+    plain_cfg.mem_cap_bytes = int(spec["cap"])
+    plain_cfg.batch_vertices = 0
+    plain_cfg.merge_reach = 0
+    plain_cfg.prefetch = 0
+    launches0 = scc.scc_debug_launch_count()
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    st, wall, t_sub = _serve_once(scc, cfg, pool_h, res_h, resident, trace)
+    clk = clocks.stop()
+    launches = scc.scc_debug_launch_count() - launches0
+    plain = None
+    if not args.no_plain:
+        pst, pwall, _ = _serve_once(scc, plain_cfg, pool_h, res_h, resident, trace)
+        plain = {"graphs_per_s": n_scc / pwall, "requests_per_s": len(trace) / pwall, "p50_ms": pst["p50_ms"],
+                 "p99_ms": pst["p99_ms"], "scc_p99_ms": pst["scc_p99_ms"], "reach_p99_ms": pst["reach_p99_ms"],
+                 "wall_s": pwall, "failed": pst["failed"],
+                 "how": "same trace; every request alone on the plain path (scc_graph_create + scc_run, or one "
+                        "reach_multi), no batching, no merging, no upload ahead"}
+    if rank == 0:
+        value = arcs_scc / wall
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": 1, "warmup": 0,
+                "ms_per_step": 1e3 * wall, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "int32", "data": "synthetic",
+                "config": {"workload": f"serve_poisson{int(spec['rate'])}_{spec['seconds']}s_scc{spec['scc_frac']}",
+                           "requests": len(trace), "scc_requests": n_scc, "reach_requests": len(trace) - n_scc,
+                           "scc_pool": [f"{g.name} (n={g.n}, m={g.m})" for g in pool],
+                           "resident": [f"{g.name} (n={g.n}, m={g.m})" for g in resident],
+                           "mem_cap_gb": spec["cap"] / 1e9, "parallelism": f"replicas{world}",
+                           "step": "one open-loop replay of the arrival trace, drained"},
+                "graphs_per_s": n_scc / wall, "requests_per_s": len(trace) / wall, "submit_s": t_sub,
+                "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "scc_p50_ms": st["scc_p50_ms"],
+                "scc_p99_ms": st["scc_p99_ms"], "reach_p50_ms": st["reach_p50_ms"], "reach_p99_ms": st["reach_p99_ms"],
+                "server": {k: st[k] for k in ("units", "batched_launches", "batched_graphs", "plain_scc",
+                                              "reach_launches", "reach_shared", "mem_peak", "max_admitted",
+                                              "failed")},
+                "plain_per_graph": plain,
+                "speedup_vs_plain": {"graphs_per_s": (n_scc / wall) / plain["graphs_per_s"],
+                                     "p99": plain["p99_ms"] / max(st["p99_ms"], 1e-9)} if plain else None,
+                "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": None, "d2h_bytes_per_step": None,
+                        "note": "every request is host in, host out: the served numbers are end to end"},
+                "roofline": None, "cpu_baseline": None, "gpu_launches": launches, "clocks": clk,
+                "gen_seconds": t_gen}
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 # ------------------------------------------------------------------- ours --
 def main():
     ap = argparse.ArgumentParser()
@@ -431,10 +578,14 @@ def main():
     ap.add_argument("--no-plain", action="store_true", help="batch workloads: skip the per-graph comparison")
     ap.add_argument("--batch-block", type=int, default=None, help="batch workloads: threads per block")
     ap.add_argument("--batch-bps", type=int, default=None, help="batch workloads: blocks per SM (0 = auto)")
+    ap.add_argument("--serve-seconds", type=float, default=None, help="serve workload: trace length")
+    ap.add_argument("--serve-rate", type=float, default=None, help="serve workload: arrivals per second")
     args = ap.parse_args()
     spec = dict(WORKLOADS[args.workload])
     if spec["kind"] == "batch":
         return run_batch(args, spec)
+    if spec["kind"] == "serve":
+        return run_serve(args, spec)
     if args.rmat_scale and spec["kind"] == "rmat":
         spec["scale"] = args.rmat_scale
     if args.impl == "reference":
