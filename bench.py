@@ -80,6 +80,22 @@ def workload_name(spec, g):
     return f"knn_n{spec['n']}_k{spec['k']}"
 
 
+# ---------------------------------------------------------------- replicas --
+def max_over_ranks(x: float, dist, device) -> float:
+    """The largest of every rank's x (the job's time is its slowest replica's)."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: float, world: int, seconds: float) -> float:
+    """Replicas of the same workload: units of all ranks over the slowest rank's time."""
+    return world * units_per_rank / seconds
+
+
 # ------------------------------------------------------------------ clocks --
 class ClockSampler:
     """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
@@ -296,11 +312,7 @@ def run_batch(args, spec):
     barrier()
     launches = scc.scc_debug_launch_count() - launches0
     clk = clocks.stop()
-    ms = ev0.elapsed_time(ev1)
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ev0.elapsed_time(ev1), dist, "cuda")
     st = scc.scc_batch_get_stats(h)
     per_graph = None
     if args.verbose:
@@ -318,8 +330,8 @@ def run_batch(args, spec):
                                   "phases_ms": [float(x) for x in np.diff(tm[i, :6]) / 1e6],
                                   "rounds_searches_reruns_batches": [int(x) for x in tm[i, 7:11]]} for i in top],
                      "totals_rounds_searches_reruns_batches": [int(x) for x in tm[:, 7:11].sum(axis=0)]}
-    value = world * na * args.steps / (ms / 1e3)
-    graphs_per_s = world * G * args.steps / (ms / 1e3)
+    value = whole_job_rate(na * args.steps, world, ms / 1e3)
+    graphs_per_s = whole_job_rate(G * args.steps, world, ms / 1e3)
     # roofline of the persistent kernel (the only kernel of a step besides a
     # one-thread reset): algorithmic bytes per graph = building G^T (read the
     # targets twice, write them once, 12 B per arc, + 12 B per vertex of
@@ -659,12 +671,8 @@ def main():
     barrier()
     launches = scc.scc_debug_launch_count() - launches0
     clk = clocks.stop()
-    ms = ev0.elapsed_time(ev1)
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * m * args.steps / (ms / 1e3)
+    ms = max_over_ranks(ev0.elapsed_time(ev1), dist, "cuda")
+    value = whole_job_rate(m * args.steps, world, ms / 1e3)
 
     # ---- roofline of the dominant kernel. Candidates, each timed live with CUDA
     # events on its launching stream inside the library, with its algorithmic
@@ -741,12 +749,8 @@ def main():
             torch.cuda.synchronize()
             t1 = time.perf_counter()
         barrier()
-        te = t1 - t0
-        if dist is not None:
-            t = torch.tensor([te], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            te = float(t.item())
-        e2e = {"value": world * m * k2 / te, "unit": UNIT, "h2d_bytes_per_step": 4 * (n + 1) + 4 * m,
+        te = max_over_ranks(t1 - t0, dist, "cuda")
+        e2e = {"value": whole_job_rate(m * k2, world, te), "unit": UNIT, "h2d_bytes_per_step": 4 * (n + 1) + 4 * m,
                "d2h_bytes_per_step": 4 * n, "steps": k2}
 
     # ---- CPU oracle on the host cores (rank 0, N = 1 only)
