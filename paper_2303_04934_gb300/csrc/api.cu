@@ -215,6 +215,9 @@ int reserve_table(scc_graph* h, int d, int64_t cap, cudaStream_t s) {
 
 // at most this many class-trimming passes after the first SCC
 constexpr int kClassTrimPasses = 4;
+// average degree from which the first SCC's two searches run one after the
+// other with dense rounds (below it they share one launch without)
+constexpr double kDenseDegree = 8.0;
 
 struct EvTimer {
     cudaEvent_t a = nullptr, b = nullptr;
@@ -556,12 +559,22 @@ static int scc_run_impl(scc_graph* h, int32_t* labels_out, cudaStream_t s) {
         int32_t s0 = 0;
         SCC_CUDA(cudaMemcpyAsync(&s0, h->act + p0, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
         SCC_CUDA(cudaStreamSynchronize(s));
-        SCC_TRY(engine_reserve(&h->eb32, 4, N + 1024, h->cfg.lambda, h->mt, s));
+        // Dense (bottom-up) rounds pay off on low-diameter graphs, whose
+        // frontiers grow to a large part of the class; those have a high average
+        // degree. Below kDenseDegree arcs per vertex (lattices, k-NN graphs) the
+        // forward and backward searches share the rounds of one launch instead.
+        const bool both = (h->cfg.dense == 0 || (double)h->mt < kDenseDegree * (double)n) && n < INT32_MAX - 2;
+        SCC_TRY(engine_reserve(&h->eb32, 4, (both ? 2 * N : N) + 1024, h->cfg.lambda, h->mt, s));
         SCC_TRY(launch_prefill_bits(h->label, 0, n, h->bits_f, s));
         SCC_TRY(launch_prefill_bits(h->label, 0, n, h->bits_b, s));
         EngineRun r0, r1;
-        SCC_TRY(run_single(h->off, h->adj, n, s0, h->bits_f, dense_opts(h, 0, N), &h->eb32, o, &r0, s));
-        SCC_TRY(run_single(h->toff, h->tadj, n, s0, h->bits_b, dense_opts(h, 1, N), &h->eb32, o, &r1, s));
+        if (both) {
+            SCC_TRY(run_single_both(h->off, h->adj, h->toff, h->tadj, n, s0, h->bits_f, h->bits_b, &h->eb32, o, &r0,
+                                    s));
+        } else {
+            SCC_TRY(run_single(h->off, h->adj, n, s0, h->bits_f, dense_opts(h, 0, N), &h->eb32, o, &r0, s));
+            SCC_TRY(run_single(h->toff, h->tadj, n, s0, h->bits_b, dense_opts(h, 1, N), &h->eb32, o, &r1, s));
+        }
         SCC_TRY(launch_label_first(h->bits_f, h->bits_b, n, s0, h->label, h->rep, &h->counters[1], s));
         SCC_CUDA(cudaMemcpyAsync(hc, h->counters, sizeof(hc), cudaMemcpyDeviceToHost, s));
         st.ms_first_scc = t.stop();
@@ -587,6 +600,7 @@ static int scc_run_impl(scc_graph* h, int32_t* labels_out, cudaStream_t s) {
         }
         st.ms_class_trim = t.stop();
         for (const EngineRun* r : {&r0, &r1}) {
+            if (both && r == &r1) continue;
             st.engine_launches++;
             st.ms_engine += r->ms;
             st.engine_arcs += (int64_t)r->edges;

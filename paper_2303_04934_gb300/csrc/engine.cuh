@@ -799,6 +799,40 @@ struct PolSingle {
     }
 };
 
+// Forward and backward single-reachability from the same source in one search
+// (they are independent, so they can share rounds): vertex items with a
+// direction bit (bit 31); direction 0 follows G and marks bits[0], direction 1
+// follows G^T and marks bits[1]. No dense rounds (the dense test is per
+// direction). The sentinels (0xffffffff, 0xfffffffe) are never items as long
+// as vertex ids stay below 2^31 - 2.
+struct PolSingleBoth {
+    using Item = uint32_t;
+    static constexpr int kQueue = 256;
+    static constexpr bool kCountInserts = false;
+    static constexpr bool kDense = false;
+    static constexpr bool kCtxInQueue = false;
+    static constexpr bool kTwoGraphs = true;
+    static constexpr const char* kName = "single-reach-both";
+    static constexpr uint32_t kDir = 1u << 31;
+    uint32_t* bits[2];
+    __device__ __forceinline__ int vertex(Item it) const { return (int)(it & ~kDir); }
+    __device__ __forceinline__ int graph(Item it) const { return (int)(it >> 31); }
+    __device__ __forceinline__ uint64_t ctx(Item) const { return 0; }
+    __device__ __forceinline__ bool seed(Item it) const {
+        uint32_t* B = graph(it) ? bits[1] : bits[0];
+        const int v = vertex(it);
+        const uint32_t b = 1u << (v & 31);
+        return (atomicOr(&B[v >> 5], b) & b) == 0;
+    }
+    __device__ __forceinline__ bool visit(Item parent, uint64_t, int w, Item& child) const {
+        uint32_t* B = (parent >> 31) ? bits[1] : bits[0];
+        const uint32_t b = 1u << (w & 31);
+        if (ld_volatile(&B[w >> 5]) & b) return false;
+        child = (parent & kDir) | (uint32_t)w;
+        return (atomicOr(&B[w >> 5], b) & b) == 0;
+    }
+};
+
 // Pair table (Sec. 4.3 phase-concurrent hash table of reachability pairs):
 // open addressing over uint64 keys v << 32 | s, linear probing, insert-if-absent.
 struct PairTable {

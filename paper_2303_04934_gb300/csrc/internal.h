@@ -210,6 +210,11 @@ struct DenseOpts {
     int frac_inv = 0;
 };
 // Single reachability from `s` over (off, adj) with the bitmap (already prefilled).
+// Forward (off/adj, marks bits_f) and backward (toff/tadj, marks bits_b)
+// single-reachability from s in one search, without dense rounds.
+int run_single_both(const int32_t* off, const int32_t* adj, const int32_t* toff, const int32_t* tadj, int32_t n,
+                    int32_t s, uint32_t* bits_f, uint32_t* bits_b, EngineBuf* b, const EngineOpts& o, EngineRun* out,
+                    cudaStream_t st);
 int run_single(const int32_t* off, const int32_t* adj, int32_t n, int32_t s, uint32_t* bits, const DenseOpts& dn,
                EngineBuf* b, const EngineOpts& o, EngineRun* out, cudaStream_t st);
 // Multi reachability: init pairs (s,s) from sources (device int32[k]); pairs into table.

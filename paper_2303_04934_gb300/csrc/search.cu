@@ -197,6 +197,28 @@ int run_single(const int32_t* off, const int32_t* adj, int32_t n, int32_t s, uin
     return out->err ? out->err : SCC_OK;
 }
 
+int run_single_both(const int32_t* off, const int32_t* adj, const int32_t* toff, const int32_t* tadj, int32_t n,
+                    int32_t s, uint32_t* bits_f, uint32_t* bits_b, EngineBuf* b, const EngineOpts& o, EngineRun* out,
+                    cudaStream_t st) {
+    if (n >= INT32_MAX - 2) return SCC_ERR_INVALID_ARG;  // ids must stay clear of the direction bit's sentinels
+    auto P = make_engine_params<uint32_t>(off, adj, n, b, o);
+    P.off2 = toff;
+    P.adj2 = tadj;
+    SCC_TRY(reserve_init(b, 2 * sizeof(uint32_t), st));
+    const uint32_t init[2] = {(uint32_t)s, (uint32_t)s | PolSingleBoth::kDir};
+    SCC_CUDA(cudaMemcpyAsync(b->init, init, sizeof(init), cudaMemcpyHostToDevice, st));
+    SCC_CUDA(cudaStreamSynchronize(st));  // init is a stack array
+    P.init = reinterpret_cast<const uint32_t*>(b->init);
+    P.ninit = 2;
+    PolSingleBoth pol;
+    pol.bits[0] = bits_f;
+    pol.bits[1] = bits_b;
+    int rc = launch_engine(P, pol, o, out, st);
+    if (rc != SCC_OK || out->err) SCC_TRY(engine_reset_slots(b, st));
+    SCC_TRY(rc);
+    return out->err ? out->err : SCC_OK;
+}
+
 int run_pairs(const int32_t* off, const int32_t* adj, int32_t n, const int32_t* label, const int32_t* sources,
               int32_t k, unsigned long long* table, int64_t cap, long long max_inserted, EngineBuf* b,
               const EngineOpts& o, EngineRun* out, cudaStream_t st) {
