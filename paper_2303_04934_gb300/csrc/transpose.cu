@@ -312,11 +312,17 @@ __device__ __forceinline__ void unpack8(const uint4 r, unsigned int (&lv)[8]) {
     lv[6] = r.w & 0xffffu;
     lv[7] = r.w >> 16;
 }
+// Counter i of a bucket lives at i + i / 32 in shared memory: the scan below
+// gives each thread a run of consecutive counters, and with one padding word
+// per 32 the lanes of a warp reading the j-th counter of their runs hit 32
+// different banks (without it they would all hit one).
+__device__ __forceinline__ int cpad(int i) { return i + (i >> 5); }
+
 __global__ void __launch_bounds__(kBlkB) k_bucket_rows(const int32_t* __restrict__ uu, const uint16_t* __restrict__ lvv,
                                                        const unsigned long long* __restrict__ start,
                                                        const int32_t* __restrict__ order, int nb, int shift,
                                                        int32_t n, int32_t* toff, int32_t* tadj, int* err) {
-    extern __shared__ int s_cnt[];  // 2^shift counters
+    extern __shared__ int s_cnt[];  // 2^shift counters, padded (cpad)
     __shared__ int s_wsum[kBlkB / 32];
     const int W = 1 << shift;
     constexpr int kCh = 2;  // chunks per thread per step
@@ -325,7 +331,7 @@ __global__ void __launch_bounds__(kBlkB) k_bucket_rows(const int32_t* __restrict
         const int v0 = b << shift;
         const int vw = min(W, n - v0);
         const long long a0 = (long long)start[b], a1 = (long long)start[b + 1];
-        for (int i = threadIdx.x; i < vw; i += blockDim.x) s_cnt[i] = 0;
+        for (int i = threadIdx.x; i < cpad(vw); i += blockDim.x) s_cnt[i] = 0;
         __syncthreads();
         const long long c0 = (a0 & ~7ll) + 8ll * threadIdx.x;
         const long long cstep = 8ll * blockDim.x;
@@ -344,7 +350,7 @@ __global__ void __launch_bounds__(kBlkB) k_bucket_rows(const int32_t* __restrict
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
                     if (cc + j < a0 || cc + j >= a1) continue;
-                    if (lv[j] < (unsigned int)vw) atomicAdd(&s_cnt[lv[j]], 1);
+                    if (lv[j] < (unsigned int)vw) atomicAdd(&s_cnt[cpad((int)lv[j])], 1);
                     else atomicExch(err, SCC_ERR_INTERNAL);  // arc outside its bucket: skip it, report
                 }
             }
@@ -354,7 +360,7 @@ __global__ void __launch_bounds__(kBlkB) k_bucket_rows(const int32_t* __restrict
         const int per = (vw + blockDim.x - 1) / blockDim.x;
         const int q0 = threadIdx.x * per, q1 = min(q0 + per, vw);
         int sum = 0;
-        for (int i = q0; i < q1; ++i) sum += s_cnt[i];
+        for (int i = q0; i < q1; ++i) sum += s_cnt[cpad(i)];
         int incl = warp_incl_scan(sum);
         if (lane_id() == 31) s_wsum[threadIdx.x >> 5] = incl;
         __syncthreads();
@@ -366,11 +372,14 @@ __global__ void __launch_bounds__(kBlkB) k_bucket_rows(const int32_t* __restrict
         __syncthreads();
         int run = s_wsum[threadIdx.x >> 5] + incl - sum;
         for (int i = q0; i < q1; ++i) {
-            int cn = s_cnt[i];
-            s_cnt[i] = run;
-            toff[v0 + i] = (int32_t)(a0 + run);
+            const int cn = s_cnt[cpad(i)];
+            s_cnt[cpad(i)] = run;
             run += cn;
         }
+        __syncthreads();
+        // the bucket's row offsets, written coalesced (before the placement
+        // below advances the counters)
+        for (int i = threadIdx.x; i < vw; i += blockDim.x) toff[v0 + i] = (int32_t)(a0 + s_cnt[cpad(i)]);
         __syncthreads();
         for (long long c = c0; c < a1; c += kCh * cstep) {
             uint4 r[kCh];
@@ -392,7 +401,7 @@ __global__ void __launch_bounds__(kBlkB) k_bucket_rows(const int32_t* __restrict
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
                     if (cc + j < a0 || cc + j >= a1 || lv[j] >= (unsigned int)vw) continue;
-                    const int p = atomicAdd(&s_cnt[lv[j]], 1);
+                    const int p = atomicAdd(&s_cnt[cpad((int)lv[j])], 1);
                     if (a0 + p < a1) tadj[a0 + p] = u8[j];
                     else atomicExch(err, SCC_ERR_INTERNAL);
                 }
@@ -531,7 +540,7 @@ int launch_transpose(const int32_t* off, const int32_t* adj, const int32_t* trow
     std::iota(ord.begin(), ord.end(), 0);
     std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return hc[a] > hc[b]; });
     SCC_CUDA(cudaMemcpyAsync(order_tmp, ord.data(), sizeof(int32_t) * nb, cudaMemcpyHostToDevice, s));
-    const size_t smem = sizeof(int) << shift;
+    const size_t smem = sizeof(int) * (((size_t)1 << shift) + ((size_t)1 << shift) / 32 + 1);
     if (smem > 48 * 1024)
         SCC_CUDA(cudaFuncSetAttribute(k_bucket_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     if (ev) cudaEventRecord(ev[2], s);
