@@ -581,6 +581,8 @@ def main():
     ap.add_argument("--workload", default="rmat24", choices=sorted(WORKLOADS))
     ap.add_argument("--rmat-scale", type=int, default=None,
                     help="profiling aid: R-MAT scale instead of the workload's (not a bench line)")
+    ap.add_argument("--rmat-ef", type=int, default=None,
+                    help="profiling aid: R-MAT edge factor instead of the workload's (not a bench line)")
     ap.add_argument("--tau", type=int, default=None)
     ap.add_argument("--seeds", type=int, default=None)
     ap.add_argument("--no-e2e", action="store_true")
@@ -600,6 +602,8 @@ def main():
         return run_serve(args, spec)
     if args.rmat_scale and spec["kind"] == "rmat":
         spec["scale"] = args.rmat_scale
+    if args.rmat_ef and spec["kind"] == "rmat":
+        spec["ef"] = args.rmat_ef
     if args.impl == "reference":
         return run_reference(args, spec)
 
