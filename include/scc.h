@@ -76,8 +76,10 @@ SCC_API const char* scc_error_string(int code);
  *   block       threads per block of the search kernels (256; other values are
  *               rejected with SCC_ERR_INVALID_ARG).
  *   seeds       frontier items one warp takes per task, 1..32 (default 32).
- *   dense       1: the first-SCC single-reachability may switch to the dense
- *               (bottom-up) mode of Sec. 4.2 on large frontiers; 0: never.
+ *   dense       0: the first-SCC single-reachability never switches to the dense
+ *               (bottom-up) mode of Sec. 4.2; 1: it does once a round's frontier
+ *               holds 1/20 of the searched class; k in [2, 1024]: once it holds
+ *               1/k of it.
  *   seed        seed of the pivot permutation.
  */
 typedef struct scc_config {

@@ -161,7 +161,7 @@ int valid_config(const scc_config* c) {
     if (c->sigma < 1 || c->sigma > (1 << 20)) return SCC_ERR_INVALID_ARG;
     if (c->block != 256) return SCC_ERR_INVALID_ARG;
     if (c->seeds < 1 || c->seeds > 32) return SCC_ERR_INVALID_ARG;
-    if (c->dense != 0 && c->dense != 1) return SCC_ERR_INVALID_ARG;
+    if (c->dense < 0 || c->dense > 1024) return SCC_ERR_INVALID_ARG;
     return SCC_OK;
 }
 
@@ -199,7 +199,7 @@ DenseOpts dense_opts(const scc_graph* h, int dir, long long n_active) {
     d.fbits[0] = h->fbits;
     d.fbits[1] = h->fbits + nw;
     d.n_active = n_active;
-    d.frac_inv = h->cfg.dense ? 20 : 0;
+    d.frac_inv = h->cfg.dense == 1 ? 20 : h->cfg.dense;
     return d;
 }
 

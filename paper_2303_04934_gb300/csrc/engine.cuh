@@ -44,6 +44,9 @@ constexpr int kHubSeg = 1024;     // arcs of one hub segment
 constexpr int kMaxChunks = 48;
 constexpr int kBagProbe = 16;     // kappa: segment probes before a chunk advance
 constexpr int kTableProbe = 256;  // pair-table probe limit (then: overflow, regrow)
+// bag slots held by partly filled segments: two 32-slot segments for each warp
+// of the largest cooperative grid (4 blocks of 8 warps on each of up to 160 SMs)
+constexpr long long kBagWarpSlots = 2ll * kSeg * 8 * 4 * 160;
 
 template <class Item>
 struct Sent;

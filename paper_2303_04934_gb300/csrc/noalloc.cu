@@ -54,7 +54,7 @@ size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 // the bytes needed (the layout is only written when base != nullptr).
 size_t carve(unsigned char* base, int32_t n, int64_t mt, int lambda, EngineBuf* b, int** bad) {
     long long items = std::max<long long>(2ll * n + 1024, lambda);
-    long long nslots = (std::max<long long>(4 * items, 4ll * lambda) + kSeg - 1) / kSeg * kSeg;
+    long long nslots = (std::max<long long>(4 * items, 4ll * lambda) + kBagWarpSlots + kSeg - 1) / kSeg * kSeg;
     int hub_cap = (int)std::min<long long>(items, 8192);
     long long segmap_cap = 2 * (mt / kHubSeg) + hub_cap + 1024;
     size_t off = 0;

@@ -142,7 +142,9 @@ int engine_reset_slots(EngineBuf* b, cudaStream_t st) {
 
 int engine_reserve(EngineBuf* b, int item_bytes, long long items, int lambda, int64_t m, cudaStream_t s) {
     if (items < 1) items = 1;
-    long long need_slots = std::max<long long>(4 * items, 4ll * lambda);
+    // every warp that pushes holds a partly filled 32-slot segment, so the bag
+    // needs room for two segments per warp of the largest grid besides the items
+    long long need_slots = std::max<long long>(4 * items, 4ll * lambda) + kBagWarpSlots;
     need_slots = (need_slots + kSeg - 1) / kSeg * kSeg;
     if (b->slots[0] && b->item_bytes == item_bytes && b->nslots >= need_slots && b->lambda == lambda &&
         b->items >= items)
