@@ -30,6 +30,20 @@ def _batch():
     gs += [gg.torus(2, s, 0.5, seed=910 + s) for s in (8, 23, 40, 64)]
     gs += [gg.rmat(s, 8, seed=920 + s) for s in (6, 9, 12, 14)]
     gs += [gg.torus(3, 12, 0.3, seed=930), gg.knn(3000, 5, seed=931)]
+    # deep and skewed structures: a long path and a long cycle (ids shuffled),
+    # a star with a 20k-arc hub in both directions, a chain of small cliques
+    rng = np.random.default_rng(940)
+    p = rng.permutation(8000)
+    gs.append(gg.from_edges(8000, [(int(p[i]), int(p[i + 1])) for i in range(7999)], name="path8k"))
+    gs.append(gg.from_edges(8000, [(int(p[i]), int(p[(i + 1) % 8000])) for i in range(8000)], name="cycle8k"))
+    k = 20000
+    gs.append(gg.from_edges(k, [(0, i) for i in range(1, k)] + [(i, 0) for i in range(1, k, 3)], name="star20k"))
+    e = []
+    for c in range(500):
+        e += [(4 * c + x, 4 * c + y) for x in range(4) for y in range(4) if x != y]
+        if c < 499:
+            e.append((4 * c + 3, 4 * c + 4))
+    gs.append(gg.from_edges(2000, e, name="clique_chain"))
     return gg.pack(gs)
 
 

@@ -102,3 +102,37 @@ def test_invariants_hold_on_gpu_output():
     with make_graph(g) as G:
         lab = labels_of(G)
     check_scc_labels(g.n, g.offsets, g.targets, lab)
+
+
+def _shuffled(n, edges, seed, name):
+    """The same graph with vertex ids permuted (so structure and ids do not align)."""
+    p = np.random.default_rng(seed).permutation(n)
+    return gg.from_edges(n, [(int(p[a]), int(p[b])) for a, b in edges], name=name)
+
+
+def test_deep_and_skewed_structures():
+    """Long chains and cycles (searches thousands of levels deep, so many rounds),
+    a hub with 200k out- and in-arcs (hub items cut into segments), cycles tied
+    into a DAG by chains, and a complete bipartite orientation (one huge level)."""
+    n = 30000
+    _check(_shuffled(n, [(i, i + 1) for i in range(n - 1)], 1, "path30k"))
+    _check(_shuffled(n, [(i, (i + 1) % n) for i in range(n)], 2, "cycle30k"))
+    # two long cycles joined one way, plus a tail
+    e = [(i, (i + 1) % 10000) for i in range(10000)] + [(10000 + i, 10000 + (i + 1) % 10000) for i in range(10000)]
+    e += [(5, 10005)] + [(20000 + i, 20001 + i) for i in range(4999)] + [(10007, 20000)]
+    _check(_shuffled(25000, e, 3, "cycles_and_tail"))
+    # a star: hub 0 -> every leaf, every leaf -> hub (one SCC), plus leaves with one direction only
+    k = 200000
+    e = [(0, i) for i in range(1, k)] + [(i, 0) for i in range(1, k, 2)]
+    _check(gg.from_edges(k, e, name="star200k"))
+    # complete bipartite orientation: every arc from side A to side B, a few back arcs
+    a, b = 300, 300
+    e = [(i, a + j) for i in range(a) for j in range(b)] + [(a + j, j) for j in range(0, a, 7)]
+    _check(_shuffled(a + b, e, 4, "bipartite"))
+    # a deep ring of small cliques (many small SCCs along a long chain)
+    e = []
+    for c in range(3000):
+        base = 4 * c
+        e += [(base + x, base + y) for x in range(4) for y in range(4) if x != y]
+        e.append((base + 3, base + 4)) if c < 2999 else None
+    _check(_shuffled(12000, e, 5, "clique_chain"))
