@@ -143,6 +143,10 @@ int from_device(void* dst, const void* src, size_t bytes, cudaStream_t s) {
     return SCC_OK;
 }
 
+// average degree from which the first SCC's two searches run one after the
+// other with dense rounds (below it they share one launch without)
+constexpr double kDenseDegree = 8.0;
+
 EngineOpts opts_of(const scc_graph* h) {
     EngineOpts o;
     o.tau = h->cfg.tau;
@@ -150,6 +154,7 @@ EngineOpts opts_of(const scc_graph* h) {
     o.sigma = h->cfg.sigma;
     o.block = h->cfg.block;
     o.num_sms = h->di.num_sms;
+    o.high_degree = (double)h->mt >= kDenseDegree * (double)std::max<int32_t>(h->n, 1);
     return o;
 }
 
@@ -215,9 +220,6 @@ int reserve_table(scc_graph* h, int d, int64_t cap, cudaStream_t s) {
 
 // at most this many class-trimming passes after the first SCC
 constexpr int kClassTrimPasses = 4;
-// average degree from which the first SCC's two searches run one after the
-// other with dense rounds (below it they share one launch without)
-constexpr double kDenseDegree = 8.0;
 
 struct EvTimer {
     cudaEvent_t a = nullptr, b = nullptr;

@@ -827,10 +827,11 @@ struct PolSingleBoth {
         const uint32_t b = 1u << (v & 31);
         return (atomicOr(&B[v >> 5], b) & b) == 0;
     }
+    // the atomic is the test (no read before it): these searches run on
+    // low-degree graphs, where a step's dependent accesses are its cost
     __device__ __forceinline__ bool visit(Item parent, uint64_t, int w, Item& child) const {
         uint32_t* B = (parent >> 31) ? bits[1] : bits[0];
         const uint32_t b = 1u << (w & 31);
-        if (ld_volatile(&B[w >> 5]) & b) return false;
         child = (parent & kDir) | (uint32_t)w;
         return (atomicOr(&B[w >> 5], b) & b) == 0;
     }
@@ -961,12 +962,16 @@ struct PolMask {
     static constexpr bool kTwoGraphs = false;
     static constexpr const char* kName = "mask-reach";
     unsigned long long* mask;
+    bool test_first;  // read the target's mask before the atomic (high-degree graphs)
     __device__ __forceinline__ int vertex(Item it) const { return (int)it; }
     __device__ __forceinline__ uint64_t ctx(Item it) const { return ld_volatile(&mask[it]); }
     __device__ __forceinline__ bool seed(Item) const { return true; }
+    // on low-degree graphs the atomic is the test (one dependent access less
+    // per step); on high-degree ones most targets already carry the sources,
+    // and a plain read first saves the atomic
     __device__ __forceinline__ bool visit(Item, uint64_t mu, int w, Item& child) const {
-        if ((mu & ~ld_volatile(&mask[w])) == 0) return false;
-        unsigned long long old = atomicOr(&mask[w], (unsigned long long)mu);
+        if (test_first && (mu & ~ld_volatile(&mask[w])) == 0) return false;
+        const unsigned long long old = atomicOr(&mask[w], (unsigned long long)mu);
         child = (Item)w;
         return (mu & ~old) != 0;
     }

@@ -197,6 +197,9 @@ struct EngineOpts {
     int sigma = 50;
     int block = 256;
     int num_sms = 0;
+    // average degree of at least 8: most targets of a mask search already
+    // carry the sources, and a plain read before each atomic saves atomics
+    bool high_degree = false;
 };
 
 // Dense-round inputs of a single-reachability search (Sec. 4.2 dense mode):

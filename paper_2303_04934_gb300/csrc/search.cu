@@ -252,7 +252,7 @@ int run_mask(const int32_t* off, const int32_t* adj, int32_t n, const int32_t* s
     auto P = make_engine_params<uint32_t>(off, adj, n, b, o);
     P.init = reinterpret_cast<const uint32_t*>(sources);
     P.ninit = k;
-    PolMask pol{mask};
+    PolMask pol{mask, o.high_degree};
     int rc = launch_engine(P, pol, o, out, st);
     if (rc != SCC_OK || out->err) SCC_TRY(engine_reset_slots(b, st));
     SCC_TRY(rc);
@@ -269,7 +269,7 @@ int run_mask_fixed(const int32_t* off, const int32_t* adj, int32_t n, const int3
     auto P = make_engine_params<uint32_t>(off, adj, n, b, o);
     P.init = reinterpret_cast<const uint32_t*>(sources);
     P.ninit = k;
-    PolMask pol{mask};
+    PolMask pol{mask, o.high_degree};
     DenseParams dp{nullptr, nullptr, {nullptr, nullptr}, 0, 0};
     int grid = 0;
     SCC_TRY(coop_grid<PolMask>(o.num_sms, &grid));
