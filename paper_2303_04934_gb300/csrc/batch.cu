@@ -9,7 +9,8 @@
 //   2. Trimming (Sec. 4.1): vertices without in- or out-arcs are singletons.
 //   3. The pivot order: a seeded Feistel permutation of the active vertices.
 //   4. The first SCC (Sec. 4.2): forward and backward single-reachability from
-//      the first pivot, the VGC engine with vertex items and visited bitmaps.
+//      the first pivot in the same rounds (vertex items with a direction bit),
+//      the VGC engine with visited bitmaps.
 //   5. Trimming inside the three classes the first SCC leaves.
 //   6. Prefix-doubling batches (Alg. 1): forward and backward multi-
 //      reachability sharing the rounds of one search (pair items with a
@@ -267,9 +268,10 @@ __device__ __forceinline__ int row_of(const int32_t* off, int n, long long e) {
 }
 
 // ------------------------------------------------------------- initial items --
-struct InitVertex {
+// the pivot in both directions (items 0 and 1 of a PolSingleBoth search)
+struct InitPivotBoth {
     uint32_t v;
-    __device__ __forceinline__ uint32_t operator()(long long) const { return v; }
+    __device__ __forceinline__ uint32_t operator()(long long i) const { return i ? (v | PolSingleBoth::kDir) : v; }
 };
 
 // ------------------------------------------------------------ one graph --
@@ -352,16 +354,21 @@ __device__ bool scc_one_graph(const BatchArgs& A, Ws& W, int g, BlockShared& sh,
             W.bits_b[w] = m0;
         }
         __syncthreads();
-        for (int d = 0; d < 2; ++d) {
+        {
+            // forward (G) and backward (G^T) searches in the same rounds
             EngineParams<uint32_t> P = W.P32;
-            P.off = d == 0 ? off : W.toff;
-            P.adj = d == 0 ? adj : W.tadj;
+            P.off = off;
+            P.adj = adj;
+            P.off2 = W.toff;
+            P.adj2 = W.tadj;
             P.n = n;
-            PolSingle pol{d == 0 ? W.bits_f : W.bits_b};
+            PolSingleBoth pol;
+            pol.bits[0] = W.bits_f;
+            pol.bits[1] = W.bits_b;
             WarpStats ws;
             int why = 0;
-            if (!engine_search<PolSingle, InitVertex, CtaScope>(P, pol, InitVertex{(uint32_t)p0}, 1, nullptr, q32, ws,
-                                                                  gr, si, why))
+            const InitPivotBoth init{(uint32_t)p0};
+            if (!engine_search<PolSingleBoth, InitPivotBoth, CtaScope>(P, pol, init, 2, nullptr, q32, ws, gr, si, why))
                 return false;
             ++si;
             if (why != 0) {  // the hash bag is sized so that this never happens
