@@ -559,7 +559,7 @@ def run_serve(args, spec):
                 "scc_p99_ms": st["scc_p99_ms"], "reach_p50_ms": st["reach_p50_ms"], "reach_p99_ms": st["reach_p99_ms"],
                 "server": {k: st[k] for k in ("units", "batched_launches", "batched_graphs", "plain_scc",
                                               "reach_launches", "reach_shared", "mem_peak", "max_admitted",
-                                              "failed")},
+                                              "failed", "busy_reach_ms", "busy_batched_ms", "busy_plain_ms")},
                 "plain_per_graph": plain,
                 "speedup_vs_plain": {"graphs_per_s": (n_scc / wall) / plain["graphs_per_s"],
                                      "p99": plain["p99_ms"] / max(st["p99_ms"], 1e-9)} if plain else None,

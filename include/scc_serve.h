@@ -95,6 +95,7 @@ typedef struct scc_server_stats {
     int32_t resident_graphs;
     double p50_ms, p99_ms;    /* latency percentiles of the completed requests */
     double scc_p50_ms, scc_p99_ms, reach_p50_ms, reach_p99_ms;
+    double busy_reach_ms, busy_batched_ms, busy_plain_ms;  /* server-thread time in each kind of unit */
 } scc_server_stats;
 
 SCC_API int scc_server_get_stats(scc_server_handle h, scc_server_stats* out);

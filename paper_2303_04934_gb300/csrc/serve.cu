@@ -384,6 +384,8 @@ void run_batched(scc_server* S, std::vector<ReqPtr>& u) {
 void run_unit(scc_server* S) {
     ReqPtr head = S->admitted.front();
     std::vector<ReqPtr> u;
+    const auto t0 = Clock::now();
+    double* busy = nullptr;
     if (head->kind == 1) {
         int k = 0;
         for (auto it = S->admitted.begin(); it != S->admitted.end();) {
@@ -399,6 +401,7 @@ void run_unit(scc_server* S) {
             if (!S->cfg.merge_reach) break;
         }
         run_reach(S, u);
+        busy = &S->st.busy_reach_ms;
     } else if (is_small(S, *head)) {
         for (auto it = S->admitted.begin(); it != S->admitted.end() && (int)u.size() < S->cfg.batch_graphs;) {
             if (is_small(S, **it)) {
@@ -409,12 +412,15 @@ void run_unit(scc_server* S) {
             }
         }
         run_batched(S, u);
+        busy = &S->st.busy_batched_ms;
     } else {
         S->admitted.pop_front();
         run_plain(S, *head);
+        busy = &S->st.busy_plain_ms;
     }
     std::lock_guard<std::mutex> lk(S->mu);
     S->st.units++;
+    *busy += ms_between(t0, Clock::now());
 }
 
 void server_main(scc_server* S) {

@@ -94,7 +94,7 @@ class scc_server_stats(ctypes.Structure):
         "batched_graphs", "plain_scc", "reach_launches", "reach_shared", "mem_in_use", "mem_peak", "mem_cap")] + [
         ("max_admitted", ctypes.c_int32), ("resident_graphs", ctypes.c_int32)] + [
         (f, ctypes.c_double) for f in ("p50_ms", "p99_ms", "scc_p50_ms", "scc_p99_ms", "reach_p50_ms",
-                                        "reach_p99_ms")]
+                                        "reach_p99_ms", "busy_reach_ms", "busy_batched_ms", "busy_plain_ms")]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
