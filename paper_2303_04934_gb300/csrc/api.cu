@@ -113,6 +113,17 @@ bool is_device_ptr(const void* p) {
     }
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
+
+// The device address of page-locked host memory (NULL for pageable memory).
+const void* mapped_host_ptr(const void* p) {
+    if (!p) return nullptr;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
 int device_info(DeviceInfo* out) {
     SCC_CUDA(cudaGetDevice(&out->dev));
     SCC_CUDA(cudaDeviceGetAttribute(&out->num_sms, cudaDevAttrMultiProcessorCount, out->dev));
@@ -301,12 +312,17 @@ static int graph_create_impl(scc_graph* h, int32_t n, int64_t m, const int32_t* 
     h->off = off_in;
     h->adj = adj_in;
     SCC_TRY(to_device(off_in, offsets, sizeof(int32_t) * ((size_t)n + 1), s));
-    // a device target array is copied by the intake pass itself (one read);
-    // a host one is staged first
+    // a device target array is copied by the intake pass itself (one read), and
+    // so is a page-locked host one (the pass reads it over the host link, so the
+    // transfer and the pass are one); a pageable one is staged first
     const int32_t* src = targets;
     if (m > 0 && !is_device_ptr(targets)) {
-        SCC_TRY(to_device(adj_in, targets, sizeof(int32_t) * (size_t)m, s));
-        src = adj_in;
+        if (const void* mp = mapped_host_ptr(targets)) {
+            src = static_cast<const int32_t*>(mp);
+        } else {
+            SCC_TRY(to_device(adj_in, targets, sizeof(int32_t) * (size_t)m, s));
+            src = adj_in;
+        }
     }
     const int shift = bucket_shift(n);
     const int nb = std::max(1, (int)(((int64_t)n + (1ll << shift) - 1) >> shift));
@@ -527,7 +543,7 @@ static int scc_run_impl(scc_graph* h, int32_t* labels_out, cudaStream_t s) {
     SCC_CUDA(cudaMemsetAsync(h->bmax, 0, (size_t)n * 8, s));
     SCC_CUDA(cudaMemsetAsync(h->hit, 0, (size_t)n * 8, s));
     SCC_TRY(launch_init_labels(h->off, h->toff, n, h->label, h->rep, &h->counters[0], s));
-    SCC_TRY(launch_compact_active(h->label, n, h->tmp_a, h->tmp_b, h->scan_tmp, h->act, s));
+    SCC_TRY(launch_compact_active(h->label, n, h->scan_tmp, h->act, s));
     unsigned long long hc[4];
     SCC_CUDA(cudaMemcpyAsync(hc, h->counters, sizeof(hc), cudaMemcpyDeviceToHost, s));
     st.ms_trim = t.stop();
@@ -567,8 +583,7 @@ static int scc_run_impl(scc_graph* h, int32_t* labels_out, cudaStream_t s) {
         // forward and backward searches share the rounds of one launch instead.
         const bool both = (h->cfg.dense == 0 || (double)h->mt < kDenseDegree * (double)n) && n < INT32_MAX - 2;
         SCC_TRY(engine_reserve(&h->eb32, 4, (both ? 2 * N : N) + 1024, h->cfg.lambda, h->mt, s));
-        SCC_TRY(launch_prefill_bits(h->label, 0, n, h->bits_f, s));
-        SCC_TRY(launch_prefill_bits(h->label, 0, n, h->bits_b, s));
+        SCC_TRY(launch_prefill_bits(h->label, 0, n, h->bits_f, h->bits_b, s));
         EngineRun r0, r1;
         if (both) {
             SCC_TRY(run_single_both(h->off, h->adj, h->toff, h->tadj, n, s0, h->bits_f, h->bits_b, &h->eb32, o, &r0,
@@ -822,7 +837,7 @@ int scc_debug_pivot_order(scc_handle h, int32_t* order, int32_t* n_active, void*
     SCC_TRY(reserve_run_state(h, s));
     SCC_CUDA(cudaMemsetAsync(h->counters, 0, 4 * sizeof(unsigned long long), s));
     SCC_TRY(launch_init_labels(h->off, h->toff, h->n, h->label, h->rep, &h->counters[0], s));
-    SCC_TRY(launch_compact_active(h->label, h->n, h->tmp_a, h->tmp_b, h->scan_tmp, h->act, s));
+    SCC_TRY(launch_compact_active(h->label, h->n, h->scan_tmp, h->act, s));
     unsigned long long N = 0;
     SCC_CUDA(cudaMemcpyAsync(&N, h->counters, sizeof(N), cudaMemcpyDeviceToHost, s));
     SCC_CUDA(cudaStreamSynchronize(s));
@@ -854,7 +869,7 @@ int scc_debug_single_reach(scc_handle h, const int32_t* labels, int32_t src, int
     if (labels && L < 0) {
         rc = cuda_err(cudaMemsetAsync(d, 0, (size_t)n, s));  // a finished source reaches nothing
     } else {
-        rc = launch_prefill_bits(dl, L, n, h->bits_f, s);
+        rc = launch_prefill_bits(dl, L, n, h->bits_f, nullptr, s);
         if (rc == SCC_OK) rc = engine_reserve(&h->eb32, 4, (long long)n + 1024, h->cfg.lambda, h->mt, s);
         EngineRun r;
         if (rc == SCC_OK)

@@ -42,6 +42,7 @@ inline int dalloc_t(T** p, size_t count, cudaStream_t s) {
 
 // True when p is device (or managed) memory.
 bool is_device_ptr(const void* p);
+const void* mapped_host_ptr(const void* p);
 
 struct DeviceInfo {
     int dev = -1;
@@ -102,8 +103,7 @@ int launch_trim(const int32_t* off, const int32_t* toff, int32_t n, uint8_t* fla
 int launch_init_labels(const int32_t* off, const int32_t* toff, int32_t n, int32_t* label, int32_t* rep,
                        unsigned long long* nact, cudaStream_t s);
 // act = increasing list of v with label[v] >= 0 (scan-based, order preserving).
-int launch_compact_active(const int32_t* label, int32_t n, int32_t* flags_tmp, int32_t* pos_tmp, void* scan_tmp,
-                          int32_t* act, cudaStream_t s);
+int launch_compact_active(const int32_t* label, int32_t n, void* scan_tmp, int32_t* act, cudaStream_t s);
 // sources = { act[pi(p)] : p in [p0, p1), label >= 0 }, *k = count (device).
 int launch_batch_sources(const int32_t* act, int64_t N, uint64_t seed, int64_t p0, int64_t p1, const int32_t* label,
                          int32_t* sources, int* k, cudaStream_t s);
@@ -120,7 +120,7 @@ int launch_pivot_order(const int32_t* act, int64_t N, uint64_t seed, int32_t* or
 int64_t feistel_perm_host(int64_t p, int64_t N, uint64_t seed);
 
 // bitmap bit v = (label == NULL ? done-free : label[v] != L)  (pre-set "not in class")
-int launch_prefill_bits(const int32_t* label, int32_t L, int32_t n, uint32_t* bits, cudaStream_t s);
+int launch_prefill_bits(const int32_t* label, int32_t L, int32_t n, uint32_t* bits, uint32_t* bits2, cudaStream_t s);
 // visited[v] = bit v of bits AND label[v] == L (undo the prefill) -> uint8
 int launch_bits_to_bytes(const uint32_t* bits, const int32_t* label, int32_t L, int32_t n, uint8_t* out,
                          cudaStream_t s);

@@ -235,27 +235,68 @@ __global__ void k_rem_scatter(const int32_t* __restrict__ act, int64_t N, Feiste
         }
 }
 
-__global__ void k_active_flags(const int32_t* __restrict__ label, int32_t n, int32_t* flags) {
-    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
-        flags[v] = label[v] >= 0;
+// Active list (vertices with label >= 0, in increasing order) in two passes
+// over the labels: per-tile counts, then (after the scan of the counts) a
+// block scan of the flags and the scatter. Thread t of a tile owns the
+// kScanItems consecutive vertices from tile + t * kScanItems.
+__device__ __forceinline__ int active_bits(const int32_t* __restrict__ label, int32_t n, int64_t base) {
+    int f = 0;
+    if (base + kScanItems <= n && (base & 3) == 0) {
+        const int4* p = reinterpret_cast<const int4*>(label + base);
+#pragma unroll
+        for (int q = 0; q < kScanItems / 4; ++q) {
+            const int4 x = __ldg(p + q);
+            f |= (x.x >= 0) << (4 * q) | (x.y >= 0) << (4 * q + 1) | (x.z >= 0) << (4 * q + 2) |
+                 (x.w >= 0) << (4 * q + 3);
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < kScanItems; ++k) f |= (base + k < n && __ldg(&label[base + k]) >= 0) << k;
+    }
+    return f;
 }
-__global__ void k_scatter_active(const int32_t* __restrict__ flags, const int32_t* __restrict__ pos, int32_t n,
-                                 int32_t* act) {
-    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
-        if (flags[v]) act[pos[v]] = (int32_t)v;
+__global__ void __launch_bounds__(kBlk) k_active_count(const int32_t* __restrict__ label, int32_t n, long long* sums) {
+    const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+    int c = __popc(active_bits(label, n, base));
+    for (int d = 16; d >= 1; d >>= 1) c += __shfl_xor_sync(kFull, c, d);
+    __shared__ int s_c[kBlk / 32];
+    if (lane_id() == 0) s_c[threadIdx.x >> 5] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        long long t = 0;
+        for (int i = 0; i < kBlk / 32; ++i) t += s_c[i];
+        sums[blockIdx.x] = t;
+    }
+}
+__global__ void __launch_bounds__(kBlk) k_active_scatter(const int32_t* __restrict__ label, int32_t n,
+                                                         const long long* __restrict__ sums, int32_t* act) {
+    const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+    int f = active_bits(label, n, base);
+    __shared__ long long tot;
+    long long pos = block_excl_scan(__popc(f), &tot) + sums[blockIdx.x];
+    while (f) {
+        const int k = __ffs(f) - 1;
+        f &= f - 1;
+        act[pos++] = (int32_t)(base + k);
+    }
 }
 
 // --------------------------------------------------------------- bitmaps --
-__global__ void k_prefill_bits(const int32_t* __restrict__ label, int32_t L, int32_t n, uint32_t* bits) {
-    int64_t nw = (n + 31) / 32;
-    for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < nw; w += (int64_t)gridDim.x * blockDim.x) {
-        uint32_t b = 0;
-        for (int i = 0; i < 32; ++i) {
-            int64_t v = w * 32 + i;
-            bool out = v >= n || (label != nullptr && label[v] != L);
-            b |= (uint32_t)out << i;
+// Bit v set for every vertex outside class L (and past n): lane l of a warp
+// reads vertex 32 w + l, a ballot makes word w. bits2, if not null, gets the
+// same words.
+__global__ void k_prefill_bits(const int32_t* __restrict__ label, int32_t L, int32_t n, uint32_t* bits,
+                               uint32_t* bits2) {
+    const int64_t nw = ((int64_t)n + 31) / 32;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < nw; w += warps) {
+        const int64_t v = w * 32 + lane_id();
+        const bool out = v >= n || (label != nullptr && __ldg(&label[v]) != L);
+        const uint32_t b = __ballot_sync(kFull, out);
+        if (lane_id() == 0) {
+            bits[w] = b;
+            if (bits2) bits2[w] = b;
         }
-        bits[w] = b;
     }
 }
 __global__ void k_bits_to_bytes(const uint32_t* __restrict__ bits, const int32_t* __restrict__ label, int32_t L,
@@ -336,23 +377,39 @@ __global__ void k_fill_i32(int32_t* p, int64_t n, int32_t v) {
 // minid[rep[v]] = min v. Lanes of a warp hold consecutive v, so among lanes with
 // the same rep the lowest lane has the smallest v: one atomic per group, and
 // only when it can still lower the stored minimum (an SCC of millions of
-// vertices then costs a few atomics instead of one per vertex).
+// vertices then costs a few atomics instead of one per vertex). A warp's v only
+// grow, so a lane that has already offered its v for a rep skips that rep
+// after: a large SCC is then read once per warp, not once per iteration (its
+// minid word would otherwise take every warp's reads).
 __global__ void k_min_of_rep(const int32_t* __restrict__ rep, int32_t n, int32_t* minid, int* bad) {
+    int last = -1;
     for (int64_t b = (int64_t)blockIdx.x * blockDim.x; b < n; b += (int64_t)gridDim.x * blockDim.x) {
         int64_t v = b + threadIdx.x;
         int r = v < n ? rep[v] : -1;
         bool ok = r >= 0 && r < n;
         if (v < n && !ok) atomicExch(bad, 1);
         int key = ok ? r : -1;
-        uint32_t peers = __match_any_sync(kFull, key);
-        if (ok && lane_id() == __ffs(peers) - 1 && ld_volatile(&minid[r]) > (int32_t)v) atomicMin(&minid[r], (int32_t)v);
+        // a warp inside one SCC (the common case on a large SCC) needs no match
+        const int key0 = __shfl_sync(kFull, key, 0);
+        const uint32_t peers = __all_sync(kFull, key == key0) ? kFull : __match_any_sync(kFull, key);
+        if (ok && lane_id() == __ffs(peers) - 1 && r != last) {
+            last = r;
+            if (ld_volatile(&minid[r]) > (int32_t)v) atomicMin(&minid[r], (int32_t)v);
+        }
     }
 }
+// out[v] = minid[rep[v]], the last rep looked up kept per thread (a large SCC
+// is then one read per thread).
 __global__ void k_write_labels(const int32_t* __restrict__ rep, int32_t n, const int32_t* __restrict__ minid,
                                int32_t* out) {
+    int ck = -1, cv = -1;
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
-        int r = rep[v];
-        out[v] = (r >= 0 && r < n) ? minid[r] : -1;
+        const int r = __ldg(&rep[v]);
+        if (r != ck && r >= 0 && r < n) {
+            ck = r;
+            cv = __ldg(&minid[r]);
+        }
+        out[v] = (r >= 0 && r < n) ? cv : -1;
     }
 }
 
@@ -474,13 +531,15 @@ int launch_init_labels(const int32_t* off, const int32_t* toff, int32_t n, int32
     return SCC_OK;
 }
 
-int launch_compact_active(const int32_t* label, int32_t n, int32_t* flags_tmp, int32_t* pos_tmp, void* scan_tmp,
-                          int32_t* act, cudaStream_t s) {
+int launch_compact_active(const int32_t* label, int32_t n, void* scan_tmp, int32_t* act, cudaStream_t s) {
     if (n == 0) return SCC_OK;
-    k_active_flags<<<grid_for(n, kBlk), kBlk, 0, s>>>(label, n, flags_tmp);
+    const int64_t nb = ceil_div((int64_t)n, kScanTile);
+    long long* sums = (long long*)scan_tmp;
+    k_active_count<<<(unsigned)nb, kBlk, 0, s>>>(label, n, sums);
     SCC_LAUNCH();
-    SCC_TRY(launch_scan(flags_tmp, pos_tmp, n, scan_tmp, s));
-    k_scatter_active<<<grid_for(n, kBlk), kBlk, 0, s>>>(flags_tmp, pos_tmp, n, act);
+    k_scan_sums<<<1, 1024, 0, s>>>(sums, nb, sums + nb);
+    SCC_LAUNCH();
+    k_active_scatter<<<(unsigned)nb, kBlk, 0, s>>>(label, n, sums, act);
     SCC_LAUNCH();
     return SCC_OK;
 }
@@ -525,10 +584,10 @@ int launch_pivot_order(const int32_t* act, int64_t N, uint64_t seed, int32_t* or
     return SCC_OK;
 }
 
-int launch_prefill_bits(const int32_t* label, int32_t L, int32_t n, uint32_t* bits, cudaStream_t s) {
-    int64_t nw = (n + 31) / 32;
+int launch_prefill_bits(const int32_t* label, int32_t L, int32_t n, uint32_t* bits, uint32_t* bits2, cudaStream_t s) {
+    int64_t nw = ((int64_t)n + 31) / 32;
     if (nw == 0) return SCC_OK;
-    k_prefill_bits<<<grid_for(nw, kBlk), kBlk, 0, s>>>(label, L, n, bits);
+    k_prefill_bits<<<grid_for(nw, kBlk / 32), kBlk, 0, s>>>(label, L, n, bits, bits2);
     SCC_LAUNCH();
     return SCC_OK;
 }

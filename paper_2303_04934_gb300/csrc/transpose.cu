@@ -200,9 +200,10 @@ __global__ void __launch_bounds__(kBlkA) k_bucket_hist(const int32_t* __restrict
     if (my_self) atomicAdd(nself, my_self);
 }
 
-// exclusive scan of the bucket counts (one block, sequential: nb <= 2048)
+// exclusive scan of the bucket counts (one block, sequential: nb <= 2048);
+// also zeroes the work counter of the rows pass
 __global__ void k_bucket_scan(const unsigned long long* cnt, int nb, unsigned long long* start,
-                              unsigned long long* cursor) {
+                              unsigned long long* cursor, unsigned int* rows_next) {
     if (threadIdx.x == 0) {
         unsigned long long s = 0;
         for (int i = 0; i < nb; ++i) {
@@ -211,6 +212,7 @@ __global__ void k_bucket_scan(const unsigned long long* cnt, int nb, unsigned lo
             s += cnt[i];
         }
         start[nb] = s;
+        *rows_next = 0;
     }
 }
 
@@ -298,7 +300,9 @@ __global__ void __launch_bounds__(kBlkA) k_bucket_part(const int32_t* __restrict
 }
 
 // B. one block per bucket: per-vertex counts in shared memory, row offsets of
-// G^T for the bucket's vertices, placement with shared cursors. The arcs are
+// G^T for the bucket's vertices, placement with shared cursors. The grid is
+// persistent (the resident blocks); each block takes the next bucket of the
+// largest-first order from a global counter when it is done with one. The arcs are
 // read in aligned chunks of 8 (one 16-byte load of local targets, two of
 // sources), two chunks per thread per step; the arrays are padded by 8 entries
 // so the last chunk may read past the last arc.
@@ -321,12 +325,18 @@ __device__ __forceinline__ int cpad(int i) { return i + (i >> 5); }
 __global__ void __launch_bounds__(kBlkB) k_bucket_rows(const int32_t* __restrict__ uu, const uint16_t* __restrict__ lvv,
                                                        const unsigned long long* __restrict__ start,
                                                        const int32_t* __restrict__ order, int nb, int shift,
-                                                       int32_t n, int32_t* toff, int32_t* tadj, int* err) {
+                                                       int32_t n, int32_t* toff, int32_t* tadj,
+                                                       unsigned int* rows_next, int* err) {
     extern __shared__ int s_cnt[];  // 2^shift counters, padded (cpad)
     __shared__ int s_wsum[kBlkB / 32];
+    __shared__ int s_oi;
     const int W = 1 << shift;
     constexpr int kCh = 2;  // chunks per thread per step
-    for (int oi = blockIdx.x; oi < nb; oi += gridDim.x) {
+    for (;;) {
+        if (threadIdx.x == 0) s_oi = (int)atomicAdd(rows_next, 1u);
+        __syncthreads();
+        const int oi = s_oi;
+        if (oi >= nb) break;
         const int b = order[oi];
         const int v0 = b << shift;
         const int vw = min(W, n - v0);
@@ -509,11 +519,12 @@ int launch_transpose(const int32_t* off, const int32_t* adj, const int32_t* trow
     const int nb = std::max(1, (int)(((int64_t)n + (1ll << shift) - 1) >> shift));
     unsigned long long* start = bucket_tmp;
     unsigned long long* cursor = bucket_tmp + nb + 1;
+    unsigned int* rows_next = reinterpret_cast<unsigned int*>(bucket_tmp + 2 * nb + 1);
     if (n == 0) {
         SCC_CUDA(cudaMemsetAsync(toff, 0, sizeof(int32_t), s));
         return SCC_OK;
     }
-    k_bucket_scan<<<1, 32, 0, s>>>(bucket_cnt, nb, start, cursor);
+    k_bucket_scan<<<1, 32, 0, s>>>(bucket_cnt, nb, start, cursor, rows_next);
     SCC_LAUNCH();
     if (mt > 0) {
         const int stage = 2 * kStep * (int)sizeof(int32_t);
@@ -543,9 +554,12 @@ int launch_transpose(const int32_t* off, const int32_t* adj, const int32_t* trow
     const size_t smem = sizeof(int) * (((size_t)1 << shift) + ((size_t)1 << shift) / 32 + 1);
     if (smem > 48 * 1024)
         SCC_CUDA(cudaFuncSetAttribute(k_bucket_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    SCC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bucket_rows, kBlkB, smem));
     if (ev) cudaEventRecord(ev[2], s);
-    k_bucket_rows<<<std::min(nb, num_sms * 2), kBlkB, smem, s>>>(tmp_u, tmp_lv, start, order_tmp, nb, shift, n, toff,
-                                                                   tadj, err);
+    k_bucket_rows<<<std::min(nb, num_sms * std::max(1, per_sm)), kBlkB, smem, s>>>(tmp_u, tmp_lv, start, order_tmp,
+                                                                                     nb, shift, n, toff, tadj,
+                                                                                     rows_next, err);
     SCC_LAUNCH();
     if (ev) cudaEventRecord(ev[3], s);
     SCC_CUDA(cudaStreamSynchronize(s));  // ord (host) must outlive the copy

@@ -97,6 +97,26 @@ def test_host_buffers_and_repeat_runs():
             assert np.array_equal(labels_of(G, host=False), want)
 
 
+def test_page_locked_host_input():
+    """Page-locked host targets are read by the intake pass directly: aligned
+    and unaligned starts, self-loops (the CSR is rebuilt) and a bad target."""
+    import torch
+    for g in (gg.rmat(14, 8, seed=42), gg.torus(2, 90, 0.5, seed=43),
+              gg.gnp(300, 0.02, seed=44, allow_self=True)):
+        want, _ = oracle.scc_labels(g.n, g.offsets, g.targets)
+        for shift in (0, 1, 3):
+            buf = torch.zeros(g.m + shift + 1, dtype=torch.int32).pin_memory()
+            buf[shift:shift + g.m] = torch.from_numpy(g.targets)
+            off = torch.from_numpy(g.offsets).pin_memory()
+            with scc.SccGraph(g.n, off, buf[shift:shift + g.m]) as G:
+                assert np.array_equal(labels_of(G, host=True), want), (g.name, shift)
+    g = gg.torus(2, 20, 0.5, seed=45)
+    bad = torch.from_numpy(g.targets.copy()).pin_memory()
+    bad[len(bad) // 2] = g.n
+    with pytest.raises(scc.SccError):
+        scc.SccGraph(g.n, torch.from_numpy(g.offsets).pin_memory(), bad)
+
+
 def test_invariants_hold_on_gpu_output():
     g = gg.rmat(15, 8, seed=51)
     with make_graph(g) as G:
