@@ -776,7 +776,8 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
             "config": {"workload": workload_name(spec, g), "n": n, "m": m, "seed": spec["seed"],
                        "parallelism": f"replicas{world}", "l2": "inputs larger than L2 (CSR + transpose > 2 GB)",
-                       "tau": cfg.tau, "seeds": cfg.seeds, "beta": cfg.beta, "lambda": cfg.lambda_,
+                       "tau": cfg.tau or last["tau"], "tau_auto": cfg.tau == 0, "seeds": cfg.seeds,
+                       "beta": cfg.beta, "lambda": cfg.lambda_,
                        "step": "scc_graph_create + scc_run + scc_graph_destroy"},
             "e2e": e2e, "roofline": roofline, "cpu_baseline": cpu, "gpu_launches": launches,
             "clocks": clk}

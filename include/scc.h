@@ -64,7 +64,12 @@ SCC_API const char* scc_error_string(int code);
  *   tau         VGC edge budget of one local search (Sec. 3.2 "Control of
  *               Granularity"): a warp task stops expanding after visiting about
  *               tau arcs; vertices with more than tau out-arcs are expanded by
- *               many warps in parallel instead. Default 512 (the paper's 2^9).
+ *               many warps in parallel instead. 1..2^20, or 0 (the default):
+ *               chosen per graph, 128 when the average degree is at least 8,
+ *               2048 below. The paper's 2^9 = 512 is the middle of that range;
+ *               on the GPU a round's time is set by its longest local search,
+ *               which on a graph of high degree grows faster with tau than the
+ *               rounds it saves, and on a lattice or k-NN graph more slowly.
  *   beta        prefix-doubling multiplier, > 1 (Alg. 1 doubles the batches, the
  *               experiments use 1.5). Default 2: a batch costs rounds whose
  *               time on the GPU is set by memory latency more than by the pairs
@@ -203,6 +208,7 @@ typedef struct scc_stats {
     int32_t multi_launches;
     int64_t multi_arcs;        /* arcs examined */
     int64_t multi_items;       /* items expanded */
+    int32_t tau;               /* the VGC edge budget used (config tau, or the automatic one) */
 } scc_stats;
 
 SCC_API int scc_get_stats(scc_handle h, scc_stats* out);

@@ -158,20 +158,24 @@ int from_device(void* dst, const void* src, size_t bytes, cudaStream_t s) {
 // other with dense rounds (below it they share one launch without)
 constexpr double kDenseDegree = 8.0;
 
+// automatic VGC budgets (config tau 0), by average degree
+constexpr int kAutoTauHighDegree = 128;
+constexpr int kAutoTauLowDegree = 2048;
+
 EngineOpts opts_of(const scc_graph* h) {
     EngineOpts o;
-    o.tau = h->cfg.tau;
     o.seeds = h->cfg.seeds;
     o.sigma = h->cfg.sigma;
     o.block = h->cfg.block;
     o.num_sms = h->di.num_sms;
     o.high_degree = (double)h->mt >= kDenseDegree * (double)std::max<int32_t>(h->n, 1);
+    o.tau = h->cfg.tau ? h->cfg.tau : (o.high_degree ? kAutoTauHighDegree : kAutoTauLowDegree);
     return o;
 }
 
 int valid_config(const scc_config* c) {
     if (!c) return SCC_ERR_INVALID_ARG;
-    if (c->tau < 1 || c->tau > (1 << 20)) return SCC_ERR_INVALID_ARG;
+    if (c->tau < 0 || c->tau > (1 << 20)) return SCC_ERR_INVALID_ARG;
     if (!(c->beta > 1.0 && c->beta <= 64.0)) return SCC_ERR_INVALID_ARG;
     if (c->lambda < 1024 || c->lambda > (1 << 24) || (c->lambda & (c->lambda - 1))) return SCC_ERR_INVALID_ARG;
     if (c->sigma < 1 || c->sigma > (1 << 20)) return SCC_ERR_INVALID_ARG;
@@ -273,7 +277,7 @@ const char* scc_error_string(int code) {
 
 int scc_config_default(scc_config* cfg) {
     if (!cfg) return SCC_ERR_INVALID_ARG;
-    cfg->tau = 512;
+    cfg->tau = 0;
     cfg->beta = 2.0;
     cfg->lambda = 1 << 14;
     cfg->sigma = 50;
@@ -531,6 +535,7 @@ static int scc_run_impl(scc_graph* h, int32_t* labels_out, cudaStream_t s) {
     const int32_t n = h->n;
     scc_stats& st = h->stats;
     memset(&st, 0, sizeof(st));
+    st.tau = opts_of(h).tau;
     if (n == 0) return SCC_OK;
     SCC_TRY(reserve_run_state(h, s));
     EngineOpts o = opts_of(h);

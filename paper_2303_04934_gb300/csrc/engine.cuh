@@ -553,73 +553,92 @@ __device__ bool engine_search(const EngineParams<typename Pol::Item>& P, Pol& po
                 if (!S::sync(&ctl->bar, &ctl->err)) return false;
                 const long long nw = ((long long)P.n + 31) / 32;
                 // each warp takes 32 consecutive words at a time (one coalesced
-                // load) and works only on words with unvisited vertices, kDW of
-                // them together: lane l scans the in-arcs of vertex l of each of
-                // the kDW words, two arcs per vertex per step, so up to 2 * kDW
-                // independent loads per lane are in flight
-                constexpr int kDW = 4;
+                // load); their unvisited vertices form the warp's work list,
+                // handed to lanes one vertex at a time: a lane whose vertex is
+                // done (a parent in the frontier found, or its in-arcs
+                // exhausted) takes the next entry, so a few long in-lists do not
+                // hold the other lanes. A lane keeps kDV vertices in flight and
+                // reads two in-arcs of each per step. Found bits gather in 32
+                // shared words (the warp's local queue is idle in dense rounds)
+                // and are written once per word: the warp owns its words.
+                constexpr int kDV = 2;
+                static_assert(sizeof(Item) * Pol::kQueue >= 32 * sizeof(uint32_t), "queue holds 32 words");
+                uint32_t* s_found = reinterpret_cast<uint32_t*>(q.it);
+                unsigned long long scanned = 0;
                 for (long long w0 = (long long)wid * 32; w0 < nw; w0 += (long long)nwarps * 32) {
                     const uint32_t mine = w0 + lane < nw ? ld_volatile(&pol.bits[w0 + lane]) : ~0u;
-                    uint32_t todo = __ballot_sync(kFull, mine != ~0u);
-                    while (todo) {
-                        int jw[kDW];
-                        uint32_t word[kDW];
-                        int e[kDW], e1[kDW];
-                        bool found[kDW];
+                    const uint32_t unv = ~mine;  // bits past n are set by the prefill
+                    const int cnt = __popc(unv);
+                    const int incl = warp_incl_scan(cnt);
+                    const int T = __shfl_sync(kFull, incl, 31);
+                    if (T == 0) continue;  // warp-uniform
+                    s_found[lane] = 0;
+                    __syncwarp();
+                    int next = 0;  // warp-uniform cursor into the list
+                    int vv[kDV], e[kDV], e1[kDV];
 #pragma unroll
-                        for (int k = 0; k < kDW; ++k) {
-                            jw[k] = todo ? __ffs(todo) - 1 : -1;  // warp-uniform
-                            if (todo) todo &= todo - 1;
-                            word[k] = jw[k] >= 0 ? __shfl_sync(kFull, mine, jw[k]) : ~0u;
-                            const long long v = (w0 + (jw[k] >= 0 ? jw[k] : 0)) * 32 + lane;
-                            const bool act = jw[k] >= 0 && v < P.n && !((word[k] >> lane) & 1u);
-                            e[k] = act ? S::ld(&dp->roff[v]) : 0;
-                            e1[k] = act ? S::ld(&dp->roff[v + 1]) : 0;
-                            found[k] = false;
+                    for (int k = 0; k < kDV; ++k) vv[k] = e[k] = e1[k] = -1;
+                    for (;;) {
+#pragma unroll
+                        for (int k = 0; k < kDV; ++k) {
+                            const bool idle = vv[k] < 0;
+                            const uint32_t need = __ballot_sync(kFull, idle);
+                            const int idx = next + __popc(need & lanemask_lt());
+                            next += __popc(need);
+                            // list entry idx lies in word j, the first with incl > idx
+                            int j = 0;
+#pragma unroll
+                            for (int sh = 16; sh >= 1; sh >>= 1)
+                                if (__shfl_sync(kFull, incl, j + sh - 1) <= idx) j += sh;
+                            const uint32_t uj = __shfl_sync(kFull, unv, j);
+                            const int bj = __shfl_sync(kFull, incl - cnt, j);
+                            if (idle && idx < T) {
+                                const int v = (int)((w0 + j) * 32 + (long long)__fns(uj, 0, idx - bj + 1));
+                                vv[k] = v;
+                                e[k] = S::ld(&dp->roff[v]);
+                                e1[k] = S::ld(&dp->roff[v + 1]);
+                            }
                         }
-                        unsigned long long scanned = 0;
-                        for (;;) {
-                            int u[kDW][2];
-                            bool any = false;
+                        bool busy = false;
 #pragma unroll
-                            for (int k = 0; k < kDW; ++k) {
+                        for (int k = 0; k < kDV; ++k) busy |= vv[k] >= 0;
+                        if (!__any_sync(kFull, busy)) break;  // every lane idle: the list is done
+                        int u[kDV][2];
 #pragma unroll
-                                for (int a = 0; a < 2; ++a) {
-                                    const bool go = !found[k] && e[k] + a < e1[k];
-                                    u[k][a] = go ? S::ld(&dp->radj[e[k] + a]) : -1;
-                                    any |= go;
+                        for (int k = 0; k < kDV; ++k)
+#pragma unroll
+                            for (int a = 0; a < 2; ++a)
+                                u[k][a] = vv[k] >= 0 && e[k] + a < e1[k] ? S::ld(&dp->radj[e[k] + a]) : -1;
+                        uint32_t fw[kDV][2];
+#pragma unroll
+                        for (int k = 0; k < kDV; ++k)
+#pragma unroll
+                            for (int a = 0; a < 2; ++a) fw[k][a] = u[k][a] >= 0 ? ld_volatile(&fb[u[k][a] >> 5]) : 0u;
+#pragma unroll
+                        for (int k = 0; k < kDV; ++k) {
+                            bool f = false;
+#pragma unroll
+                            for (int a = 0; a < 2; ++a)
+                                if (!f && u[k][a] >= 0) {
+                                    ++scanned;
+                                    f = (fw[k][a] >> (u[k][a] & 31)) & 1u;
                                 }
-                            }
-                            if (!any) break;
-                            uint32_t fw[kDW][2];
-#pragma unroll
-                            for (int k = 0; k < kDW; ++k)
-#pragma unroll
-                                for (int a = 0; a < 2; ++a) fw[k][a] = u[k][a] >= 0 ? ld_volatile(&fb[u[k][a] >> 5]) : 0u;
-#pragma unroll
-                            for (int k = 0; k < kDW; ++k) {
-#pragma unroll
-                                for (int a = 0; a < 2; ++a)
-                                    if (!found[k] && u[k][a] >= 0) {
-                                        ++scanned;
-                                        found[k] = (fw[k][a] >> (u[k][a] & 31)) & 1u;
-                                    }
-                                e[k] += 2;
-                            }
-                        }
-                        for (int dd = 16; dd >= 1; dd >>= 1) scanned += __shfl_xor_sync(kFull, scanned, dd);
-                        if (lane == 0) ws.edges += scanned;
-#pragma unroll
-                        for (int k = 0; k < kDW; ++k) {
-                            if (jw[k] < 0) break;  // warp-uniform
-                            const long long w = w0 + jw[k];
-                            const uint32_t m = __ballot_sync(kFull, found[k]);
-                            if (lane == 0 && m) pol.bits[w] = word[k] | m;  // this warp owns word w in this round
-                            if (lane == 0) ws.items += __popc(m);
-                            pushed += bag_push<Item>(out, st, found[k], (Item)(w * 32 + lane), wid, gr);
+                            e[k] += 2;
+                            if (f) atomicOr(&s_found[(vv[k] >> 5) - w0], 1u << (vv[k] & 31));
+                            pushed += bag_push<Item>(out, st, f, (Item)vv[k], wid, gr);
+                            if (f || e[k] >= e1[k]) vv[k] = -1;
                         }
                     }
+                    __syncwarp();
+                    const uint32_t fm = s_found[lane];
+                    if (fm) pol.bits[w0 + lane] = mine | fm;  // fm != 0 only for words < nw
+                    int nf = __popc(fm);
+                    for (int dd = 16; dd >= 1; dd >>= 1) nf += __shfl_xor_sync(kFull, nf, dd);
+                    if (lane == 0) ws.items += nf;
+                    __syncwarp();  // the next group resets s_found
                 }
+                for (int dd = 16; dd >= 1; dd >>= 1) scanned += __shfl_xor_sync(kFull, scanned, dd);
+                if (lane == 0) ws.edges += scanned;
             }
         } else {
             // once a table overflows the round's work is moot: stop taking work

@@ -39,7 +39,7 @@ def test_error_strings_and_default_config(lib):
     for code in (0, -1, -2, -3, -4, -5, -6):
         assert lib.scc_error_string(code)
     cfg = scc.scc_config_default()
-    assert cfg.tau == 512 and cfg.beta == 2.0 and cfg.sigma == 50 and cfg.lambda_ == 16384
+    assert cfg.tau == 0 and cfg.beta == 2.0 and cfg.sigma == 50 and cfg.lambda_ == 16384
 
 
 def test_invalid_arguments_rejected_on_the_host(lib):
