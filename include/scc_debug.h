@@ -69,6 +69,18 @@ SCC_API int scc_debug_multi_reach(scc_handle h, const int32_t* labels, const int
                           int64_t table_cap, void* stream);
 
 /*
+ * reach_multi (scc.h) with up to 128 sources, as the serving loop runs it when
+ * it merges queries (Sec. 2 reachability; the wider mask has no counterpart in
+ * the paper): out[2 v + j / 64] gets bit j % 64 set iff sources[j] reaches v
+ * (dir 0) or v reaches sources[j] (dir 1).
+ *   sources  host or device int32[k], 1 <= k <= 128, each in [0, n).
+ *   out      host or device uint64[2 n].
+ * SCC_ERR_INVALID_ARG for k or a source out of range.
+ */
+SCC_API int scc_debug_reach_multi_wide(scc_handle h, const int32_t* sources, int32_t k, int32_t dir, uint64_t* out,
+                                       void* stream);
+
+/*
  * Hash bag (Sec. 3.3, Fig. 5): insert items[0..count) from many warps
  * concurrently (each warp claims random 32-slot segments of the current chunk by
  * CAS, with sampled chunk advance), then ExtractAll by warp-aggregated

@@ -16,8 +16,9 @@
  *   - units, oldest request first: every admitted SCC request small enough for
  *     the batched kernel (scc_batch.h: one block per graph) joins one launch;
  *     reachability queries on the same resident graph and direction share one
- *     reach_multi launch (up to 64 sources; each query's bits are split out on
- *     the device); a larger SCC request runs the full-GPU path (scc.h).
+ *     reachability launch (up to 128 sources: above 64 the search carries two
+ *     mask words per vertex; each query's bits are split out on the device); a
+ *     larger SCC request runs the full-GPU path (scc.h).
  *     Requests that arrive while a unit runs are admitted when it ends.
  * Results are identical whether a request runs alone or in any mix.
  *

@@ -260,6 +260,37 @@ struct EvTimer {
 }  // namespace
 
 // ==================================================================== ABI ====
+namespace scc {
+
+// reach_multi with 1..128 sources already on the device: mask2 (device, two
+// words per vertex) gets bit j of vertex v (word 2 v + j / 64, bit j % 64) iff
+// sources[j] reaches v (dir 0) or v reaches sources[j] (dir 1).
+int reach_multi_wide(scc_graph* h, const int32_t* sources_d, int32_t k, int32_t dir,
+                          unsigned long long* mask2, cudaStream_t s) {
+    if (!h || !sources_d || !mask2 || k < 1 || k > 128 || (dir != 0 && dir != 1)) return SCC_ERR_INVALID_ARG;
+    h->last = s;
+    const int32_t n = h->n;
+    SCC_TRY(reserve_run_state(h, s));
+    for (int attempt = 0;; ++attempt) {  // bag too small: restart with twice the buffers
+        if (attempt > 8) return SCC_ERR_CAPACITY;
+        SCC_CUDA(cudaMemsetAsync(mask2, 0, (size_t)n * 16, s));
+        SCC_CUDA(cudaMemsetAsync(h->flags + 1, 0, sizeof(int), s));
+        SCC_TRY(launch_mask_init(sources_d, k, n, 2, mask2, h->flags + 1, s));
+        int bad = 0;
+        SCC_CUDA(cudaMemcpyAsync(&bad, h->flags + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
+        SCC_CUDA(cudaStreamSynchronize(s));
+        if (bad) return SCC_ERR_INVALID_ARG;
+        SCC_TRY(engine_reserve(&h->eb32, 4, ((long long)n + 1024) << attempt, h->cfg.lambda, h->mt, s));
+        EngineRun r;
+        int rc = run_mask2(dir == 0 ? h->off : h->toff, dir == 0 ? h->adj : h->tadj, n, sources_d, k, mask2, &h->eb32,
+                           opts_of(h), &r, s);
+        if (rc == SCC_ERR_CAPACITY) continue;
+        return rc;
+    }
+}
+
+}  // namespace scc
+
 extern "C" {
 
 const char* scc_error_string(int code) {
@@ -779,7 +810,7 @@ int reach_multi(scc_handle h, const int32_t* sources, int32_t k, int32_t dir, ui
         if (attempt > 8) return SCC_ERR_CAPACITY;
         SCC_CUDA(cudaMemsetAsync(mask, 0, (size_t)n * 8, s));
         SCC_CUDA(cudaMemsetAsync(h->flags + 1, 0, sizeof(int), s));
-        SCC_TRY(launch_mask_init(dsrc, k, n, mask, h->flags + 1, s));
+        SCC_TRY(launch_mask_init(dsrc, k, n, 1, mask, h->flags + 1, s));
         int bad = 0;
         SCC_CUDA(cudaMemcpyAsync(&bad, h->flags + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
         SCC_CUDA(cudaStreamSynchronize(s));
@@ -885,6 +916,28 @@ int scc_debug_single_reach(scc_handle h, const int32_t* labels, int32_t src, int
     if (rc == SCC_OK) rc = from_device(visited, d, (size_t)n, s);
     if (rc == SCC_OK) rc = cuda_err(cudaStreamSynchronize(s));
     dfree(d, s);
+    return rc;
+}
+
+int scc_debug_reach_multi_wide(scc_handle h, const int32_t* sources, int32_t k, int32_t dir, uint64_t* out,
+                               void* stream) {
+    if (!h || !sources || !out || k < 1 || k > 128 || (dir != 0 && dir != 1)) return SCC_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    h->last = s;
+    const int32_t n = h->n;
+    if (!is_device_ptr(sources)) {
+        for (int j = 0; j < k; ++j)
+            if (sources[j] < 0 || sources[j] >= n) return SCC_ERR_INVALID_ARG;
+    }
+    SCC_TRY(reserve_run_state(h, s));
+    SCC_TRY(to_device(h->sources, sources, sizeof(int32_t) * (size_t)k, s));
+    const bool dev_out = is_device_ptr(out);
+    unsigned long long* mask2 = reinterpret_cast<unsigned long long*>(out);
+    if (!dev_out) SCC_TRY(dalloc_t(&mask2, 2 * (size_t)std::max(n, 1), s));
+    int rc = reach_multi_wide(h, h->sources, k, dir, mask2, s);
+    if (rc == SCC_OK && !dev_out) rc = from_device(out, mask2, (size_t)n * 16, s);
+    if (rc == SCC_OK) rc = cuda_err(cudaStreamSynchronize(s));
+    if (!dev_out) dfree(mask2, s);
     return rc;
 }
 

@@ -321,7 +321,8 @@ __device__ __forceinline__ void expand_batch(const EngineParams<typename Pol::It
     if (seeds_phase && avail > max_take) avail = max_take;
     Item it = Sent<Item>::empty;
     int beg = 0, deg = 0;
-    uint64_t qctx = 0;
+    using Ctx = typename Pol::Ctx;
+    Ctx qctx{};
     if (lane < avail) {
         const uint32_t k = (qh + lane) & QM;
         it = q.it[k];
@@ -348,8 +349,8 @@ __device__ __forceinline__ void expand_batch(const EngineParams<typename Pol::It
     }
     qh += take;
     pushed += bag_push<Item>(out, st, hub, it, wid, round);
-    uint64_t ctx = qctx;
-    if constexpr (!Pol::kCtxInQueue) ctx = (lane < take && !hub) ? pol.ctx(it) : 0;
+    Ctx ctx = qctx;
+    if constexpr (!Pol::kCtxInQueue) ctx = (lane < take && !hub) ? pol.ctx(it) : Ctx{};
     const int total = __shfl_sync(kFull, pre, 31);
     const int excl = pre - d;
     // four groups of 32 arcs per step: the adjacency loads and the visit tests of
@@ -358,7 +359,7 @@ __device__ __forceinline__ void expand_batch(const EngineParams<typename Pol::It
     for (int base = 0; base < total; base += 32 * U) {
         int w[U];
         Item jit[U];
-        uint64_t jctx[U];
+        Ctx jctx[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             const int e = base + u * 32 + lane;
@@ -658,7 +659,7 @@ __device__ bool engine_search(const EngineParams<typename Pol::Item>& P, Pol& po
                     const long long j0 = (gs - P.hub_segbase[ipar][h]) * kHubSeg;
                     const int b0 = P.hub_beg[ipar][h] + (int)j0;
                     const int len = (int)min((long long)kHubSeg, (long long)P.hub_deg[ipar][h] - j0);
-                    const uint64_t hctx = pol.ctx(hit);
+                    const typename Pol::Ctx hctx = pol.ctx(hit);
                     for (int e0 = 0; e0 < len; e0 += 32) {
                         bool nw = false;
                         Item child = Sent<Item>::empty;
@@ -804,6 +805,7 @@ struct PolSingle {
     static constexpr bool kCountInserts = false;
     static constexpr bool kDense = true;
     static constexpr bool kCtxInQueue = false;
+    using Ctx = uint64_t;  // the per-item value an arc test reads
     static constexpr bool kTwoGraphs = false;
     static constexpr const char* kName = "single-reach";
     uint32_t* bits;
@@ -833,6 +835,7 @@ struct PolSingleBoth {
     static constexpr bool kCountInserts = false;
     static constexpr bool kDense = false;
     static constexpr bool kCtxInQueue = false;
+    using Ctx = uint64_t;  // the per-item value an arc test reads
     static constexpr bool kTwoGraphs = true;
     static constexpr const char* kName = "single-reach-both";
     static constexpr uint32_t kDir = 1u << 31;
@@ -906,6 +909,7 @@ struct PolPair {
     static constexpr bool kCountInserts = true;
     static constexpr bool kDense = false;
     static constexpr bool kCtxInQueue = true;
+    using Ctx = uint64_t;  // the per-item value an arc test reads
     static constexpr bool kTwoGraphs = true;
     static constexpr const char* kName = "multi-reach";
     static constexpr uint64_t kDir = 1ull << 63;
@@ -978,6 +982,7 @@ struct PolMask {
     static constexpr bool kCountInserts = false;
     static constexpr bool kDense = false;
     static constexpr bool kCtxInQueue = false;
+    using Ctx = uint64_t;  // the per-item value an arc test reads
     static constexpr bool kTwoGraphs = false;
     static constexpr const char* kName = "mask-reach";
     unsigned long long* mask;
@@ -993,6 +998,41 @@ struct PolMask {
         const unsigned long long old = atomicOr(&mask[w], (unsigned long long)mu);
         child = (Item)w;
         return (mu & ~old) != 0;
+    }
+};
+
+// reach_multi with up to 128 sources: two 64-bit words per vertex, mask[2 v]
+// holding sources 0..63 and mask[2 v + 1] sources 64..127 (the same search as
+// PolMask, with the item's two words as its context).
+struct Mask128 {
+    unsigned long long lo, hi;
+};
+__device__ __forceinline__ Mask128 shfl_any(const Mask128& v, int src) {
+    return {__shfl_sync(kFull, v.lo, src), __shfl_sync(kFull, v.hi, src)};
+}
+struct PolMask2 {
+    using Item = uint32_t;
+    static constexpr int kQueue = 256;
+    static constexpr bool kCountInserts = false;
+    static constexpr bool kDense = false;
+    static constexpr bool kCtxInQueue = false;
+    using Ctx = Mask128;
+    static constexpr bool kTwoGraphs = false;
+    static constexpr const char* kName = "mask-reach-128";
+    unsigned long long* mask;
+    bool test_first;  // read the target's words before the atomics (high-degree graphs)
+    __device__ __forceinline__ int vertex(Item it) const { return (int)it; }
+    __device__ __forceinline__ Mask128 ctx(Item it) const {
+        return {ld_volatile(&mask[2 * (size_t)it]), ld_volatile(&mask[2 * (size_t)it + 1])};
+    }
+    __device__ __forceinline__ bool seed(Item) const { return true; }
+    __device__ __forceinline__ bool visit(Item, const Mask128& mu, int w, Item& child) const {
+        unsigned long long* tw = mask + 2 * (size_t)w;
+        if (test_first && ((mu.lo & ~ld_volatile(&tw[0])) | (mu.hi & ~ld_volatile(&tw[1]))) == 0) return false;
+        const unsigned long long o0 = mu.lo ? atomicOr(&tw[0], mu.lo) : 0ull;
+        const unsigned long long o1 = mu.hi ? atomicOr(&tw[1], mu.hi) : 0ull;
+        child = (Item)w;
+        return ((mu.lo & ~o0) | (mu.hi & ~o1)) != 0;
     }
 };
 

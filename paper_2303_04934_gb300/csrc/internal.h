@@ -138,7 +138,7 @@ int launch_canonicalize(const int32_t* rep, int32_t n, int32_t* minid, int32_t* 
                         cudaStream_t s);
 
 // mask[sources[j]] |= 1 << j; *bad = 1 if a source is outside [0, n).
-int launch_mask_init(const int32_t* sources, int32_t k, int32_t n, unsigned long long* mask, int* bad,
+int launch_mask_init(const int32_t* sources, int32_t k, int32_t n, int words, unsigned long long* mask, int* bad,
                      cudaStream_t s);
 // out = the sources with label >= 0 (count in *cnt); *bad = 1 if one is outside [0, n).
 int launch_filter_sources(const int32_t* in, int32_t k, int32_t n, const int32_t* label, int32_t* out, int* cnt,
@@ -225,6 +225,9 @@ int run_pairs(const int32_t* off, const int32_t* adj, int32_t n, const int32_t* 
               int32_t k, unsigned long long* table, int64_t cap, long long max_inserted, EngineBuf* b,
               const EngineOpts& o, EngineRun* out, cudaStream_t st);
 // Mask reachability: mask already holds the source bits; init = sources.
+// mask2: two words per vertex, k <= 128
+int run_mask2(const int32_t* off, const int32_t* adj, int32_t n, const int32_t* sources, int32_t k,
+              unsigned long long* mask2, EngineBuf* b, const EngineOpts& o, EngineRun* out, cudaStream_t st);
 int run_mask(const int32_t* off, const int32_t* adj, int32_t n, const int32_t* sources, int32_t k,
              unsigned long long* mask, EngineBuf* b, const EngineOpts& o, EngineRun* out, cudaStream_t st);
 
@@ -291,6 +294,9 @@ int batch_runner_enqueue(BatchRunner* r, int32_t G, const long long* vbase, cons
 int run_mask_fixed(const int32_t* off, const int32_t* adj, int32_t n, const int32_t* sources, int32_t k,
                    unsigned long long* mask, const EngineBuf* b, const EngineOpts& o, EngineRun* out,
                    cudaStream_t st);
+// reach_multi with 1..128 device sources into two mask words per vertex (api.cu).
+int reach_multi_wide(scc_graph* h, const int32_t* sources_d, int32_t k, int32_t dir, unsigned long long* mask2,
+                     cudaStream_t s);
 // reach_multi on the library's fixed device scratch array (noalloc.cu).
 int reach_multi_noalloc_impl(const int32_t* off, const int32_t* adj, int32_t n, int64_t mt, int lambda,
                              const EngineOpts& o, const int32_t* sources, int32_t k, uint64_t* out,

@@ -118,7 +118,7 @@ int reach_multi_noalloc_impl(const int32_t* off, const int32_t* adj, int32_t n, 
     SCC_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), s));
     SCC_CUDA(cudaMemsetAsync(out, 0, (size_t)n * 8, s));
     auto* mask = reinterpret_cast<unsigned long long*>(out);
-    SCC_TRY(launch_mask_init(sources, k, n, mask, bad, s));
+    SCC_TRY(launch_mask_init(sources, k, n, 1, mask, bad, s));
     int hbad = 0;
     SCC_CUDA(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
     SCC_CUDA(cudaStreamSynchronize(s));

@@ -259,6 +259,19 @@ int run_mask(const int32_t* off, const int32_t* adj, int32_t n, const int32_t* s
     return out->err ? out->err : SCC_OK;
 }
 
+// reach_multi with up to 128 sources (two mask words per vertex).
+int run_mask2(const int32_t* off, const int32_t* adj, int32_t n, const int32_t* sources, int32_t k,
+              unsigned long long* mask2, EngineBuf* b, const EngineOpts& o, EngineRun* out, cudaStream_t st) {
+    auto P = make_engine_params<uint32_t>(off, adj, n, b, o);
+    P.init = reinterpret_cast<const uint32_t*>(sources);
+    P.ninit = k;
+    PolMask2 pol{mask2, o.high_degree};
+    int rc = launch_engine(P, pol, o, out, st);
+    if (rc != SCC_OK || out->err) SCC_TRY(engine_reset_slots(b, st));
+    SCC_TRY(rc);
+    return out->err ? out->err : SCC_OK;
+}
+
 // Mask reachability on caller-provided (fixed) engine buffers: no device
 // allocation and no CUDA event; the caller has emptied the bag and the control
 // block. A search that needs more bag space than the buffers hold returns

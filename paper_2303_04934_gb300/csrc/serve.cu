@@ -33,13 +33,23 @@ namespace {
 
 using Clock = std::chrono::steady_clock;
 
-// out[v] = the k bits of mask[v] starting at bit `shift` (one query's share of
-// a merged reach_multi launch)
-__global__ void k_split_bits(const unsigned long long* __restrict__ mask, int32_t n, int shift, int k,
+// Sources of one merged reach launch (two mask words per vertex above 64).
+constexpr int kMaxMergedSources = 128;
+
+// out[v] = the k <= 64 bits starting at bit `shift` of vertex v's mask, which
+// is `words` (1 or 2) 64-bit words, the first holding bits 0..63 (one query's
+// share of a merged reach launch)
+__global__ void k_split_bits(const unsigned long long* __restrict__ mask, int words, int32_t n, int shift, int k,
                              unsigned long long* __restrict__ out) {
     const unsigned long long lm = k >= 64 ? ~0ull : ((1ull << k) - 1ull);
-    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
-        out[v] = (mask[v] >> shift) & lm;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+        const unsigned long long lo = mask[words * v], hi = words > 1 ? mask[words * v + 1] : 0ull;
+        unsigned long long x;
+        if (shift == 0) x = lo;
+        else if (shift < 64) x = (lo >> shift) | (hi << (64 - shift));
+        else x = hi >> (shift - 64);
+        out[v] = x & lm;
+    }
 }
 
 struct Request {
@@ -235,14 +245,17 @@ void run_reach(scc_server* S, std::vector<ReqPtr>& u) {
     std::vector<int32_t> all;
     for (auto& r : u) all.insert(all.end(), r->src.begin(), r->src.end());
     const int32_t K = (int32_t)all.size();
+    const int words = K > 64 ? 2 : 1;  // above 64 sources: the two-word search
     int32_t* src_d = nullptr;
     unsigned long long* mask_d = nullptr;
     unsigned long long* part_d = nullptr;
     int rc = dalloc_t(&src_d, (size_t)K, S->cs);
-    if (rc == SCC_OK) rc = dalloc_t(&mask_d, (size_t)std::max(n, 1), S->cs);
+    if (rc == SCC_OK) rc = dalloc_t(&mask_d, (size_t)words * std::max(n, 1), S->cs);
     if (rc == SCC_OK && u.size() > 1) rc = dalloc_t(&part_d, (size_t)std::max(n, 1), S->cs);
     if (rc == SCC_OK) rc = cuda_err(cudaMemcpyAsync(src_d, all.data(), sizeof(int32_t) * K, cudaMemcpyHostToDevice, S->cs));
-    if (rc == SCC_OK) rc = reach_multi(R->g, src_d, K, u[0]->dir, reinterpret_cast<uint64_t*>(mask_d), S->cs);
+    if (rc == SCC_OK)
+        rc = words == 1 ? reach_multi(R->g, src_d, K, u[0]->dir, reinterpret_cast<uint64_t*>(mask_d), S->cs)
+                        : reach_multi_wide(R->g, src_d, K, u[0]->dir, mask_d, S->cs);
     if (rc == SCC_OK) {
         int shift = 0;
         for (auto& r : u) {
@@ -251,8 +264,8 @@ void run_reach(scc_server* S, std::vector<ReqPtr>& u) {
                 rc = cuda_err(cudaMemcpyAsync(r->out_h, mask_d, sizeof(uint64_t) * (size_t)n, cudaMemcpyDefault,
                                               S->cs));
             } else {
-                k_split_bits<<<std::max(1, std::min(4096, (n + 255) / 256)), 256, 0, S->cs>>>(mask_d, n, shift, k,
-                                                                                                part_d);
+                k_split_bits<<<std::max(1, std::min(4096, (n + 255) / 256)), 256, 0, S->cs>>>(mask_d, words, n, shift,
+                                                                                                k, part_d);
                 count_launch();
                 rc = cuda_err(cudaGetLastError());
                 if (rc == SCC_OK)
@@ -391,7 +404,7 @@ void run_unit(scc_server* S) {
         for (auto it = S->admitted.begin(); it != S->admitted.end();) {
             Request& r = **it;
             const bool same = r.kind == 1 && r.graph == head->graph && r.dir == head->dir;
-            if (same && (u.empty() || (S->cfg.merge_reach && k + (int)r.src.size() <= 64))) {
+            if (same && (u.empty() || (S->cfg.merge_reach && k + (int)r.src.size() <= kMaxMergedSources))) {
                 k += (int)r.src.size();
                 u.push_back(*it);
                 it = S->admitted.erase(it);

@@ -479,7 +479,9 @@ int launch_row_nonself(const int32_t* off, const int32_t* selfrow, int32_t n, in
 }
 
 namespace {
-__global__ void k_mask_init(const int32_t* __restrict__ src, int32_t k, int32_t n, unsigned long long* mask, int* bad) {
+// bit j of vertex sources[j]'s mask (words 64-bit words per vertex)
+__global__ void k_mask_init(const int32_t* __restrict__ src, int32_t k, int32_t n, int words,
+                            unsigned long long* mask, int* bad) {
     int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= k) return;
     int v = src[j];
@@ -487,7 +489,7 @@ __global__ void k_mask_init(const int32_t* __restrict__ src, int32_t k, int32_t 
         atomicExch(bad, 1);
         return;
     }
-    atomicOr(&mask[v], 1ull << j);
+    atomicOr(&mask[(size_t)words * v + (j >> 6)], 1ull << (j & 63));
 }
 __global__ void k_filter_sources(const int32_t* __restrict__ in, int32_t k, int32_t n,
                                  const int32_t* __restrict__ label, int32_t* out, int* cnt, int* bad) {
@@ -502,9 +504,10 @@ __global__ void k_filter_sources(const int32_t* __restrict__ in, int32_t k, int3
 }
 }  // namespace
 
-int launch_mask_init(const int32_t* sources, int32_t k, int32_t n, unsigned long long* mask, int* bad,
+int launch_mask_init(const int32_t* sources, int32_t k, int32_t n, int words, unsigned long long* mask, int* bad,
                      cudaStream_t s) {
-    k_mask_init<<<1, 64, 0, s>>>(sources, k, n, mask, bad);
+    if (k < 1 || k > 64 * words) return SCC_ERR_INVALID_ARG;
+    k_mask_init<<<1, 64 * words, 0, s>>>(sources, k, n, words, mask, bad);
     SCC_LAUNCH();
     return SCC_OK;
 }

@@ -31,7 +31,7 @@ EXPORTED = [
     "scc_error_string", "scc_config_default", "scc_graph_create", "scc_graph_destroy", "scc_set_config",
     "scc_run", "reach_multi", "reach_multi_noalloc", "scc_get_stats",
     "scc_graph_info", "scc_debug_csr", "scc_debug_trim", "scc_debug_pivot_order", "scc_debug_single_reach",
-    "scc_debug_multi_reach", "scc_debug_hashbag", "scc_debug_pair_table", "scc_debug_launch_count",
+    "scc_debug_multi_reach", "scc_debug_reach_multi_wide", "scc_debug_hashbag", "scc_debug_pair_table", "scc_debug_launch_count",
     "scc_batch_config_default", "scc_batch_create", "scc_batch_destroy", "scc_batch_set_config",
     "scc_batch_get_config", "scc_batch_run", "scc_batch_autotune", "scc_batch_get_stats",
     "scc_debug_batch_times",
@@ -142,6 +142,7 @@ def load() -> ctypes.CDLL:
         "scc_debug_pivot_order": ([vp, vp, P(i32), vp], ctypes.c_int),
         "scc_debug_single_reach": ([vp, vp, i32, i32, vp, vp], ctypes.c_int),
         "scc_debug_multi_reach": ([vp, vp, vp, i32, i32, vp, i64, P(i64), i64, vp], ctypes.c_int),
+        "scc_debug_reach_multi_wide": ([vp, vp, i32, i32, vp, vp], ctypes.c_int),
         "scc_debug_hashbag": ([vp, i64, i32, i32, vp, P(i64), P(i32), vp], ctypes.c_int),
         "scc_debug_pair_table": ([vp, i64, i64, vp, P(i64), P(i32), vp], ctypes.c_int),
         "scc_debug_launch_count": ([], ctypes.c_int64),
@@ -461,6 +462,11 @@ def scc_debug_multi_reach(h, labels, sources, k: int, dir: int, pairs, cap: int,
     _check(load().scc_debug_multi_reach(h, _ptr(labels), _ptr(sources), k, dir, _ptr(pairs), cap,
                                         ctypes.byref(npairs), table_cap, _stream(stream)), "scc_debug_multi_reach")
     return npairs.value
+
+
+def scc_debug_reach_multi_wide(h, sources, k: int, dir: int, out, stream=None) -> None:
+    _check(load().scc_debug_reach_multi_wide(h, _ptr(sources), k, dir, _ptr(out), _stream(stream)),
+           "scc_debug_reach_multi_wide")
 
 
 def scc_debug_hashbag(items, count: int, lam: int, sigma: int, out, stream=None):

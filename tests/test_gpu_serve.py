@@ -37,7 +37,7 @@ def _requests(rng):
     for _ in range(24):
         gi = int(rng.integers(0, 2))
         n = _resident()[gi].n
-        k = int(rng.integers(1, 17))
+        k = int(rng.integers(1, 49))  # merged launches pass 64 sources (two mask words)
         reqs.append(("reach", gi, rng.integers(0, n, k).astype(np.int32), int(rng.integers(0, 2))))
     order = rng.permutation(len(reqs))
     return [reqs[i] for i in order]

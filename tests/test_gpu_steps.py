@@ -173,6 +173,38 @@ def test_reach_multi_masks(g):
             scc.reach_multi(G.h, np.zeros(65, np.int32), 65, 0, np.empty(g.n, np.uint64))
 
 
+@pytest.mark.parametrize("tau", [0, 1, 64])
+@pytest.mark.parametrize("g", list(_reach_cases()), ids=lambda g: g.name)
+def test_reach_multi_wide_masks(g, tau):
+    """Up to 128 sources in two mask words per vertex (the serving loop's merged
+    launches): each word equals the 64-source masks of its half of the sources."""
+    import torch
+    rng = np.random.default_rng(g.n + 5 + tau)
+    toff, tadj = oracle.transpose(g.n, g.offsets, g.targets)
+    with make_graph(g, config(tau=tau)) as G:
+        for k in (1, 65, 100, 128):
+            src = rng.integers(0, g.n, k).astype(np.int32)
+            if k > 64:
+                src[64] = src[0]  # one vertex in both words
+            for d in (0, 1):
+                o, a = (g.offsets, g.targets) if d == 0 else (toff, tadj)
+                want = np.zeros(2 * g.n, np.uint64)
+                want[0::2] = oracle.reach_mask(g.n, o, a, src[:64])
+                if k > 64:
+                    want[1::2] = oracle.reach_mask(g.n, o, a, src[64:])
+                out = np.empty(2 * g.n, np.uint64)
+                scc.scc_debug_reach_multi_wide(G.h, src, k, d, out)
+                assert np.array_equal(out, want), (k, d)
+                out_d = torch.empty(2 * g.n, dtype=torch.int64, device="cuda")
+                scc.scc_debug_reach_multi_wide(G.h, dev(src), k, d, out_d)
+                torch.cuda.synchronize()
+                assert np.array_equal(out_d.cpu().numpy().view(np.uint64), want), (k, d)
+        with pytest.raises(scc.SccError):
+            scc.scc_debug_reach_multi_wide(G.h, np.zeros(129, np.int32), 129, 0, np.empty(2 * g.n, np.uint64))
+        with pytest.raises(scc.SccError):
+            scc.scc_debug_reach_multi_wide(G.h, np.array([g.n], np.int32), 1, 0, np.empty(2 * g.n, np.uint64))
+
+
 def test_transpose_large_vertex_count_direct_path():
     """n above 2^26 takes the direct (global-atomic) transpose path."""
     import torch
