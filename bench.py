@@ -680,11 +680,12 @@ def main():
 
     # ---- roofline of the dominant kernel. Candidates, each timed live with CUDA
     # events on its launching stream inside the library, with its algorithmic
-    # bytes per launch (the data the algorithm must move, see DESIGN.md):
+    # bytes per launch (the data the algorithm must move):
     #   first-SCC engine (2 launches): 4 B arc target + 4 B visited word per arc
     #     examined, 8 B row offsets per item expanded;
     #   transpose rows pass: read the 2 B local target twice and the 4 B source
     #     once, write the source and the row offset: 12 B per arc + 4 B per vertex;
+    #   transpose split pass: read and write (u, local target): 12 B per arc;
     #   transpose partition pass: read the arc, write (u, local target): 10 B per
     #     arc + 4 B per vertex (row offsets of the tiles);
     #   intake pass (copy + range check + bucket histogram of the targets):
@@ -704,8 +705,10 @@ def main():
         "engine_kernel<PolSingle> (first-SCC VGC reachability)": (
             sum(s["ms_engine"] for s in stats), sum(s["engine_launches"] for s in stats),
             sum(8 * s["engine_arcs"] + 8 * s["engine_items"] for s in stats)),
-        "k_bucket_rows (transpose, per-bucket rows)": (
+        "k_sub_rows (transpose, per-sub-bucket rows)": (
             sum(s["ms_transpose_rows"] for s in stats), len(stats), len(stats) * (12 * mt + 4 * n)),
+        "k_bucket_split (transpose, buckets into sub-buckets)": (
+            sum(s["ms_transpose_split"] for s in stats), len(stats), len(stats) * (12 * mt)),
         "k_bucket_part (transpose, bucket partition)": (
             sum(s["ms_transpose_part"] for s in stats), len(stats), len(stats) * (10 * m + 4 * n)),
         "k_copy_check_hist (intake: copy, range check, bucket histogram)": (

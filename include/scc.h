@@ -196,8 +196,9 @@ typedef struct scc_stats {
     int64_t engine_inserted;   /* reachability pairs inserted by multi-reachability */
     /* graph construction (scc_graph_create of this handle), CUDA events on the
        creating stream: total; the intake pass (copy and range check of the
-       targets with the bucket histogram of the transpose); the two passes that
-       build the transpose (bucket partition, per-bucket rows) */
+       targets with the sub-bucket histogram of the transpose); the passes that
+       build the transpose: bucket partition, per-sub-bucket rows (and the split
+       of buckets into sub-buckets, ms_transpose_split below) */
     double ms_create, ms_transpose_hist, ms_transpose_part, ms_transpose_rows;
     /* trimming inside the classes left by the first SCC: vertices with no arc
        from or no arc to a vertex of their own class are singleton SCCs */
@@ -209,6 +210,7 @@ typedef struct scc_stats {
     int64_t multi_arcs;        /* arcs examined */
     int64_t multi_items;       /* items expanded */
     int32_t tau;               /* the VGC edge budget used (config tau, or the automatic one) */
+    double ms_transpose_split; /* transpose: buckets cut into sub-buckets (ms_transpose_rows: their rows) */
 } scc_stats;
 
 SCC_API int scc_get_stats(scc_handle h, scc_stats* out);

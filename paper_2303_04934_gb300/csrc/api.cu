@@ -53,7 +53,7 @@ struct scc_graph {
     int64_t tab_alloc[2] = {0, 0};
     EngineBuf eb32, eb64;
     scc_stats stats;
-    double create_ms[4] = {0, 0, 0, 0};  // total, histogram, partition, rows
+    double create_ms[5] = {0, 0, 0, 0, 0};  // total, histogram, partition, rows, split
 };
 
 namespace scc {
@@ -320,7 +320,7 @@ int scc_config_default(scc_config* cfg) {
 }
 
 struct CreateEvents {
-    cudaEvent_t e[8] = {};
+    cudaEvent_t e[10] = {};
     CreateEvents() {
         for (auto& x : e) cudaEventCreate(&x);
     }
@@ -367,12 +367,13 @@ static int graph_create_impl(scc_graph* h, int32_t n, int64_t m, const int32_t* 
     void* stmp = nullptr;
     SCC_TRY(dalloc_t(&bad, 1, s));
     SCC_TRY(dalloc_t(&selfrow, (size_t)n + 1, s));
-    SCC_TRY(dalloc_t(&bcnt, (size_t)nb + 2, s));  // [nb + 1]: self-loops found
-    SCC_TRY(dalloc_t(&btmp, 2 * (size_t)nb + 2, s));
+    const int nf = transpose_bins(n, shift);
+    SCC_TRY(dalloc_t(&bcnt, (size_t)nf + 2, s));  // [nf + 1]: self-loops found
+    SCC_TRY(dalloc_t(&btmp, 2 * ((size_t)nf + (size_t)nb) + 3, s));
     SCC_TRY(dalloc(&stmp, scan_tmp_bytes(n), s));
     SCC_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), s));
     SCC_CUDA(cudaMemsetAsync(selfrow, 0, sizeof(int32_t) * ((size_t)n + 1), s));
-    SCC_CUDA(cudaMemsetAsync(bcnt, 0, sizeof(unsigned long long) * ((size_t)nb + 2), s));
+    SCC_CUDA(cudaMemsetAsync(bcnt, 0, sizeof(unsigned long long) * ((size_t)nf + 2), s));
     // validation before any kernel indexes with these arrays: the offsets, then
     // the targets within the intake pass (copy, range check, bucket histogram)
     SCC_TRY(launch_validate_offsets(off_in, n, m, bad, s));
@@ -414,26 +415,30 @@ static int graph_create_impl(scc_graph* h, int32_t n, int64_t m, const int32_t* 
     h->toff = toff;
     SCC_TRY(dalloc_t(&h->tadj, (size_t)m, s));
     if (transpose_bucketed(shift)) {
-        int32_t *tmp_u = nullptr, *ord = nullptr;
-        uint16_t* tmp_lv = nullptr;
+        int32_t *tmp_u = nullptr, *tmp2_u = nullptr, *ord = nullptr, *tiles = nullptr;
+        uint16_t *tmp_lv = nullptr, *tmp2_lv = nullptr;
         int* terr = nullptr;
         SCC_TRY(dalloc_t(&tmp_u, (size_t)m + 8, s));
         SCC_TRY(dalloc_t(&tmp_lv, (size_t)m + 8, s));
-        SCC_TRY(dalloc_t(&ord, (size_t)nb, s));
+        SCC_TRY(dalloc_t(&tmp2_u, (size_t)m + 8, s));
+        SCC_TRY(dalloc_t(&tmp2_lv, (size_t)m + 8, s));
+        SCC_TRY(dalloc_t(&ord, (size_t)nf, s));
+        SCC_TRY(dalloc_t(&tiles, transpose_split_tiles(m, n, shift), s));
         SCC_TRY(dalloc_t(&terr, 1, s));
         SCC_CUDA(cudaMemsetAsync(terr, 0, sizeof(int), s));
         for (int attempt = 0;; ++attempt) {
             bool self_found = false;
-            SCC_TRY(launch_transpose(h->off, h->adj, trow, n, m_cur, m_cur, shift, bcnt, btmp, tmp_u, tmp_lv, ord, toff,
-                                     h->tadj, selfrow, bcnt + nb + 1, &self_found, terr, h->di.num_sms, s, &ce.e[3]));
+            SCC_TRY(launch_transpose(h->off, h->adj, trow, n, m_cur, m_cur, shift, bcnt, btmp, tmp_u, tmp_lv, tmp2_u,
+                                     tmp2_lv, ord, tiles, toff, h->tadj, selfrow, bcnt + nf + 1, &self_found, terr,
+                                     h->di.num_sms, s, &ce.e[3]));
             if (!self_found) break;
             if (attempt > 0) return SCC_ERR_INTERNAL;  // the rebuilt CSR has no self-loops
             // self-loops: rebuild the forward CSR without them and start over
             unsigned long long hself = 0;
-            SCC_CUDA(cudaMemcpyAsync(&hself, bcnt + nb + 1, sizeof(hself), cudaMemcpyDeviceToHost, s));
+            SCC_CUDA(cudaMemcpyAsync(&hself, bcnt + nf + 1, sizeof(hself), cudaMemcpyDeviceToHost, s));
             SCC_CUDA(cudaStreamSynchronize(s));
             SCC_TRY(drop_self_loops(hself));
-            SCC_CUDA(cudaMemsetAsync(bcnt, 0, sizeof(unsigned long long) * ((size_t)nb + 2), s));
+            SCC_CUDA(cudaMemsetAsync(bcnt, 0, sizeof(unsigned long long) * ((size_t)nf + 2), s));
             int* bad2 = nullptr;
             SCC_TRY(dalloc_t(&bad2, 1, s));
             SCC_TRY(launch_copy_check_hist(h->adj, h->adj, n, m_cur, shift, bcnt, bad2, h->di.num_sms, s));
@@ -444,15 +449,18 @@ static int graph_create_impl(scc_graph* h, int32_t n, int64_t m, const int32_t* 
         SCC_CUDA(cudaStreamSynchronize(s));
         dfree(tmp_u, s);
         dfree(tmp_lv, s);
+        dfree(tmp2_u, s);
+        dfree(tmp2_lv, s);
+        dfree(tiles, s);
         dfree(ord, s);
         dfree(terr, s);
         if (herr) return herr;
     } else {
         // self-loops from the row-aware histogram pass, then direct placement
-        SCC_CUDA(cudaMemsetAsync(bcnt, 0, sizeof(unsigned long long) * ((size_t)nb + 2), s));
-        SCC_TRY(launch_bucket_hist(h->off, h->adj, trow, n, m, shift, bcnt, selfrow, bcnt + nb + 1, h->di.num_sms, s));
+        SCC_CUDA(cudaMemsetAsync(bcnt, 0, sizeof(unsigned long long) * ((size_t)nf + 2), s));
+        SCC_TRY(launch_bucket_hist(h->off, h->adj, trow, n, m, shift, bcnt, selfrow, bcnt + nf + 1, h->di.num_sms, s));
         unsigned long long hself = 0;
-        SCC_CUDA(cudaMemcpyAsync(&hself, bcnt + nb + 1, sizeof(hself), cudaMemcpyDeviceToHost, s));
+        SCC_CUDA(cudaMemcpyAsync(&hself, bcnt + nf + 1, sizeof(hself), cudaMemcpyDeviceToHost, s));
         SCC_CUDA(cudaStreamSynchronize(s));
         if (hself > 0) SCC_TRY(drop_self_loops(hself));
         int32_t* indeg = nullptr;
@@ -465,13 +473,14 @@ static int graph_create_impl(scc_graph* h, int32_t n, int64_t m, const int32_t* 
     dfree(bcnt, s);
     dfree(btmp, s);
     dfree(stmp, s);
-    cudaEventRecord(ce.e[7], s);
+    cudaEventRecord(ce.e[9], s);
     SCC_CUDA(cudaStreamSynchronize(s));
-    h->create_ms[0] = ce.ms(0, 7);
+    h->create_ms[0] = ce.ms(0, 9);
     h->create_ms[1] = ce.ms(1, 2);
     if (transpose_bucketed(shift) && h->mt > 0) {
         h->create_ms[2] = ce.ms(3, 4);
-        h->create_ms[3] = ce.ms(5, 6);
+        h->create_ms[4] = ce.ms(5, 6);
+        h->create_ms[3] = ce.ms(7, 8);
     }
     return SCC_OK;
 }
@@ -551,6 +560,7 @@ int scc_get_stats(scc_handle h, scc_stats* out) {
     out->ms_transpose_hist = h->create_ms[1];
     out->ms_transpose_part = h->create_ms[2];
     out->ms_transpose_rows = h->create_ms[3];
+    out->ms_transpose_split = h->create_ms[4];
     return SCC_OK;
 }
 

@@ -61,28 +61,34 @@ int bucket_shift(int32_t n);
 // table has tile_rows_count(m) entries and drives the arc passes below.
 size_t tile_rows_count(int64_t m);
 int launch_tile_rows(const int32_t* off, int32_t n, int64_t m, int32_t* trow, cudaStream_t s);
+// Sub-bucket bins of the histogram (at most 16384): the transpose's finest
+// level, up to 32 per bucket.
+int transpose_bins(int32_t n, int shift);
 // Intake of the target array: dst = src (no copy when equal), targets outside
-// [0, n) set *bad, bucket_cnt[b] += arcs into bucket b (self-loops included).
+// [0, n) set *bad, bucket_cnt[f] += arcs into sub-bucket f (transpose_bins
+// bins; self-loops included).
 int launch_copy_check_hist(const int32_t* src, int32_t* dst, int32_t n, int64_t m, int shift,
                            unsigned long long* bucket_cnt, int* bad, int num_sms, cudaStream_t s);
 // bucket_cnt[b] += non-self arcs into bucket b; selfrow[u] += self-loops of u.
 int launch_bucket_hist(const int32_t* off, const int32_t* adj, const int32_t* trow, int32_t n, int64_t m, int shift,
                        unsigned long long* bucket_cnt, int32_t* selfrow, unsigned long long* nself, int num_sms,
                        cudaStream_t s);
-// G^T of the CSR (off, adj) with m arcs, by the two-level bucketed counting
+// G^T of the CSR (off, adj) with m arcs, by the three-level bucketed counting
 // sort (when transpose_bucketed(shift)); bucket_cnt from launch_copy_check_hist.
-// bucket_tmp: 2 * nbuckets + 2 words; tmp_u: m + 8 entries, tmp_lv: m + 8
-// entries (the padding is read, never used); order_tmp: nbuckets.
+// bucket_tmp: 2 * (transpose_bins + nbuckets) + 3 words; tmp_u, tmp2_u: m + 8
+// entries, tmp_lv, tmp2_lv: m + 8 entries (the padding is read, never used);
+// order_tmp: transpose_bins entries; tile_tmp: transpose_split_tiles entries.
+size_t transpose_split_tiles(int64_t m, int32_t n, int shift);
 // If the CSR has self-loops, nothing is written to toff/tadj: *self_found is
 // set, selfrow[u] (zeroed by the caller) counts u's self-loops and *nself
 // (zeroed by the caller) their total.
 bool transpose_bucketed(int shift);
 int launch_transpose(const int32_t* off, const int32_t* adj, const int32_t* trow, int32_t n, int64_t m, int64_t mt,
-                     int shift,
-                     const unsigned long long* bucket_cnt, unsigned long long* bucket_tmp, int32_t* tmp_u,
-                     uint16_t* tmp_lv, int32_t* order_tmp, int32_t* toff, int32_t* tadj, int32_t* selfrow,
-                     unsigned long long* nself, bool* self_found, int* err, int num_sms, cudaStream_t s,
-                     cudaEvent_t* ev = nullptr);  // ev[0..3]: around the partition and the rows pass
+                     int shift, const unsigned long long* bucket_cnt, unsigned long long* bucket_tmp, int32_t* tmp_u,
+                     uint16_t* tmp_lv, int32_t* tmp2_u, uint16_t* tmp2_lv, int32_t* order_tmp, int32_t* tile_tmp,
+                     int32_t* toff, int32_t* tadj, int32_t* selfrow, unsigned long long* nself, bool* self_found,
+                     int* err, int num_sms, cudaStream_t s,
+                     cudaEvent_t* ev = nullptr);  // ev[0..5]: around the partition, split and rows passes
 // Direct G^T for very large n: global atomics. indeg: n + 1.
 int launch_transpose_direct(const int32_t* off, const int32_t* adj, const int32_t* trow, int32_t n, int64_t m,
                             int32_t* indeg, void* scan_tmp, int32_t* toff, int32_t* tadj, int num_sms,

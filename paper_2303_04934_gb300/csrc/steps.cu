@@ -182,14 +182,33 @@ __global__ void k_trim(const int32_t* __restrict__ off, const int32_t* __restric
         flags[v] = (off[v + 1] == off[v]) || (toff[v + 1] == toff[v]);
 }
 
+// Four consecutive vertices per thread (16-byte loads and stores; the arrays
+// are 16-byte aligned), the last partial group one by one.
 __global__ void k_init_labels(const int32_t* __restrict__ off, const int32_t* __restrict__ toff, int32_t n,
                               int32_t* label, int32_t* rep, unsigned long long* nact) {
     unsigned long long c = 0;
-    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
-        bool tr = (off[v + 1] == off[v]) || (toff[v + 1] == toff[v]);
-        label[v] = tr ? kDone : 0;
-        rep[v] = tr ? (int32_t)v : -1;
-        c += !tr;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; 4 * i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t v0 = 4 * i;
+        if (v0 + 4 <= n) {
+            const int4 a = __ldg(reinterpret_cast<const int4*>(off + v0));
+            const int4 b = __ldg(reinterpret_cast<const int4*>(toff + v0));
+            const int a4 = __ldg(off + v0 + 4), b4 = __ldg(toff + v0 + 4);
+            const bool t0 = a.y == a.x || b.y == b.x, t1 = a.z == a.y || b.z == b.y;
+            const bool t2 = a.w == a.z || b.w == b.z, t3 = a4 == a.w || b4 == b.w;
+            *reinterpret_cast<int4*>(label + v0) = make_int4(t0 ? kDone : 0, t1 ? kDone : 0, t2 ? kDone : 0,
+                                                             t3 ? kDone : 0);
+            const int u = (int)v0;
+            *reinterpret_cast<int4*>(rep + v0) = make_int4(t0 ? u : -1, t1 ? u + 1 : -1, t2 ? u + 2 : -1,
+                                                           t3 ? u + 3 : -1);
+            c += (unsigned long long)(!t0 + !t1 + !t2 + !t3);
+        } else {
+            for (int64_t v = v0; v < n; ++v) {
+                const bool tr = (off[v + 1] == off[v]) || (toff[v + 1] == toff[v]);
+                label[v] = tr ? kDone : 0;
+                rep[v] = tr ? (int32_t)v : -1;
+                c += !tr;
+            }
+        }
     }
     for (int d = 16; d >= 1; d >>= 1) c += __shfl_xor_sync(kFull, c, d);
     if (lane_id() == 0 && c) atomicAdd(nact, c);
@@ -351,18 +370,32 @@ __global__ void k_class_trim(const int32_t* __restrict__ act, int64_t N, const i
     if (lane_id() == 0 && c) atomicAdd(ndone, c);
 }
 
+// Four consecutive vertices per thread (one 16-byte label load; their bits
+// share a bitmap word).
 __global__ void k_label_first(const uint32_t* __restrict__ bf, const uint32_t* __restrict__ bb, int32_t n, int32_t s,
                               int32_t L, int32_t* label, int32_t* rep, unsigned long long* ndone) {
     unsigned long long c = 0;
-    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
-        if (label[v] != L) continue;
-        bool f = (bf[v >> 5] >> (v & 31)) & 1u, b = (bb[v >> 5] >> (v & 31)) & 1u;
+    auto one = [&](int64_t v, int lv, uint32_t wf, uint32_t wb) -> int {
+        if (lv != L) return lv;
+        const bool f = (wf >> (v & 31)) & 1u, b = (wb >> (v & 31)) & 1u;
         if (f && b) {
-            label[v] = kDone;
             rep[v] = s;
             ++c;
-        } else if (f || b) {
-            label[v] = class_hash(L, f ? s : -1, b ? s : -1);
+            return kDone;
+        }
+        return (f || b) ? class_hash(L, f ? s : -1, b ? s : -1) : lv;
+    };
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; 4 * i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t v0 = 4 * i;
+        if (v0 + 4 <= n) {
+            const int4 lab = *reinterpret_cast<const int4*>(label + v0);
+            if (lab.x != L && lab.y != L && lab.z != L && lab.w != L) continue;
+            const uint32_t wf = __ldg(&bf[v0 >> 5]), wb = __ldg(&bb[v0 >> 5]);
+            const int4 o = make_int4(one(v0, lab.x, wf, wb), one(v0 + 1, lab.y, wf, wb), one(v0 + 2, lab.z, wf, wb),
+                                     one(v0 + 3, lab.w, wf, wb));
+            *reinterpret_cast<int4*>(label + v0) = o;
+        } else {
+            for (int64_t v = v0; v < n; ++v) label[v] = one(v, label[v], bf[v >> 5], bb[v >> 5]);
         }
     }
     for (int d = 16; d >= 1; d >>= 1) c += __shfl_xor_sync(kFull, c, d);
@@ -370,9 +403,22 @@ __global__ void k_label_first(const uint32_t* __restrict__ bf, const uint32_t* _
 }
 
 // ---------------------------------------------------------- canonicalise --
-__global__ void k_fill_i32(int32_t* p, int64_t n, int32_t v) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        p[i] = v;
+// minid[v] = v where v is its own representative (every trimmed singleton, and
+// the representative of each larger SCC), INT_MAX elsewhere: the pass below
+// then needs no atomic for a vertex with rep[v] = v. Four vertices per thread.
+__global__ void k_minid_init(const int32_t* __restrict__ rep, int32_t n, int32_t* minid) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; 4 * i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t v0 = 4 * i;
+        if (v0 + 4 <= n) {
+            const int4 r = __ldg(reinterpret_cast<const int4*>(rep + v0));
+            const int u = (int)v0;
+            *reinterpret_cast<int4*>(minid + v0) = make_int4(r.x == u ? u : INT_MAX, r.y == u + 1 ? u + 1 : INT_MAX,
+                                                             r.z == u + 2 ? u + 2 : INT_MAX,
+                                                             r.w == u + 3 ? u + 3 : INT_MAX);
+        } else {
+            for (int64_t v = v0; v < n; ++v) minid[v] = rep[v] == (int32_t)v ? (int32_t)v : INT_MAX;
+        }
+    }
 }
 // minid[rep[v]] = min v. Lanes of a warp hold consecutive v, so among lanes with
 // the same rep the lowest lane has the smallest v: one atomic per group, and
@@ -388,28 +434,51 @@ __global__ void k_min_of_rep(const int32_t* __restrict__ rep, int32_t n, int32_t
         int r = v < n ? rep[v] : -1;
         bool ok = r >= 0 && r < n;
         if (v < n && !ok) atomicExch(bad, 1);
+        ok = ok && r != (int)v;  // minid[v] = v already (k_minid_init)
         int key = ok ? r : -1;
-        // a warp inside one SCC (the common case on a large SCC) needs no match
-        const int key0 = __shfl_sync(kFull, key, 0);
-        const uint32_t peers = __all_sync(kFull, key == key0) ? kFull : __match_any_sync(kFull, key);
-        if (ok && lane_id() == __ffs(peers) - 1 && r != last) {
+        // lanes whose reps are all one SCC's (the common case: a large SCC
+        // among singletons) need no match: their first lane has the smallest v
+        const uint32_t okm = __ballot_sync(kFull, ok);
+        if (okm == 0) continue;
+        const int key0 = __shfl_sync(kFull, key, __ffs(okm) - 1);
+        const uint32_t peers = __ballot_sync(kFull, ok && key != key0) == 0 ? okm : __match_any_sync(kFull, key);
+        if (ok && lane_id() == __ffs(peers & okm) - 1 && r != last) {
             last = r;
             if (ld_volatile(&minid[r]) > (int32_t)v) atomicMin(&minid[r], (int32_t)v);
         }
     }
 }
 // out[v] = minid[rep[v]], the last rep looked up kept per thread (a large SCC
-// is then one read per thread).
+// is then one read per thread). Four vertices per thread; out may be any
+// device buffer, so the 16-byte stores are used only when it is aligned.
 __global__ void k_write_labels(const int32_t* __restrict__ rep, int32_t n, const int32_t* __restrict__ minid,
                                int32_t* out) {
     int ck = -1, cv = -1;
-    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
-        const int r = __ldg(&rep[v]);
-        if (r != ck && r >= 0 && r < n) {
+    auto look = [&](int r) {
+        if (r < 0 || r >= n) return -1;
+        if (r != ck) {
             ck = r;
             cv = __ldg(&minid[r]);
         }
-        out[v] = (r >= 0 && r < n) ? cv : -1;
+        return cv;
+    };
+    const bool vec = ((uintptr_t)out & 15) == 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; 4 * i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t v0 = 4 * i;
+        if (v0 + 4 <= n) {
+            const int4 r = __ldg(reinterpret_cast<const int4*>(rep + v0));
+            const int4 o = make_int4(look(r.x), look(r.y), look(r.z), look(r.w));
+            if (vec) {
+                *reinterpret_cast<int4*>(out + v0) = o;
+            } else {
+                out[v0] = o.x;
+                out[v0 + 1] = o.y;
+                out[v0 + 2] = o.z;
+                out[v0 + 3] = o.w;
+            }
+        } else {
+            for (int64_t v = v0; v < n; ++v) out[v] = look(rep[v]);
+        }
     }
 }
 
@@ -529,7 +598,7 @@ int launch_trim(const int32_t* off, const int32_t* toff, int32_t n, uint8_t* fla
 int launch_init_labels(const int32_t* off, const int32_t* toff, int32_t n, int32_t* label, int32_t* rep,
                        unsigned long long* nact, cudaStream_t s) {
     if (n == 0) return SCC_OK;
-    k_init_labels<<<grid_for(n, kBlk), kBlk, 0, s>>>(off, toff, n, label, rep, nact);
+    k_init_labels<<<grid_for(ceil_div((int64_t)n, 4), kBlk), kBlk, 0, s>>>(off, toff, n, label, rep, nact);
     SCC_LAUNCH();
     return SCC_OK;
 }
@@ -615,7 +684,7 @@ int launch_label_first(const uint32_t* bf, const uint32_t* bb, int32_t n, int32_
                        unsigned long long* ndone, cudaStream_t st) {
     if (n == 0) return SCC_OK;
     // the class of the pivot is 0 in the first round (every untrimmed vertex)
-    k_label_first<<<grid_for(n, kBlk), kBlk, 0, st>>>(bf, bb, n, s, 0, label, rep, ndone);
+    k_label_first<<<grid_for(ceil_div((int64_t)n, 4), kBlk), kBlk, 0, st>>>(bf, bb, n, s, 0, label, rep, ndone);
     SCC_LAUNCH();
     return SCC_OK;
 }
@@ -623,11 +692,11 @@ int launch_label_first(const uint32_t* bf, const uint32_t* bb, int32_t n, int32_
 int launch_canonicalize(const int32_t* rep, int32_t n, int32_t* minid, int32_t* labels_out, int* bad,
                         cudaStream_t s) {
     if (n == 0) return SCC_OK;
-    k_fill_i32<<<grid_for(n, kBlk), kBlk, 0, s>>>(minid, n, INT_MAX);
+    k_minid_init<<<grid_for(ceil_div((int64_t)n, 4), kBlk), kBlk, 0, s>>>(rep, n, minid);
     SCC_LAUNCH();
     k_min_of_rep<<<grid_for(n, kBlk), kBlk, 0, s>>>(rep, n, minid, bad);
     SCC_LAUNCH();
-    k_write_labels<<<grid_for(n, kBlk), kBlk, 0, s>>>(rep, n, minid, labels_out);
+    k_write_labels<<<grid_for(ceil_div((int64_t)n, 4), kBlk), kBlk, 0, s>>>(rep, n, minid, labels_out);
     SCC_LAUNCH();
     return SCC_OK;
 }

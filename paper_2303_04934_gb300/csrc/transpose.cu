@@ -2,25 +2,33 @@
 //
 // Every non-self arc (u, v) of G becomes the entry u of row v of G^T (Sec. 2: a
 // backward reachability search is a forward search on G^T). This is a counting
-// sort of the arcs by target, done in two levels so that every per-arc atomic is
-// a shared-memory atomic:
+// sort of the arcs by target in three levels, so that every per-arc atomic is a
+// shared-memory atomic and every pass writes in runs:
 //
 //   A. coarse partition by bucket b = v >> shift (at most 512 buckets):
-//      A1 histogram of buckets (per-block shared histogram, one global add per
-//         block and bucket), fused with the copy and range check of the
-//         targets: it needs no arc sources, so it reads the targets once as a
-//         flat array;
+//      A1 histogram of sub-buckets (2^sb vertices, up to 32 per bucket;
+//         per-block shared histogram, one global add per block and bin), fused
+//         with the copy and range check of the targets: it needs no arc
+//         sources, so it reads the targets once as a flat array. One scan
+//         gives the start of every sub-bucket's rows in G^T; a bucket's run
+//         starts where its first sub-bucket's rows start.
 //      A2 partition: a block takes a tile of 8k arcs, counting-sorts it by
 //         bucket in shared memory, reserves one run per non-empty bucket with a
 //         global atomicAdd, and writes the sorted tile out, so consecutive lanes
 //         store consecutive positions of a run.
 //      Each arc is written as its source u (4 B) and its target's offset within
 //      the bucket (2 B: buckets hold at most 2^15 vertices).
-//   B. one block per bucket (largest buckets first): per-vertex counts of the
-//      bucket in shared memory, their scan gives the bucket's rows of G^T
-//      (offsets written directly: the bucket's first row starts at the bucket's
-//      start), then the arcs are placed with shared-memory cursors. The rows a
-//      block writes span one bucket, so partial-sector writes merge in L2.
+//   B. split: one block per bucket cuts its run into the runs of its
+//      sub-buckets (tiles counting-sorted in shared memory by a warp
+//      multi-split, written out through per-sub-bucket cursors the block owns).
+//   C. rows: one block per sub-bucket (those with more arcs than the window
+//      first): per-vertex counts in shared memory, their scan gives the rows
+//      of G^T, then each arc's source is placed in a shared-memory copy of the
+//      sub-bucket's rows, which is written out in order. A sub-bucket with more
+//      arcs than the window places its arcs directly; its rows span only it.
+//   Placing arcs straight into a bucket's rows instead (2 MB of rows per block,
+//   about 300 MB in flight over the GPU, far more than L2) cost more than the
+//   split pass: the scattered 4-byte stores left L2 before their sectors filled.
 //
 // Rows of each arc tile are found by one binary search per thread followed by a
 // forward walk over the tile's row offsets staged in shared memory.
@@ -36,13 +44,19 @@ namespace scc {
 namespace {
 
 constexpr int kMaxBuckets = 512;
-constexpr int kBucketLog = 15;          // at most 2^15 vertices per bucket (128 KB of shared counters)
+constexpr int kBucketLog = 15;          // at most 2^15 vertices per bucket (16-bit offsets within it)
+constexpr int kSubLog = 5;              // at most 2^5 sub-buckets per bucket
+constexpr int kMaxSubVertsLog = 10;     // at most 2^10 vertices per sub-bucket
+constexpr int kMaxBins = kMaxBuckets << kSubLog;  // 16384 sub-buckets
 constexpr int kBlkA = 512;
 static_assert(kMaxBuckets <= kBlkA, "bucket scan uses one thread per bucket");
 constexpr int kChunk = 16;              // consecutive arcs per thread per step
 constexpr int kStep = kBlkA * kChunk;   // arcs per block step (8192) = partition tile
 constexpr int kRowsCap = 4096;          // row offsets of one step staged in shared memory
-constexpr int kBlkB = 1024;
+constexpr int kBlkS = 1024;                    // split pass
+constexpr int kSplitTile = kBlkS * 8;           // arcs per split tile
+constexpr int kBlkR = 512;                      // rows pass
+constexpr int kWinArcs = 16384;                 // rows staged in shared memory (64 KB)
 
 // Largest r in [lo, hi] with off[r] <= e.
 __device__ __forceinline__ int row_search_g(const int32_t* __restrict__ off, int lo, int hi, int64_t e) {
@@ -127,7 +141,7 @@ __device__ __forceinline__ void for_step_arcs(const int32_t* __restrict__ off, c
 __global__ void __launch_bounds__(kBlkA) k_copy_check_hist(const int32_t* __restrict__ src, int32_t* __restrict__ dst,
                                                            int64_t m, int32_t n, int shift, int nb,
                                                            unsigned long long* bucket_cnt, int* bad) {
-    __shared__ unsigned int s_hist[kMaxBuckets];
+    extern __shared__ unsigned int s_hist[];  // nb bins
     for (int i = threadIdx.x; i < nb; i += blockDim.x) s_hist[i] = 0;
     __syncthreads();
     const bool copy = src != dst;
@@ -200,20 +214,89 @@ __global__ void __launch_bounds__(kBlkA) k_bucket_hist(const int32_t* __restrict
     if (my_self) atomicAdd(nself, my_self);
 }
 
-// exclusive scan of the bucket counts (one block, sequential: nb <= 2048);
-// also zeroes the work counter of the rows pass
-__global__ void k_bucket_scan(const unsigned long long* cnt, int nb, unsigned long long* start,
-                              unsigned long long* cursor, unsigned int* rows_next) {
-    if (threadIdx.x == 0) {
-        unsigned long long s = 0;
-        for (int i = 0; i < nb; ++i) {
-            start[i] = s;
-            cursor[i] = s;
-            s += cnt[i];
-        }
-        start[nb] = s;
-        *rows_next = 0;
+// Block-wide exclusive scan (blockDim.x a multiple of 32, <= 1024); *total
+// gets the sum. Every thread must call it.
+__device__ __forceinline__ unsigned long long block_scan_u64(unsigned long long x, unsigned long long* s_w,
+                                                             unsigned long long* total) {
+    unsigned long long incl = x;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const unsigned long long y = __shfl_up_sync(kFull, incl, d);
+        if (lane_id() >= d) incl += y;
     }
+    if (lane_id() == 31) s_w[threadIdx.x >> 5] = incl;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        const int nw = (int)(blockDim.x >> 5);
+        unsigned long long w = threadIdx.x < nw ? s_w[threadIdx.x] : 0ull;
+        unsigned long long wi = w;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const unsigned long long y = __shfl_up_sync(kFull, wi, d);
+            if (lane_id() >= d) wi += y;
+        }
+        if (threadIdx.x < nw) s_w[threadIdx.x] = wi - w;
+        if (threadIdx.x == 31) *total = wi;
+    }
+    __syncthreads();
+    const unsigned long long r = s_w[threadIdx.x >> 5] + incl - x;
+    __syncthreads();
+    return r;
+}
+
+// One block of 1024 threads over the nf sub-bucket counts: start[0 .. nf]
+// (exclusive scan) and gcur = start (the split pass's cursors), cursor[b] =
+// start[b << sublog] (bucket b's partition run), order = the sub-buckets with
+// more than kWinArcs arcs, then the others (each group increasing), the split
+// pass's tiles (bucket b's run, from its first multiple of 8, in tiles of
+// kSplitTile arcs: tile_base[b] = its first tile, tile_bucket[t] = the bucket of
+// tile t), counters[0] = 0 (work counter of the rows pass).
+__global__ void __launch_bounds__(1024) k_fine_scan(const unsigned long long* __restrict__ cnt, int nf, int sublog,
+                                                   int nb, unsigned long long* start, unsigned long long* gcur,
+                                                   unsigned long long* cursor, int32_t* order,
+                                                   unsigned long long* tile_base, int32_t* tile_bucket,
+                                                   unsigned int* counters) {
+    __shared__ unsigned long long s_w[32];
+    __shared__ unsigned long long s_tot, s_hot;
+    const int per = (nf + (int)blockDim.x - 1) / (int)blockDim.x;
+    const int i0 = min((int)threadIdx.x * per, nf), i1 = min(i0 + per, nf);
+    unsigned long long sum = 0, hot = 0;
+    for (int i = i0; i < i1; ++i) {
+        sum += cnt[i];
+        hot += cnt[i] > (unsigned long long)kWinArcs;
+    }
+    unsigned long long run = block_scan_u64(sum, s_w, &s_tot);
+    const unsigned long long hbase = block_scan_u64(hot, s_w, &s_hot);
+    const unsigned long long nhot = s_hot;
+    unsigned long long h = hbase, c = nhot + ((unsigned long long)i0 - hbase);
+    for (int i = i0; i < i1; ++i) {
+        start[i] = run;
+        gcur[i] = run;
+        run += cnt[i];
+        if (cnt[i] > (unsigned long long)kWinArcs) order[h++] = i;
+        else order[c++] = i;
+    }
+    if (threadIdx.x == 0) {
+        start[nf] = s_tot;
+        counters[0] = 0;
+    }
+    __syncthreads();
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) cursor[b] = start[(size_t)b << sublog];
+    // split tiles per bucket (nb <= 1024: one bucket per thread)
+    unsigned long long nt = 0;
+    const int b = threadIdx.x;
+    if (b < nb) {
+        const long long r0 = (long long)start[(size_t)b << sublog], r1 = (long long)start[(size_t)(b + 1) << sublog];
+        nt = r1 > r0 ? (unsigned long long)(((r1 - (r0 & ~7ll)) + kSplitTile - 1) / kSplitTile) : 0ull;
+    }
+    unsigned long long ntot;
+    const unsigned long long tb = block_scan_u64(nt, s_w, &s_tot);
+    ntot = s_tot;
+    if (b < nb) {
+        tile_base[b] = tb;
+        for (unsigned long long t = 0; t < nt; ++t) tile_bucket[tb + t] = b;
+    }
+    if (threadIdx.x == 0) tile_base[nb] = ntot;
 }
 
 // A2. partition: per 8k-arc tile, a shared-memory counting sort by bucket,
@@ -268,21 +351,22 @@ __global__ void __launch_bounds__(kBlkA) k_bucket_part(const int32_t* __restrict
                 if (i == 31) s_total = y;
             }
             __syncthreads();
-            if (i < nb) {
-                s_start[i] = s_wsum[i >> 5] + incl - c;
-                s_gbase[i] = c ? atomicAdd(&cursor[i], (unsigned long long)c) : 0ull;
-            }
+            if (i < nb) s_start[i] = s_wsum[i >> 5] + incl - c;
+            __syncthreads();
+            // reserve the tile's run in each bucket; the atomics' latency
+            // overlaps the staging below
+            const unsigned long long g = (i < nb && c) ? atomicAdd(&cursor[i], (unsigned long long)c) : 0ull;
+            // stage the tile sorted by bucket
+#pragma unroll
+            for (int q = 0; q < kChunk; ++q)
+                if (vv[q] >= 0) {
+                    const unsigned int j = s_start[vv[q] >> shift] + rk[q];
+                    s_u[j] = uu[q];
+                    s_v[j] = vv[q];
+                }
+            if (i < nb) s_gbase[i] = g;
             __syncthreads();
         }
-        // stage the tile sorted by bucket
-#pragma unroll
-        for (int q = 0; q < kChunk; ++q)
-            if (vv[q] >= 0) {
-                const unsigned int j = s_start[vv[q] >> shift] + rk[q];
-                s_u[j] = uu[q];
-                s_v[j] = vv[q];
-            }
-        __syncthreads();
         const unsigned int total = s_total;
         for (unsigned int j = threadIdx.x; j < total; j += blockDim.x) {
             const int v = s_v[j];
@@ -299,13 +383,6 @@ __global__ void __launch_bounds__(kBlkA) k_bucket_part(const int32_t* __restrict
     }
 }
 
-// B. one block per bucket: per-vertex counts in shared memory, row offsets of
-// G^T for the bucket's vertices, placement with shared cursors. The grid is
-// persistent (the resident blocks); each block takes the next bucket of the
-// largest-first order from a global counter when it is done with one. The arcs are
-// read in aligned chunks of 8 (one 16-byte load of local targets, two of
-// sources), two chunks per thread per step; the arrays are padded by 8 entries
-// so the last chunk may read past the last arc.
 __device__ __forceinline__ void unpack8(const uint4 r, unsigned int (&lv)[8]) {
     lv[0] = r.x & 0xffffu;
     lv[1] = r.x >> 16;
@@ -316,59 +393,162 @@ __device__ __forceinline__ void unpack8(const uint4 r, unsigned int (&lv)[8]) {
     lv[6] = r.w & 0xffffu;
     lv[7] = r.w >> 16;
 }
-// Counter i of a bucket lives at i + i / 32 in shared memory: the scan below
-// gives each thread a run of consecutive counters, and with one padding word
-// per 32 the lanes of a warp reading the j-th counter of their runs hit 32
-// different banks (without it they would all hit one).
-__device__ __forceinline__ int cpad(int i) { return i + (i >> 5); }
 
-__global__ void __launch_bounds__(kBlkB) k_bucket_rows(const int32_t* __restrict__ uu, const uint16_t* __restrict__ lvv,
-                                                       const unsigned long long* __restrict__ start,
-                                                       const int32_t* __restrict__ order, int nb, int shift,
-                                                       int32_t n, int32_t* toff, int32_t* tadj,
-                                                       unsigned int* rows_next, int* err) {
-    extern __shared__ int s_cnt[];  // 2^shift counters, padded (cpad)
-    __shared__ int s_wsum[kBlkB / 32];
+// B. split over tiles: tile t of bucket b = tile_bucket[t] covers kSplitTile
+// arcs of the bucket's run from its first multiple of 8 (8 per thread; the
+// arrays are padded by 8 entries), blocks take tiles in a grid-stride loop and
+// load the next tile while they work on this one. A tile's arcs are counted
+// per sub-bucket in shared memory (the count is the arc's rank); one global
+// atomicAdd per non-empty sub-bucket reserves the tile's run in it; the tile is
+// staged in sub-bucket order and written out, consecutive lanes to consecutive
+// positions. The target is kept as its offset within the sub-bucket.
+struct SplitLoad {
+    uint4 lv;
+    int4 ua, ub;
+    long long c, r0, r1;
+    int b;
+};
+__device__ __forceinline__ SplitLoad split_load(const int32_t* __restrict__ uu, const uint16_t* __restrict__ lvv,
+                                                const unsigned long long* __restrict__ start,
+                                                const unsigned long long* __restrict__ tile_base,
+                                                const int32_t* __restrict__ tile_bucket, int sublog, long long t) {
+    SplitLoad L;
+    L.b = __ldg(&tile_bucket[t]);
+    L.r0 = (long long)__ldg(&start[(size_t)L.b << sublog]);
+    L.r1 = (long long)__ldg(&start[(size_t)(L.b + 1) << sublog]);
+    L.c = (L.r0 & ~7ll) + ((long long)t - (long long)__ldg(&tile_base[L.b])) * kSplitTile + 8ll * threadIdx.x;
+    const bool in = L.c < L.r1;
+    L.lv = in ? __ldg(reinterpret_cast<const uint4*>(lvv + L.c)) : make_uint4(0, 0, 0, 0);
+    L.ua = in ? __ldg(reinterpret_cast<const int4*>(uu + L.c)) : make_int4(0, 0, 0, 0);
+    L.ub = in ? __ldg(reinterpret_cast<const int4*>(uu + L.c + 4)) : make_int4(0, 0, 0, 0);
+    return L;
+}
+
+__global__ void __launch_bounds__(kBlkS, 1) k_bucket_split(const int32_t* __restrict__ uu,
+                                                           const uint16_t* __restrict__ lvv,
+                                                           const unsigned long long* __restrict__ start,
+                                                           const unsigned long long* __restrict__ tile_base,
+                                                           const int32_t* __restrict__ tile_bucket, long long ntiles,
+                                                           int sublog, int sb, unsigned long long* gcur, int32_t* u2,
+                                                           uint16_t* lv2, int* err) {
+    __shared__ unsigned int s_tcnt[1 << kSubLog];
+    __shared__ unsigned int s_tstart[1 << kSubLog];
+    __shared__ unsigned long long s_gb[1 << kSubLog];
+    extern __shared__ int32_t s_u[];                                // [kSplitTile]
+    uint16_t* s_lv = reinterpret_cast<uint16_t*>(s_u + kSplitTile);  // [kSplitTile]
+    const int S = 1 << sublog;
+    const unsigned int lmask = (1u << sb) - 1u;
+    long long t = blockIdx.x;
+    if (t >= ntiles) return;
+    SplitLoad cur = split_load(uu, lvv, start, tile_base, tile_bucket, sublog, t);
+    for (; t < ntiles; t += gridDim.x) {
+        const long long tn = t + gridDim.x;
+        SplitLoad nxt;
+        if (tn < ntiles) nxt = split_load(uu, lvv, start, tile_base, tile_bucket, sublog, tn);
+        if (threadIdx.x < (unsigned)S) s_tcnt[threadIdx.x] = 0;
+        __syncthreads();
+        const size_t f0 = (size_t)cur.b << sublog;
+        unsigned int lv[8];
+        unpack8(cur.lv, lv);
+        unsigned int rk[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const bool valid = cur.c + j >= cur.r0 && cur.c + j < cur.r1;
+            const unsigned int sub = lv[j] >> sb;
+            rk[j] = ~0u;
+            if (valid) {
+                if (sub < (unsigned)S) rk[j] = atomicAdd(&s_tcnt[sub], 1u);
+                else atomicExch(err, SCC_ERR_INTERNAL);
+            }
+        }
+        __syncthreads();
+        unsigned int x = 0;
+        if (threadIdx.x < 32) {  // scan of the tile's sub-bucket counts
+            x = threadIdx.x < (unsigned)S ? s_tcnt[threadIdx.x] : 0u;
+            const unsigned int y = (unsigned int)warp_incl_scan((int)x);
+            s_tstart[threadIdx.x] = y - x;
+        }
+        __syncthreads();
+        // reserve the tile's run in each sub-bucket; the atomics' latency
+        // overlaps the staging below
+        const unsigned long long g = x ? atomicAdd(&gcur[f0 + threadIdx.x], (unsigned long long)x) : 0ull;
+        const int u8[8] = {cur.ua.x, cur.ua.y, cur.ua.z, cur.ua.w, cur.ub.x, cur.ub.y, cur.ub.z, cur.ub.w};
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+            if (rk[j] != ~0u) {
+                const unsigned int q = s_tstart[lv[j] >> sb] + rk[j];
+                s_u[q] = u8[j];
+                s_lv[q] = (uint16_t)lv[j];
+            }
+        if (x) s_gb[threadIdx.x] = g;
+        __syncthreads();
+        const unsigned int total = s_tstart[S - 1] + s_tcnt[S - 1];
+        for (unsigned int q = threadIdx.x; q < total; q += blockDim.x) {
+            const unsigned int lvq = s_lv[q];
+            const unsigned int sub = lvq >> sb;
+            const unsigned long long pos = s_gb[sub] + (q - s_tstart[sub]);
+            if (pos < __ldg(&start[f0 + sub + 1])) {
+                u2[pos] = s_u[q];
+                lv2[pos] = (uint16_t)(lvq & lmask);
+            } else {
+                atomicExch(err, SCC_ERR_INTERNAL);
+            }
+        }
+        __syncthreads();  // the staging and the counts are reused by the next tile
+        if (tn < ntiles) cur = nxt;
+    }
+}
+
+// C. rows: block takes the next sub-bucket of `order` (a work counter). Counter
+// i of the sub-bucket lives at i + i / 32 in shared memory: the scan gives each
+// thread a run of consecutive counters, and with one padding word per 32 the
+// lanes of a warp reading the j-th counter of their runs hit 32 different banks.
+__device__ __forceinline__ int cpad(int i) { return i + (i >> 5); }
+constexpr int kCntWords = (1 << kMaxSubVertsLog) + (1 << kMaxSubVertsLog) / 32 + 4;  // 16-byte multiple
+size_t rows_smem_bytes() { return sizeof(int) * ((size_t)kCntWords + kWinArcs); }
+
+__global__ void __launch_bounds__(kBlkR, 3) k_sub_rows(const int32_t* __restrict__ u2, const uint16_t* __restrict__ lv2,
+                                                      const unsigned long long* __restrict__ start,
+                                                      const int32_t* __restrict__ order, int nf, int sb, int32_t n,
+                                                      int32_t* toff, int32_t* tadj, unsigned int* next, int* err) {
+    extern __shared__ int s_dyn[];
+    int* s_cnt = s_dyn;                // 2^sb counters, padded (cpad)
+    int32_t* s_win = s_dyn + kCntWords;  // the sub-bucket's rows while they fit
+    __shared__ int s_wsum[kBlkR / 32];
     __shared__ int s_oi;
-    const int W = 1 << shift;
-    constexpr int kCh = 2;  // chunks per thread per step
+    const int W = 1 << sb;
     for (;;) {
-        if (threadIdx.x == 0) s_oi = (int)atomicAdd(rows_next, 1u);
+        if (threadIdx.x == 0) s_oi = (int)atomicAdd(next, 1u);
         __syncthreads();
         const int oi = s_oi;
-        if (oi >= nb) break;
-        const int b = order[oi];
-        const int v0 = b << shift;
-        const int vw = min(W, n - v0);
-        const long long a0 = (long long)start[b], a1 = (long long)start[b + 1];
+        if (oi >= nf) break;
+        const int f = order[oi];
+        const long long v0 = (long long)f << sb;
+        const int vw = (int)min((long long)W, (long long)n - v0);
+        if (vw <= 0) {  // bins past the last vertex hold nothing; uniform
+            __syncthreads();  // every thread has read s_oi before it is rewritten
+            continue;
+        }
+        const long long a0 = (long long)start[f], a1 = (long long)start[f + 1];
+        const bool win = a1 - a0 <= kWinArcs;
         for (int i = threadIdx.x; i < cpad(vw); i += blockDim.x) s_cnt[i] = 0;
         __syncthreads();
         const long long c0 = (a0 & ~7ll) + 8ll * threadIdx.x;
         const long long cstep = 8ll * blockDim.x;
-        for (long long c = c0; c < a1; c += kCh * cstep) {
-            uint4 r[kCh];
+        for (long long c = c0; c < a1; c += cstep) {
+            unsigned int lv[8];
+            unpack8(__ldg(reinterpret_cast<const uint4*>(lv2 + c)), lv);
 #pragma unroll
-            for (int k = 0; k < kCh; ++k) {
-                const long long cc = c + k * cstep;
-                r[k] = cc < a1 ? __ldg(reinterpret_cast<const uint4*>(lvv + cc)) : make_uint4(0, 0, 0, 0);
-            }
-#pragma unroll
-            for (int k = 0; k < kCh; ++k) {
-                const long long cc = c + k * cstep;
-                unsigned int lv[8];
-                unpack8(r[k], lv);
-#pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    if (cc + j < a0 || cc + j >= a1) continue;
-                    if (lv[j] < (unsigned int)vw) atomicAdd(&s_cnt[cpad((int)lv[j])], 1);
-                    else atomicExch(err, SCC_ERR_INTERNAL);  // arc outside its bucket: skip it, report
-                }
+            for (int j = 0; j < 8; ++j) {
+                if (c + j < a0 || c + j >= a1) continue;
+                if (lv[j] < (unsigned int)vw) atomicAdd(&s_cnt[cpad((int)lv[j])], 1);
+                else atomicExch(err, SCC_ERR_INTERNAL);  // arc outside its sub-bucket: skip it, report
             }
         }
         __syncthreads();
         // exclusive scan of s_cnt[0..vw) in place; each thread owns a contiguous run
         const int per = (vw + blockDim.x - 1) / blockDim.x;
-        const int q0 = threadIdx.x * per, q1 = min(q0 + per, vw);
+        const int q0 = min((int)threadIdx.x * per, vw), q1 = min(q0 + per, vw);
         int sum = 0;
         for (int i = q0; i < q1; ++i) sum += s_cnt[cpad(i)];
         int incl = warp_incl_scan(sum);
@@ -387,39 +567,34 @@ __global__ void __launch_bounds__(kBlkB) k_bucket_rows(const int32_t* __restrict
             run += cn;
         }
         __syncthreads();
-        // the bucket's row offsets, written coalesced (before the placement
+        // the sub-bucket's row offsets, written coalesced (before the placement
         // below advances the counters)
         for (int i = threadIdx.x; i < vw; i += blockDim.x) toff[v0 + i] = (int32_t)(a0 + s_cnt[cpad(i)]);
         __syncthreads();
-        for (long long c = c0; c < a1; c += kCh * cstep) {
-            uint4 r[kCh];
-            int4 ua[kCh], ub[kCh];
+        for (long long c = c0; c < a1; c += cstep) {
+            unsigned int lv[8];
+            unpack8(__ldg(reinterpret_cast<const uint4*>(lv2 + c)), lv);
+            const int4 ua = __ldg(reinterpret_cast<const int4*>(u2 + c));
+            const int4 ub = __ldg(reinterpret_cast<const int4*>(u2 + c + 4));
+            const int u8[8] = {ua.x, ua.y, ua.z, ua.w, ub.x, ub.y, ub.z, ub.w};
 #pragma unroll
-            for (int k = 0; k < kCh; ++k) {
-                const long long cc = c + k * cstep;
-                const bool in = cc < a1;
-                r[k] = in ? __ldg(reinterpret_cast<const uint4*>(lvv + cc)) : make_uint4(0, 0, 0, 0);
-                ua[k] = in ? __ldg(reinterpret_cast<const int4*>(uu + cc)) : make_int4(0, 0, 0, 0);
-                ub[k] = in ? __ldg(reinterpret_cast<const int4*>(uu + cc + 4)) : make_int4(0, 0, 0, 0);
-            }
-#pragma unroll
-            for (int k = 0; k < kCh; ++k) {
-                const long long cc = c + k * cstep;
-                unsigned int lv[8];
-                unpack8(r[k], lv);
-                const int u8[8] = {ua[k].x, ua[k].y, ua[k].z, ua[k].w, ub[k].x, ub[k].y, ub[k].z, ub[k].w};
-#pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    if (cc + j < a0 || cc + j >= a1 || lv[j] >= (unsigned int)vw) continue;
-                    const int p = atomicAdd(&s_cnt[cpad((int)lv[j])], 1);
-                    if (a0 + p < a1) tadj[a0 + p] = u8[j];
-                    else atomicExch(err, SCC_ERR_INTERNAL);
+            for (int j = 0; j < 8; ++j) {
+                if (c + j < a0 || c + j >= a1 || lv[j] >= (unsigned int)vw) continue;
+                const int p = atomicAdd(&s_cnt[cpad((int)lv[j])], 1);
+                if (p < a1 - a0) {
+                    if (win) s_win[p] = u8[j];
+                    else tadj[a0 + p] = u8[j];
+                } else {
+                    atomicExch(err, SCC_ERR_INTERNAL);
                 }
             }
         }
         __syncthreads();
+        if (win)
+            for (int i = threadIdx.x; i < (int)(a1 - a0); i += blockDim.x) tadj[a0 + i] = s_win[i];
+        __syncthreads();
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) toff[n] = (int32_t)start[nb];
+    if (blockIdx.x == 0 && threadIdx.x == 0) toff[n] = (int32_t)start[nf];
 }
 
 // Direct path for graphs too large for shared per-bucket counters: global
@@ -452,6 +627,10 @@ int grid_for_arcs(int64_t m, int per_block, int num_sms, int per_sm) {
 
 }  // namespace
 
+// sub-buckets: 2^sb vertices, 2^sublog of them per bucket
+inline int sub_vert_log(int shift) { return std::min(shift, std::max(shift - kSubLog, 5)); }
+inline int sub_log(int shift) { return shift - sub_vert_log(shift); }
+
 int bucket_shift(int32_t n) {
     int shift = 6;
     while (((int64_t)n + (1ll << shift) - 1) >> shift > kMaxBuckets) ++shift;
@@ -460,12 +639,26 @@ int bucket_shift(int32_t n) {
 
 size_t tile_rows_count(int64_t m) { return (size_t)((m + kStep - 1) / kStep) + 1; }
 
+size_t transpose_split_tiles(int64_t m, int32_t n, int shift) {
+    const int nb = std::max(1, (int)(((int64_t)n + (1ll << shift) - 1) >> shift));
+    return (size_t)(m / kSplitTile) + (size_t)nb + 2;
+}
+
+int transpose_bins(int32_t n, int shift) {
+    const int nb = std::max(1, (int)(((int64_t)n + (1ll << shift) - 1) >> shift));
+    return nb << sub_log(shift);
+}
+
 int launch_copy_check_hist(const int32_t* src, int32_t* dst, int32_t n, int64_t m, int shift,
                            unsigned long long* bucket_cnt, int* bad, int num_sms, cudaStream_t s) {
     if (m == 0) return SCC_OK;
-    const int nb = std::max(1, (int)(((int64_t)n + (1ll << shift) - 1) >> shift));
-    k_copy_check_hist<<<grid_for_arcs(m, 4 * kBlkA * 4, num_sms, 2), kBlkA, 0, s>>>(src, dst, m, n, shift, nb,
-                                                                                   bucket_cnt, bad);
+    const int nf = transpose_bins(n, shift);  // sub-bucket bins (<= 16384)
+    const size_t smem = sizeof(unsigned int) * (size_t)nf;
+    if (smem > 48 * 1024)
+        SCC_CUDA(cudaFuncSetAttribute(k_copy_check_hist, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_copy_check_hist<<<grid_for_arcs(m, 4 * kBlkA * 4, num_sms, 2), kBlkA, smem, s>>>(src, dst, m, n,
+                                                                                      sub_vert_log(shift), nf,
+                                                                                      bucket_cnt, bad);
     SCC_LAUNCH();
     return SCC_OK;
 }
@@ -510,21 +703,25 @@ int launch_transpose_direct(const int32_t* off, const int32_t* adj, const int32_
 bool transpose_bucketed(int shift) { return shift <= kBucketLog; }
 
 int launch_transpose(const int32_t* off, const int32_t* adj, const int32_t* trow, int32_t n, int64_t m, int64_t mt,
-                     int shift,
-                     const unsigned long long* bucket_cnt, unsigned long long* bucket_tmp, int32_t* tmp_u,
-                     uint16_t* tmp_lv, int32_t* order_tmp, int32_t* toff, int32_t* tadj, int32_t* selfrow,
-                     unsigned long long* nself, bool* self_found, int* err, int num_sms, cudaStream_t s,
-                     cudaEvent_t* ev) {
+                     int shift, const unsigned long long* bucket_cnt, unsigned long long* bucket_tmp, int32_t* tmp_u,
+                     uint16_t* tmp_lv, int32_t* tmp2_u, uint16_t* tmp2_lv, int32_t* order_tmp, int32_t* tile_bucket,
+                     int32_t* toff, int32_t* tadj, int32_t* selfrow, unsigned long long* nself, bool* self_found,
+                     int* err, int num_sms, cudaStream_t s, cudaEvent_t* ev) {
     *self_found = false;
     const int nb = std::max(1, (int)(((int64_t)n + (1ll << shift) - 1) >> shift));
-    unsigned long long* start = bucket_tmp;
-    unsigned long long* cursor = bucket_tmp + nb + 1;
-    unsigned int* rows_next = reinterpret_cast<unsigned int*>(bucket_tmp + 2 * nb + 1);
+    const int sb = sub_vert_log(shift), sublog = sub_log(shift);
+    const int nf = nb << sublog;
+    unsigned long long* start = bucket_tmp;                       // [nf + 1]
+    unsigned long long* gcur = start + nf + 1;                    // [nf]
+    unsigned long long* cursor = gcur + nf;                       // [nb]
+    unsigned long long* tile_base = cursor + nb;                  // [nb + 1]
+    unsigned int* counters = reinterpret_cast<unsigned int*>(tile_base + nb + 1);  // rows pass
     if (n == 0) {
         SCC_CUDA(cudaMemsetAsync(toff, 0, sizeof(int32_t), s));
         return SCC_OK;
     }
-    k_bucket_scan<<<1, 32, 0, s>>>(bucket_cnt, nb, start, cursor, rows_next);
+    k_fine_scan<<<1, 1024, 0, s>>>(bucket_cnt, nf, sublog, nb, start, gcur, cursor, order_tmp, tile_base, tile_bucket,
+                                   counters);
     SCC_LAUNCH();
     if (mt > 0) {
         const int stage = 2 * kStep * (int)sizeof(int32_t);
@@ -537,32 +734,36 @@ int launch_transpose(const int32_t* off, const int32_t* adj, const int32_t* trow
         SCC_LAUNCH();
         if (ev) cudaEventRecord(ev[1], s);
     }
-    // buckets by decreasing size (longest first), from the host copy of the counts
-    std::vector<unsigned long long> hc(nb);
     unsigned long long hself = 0;
-    SCC_CUDA(cudaMemcpyAsync(hc.data(), bucket_cnt, sizeof(unsigned long long) * nb, cudaMemcpyDeviceToHost, s));
     SCC_CUDA(cudaMemcpyAsync(&hself, nself, sizeof(hself), cudaMemcpyDeviceToHost, s));
     SCC_CUDA(cudaStreamSynchronize(s));
     if (hself > 0) {  // the caller drops the self-loops and calls again
         *self_found = true;
         return SCC_OK;
     }
-    std::vector<int32_t> ord(nb);
-    std::iota(ord.begin(), ord.end(), 0);
-    std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return hc[a] > hc[b]; });
-    SCC_CUDA(cudaMemcpyAsync(order_tmp, ord.data(), sizeof(int32_t) * nb, cudaMemcpyHostToDevice, s));
-    const size_t smem = sizeof(int) * (((size_t)1 << shift) + ((size_t)1 << shift) / 32 + 1);
-    if (smem > 48 * 1024)
-        SCC_CUDA(cudaFuncSetAttribute(k_bucket_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
-    SCC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bucket_rows, kBlkB, smem));
+    const size_t split_smem = (size_t)kSplitTile * (sizeof(int32_t) + sizeof(uint16_t));
+    SCC_CUDA(cudaFuncSetAttribute(k_bucket_split, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)split_smem));
+    SCC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bucket_split, kBlkS, split_smem));
+    unsigned long long ntiles = 0;
+    SCC_CUDA(cudaMemcpyAsync(&ntiles, tile_base + nb, sizeof(ntiles), cudaMemcpyDeviceToHost, s));
+    SCC_CUDA(cudaStreamSynchronize(s));
     if (ev) cudaEventRecord(ev[2], s);
-    k_bucket_rows<<<std::min(nb, num_sms * std::max(1, per_sm)), kBlkB, smem, s>>>(tmp_u, tmp_lv, start, order_tmp,
-                                                                                     nb, shift, n, toff, tadj,
-                                                                                     rows_next, err);
-    SCC_LAUNCH();
+    if (ntiles > 0) {
+        k_bucket_split<<<(unsigned)std::min<unsigned long long>(ntiles, (unsigned long long)num_sms * std::max(1, per_sm)),
+                         kBlkS, split_smem, s>>>(tmp_u, tmp_lv, start, tile_base, tile_bucket, (long long)ntiles, sublog, sb,
+                                        gcur, tmp2_u, tmp2_lv, err);
+        SCC_LAUNCH();
+    }
     if (ev) cudaEventRecord(ev[3], s);
-    SCC_CUDA(cudaStreamSynchronize(s));  // ord (host) must outlive the copy
+    const size_t smem = rows_smem_bytes();
+    SCC_CUDA(cudaFuncSetAttribute(k_sub_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    SCC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sub_rows, kBlkR, smem));
+    if (ev) cudaEventRecord(ev[4], s);
+    k_sub_rows<<<std::min(nf, num_sms * std::max(1, per_sm)), kBlkR, smem, s>>>(tmp2_u, tmp2_lv, start, order_tmp, nf,
+                                                                                 sb, n, toff, tadj, counters, err);
+    SCC_LAUNCH();
+    if (ev) cudaEventRecord(ev[5], s);
     return SCC_OK;
 }
 

@@ -58,7 +58,7 @@ class scc_stats(ctypes.Structure):
                 ("ms_transpose_rows", ctypes.c_double), ("n_class_trimmed", ctypes.c_int32),
                 ("class_trim_passes", ctypes.c_int32), ("ms_class_trim", ctypes.c_double),
                 ("multi_launches", ctypes.c_int32), ("multi_arcs", ctypes.c_int64), ("multi_items", ctypes.c_int64),
-                ("tau", ctypes.c_int32)]
+                ("tau", ctypes.c_int32), ("ms_transpose_split", ctypes.c_double)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
