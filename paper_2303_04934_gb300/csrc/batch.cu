@@ -4,8 +4,13 @@
 // decreasing size, so the longest ones start first) and runs the whole method
 // on it alone, with __syncthreads between rounds (CtaScope of engine.cuh):
 //
-//   1. G^T of the graph: in-degree counts, a block scan, placement (Sec. 2: a
-//      backward search is a forward search on G^T).
+//   1. G^T of the graph (Sec. 2: a backward search is a forward search on
+//      G^T). A run through a batch handle computes it before the persistent
+//      launch for groups of consecutive graphs at once (each group, up to 2^24
+//      vertices, is one graph of disjoint parts for the grid-wide transpose of
+//      transpose.cu), and a block only points at its graph's part; graphs
+//      outside the groups (and the server's launches) build it in the block:
+//      in-degree counts, a block scan, placement.
 //   2. Trimming (Sec. 4.1): vertices without in- or out-arcs are singletons.
 //   3. The pivot order: a seeded Feistel permutation of the active vertices.
 //   4. The first SCC (Sec. 4.2): forward and backward single-reachability from
@@ -127,11 +132,18 @@ struct BatchArgs {
     int tau, seeds, lambda, sigma;
     double beta;
     uint64_t seed;
+    // G^T computed before the launch, packed like the input (per graph n + 1
+    // local offsets at vbase[g] + g, local sources at ebase[g]) for the graphs
+    // with gt_ok[g] != 0; null: every block builds its graph's G^T
+    const int32_t* gt_off;
+    const int32_t* gt_adj;
+    const unsigned char* gt_ok;
 };
 
 // Per-block pointers into its slice.
 struct Ws {
     int32_t *toff, *tadj, *cnt, *label, *rep, *act, *src;
+    int32_t *toff_slice, *tadj_slice;  // the slice's own G^T arrays
     unsigned long long *fmax, *bmax, *hit;
     uint32_t *bits_f, *bits_b;
     unsigned long long *tab0, *tab1;
@@ -148,8 +160,8 @@ __device__ __forceinline__ T* at(unsigned char* base, size_t off) {
 __device__ void bind_ws(const BatchArgs& A, Ws& W) {
     unsigned char* b = A.ws + A.ws_stride * blockIdx.x;
     const WsLayout& L = A.L;
-    W.toff = at<int32_t>(b, L.toff);
-    W.tadj = at<int32_t>(b, L.tadj);
+    W.toff = W.toff_slice = at<int32_t>(b, L.toff);
+    W.tadj = W.tadj_slice = at<int32_t>(b, L.tadj);
     W.cnt = at<int32_t>(b, L.cnt);
     W.label = at<int32_t>(b, L.label);
     W.rep = at<int32_t>(b, L.rep);
@@ -295,15 +307,20 @@ __device__ bool scc_one_graph(const BatchArgs& A, Ws& W, int g, BlockShared& sh,
         return true;
     }
 
-    // ---- 1. G^T: in-degrees, scan, placement
-    for (int v = tid; v <= n; v += nt) W.cnt[v] = 0;
-    __syncthreads();
-    for (long long e = tid; e < m; e += nt) atomicAdd(&W.cnt[adj[e]], 1);
-    __syncthreads();
-    block_exclusive_scan(W.cnt, n, sh);
-    for (int v = tid; v <= n; v += nt) W.toff[v] = W.cnt[v];
-    __syncthreads();
-    {
+    // ---- 1. G^T: computed before the launch, or in-degrees, scan, placement
+    if (A.gt_ok != nullptr && A.gt_ok[g]) {
+        W.toff = const_cast<int32_t*>(A.gt_off + vb + g);
+        W.tadj = const_cast<int32_t*>(A.gt_adj + eb);
+    } else {
+        W.toff = W.toff_slice;
+        W.tadj = W.tadj_slice;
+        for (int v = tid; v <= n; v += nt) W.cnt[v] = 0;
+        __syncthreads();
+        for (long long e = tid; e < m; e += nt) atomicAdd(&W.cnt[adj[e]], 1);
+        __syncthreads();
+        block_exclusive_scan(W.cnt, n, sh);
+        for (int v = tid; v <= n; v += nt) W.toff[v] = W.cnt[v];
+        __syncthreads();
         // 16 consecutive arcs per thread: one row search, then a forward walk
         constexpr int kC = 16;
         for (long long e0 = (long long)tid * kC; e0 < m; e0 += (long long)nt * kC) {
@@ -315,8 +332,8 @@ __device__ bool scc_one_graph(const BatchArgs& A, Ws& W, int g, BlockShared& sh,
                 W.tadj[atomicAdd(&W.cnt[w], 1)] = u;
             }
         }
+        __syncthreads();
     }
-    __syncthreads();
 
     mark(1);
     // ---- 2. trimming; 3. active list (ordered) for the pivot permutation
@@ -624,7 +641,83 @@ __global__ void k_batch_init_ws(unsigned char* ws, size_t stride, int blocks, Ws
 // ---------------------------------------------------------------- host side --
 using scc::BatchDims;
 using scc::DeviceInfo;
+using scc::TransposeScratch;
 using scc::WsLayout;
+
+namespace scc {
+namespace {
+
+// ------------------------------------------------------ groups of graphs --
+// Graphs [g0, g1) of a packed batch as one graph: vertices [v0, v0 + ng),
+// arcs [e0, e0 + mg). The vertex (or arc) -> graph map is a search for the
+// first of 16 consecutive entries of a thread, then a walk.
+constexpr long long kGroupVerts = 1ll << 24;  // the bucketed transpose's limit
+constexpr long long kGroupArcs = 1ll << 27;   // bounds the groups' scratch
+
+// last g in [lo, hi) with a[g] <= x (a non-decreasing, a[lo] <= x)
+__device__ __forceinline__ int last_le(const long long* __restrict__ a, int lo, int hi, long long x) {
+    while (hi - lo > 1) {
+        const int mid = lo + ((hi - lo) >> 1);
+        if (a[mid] <= x) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// The group's CSR: offsets from its first arc, targets from its first vertex.
+__global__ void k_group_csr(const long long* __restrict__ vbase, const long long* __restrict__ ebase,
+                            const int32_t* __restrict__ offsets, const int32_t* __restrict__ targets, int g0, int g1,
+                            long long v0, long long e0, long long ng, long long mg, int32_t* goff, int32_t* gadj) {
+    const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i0 = 16 * tid; i0 < ng; i0 += 16 * stride) {
+        const long long i1 = min(i0 + 16, ng);
+        int g = last_le(vbase, g0, g1, v0 + i0);
+        for (long long i = i0; i < i1; ++i) {
+            while (g + 1 < g1 && vbase[g + 1] <= v0 + i) ++g;
+            goff[i] = offsets[vbase[g] + g + (v0 + i - vbase[g])] + (int32_t)(ebase[g] - e0);
+        }
+    }
+    if (tid == 0) goff[ng] = (int32_t)mg;
+    for (long long j0 = 16 * tid; j0 < mg; j0 += 16 * stride) {
+        const long long j1 = min(j0 + 16, mg);
+        int g = last_le(ebase, g0, g1, e0 + j0);
+        for (long long j = j0; j < j1; ++j) {
+            while (g + 1 < g1 && ebase[g + 1] <= e0 + j) ++g;
+            gadj[j] = targets[e0 + j] + (int32_t)(vbase[g] - v0);
+        }
+    }
+}
+
+// The group's G^T back to per-graph local form, packed like the input:
+// offsets from each graph's first arc (and its closing offset), sources from
+// its first vertex (in place: the group's G^T arcs are gt_adj[e0 ..)).
+__global__ void k_group_localize(const long long* __restrict__ vbase, const long long* __restrict__ ebase, int g0,
+                                 int g1, long long v0, long long e0, long long ng, long long mg,
+                                 const int32_t* __restrict__ gtoff, int32_t* gt_off, int32_t* gt_adj) {
+    const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i0 = 16 * tid; i0 < ng; i0 += 16 * stride) {
+        const long long i1 = min(i0 + 16, ng);
+        int g = last_le(vbase, g0, g1, v0 + i0);
+        for (long long i = i0; i < i1; ++i) {
+            while (g + 1 < g1 && vbase[g + 1] <= v0 + i) ++g;
+            gt_off[vbase[g] + g + (v0 + i - vbase[g])] = gtoff[i] - (int32_t)(ebase[g] - e0);
+        }
+    }
+    for (long long g = g0 + tid; g < g1; g += stride) gt_off[vbase[g + 1] + g] = (int32_t)(ebase[g + 1] - ebase[g]);
+    for (long long j0 = 16 * tid; j0 < mg; j0 += 16 * stride) {
+        const long long j1 = min(j0 + 16, mg);
+        int g = last_le(ebase, g0, g1, e0 + j0);
+        for (long long j = j0; j < j1; ++j) {
+            while (g + 1 < g1 && ebase[g + 1] <= e0 + j) ++g;
+            gt_adj[e0 + j] -= (int32_t)(vbase[g] - v0);
+        }
+    }
+}
+
+}  // namespace
+}  // namespace scc
 
 struct scc_batch {
     DeviceInfo di;
@@ -641,6 +734,19 @@ struct scc_batch {
     int* flags = nullptr;           // [0] work-queue head, [1] error
     unsigned long long* times = nullptr;  // per graph: start, end, block (3 words)
     int32_t* labels = nullptr;      // internal output (host destinations, tuning)
+    // G^T computed before the persistent launch, for groups of consecutive
+    // graphs (one grid-wide transpose each)
+    struct Group {
+        int g0, g1;
+        long long v0, v1, e0, e1;
+    };
+    std::vector<Group> groups;
+    int32_t* gt_off = nullptr;       // packed like offsets
+    int32_t* gt_adj = nullptr;       // packed like targets
+    unsigned char* gt_ok = nullptr;  // graph is in a group
+    int32_t *grp_off = nullptr, *grp_adj = nullptr, *grp_toff = nullptr;  // one group's CSR and G^T offsets
+    unsigned char* grp_scratch = nullptr;
+    TransposeScratch ts{};
     scc_batch_config cfg;
     // working memory for the current configuration
     unsigned char* ws = nullptr;
@@ -756,9 +862,14 @@ int prepare(scc_batch* h, cudaStream_t s) {
 
 BatchArgs args_for(const scc_batch_config& cfg, unsigned char* ws, const WsLayout& L, const BatchDims& D, int* flags,
                    unsigned long long* times, int32_t G, const long long* vbase, const long long* ebase,
-                   const int32_t* offsets, const int32_t* targets, const int32_t* order, int norder, int32_t* out) {
+                   const int32_t* offsets, const int32_t* targets, const int32_t* order, int norder, int32_t* out,
+                   const int32_t* gt_off = nullptr, const int32_t* gt_adj = nullptr,
+                   const unsigned char* gt_ok = nullptr) {
     BatchArgs A;
     memset(&A, 0, sizeof(A));
+    A.gt_off = gt_off;
+    A.gt_adj = gt_adj;
+    A.gt_ok = gt_ok;
     A.G = G;
     A.vbase = vbase;
     A.ebase = ebase;
@@ -785,13 +896,34 @@ BatchArgs args_for(const scc_batch_config& cfg, unsigned char* ws, const WsLayou
 
 BatchArgs make_args(scc_batch* h, const int32_t* order, int norder, int32_t* out) {
     return args_for(h->cfg, h->ws, h->L, h->D, h->flags, h->times, h->G, h->vbase, h->ebase, h->offsets, h->targets,
-                    order, norder, out);
+                    order, norder, out, h->gt_off, h->gt_adj, h->gt_ok);
+}
+
+// G^T of every group (after the reset kernel, before the persistent launch);
+// the passes' self-check errors go to the batch's error flag.
+int enqueue_groups(scc_batch* h, cudaStream_t s) {
+    TransposeScratch ts = h->ts;
+    ts.err = h->flags + 1;
+    for (const auto& gr : h->groups) {
+        const long long ng = gr.v1 - gr.v0, mg = gr.e1 - gr.e0;
+        const int grid = h->di.num_sms * 4;
+        k_group_csr<<<grid, 256, 0, s>>>(h->vbase, h->ebase, h->offsets, h->targets, gr.g0, gr.g1, gr.v0, gr.e0, ng,
+                                         mg, h->grp_off, h->grp_adj);
+        SCC_LAUNCH();
+        SCC_TRY(launch_transpose_keep_self(h->grp_off, h->grp_adj, (int32_t)ng, mg, ts, h->grp_toff,
+                                           h->gt_adj + gr.e0, h->di.num_sms, s));
+        k_group_localize<<<grid, 256, 0, s>>>(h->vbase, h->ebase, gr.g0, gr.g1, gr.v0, gr.e0, ng, mg, h->grp_toff,
+                                              h->gt_off, h->gt_adj);
+        SCC_LAUNCH();
+    }
+    return SCC_OK;
 }
 
 int enqueue(scc_batch* h, const int32_t* order, int norder, int32_t* out, cudaStream_t s) {
     BatchArgs A = make_args(h, order, norder, out);
     k_batch_reset<<<1, 1, 0, s>>>(h->flags, h->flags + 1);
     SCC_LAUNCH();
+    SCC_TRY(enqueue_groups(h, s));
     batch_kernel_for(h->cfg)<<<h->blocks, h->cfg.block, batch_smem_bytes(h->cfg.block), s>>>(A);
     SCC_LAUNCH();
     return SCC_OK;
@@ -807,8 +939,11 @@ int capture(scc_batch* h, const int32_t* order, int norder, int32_t* out) {
     if (rc == SCC_OK) {
         BatchArgs A = make_args(h, order, norder, out);
         k_batch_reset<<<1, 1, 0, cs>>>(h->flags, h->flags + 1);
-        batch_kernel_for(h->cfg)<<<h->blocks, h->cfg.block, batch_smem_bytes(h->cfg.block), cs>>>(A);
-        rc = cuda_err(cudaGetLastError());
+        rc = enqueue_groups(h, cs);
+        if (rc == SCC_OK) {
+            batch_kernel_for(h->cfg)<<<h->blocks, h->cfg.block, batch_smem_bytes(h->cfg.block), cs>>>(A);
+            rc = cuda_err(cudaGetLastError());
+        }
         const int rc2 = cuda_err(cudaStreamEndCapture(cs, &graph));
         if (rc == SCC_OK) rc = rc2;
     }
@@ -862,6 +997,13 @@ int run_order(scc_batch* h, const int32_t* order, int norder, int32_t* out, cuda
 void batch_free(scc_batch* h, cudaStream_t s) {
     drop_exec(h);
     dfree(h->ws, s);
+    dfree(h->gt_off, s);
+    dfree(h->gt_adj, s);
+    dfree(h->gt_ok, s);
+    dfree(h->grp_off, s);
+    dfree(h->grp_adj, s);
+    dfree(h->grp_toff, s);
+    dfree(h->grp_scratch, s);
     dfree(h->vbase, s);
     dfree(h->ebase, s);
     dfree(h->offsets, s);
@@ -943,6 +1085,49 @@ int batch_create_impl(scc_batch* h, int32_t G, const int64_t* vbase, const int64
     SCC_TRY(dalloc_t(&h->order, (size_t)G + 1, s));
     if (G > 0)
         SCC_CUDA(cudaMemcpyAsync(h->order, h->order_h.data(), sizeof(int32_t) * (size_t)G, cudaMemcpyHostToDevice, s));
+    // groups of consecutive graphs for the G^T computed before each launch: up
+    // to kGroupVerts vertices and kGroupArcs arcs each; a larger graph is left
+    // to its block
+    std::vector<unsigned char> ok((size_t)G + 1, 0);
+    long long ng_max = 0, mg_max = 0;
+    {
+        scc_batch::Group cur{0, 0, 0, 0, 0, 0};
+        auto flush = [&](int g) {
+            if (cur.g1 > cur.g0 && cur.v1 > cur.v0) {
+                h->groups.push_back(cur);
+                ng_max = std::max(ng_max, cur.v1 - cur.v0);
+                mg_max = std::max(mg_max, cur.e1 - cur.e0);
+            } else {
+                for (int k = cur.g0; k < cur.g1; ++k) ok[k] = 0;
+            }
+            cur = {g, g, h->vb_h[g], h->vb_h[g], h->eb_h[g], h->eb_h[g]};
+        };
+        for (int32_t g = 0; g < G; ++g) {
+            const long long n = h->vb_h[g + 1] - h->vb_h[g], m = h->eb_h[g + 1] - h->eb_h[g];
+            if (n > kGroupVerts || m > kGroupArcs) {
+                flush(g + 1);  // the current group ends before g; g builds its own G^T
+                continue;
+            }
+            if ((cur.v1 - cur.v0) + n > kGroupVerts || (cur.e1 - cur.e0) + m > kGroupArcs) flush(g);
+            cur.g1 = g + 1;
+            cur.v1 = h->vb_h[g + 1];
+            cur.e1 = h->eb_h[g + 1];
+            ok[g] = 1;
+        }
+        flush(G);
+    }
+    if (!h->groups.empty()) {
+        SCC_TRY(dalloc_t(&h->gt_off, (size_t)(h->nv + G) + 1, s));
+        SCC_TRY(dalloc_t(&h->gt_adj, (size_t)h->na + 1, s));
+        SCC_TRY(dalloc_t(&h->gt_ok, (size_t)G + 1, s));
+        SCC_CUDA(cudaMemcpyAsync(h->gt_ok, ok.data(), (size_t)G, cudaMemcpyHostToDevice, s));
+        SCC_TRY(dalloc_t(&h->grp_off, (size_t)ng_max + 1, s));
+        SCC_TRY(dalloc_t(&h->grp_toff, (size_t)ng_max + 1, s));
+        SCC_TRY(dalloc_t(&h->grp_adj, (size_t)mg_max + 8, s));
+        SCC_TRY(dalloc_t(&h->grp_scratch, transpose_scratch_bytes(mg_max), s));
+        transpose_scratch_carve(h->grp_scratch, mg_max, &h->ts);
+        SCC_TRY(transpose_set_attributes());  // before any capture
+    }
     SCC_CUDA(cudaStreamSynchronize(s));
     memset(&h->st, 0, sizeof(h->st));
     h->st.graphs = G;

@@ -89,6 +89,19 @@ int launch_transpose(const int32_t* off, const int32_t* adj, const int32_t* trow
                      int32_t* toff, int32_t* tadj, int32_t* selfrow, unsigned long long* nself, bool* self_found,
                      int* err, int num_sms, cudaStream_t s,
                      cudaEvent_t* ev = nullptr);  // ev[0..5]: around the partition, split and rows passes
+// G^T without host synchronisation for packed groups of graphs (batch.cu):
+// self-loops are kept (they change no reachability), targets must be valid.
+struct TransposeScratch {
+    unsigned long long *bcnt, *btmp;
+    int32_t *tmp_u, *tmp2_u, *order, *tiles, *trow;
+    uint16_t *tmp_lv, *tmp2_lv;
+    int *bad, *err;
+};
+size_t transpose_scratch_bytes(int64_t m_max);
+void transpose_scratch_carve(unsigned char* base, int64_t m_max, TransposeScratch* ts);
+int launch_transpose_keep_self(const int32_t* off, const int32_t* adj, int32_t n, int64_t m, const TransposeScratch& ts,
+                               int32_t* toff, int32_t* tadj, int num_sms, cudaStream_t s);
+int transpose_set_attributes();
 // Direct G^T for very large n: global atomics. indeg: n + 1.
 int launch_transpose_direct(const int32_t* off, const int32_t* adj, const int32_t* trow, int32_t n, int64_t m,
                             int32_t* indeg, void* scan_tmp, int32_t* toff, int32_t* tadj, int num_sms,

@@ -332,7 +332,7 @@ __global__ void __launch_bounds__(kBlkA) k_bucket_part(const int32_t* __restrict
             uu[q] = u;
             vv[q] = v;
             rk[q] = atomicAdd(&s_cnt[v >> shift], 1u);
-            if (u == v) {
+            if (u == v && selfrow != nullptr) {  // without selfrow, self-loops are kept
                 atomicAdd(&selfrow[u], 1);
                 atomicAdd(nself, 1ull);
             }
@@ -428,7 +428,7 @@ __global__ void __launch_bounds__(kBlkS, 1) k_bucket_split(const int32_t* __rest
                                                            const uint16_t* __restrict__ lvv,
                                                            const unsigned long long* __restrict__ start,
                                                            const unsigned long long* __restrict__ tile_base,
-                                                           const int32_t* __restrict__ tile_bucket, long long ntiles,
+                                                           const int32_t* __restrict__ tile_bucket, int nb,
                                                            int sublog, int sb, unsigned long long* gcur, int32_t* u2,
                                                            uint16_t* lv2, int* err) {
     __shared__ unsigned int s_tcnt[1 << kSubLog];
@@ -438,6 +438,7 @@ __global__ void __launch_bounds__(kBlkS, 1) k_bucket_split(const int32_t* __rest
     uint16_t* s_lv = reinterpret_cast<uint16_t*>(s_u + kSplitTile);  // [kSplitTile]
     const int S = 1 << sublog;
     const unsigned int lmask = (1u << sb) - 1u;
+    const long long ntiles = (long long)tile_base[nb];
     long long t = blockIdx.x;
     if (t >= ntiles) return;
     SplitLoad cur = split_load(uu, lvv, start, tile_base, tile_bucket, sublog, t);
@@ -631,6 +632,14 @@ int grid_for_arcs(int64_t m, int per_block, int num_sms, int per_sm) {
 inline int sub_vert_log(int shift) { return std::min(shift, std::max(shift - kSubLog, 5)); }
 inline int sub_log(int shift) { return shift - sub_vert_log(shift); }
 
+int transpose_set_attributes_impl();
+// The kernels' shared-memory limits, set once per process (the first call is
+// outside any stream capture: graph creation, or the batched setup).
+int ensure_attributes() {
+    static const int rc = transpose_set_attributes_impl();
+    return rc;
+}
+
 int bucket_shift(int32_t n) {
     int shift = 6;
     while (((int64_t)n + (1ll << shift) - 1) >> shift > kMaxBuckets) ++shift;
@@ -654,8 +663,7 @@ int launch_copy_check_hist(const int32_t* src, int32_t* dst, int32_t n, int64_t 
     if (m == 0) return SCC_OK;
     const int nf = transpose_bins(n, shift);  // sub-bucket bins (<= 16384)
     const size_t smem = sizeof(unsigned int) * (size_t)nf;
-    if (smem > 48 * 1024)
-        SCC_CUDA(cudaFuncSetAttribute(k_copy_check_hist, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    SCC_TRY(ensure_attributes());
     k_copy_check_hist<<<grid_for_arcs(m, 4 * kBlkA * 4, num_sms, 2), kBlkA, smem, s>>>(src, dst, m, n,
                                                                                       sub_vert_log(shift), nf,
                                                                                       bucket_cnt, bad);
@@ -707,6 +715,8 @@ int launch_transpose(const int32_t* off, const int32_t* adj, const int32_t* trow
                      uint16_t* tmp_lv, int32_t* tmp2_u, uint16_t* tmp2_lv, int32_t* order_tmp, int32_t* tile_bucket,
                      int32_t* toff, int32_t* tadj, int32_t* selfrow, unsigned long long* nself, bool* self_found,
                      int* err, int num_sms, cudaStream_t s, cudaEvent_t* ev) {
+    // selfrow == nullptr: self-loops are kept as arcs of G^T and nothing is read
+    // back to the host (the launches can be captured in a CUDA graph)
     *self_found = false;
     const int nb = std::max(1, (int)(((int64_t)n + (1ll << shift) - 1) >> shift));
     const int sb = sub_vert_log(shift), sublog = sub_log(shift);
@@ -725,7 +735,7 @@ int launch_transpose(const int32_t* off, const int32_t* adj, const int32_t* trow
     SCC_LAUNCH();
     if (mt > 0) {
         const int stage = 2 * kStep * (int)sizeof(int32_t);
-        SCC_CUDA(cudaFuncSetAttribute(k_bucket_part, cudaFuncAttributeMaxDynamicSharedMemorySize, stage));
+        SCC_TRY(ensure_attributes());
         if (ev) cudaEventRecord(ev[0], s);
         k_bucket_part<<<grid_for_arcs(m, kStep, num_sms, 2), kBlkA, stage, s>>>(off, adj, trow, n, m, shift, nb, cursor,
                                                                                   tmp_u, tmp_lv,
@@ -734,36 +744,97 @@ int launch_transpose(const int32_t* off, const int32_t* adj, const int32_t* trow
         SCC_LAUNCH();
         if (ev) cudaEventRecord(ev[1], s);
     }
-    unsigned long long hself = 0;
-    SCC_CUDA(cudaMemcpyAsync(&hself, nself, sizeof(hself), cudaMemcpyDeviceToHost, s));
-    SCC_CUDA(cudaStreamSynchronize(s));
-    if (hself > 0) {  // the caller drops the self-loops and calls again
-        *self_found = true;
-        return SCC_OK;
+    if (selfrow != nullptr) {
+        unsigned long long hself = 0;
+        SCC_CUDA(cudaMemcpyAsync(&hself, nself, sizeof(hself), cudaMemcpyDeviceToHost, s));
+        SCC_CUDA(cudaStreamSynchronize(s));
+        if (hself > 0) {  // the caller drops the self-loops and calls again
+            *self_found = true;
+            return SCC_OK;
+        }
     }
     int per_sm = 0;
     const size_t split_smem = (size_t)kSplitTile * (sizeof(int32_t) + sizeof(uint16_t));
-    SCC_CUDA(cudaFuncSetAttribute(k_bucket_split, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)split_smem));
+    SCC_TRY(ensure_attributes());
     SCC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bucket_split, kBlkS, split_smem));
-    unsigned long long ntiles = 0;
-    SCC_CUDA(cudaMemcpyAsync(&ntiles, tile_base + nb, sizeof(ntiles), cudaMemcpyDeviceToHost, s));
-    SCC_CUDA(cudaStreamSynchronize(s));
     if (ev) cudaEventRecord(ev[2], s);
-    if (ntiles > 0) {
-        k_bucket_split<<<(unsigned)std::min<unsigned long long>(ntiles, (unsigned long long)num_sms * std::max(1, per_sm)),
-                         kBlkS, split_smem, s>>>(tmp_u, tmp_lv, start, tile_base, tile_bucket, (long long)ntiles, sublog, sb,
-                                        gcur, tmp2_u, tmp2_lv, err);
+    if (mt > 0) {  // the tile count is read on the device; spare blocks return at once
+        k_bucket_split<<<num_sms * std::max(1, per_sm), kBlkS, split_smem, s>>>(tmp_u, tmp_lv, start, tile_base,
+                                                                               tile_bucket, nb, sublog, sb, gcur,
+                                                                               tmp2_u, tmp2_lv, err);
         SCC_LAUNCH();
     }
     if (ev) cudaEventRecord(ev[3], s);
     const size_t smem = rows_smem_bytes();
-    SCC_CUDA(cudaFuncSetAttribute(k_sub_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     SCC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sub_rows, kBlkR, smem));
     if (ev) cudaEventRecord(ev[4], s);
     k_sub_rows<<<std::min(nf, num_sms * std::max(1, per_sm)), kBlkR, smem, s>>>(tmp2_u, tmp2_lv, start, order_tmp, nf,
                                                                                  sb, n, toff, tadj, counters, err);
     SCC_LAUNCH();
     if (ev) cudaEventRecord(ev[5], s);
+    return SCC_OK;
+}
+
+// ---------------------------------------------------- packed graph groups --
+// Scratch of launch_transpose_keep_self for graphs of up to 2^24 vertices and
+// m_max arcs, carved from one allocation.
+size_t transpose_scratch_bytes(int64_t m_max) {
+    const size_t nf = (size_t)kMaxBins, nb = (size_t)kMaxBuckets;
+    auto a = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    const size_t m8 = (size_t)std::max<int64_t>(m_max, 1) + 8;
+    return a(8 * (nf + 2)) + a(8 * (2 * (nf + nb) + 3)) + 2 * a(4 * m8) + 2 * a(2 * m8) + a(4 * nf) +
+           a(4 * ((size_t)m_max / kSplitTile + nb + 2)) + a(4 * tile_rows_count(std::max<int64_t>(m_max, 1))) +
+           2 * a(sizeof(int));
+}
+void transpose_scratch_carve(unsigned char* base, int64_t m_max, TransposeScratch* ts) {
+    const size_t nf = (size_t)kMaxBins, nb = (size_t)kMaxBuckets;
+    size_t o = 0;
+    auto take = [&](size_t x) {
+        unsigned char* p = base + o;
+        o += (x + 255) & ~(size_t)255;
+        return p;
+    };
+    const size_t m8 = (size_t)std::max<int64_t>(m_max, 1) + 8;
+    ts->bcnt = reinterpret_cast<unsigned long long*>(take(8 * (nf + 2)));
+    ts->btmp = reinterpret_cast<unsigned long long*>(take(8 * (2 * (nf + nb) + 3)));
+    ts->tmp_u = reinterpret_cast<int32_t*>(take(4 * m8));
+    ts->tmp2_u = reinterpret_cast<int32_t*>(take(4 * m8));
+    ts->tmp_lv = reinterpret_cast<uint16_t*>(take(2 * m8));
+    ts->tmp2_lv = reinterpret_cast<uint16_t*>(take(2 * m8));
+    ts->order = reinterpret_cast<int32_t*>(take(4 * nf));
+    ts->tiles = reinterpret_cast<int32_t*>(take(4 * ((size_t)m_max / kSplitTile + nb + 2)));
+    ts->trow = reinterpret_cast<int32_t*>(take(4 * tile_rows_count(std::max<int64_t>(m_max, 1))));
+    ts->bad = reinterpret_cast<int*>(take(sizeof(int)));
+    ts->err = reinterpret_cast<int*>(take(sizeof(int)));
+}
+
+// G^T of a CSR whose targets were validated already, self-loops kept, with no
+// host synchronisation: the launches can be captured in a CUDA graph. Needs
+// n <= 2^24 (transpose_bucketed) and m within the scratch. Errors of the
+// passes' self-checks go to ts.err (device).
+int launch_transpose_keep_self(const int32_t* off, const int32_t* adj, int32_t n, int64_t m, const TransposeScratch& ts,
+                               int32_t* toff, int32_t* tadj, int num_sms, cudaStream_t s) {
+    const int shift = bucket_shift(n);
+    if (!transpose_bucketed(shift)) return SCC_ERR_INVALID_ARG;
+    const int nf = transpose_bins(n, shift);
+    SCC_CUDA(cudaMemsetAsync(ts.bcnt, 0, sizeof(unsigned long long) * ((size_t)nf + 2), s));
+    SCC_TRY(launch_copy_check_hist(adj, const_cast<int32_t*>(adj), n, m, shift, ts.bcnt, ts.bad, num_sms, s));
+    SCC_TRY(launch_tile_rows(off, n, m, ts.trow, s));
+    bool self_found = false;
+    return launch_transpose(off, adj, ts.trow, n, m, m, shift, ts.bcnt, ts.btmp, ts.tmp_u, ts.tmp_lv, ts.tmp2_u,
+                            ts.tmp2_lv, ts.order, ts.tiles, toff, tadj, nullptr, nullptr, &self_found, ts.err, num_sms,
+                            s, nullptr);
+}
+
+int transpose_set_attributes() { return ensure_attributes(); }
+int transpose_set_attributes_impl() {
+    SCC_CUDA(cudaFuncSetAttribute(k_copy_check_hist, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)(sizeof(unsigned int) * kMaxBins)));
+    SCC_CUDA(cudaFuncSetAttribute(k_bucket_part, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  2 * kStep * (int)sizeof(int32_t)));
+    SCC_CUDA(cudaFuncSetAttribute(k_bucket_split, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)((size_t)kSplitTile * (sizeof(int32_t) + sizeof(uint16_t)))));
+    SCC_CUDA(cudaFuncSetAttribute(k_sub_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rows_smem_bytes()));
     return SCC_OK;
 }
 

@@ -134,6 +134,26 @@ def test_batch_mixed_generator_and_autotune():
             assert np.array_equal(p.labels_of(lab, g), want_l[g]), g
 
 
+def test_batch_precomputed_transpose_spans_groups():
+    """The G^T computed before the launch is built for groups of consecutive
+    graphs of at most 2^24 vertices: 18 graphs of 10^6 vertices make two
+    groups (and an empty graph and a self-loop graph sit inside them). The
+    graphs at the group boundary and at both ends are checked."""
+    import torch
+    ensure_lib()
+    gs = [gg.torus(2, 1000, 0.5, seed=950 + i) for i in range(18)]
+    gs.insert(7, gg.from_edges(0, [], name="empty"))
+    gs.insert(12, gg.from_edges(3, [(0, 0), (0, 1), (1, 0), (2, 2)], name="self_loops"))
+    p = gg.pack(gs)
+    with scc.SccBatch(p) as B:
+        out = B.labels()
+        torch.cuda.synchronize()
+        lab = out.cpu().numpy()
+    for g in (0, 7, 12, 16, 17, 18, 19):
+        want, _ = oracle.scc_labels(p.graph(g).n, p.graph(g).offsets, p.graph(g).targets)
+        assert np.array_equal(p.labels_of(lab, g), want), g
+
+
 def test_batch_rejects_malformed_input():
     ensure_lib()
     g = gg.from_edges(3, [(0, 1), (1, 2)])
