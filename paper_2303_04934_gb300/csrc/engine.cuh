@@ -520,7 +520,7 @@ __device__ bool engine_search(const EngineParams<typename Pol::Item>& P, Pol& po
         Item* const in_slots = P.slots[ipar];
         SegState st{-1, 0, (uint32_t)(wid * 2654435761u) ^ gr};
         unsigned long long pushed = 0;
-        const long long in_end = i == 0 ? 0 : chunk_end(P.lambda, ld_volatile(&prev.bag.r), P.nslots);
+        long long in_end = i == 0 ? 0 : chunk_end(P.lambda, ld_volatile(&prev.bag.r), P.nslots);
         const long long fr_items = i == 0 ? ninit : ld_volatile(&prev.items);
         const int fr_hubs = i == 0 ? 0 : min(ld_volatile(&prev.nhub), P.hub_cap);
         bool dense = false;
@@ -536,20 +536,26 @@ __device__ bool engine_search(const EngineParams<typename Pol::Item>& P, Pol& po
         }
         if (dense) {
             if constexpr (Pol::kDense) {
-                // ---- dense round: frontier bitmap (the input bag, read and reset,
-                // and last round's hubs), then bottom-up over unvisited vertices
+                // ---- dense round: frontier bitmap, then bottom-up over unvisited
+                // vertices. After a dense round the bitmap is ready (that round
+                // wrote its new vertices into it, and into no bag); after a
+                // sparse one it is built from the input bag (read and reset)
+                // and last round's hubs.
                 uint32_t* fb = dp->fbits[par];
-                for (long long j = gtid; j < in_end; j += gstride) {
-                    const Item x = in_slots[j];
-                    if (x == Sent<Item>::empty) continue;
-                    in_slots[j] = Sent<Item>::empty;
-                    if (x == Sent<Item>::claimed) continue;
-                    const int v = pol.vertex(x);
-                    atomicOr(&fb[v >> 5], 1u << (v & 31));
-                }
-                for (long long j = gtid; j < fr_hubs; j += gstride) {
-                    const int v = pol.vertex(P.hub_item[ipar][j]);
-                    atomicOr(&fb[v >> 5], 1u << (v & 31));
+                uint32_t* nfb = dp->fbits[ipar];  // the next round's frontier (cleared above)
+                if (!prev_dense) {
+                    for (long long j = gtid; j < in_end; j += gstride) {
+                        const Item x = in_slots[j];
+                        if (x == Sent<Item>::empty) continue;
+                        in_slots[j] = Sent<Item>::empty;
+                        if (x == Sent<Item>::claimed) continue;
+                        const int v = pol.vertex(x);
+                        atomicOr(&fb[v >> 5], 1u << (v & 31));
+                    }
+                    for (long long j = gtid; j < fr_hubs; j += gstride) {
+                        const int v = pol.vertex(P.hub_item[ipar][j]);
+                        atomicOr(&fb[v >> 5], 1u << (v & 31));
+                    }
                 }
                 if (!S::sync(&ctl->bar, &ctl->err)) return false;
                 const long long nw = ((long long)P.n + 31) / 32;
@@ -626,22 +632,50 @@ __device__ bool engine_search(const EngineParams<typename Pol::Item>& P, Pol& po
                                 }
                             e[k] += 2;
                             if (f) atomicOr(&s_found[(vv[k] >> 5) - w0], 1u << (vv[k] & 31));
-                            pushed += bag_push<Item>(out, st, f, (Item)vv[k], wid, gr);
                             if (f || e[k] >= e1[k]) vv[k] = -1;
                         }
                     }
                     __syncwarp();
                     const uint32_t fm = s_found[lane];
-                    if (fm) pol.bits[w0 + lane] = mine | fm;  // fm != 0 only for words < nw
+                    if (fm) {  // fm != 0 only for words < nw
+                        pol.bits[w0 + lane] = mine | fm;
+                        nfb[w0 + lane] = fm;  // the new frontier
+                    }
                     int nf = __popc(fm);
                     for (int dd = 16; dd >= 1; dd >>= 1) nf += __shfl_xor_sync(kFull, nf, dd);
                     if (lane == 0) ws.items += nf;
+                    pushed += (unsigned long long)nf;
                     __syncwarp();  // the next group resets s_found
                 }
                 for (int dd = 16; dd >= 1; dd >>= 1) scanned += __shfl_xor_sync(kFull, scanned, dd);
                 if (lane == 0) ws.edges += scanned;
             }
         } else {
+            if constexpr (Pol::kDense) {
+                if (prev_dense) {
+                    // the last (dense) round left its new vertices in a bitmap:
+                    // push them into that round's bag (read and reset the words)
+                    // and read the bag as usual
+                    const BagRef<Item> pin{P.slots[ipar], P.nslots, P.lambda, P.sigma, &prev.bag, &cur.err,
+                                           &ctl->max_chunk};
+                    SegState pst{-1, 0, (uint32_t)(wid * 2654435761u) ^ (gr - 1u)};
+                    uint32_t* pfb = dp->fbits[par];
+                    const long long nw = ((long long)P.n + 31) / 32;
+                    for (long long w0 = (long long)wid * 32; w0 < nw; w0 += (long long)nwarps * 32) {
+                        const long long w = w0 + lane;
+                        uint32_t x = w < nw ? pfb[w] : 0u;
+                        if (x) pfb[w] = 0;
+                        while (__any_sync(kFull, x != 0)) {
+                            const int b = x ? __ffs(x) - 1 : 0;
+                            const bool has = x != 0;
+                            if (has) x &= x - 1;
+                            bag_push<Item>(pin, pst, has, (Item)(w * 32 + b), wid, gr - 1u);
+                        }
+                    }
+                    if (!S::sync(&ctl->bar, &ctl->err)) return false;
+                    in_end = chunk_end(P.lambda, ld_volatile(&prev.bag.r), P.nslots);
+                }
+            }
             // once a table overflows the round's work is moot: stop taking work
             // (lane 0 reads the flag for the warp, so the warp stays converged)
             auto stop = [&]() {
