@@ -585,9 +585,6 @@ static int scc_run_impl(scc_graph* h, int32_t* labels_out, cudaStream_t s) {
     EvTimer t(s);
     t.start();
     SCC_CUDA(cudaMemsetAsync(h->counters, 0, 4 * sizeof(unsigned long long), s));
-    SCC_CUDA(cudaMemsetAsync(h->fmax, 0, (size_t)n * 8, s));
-    SCC_CUDA(cudaMemsetAsync(h->bmax, 0, (size_t)n * 8, s));
-    SCC_CUDA(cudaMemsetAsync(h->hit, 0, (size_t)n * 8, s));
     SCC_TRY(launch_init_labels(h->off, h->toff, n, h->label, h->rep, &h->counters[0], s));
     SCC_TRY(launch_compact_active(h->label, n, h->scan_tmp, h->act, s));
     unsigned long long hc[4];
@@ -683,6 +680,10 @@ static int scc_run_impl(scc_graph* h, int32_t* labels_out, cudaStream_t s) {
             SCC_CUDA(cudaMemcpyAsync(h->bounds_d, bounds.data(), sizeof(long long) * (size_t)(nb + 1),
                                      cudaMemcpyHostToDevice, s));
             long long tab_alloc = std::max<long long>(1 << 14, pow2ceil(4 * (int64_t)std::ceil(0.3 * (double)(N - (int64_t)hc[1]))));
+            // the labelling maxima start untagged (only the batches use them)
+            SCC_CUDA(cudaMemsetAsync(h->fmax, 0, (size_t)n * 8, s));
+            SCC_CUDA(cudaMemsetAsync(h->bmax, 0, (size_t)n * 8, s));
+            SCC_CUDA(cudaMemsetAsync(h->hit, 0, (size_t)n * 8, s));
             BgssArgs a;
             a.off = h->off;
             a.adj = h->adj;

@@ -289,14 +289,21 @@ __global__ void __launch_bounds__(1024) k_fine_scan(const unsigned long long* __
         const long long r0 = (long long)start[(size_t)b << sublog], r1 = (long long)start[(size_t)(b + 1) << sublog];
         nt = r1 > r0 ? (unsigned long long)(((r1 - (r0 & ~7ll)) + kSplitTile - 1) / kSplitTile) : 0ull;
     }
-    unsigned long long ntot;
     const unsigned long long tb = block_scan_u64(nt, s_w, &s_tot);
-    ntot = s_tot;
-    if (b < nb) {
-        tile_base[b] = tb;
-        for (unsigned long long t = 0; t < nt; ++t) tile_bucket[tb + t] = b;
-    }
+    const unsigned long long ntot = s_tot;
+    if (b < nb) tile_base[b] = tb;
     if (threadIdx.x == 0) tile_base[nb] = ntot;
+    __syncthreads();
+    // bucket of every tile: the last b with tile_base[b] <= t (all threads)
+    for (unsigned long long t = threadIdx.x; t < ntot; t += blockDim.x) {
+        int lo = 0, hi = nb;
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (tile_base[mid] <= t) lo = mid;
+            else hi = mid;
+        }
+        tile_bucket[t] = lo;
+    }
 }
 
 // A2. partition: per 8k-arc tile, a shared-memory counting sort by bucket,
