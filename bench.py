@@ -752,13 +752,15 @@ def main():
             barrier()
             t0 = time.perf_counter()
             for _ in range(k2):
-                step(off_h, adj_h, lab_h)
+                st_e2e = step(off_h, adj_h, lab_h)
             torch.cuda.synchronize()
             t1 = time.perf_counter()
         barrier()
         te = max_over_ranks(t1 - t0, dist, "cuda")
         e2e = {"value": whole_job_rate(m * k2, world, te), "unit": UNIT, "h2d_bytes_per_step": 4 * (n + 1) + 4 * m,
-               "d2h_bytes_per_step": 4 * n, "steps": k2}
+               "d2h_bytes_per_step": 4 * n, "steps": k2, "ms_per_step": 1e3 * te / k2,
+               "create_ms_last_step": {k: st_e2e[k] for k in ("ms_create", "ms_transpose_hist", "ms_transpose_part",
+                                                              "ms_transpose_split", "ms_transpose_rows")}}
 
     # ---- CPU oracle on the host cores (rank 0, N = 1 only)
     cpu = None

@@ -330,7 +330,9 @@ struct CreateEvents {
     }
     double ms(int a, int b) {
         float t = 0;
-        return cudaEventElapsedTime(&t, e[a], e[b]) == cudaSuccess ? (double)t : 0.0;
+        if (cudaEventElapsedTime(&t, e[a], e[b]) == cudaSuccess) return (double)t;
+        cudaGetLastError();  // a pass that did not run recorded no events: not an error of later calls
+        return 0.0;
     }
 };
 
@@ -351,43 +353,94 @@ static int graph_create_impl(scc_graph* h, int32_t n, int64_t m, const int32_t* 
     // so is a page-locked host one (the pass reads it over the host link, so the
     // transfer and the pass are one); a pageable one is staged first
     const int32_t* src = targets;
+    bool host_src = false;
     if (m > 0 && !is_device_ptr(targets)) {
         if (const void* mp = mapped_host_ptr(targets)) {
             src = static_cast<const int32_t*>(mp);
+            host_src = true;
         } else {
             SCC_TRY(to_device(adj_in, targets, sizeof(int32_t) * (size_t)m, s));
             src = adj_in;
         }
     }
     const int shift = bucket_shift(n);
-    const int nb = std::max(1, (int)(((int64_t)n + (1ll << shift) - 1) >> shift));
+    const bool bucketed = transpose_bucketed(shift);
+    // host input: intake and partition in chunks on two streams, so that each
+    // chunk's partition runs while the next chunk crosses the host link
+    const int K = bucketed ? transpose_chunks(m, host_src) : 1;
     int* bad = nullptr;
     int32_t* selfrow = nullptr;
     unsigned long long *bcnt = nullptr, *btmp = nullptr;
     void* stmp = nullptr;
     SCC_TRY(dalloc_t(&bad, 1, s));
     SCC_TRY(dalloc_t(&selfrow, (size_t)n + 1, s));
-    const int nf = transpose_bins(n, shift);
-    SCC_TRY(dalloc_t(&bcnt, (size_t)nf + 2, s));  // [nf + 1]: self-loops found
-    SCC_TRY(dalloc_t(&btmp, 2 * ((size_t)nf + (size_t)nb) + 3, s));
+    const size_t hist_words = transpose_hist_words(n, shift, K);  // [hist_words - 1]: self-loops found
+    SCC_TRY(dalloc_t(&bcnt, hist_words, s));
+    SCC_TRY(dalloc_t(&btmp, transpose_tmp_words(n, shift, K), s));
     SCC_TRY(dalloc(&stmp, scan_tmp_bytes(n), s));
+    unsigned long long* self_cnt = bcnt + hist_words - 1;
     SCC_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), s));
     SCC_CUDA(cudaMemsetAsync(selfrow, 0, sizeof(int32_t) * ((size_t)n + 1), s));
-    SCC_CUDA(cudaMemsetAsync(bcnt, 0, sizeof(unsigned long long) * ((size_t)nf + 2), s));
+    SCC_CUDA(cudaMemsetAsync(bcnt, 0, sizeof(unsigned long long) * hist_words, s));
     // validation before any kernel indexes with these arrays: the offsets, then
-    // the targets within the intake pass (copy, range check, bucket histogram)
+    // the targets within the intake pass (copy, range check, histogram); the
+    // partition runs only if no target was out of range
     SCC_TRY(launch_validate_offsets(off_in, n, m, bad, s));
-    cudaEventRecord(ce.e[1], s);
-    SCC_TRY(launch_copy_check_hist(src, adj_in, n, m, shift, bcnt, bad, h->di.num_sms, s));
-    cudaEventRecord(ce.e[2], s);
+    int32_t* trow = nullptr;
+    SCC_TRY(dalloc_t(&trow, tile_rows_count(m), s));
+    SCC_TRY(launch_tile_rows(off_in, n, m, trow, s));
+    int32_t *tmp_u = nullptr, *tmp2_u = nullptr, *ord = nullptr, *tiles = nullptr;
+    uint16_t *tmp_lv = nullptr, *tmp2_lv = nullptr;
+    int* terr = nullptr;
+    cudaStream_t s2 = nullptr;
+    cudaEvent_t cev[9] = {};
+    auto release = [&]() {
+        dfree(tmp_u, s);
+        dfree(tmp_lv, s);
+        dfree(tmp2_u, s);
+        dfree(tmp2_lv, s);
+        dfree(tiles, s);
+        dfree(ord, s);
+        dfree(terr, s);
+        for (auto& e : cev)
+            if (e) cudaEventDestroy(e);
+        if (s2) cudaStreamDestroy(s2);
+        s2 = nullptr;
+        for (auto& e : cev) e = nullptr;
+    };
+    if (bucketed) {
+        SCC_TRY(dalloc_t(&tmp_u, (size_t)m + 8, s));
+        SCC_TRY(dalloc_t(&tmp_lv, (size_t)m + 8, s));
+        SCC_TRY(dalloc_t(&terr, 1, s));
+        SCC_CUDA(cudaMemsetAsync(terr, 0, sizeof(int), s));
+        if (K > 1) {
+            SCC_CUDA(cudaStreamCreateWithFlags(&s2, cudaStreamNonBlocking));
+            for (int k = 0; k <= K; ++k) SCC_CUDA(cudaEventCreateWithFlags(&cev[k], cudaEventDisableTiming));
+        }
+        const int rc = launch_intake_partition(src, adj_in, off_in, trow, n, m, shift, K, bcnt, btmp, tmp_u, tmp_lv,
+                                               selfrow, self_cnt, bad, terr, h->di.num_sms, s, s2, cev, &ce.e[1]);
+        if (rc != SCC_OK) {
+            release();
+            return rc;
+        }
+    } else {
+        cudaEventRecord(ce.e[1], s);
+        SCC_TRY(launch_copy_check_hist(src, adj_in, n, m, shift, bcnt, bad, h->di.num_sms, s));
+        cudaEventRecord(ce.e[2], s);
+    }
     int hbad = 0;
     SCC_CUDA(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
     SCC_CUDA(cudaStreamSynchronize(s));
     dfree(bad, s);
-    if (hbad) return SCC_ERR_INVALID_ARG;
-    int32_t* trow = nullptr;
-    SCC_TRY(dalloc_t(&trow, tile_rows_count(m), s));
-    SCC_TRY(launch_tile_rows(off_in, n, m, trow, s));
+    if (hbad) {
+        release();
+        dfree(trow, s);
+        dfree(selfrow, s);
+        dfree(bcnt, s);
+        dfree(btmp, s);
+        dfree(stmp, s);
+        return SCC_ERR_INVALID_ARG;
+    }
     h->mt = m;
     int64_t m_cur = m;
     // forward CSR without its self-loops (selfrow counts them per row)
@@ -409,58 +462,52 @@ static int graph_create_impl(scc_graph* h, int32_t n, int64_t m, const int32_t* 
         SCC_TRY(launch_tile_rows(h->off, n, m_cur, trow, s));  // rows of the new CSR's tiles
         return SCC_OK;
     };
-    // G^T: two-level bucketed counting sort by target (direct atomics when n is huge)
+    // G^T: three-level bucketed counting sort by target (direct atomics when n is huge)
     int32_t* toff = nullptr;
     SCC_TRY(dalloc_t(&toff, (size_t)n + 1, s));
     h->toff = toff;
     SCC_TRY(dalloc_t(&h->tadj, (size_t)m, s));
-    if (transpose_bucketed(shift)) {
-        int32_t *tmp_u = nullptr, *tmp2_u = nullptr, *ord = nullptr, *tiles = nullptr;
-        uint16_t *tmp_lv = nullptr, *tmp2_lv = nullptr;
-        int* terr = nullptr;
-        SCC_TRY(dalloc_t(&tmp_u, (size_t)m + 8, s));
-        SCC_TRY(dalloc_t(&tmp_lv, (size_t)m + 8, s));
-        SCC_TRY(dalloc_t(&tmp2_u, (size_t)m + 8, s));
-        SCC_TRY(dalloc_t(&tmp2_lv, (size_t)m + 8, s));
-        SCC_TRY(dalloc_t(&ord, (size_t)nf, s));
-        SCC_TRY(dalloc_t(&tiles, transpose_split_tiles(m, n, shift), s));
-        SCC_TRY(dalloc_t(&terr, 1, s));
-        SCC_CUDA(cudaMemsetAsync(terr, 0, sizeof(int), s));
-        for (int attempt = 0;; ++attempt) {
+    if (bucketed) {
+        int rc = SCC_OK;
+        if (rc == SCC_OK) rc = dalloc_t(&tmp2_u, (size_t)m + 8, s);
+        if (rc == SCC_OK) rc = dalloc_t(&tmp2_lv, (size_t)m + 8, s);
+        if (rc == SCC_OK) rc = dalloc_t(&ord, (size_t)transpose_bins(n, shift), s);
+        if (rc == SCC_OK) rc = dalloc_t(&tiles, transpose_split_tiles(m, n, shift), s);
+        int k_cur = K;
+        for (int attempt = 0; rc == SCC_OK; ++attempt) {
             bool self_found = false;
-            SCC_TRY(launch_transpose(h->off, h->adj, trow, n, m_cur, m_cur, shift, bcnt, btmp, tmp_u, tmp_lv, tmp2_u,
-                                     tmp2_lv, ord, tiles, toff, h->tadj, selfrow, bcnt + nf + 1, &self_found, terr,
-                                     h->di.num_sms, s, &ce.e[3]));
-            if (!self_found) break;
-            if (attempt > 0) return SCC_ERR_INTERNAL;  // the rebuilt CSR has no self-loops
+            rc = launch_transpose_rest(n, m_cur, shift, k_cur, bcnt, btmp, tmp_u, tmp_lv, tmp2_u, tmp2_lv, ord, tiles,
+                                       toff, h->tadj, self_cnt, &self_found, terr, h->di.num_sms, s, &ce.e[5]);
+            if (rc != SCC_OK || !self_found) break;
+            if (attempt > 0) {
+                rc = SCC_ERR_INTERNAL;  // the rebuilt CSR has no self-loops
+                break;
+            }
             // self-loops: rebuild the forward CSR without them and start over
             unsigned long long hself = 0;
-            SCC_CUDA(cudaMemcpyAsync(&hself, bcnt + nf + 1, sizeof(hself), cudaMemcpyDeviceToHost, s));
-            SCC_CUDA(cudaStreamSynchronize(s));
-            SCC_TRY(drop_self_loops(hself));
-            SCC_CUDA(cudaMemsetAsync(bcnt, 0, sizeof(unsigned long long) * ((size_t)nf + 2), s));
-            int* bad2 = nullptr;
-            SCC_TRY(dalloc_t(&bad2, 1, s));
-            SCC_TRY(launch_copy_check_hist(h->adj, h->adj, n, m_cur, shift, bcnt, bad2, h->di.num_sms, s));
-            dfree(bad2, s);  // nothing to report: the targets were checked above
+            rc = cuda_err(cudaMemcpyAsync(&hself, self_cnt, sizeof(hself), cudaMemcpyDeviceToHost, s));
+            if (rc == SCC_OK) rc = cuda_err(cudaStreamSynchronize(s));
+            if (rc == SCC_OK) rc = drop_self_loops(hself);
+            k_cur = 1;
+            if (rc == SCC_OK)  // histograms and the self-loop count start over
+                rc = cuda_err(cudaMemsetAsync(bcnt, 0, sizeof(unsigned long long) * hist_words, s));
+            if (rc == SCC_OK)
+                rc = launch_intake_partition(h->adj, h->adj, h->off, trow, n, m_cur, shift, 1, bcnt, btmp, tmp_u,
+                                             tmp_lv, nullptr, nullptr, nullptr, terr, h->di.num_sms, s, s, nullptr,
+                                             &ce.e[1]);
         }
         int herr = 0;
-        SCC_CUDA(cudaMemcpyAsync(&herr, terr, sizeof(int), cudaMemcpyDeviceToHost, s));
-        SCC_CUDA(cudaStreamSynchronize(s));
-        dfree(tmp_u, s);
-        dfree(tmp_lv, s);
-        dfree(tmp2_u, s);
-        dfree(tmp2_lv, s);
-        dfree(tiles, s);
-        dfree(ord, s);
-        dfree(terr, s);
+        if (rc == SCC_OK) rc = cuda_err(cudaMemcpyAsync(&herr, terr, sizeof(int), cudaMemcpyDeviceToHost, s));
+        if (rc == SCC_OK) rc = cuda_err(cudaStreamSynchronize(s));
+        release();
+        if (rc != SCC_OK) return rc;
         if (herr) return herr;
     } else {
         // self-loops from the row-aware histogram pass, then direct placement
-        SCC_CUDA(cudaMemsetAsync(bcnt, 0, sizeof(unsigned long long) * ((size_t)nf + 2), s));
-        SCC_TRY(launch_bucket_hist(h->off, h->adj, trow, n, m, shift, bcnt, selfrow, bcnt + nf + 1, h->di.num_sms, s));
+        SCC_CUDA(cudaMemsetAsync(bcnt, 0, sizeof(unsigned long long) * hist_words, s));
+        SCC_TRY(launch_bucket_hist(h->off, h->adj, trow, n, m, shift, bcnt, selfrow, self_cnt, h->di.num_sms, s));
         unsigned long long hself = 0;
-        SCC_CUDA(cudaMemcpyAsync(&hself, bcnt + nf + 1, sizeof(hself), cudaMemcpyDeviceToHost, s));
+        SCC_CUDA(cudaMemcpyAsync(&hself, self_cnt, sizeof(hself), cudaMemcpyDeviceToHost, s));
         SCC_CUDA(cudaStreamSynchronize(s));
         if (hself > 0) SCC_TRY(drop_self_loops(hself));
         int32_t* indeg = nullptr;

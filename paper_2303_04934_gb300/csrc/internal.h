@@ -73,22 +73,39 @@ int launch_copy_check_hist(const int32_t* src, int32_t* dst, int32_t n, int64_t 
 int launch_bucket_hist(const int32_t* off, const int32_t* adj, const int32_t* trow, int32_t n, int64_t m, int shift,
                        unsigned long long* bucket_cnt, int32_t* selfrow, unsigned long long* nself, int num_sms,
                        cudaStream_t s);
-// G^T of the CSR (off, adj) with m arcs, by the three-level bucketed counting
-// sort (when transpose_bucketed(shift)); bucket_cnt from launch_copy_check_hist.
-// bucket_tmp: 2 * (transpose_bins + nbuckets) + 3 words; tmp_u, tmp2_u: m + 8
-// entries, tmp_lv, tmp2_lv: m + 8 entries (the padding is read, never used);
-// order_tmp: transpose_bins entries; tile_tmp: transpose_split_tiles entries.
-size_t transpose_split_tiles(int64_t m, int32_t n, int shift);
-// If the CSR has self-loops, nothing is written to toff/tadj: *self_found is
-// set, selfrow[u] (zeroed by the caller) counts u's self-loops and *nself
-// (zeroed by the caller) their total.
+// G^T of the CSR (off, adj) with m arcs by the three-level bucketed counting
+// sort (when transpose_bucketed(shift)), in two calls:
+//  * launch_intake_partition: in K chunks of whole tiles (transpose_chunks:
+//    1 unless `overlap`), the intake of the targets (src -> adj, no copy when
+//    equal; targets outside [0, n) set *bad) with a per-chunk sub-bucket
+//    histogram (hist: K x transpose_bins words), then the chunk's partition
+//    into its buckets (skipped once *bad is set). With K > 1 the partitions run
+//    on s2 after each chunk's intake on s (events cev[0..K]), so a chunk's
+//    partition overlaps the next chunk's intake; s waits for the last one.
+//    selfrow == nullptr: self-loops are kept (not counted).
+//  * launch_transpose_rest: sub-bucket offsets, the split into sub-buckets and
+//    the rows. With nself != nullptr, self-loops found by the partition are
+//    reported (*self_found; nothing is written to toff/tadj) after a host read;
+//    with nullptr nothing is read back (the launches can be captured).
+// bucket_tmp: transpose_tmp_words; tmp_u, tmp2_u, tmp_lv, tmp2_lv: m + 8
+// entries (the padding is read, never used); order_tmp: transpose_bins
+// entries; tile_tmp: transpose_split_tiles entries. Events: ev[0..3] around
+// the intakes (s) and the partitions (their stream); around the split and the
+// rows.
 bool transpose_bucketed(int shift);
-int launch_transpose(const int32_t* off, const int32_t* adj, const int32_t* trow, int32_t n, int64_t m, int64_t mt,
-                     int shift, const unsigned long long* bucket_cnt, unsigned long long* bucket_tmp, int32_t* tmp_u,
-                     uint16_t* tmp_lv, int32_t* tmp2_u, uint16_t* tmp2_lv, int32_t* order_tmp, int32_t* tile_tmp,
-                     int32_t* toff, int32_t* tadj, int32_t* selfrow, unsigned long long* nself, bool* self_found,
-                     int* err, int num_sms, cudaStream_t s,
-                     cudaEvent_t* ev = nullptr);  // ev[0..5]: around the partition, split and rows passes
+int transpose_chunks(int64_t m, bool overlap);
+size_t transpose_hist_words(int32_t n, int shift, int K);
+size_t transpose_tmp_words(int32_t n, int shift, int K);
+size_t transpose_split_tiles(int64_t m, int32_t n, int shift);
+int launch_intake_partition(const int32_t* src, int32_t* adj, const int32_t* off, const int32_t* trow, int32_t n,
+                            int64_t m, int shift, int K, unsigned long long* hist, unsigned long long* bucket_tmp,
+                            int32_t* tmp_u, uint16_t* tmp_lv, int32_t* selfrow, unsigned long long* nself, int* bad,
+                            int* err, int num_sms, cudaStream_t s, cudaStream_t s2, cudaEvent_t* cev, cudaEvent_t* ev);
+int launch_transpose_rest(int32_t n, int64_t mt, int shift, int K, const unsigned long long* hist,
+                          unsigned long long* bucket_tmp, const int32_t* tmp_u, const uint16_t* tmp_lv, int32_t* tmp2_u,
+                          uint16_t* tmp2_lv, int32_t* order_tmp, int32_t* tile_tmp, int32_t* toff, int32_t* tadj,
+                          const unsigned long long* nself, bool* self_found, int* err, int num_sms, cudaStream_t s,
+                          cudaEvent_t* ev);
 // G^T without host synchronisation for packed groups of graphs (batch.cu):
 // self-loops are kept (they change no reachability), targets must be valid.
 struct TransposeScratch {

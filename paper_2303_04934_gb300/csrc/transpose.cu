@@ -48,6 +48,7 @@ constexpr int kBucketLog = 15;          // at most 2^15 vertices per bucket (16-
 constexpr int kSubLog = 5;              // at most 2^5 sub-buckets per bucket
 constexpr int kMaxSubVertsLog = 10;     // at most 2^10 vertices per sub-bucket
 constexpr int kMaxBins = kMaxBuckets << kSubLog;  // 16384 sub-buckets
+constexpr int kMaxChunks = 8;                     // intake/partition chunks (host input)
 constexpr int kBlkA = 512;
 static_assert(kMaxBuckets <= kBlkA, "bucket scan uses one thread per bucket");
 constexpr int kChunk = 16;              // consecutive arcs per thread per step
@@ -244,76 +245,110 @@ __device__ __forceinline__ unsigned long long block_scan_u64(unsigned long long 
     return r;
 }
 
-// One block of 1024 threads over the nf sub-bucket counts: start[0 .. nf]
-// (exclusive scan) and gcur = start (the split pass's cursors), cursor[b] =
-// start[b << sublog] (bucket b's partition run), order = the sub-buckets with
-// more than kWinArcs arcs, then the others (each group increasing), the split
-// pass's tiles (bucket b's run, from its first multiple of 8, in tiles of
-// kSplitTile arcs: tile_base[b] = its first tile, tile_bucket[t] = the bucket of
-// tile t), counters[0] = 0 (work counter of the rows pass).
-__global__ void __launch_bounds__(1024) k_fine_scan(const unsigned long long* __restrict__ cnt, int nf, int sublog,
+// One block of 512 threads: chunk c's partition cursors. Bucket b's arcs of
+// the chunk form segment (c, b) = [seg_start, seg_start + seg_len), laid out in
+// bucket order from the chunk's first arc base (the chunk's arcs keep their
+// range); cursor = seg_start (advanced by the partition's reservations).
+__global__ void __launch_bounds__(512) k_chunk_cursor(const unsigned long long* __restrict__ hist, int nb, int sublog,
+                                                     long long base, unsigned long long* seg_start,
+                                                     unsigned long long* seg_len, unsigned long long* cursor) {
+    __shared__ unsigned long long s_w[32];
+    __shared__ unsigned long long s_tot;
+    const int b = threadIdx.x;
+    unsigned long long len = 0;
+    if (b < nb)
+        for (int q = 0; q < (1 << sublog); ++q) len += hist[((size_t)b << sublog) + q];
+    const unsigned long long pre = block_scan_u64(len, s_w, &s_tot);
+    if (b < nb) {
+        seg_start[b] = (unsigned long long)base + pre;
+        seg_len[b] = len;
+        cursor[b] = (unsigned long long)base + pre;
+    }
+}
+
+// One block of 1024 threads over the sub-bucket counts (the sum of K chunk
+// histograms of nf bins): start[0 .. nf] (exclusive scan) and gcur = start
+// (the split pass's cursors), order = the sub-buckets with more than kWinArcs
+// arcs, then the others (each group increasing), the split pass's tiles (each
+// segment, from its first multiple of 8, in tiles of kSplitTile arcs:
+// tile_base[g] = the first tile of segment g = c * nb + b, tile_seg[t] = the
+// segment of tile t), counters[0] = 0 (work counter of the rows pass).
+__global__ void __launch_bounds__(1024) k_fine_scan(const unsigned long long* __restrict__ hist, int K, int nf,
                                                    int nb, unsigned long long* start, unsigned long long* gcur,
-                                                   unsigned long long* cursor, int32_t* order,
-                                                   unsigned long long* tile_base, int32_t* tile_bucket,
+                                                   int32_t* order, const unsigned long long* __restrict__ seg_start,
+                                                   const unsigned long long* __restrict__ seg_len,
+                                                   unsigned long long* tile_base, int32_t* tile_seg,
                                                    unsigned int* counters) {
     __shared__ unsigned long long s_w[32];
     __shared__ unsigned long long s_tot, s_hot;
+    auto count = [&](int i) {
+        unsigned long long c = 0;
+        for (int k = 0; k < K; ++k) c += hist[(size_t)k * nf + i];
+        return c;
+    };
     const int per = (nf + (int)blockDim.x - 1) / (int)blockDim.x;
     const int i0 = min((int)threadIdx.x * per, nf), i1 = min(i0 + per, nf);
     unsigned long long sum = 0, hot = 0;
     for (int i = i0; i < i1; ++i) {
-        sum += cnt[i];
-        hot += cnt[i] > (unsigned long long)kWinArcs;
+        const unsigned long long c = count(i);
+        sum += c;
+        hot += c > (unsigned long long)kWinArcs;
     }
     unsigned long long run = block_scan_u64(sum, s_w, &s_tot);
     const unsigned long long hbase = block_scan_u64(hot, s_w, &s_hot);
     const unsigned long long nhot = s_hot;
     unsigned long long h = hbase, c = nhot + ((unsigned long long)i0 - hbase);
     for (int i = i0; i < i1; ++i) {
+        const unsigned long long ci = count(i);
         start[i] = run;
         gcur[i] = run;
-        run += cnt[i];
-        if (cnt[i] > (unsigned long long)kWinArcs) order[h++] = i;
+        run += ci;
+        if (ci > (unsigned long long)kWinArcs) order[h++] = i;
         else order[c++] = i;
     }
     if (threadIdx.x == 0) {
         start[nf] = s_tot;
         counters[0] = 0;
     }
-    __syncthreads();
-    for (int b = threadIdx.x; b < nb; b += blockDim.x) cursor[b] = start[(size_t)b << sublog];
-    // split tiles per bucket (nb <= 1024: one bucket per thread)
+    // split tiles per segment (up to 8 x 512 segments: a run of them per thread)
+    const int ns = K * nb;
+    const int sper = (ns + (int)blockDim.x - 1) / (int)blockDim.x;
+    const int s0 = min((int)threadIdx.x * sper, ns), s1 = min(s0 + sper, ns);
+    auto tiles_of = [&](int g) {
+        const long long r0 = (long long)seg_start[g], r1 = r0 + (long long)seg_len[g];
+        return r1 > r0 ? (unsigned long long)(((r1 - (r0 & ~7ll)) + kSplitTile - 1) / kSplitTile) : 0ull;
+    };
     unsigned long long nt = 0;
-    const int b = threadIdx.x;
-    if (b < nb) {
-        const long long r0 = (long long)start[(size_t)b << sublog], r1 = (long long)start[(size_t)(b + 1) << sublog];
-        nt = r1 > r0 ? (unsigned long long)(((r1 - (r0 & ~7ll)) + kSplitTile - 1) / kSplitTile) : 0ull;
-    }
-    const unsigned long long tb = block_scan_u64(nt, s_w, &s_tot);
+    for (int g = s0; g < s1; ++g) nt += tiles_of(g);
+    unsigned long long tb = block_scan_u64(nt, s_w, &s_tot);
     const unsigned long long ntot = s_tot;
-    if (b < nb) tile_base[b] = tb;
-    if (threadIdx.x == 0) tile_base[nb] = ntot;
+    for (int g = s0; g < s1; ++g) {
+        tile_base[g] = tb;
+        tb += tiles_of(g);
+    }
+    if (threadIdx.x == 0) tile_base[ns] = ntot;
     __syncthreads();
-    // bucket of every tile: the last b with tile_base[b] <= t (all threads)
+    // segment of every tile: the last g with tile_base[g] <= t (all threads)
     for (unsigned long long t = threadIdx.x; t < ntot; t += blockDim.x) {
-        int lo = 0, hi = nb;
+        int lo = 0, hi = ns;
         while (hi - lo > 1) {
             const int mid = (lo + hi) >> 1;
             if (tile_base[mid] <= t) lo = mid;
             else hi = mid;
         }
-        tile_bucket[t] = lo;
+        tile_seg[t] = lo;
     }
 }
 
 // A2. partition: per 8k-arc tile, a shared-memory counting sort by bucket,
 // one global reservation per non-empty bucket, then a coalesced write-out.
 __global__ void __launch_bounds__(kBlkA) k_bucket_part(const int32_t* __restrict__ off, const int32_t* __restrict__ adj,
-                                                       const int32_t* __restrict__ trow, int32_t n, int64_t m,
-                                                       int shift, int nb,
+                                                       const int32_t* __restrict__ trow, int32_t n, int64_t a_lo,
+                                                       int64_t a_hi, int shift, int nb,
                                                        unsigned long long* cursor, int32_t* out_u, uint16_t* out_lv,
                                                        unsigned long long mt, int32_t* selfrow,
-                                                       unsigned long long* nself, int* err) {
+                                                       unsigned long long* nself, const int* bad, int* err) {
+    if (bad != nullptr && ld_volatile(bad) != 0) return;  // a target out of range: nothing is partitioned
     __shared__ int32_t s_off[kRowsCap];
     __shared__ unsigned int s_cnt[kMaxBuckets];
     __shared__ unsigned int s_start[kMaxBuckets];
@@ -323,8 +358,8 @@ __global__ void __launch_bounds__(kBlkA) k_bucket_part(const int32_t* __restrict
     int32_t* s_v = s_stage + kStep;
     __shared__ unsigned int s_wsum[kBlkA / 32];
     __shared__ unsigned int s_total;
-    for (int64_t t0 = (int64_t)blockIdx.x * kStep; t0 < m; t0 += (int64_t)gridDim.x * kStep) {
-        const int64_t t1 = min(t0 + (int64_t)kStep, m);
+    for (int64_t t0 = a_lo + (int64_t)blockIdx.x * kStep; t0 < a_hi; t0 += (int64_t)gridDim.x * kStep) {
+        const int64_t t1 = min(t0 + (int64_t)kStep, a_hi);
         for (int i = threadIdx.x; i < nb; i += blockDim.x) s_cnt[i] = 0;
         __syncthreads();
         // ranks within (tile, bucket), kept per thread
@@ -413,17 +448,19 @@ struct SplitLoad {
     uint4 lv;
     int4 ua, ub;
     long long c, r0, r1;
-    int b;
+    int b;  // the bucket
 };
 __device__ __forceinline__ SplitLoad split_load(const int32_t* __restrict__ uu, const uint16_t* __restrict__ lvv,
-                                                const unsigned long long* __restrict__ start,
+                                                const unsigned long long* __restrict__ seg_start,
+                                                const unsigned long long* __restrict__ seg_len,
                                                 const unsigned long long* __restrict__ tile_base,
-                                                const int32_t* __restrict__ tile_bucket, int sublog, long long t) {
+                                                const int32_t* __restrict__ tile_seg, int nb, long long t) {
     SplitLoad L;
-    L.b = __ldg(&tile_bucket[t]);
-    L.r0 = (long long)__ldg(&start[(size_t)L.b << sublog]);
-    L.r1 = (long long)__ldg(&start[(size_t)(L.b + 1) << sublog]);
-    L.c = (L.r0 & ~7ll) + ((long long)t - (long long)__ldg(&tile_base[L.b])) * kSplitTile + 8ll * threadIdx.x;
+    const int g = __ldg(&tile_seg[t]);
+    L.b = g % nb;
+    L.r0 = (long long)__ldg(&seg_start[g]);
+    L.r1 = L.r0 + (long long)__ldg(&seg_len[g]);
+    L.c = (L.r0 & ~7ll) + ((long long)t - (long long)__ldg(&tile_base[g])) * kSplitTile + 8ll * threadIdx.x;
     const bool in = L.c < L.r1;
     L.lv = in ? __ldg(reinterpret_cast<const uint4*>(lvv + L.c)) : make_uint4(0, 0, 0, 0);
     L.ua = in ? __ldg(reinterpret_cast<const int4*>(uu + L.c)) : make_int4(0, 0, 0, 0);
@@ -434,8 +471,10 @@ __device__ __forceinline__ SplitLoad split_load(const int32_t* __restrict__ uu, 
 __global__ void __launch_bounds__(kBlkS, 1) k_bucket_split(const int32_t* __restrict__ uu,
                                                            const uint16_t* __restrict__ lvv,
                                                            const unsigned long long* __restrict__ start,
+                                                           const unsigned long long* __restrict__ seg_start,
+                                                           const unsigned long long* __restrict__ seg_len,
                                                            const unsigned long long* __restrict__ tile_base,
-                                                           const int32_t* __restrict__ tile_bucket, int nb,
+                                                           const int32_t* __restrict__ tile_seg, int nseg, int nb,
                                                            int sublog, int sb, unsigned long long* gcur, int32_t* u2,
                                                            uint16_t* lv2, int* err) {
     __shared__ unsigned int s_tcnt[1 << kSubLog];
@@ -445,14 +484,14 @@ __global__ void __launch_bounds__(kBlkS, 1) k_bucket_split(const int32_t* __rest
     uint16_t* s_lv = reinterpret_cast<uint16_t*>(s_u + kSplitTile);  // [kSplitTile]
     const int S = 1 << sublog;
     const unsigned int lmask = (1u << sb) - 1u;
-    const long long ntiles = (long long)tile_base[nb];
+    const long long ntiles = (long long)tile_base[nseg];
     long long t = blockIdx.x;
     if (t >= ntiles) return;
-    SplitLoad cur = split_load(uu, lvv, start, tile_base, tile_bucket, sublog, t);
+    SplitLoad cur = split_load(uu, lvv, seg_start, seg_len, tile_base, tile_seg, nb, t);
     for (; t < ntiles; t += gridDim.x) {
         const long long tn = t + gridDim.x;
         SplitLoad nxt;
-        if (tn < ntiles) nxt = split_load(uu, lvv, start, tile_base, tile_bucket, sublog, tn);
+        if (tn < ntiles) nxt = split_load(uu, lvv, seg_start, seg_len, tile_base, tile_seg, nb, tn);
         if (threadIdx.x < (unsigned)S) s_tcnt[threadIdx.x] = 0;
         __syncthreads();
         const size_t f0 = (size_t)cur.b << sublog;
@@ -717,41 +756,108 @@ int launch_transpose_direct(const int32_t* off, const int32_t* adj, const int32_
 
 bool transpose_bucketed(int shift) { return shift <= kBucketLog; }
 
-int launch_transpose(const int32_t* off, const int32_t* adj, const int32_t* trow, int32_t n, int64_t m, int64_t mt,
-                     int shift, const unsigned long long* bucket_cnt, unsigned long long* bucket_tmp, int32_t* tmp_u,
-                     uint16_t* tmp_lv, int32_t* tmp2_u, uint16_t* tmp2_lv, int32_t* order_tmp, int32_t* tile_bucket,
-                     int32_t* toff, int32_t* tadj, int32_t* selfrow, unsigned long long* nself, bool* self_found,
-                     int* err, int num_sms, cudaStream_t s, cudaEvent_t* ev) {
-    // selfrow == nullptr: self-loops are kept as arcs of G^T and nothing is read
+int transpose_chunks(int64_t m, bool overlap) {
+    if (!overlap) return 1;
+    const int64_t T = (m + kStep - 1) / kStep;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(kMaxChunks, T / 64));
+}
+size_t transpose_hist_words(int32_t n, int shift, int K) { return (size_t)K * transpose_bins(n, shift) + 2; }
+size_t transpose_tmp_words(int32_t n, int shift, int K) {
+    const int nb = std::max(1, (int)(((int64_t)n + (1ll << shift) - 1) >> shift));
+    return 2 * (size_t)transpose_bins(n, shift) + 4 * (size_t)K * nb + 4;
+}
+
+namespace {
+// bucket_tmp: start [nf + 1] | gcur [nf] | tile_base [K nb + 1] | counter |
+// seg_start [K nb] | seg_len [K nb] | cursor [K nb]
+struct TmpLayout {
+    unsigned long long *start, *gcur, *tile_base, *seg_start, *seg_len, *cursor;
+    unsigned int* counters;
+};
+TmpLayout tmp_layout(unsigned long long* t, int nf, int nb, int K) {
+    TmpLayout L;
+    L.start = t;
+    L.gcur = L.start + nf + 1;
+    L.tile_base = L.gcur + nf;
+    L.counters = reinterpret_cast<unsigned int*>(L.tile_base + (size_t)K * nb + 1);
+    L.seg_start = L.tile_base + (size_t)K * nb + 2;
+    L.seg_len = L.seg_start + (size_t)K * nb;
+    L.cursor = L.seg_len + (size_t)K * nb;
+    return L;
+}
+}  // namespace
+
+int launch_intake_partition(const int32_t* src, int32_t* adj, const int32_t* off, const int32_t* trow, int32_t n,
+                            int64_t m, int shift, int K, unsigned long long* hist, unsigned long long* bucket_tmp,
+                            int32_t* tmp_u, uint16_t* tmp_lv, int32_t* selfrow, unsigned long long* nself, int* bad,
+                            int* err, int num_sms, cudaStream_t s, cudaStream_t s2, cudaEvent_t* cev, cudaEvent_t* ev) {
+    const int nb = std::max(1, (int)(((int64_t)n + (1ll << shift) - 1) >> shift));
+    const int sublog = sub_log(shift);
+    const int nf = nb << sublog;
+    const TmpLayout T = tmp_layout(bucket_tmp, nf, nb, K);
+    SCC_TRY(ensure_attributes());
+    SCC_CUDA(cudaMemsetAsync(hist, 0, sizeof(unsigned long long) * (size_t)K * nf, s));
+    if (n == 0) return SCC_OK;
+    const int64_t tiles = (m + kStep - 1) / kStep;
+    const int64_t tpc = (tiles + K - 1) / K;  // tiles per chunk
+    cudaStream_t sp = K > 1 ? s2 : s;          // the partitions' stream
+    if (ev) cudaEventRecord(ev[0], s);
+    for (int c = 0; c < K; ++c) {
+        const int64_t e0 = std::min<int64_t>(m, (int64_t)c * tpc * kStep);
+        const int64_t e1 = std::min<int64_t>(m, (int64_t)(c + 1) * tpc * kStep);
+        unsigned long long* hc = hist + (size_t)c * nf;
+        if (e1 > e0) {
+            // chunk c's intake (a multiple of kStep arcs in: 16-byte aligned)
+            k_copy_check_hist<<<grid_for_arcs(e1 - e0, 4 * kBlkA * 4, num_sms, 2), kBlkA, sizeof(unsigned int) * nf,
+                                s>>>(src + e0, adj + e0, e1 - e0, n, sub_vert_log(shift), nf, hc, bad);
+            SCC_LAUNCH();
+        }
+        if (ev && c == K - 1) cudaEventRecord(ev[1], s);  // the last intake
+        if (K > 1) {
+            SCC_CUDA(cudaEventRecord(cev[c], s));
+            SCC_CUDA(cudaStreamWaitEvent(sp, cev[c], 0));
+        }
+        if (ev && c == 0) cudaEventRecord(ev[2], sp);
+        k_chunk_cursor<<<1, 512, 0, sp>>>(hc, nb, sublog, (long long)e0, T.seg_start + (size_t)c * nb,
+                                         T.seg_len + (size_t)c * nb, T.cursor + (size_t)c * nb);
+        SCC_LAUNCH();
+        if (e1 > e0) {
+            const int stage = 2 * kStep * (int)sizeof(int32_t);
+            k_bucket_part<<<grid_for_arcs(e1 - e0, kStep, num_sms, 2), kBlkA, stage, sp>>>(
+                off, adj, trow, n, e0, e1, shift, nb, T.cursor + (size_t)c * nb, tmp_u, tmp_lv, (unsigned long long)m,
+                selfrow, nself, bad, err);
+            SCC_LAUNCH();
+        }
+    }
+    if (ev) cudaEventRecord(ev[3], sp);
+    if (K > 1) {  // the stream continues after the last partition
+        SCC_CUDA(cudaEventRecord(cev[K], sp));
+        SCC_CUDA(cudaStreamWaitEvent(s, cev[K], 0));
+    }
+    return SCC_OK;
+}
+
+int launch_transpose_rest(int32_t n, int64_t mt, int shift, int K, const unsigned long long* hist,
+                          unsigned long long* bucket_tmp, const int32_t* tmp_u, const uint16_t* tmp_lv, int32_t* tmp2_u,
+                          uint16_t* tmp2_lv, int32_t* order_tmp, int32_t* tile_tmp, int32_t* toff, int32_t* tadj,
+                          const unsigned long long* nself, bool* self_found, int* err, int num_sms, cudaStream_t s,
+                          cudaEvent_t* ev) {
+    // nself == nullptr: self-loops are kept as arcs of G^T and nothing is read
     // back to the host (the launches can be captured in a CUDA graph)
     *self_found = false;
     const int nb = std::max(1, (int)(((int64_t)n + (1ll << shift) - 1) >> shift));
     const int sb = sub_vert_log(shift), sublog = sub_log(shift);
     const int nf = nb << sublog;
-    unsigned long long* start = bucket_tmp;                       // [nf + 1]
-    unsigned long long* gcur = start + nf + 1;                    // [nf]
-    unsigned long long* cursor = gcur + nf;                       // [nb]
-    unsigned long long* tile_base = cursor + nb;                  // [nb + 1]
-    unsigned int* counters = reinterpret_cast<unsigned int*>(tile_base + nb + 1);  // rows pass
+    const TmpLayout T = tmp_layout(bucket_tmp, nf, nb, K);
     if (n == 0) {
         SCC_CUDA(cudaMemsetAsync(toff, 0, sizeof(int32_t), s));
         return SCC_OK;
     }
-    k_fine_scan<<<1, 1024, 0, s>>>(bucket_cnt, nf, sublog, nb, start, gcur, cursor, order_tmp, tile_base, tile_bucket,
-                                   counters);
+    SCC_TRY(ensure_attributes());
+    k_fine_scan<<<1, 1024, 0, s>>>(hist, K, nf, nb, T.start, T.gcur, order_tmp, T.seg_start, T.seg_len, T.tile_base,
+                                   tile_tmp, T.counters);
     SCC_LAUNCH();
-    if (mt > 0) {
-        const int stage = 2 * kStep * (int)sizeof(int32_t);
-        SCC_TRY(ensure_attributes());
-        if (ev) cudaEventRecord(ev[0], s);
-        k_bucket_part<<<grid_for_arcs(m, kStep, num_sms, 2), kBlkA, stage, s>>>(off, adj, trow, n, m, shift, nb, cursor,
-                                                                                  tmp_u, tmp_lv,
-                                                                                  (unsigned long long)mt, selfrow,
-                                                                                  nself, err);
-        SCC_LAUNCH();
-        if (ev) cudaEventRecord(ev[1], s);
-    }
-    if (selfrow != nullptr) {
+    if (nself != nullptr) {
         unsigned long long hself = 0;
         SCC_CUDA(cudaMemcpyAsync(&hself, nself, sizeof(hself), cudaMemcpyDeviceToHost, s));
         SCC_CUDA(cudaStreamSynchronize(s));
@@ -762,23 +868,23 @@ int launch_transpose(const int32_t* off, const int32_t* adj, const int32_t* trow
     }
     int per_sm = 0;
     const size_t split_smem = (size_t)kSplitTile * (sizeof(int32_t) + sizeof(uint16_t));
-    SCC_TRY(ensure_attributes());
     SCC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bucket_split, kBlkS, split_smem));
-    if (ev) cudaEventRecord(ev[2], s);
+    if (ev) cudaEventRecord(ev[0], s);
     if (mt > 0) {  // the tile count is read on the device; spare blocks return at once
-        k_bucket_split<<<num_sms * std::max(1, per_sm), kBlkS, split_smem, s>>>(tmp_u, tmp_lv, start, tile_base,
-                                                                               tile_bucket, nb, sublog, sb, gcur,
-                                                                               tmp2_u, tmp2_lv, err);
+        k_bucket_split<<<num_sms * std::max(1, per_sm), kBlkS, split_smem, s>>>(tmp_u, tmp_lv, T.start, T.seg_start,
+                                                                               T.seg_len, T.tile_base, tile_tmp, K * nb,
+                                                                               nb, sublog, sb, T.gcur, tmp2_u, tmp2_lv,
+                                                                               err);
         SCC_LAUNCH();
     }
-    if (ev) cudaEventRecord(ev[3], s);
+    if (ev) cudaEventRecord(ev[1], s);
     const size_t smem = rows_smem_bytes();
     SCC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sub_rows, kBlkR, smem));
-    if (ev) cudaEventRecord(ev[4], s);
-    k_sub_rows<<<std::min(nf, num_sms * std::max(1, per_sm)), kBlkR, smem, s>>>(tmp2_u, tmp2_lv, start, order_tmp, nf,
-                                                                                 sb, n, toff, tadj, counters, err);
+    if (ev) cudaEventRecord(ev[2], s);
+    k_sub_rows<<<std::min(nf, num_sms * std::max(1, per_sm)), kBlkR, smem, s>>>(tmp2_u, tmp2_lv, T.start, order_tmp, nf,
+                                                                                 sb, n, toff, tadj, T.counters, err);
     SCC_LAUNCH();
-    if (ev) cudaEventRecord(ev[5], s);
+    if (ev) cudaEventRecord(ev[3], s);
     return SCC_OK;
 }
 
@@ -789,7 +895,7 @@ size_t transpose_scratch_bytes(int64_t m_max) {
     const size_t nf = (size_t)kMaxBins, nb = (size_t)kMaxBuckets;
     auto a = [](size_t x) { return (x + 255) & ~(size_t)255; };
     const size_t m8 = (size_t)std::max<int64_t>(m_max, 1) + 8;
-    return a(8 * (nf + 2)) + a(8 * (2 * (nf + nb) + 3)) + 2 * a(4 * m8) + 2 * a(2 * m8) + a(4 * nf) +
+    return a(8 * (nf + 2)) + a(8 * (2 * nf + 4 * nb + 4)) + 2 * a(4 * m8) + 2 * a(2 * m8) + a(4 * nf) +
            a(4 * ((size_t)m_max / kSplitTile + nb + 2)) + a(4 * tile_rows_count(std::max<int64_t>(m_max, 1))) +
            2 * a(sizeof(int));
 }
@@ -803,7 +909,7 @@ void transpose_scratch_carve(unsigned char* base, int64_t m_max, TransposeScratc
     };
     const size_t m8 = (size_t)std::max<int64_t>(m_max, 1) + 8;
     ts->bcnt = reinterpret_cast<unsigned long long*>(take(8 * (nf + 2)));
-    ts->btmp = reinterpret_cast<unsigned long long*>(take(8 * (2 * (nf + nb) + 3)));
+    ts->btmp = reinterpret_cast<unsigned long long*>(take(8 * (2 * nf + 4 * nb + 4)));
     ts->tmp_u = reinterpret_cast<int32_t*>(take(4 * m8));
     ts->tmp2_u = reinterpret_cast<int32_t*>(take(4 * m8));
     ts->tmp_lv = reinterpret_cast<uint16_t*>(take(2 * m8));
@@ -823,14 +929,14 @@ int launch_transpose_keep_self(const int32_t* off, const int32_t* adj, int32_t n
                                int32_t* toff, int32_t* tadj, int num_sms, cudaStream_t s) {
     const int shift = bucket_shift(n);
     if (!transpose_bucketed(shift)) return SCC_ERR_INVALID_ARG;
-    const int nf = transpose_bins(n, shift);
-    SCC_CUDA(cudaMemsetAsync(ts.bcnt, 0, sizeof(unsigned long long) * ((size_t)nf + 2), s));
-    SCC_TRY(launch_copy_check_hist(adj, const_cast<int32_t*>(adj), n, m, shift, ts.bcnt, ts.bad, num_sms, s));
     SCC_TRY(launch_tile_rows(off, n, m, ts.trow, s));
+    SCC_CUDA(cudaMemsetAsync(ts.bad, 0, sizeof(int), s));
+    SCC_TRY(launch_intake_partition(adj, const_cast<int32_t*>(adj), off, ts.trow, n, m, shift, 1, ts.bcnt, ts.btmp,
+                                    ts.tmp_u, ts.tmp_lv, nullptr, nullptr, ts.bad, ts.err, num_sms, s, s, nullptr,
+                                    nullptr));
     bool self_found = false;
-    return launch_transpose(off, adj, ts.trow, n, m, m, shift, ts.bcnt, ts.btmp, ts.tmp_u, ts.tmp_lv, ts.tmp2_u,
-                            ts.tmp2_lv, ts.order, ts.tiles, toff, tadj, nullptr, nullptr, &self_found, ts.err, num_sms,
-                            s, nullptr);
+    return launch_transpose_rest(n, m, shift, 1, ts.bcnt, ts.btmp, ts.tmp_u, ts.tmp_lv, ts.tmp2_u, ts.tmp2_lv, ts.order,
+                                 ts.tiles, toff, tadj, nullptr, &self_found, ts.err, num_sms, s, nullptr);
 }
 
 int transpose_set_attributes() { return ensure_attributes(); }

@@ -101,8 +101,10 @@ def test_page_locked_host_input():
     """Page-locked host targets are read by the intake pass directly: aligned
     and unaligned starts, self-loops (the CSR is rebuilt) and a bad target."""
     import torch
+    # R-MAT 2^18 (4 M arcs) is read in several chunks, each partitioned while
+    # the next one is read; the others in one
     for g in (gg.rmat(14, 8, seed=42), gg.torus(2, 90, 0.5, seed=43),
-              gg.gnp(300, 0.02, seed=44, allow_self=True)):
+              gg.gnp(300, 0.02, seed=44, allow_self=True), gg.rmat(18, 16, seed=46)):
         want, _ = oracle.scc_labels(g.n, g.offsets, g.targets)
         for shift in (0, 1, 3):
             buf = torch.zeros(g.m + shift + 1, dtype=torch.int32).pin_memory()
