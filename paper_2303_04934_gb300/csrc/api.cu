@@ -428,8 +428,12 @@ static int graph_create_impl(scc_graph* h, int32_t n, int64_t m, const int32_t* 
         SCC_TRY(launch_copy_check_hist(src, adj_in, n, m, shift, bcnt, bad, h->di.num_sms, s));
         cudaEventRecord(ce.e[2], s);
     }
+    // the range check and (bucketed path) the partition's self-loop count in
+    // one host round trip
     int hbad = 0;
+    unsigned long long hself0 = 0;
     SCC_CUDA(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
+    if (bucketed) SCC_CUDA(cudaMemcpyAsync(&hself0, self_cnt, sizeof(hself0), cudaMemcpyDeviceToHost, s));
     SCC_CUDA(cudaStreamSynchronize(s));
     dfree(bad, s);
     if (hbad) {
@@ -476,8 +480,10 @@ static int graph_create_impl(scc_graph* h, int32_t n, int64_t m, const int32_t* 
         int k_cur = K;
         for (int attempt = 0; rc == SCC_OK; ++attempt) {
             bool self_found = false;
+            // the self-loop count of the first attempt is known already
             rc = launch_transpose_rest(n, m_cur, shift, k_cur, bcnt, btmp, tmp_u, tmp_lv, tmp2_u, tmp2_lv, ord, tiles,
-                                       toff, h->tadj, self_cnt, &self_found, terr, h->di.num_sms, s, &ce.e[5]);
+                                       toff, h->tadj, (attempt == 0 && hself0 == 0) ? nullptr : self_cnt,
+                                       &self_found, terr, h->di.num_sms, s, &ce.e[5]);
             if (rc != SCC_OK || !self_found) break;
             if (attempt > 0) {
                 rc = SCC_ERR_INTERNAL;  // the rebuilt CSR has no self-loops

@@ -757,6 +757,7 @@ struct scc_batch {
     BatchDims D;
     // captured launch
     cudaGraphExec_t exec = nullptr;
+    int exec_kernels = 0;  // kernel nodes of the captured graph (launches per replay)
     int32_t* exec_out = nullptr;
     const int32_t* exec_order = nullptr;
     int exec_norder = -1;
@@ -947,6 +948,17 @@ int capture(scc_batch* h, const int32_t* order, int norder, int32_t* out) {
         const int rc2 = cuda_err(cudaStreamEndCapture(cs, &graph));
         if (rc == SCC_OK) rc = rc2;
     }
+    if (rc == SCC_OK) {
+        size_t nn = 0;
+        rc = cuda_err(cudaGraphGetNodes(graph, nullptr, &nn));
+        std::vector<cudaGraphNode_t> nodes(nn);
+        if (rc == SCC_OK && nn > 0) rc = cuda_err(cudaGraphGetNodes(graph, nodes.data(), &nn));
+        h->exec_kernels = 0;
+        for (size_t k = 0; rc == SCC_OK && k < nn; ++k) {
+            cudaGraphNodeType t;
+            if (cudaGraphNodeGetType(nodes[k], &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) h->exec_kernels++;
+        }
+    }
     if (rc == SCC_OK) rc = cuda_err(cudaGraphInstantiate(&h->exec, graph, 0));
     if (graph) cudaGraphDestroy(graph);
     cudaStreamDestroy(cs);
@@ -976,8 +988,7 @@ int run_order(scc_batch* h, const int32_t* order, int norder, int32_t* out, cuda
     cudaEventRecord(e0, s);
     cudaError_t le = cudaGraphLaunch(h->exec, s);
     cudaEventRecord(e1, s);
-    count_launch();  // the reset kernel
-    count_launch();  // the persistent kernel
+    for (int k = 0; k < h->exec_kernels; ++k) count_launch();  // the graph's kernels (reset, G^T, persistent)
     int herr = 0;
     cudaError_t ce = cudaMemcpyAsync(&herr, h->flags + 1, sizeof(int), cudaMemcpyDeviceToHost, s);
     cudaError_t se = cudaStreamSynchronize(s);
