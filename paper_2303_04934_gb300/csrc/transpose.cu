@@ -281,34 +281,71 @@ __global__ void __launch_bounds__(1024) k_fine_scan(const unsigned long long* __
                                                    unsigned int* counters) {
     __shared__ unsigned long long s_w[32];
     __shared__ unsigned long long s_tot, s_hot;
+    __shared__ unsigned long long s_wsum[32], s_whot[32];
     auto count = [&](int i) {
         unsigned long long c = 0;
         for (int k = 0; k < K; ++k) c += hist[(size_t)k * nf + i];
         return c;
     };
-    const int per = (nf + (int)blockDim.x - 1) / (int)blockDim.x;
-    const int i0 = min((int)threadIdx.x * per, nf), i1 = min(i0 + per, nf);
+    // each warp scans a contiguous range of the bins, 32 consecutive bins per
+    // step (coalesced loads and stores); the warps' totals are scanned first
+    const int lane = lane_id(), warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const int per_w = ((nf + nwarps - 1) / nwarps + 31) & ~31;
+    const int w0 = min(warp * per_w, nf), w1 = min(w0 + per_w, nf);
     unsigned long long sum = 0, hot = 0;
-    for (int i = i0; i < i1; ++i) {
+    for (int i = w0 + lane; i < w1; i += 32) {
         const unsigned long long c = count(i);
         sum += c;
         hot += c > (unsigned long long)kWinArcs;
     }
-    unsigned long long run = block_scan_u64(sum, s_w, &s_tot);
-    const unsigned long long hbase = block_scan_u64(hot, s_w, &s_hot);
-    const unsigned long long nhot = s_hot;
-    unsigned long long h = hbase, c = nhot + ((unsigned long long)i0 - hbase);
-    for (int i = i0; i < i1; ++i) {
-        const unsigned long long ci = count(i);
-        start[i] = run;
-        gcur[i] = run;
-        run += ci;
-        if (ci > (unsigned long long)kWinArcs) order[h++] = i;
-        else order[c++] = i;
+    for (int d = 16; d >= 1; d >>= 1) {
+        sum += __shfl_xor_sync(kFull, sum, d);
+        hot += __shfl_xor_sync(kFull, hot, d);
     }
+    if (lane == 0) {
+        s_wsum[warp] = sum;
+        s_whot[warp] = hot;
+    }
+    __syncthreads();
     if (threadIdx.x == 0) {
-        start[nf] = s_tot;
+        unsigned long long a = 0, b = 0;
+        for (int w = 0; w < nwarps; ++w) {
+            const unsigned long long x = s_wsum[w], y = s_whot[w];
+            s_wsum[w] = a;
+            s_whot[w] = b;
+            a += x;
+            b += y;
+        }
+        s_tot = a;
+        s_hot = b;
+        start[nf] = a;
         counters[0] = 0;
+    }
+    __syncthreads();
+    const unsigned long long nhot = s_hot;
+    unsigned long long run = s_wsum[warp], hrun = s_whot[warp];
+    for (int b0 = w0; b0 < w1; b0 += 32) {
+        const int i = b0 + lane;
+        const unsigned long long c = i < w1 ? count(i) : 0ull;
+        const unsigned long long h = c > (unsigned long long)kWinArcs ? 1ull : 0ull;
+        unsigned long long ci = c, hi = h;  // inclusive scans over the 32 lanes
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const unsigned long long yc = __shfl_up_sync(kFull, ci, d), yh = __shfl_up_sync(kFull, hi, d);
+            if (lane >= d) {
+                ci += yc;
+                hi += yh;
+            }
+        }
+        if (i < w1) {
+            const unsigned long long st = run + ci - c;
+            start[i] = st;
+            gcur[i] = st;
+            const unsigned long long hb = hrun + hi - h;  // hot bins before i
+            order[h ? hb : nhot + (unsigned long long)i - hb] = i;
+        }
+        run += __shfl_sync(kFull, ci, 31);
+        hrun += __shfl_sync(kFull, hi, 31);
     }
     // split tiles per segment (up to 8 x 512 segments: a run of them per thread)
     const int ns = K * nb;
