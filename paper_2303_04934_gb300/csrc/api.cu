@@ -476,7 +476,7 @@ static int graph_create_impl(scc_graph* h, int32_t n, int64_t m, const int32_t* 
         if (rc == SCC_OK) rc = dalloc_t(&tmp2_u, (size_t)m + 8, s);
         if (rc == SCC_OK) rc = dalloc_t(&tmp2_lv, (size_t)m + 8, s);
         if (rc == SCC_OK) rc = dalloc_t(&ord, (size_t)transpose_bins(n, shift), s);
-        if (rc == SCC_OK) rc = dalloc_t(&tiles, transpose_split_tiles(m, n, shift), s);
+        if (rc == SCC_OK) rc = dalloc_t(&tiles, transpose_split_tiles(m, n, shift, K), s);
         int k_cur = K;
         for (int attempt = 0; rc == SCC_OK; ++attempt) {
             bool self_found = false;

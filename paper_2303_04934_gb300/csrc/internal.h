@@ -96,7 +96,7 @@ bool transpose_bucketed(int shift);
 int transpose_chunks(int64_t m, bool overlap);
 size_t transpose_hist_words(int32_t n, int shift, int K);
 size_t transpose_tmp_words(int32_t n, int shift, int K);
-size_t transpose_split_tiles(int64_t m, int32_t n, int shift);
+size_t transpose_split_tiles(int64_t m, int32_t n, int shift, int K);
 int launch_intake_partition(const int32_t* src, int32_t* adj, const int32_t* off, const int32_t* trow, int32_t n,
                             int64_t m, int shift, int K, unsigned long long* hist, unsigned long long* bucket_tmp,
                             int32_t* tmp_u, uint16_t* tmp_lv, int32_t* selfrow, unsigned long long* nself, int* bad,

@@ -278,7 +278,7 @@ __global__ void __launch_bounds__(1024) k_fine_scan(const unsigned long long* __
                                                    int32_t* order, const unsigned long long* __restrict__ seg_start,
                                                    const unsigned long long* __restrict__ seg_len,
                                                    unsigned long long* tile_base, int32_t* tile_seg,
-                                                   unsigned int* counters) {
+                                                   long long tile_cap, unsigned int* counters, int* err) {
     __shared__ unsigned long long s_w[32];
     __shared__ unsigned long long s_tot, s_hot;
     __shared__ unsigned long long s_wsum[32], s_whot[32];
@@ -358,7 +358,11 @@ __global__ void __launch_bounds__(1024) k_fine_scan(const unsigned long long* __
     unsigned long long nt = 0;
     for (int g = s0; g < s1; ++g) nt += tiles_of(g);
     unsigned long long tb = block_scan_u64(nt, s_w, &s_tot);
-    const unsigned long long ntot = s_tot;
+    unsigned long long ntot = s_tot;
+    if (ntot > (unsigned long long)tile_cap) {  // the tile table is too small: report, split nothing past it
+        if (threadIdx.x == 0) atomicExch(err, SCC_ERR_INTERNAL);
+        ntot = (unsigned long long)tile_cap;
+    }
     for (int g = s0; g < s1; ++g) {
         tile_base[g] = tb;
         tb += tiles_of(g);
@@ -731,9 +735,12 @@ int bucket_shift(int32_t n) {
 
 size_t tile_rows_count(int64_t m) { return (size_t)((m + kStep - 1) / kStep) + 1; }
 
-size_t transpose_split_tiles(int64_t m, int32_t n, int shift) {
+// Tiles of the split pass: one run per segment (chunk, bucket), each from its
+// first multiple of 8, so at most m / T + 7 ns / T + ns tiles for ns segments.
+size_t transpose_split_tiles(int64_t m, int32_t n, int shift, int K) {
     const int nb = std::max(1, (int)(((int64_t)n + (1ll << shift) - 1) >> shift));
-    return (size_t)(m / kSplitTile) + (size_t)nb + 2;
+    const size_t ns = (size_t)K * nb;
+    return (size_t)(m / kSplitTile) + ns + (7 * ns) / kSplitTile + 2;
 }
 
 int transpose_bins(int32_t n, int shift) {
@@ -892,7 +899,7 @@ int launch_transpose_rest(int32_t n, int64_t mt, int shift, int K, const unsigne
     }
     SCC_TRY(ensure_attributes());
     k_fine_scan<<<1, 1024, 0, s>>>(hist, K, nf, nb, T.start, T.gcur, order_tmp, T.seg_start, T.seg_len, T.tile_base,
-                                   tile_tmp, T.counters);
+                                   tile_tmp, (long long)transpose_split_tiles(mt, n, shift, K), T.counters, err);
     SCC_LAUNCH();
     if (nself != nullptr) {
         unsigned long long hself = 0;
@@ -933,7 +940,8 @@ size_t transpose_scratch_bytes(int64_t m_max) {
     auto a = [](size_t x) { return (x + 255) & ~(size_t)255; };
     const size_t m8 = (size_t)std::max<int64_t>(m_max, 1) + 8;
     return a(8 * (nf + 2)) + a(8 * (2 * nf + 4 * nb + 4)) + 2 * a(4 * m8) + 2 * a(2 * m8) + a(4 * nf) +
-           a(4 * ((size_t)m_max / kSplitTile + nb + 2)) + a(4 * tile_rows_count(std::max<int64_t>(m_max, 1))) +
+           a(4 * ((size_t)m_max / kSplitTile + nb + (7 * nb) / kSplitTile + 2)) +
+           a(4 * tile_rows_count(std::max<int64_t>(m_max, 1))) +
            2 * a(sizeof(int));
 }
 void transpose_scratch_carve(unsigned char* base, int64_t m_max, TransposeScratch* ts) {
@@ -952,7 +960,7 @@ void transpose_scratch_carve(unsigned char* base, int64_t m_max, TransposeScratc
     ts->tmp_lv = reinterpret_cast<uint16_t*>(take(2 * m8));
     ts->tmp2_lv = reinterpret_cast<uint16_t*>(take(2 * m8));
     ts->order = reinterpret_cast<int32_t*>(take(4 * nf));
-    ts->tiles = reinterpret_cast<int32_t*>(take(4 * ((size_t)m_max / kSplitTile + nb + 2)));
+    ts->tiles = reinterpret_cast<int32_t*>(take(4 * ((size_t)m_max / kSplitTile + nb + (7 * nb) / kSplitTile + 2)));
     ts->trow = reinterpret_cast<int32_t*>(take(4 * tile_rows_count(std::max<int64_t>(m_max, 1))));
     ts->bad = reinterpret_cast<int*>(take(sizeof(int)));
     ts->err = reinterpret_cast<int*>(take(sizeof(int)));
