@@ -114,6 +114,20 @@ SCC_API int64_t scc_debug_launch_count(void);
    table or the bag filled up, batches labelled. out: host uint64[11 * G]. */
 SCC_API int scc_debug_batch_times(struct scc_batch* h, uint64_t* out);
 
+/*
+ * The grouping of a batched run's G^T passes (scc_batch.h; host only, no
+ * device work): graphs are taken in packed order, as many consecutive ones per
+ * group as fit in max_vertices vertices and max_arcs arcs; a graph larger than
+ * either limit ends the current group and is in none (its block builds its
+ * G^T); groups without vertices are dropped. The library uses 2^24 vertices
+ * and 2^27 arcs.
+ *   vbase, ebase  host int64[G + 1], non-decreasing (scc_batch.h layout).
+ *   groups        host int32[2 G]: group k is graphs [groups[2k], groups[2k+1]).
+ *   *ngroups      (host) the number of groups.
+ */
+SCC_API int scc_debug_batch_groups(int32_t G, const int64_t* vbase, const int64_t* ebase, int64_t max_vertices,
+                                   int64_t max_arcs, int32_t* groups, int32_t* ngroups);
+
 #ifdef __cplusplus
 }
 #endif

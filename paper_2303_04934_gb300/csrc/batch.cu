@@ -654,6 +654,43 @@ namespace {
 constexpr long long kGroupVerts = 1ll << 24;  // the bucketed transpose's limit
 constexpr long long kGroupArcs = 1ll << 27;   // bounds the groups' scratch
 
+struct GroupPlan {
+    int g0, g1;
+    long long v0, v1, e0, e1;
+};
+
+// Groups of consecutive graphs (host only): greedily, as many consecutive
+// graphs as fit in max_v vertices and max_a arcs; a graph larger than either
+// limit ends the current group and belongs to none (its block builds its
+// G^T). Groups without vertices are dropped. ok[g] = 1 for the grouped graphs.
+void plan_groups(int G, const long long* vb, const long long* eb, long long max_v, long long max_a,
+                 std::vector<GroupPlan>& groups, std::vector<unsigned char>& ok) {
+    groups.clear();
+    ok.assign((size_t)G + 1, 0);
+    GroupPlan cur{0, 0, vb[0], vb[0], eb[0], eb[0]};
+    auto flush = [&](int g) {
+        if (cur.g1 > cur.g0 && cur.v1 > cur.v0) {
+            groups.push_back(cur);
+        } else {
+            for (int k = cur.g0; k < cur.g1; ++k) ok[k] = 0;
+        }
+        cur = {g, g, vb[g], vb[g], eb[g], eb[g]};
+    };
+    for (int g = 0; g < G; ++g) {
+        const long long n = vb[g + 1] - vb[g], m = eb[g + 1] - eb[g];
+        if (n > max_v || m > max_a) {
+            flush(g + 1);  // the current group ends before g
+            continue;
+        }
+        if ((cur.v1 - cur.v0) + n > max_v || (cur.e1 - cur.e0) + m > max_a) flush(g);
+        cur.g1 = g + 1;
+        cur.v1 = vb[g + 1];
+        cur.e1 = eb[g + 1];
+        ok[g] = 1;
+    }
+    flush(G);
+}
+
 // last g in [lo, hi) with a[g] <= x (a non-decreasing, a[lo] <= x)
 __device__ __forceinline__ int last_le(const long long* __restrict__ a, int lo, int hi, long long x) {
     while (hi - lo > 1) {
@@ -736,11 +773,7 @@ struct scc_batch {
     int32_t* labels = nullptr;      // internal output (host destinations, tuning)
     // G^T computed before the persistent launch, for groups of consecutive
     // graphs (one grid-wide transpose each)
-    struct Group {
-        int g0, g1;
-        long long v0, v1, e0, e1;
-    };
-    std::vector<Group> groups;
+    std::vector<scc::GroupPlan> groups;
     int32_t* gt_off = nullptr;       // packed like offsets
     int32_t* gt_adj = nullptr;       // packed like targets
     unsigned char* gt_ok = nullptr;  // graph is in a group
@@ -1099,33 +1132,12 @@ int batch_create_impl(scc_batch* h, int32_t G, const int64_t* vbase, const int64
     // groups of consecutive graphs for the G^T computed before each launch: up
     // to kGroupVerts vertices and kGroupArcs arcs each; a larger graph is left
     // to its block
-    std::vector<unsigned char> ok((size_t)G + 1, 0);
+    std::vector<unsigned char> ok;
+    plan_groups(G, h->vb_h.data(), h->eb_h.data(), kGroupVerts, kGroupArcs, h->groups, ok);
     long long ng_max = 0, mg_max = 0;
-    {
-        scc_batch::Group cur{0, 0, 0, 0, 0, 0};
-        auto flush = [&](int g) {
-            if (cur.g1 > cur.g0 && cur.v1 > cur.v0) {
-                h->groups.push_back(cur);
-                ng_max = std::max(ng_max, cur.v1 - cur.v0);
-                mg_max = std::max(mg_max, cur.e1 - cur.e0);
-            } else {
-                for (int k = cur.g0; k < cur.g1; ++k) ok[k] = 0;
-            }
-            cur = {g, g, h->vb_h[g], h->vb_h[g], h->eb_h[g], h->eb_h[g]};
-        };
-        for (int32_t g = 0; g < G; ++g) {
-            const long long n = h->vb_h[g + 1] - h->vb_h[g], m = h->eb_h[g + 1] - h->eb_h[g];
-            if (n > kGroupVerts || m > kGroupArcs) {
-                flush(g + 1);  // the current group ends before g; g builds its own G^T
-                continue;
-            }
-            if ((cur.v1 - cur.v0) + n > kGroupVerts || (cur.e1 - cur.e0) + m > kGroupArcs) flush(g);
-            cur.g1 = g + 1;
-            cur.v1 = h->vb_h[g + 1];
-            cur.e1 = h->eb_h[g + 1];
-            ok[g] = 1;
-        }
-        flush(G);
+    for (const auto& gr : h->groups) {
+        ng_max = std::max(ng_max, gr.v1 - gr.v0);
+        mg_max = std::max(mg_max, gr.e1 - gr.e0);
     }
     if (!h->groups.empty()) {
         SCC_TRY(dalloc_t(&h->gt_off, (size_t)(h->nv + G) + 1, s));
@@ -1384,6 +1396,27 @@ SCC_API int scc_batch_autotune(scc_batch_handle h, int32_t sample, cudaStream_t 
     if (rc2 != SCC_OK) return rc2;
     if (best) *best = bc;
     if (best_ms) *best_ms = bms;
+    return SCC_OK;
+}
+
+SCC_API int scc_debug_batch_groups(int32_t G, const int64_t* vbase, const int64_t* ebase, int64_t max_vertices,
+                                   int64_t max_arcs, int32_t* groups, int32_t* ngroups) {
+    if (G < 0 || !ngroups || max_vertices < 1 || max_arcs < 0 || (G > 0 && (!vbase || !ebase || !groups)))
+        return SCC_ERR_INVALID_ARG;
+    std::vector<long long> vb((size_t)G + 1), eb((size_t)G + 1);
+    for (int32_t g = 0; g <= G; ++g) {
+        vb[g] = vbase[g];
+        eb[g] = ebase[g];
+        if (g > 0 && (vb[g] < vb[g - 1] || eb[g] < eb[g - 1])) return SCC_ERR_INVALID_ARG;
+    }
+    std::vector<scc::GroupPlan> plan;
+    std::vector<unsigned char> ok;
+    scc::plan_groups(G, vb.data(), eb.data(), max_vertices, max_arcs, plan, ok);
+    for (size_t k = 0; k < plan.size(); ++k) {
+        groups[2 * k] = plan[k].g0;
+        groups[2 * k + 1] = plan[k].g1;
+    }
+    *ngroups = (int32_t)plan.size();
     return SCC_OK;
 }
 

@@ -34,7 +34,7 @@ EXPORTED = [
     "scc_debug_multi_reach", "scc_debug_reach_multi_wide", "scc_debug_hashbag", "scc_debug_pair_table", "scc_debug_launch_count",
     "scc_batch_config_default", "scc_batch_create", "scc_batch_destroy", "scc_batch_set_config",
     "scc_batch_get_config", "scc_batch_run", "scc_batch_autotune", "scc_batch_get_stats",
-    "scc_debug_batch_times",
+    "scc_debug_batch_times", "scc_debug_batch_groups",
     "scc_server_config_default", "scc_server_create", "scc_server_destroy", "scc_server_add_graph",
     "scc_server_remove_graph", "scc_server_submit_scc", "scc_server_submit_reach", "scc_server_wait",
     "scc_server_drain", "scc_server_get_stats", "scc_server_reset_stats",
@@ -155,6 +155,7 @@ def load() -> ctypes.CDLL:
         "scc_batch_autotune": ([vp, i32, vp, P(scc_batch_config), P(ctypes.c_double)], ctypes.c_int),
         "scc_batch_get_stats": ([vp, P(scc_batch_stats)], ctypes.c_int),
         "scc_debug_batch_times": ([vp, vp], ctypes.c_int),
+        "scc_debug_batch_groups": ([i32, vp, vp, i64, i64, vp, P(i32)], ctypes.c_int),
         "scc_server_config_default": ([P(scc_server_config)], ctypes.c_int),
         "scc_server_create": ([P(scc_server_config), P(vp)], ctypes.c_int),
         "scc_server_destroy": ([vp], ctypes.c_int),
@@ -308,6 +309,19 @@ def scc_debug_batch_times(h, G: int) -> np.ndarray:
     out = np.zeros(11 * max(G, 1), np.uint64)
     _check(load().scc_debug_batch_times(h, _ptr(out)), "scc_debug_batch_times")
     return out[:11 * G].reshape(G, 11)
+
+
+def scc_debug_batch_groups(vbase, ebase, max_vertices: int = 1 << 24, max_arcs: int = 1 << 27) -> list:
+    """Groups [(g0, g1), ...] of consecutive graphs for the G^T passes of a
+    batched run (host only)."""
+    vb = np.ascontiguousarray(vbase, dtype=np.int64)
+    eb = np.ascontiguousarray(ebase, dtype=np.int64)
+    G = len(vb) - 1
+    out = np.zeros(2 * max(G, 1), np.int32)
+    ng = ctypes.c_int32()
+    _check(load().scc_debug_batch_groups(G, _ptr(vb), _ptr(eb), max_vertices, max_arcs, _ptr(out), ctypes.byref(ng)),
+           "scc_debug_batch_groups")
+    return [(int(out[2 * k]), int(out[2 * k + 1])) for k in range(ng.value)]
 
 
 class SccBatch:
