@@ -336,6 +336,24 @@ struct CreateEvents {
     }
 };
 
+// The second stream and its events of a chunked intake; on exit the stream's
+// work finishes before the call's temporaries are freed on the main stream.
+struct ChunkStreams {
+    cudaStream_t s2 = nullptr;
+    cudaEvent_t cev[9] = {};
+    ChunkStreams() = default;
+    ChunkStreams(const ChunkStreams&) = delete;
+    ChunkStreams& operator=(const ChunkStreams&) = delete;
+    ~ChunkStreams() {
+        if (s2) {
+            cudaStreamSynchronize(s2);
+            cudaStreamDestroy(s2);
+        }
+        for (auto& e : cev)
+            if (e) cudaEventDestroy(e);
+    }
+};
+
 static int graph_create_impl(scc_graph* h, int32_t n, int64_t m, const int32_t* offsets, const int32_t* targets,
                              cudaStream_t s) {
     SCC_TRY(device_info(&h->di));
@@ -343,11 +361,10 @@ static int graph_create_impl(scc_graph* h, int32_t n, int64_t m, const int32_t* 
     cudaEventRecord(ce.e[0], s);
     h->n = n;
     h->m_in = m;
-    int32_t *off_in = nullptr, *adj_in = nullptr;
-    SCC_TRY(dalloc_t(&off_in, (size_t)n + 1, s));
-    SCC_TRY(dalloc_t(&adj_in, (size_t)m, s));
-    h->off = off_in;
-    h->adj = adj_in;
+    SCC_TRY(dalloc_t(&h->off, (size_t)n + 1, s));
+    SCC_TRY(dalloc_t(&h->adj, (size_t)m, s));
+    int32_t* const off_in = h->off;
+    int32_t* const adj_in = h->adj;
     SCC_TRY(to_device(off_in, offsets, sizeof(int32_t) * ((size_t)n + 1), s));
     // a device target array is copied by the intake pass itself (one read), and
     // so is a page-locked host one (the pass reads it over the host link, so the
@@ -368,16 +385,17 @@ static int graph_create_impl(scc_graph* h, int32_t n, int64_t m, const int32_t* 
     // host input: intake and partition in chunks on two streams, so that each
     // chunk's partition runs while the next chunk crosses the host link
     const int K = bucketed ? transpose_chunks(m, host_src) : 1;
+    Scratch tmp(s);  // every temporary below is freed when the call returns
     int* bad = nullptr;
     int32_t* selfrow = nullptr;
     unsigned long long *bcnt = nullptr, *btmp = nullptr;
-    void* stmp = nullptr;
-    SCC_TRY(dalloc_t(&bad, 1, s));
-    SCC_TRY(dalloc_t(&selfrow, (size_t)n + 1, s));
+    unsigned char* stmp = nullptr;
+    SCC_TRY(tmp.alloc(&bad, 1));
+    SCC_TRY(tmp.alloc(&selfrow, (size_t)n + 1));
     const size_t hist_words = transpose_hist_words(n, shift, K);  // [hist_words - 1]: self-loops found
-    SCC_TRY(dalloc_t(&bcnt, hist_words, s));
-    SCC_TRY(dalloc_t(&btmp, transpose_tmp_words(n, shift, K), s));
-    SCC_TRY(dalloc(&stmp, scan_tmp_bytes(n), s));
+    SCC_TRY(tmp.alloc(&bcnt, hist_words));
+    SCC_TRY(tmp.alloc(&btmp, transpose_tmp_words(n, shift, K)));
+    SCC_TRY(tmp.alloc(&stmp, scan_tmp_bytes(n)));
     unsigned long long* self_cnt = bcnt + hist_words - 1;
     SCC_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), s));
     SCC_CUDA(cudaMemsetAsync(selfrow, 0, sizeof(int32_t) * ((size_t)n + 1), s));
@@ -387,42 +405,23 @@ static int graph_create_impl(scc_graph* h, int32_t n, int64_t m, const int32_t* 
     // partition runs only if no target was out of range
     SCC_TRY(launch_validate_offsets(off_in, n, m, bad, s));
     int32_t* trow = nullptr;
-    SCC_TRY(dalloc_t(&trow, tile_rows_count(m), s));
+    SCC_TRY(tmp.alloc(&trow, tile_rows_count(m)));
     SCC_TRY(launch_tile_rows(off_in, n, m, trow, s));
     int32_t *tmp_u = nullptr, *tmp2_u = nullptr, *ord = nullptr, *tiles = nullptr;
     uint16_t *tmp_lv = nullptr, *tmp2_lv = nullptr;
     int* terr = nullptr;
-    cudaStream_t s2 = nullptr;
-    cudaEvent_t cev[9] = {};
-    auto release = [&]() {
-        dfree(tmp_u, s);
-        dfree(tmp_lv, s);
-        dfree(tmp2_u, s);
-        dfree(tmp2_lv, s);
-        dfree(tiles, s);
-        dfree(ord, s);
-        dfree(terr, s);
-        for (auto& e : cev)
-            if (e) cudaEventDestroy(e);
-        if (s2) cudaStreamDestroy(s2);
-        s2 = nullptr;
-        for (auto& e : cev) e = nullptr;
-    };
+    ChunkStreams cs;  // declared after tmp: its stream is drained before tmp frees
     if (bucketed) {
-        SCC_TRY(dalloc_t(&tmp_u, (size_t)m + 8, s));
-        SCC_TRY(dalloc_t(&tmp_lv, (size_t)m + 8, s));
-        SCC_TRY(dalloc_t(&terr, 1, s));
+        SCC_TRY(tmp.alloc(&tmp_u, (size_t)m + 8));
+        SCC_TRY(tmp.alloc(&tmp_lv, (size_t)m + 8));
+        SCC_TRY(tmp.alloc(&terr, 1));
         SCC_CUDA(cudaMemsetAsync(terr, 0, sizeof(int), s));
         if (K > 1) {
-            SCC_CUDA(cudaStreamCreateWithFlags(&s2, cudaStreamNonBlocking));
-            for (int k = 0; k <= K; ++k) SCC_CUDA(cudaEventCreateWithFlags(&cev[k], cudaEventDisableTiming));
+            SCC_CUDA(cudaStreamCreateWithFlags(&cs.s2, cudaStreamNonBlocking));
+            for (int k = 0; k <= K; ++k) SCC_CUDA(cudaEventCreateWithFlags(&cs.cev[k], cudaEventDisableTiming));
         }
-        const int rc = launch_intake_partition(src, adj_in, off_in, trow, n, m, shift, K, bcnt, btmp, tmp_u, tmp_lv,
-                                               selfrow, self_cnt, bad, terr, h->di.num_sms, s, s2, cev, &ce.e[1]);
-        if (rc != SCC_OK) {
-            release();
-            return rc;
-        }
+        SCC_TRY(launch_intake_partition(src, adj_in, off_in, trow, n, m, shift, K, bcnt, btmp, tmp_u, tmp_lv, selfrow,
+                                        self_cnt, bad, terr, h->di.num_sms, s, cs.s2, cs.cev, &ce.e[1]));
     } else {
         cudaEventRecord(ce.e[1], s);
         SCC_TRY(launch_copy_check_hist(src, adj_in, n, m, shift, bcnt, bad, h->di.num_sms, s));
@@ -435,78 +434,64 @@ static int graph_create_impl(scc_graph* h, int32_t n, int64_t m, const int32_t* 
     SCC_CUDA(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
     if (bucketed) SCC_CUDA(cudaMemcpyAsync(&hself0, self_cnt, sizeof(hself0), cudaMemcpyDeviceToHost, s));
     SCC_CUDA(cudaStreamSynchronize(s));
-    dfree(bad, s);
-    if (hbad) {
-        release();
-        dfree(trow, s);
-        dfree(selfrow, s);
-        dfree(bcnt, s);
-        dfree(btmp, s);
-        dfree(stmp, s);
-        return SCC_ERR_INVALID_ARG;
-    }
+    tmp.release(bad);
+    if (hbad) return SCC_ERR_INVALID_ARG;
     h->mt = m;
     int64_t m_cur = m;
     // forward CSR without its self-loops (selfrow counts them per row)
     auto drop_self_loops = [&](unsigned long long hself) -> int {
-        h->mt = m - (int64_t)hself;
+        const int64_t mt = m - (int64_t)hself;
         int32_t *cnt = nullptr, *off2 = nullptr, *adj2 = nullptr;
-        SCC_TRY(dalloc_t(&cnt, (size_t)n + 1, s));
-        SCC_TRY(dalloc_t(&off2, (size_t)n + 1, s));
-        SCC_TRY(dalloc_t(&adj2, (size_t)h->mt, s));
+        SCC_TRY(tmp.alloc(&cnt, (size_t)n + 1));
+        SCC_TRY(tmp.alloc(&off2, (size_t)n + 1));
+        SCC_TRY(tmp.alloc(&adj2, (size_t)mt));
         SCC_TRY(launch_row_nonself(h->off, selfrow, n, cnt, s));
         SCC_TRY(launch_scan(cnt, off2, n, stmp, s));
         SCC_TRY(launch_drop_self_loops(h->off, h->adj, n, m, selfrow, off2, adj2, s));
-        dfree(cnt, s);
+        tmp.release(cnt);
         dfree(h->off, s);
         dfree(h->adj, s);
         h->off = off2;
         h->adj = adj2;
-        m_cur = h->mt;
+        tmp.keep(off2);
+        tmp.keep(adj2);
+        h->mt = mt;
+        m_cur = mt;
         SCC_TRY(launch_tile_rows(h->off, n, m_cur, trow, s));  // rows of the new CSR's tiles
         return SCC_OK;
     };
     // G^T: three-level bucketed counting sort by target (direct atomics when n is huge)
-    int32_t* toff = nullptr;
-    SCC_TRY(dalloc_t(&toff, (size_t)n + 1, s));
-    h->toff = toff;
+    SCC_TRY(dalloc_t(&h->toff, (size_t)n + 1, s));
     SCC_TRY(dalloc_t(&h->tadj, (size_t)m, s));
     if (bucketed) {
-        int rc = SCC_OK;
-        if (rc == SCC_OK) rc = dalloc_t(&tmp2_u, (size_t)m + 8, s);
-        if (rc == SCC_OK) rc = dalloc_t(&tmp2_lv, (size_t)m + 8, s);
-        if (rc == SCC_OK) rc = dalloc_t(&ord, (size_t)transpose_bins(n, shift), s);
-        if (rc == SCC_OK) rc = dalloc_t(&tiles, transpose_split_tiles(m, n, shift, K), s);
+        SCC_TRY(tmp.alloc(&tmp2_u, (size_t)m + 8));
+        SCC_TRY(tmp.alloc(&tmp2_lv, (size_t)m + 8));
+        SCC_TRY(tmp.alloc(&ord, (size_t)transpose_bins(n, shift)));
+        SCC_TRY(tmp.alloc(&tiles, transpose_split_tiles(m, n, shift, K)));
         int k_cur = K;
-        for (int attempt = 0; rc == SCC_OK; ++attempt) {
+        for (int attempt = 0;; ++attempt) {
             bool self_found = false;
             // the self-loop count of the first attempt is known already
-            rc = launch_transpose_rest(n, m_cur, shift, k_cur, bcnt, btmp, tmp_u, tmp_lv, tmp2_u, tmp2_lv, ord, tiles,
-                                       toff, h->tadj, (attempt == 0 && hself0 == 0) ? nullptr : self_cnt,
-                                       &self_found, terr, h->di.num_sms, s, &ce.e[5]);
-            if (rc != SCC_OK || !self_found) break;
-            if (attempt > 0) {
-                rc = SCC_ERR_INTERNAL;  // the rebuilt CSR has no self-loops
-                break;
-            }
+            SCC_TRY(launch_transpose_rest(n, m_cur, shift, k_cur, bcnt, btmp, tmp_u, tmp_lv, tmp2_u, tmp2_lv, ord,
+                                          tiles, h->toff, h->tadj, (attempt == 0 && hself0 == 0) ? nullptr : self_cnt,
+                                          &self_found, terr, h->di.num_sms, s, &ce.e[5]));
+            if (!self_found) break;
+            if (attempt > 0) return SCC_ERR_INTERNAL;  // the rebuilt CSR has no self-loops
             // self-loops: rebuild the forward CSR without them and start over
             unsigned long long hself = 0;
-            rc = cuda_err(cudaMemcpyAsync(&hself, self_cnt, sizeof(hself), cudaMemcpyDeviceToHost, s));
-            if (rc == SCC_OK) rc = cuda_err(cudaStreamSynchronize(s));
-            if (rc == SCC_OK) rc = drop_self_loops(hself);
+            SCC_CUDA(cudaMemcpyAsync(&hself, self_cnt, sizeof(hself), cudaMemcpyDeviceToHost, s));
+            SCC_CUDA(cudaStreamSynchronize(s));
+            SCC_TRY(drop_self_loops(hself));
             k_cur = 1;
-            if (rc == SCC_OK)  // histograms and the self-loop count start over
-                rc = cuda_err(cudaMemsetAsync(bcnt, 0, sizeof(unsigned long long) * hist_words, s));
-            if (rc == SCC_OK)
-                rc = launch_intake_partition(h->adj, h->adj, h->off, trow, n, m_cur, shift, 1, bcnt, btmp, tmp_u,
-                                             tmp_lv, nullptr, nullptr, nullptr, terr, h->di.num_sms, s, s, nullptr,
-                                             &ce.e[1]);
+            // histograms and the self-loop count start over
+            SCC_CUDA(cudaMemsetAsync(bcnt, 0, sizeof(unsigned long long) * hist_words, s));
+            SCC_TRY(launch_intake_partition(h->adj, h->adj, h->off, trow, n, m_cur, shift, 1, bcnt, btmp, tmp_u,
+                                            tmp_lv, nullptr, nullptr, nullptr, terr, h->di.num_sms, s, s, nullptr,
+                                            &ce.e[1]));
         }
         int herr = 0;
-        if (rc == SCC_OK) rc = cuda_err(cudaMemcpyAsync(&herr, terr, sizeof(int), cudaMemcpyDeviceToHost, s));
-        if (rc == SCC_OK) rc = cuda_err(cudaStreamSynchronize(s));
-        release();
-        if (rc != SCC_OK) return rc;
+        SCC_CUDA(cudaMemcpyAsync(&herr, terr, sizeof(int), cudaMemcpyDeviceToHost, s));
+        SCC_CUDA(cudaStreamSynchronize(s));
         if (herr) return herr;
     } else {
         // self-loops from the row-aware histogram pass, then direct placement
@@ -517,15 +502,10 @@ static int graph_create_impl(scc_graph* h, int32_t n, int64_t m, const int32_t* 
         SCC_CUDA(cudaStreamSynchronize(s));
         if (hself > 0) SCC_TRY(drop_self_loops(hself));
         int32_t* indeg = nullptr;
-        SCC_TRY(dalloc_t(&indeg, (size_t)n + 1, s));
-        SCC_TRY(launch_transpose_direct(h->off, h->adj, trow, n, m_cur, indeg, stmp, toff, h->tadj, h->di.num_sms, s));
-        dfree(indeg, s);
+        SCC_TRY(tmp.alloc(&indeg, (size_t)n + 1));
+        SCC_TRY(launch_transpose_direct(h->off, h->adj, trow, n, m_cur, indeg, stmp, h->toff, h->tadj,
+                                        h->di.num_sms, s));
     }
-    dfree(trow, s);
-    dfree(selfrow, s);
-    dfree(bcnt, s);
-    dfree(btmp, s);
-    dfree(stmp, s);
     cudaEventRecord(ce.e[9], s);
     SCC_CUDA(cudaStreamSynchronize(s));
     h->create_ms[0] = ce.ms(0, 9);
@@ -919,12 +899,12 @@ int scc_debug_trim(scc_handle h, uint8_t* flags, void* stream) {
     cudaStream_t s = (cudaStream_t)stream;
     h->last = s;
     if (h->n == 0) return SCC_OK;
+    Scratch tmp(s);
     uint8_t* d = nullptr;
-    SCC_TRY(dalloc_t(&d, (size_t)h->n, s));
+    SCC_TRY(tmp.alloc(&d, (size_t)h->n));
     int rc = launch_trim(h->off, h->toff, h->n, d, s);
     if (rc == SCC_OK) rc = from_device(flags, d, (size_t)h->n, s);
     if (rc == SCC_OK) rc = cuda_err(cudaStreamSynchronize(s));
-    dfree(d, s);
     return rc;
 }
 
@@ -1051,13 +1031,14 @@ int scc_debug_multi_reach(scc_handle h, const int32_t* labels, const int32_t* so
     }
     h->stats.table_resizes = resizes;
     // gather the table
+    Scratch tmp(s);
     unsigned long long* dout = nullptr;
     bool dev_out = is_device_ptr(pairs);
     SCC_CUDA(cudaMemsetAsync(h->counters + 2, 0, sizeof(unsigned long long), s));
     if (dev_out) {
         SCC_TRY(launch_table_gather(h->tab[d], tcap, reinterpret_cast<unsigned long long*>(pairs), cap, h->counters + 2, s));
     } else {
-        SCC_TRY(dalloc_t(&dout, (size_t)std::max<int64_t>(cap, 1), s));
+        SCC_TRY(tmp.alloc(&dout, (size_t)std::max<int64_t>(cap, 1)));
         SCC_TRY(launch_table_gather(h->tab[d], tcap, dout, cap, h->counters + 2, s));
     }
     unsigned long long tot = 0;
@@ -1065,10 +1046,8 @@ int scc_debug_multi_reach(scc_handle h, const int32_t* labels, const int32_t* so
     SCC_CUDA(cudaStreamSynchronize(s));
     if (!dev_out) {
         int64_t c = std::min<int64_t>((int64_t)tot, cap);
-        int rc = cuda_err(cudaMemcpyAsync(pairs, dout, sizeof(uint64_t) * (size_t)c, cudaMemcpyDeviceToHost, s));
-        if (rc == SCC_OK) rc = cuda_err(cudaStreamSynchronize(s));
-        dfree(dout, s);
-        SCC_TRY(rc);
+        SCC_CUDA(cudaMemcpyAsync(pairs, dout, sizeof(uint64_t) * (size_t)c, cudaMemcpyDeviceToHost, s));
+        SCC_CUDA(cudaStreamSynchronize(s));
     }
     *npairs = (int64_t)tot;
     return SCC_OK;
@@ -1081,20 +1060,17 @@ int scc_debug_hashbag(const int32_t* items, int64_t count, int32_t lambda, int32
     if (!items || !out || !nout || count < 1 || lambda < 1024 || (lambda & (lambda - 1)) || sigma < 1)
         return SCC_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
+    Scratch tmp(s);
     int32_t *din = nullptr, *dout = nullptr;
-    SCC_TRY(dalloc_t(&din, (size_t)count, s));
-    SCC_TRY(dalloc_t(&dout, (size_t)count, s));
-    int rc = to_device(din, items, sizeof(int32_t) * (size_t)count, s);
+    SCC_TRY(tmp.alloc(&din, (size_t)count));
+    SCC_TRY(tmp.alloc(&dout, (size_t)count));
+    SCC_TRY(to_device(din, items, sizeof(int32_t) * (size_t)count, s));
     int64_t got = 0;
     int ch = 0;
-    if (rc == SCC_OK) rc = run_bag_only(din, count, lambda, sigma, dout, &got, &ch, s);
-    if (rc == SCC_OK && got > count) rc = SCC_ERR_INTERNAL;
-    if (rc == SCC_OK) rc = from_device(out, dout, sizeof(int32_t) * (size_t)got, s);
-    if (rc == SCC_OK) rc = cuda_err(cudaStreamSynchronize(s));
-    dfree(din, s);
-    dfree(dout, s);
-    cudaStreamSynchronize(s);
-    SCC_TRY(rc);
+    SCC_TRY(run_bag_only(din, count, lambda, sigma, dout, &got, &ch, s));
+    if (got > count) return SCC_ERR_INTERNAL;
+    SCC_TRY(from_device(out, dout, sizeof(int32_t) * (size_t)got, s));
+    SCC_CUDA(cudaStreamSynchronize(s));
     *nout = got;
     if (chunks) *chunks = ch;
     return SCC_OK;
@@ -1107,15 +1083,16 @@ int scc_debug_pair_table(const uint64_t* keys, int64_t count, int64_t init_cap, 
     cudaStream_t s = (cudaStream_t)stream;
     unsigned long long *dk = nullptr, *tab = nullptr, *cnt = nullptr, *dout = nullptr;
     int* ovf = nullptr;
-    SCC_TRY(dalloc_t(&dk, (size_t)count, s));
-    SCC_TRY(dalloc_t(&cnt, 2, s));
-    SCC_TRY(dalloc_t(&ovf, 1, s));
-    SCC_TRY(dalloc_t(&dout, (size_t)count, s));
+    Scratch tmp(s);
+    SCC_TRY(tmp.alloc(&dk, (size_t)count));
+    SCC_TRY(tmp.alloc(&cnt, 2));
+    SCC_TRY(tmp.alloc(&ovf, 1));
+    SCC_TRY(tmp.alloc(&dout, (size_t)count));
     SCC_TRY(to_device(dk, keys, sizeof(uint64_t) * (size_t)count, s));
     // insert in slices; when a slice pushes the load over 1/2 (or a probe runs
     // too far) the table doubles and every key is rehashed (Sec. 4.5 regrowth)
     int64_t cap = init_cap;
-    SCC_TRY(dalloc_t(&tab, (size_t)cap, s));
+    SCC_TRY(tmp.alloc(&tab, (size_t)cap));
     SCC_CUDA(cudaMemsetAsync(tab, 0xff, (size_t)cap * 8, s));
     SCC_CUDA(cudaMemsetAsync(cnt, 0, 16, s));
     int nres = 0;
@@ -1131,11 +1108,11 @@ int scc_debug_pair_table(const uint64_t* keys, int64_t count, int64_t init_cap, 
         SCC_CUDA(cudaStreamSynchronize(s));
         if (hov || 2 * (int64_t)hc > cap) {
             unsigned long long* t2 = nullptr;
-            SCC_TRY(dalloc_t(&t2, (size_t)cap * 2, s));
+            SCC_TRY(tmp.alloc(&t2, (size_t)cap * 2));
             SCC_CUDA(cudaMemsetAsync(t2, 0xff, (size_t)cap * 16, s));
             SCC_CUDA(cudaMemsetAsync(ovf, 0, sizeof(int), s));
             SCC_TRY(launch_table_rehash(tab, cap, t2, cap * 2, ovf, s));
-            dfree(tab, s);
+            tmp.release(tab);
             tab = t2;
             cap *= 2;
             ++nres;
@@ -1151,15 +1128,9 @@ int scc_debug_pair_table(const uint64_t* keys, int64_t count, int64_t init_cap, 
     unsigned long long tot = 0;
     SCC_CUDA(cudaMemcpyAsync(&tot, cnt + 1, 8, cudaMemcpyDeviceToHost, s));
     SCC_CUDA(cudaStreamSynchronize(s));
-    int rc = (int64_t)tot <= count ? from_device(out, dout, sizeof(uint64_t) * (size_t)tot, s) : SCC_ERR_INTERNAL;
-    if (rc == SCC_OK) rc = cuda_err(cudaStreamSynchronize(s));
-    dfree(dk, s);
-    dfree(tab, s);
-    dfree(cnt, s);
-    dfree(ovf, s);
-    dfree(dout, s);
-    cudaStreamSynchronize(s);
-    SCC_TRY(rc);
+    if ((int64_t)tot > count) return SCC_ERR_INTERNAL;
+    SCC_TRY(from_device(out, dout, sizeof(uint64_t) * (size_t)tot, s));
+    SCC_CUDA(cudaStreamSynchronize(s));
     *nout = (int64_t)tot;
     if (resizes) *resizes = nres;
     return SCC_OK;

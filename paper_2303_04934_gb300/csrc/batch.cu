@@ -1105,8 +1105,9 @@ int batch_create_impl(scc_batch* h, int32_t G, const int64_t* vbase, const int64
         SCC_CUDA(cudaMemcpyAsync(h->offsets, offsets, sizeof(int32_t) * (size_t)(h->nv + G), cudaMemcpyDefault, s));
     if (h->na > 0)
         SCC_CUDA(cudaMemcpyAsync(h->targets, targets, sizeof(int32_t) * (size_t)h->na, cudaMemcpyDefault, s));
+    Scratch tmp(s);
     int* bad = nullptr;
-    SCC_TRY(dalloc_t(&bad, 1, s));
+    SCC_TRY(tmp.alloc(&bad, 1));
     SCC_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), s));
     if (G > 0) {
         k_batch_validate<<<std::min<int32_t>(G, 65535), 256, 0, s>>>(G, h->vbase, h->ebase, h->offsets, h->targets,
@@ -1116,7 +1117,7 @@ int batch_create_impl(scc_batch* h, int32_t G, const int64_t* vbase, const int64
     int hbad = 0;
     SCC_CUDA(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
     SCC_CUDA(cudaStreamSynchronize(s));
-    dfree(bad, s);
+    tmp.release(bad);
     if (hbad) return SCC_ERR_INVALID_ARG;
     // processing order: decreasing work (arcs + vertices), so long graphs start first
     h->order_h.resize((size_t)G);
@@ -1358,8 +1359,9 @@ SCC_API int scc_batch_autotune(scc_batch_handle h, int32_t sample, cudaStream_t 
     const int32_t want = (sample <= 0 || sample >= h->G) ? h->G : sample;
     const double step = (double)h->G / (double)want;
     for (int32_t i = 0; i < want; ++i) sub.push_back(h->order_h[(size_t)std::min<double>(h->G - 1, i * step)]);
+    Scratch tmp(stream);
     int32_t* dsub = nullptr;
-    SCC_TRY(dalloc_t(&dsub, sub.size(), stream));
+    SCC_TRY(tmp.alloc(&dsub, sub.size()));
     SCC_CUDA(cudaMemcpyAsync(dsub, sub.data(), sizeof(int32_t) * sub.size(), cudaMemcpyHostToDevice, stream));
     const int taus[] = {16, 64, 256, 1024, 4096};
     const int blocks[] = {128, 256, 512};
@@ -1389,7 +1391,7 @@ SCC_API int scc_batch_autotune(scc_batch_handle h, int32_t sample, cudaStream_t 
         }
         if (rc != SCC_OK) break;
     }
-    dfree(dsub, stream);
+    tmp.release(dsub);
     cudaStreamSynchronize(stream);
     const int rc2 = scc_batch_set_config(h, rc == SCC_OK ? &bc : &base);
     if (rc != SCC_OK) return rc;

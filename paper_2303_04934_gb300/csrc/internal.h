@@ -40,6 +40,44 @@ inline int dalloc_t(T** p, size_t count, cudaStream_t s) {
     return dalloc(reinterpret_cast<void**>(p), count * sizeof(T), s);
 }
 
+// The device temporaries of one host call: every allocation made through it is
+// freed (stream-ordered on s) when the call returns, on error paths too, unless
+// it was freed earlier (release) or handed to a longer-lived owner (keep).
+class Scratch {
+  public:
+    explicit Scratch(cudaStream_t s) : s_(s) {}
+    Scratch(const Scratch&) = delete;
+    Scratch& operator=(const Scratch&) = delete;
+    ~Scratch() {
+        for (int i = 0; i < n_; ++i) dfree(p_[i], s_);
+    }
+    template <class T>
+    int alloc(T** p, size_t count) {
+        *p = nullptr;
+        if (n_ == kMax) return SCC_ERR_INTERNAL;
+        const int rc = dalloc_t(p, count, s_);
+        if (rc == SCC_OK) p_[n_++] = *p;
+        return rc;
+    }
+    void release(const void* p) {
+        for (int i = 0; i < n_; ++i)
+            if (p && p_[i] == p) {
+                dfree(p_[i], s_);
+                p_[i] = nullptr;
+            }
+    }
+    void keep(const void* p) {
+        for (int i = 0; i < n_; ++i)
+            if (p && p_[i] == p) p_[i] = nullptr;
+    }
+
+  private:
+    static constexpr int kMax = 32;
+    cudaStream_t s_;
+    void* p_[kMax] = {};
+    int n_ = 0;
+};
+
 // True when p is device (or managed) memory.
 bool is_device_ptr(const void* p);
 const void* mapped_host_ptr(const void* p);

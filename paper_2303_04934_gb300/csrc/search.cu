@@ -357,8 +357,9 @@ int run_bag_only(const int32_t* items, int64_t count, int lambda, int sigma, int
     P.lambda = lambda;
     P.sigma = sigma;
     P.nslots = std::max<long long>(4 * count, 4ll * lambda);
-    SCC_TRY(dalloc(reinterpret_cast<void**>(&P.slots), (size_t)P.nslots * 4, st));
-    SCC_TRY(dalloc(reinterpret_cast<void**>(&P.ctl), sizeof(EngineCtl), st));
+    Scratch tmp(st);
+    SCC_TRY(tmp.alloc(&P.slots, (size_t)P.nslots));
+    SCC_TRY(tmp.alloc(&P.ctl, 1));
     SCC_CUDA(cudaMemsetAsync(P.slots, 0xff, (size_t)P.nslots * 4, st));
     SCC_CUDA(cudaMemsetAsync(P.ctl, 0, sizeof(EngineCtl), st));
     int per_sm = 0;
@@ -371,8 +372,6 @@ int run_bag_only(const int32_t* items, int64_t count, int lambda, int sigma, int
     memset(&h, 0, sizeof(h));
     if (rc == SCC_OK) rc = cuda_err(cudaMemcpyAsync(&h, P.ctl, sizeof(EngineCtl), cudaMemcpyDeviceToHost, st));
     if (rc == SCC_OK) rc = cuda_err(cudaStreamSynchronize(st));
-    dfree(P.slots, st);
-    dfree(P.ctl, st);
     SCC_TRY(rc);
     if (h.err) return h.err;
     *nout = h.ring[1].items;
