@@ -26,8 +26,11 @@
  *    throws. On failure, outputs are undefined. A handle is not thread-safe: one
  *    host thread at a time per handle.
  *  - Memory: the library allocates its device buffers stream-ordered
- *    (cudaMallocAsync) from the device's default memory pool and frees them in
- *    scc_graph_destroy.
+ *    (cudaMallocFromPoolAsync) from a memory pool of its own on the current
+ *    device (the device's default pool if that cannot be created), whose release
+ *    threshold keeps freed memory for reuse by later calls. A handle's buffers
+ *    are freed in its destroy call; a call's temporaries are freed
+ *    (stream-ordered) when it returns, on error paths too.
  */
 #ifndef SCC_GB300_SCC_H
 #define SCC_GB300_SCC_H

@@ -40,7 +40,6 @@
 #define SCC_BATCH_H
 
 #include <stdint.h>
-#include <cuda_runtime.h>
 
 #include "scc.h"
 
@@ -81,7 +80,7 @@ typedef struct scc_batch* scc_batch_handle;
 /* Validate and copy a packed batch (layout above) to the device, stream-ordered
    on `stream`, and return a handle. G = 0 is allowed. */
 SCC_API int scc_batch_create(int32_t G, const int64_t* vbase, const int64_t* ebase, const int32_t* offsets,
-                             const int32_t* targets, cudaStream_t stream, scc_batch_handle* out);
+                             const int32_t* targets, void* stream, scc_batch_handle* out);
 SCC_API int scc_batch_destroy(scc_batch_handle h);
 /* SCC_ERR_INVALID_ARG for out-of-range values (the configuration is unchanged). */
 SCC_API int scc_batch_set_config(scc_batch_handle h, const scc_batch_config* cfg);
@@ -94,7 +93,7 @@ SCC_API int scc_batch_get_config(scc_batch_handle h, scc_batch_config* cfg);
  * device output buffer not seen before allocates working memory and captures
  * the graph first.
  */
-SCC_API int scc_batch_run(scc_batch_handle h, int32_t* labels_out, cudaStream_t stream);
+SCC_API int scc_batch_run(scc_batch_handle h, int32_t* labels_out, void* stream);
 
 /*
  * Autotuner: times the batched kernel on a sample of about `sample` graphs
@@ -104,7 +103,7 @@ SCC_API int scc_batch_run(scc_batch_handle h, int32_t* labels_out, cudaStream_t 
  * the handle and returns it (and its time in milliseconds) when the pointers
  * are not NULL.
  */
-SCC_API int scc_batch_autotune(scc_batch_handle h, int32_t sample, cudaStream_t stream, scc_batch_config* best,
+SCC_API int scc_batch_autotune(scc_batch_handle h, int32_t sample, void* stream, scc_batch_config* best,
                                double* best_ms);
 
 typedef struct scc_batch_stats {

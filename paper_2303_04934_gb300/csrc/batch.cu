@@ -1282,7 +1282,8 @@ SCC_API int scc_batch_config_default(scc_batch_config* cfg) {
 }
 
 SCC_API int scc_batch_create(int32_t G, const int64_t* vbase, const int64_t* ebase, const int32_t* offsets,
-                             const int32_t* targets, cudaStream_t stream, scc_batch_handle* out) {
+                             const int32_t* targets, void* stream_, scc_batch_handle* out) {
+    cudaStream_t stream = (cudaStream_t)stream_;
     if (!out || G < 0 || !vbase || !ebase) return SCC_ERR_INVALID_ARG;
     *out = nullptr;
     scc_batch* h = new (std::nothrow) scc_batch();
@@ -1332,7 +1333,8 @@ SCC_API int scc_batch_get_config(scc_batch_handle h, scc_batch_config* cfg) {
     return SCC_OK;
 }
 
-SCC_API int scc_batch_run(scc_batch_handle h, int32_t* labels_out, cudaStream_t stream) {
+SCC_API int scc_batch_run(scc_batch_handle h, int32_t* labels_out, void* stream_) {
+    cudaStream_t stream = (cudaStream_t)stream_;
     if (!h || (!labels_out && h->nv > 0)) return SCC_ERR_INVALID_ARG;
     if (h->G == 0 || h->nv == 0) return SCC_OK;
     const bool dev_out = is_device_ptr(labels_out);
@@ -1345,8 +1347,9 @@ SCC_API int scc_batch_run(scc_batch_handle h, int32_t* labels_out, cudaStream_t 
     return SCC_OK;
 }
 
-SCC_API int scc_batch_autotune(scc_batch_handle h, int32_t sample, cudaStream_t stream, scc_batch_config* best,
+SCC_API int scc_batch_autotune(scc_batch_handle h, int32_t sample, void* stream_, scc_batch_config* best,
                                double* best_ms) {
+    cudaStream_t stream = (cudaStream_t)stream_;
     if (!h) return SCC_ERR_INVALID_ARG;
     const scc_batch_config base = h->cfg;
     if (h->G == 0) {
