@@ -110,8 +110,11 @@ typedef struct scc_graph* scc_handle; /* opaque, owned by the library */
 /*
  * Copy a CSR graph to the device and build what every later call needs: the
  * self-loop-free forward CSR and its transpose G^T (Sec. 2: a backward search is a
- * forward search on G^T), built with an in-degree histogram, an exclusive scan and
- * a scatter.
+ * forward search on G^T). G^T is a counting sort of the arcs by target in three
+ * levels (buckets, sub-buckets of at most 1024 targets, rows), each pass reading
+ * and writing whole tiles; within a row of G^T the sources are in no set order.
+ * Page-locked host targets are read over the host link by the first pass itself,
+ * in chunks whose later passes overlap the next chunk's transfer.
  *   n        number of vertices, 0 <= n < 2^31 - 1.
  *   m        number of arcs, 0 <= m <= INT32_MAX.
  *   offsets  host or device int32[n+1]; targets host or device int32[m]. Both are
