@@ -58,6 +58,8 @@ def _load():
             lib.or_reach_mask.argtypes = [i64, vp, vp, vp, i64, vp]
             lib.or_pivot_order.argtypes = [i64, vp, u64, vp]
             lib.or_batch_bounds.argtypes = [i64, dbl, vp, i64]
+            lib.or_mix64.argtypes = [u64]
+            lib.or_mix64.restype = u64
             for f in ("or_scc_tarjan", "or_transpose", "or_trim", "or_reach_set", "or_multi_reach",
                       "or_reach_mask", "or_pivot_order", "or_batch_bounds"):
                 getattr(lib, f).restype = i64
@@ -151,6 +153,11 @@ def pivot_order(active, seed: int):
     out = np.empty(max(n, 1), np.int32)
     N = _load().or_pivot_order(n, ap, seed & (2**64 - 1), out.ctypes.data)
     return out[:N]
+
+
+def mix64(z: int) -> int:
+    """The SplitMix64 finaliser the pivot order's Feistel rounds use."""
+    return int(_load().or_mix64(z & (2**64 - 1)))
 
 
 def batch_bounds(N: int, beta: float):

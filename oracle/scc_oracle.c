@@ -236,6 +236,7 @@ static uint64_t mix64(uint64_t z) {
     z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
     return z ^ (z >> 31);
 }
+OR_API uint64_t or_mix64(uint64_t z) { return mix64(z); }
 
 /*
  * A bijection of [0, N) (Black & Rogaway, "Ciphers with arbitrary finite

@@ -202,3 +202,17 @@ def test_pivot_order_is_a_seeded_bijection():
             o2 = oracle.pivot_order(active, seed=43)
             assert not np.array_equal(o1, o2)
             assert not np.array_equal(o1, np.flatnonzero(active))
+
+
+def test_pivot_round_function_is_splitmix64():
+    """The round function is the SplitMix64 finaliser (Steele, Lea & Flood,
+    OOPSLA 2014). The generator adds 0x9E3779B97F4A7C15 to its state and returns
+    the finaliser of the new state; from state 1234567 its published reference
+    implementation (Vigna's splitmix64.c) gives the five outputs below."""
+    want = [6457827717110365317, 3203168211198807973, 9817491932198370423, 4593380528125082431,
+            16408922859458223821]
+    state, got = 1234567, []
+    for _ in want:
+        state = (state + 0x9E3779B97F4A7C15) % 2**64
+        got.append(oracle.mix64(state))
+    assert got == want
