@@ -32,7 +32,8 @@ long long launch_count();
         SCC_TRY(::scc::cuda_err(cudaGetLastError()));     \
     } while (0)
 
-// Stream-ordered device allocation from the default pool.
+// Stream-ordered device allocation from the library's memory pool on the
+// current device (the device's default pool if that cannot be created).
 int dalloc(void** p, size_t bytes, cudaStream_t s);
 void dfree(void* p, cudaStream_t s);
 template <class T>
@@ -93,7 +94,7 @@ int device_info(DeviceInfo* out);
 // *bad (device int) becomes nonzero if malformed.
 int launch_validate_offsets(const int32_t* off, int32_t n, int64_t m, int* bad, cudaStream_t s);
 // Transposed CSR (transpose.cu). bucket_shift(n): vertices per coarse bucket
-// = 2^shift, at most 1024 buckets.
+// = 2^shift, at most 512 buckets.
 int bucket_shift(int32_t n);
 // trow[t] = row of arc t * step (t < T), trow[T] = row of the last arc; the
 // table has tile_rows_count(m) entries and drives the arc passes below.
@@ -178,9 +179,6 @@ int launch_init_labels(const int32_t* off, const int32_t* toff, int32_t n, int32
                        unsigned long long* nact, cudaStream_t s);
 // act = increasing list of v with label[v] >= 0 (scan-based, order preserving).
 int launch_compact_active(const int32_t* label, int32_t n, void* scan_tmp, int32_t* act, cudaStream_t s);
-// sources = { act[pi(p)] : p in [p0, p1), label >= 0 }, *k = count (device).
-int launch_batch_sources(const int32_t* act, int64_t N, uint64_t seed, int64_t p0, int64_t p1, const int32_t* label,
-                         int32_t* sources, int* k, cudaStream_t s);
 // Pivot positions p in [p0, N) whose vertex act[pi(p)] is still active, in
 // increasing p: rem_pos[j] = p, rem_v[j] = the vertex; their number is
 // pos_tmp[N - p0] after the call (exclusive scan of the flags).

@@ -220,23 +220,6 @@ __global__ void k_pivot_order(const int32_t* __restrict__ act, int64_t N, Feiste
         order[p] = act[f.perm((uint64_t)p, (uint64_t)N)];
 }
 
-__global__ void k_batch_sources(const int32_t* __restrict__ act, int64_t N, Feistel f, int64_t p0, int64_t p1,
-                                const int32_t* __restrict__ label, int32_t* sources, int* k) {
-    for (int64_t b = p0 + (int64_t)blockIdx.x * blockDim.x; b < p1; b += (int64_t)gridDim.x * blockDim.x) {
-        int64_t p = b + threadIdx.x;
-        int v = -1;
-        if (p < p1) {
-            v = act[f.perm((uint64_t)p, (uint64_t)N)];
-            if (label[v] < 0) v = -1;
-        }
-        uint32_t msk = __ballot_sync(kFull, v >= 0);
-        int base = 0;
-        if (lane_id() == 0 && msk) base = atomicAdd(k, __popc(msk));
-        base = __shfl_sync(kFull, base, 0);
-        if (v >= 0) sources[base + __popc(msk & lanemask_lt())] = v;
-    }
-}
-
 // Remaining pivot positions p >= p0 whose vertex is still active, in order.
 __global__ void k_rem_flags(const int32_t* __restrict__ act, int64_t N, Feistel f, int64_t p0,
                             const int32_t* __restrict__ label, int32_t* flags) {
@@ -620,16 +603,6 @@ int64_t feistel_perm_host(int64_t p, int64_t N, uint64_t seed) {
     Feistel f;
     f.init(seed, (uint64_t)N);
     return (int64_t)f.perm((uint64_t)p, (uint64_t)N);
-}
-
-int launch_batch_sources(const int32_t* act, int64_t N, uint64_t seed, int64_t p0, int64_t p1, const int32_t* label,
-                         int32_t* sources, int* k, cudaStream_t s) {
-    if (p1 <= p0) return SCC_OK;
-    Feistel f;
-    f.init(seed, (uint64_t)N);
-    k_batch_sources<<<grid_for(p1 - p0, kBlk), kBlk, 0, s>>>(act, N, f, p0, p1, label, sources, k);
-    SCC_LAUNCH();
-    return SCC_OK;
 }
 
 int launch_remaining(const int32_t* act, int64_t N, uint64_t seed, int64_t p0, const int32_t* label,
