@@ -128,6 +128,34 @@ SCC_API int scc_debug_batch_times(struct scc_batch* h, uint64_t* out);
 SCC_API int scc_debug_batch_groups(int32_t G, const int64_t* vbase, const int64_t* ebase, int64_t max_vertices,
                                    int64_t max_arcs, int32_t* groups, int32_t* ngroups);
 
+/*
+ * The serving loop's scheduling decisions (scc_serve.h) on a described queue,
+ * host only (no device work). No counterpart in the paper.
+ *
+ * Admission: count pending requests in arrival order, request i needing
+ * need[i] bytes and having waited waited_ms[i]; in_use bytes are held of cap.
+ * Request i is admitted when in_use + need[i] <= cap (in_use then grows by
+ * need[i]); the first request that does not fit lets later ones pass while it
+ * has waited at most max_bypass_ms, and ends the pass once it has waited
+ * longer. admitted (int32[count]) receives the admitted indices in increasing
+ * order, *nadmitted their number.
+ */
+SCC_API int scc_debug_serve_admission(int32_t count, const int64_t* need, const double* waited_ms, int64_t in_use,
+                                      int64_t cap, double max_bypass_ms, int32_t* admitted, int32_t* nadmitted);
+/*
+ * Unit selection: count admitted requests in arrival order; kind[i] 0 (SCC;
+ * small[i] != 0 when the batched kernel takes it) or 1 (reachability on
+ * resident graph graph[i], direction dir[i], with nsrc[i] sources). The unit
+ * of request 0, as increasing indices into unit (int32[count]), *nunit their
+ * number: a reachability query with every later query on the same graph and
+ * direction while the sources stay within 128 (merge_reach != 0; otherwise
+ * request 0 alone); a small SCC request with the next small ones, batch_graphs
+ * at most; a larger SCC request alone. count = 0 gives an empty unit.
+ */
+SCC_API int scc_debug_serve_unit(int32_t count, const int32_t* kind, const int32_t* small, const int32_t* graph,
+                                 const int32_t* dir, const int32_t* nsrc, int32_t merge_reach, int32_t batch_graphs,
+                                 int32_t* unit, int32_t* nunit);
+
 #ifdef __cplusplus
 }
 #endif

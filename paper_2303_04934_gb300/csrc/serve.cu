@@ -52,6 +52,65 @@ __global__ void k_split_bits(const unsigned long long* __restrict__ mask, int wo
     }
 }
 
+// ---------------------------------------------------------------- policy --
+// The server's two scheduling decisions as functions of the queue alone, so
+// that the host can test them (scc_debug_serve_admission, _unit).
+
+// Admission in arrival order over `count` pending requests: request i is
+// admitted when fits(i) holds (fits reserves its bytes); the first request
+// that does not fit lets later ones pass while waited_ms(i) <= max_bypass_ms,
+// and ends the pass once it has waited longer. Appends the admitted indices,
+// in increasing order, to `take`.
+template <class Fits, class Waited>
+void admission_pass(size_t count, double max_bypass_ms, Fits fits, Waited waited_ms, std::vector<size_t>& take) {
+    bool blocked = false;
+    for (size_t i = 0; i < count; ++i) {
+        if (fits(i)) {
+            take.push_back(i);
+            continue;
+        }
+        if (!blocked && waited_ms(i) > max_bypass_ms) break;  // no more passing
+        blocked = true;
+    }
+}
+
+struct UnitItem {
+    int kind;       // 0 SCC, 1 reachability
+    bool small;     // an SCC request the batched kernel takes
+    int32_t graph;  // reachability: resident graph and direction
+    int32_t dir;
+    int32_t nsrc;   // reachability: sources
+};
+
+// The unit of the oldest admitted request q[0], as increasing indices into q:
+// a reachability query with every later query on the same graph and direction
+// while the sources stay within kMaxMergedSources (merge_reach; otherwise q[0]
+// alone); a small SCC request with the next small ones, batch_graphs at most;
+// a larger SCC request alone.
+std::vector<size_t> unit_select(const std::vector<UnitItem>& q, bool merge_reach, int batch_graphs) {
+    std::vector<size_t> u;
+    if (q.empty()) return u;
+    const UnitItem& h = q[0];
+    if (h.kind == 1) {
+        int k = 0;
+        for (size_t i = 0; i < q.size(); ++i) {
+            const UnitItem& r = q[i];
+            const bool same = r.kind == 1 && r.graph == h.graph && r.dir == h.dir;
+            if (same && (u.empty() || (merge_reach && k + r.nsrc <= kMaxMergedSources))) {
+                k += r.nsrc;
+                u.push_back(i);
+            }
+            if (!merge_reach) break;
+        }
+    } else if (h.small) {
+        for (size_t i = 0; i < q.size() && (int)u.size() < std::max(1, batch_graphs); ++i)
+            if (q[i].kind == 0 && q[i].small) u.push_back(i);
+    } else {
+        u.push_back(0);
+    }
+    return u;
+}
+
 struct Request {
     int64_t id = 0;
     int kind = 0;  // 0 SCC, 1 reachability
@@ -189,43 +248,55 @@ int upload(scc_server* S, Request& r) {
     return SCC_OK;
 }
 
+// Moves q[idx[0]], q[idx[1]], ... (increasing indices) into out, in that
+// order, and erases them from q.
+void take_indices(std::deque<ReqPtr>& q, const std::vector<size_t>& idx, std::vector<ReqPtr>& out) {
+    std::deque<ReqPtr> rest;
+    size_t j = 0;
+    for (size_t i = 0; i < q.size(); ++i) {
+        if (j < idx.size() && idx[j] == i) {
+            out.push_back(std::move(q[i]));
+            ++j;
+        } else {
+            rest.push_back(std::move(q[i]));
+        }
+    }
+    q.swap(rest);
+}
+
 // Admission in arrival order; a request that does not fit waits while later
-// ones that fit pass it, until it has waited max_bypass_ms.
+// ones that fit pass it, until it has waited max_bypass_ms. The admitted
+// requests' uploads start on the copy stream in arrival order.
 void admit(scc_server* S) {
     const auto now = Clock::now();
-    bool blocked = false;
-    for (auto it = S->pending.begin(); it != S->pending.end();) {
-        Request& r = **it;
-        const size_t need = request_bytes(S, r);
-        bool fits;
-        {
+    std::vector<size_t> take;
+    admission_pass(
+        S->pending.size(), S->cfg.max_bypass_ms,
+        [&](size_t i) {
+            Request& r = *S->pending[i];
+            const size_t need = request_bytes(S, r);
             std::lock_guard<std::mutex> lk(S->mu);
-            fits = S->mem_in_use + (int64_t)need <= S->cfg.mem_cap_bytes;
-            if (fits) {
-                S->mem_in_use += (int64_t)need;
-                S->mem_peak = std::max(S->mem_peak, S->mem_in_use);
-                S->admitted_now++;
-                S->st.max_admitted = std::max(S->st.max_admitted, S->admitted_now);
-            }
-        }
-        if (!fits) {
-            if (!blocked && ms_between(r.t_sub, now) > S->cfg.max_bypass_ms) break;  // no more passing
-            blocked = true;
-            ++it;
-            continue;
-        }
-        r.mem = need;
-        if (r.kind == 0 && S->cfg.prefetch) {
-            const int rc = upload(S, r);
+            if (S->mem_in_use + (int64_t)need > S->cfg.mem_cap_bytes) return false;
+            S->mem_in_use += (int64_t)need;
+            S->mem_peak = std::max(S->mem_peak, S->mem_in_use);
+            S->admitted_now++;
+            S->st.max_admitted = std::max(S->st.max_admitted, S->admitted_now);
+            r.mem = need;
+            return true;
+        },
+        [&](size_t i) { return ms_between(S->pending[i]->t_sub, now); }, take);
+    std::vector<ReqPtr> adm;
+    take_indices(S->pending, take, adm);
+    for (auto& p : adm) {
+        if (p->kind == 0 && S->cfg.prefetch) {
+            const int rc = upload(S, *p);
             if (rc != SCC_OK) {
-                release_inputs(S, r);
-                finish(S, r, rc);
-                it = S->pending.erase(it);
+                release_inputs(S, *p);
+                finish(S, *p, rc);
                 continue;
             }
         }
-        S->admitted.push_back(*it);
-        it = S->pending.erase(it);
+        S->admitted.push_back(p);
     }
 }
 
@@ -395,40 +466,23 @@ void run_batched(scc_server* S, std::vector<ReqPtr>& u) {
 
 // The unit of the oldest admitted request, run to completion.
 void run_unit(scc_server* S) {
-    ReqPtr head = S->admitted.front();
+    std::vector<UnitItem> q;
+    q.reserve(S->admitted.size());
+    for (const ReqPtr& r : S->admitted)
+        q.push_back({r->kind, is_small(S, *r), r->graph, r->dir, (int32_t)r->src.size()});
+    const std::vector<size_t> pick = unit_select(q, S->cfg.merge_reach != 0, S->cfg.batch_graphs);
     std::vector<ReqPtr> u;
+    take_indices(S->admitted, pick, u);
     const auto t0 = Clock::now();
     double* busy = nullptr;
-    if (head->kind == 1) {
-        int k = 0;
-        for (auto it = S->admitted.begin(); it != S->admitted.end();) {
-            Request& r = **it;
-            const bool same = r.kind == 1 && r.graph == head->graph && r.dir == head->dir;
-            if (same && (u.empty() || (S->cfg.merge_reach && k + (int)r.src.size() <= kMaxMergedSources))) {
-                k += (int)r.src.size();
-                u.push_back(*it);
-                it = S->admitted.erase(it);
-            } else {
-                ++it;
-            }
-            if (!S->cfg.merge_reach) break;
-        }
+    if (q[0].kind == 1) {
         run_reach(S, u);
         busy = &S->st.busy_reach_ms;
-    } else if (is_small(S, *head)) {
-        for (auto it = S->admitted.begin(); it != S->admitted.end() && (int)u.size() < S->cfg.batch_graphs;) {
-            if (is_small(S, **it)) {
-                u.push_back(*it);
-                it = S->admitted.erase(it);
-            } else {
-                ++it;
-            }
-        }
+    } else if (q[0].small) {
         run_batched(S, u);
         busy = &S->st.busy_batched_ms;
     } else {
-        S->admitted.pop_front();
-        run_plain(S, *head);
+        run_plain(S, *u[0]);
         busy = &S->st.busy_plain_ms;
     }
     std::lock_guard<std::mutex> lk(S->mu);
@@ -698,6 +752,43 @@ SCC_API int scc_server_reset_stats(scc_server_handle S) {
     S->lat_scc.clear();
     S->lat_reach.clear();
     S->mem_peak = S->mem_in_use;
+    return SCC_OK;
+}
+
+
+SCC_API int scc_debug_serve_admission(int32_t count, const int64_t* need, const double* waited_ms, int64_t in_use,
+                                      int64_t cap, double max_bypass_ms, int32_t* admitted, int32_t* nadmitted) {
+    if (count < 0 || !nadmitted || (count > 0 && (!need || !waited_ms || !admitted)) || !(max_bypass_ms >= 0))
+        return SCC_ERR_INVALID_ARG;
+    for (int32_t i = 0; i < count; ++i)
+        if (need[i] < 0) return SCC_ERR_INVALID_ARG;
+    std::vector<size_t> take;
+    admission_pass(
+        (size_t)count, max_bypass_ms,
+        [&](size_t i) {
+            if (in_use + need[i] > cap) return false;
+            in_use += need[i];
+            return true;
+        },
+        [&](size_t i) { return waited_ms[i]; }, take);
+    for (size_t j = 0; j < take.size(); ++j) admitted[j] = (int32_t)take[j];
+    *nadmitted = (int32_t)take.size();
+    return SCC_OK;
+}
+
+SCC_API int scc_debug_serve_unit(int32_t count, const int32_t* kind, const int32_t* small, const int32_t* graph,
+                                 const int32_t* dir, const int32_t* nsrc, int32_t merge_reach, int32_t batch_graphs,
+                                 int32_t* unit, int32_t* nunit) {
+    if (count < 0 || !nunit || (count > 0 && (!kind || !small || !graph || !dir || !nsrc || !unit)))
+        return SCC_ERR_INVALID_ARG;
+    std::vector<UnitItem> q((size_t)count);
+    for (int32_t i = 0; i < count; ++i) {
+        if ((kind[i] != 0 && kind[i] != 1) || nsrc[i] < 0) return SCC_ERR_INVALID_ARG;
+        q[i] = {kind[i], kind[i] == 0 && small[i] != 0, graph[i], dir[i], nsrc[i]};
+    }
+    const std::vector<size_t> u = unit_select(q, merge_reach != 0, batch_graphs);
+    for (size_t j = 0; j < u.size(); ++j) unit[j] = (int32_t)u[j];
+    *nunit = (int32_t)u.size();
     return SCC_OK;
 }
 

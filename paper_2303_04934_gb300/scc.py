@@ -34,7 +34,7 @@ EXPORTED = [
     "scc_debug_multi_reach", "scc_debug_reach_multi_wide", "scc_debug_hashbag", "scc_debug_pair_table", "scc_debug_launch_count",
     "scc_batch_config_default", "scc_batch_create", "scc_batch_destroy", "scc_batch_set_config",
     "scc_batch_get_config", "scc_batch_run", "scc_batch_autotune", "scc_batch_get_stats",
-    "scc_debug_batch_times", "scc_debug_batch_groups",
+    "scc_debug_batch_times", "scc_debug_batch_groups", "scc_debug_serve_admission", "scc_debug_serve_unit",
     "scc_server_config_default", "scc_server_create", "scc_server_destroy", "scc_server_add_graph",
     "scc_server_remove_graph", "scc_server_submit_scc", "scc_server_submit_reach", "scc_server_wait",
     "scc_server_drain", "scc_server_get_stats", "scc_server_reset_stats",
@@ -156,6 +156,8 @@ def load() -> ctypes.CDLL:
         "scc_batch_get_stats": ([vp, P(scc_batch_stats)], ctypes.c_int),
         "scc_debug_batch_times": ([vp, vp], ctypes.c_int),
         "scc_debug_batch_groups": ([i32, vp, vp, i64, i64, vp, P(i32)], ctypes.c_int),
+        "scc_debug_serve_admission": ([i32, vp, vp, i64, i64, ctypes.c_double, vp, P(i32)], ctypes.c_int),
+        "scc_debug_serve_unit": ([i32, vp, vp, vp, vp, vp, i32, i32, vp, P(i32)], ctypes.c_int),
         "scc_server_config_default": ([P(scc_server_config)], ctypes.c_int),
         "scc_server_create": ([P(scc_server_config), P(vp)], ctypes.c_int),
         "scc_server_destroy": ([vp], ctypes.c_int),
@@ -322,6 +324,34 @@ def scc_debug_batch_groups(vbase, ebase, max_vertices: int = 1 << 24, max_arcs: 
     _check(load().scc_debug_batch_groups(G, _ptr(vb), _ptr(eb), max_vertices, max_arcs, _ptr(out), ctypes.byref(ng)),
            "scc_debug_batch_groups")
     return [(int(out[2 * k]), int(out[2 * k + 1])) for k in range(ng.value)]
+
+
+def scc_debug_serve_admission(need, waited_ms, in_use: int, cap: int, max_bypass_ms: float) -> list:
+    """Indices of the pending requests (arrival order) one admission pass of the
+    server admits (host only)."""
+    nd = np.ascontiguousarray(need, dtype=np.int64)
+    wt = np.ascontiguousarray(waited_ms, dtype=np.float64)
+    if len(nd) != len(wt):
+        raise ValueError("need and waited_ms differ in length")
+    out = np.zeros(max(len(nd), 1), np.int32)
+    na = ctypes.c_int32()
+    _check(load().scc_debug_serve_admission(len(nd), _ptr(nd), _ptr(wt), in_use, cap, max_bypass_ms, _ptr(out),
+                                            ctypes.byref(na)), "scc_debug_serve_admission")
+    return out[:na.value].tolist()
+
+
+def scc_debug_serve_unit(kind, small, graph, dir, nsrc, merge_reach: bool = True, batch_graphs: int = 512) -> list:
+    """Indices of the admitted requests (arrival order) that join the unit of
+    the oldest one (host only)."""
+    cols = [np.ascontiguousarray(c, dtype=np.int32) for c in (kind, small, graph, dir, nsrc)]
+    count = len(cols[0])
+    if any(len(c) != count for c in cols):
+        raise ValueError("columns differ in length")
+    out = np.zeros(max(count, 1), np.int32)
+    nu = ctypes.c_int32()
+    _check(load().scc_debug_serve_unit(count, *[_ptr(c) for c in cols], int(bool(merge_reach)), batch_graphs,
+                                       _ptr(out), ctypes.byref(nu)), "scc_debug_serve_unit")
+    return out[:nu.value].tolist()
 
 
 class SccBatch:
