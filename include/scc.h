@@ -73,22 +73,23 @@ SCC_API const char* scc_error_string(int code);
  *               on the GPU a round's time is set by its longest local search,
  *               which on a graph of high degree grows faster with tau than the
  *               rounds it saves, and on a lattice or k-NN graph more slowly.
- *   beta        prefix-doubling multiplier, > 1 (Alg. 1 doubles the batches, the
+ *   beta        prefix-doubling multiplier in (1, 64] (Alg. 1 doubles the batches, the
  *               experiments use 1.5). Default 2: a batch costs rounds whose
  *               time on the GPU is set by memory latency more than by the pairs
  *               they visit, so fewer and larger batches are faster here.
- *   lambda      first hash-bag chunk size in slots, a power of two >= 1024
+ *   lambda      first hash-bag chunk size in slots, a power of two in [1024, 2^24]
  *               (Sec. 3.3; chunks grow lambda, 2*lambda, ...). Default 16384.
- *   sigma       hash-bag samples per chunk before it is declared full (Sec. 3.3,
- *               default 50).
+ *   sigma       hash-bag samples per chunk before it is declared full (Sec. 3.3),
+ *               1..2^20, default 50.
  *   block       threads per block of the search kernels (256; other values are
  *               rejected with SCC_ERR_INVALID_ARG).
  *   seeds       frontier items one warp takes per task, 1..32 (default 32).
  *   dense       0: the first-SCC single-reachability never switches to the dense
  *               (bottom-up) mode of Sec. 4.2; 1: it does once a round's frontier
- *               holds 1/20 of the searched class; k in [2, 1024]: once it holds
- *               1/k of it.
- *   seed        seed of the pivot permutation.
+ *               holds 1/20 of the searched class (the default); k in [2, 1024]:
+ *               once it holds 1/k of it.
+ *   seed        seed of the pivot permutation (default 0x5CC00).
+ * Out-of-range values are rejected with SCC_ERR_INVALID_ARG.
  */
 typedef struct scc_config {
     int32_t tau;

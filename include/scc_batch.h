@@ -57,9 +57,9 @@ extern "C" {
  *           block's rounds are short, so the default is the smallest, 256.
  *   sigma   hash-bag samples per chunk (Sec. 3.3), >= 1.
  *   seeds   frontier items one warp takes per task, 1..32.
- *   beta    prefix-doubling multiplier, > 1 (Alg. 1).
- *   blocks_per_sm  resident blocks per SM (0: as many as registers, shared
- *           memory and the working-memory budget allow).
+ *   beta    prefix-doubling multiplier in (1, 64] (Alg. 1).
+ *   blocks_per_sm  resident blocks per SM, 0..16 (0: as many as registers,
+ *           shared memory and the working-memory budget allow).
  *   seed    seed of the pivot permutation.
  */
 typedef struct scc_batch_config {
