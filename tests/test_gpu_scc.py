@@ -119,6 +119,42 @@ def test_page_locked_host_input():
         scc.SccGraph(g.n, torch.from_numpy(g.offsets).pin_memory(), bad)
 
 
+def _with_self_loops(g, count, seed):
+    """g with a self-loop added at the start of `count` random rows."""
+    rng = np.random.default_rng(seed)
+    sel = np.zeros(g.n, bool)
+    sel[rng.choice(g.n, count, replace=False)] = True
+    deg = np.diff(g.offsets.astype(np.int64))
+    off = np.zeros(g.n + 1, np.int64)
+    off[1:] = np.cumsum(deg + sel)
+    adj = np.empty(int(off[-1]), np.int32)
+    adj[off[:-1][sel]] = np.flatnonzero(sel)
+    rows = np.repeat(np.arange(g.n), deg)
+    within = np.arange(g.m) - np.repeat(g.offsets[:-1].astype(np.int64), deg)
+    adj[(off[:-1] + sel)[rows] + within] = g.targets
+    return gg.Graph(g.n, off.astype(np.int32), adj, g.name + "_self")
+
+
+def test_page_locked_host_input_in_chunks_with_self_loops_and_a_bad_target():
+    """A host graph large enough to be read in several chunks, with self-loops:
+    the forward CSR is rebuilt without them after the chunked intake and G^T is
+    built again in one chunk; a bad target in a late chunk is refused."""
+    import torch
+    g = _with_self_loops(gg.rmat(18, 16, seed=47), 5000, seed=48)
+    assert g.m > 3_500_000  # 7 chunks of whole 8,192-arc tiles
+    want, _ = oracle.scc_labels(g.n, g.offsets, g.targets)
+    off = torch.from_numpy(g.offsets).pin_memory()
+    adj = torch.from_numpy(g.targets).pin_memory()
+    with scc.SccGraph(g.n, off, adj) as G:
+        n, m, mt = scc.scc_graph_info(G.h)
+        assert (n, m, mt) == (g.n, g.m, g.m - 5000)
+        assert np.array_equal(labels_of(G, host=True), want)
+    bad = adj.clone().pin_memory()
+    bad[int(0.8 * g.m)] = g.n
+    with pytest.raises(scc.SccError):
+        scc.SccGraph(g.n, off, bad)
+
+
 def test_invariants_hold_on_gpu_output():
     g = gg.rmat(15, 8, seed=51)
     with make_graph(g) as G:
