@@ -155,6 +155,30 @@ def test_page_locked_host_input_in_chunks_with_self_loops_and_a_bad_target():
         scc.SccGraph(g.n, off, bad)
 
 
+@pytest.mark.parametrize("make", [
+    lambda: gg.rmat(14, 8, seed=61),
+    lambda: gg.rmat(13, 16, seed=62),                     # dense rounds (average degree >= 8)
+    lambda: gg.torus(2, 64, 0.5, seed=63),
+    lambda: gg.knn(20000, 5, seed=64),
+    lambda: gg.gnp(400, 0.004, seed=65, allow_self=True),
+    lambda: gg.from_edges(50, [(i, i + 1) for i in range(49)], name="chain"),  # one trim pass: the two ends
+], ids=["rmat14", "rmat13_ef16", "torus2d_64", "knn20k", "gnp_sparse_self", "chain"])
+def test_trim_and_first_scc_counts_match_the_oracle(make):
+    """The trimmed vertices (Sec. 4.1) and the size of the first pivot's SCC
+    (Sec. 4.2; the pivot is the first of the seeded order over the untrimmed
+    vertices) equal the oracle's."""
+    g = make()
+    want, _ = oracle.scc_labels(g.n, g.offsets, g.targets)
+    trimmed = oracle.trim(g.n, g.offsets, g.targets).astype(bool)
+    with make_graph(g) as G:
+        assert np.array_equal(labels_of(G), want)
+        st = G.stats()
+    assert st["n_trimmed"] == int(trimmed.sum())
+    order = oracle.pivot_order((~trimmed).astype(np.uint8), seed=scc.scc_config_default().seed)
+    first = int((want == want[order[0]]).sum()) if len(order) else 0
+    assert st["first_scc_size"] == first
+
+
 def test_invariants_hold_on_gpu_output():
     g = gg.rmat(15, 8, seed=51)
     with make_graph(g) as G:
