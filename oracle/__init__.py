@@ -10,6 +10,9 @@ reference leg may import this package. It shares no code with the CUDA path
 * :mod:`oracle.definition` (numpy): the definitions written out through the
   transitive closure, for tiny graphs -- the pins of the C oracle.
 * :mod:`oracle.invariants` (numpy): properties every correct SCC labelling has.
+* :mod:`oracle.bgss_model` (plain Python): the method's own steps (Alg. 1) with
+  the library's readings, sequentially on small graphs; its labels must be
+  Tarjan's.
 
 Paper: Wang, Dong, Gu, Sun, "Parallel Strong Connectivity Based on Faster
 Reachability" (SIGMOD 2023); section and algorithm numbers in the docstrings

@@ -216,3 +216,42 @@ def test_pivot_round_function_is_splitmix64():
         state = (state + 0x9E3779B97F4A7C15) % 2**64
         got.append(oracle.mix64(state))
     assert got == want
+
+
+# ------------------------------------------------- the method's own steps --
+
+def test_bgss_model_reaches_the_scc_partition():
+    """The sequential model of Alg. 1 with the library's readings (trim once,
+    first SCC, class trimming, prefix-doubling batches, classes by (old class,
+    max forward source, max backward source), canonical minimum) gives Tarjan's
+    labels: on every digraph with 3 vertices (self-loops included), on random
+    digraphs for several beta and pivot seeds, with and without class trimming."""
+    from oracle.bgss_model import bgss_labels
+    for edges in _all_digraphs(3, True):
+        off, adj = _csr(3, edges)
+        lab, _ = bgss_labels(3, off, adj)
+        assert np.array_equal(lab, oracle.scc_labels(3, off, adj)[0]), edges
+    rng = np.random.default_rng(0xB655)
+    for trial in range(400):
+        n = int(rng.integers(1, 61))
+        g = gg.gnp(n, float(rng.choice([0.02, 0.05, 0.1, 0.3])), seed=9000 + trial, allow_self=trial % 4 == 0)
+        want, _ = oracle.scc_labels(n, g.offsets, g.targets)
+        beta = float(rng.choice([1.1, 1.5, 2.0, 3.0]))
+        lab, st = bgss_labels(n, g.offsets, g.targets, beta=beta, seed=int(rng.integers(1 << 62)),
+                              class_trim=bool(trial % 2))
+        assert np.array_equal(lab, want), (trial, n, beta)
+        assert st["n_trimmed"] == int(oracle.trim(n, g.offsets, g.targets).sum())
+
+
+@pytest.mark.parametrize("make", [lambda: gg.torus(2, 16, 0.5, seed=3), lambda: gg.torus(3, 6, 0.4, seed=4),
+                                  lambda: gg.rmat(9, 4, seed=5), lambda: gg.knn(400, 3, seed=6)])
+def test_bgss_model_on_structured_graphs(make):
+    from oracle.bgss_model import bgss_labels
+    g = make()
+    want, _ = oracle.scc_labels(g.n, g.offsets, g.targets)
+    lab, st = bgss_labels(g.n, g.offsets, g.targets)
+    assert np.array_equal(lab, want)
+    # the first SCC is the SCC of the first pivot of the seeded order
+    active = 1 - oracle.trim(g.n, g.offsets, g.targets)
+    order = oracle.pivot_order(active, seed=0x5CC00)
+    assert st["first_scc_size"] == (int((want == want[order[0]]).sum()) if len(order) else 0)
