@@ -77,7 +77,9 @@ SCC_API int scc_server_submit_reach(scc_server_handle h, int32_t graph_id, const
                                     int32_t dir, uint64_t* out, int64_t* request_id);
 
 /* Block until the request has completed; its status (SCC_OK or an error code)
-   and latency (submission to results in host memory, milliseconds). */
+   and latency (submission to results in host memory, milliseconds). A result
+   is collected once: a later wait for the same id returns SCC_ERR_INVALID_ARG
+   at once, as does an id that was never returned by a submit call. */
 SCC_API int scc_server_wait(scc_server_handle h, int64_t request_id, int32_t* status, double* latency_ms);
 /* Block until every submitted request has completed. */
 SCC_API int scc_server_drain(scc_server_handle h);

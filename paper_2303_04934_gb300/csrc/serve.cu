@@ -21,6 +21,7 @@
 #include <mutex>
 #include <thread>
 #include <unordered_map>
+#include <unordered_set>
 #include <vector>
 
 #include "../../include/scc.h"
@@ -173,7 +174,8 @@ struct scc_server {
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
     std::deque<ReqPtr> intake;
-    std::unordered_map<int64_t, std::pair<int, double>> done;
+    std::unordered_map<int64_t, std::pair<int, double>> done;  // completed, not yet waited for
+    std::unordered_set<int64_t> inflight;                       // submitted, not yet completed
     int64_t next_id = 1;
     int64_t outstanding = 0;
     bool stop = false;
@@ -202,6 +204,7 @@ void finish(scc_server* S, Request& r, int status) {
     r.up = nullptr;
     std::lock_guard<std::mutex> lk(S->mu);
     S->done[r.id] = {status, lat};
+    S->inflight.erase(r.id);
     S->outstanding--;
     S->mem_in_use -= (int64_t)r.mem;
     S->admitted_now--;
@@ -527,6 +530,7 @@ int submit(scc_server* S, ReqPtr r, int64_t* id) {
     std::lock_guard<std::mutex> lk(S->mu);
     if (S->stop) return SCC_ERR_INVALID_ARG;
     r->id = S->next_id++;
+    S->inflight.insert(r->id);
     r->t_sub = Clock::now();
     S->outstanding++;
     S->st.submitted++;
@@ -712,8 +716,9 @@ SCC_API int scc_server_wait(scc_server_handle S, int64_t request_id, int32_t* st
     if (!S) return SCC_ERR_INVALID_ARG;
     std::unique_lock<std::mutex> lk(S->mu);
     if (request_id <= 0 || request_id >= S->next_id) return SCC_ERR_INVALID_ARG;
-    S->cv_done.wait(lk, [&] { return S->done.count(request_id) > 0; });
+    S->cv_done.wait(lk, [&] { return S->done.count(request_id) > 0 || S->inflight.count(request_id) == 0; });
     auto it = S->done.find(request_id);
+    if (it == S->done.end()) return SCC_ERR_INVALID_ARG;  // collected by an earlier wait
     if (status) *status = it->second.first;
     if (latency_ms) *latency_ms = it->second.second;
     S->done.erase(it);
