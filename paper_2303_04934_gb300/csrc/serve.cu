@@ -616,7 +616,7 @@ SCC_API int scc_server_destroy(scc_server_handle S) {
 
 SCC_API int scc_server_add_graph(scc_server_handle S, int32_t n, int64_t m, const int32_t* offsets,
                                  const int32_t* targets, int32_t* graph_id) {
-    if (!S || !graph_id) return SCC_ERR_INVALID_ARG;
+    if (!S || !graph_id || n < 0 || m < 0 || m > INT32_MAX) return SCC_ERR_INVALID_ARG;
     const size_t bytes = plain_bytes(n, m);
     {
         std::lock_guard<std::mutex> lk(S->mu);
