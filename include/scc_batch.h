@@ -81,6 +81,7 @@ typedef struct scc_batch* scc_batch_handle;
    on `stream`, and return a handle. G = 0 is allowed. */
 SCC_API int scc_batch_create(int32_t G, const int64_t* vbase, const int64_t* ebase, const int32_t* offsets,
                              const int32_t* targets, void* stream, scc_batch_handle* out);
+/* Free every buffer of h (the call synchronises the device first). NULL is ok. */
 SCC_API int scc_batch_destroy(scc_batch_handle h);
 /* SCC_ERR_INVALID_ARG for out-of-range values (the configuration is unchanged). */
 SCC_API int scc_batch_set_config(scc_batch_handle h, const scc_batch_config* cfg);

@@ -56,7 +56,8 @@ typedef struct scc_server* scc_server_handle;
 
 /* Start a server on the current device. */
 SCC_API int scc_server_create(const scc_server_config* cfg, scc_server_handle* out);
-/* Complete every submitted request, then stop the server and free everything. */
+/* Complete every submitted request, then stop the server and free everything.
+   NULL is ok. */
 SCC_API int scc_server_destroy(scc_server_handle h);
 
 /* A resident graph for reachability queries: its CSR and G^T stay on the

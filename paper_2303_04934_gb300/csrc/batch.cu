@@ -1303,7 +1303,7 @@ SCC_API int scc_batch_create(int32_t G, const int64_t* vbase, const int64_t* eba
 }
 
 SCC_API int scc_batch_destroy(scc_batch_handle h) {
-    if (!h) return SCC_ERR_INVALID_ARG;
+    if (!h) return SCC_OK;
     cudaDeviceSynchronize();
     batch_free(h, 0);
     cudaDeviceSynchronize();

@@ -596,7 +596,7 @@ SCC_API int scc_server_create(const scc_server_config* cfg, scc_server_handle* o
 }
 
 SCC_API int scc_server_destroy(scc_server_handle S) {
-    if (!S) return SCC_ERR_INVALID_ARG;
+    if (!S) return SCC_OK;
     {
         std::lock_guard<std::mutex> lk(S->mu);
         S->stop = true;

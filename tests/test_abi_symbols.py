@@ -53,6 +53,44 @@ def test_invalid_arguments_rejected_on_the_host(lib):
     assert lib.scc_set_config(None, None) == scc.SCC_ERR_INVALID_ARG
 
 
+def test_null_handles_and_bad_arguments_rejected_on_the_host(lib):
+    """Every entry point that takes a handle refuses NULL (destroy calls accept
+    it), and bad sizes are refused, before any CUDA call."""
+    E = scc.SCC_ERR_INVALID_ARG
+    i32, i64, dbl = ctypes.c_int32(), ctypes.c_int64(), ctypes.c_double()
+    for name, args in [
+        ("scc_get_stats", (None, None)), ("scc_graph_info", (None, None, None, None)),
+        ("reach_multi_noalloc", (None, None, 1, 0, None, None)),
+        ("scc_debug_csr", (None, 0, None, None, None)), ("scc_debug_trim", (None, None, None)),
+        ("scc_debug_pivot_order", (None, None, ctypes.byref(i32), None)),
+        ("scc_debug_single_reach", (None, None, 0, 0, None, None)),
+        ("scc_debug_multi_reach", (None, None, None, 1, 0, None, 0, ctypes.byref(i64), 0, None)),
+        ("scc_debug_reach_multi_wide", (None, None, 1, 0, None, None)),
+        ("scc_batch_create", (-1, None, None, None, None, None, None)),
+        ("scc_batch_set_config", (None, None)), ("scc_batch_get_config", (None, None)),
+        ("scc_batch_run", (None, None, None)), ("scc_batch_autotune", (None, 0, None, None, None)),
+        ("scc_batch_get_stats", (None, None)), ("scc_debug_batch_times", (None, None)),
+        ("scc_server_add_graph", (None, 1, 0, None, None, ctypes.byref(i32))),
+        ("scc_server_remove_graph", (None, 0)),
+        ("scc_server_submit_scc", (None, 1, 0, None, None, None, ctypes.byref(i64))),
+        ("scc_server_submit_reach", (None, 0, None, 1, 0, None, ctypes.byref(i64))),
+        ("scc_server_wait", (None, 1, ctypes.byref(i32), ctypes.byref(dbl))),
+        ("scc_server_drain", (None,)), ("scc_server_get_stats", (None, None)), ("scc_server_reset_stats", (None,)),
+    ]:
+        assert getattr(lib, name)(*args) == E, name
+    for name in ("scc_graph_destroy", "scc_batch_destroy", "scc_server_destroy"):
+        assert getattr(lib, name)(None) == scc.SCC_OK, name
+    # a server configuration out of range is refused before the server starts
+    cfg = scc.scc_server_config()
+    assert lib.scc_server_config_default(ctypes.byref(cfg)) == scc.SCC_OK
+    for field, bad in (("mem_cap_bytes", 0), ("batch_graphs", 0), ("batch_vertices", -1), ("max_bypass_ms", -1.0)):
+        c = scc.scc_server_config.from_buffer_copy(cfg)
+        setattr(c, field, bad)
+        h = ctypes.c_void_p()
+        assert lib.scc_server_create(ctypes.byref(c), ctypes.byref(h)) == E, field
+        assert not h.value
+
+
 def test_binding_fails_loudly_without_the_library(monkeypatch, tmp_path):
     monkeypatch.setattr(scc, "_lib", None)
     monkeypatch.setattr(libbuild, "SO_PATH", str(tmp_path / "missing.so"))
