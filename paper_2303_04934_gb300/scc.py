@@ -205,6 +205,32 @@ def _ptr(a):
     raise TypeError(f"unsupported array type {type(a)}")
 
 
+I32 = ("int32",)
+I64 = ("int64",)
+W64 = ("uint64", "int64")  # 64-bit reachability masks
+
+
+def _elements(a):
+    return int(a.size) if isinstance(a, np.ndarray) else int(a.numel())
+
+
+def _arr(a, what: str, types, count: int):
+    """_ptr of an argument the C ABI reads or writes as `count` elements of one
+    of `types`: a wrong element type or a shorter array raises SccError
+    (SCC_ERR_INVALID_ARG) here, before the library could misread it or write
+    past its end."""
+    if a is None:
+        if count > 0:
+            raise SccError(SCC_ERR_INVALID_ARG, f"{what}: missing")
+        return None
+    name = a.dtype.name if isinstance(a, np.ndarray) else str(getattr(a, "dtype", "")).replace("torch.", "")
+    if name not in types:
+        raise SccError(SCC_ERR_INVALID_ARG, f"{what}: elements of type {name}, expected {' or '.join(types)}")
+    if _elements(a) < count:
+        raise SccError(SCC_ERR_INVALID_ARG, f"{what}: {_elements(a)} elements, {count} needed")
+    return _ptr(a)
+
+
 def _stream(stream):
     if stream is None:
         import torch
@@ -226,8 +252,10 @@ def scc_config_default() -> scc_config:
 # ------------------------------------------------------------------- graphs --
 def scc_graph_create(n: int, m: int, offsets, targets, stream=None) -> int:
     h = ctypes.c_void_p()
-    _check(load().scc_graph_create(n, m, _ptr(offsets), _ptr(targets), _stream(stream), ctypes.byref(h)),
-           "scc_graph_create")
+    what = "scc_graph_create"
+    po = _arr(offsets, what + " offsets", I32, max(n, 0) + 1)
+    pt = _arr(targets, what + " targets", I32, max(m, 0))
+    _check(load().scc_graph_create(n, m, po, pt, _stream(stream), ctypes.byref(h)), what)
     return h.value
 
 
@@ -240,17 +268,23 @@ def scc_set_config(h, cfg: scc_config) -> None:
 
 
 def scc_run(h, labels_out, stream=None) -> None:
-    _check(load().scc_run(h, _ptr(labels_out), _stream(stream)), "scc_run")
+    n = scc_graph_info(h)[0]
+    _check(load().scc_run(h, _arr(labels_out, "scc_run labels_out", I32, n), _stream(stream)), "scc_run")
 
 
 def reach_multi(h, sources, k: int, dir: int, out, stream=None) -> None:
-    _check(load().reach_multi(h, _ptr(sources), k, dir, _ptr(out), _stream(stream)), "reach_multi")
+    n = scc_graph_info(h)[0]
+    ps = _arr(sources, "reach_multi sources", I32, k)
+    _check(load().reach_multi(h, ps, k, dir, _arr(out, "reach_multi out", W64, n), _stream(stream)), "reach_multi")
 
 
 def reach_multi_noalloc(h, sources, k: int, dir: int, out, stream=None) -> None:
     """reach_multi for callers that cannot allocate: device buffers only, working
     memory from the library's fixed 32 MiB device array (see include/scc.h)."""
-    _check(load().reach_multi_noalloc(h, _ptr(sources), k, dir, _ptr(out), _stream(stream)), "reach_multi_noalloc")
+    n = scc_graph_info(h)[0]
+    ps = _arr(sources, "reach_multi_noalloc sources", I32, k)
+    _check(load().reach_multi_noalloc(h, ps, k, dir, _arr(out, "reach_multi_noalloc out", W64, n), _stream(stream)),
+           "reach_multi_noalloc")
 
 
 def scc_get_stats(h) -> dict:
@@ -268,8 +302,12 @@ def scc_batch_config_default() -> scc_batch_config:
 
 def scc_batch_create(G: int, vbase, ebase, offsets, targets, stream=None) -> int:
     h = ctypes.c_void_p()
-    _check(load().scc_batch_create(G, _ptr(vbase), _ptr(ebase), _ptr(offsets), _ptr(targets), _stream(stream),
-                                   ctypes.byref(h)), "scc_batch_create")
+    what = "scc_batch_create"
+    pv = _arr(vbase, what + " vbase", I64, max(G, 0) + 1)
+    pe = _arr(ebase, what + " ebase", I64, max(G, 0) + 1)
+    po = _arr(offsets, what + " offsets", I32, 0)
+    pt = _arr(targets, what + " targets", I32, 0)
+    _check(load().scc_batch_create(G, pv, pe, po, pt, _stream(stream), ctypes.byref(h)), what)
     return h.value
 
 
@@ -288,7 +326,9 @@ def scc_batch_get_config(h) -> scc_batch_config:
 
 
 def scc_batch_run(h, labels_out, stream=None) -> None:
-    _check(load().scc_batch_run(h, _ptr(labels_out), _stream(stream)), "scc_batch_run")
+    nv = scc_batch_get_stats(h)["vertices"]
+    _check(load().scc_batch_run(h, _arr(labels_out, "scc_batch_run labels_out", I32, nv), _stream(stream)),
+           "scc_batch_run")
 
 
 def scc_batch_autotune(h, sample: int = 0, stream=None):
@@ -414,8 +454,11 @@ class SccServer:
 
     def add_graph(self, n: int, offsets, targets) -> int:
         gid = ctypes.c_int32()
-        _check(load().scc_server_add_graph(self.h, n, len(targets), _ptr(offsets), _ptr(targets), ctypes.byref(gid)),
-               "scc_server_add_graph")
+        what = "scc_server_add_graph"
+        m = _elements(targets)
+        po = _arr(offsets, what + " offsets", I32, max(n, 0) + 1)
+        _check(load().scc_server_add_graph(self.h, n, m, po, _arr(targets, what + " targets", I32, m),
+                                           ctypes.byref(gid)), what)
         return gid.value
 
     def remove_graph(self, gid: int) -> None:
@@ -423,15 +466,20 @@ class SccServer:
 
     def submit_scc(self, n: int, offsets, targets, labels_out) -> int:
         rid = ctypes.c_int64()
-        _check(load().scc_server_submit_scc(self.h, n, len(targets), _ptr(offsets), _ptr(targets), _ptr(labels_out),
-                                            ctypes.byref(rid)), "scc_server_submit_scc")
+        what = "scc_server_submit_scc"
+        m = _elements(targets)
+        po = _arr(offsets, what + " offsets", I32, max(n, 0) + 1)
+        pt = _arr(targets, what + " targets", I32, m)
+        pl = _arr(labels_out, what + " labels_out", I32, max(n, 0))
+        _check(load().scc_server_submit_scc(self.h, n, m, po, pt, pl, ctypes.byref(rid)), what)
         self._keep[rid.value] = (offsets, targets, labels_out)
         return rid.value
 
     def submit_reach(self, gid: int, sources, dir: int, out) -> int:
         rid = ctypes.c_int64()
         src = np.ascontiguousarray(sources, dtype=np.int32)
-        _check(load().scc_server_submit_reach(self.h, gid, _ptr(src), len(src), dir, _ptr(out), ctypes.byref(rid)),
+        _check(load().scc_server_submit_reach(self.h, gid, _ptr(src), len(src), dir,
+                                              _arr(out, "scc_server_submit_reach out", W64, 0), ctypes.byref(rid)),
                "scc_server_submit_reach")
         self._keep[rid.value] = (out,)
         return rid.value

@@ -4,6 +4,7 @@ import ctypes
 import os
 import re
 
+import numpy as np
 import pytest
 
 from paper_2303_04934_gb300 import build as libbuild
@@ -96,3 +97,35 @@ def test_binding_fails_loudly_without_the_library(monkeypatch, tmp_path):
     monkeypatch.setattr(libbuild, "SO_PATH", str(tmp_path / "missing.so"))
     with pytest.raises(RuntimeError, match="missing"):
         scc.load()
+
+
+def test_binding_checks_element_types_and_lengths(lib):
+    """The binding refuses arrays the C ABI would misread (wrong element type)
+    or overrun (too short) before calling the library: the graph below would
+    otherwise reach CUDA, which this host does not have (SCC_ERR_CUDA)."""
+    import torch
+    off = np.array([0, 1, 2, 3, 3], np.int32)
+    adj = np.array([1, 2, 0], np.int32)
+    for o, a, word in [(off, adj.astype(np.int64), "targets"), (off.astype(np.int64), adj, "offsets"),
+                       (off[:4], adj, "offsets"), (off, adj[:2], "targets"), (off, None, "targets"),
+                       (torch.from_numpy(off), torch.from_numpy(adj).to(torch.int64), "targets")]:
+        with pytest.raises(scc.SccError, match=word) as e:
+            scc.scc_graph_create(4, 3, o, a)
+        assert e.value.code == scc.SCC_ERR_INVALID_ARG
+    # well-typed arguments pass the checks and reach the library
+    if torch.cuda.is_available():
+        scc.scc_graph_destroy(scc.scc_graph_create(4, 3, off, adj))
+    else:
+        with pytest.raises(scc.SccError) as e:
+            scc.scc_graph_create(4, 3, off, adj)
+        assert e.value.code == scc.SCC_ERR_CUDA
+    # accepted element types: int32 ids, 64-bit masks of either signedness, numpy or torch
+    for a, types, count in [(np.zeros(5, np.int32), scc.I32, 5), (torch.zeros(5, dtype=torch.int32), scc.I32, 5),
+                            (np.zeros(3, np.uint64), scc.W64, 3), (torch.zeros(3, dtype=torch.int64), scc.W64, 3),
+                            (np.zeros(4, np.int64), scc.I64, 2), (None, scc.I32, 0)]:
+        scc._arr(a, "x", types, count)
+    for a, types, count in [(np.zeros(5, np.uint32), scc.I32, 5), (np.zeros(3, np.float64), scc.W64, 3),
+                            (np.zeros(2, np.uint64), scc.W64, 3), (None, scc.I32, 1),
+                            (torch.zeros(3, dtype=torch.int32), scc.W64, 3)]:
+        with pytest.raises(scc.SccError):
+            scc._arr(a, "x", types, count)
