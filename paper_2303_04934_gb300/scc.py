@@ -451,6 +451,7 @@ class SccServer:
                "scc_server_create")
         self.h = h.value
         self._keep = {}
+        self._graph_n = {}  # vertices of each resident graph (reach outputs hold one mask per vertex)
 
     def add_graph(self, n: int, offsets, targets) -> int:
         gid = ctypes.c_int32()
@@ -459,10 +460,12 @@ class SccServer:
         po = _arr(offsets, what + " offsets", I32, max(n, 0) + 1)
         _check(load().scc_server_add_graph(self.h, n, m, po, _arr(targets, what + " targets", I32, m),
                                            ctypes.byref(gid)), what)
+        self._graph_n[gid.value] = n
         return gid.value
 
     def remove_graph(self, gid: int) -> None:
         _check(load().scc_server_remove_graph(self.h, gid), "scc_server_remove_graph")
+        self._graph_n.pop(gid, None)
 
     def submit_scc(self, n: int, offsets, targets, labels_out) -> int:
         rid = ctypes.c_int64()
@@ -479,7 +482,8 @@ class SccServer:
         rid = ctypes.c_int64()
         src = np.ascontiguousarray(sources, dtype=np.int32)
         _check(load().scc_server_submit_reach(self.h, gid, _ptr(src), len(src), dir,
-                                              _arr(out, "scc_server_submit_reach out", W64, 0), ctypes.byref(rid)),
+                                              _arr(out, "scc_server_submit_reach out", W64, self._graph_n.get(gid, 0)),
+                                              ctypes.byref(rid)),
                "scc_server_submit_reach")
         self._keep[rid.value] = (out,)
         return rid.value
