@@ -559,6 +559,8 @@ __device__ bool scc_one_graph(const BatchArgs& A, Ws& W, int g, BlockShared& sh,
     return true;
 }
 
+// The persistent launch's work counter and error flag, reset inside the
+// captured graph before every replay.
 __global__ void k_batch_reset(int* next, int* err) {
     *next = 0;
     *err = 0;
@@ -1058,6 +1060,8 @@ void batch_free(scc_batch* h, cudaStream_t s) {
     dfree(h->labels, s);
 }
 
+// One block per graph: its CSR is well formed (offsets start at 0, do not
+// decrease and end at its arc count; targets in [0, n_g)); *bad set otherwise.
 __global__ void k_batch_validate(int32_t G, const long long* vbase, const long long* ebase, const int32_t* off,
                                  const int32_t* adj, int* bad) {
     for (int g = blockIdx.x; g < G; g += gridDim.x) {

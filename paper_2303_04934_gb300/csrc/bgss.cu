@@ -85,6 +85,8 @@ __device__ __forceinline__ long long pow2ceil_d(long long x) {
     return p;
 }
 
+// The remaining batches of Alg. 1 in one cooperative launch (the loop the file
+// header describes); B.ctl tells the host why it stopped.
 __global__ void __launch_bounds__(256, 2) bgss_kernel(BgssParams B) {
     __shared__ EngineSmem<PolPair> sm;
     const LocalQueue<uint64_t> q = warp_queue(sm);

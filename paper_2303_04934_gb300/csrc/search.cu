@@ -16,6 +16,8 @@ namespace {
 
 constexpr int kEngineBlock = 256;
 
+// The initial multi-reachability items of a batch: the pair (s, s) of every
+// source (Alg. 1: each source reaches itself).
 __global__ void k_pairs_from_sources(const int32_t* __restrict__ src, int32_t k, uint64_t* out) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < k; i += gridDim.x * blockDim.x) {
         uint32_t s = (uint32_t)src[i];
@@ -311,6 +313,9 @@ struct BagOnlyParams {
     EngineCtl* ctl;
 };
 
+// The hash bag alone (Sec. 3.3): every warp inserts a strided share of the items
+// (Insert), one grid barrier, then ExtractAll compacts the bag into `out`; a
+// test hook.
 __global__ void __launch_bounds__(256) k_bag_only(BagOnlyParams P, const int32_t* __restrict__ items, long long count,
                                                   int32_t* out) {
     const int lane = lane_id();
