@@ -75,6 +75,7 @@ __global__ void __launch_bounds__(kBlk) k_drop_self_arcs(const int32_t* __restri
         }
     }
 }
+// The rows with self-loops: one thread copies a row, skipping its self-loops.
 __global__ void k_drop_self_rows(const int32_t* __restrict__ off, const int32_t* __restrict__ adj, int32_t n,
                                  const int32_t* __restrict__ selfrow, const int32_t* __restrict__ off2,
                                  int32_t* adj2) {
@@ -85,6 +86,7 @@ __global__ void k_drop_self_rows(const int32_t* __restrict__ off, const int32_t*
             if (adj[e] != u) adj2[o++] = adj[e];
     }
 }
+// out[u] = arcs of row u that are not self-loops (the new CSR's row lengths).
 __global__ void k_sub(const int32_t* __restrict__ off, const int32_t* __restrict__ selfrow, int32_t n, int32_t* out) {
     for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n; u += (int64_t)gridDim.x * blockDim.x)
         out[u] = off[u + 1] - off[u] - selfrow[u];
@@ -120,6 +122,8 @@ __device__ __forceinline__ long long block_excl_scan(long long x, long long* tot
     return r;
 }
 
+// Exclusive scan of int32 counts in three passes: per-tile sums, a scan of the
+// sums in one block, then each tile's scan from its offset.
 __global__ void __launch_bounds__(kBlk) k_scan_reduce(const int32_t* __restrict__ in, int64_t n, long long* sums) {
     int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
     long long s = 0;
@@ -226,6 +230,7 @@ __global__ void k_rem_flags(const int32_t* __restrict__ act, int64_t N, Feistel 
     for (int64_t p = p0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < N; p += (int64_t)gridDim.x * blockDim.x)
         flags[p - p0] = label[act[f.perm((uint64_t)p, (uint64_t)N)]] >= 0;
 }
+// rem_pos/rem_v of the remaining pivots, at the places the scan of the flags gives.
 __global__ void k_rem_scatter(const int32_t* __restrict__ act, int64_t N, Feistel f, int64_t p0,
                               const int32_t* __restrict__ flags, const int32_t* __restrict__ pos, int32_t* rem_pos,
                               int32_t* rem_v) {
@@ -257,6 +262,7 @@ __device__ __forceinline__ int active_bits(const int32_t* __restrict__ label, in
     }
     return f;
 }
+// act = increasing list of the active vertices: counts per tile, then a scatter.
 __global__ void __launch_bounds__(kBlk) k_active_count(const int32_t* __restrict__ label, int32_t n, long long* sums) {
     const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
     int c = __popc(active_bits(label, n, base));
@@ -301,6 +307,8 @@ __global__ void k_prefill_bits(const int32_t* __restrict__ label, int32_t L, int
         }
     }
 }
+// out[v] = 1 iff bit v is set and v is in class L (all classes when label is
+// NULL): a visited bitmap as bytes, for the test hooks.
 __global__ void k_bits_to_bytes(const uint32_t* __restrict__ bits, const int32_t* __restrict__ label, int32_t L,
                                 int32_t n, uint8_t* out) {
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
@@ -479,6 +487,8 @@ __global__ void k_table_gather(const unsigned long long* __restrict__ tab, int64
         if (k != ~0ull && (int64_t)pos < out_cap) out[pos] = k;
     }
 }
+// Insert-if-absent of every key (Sec. 4.5 pair table); *inserted += the keys
+// that were new.
 __global__ void k_table_insert(const unsigned long long* __restrict__ keys, int64_t count, PairTable t,
                                unsigned long long* inserted) {
     unsigned long long c = 0;
@@ -543,6 +553,8 @@ __global__ void k_mask_init(const int32_t* __restrict__ src, int32_t k, int32_t 
     }
     atomicOr(&mask[(size_t)words * v + (j >> 6)], 1ull << (j & 63));
 }
+// The sources given to the test hook that are in [0, n) and unfinished (an
+// id out of range sets *bad), compacted into out.
 __global__ void k_filter_sources(const int32_t* __restrict__ in, int32_t k, int32_t n,
                                  const int32_t* __restrict__ label, int32_t* out, int* cnt, int* bad) {
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < k; j += gridDim.x * blockDim.x) {
@@ -682,6 +694,7 @@ int launch_table_gather(const unsigned long long* tab, int64_t cap, unsigned lon
 }
 
 namespace {
+// Every key of the old table into the new one (the regrowth of Sec. 4.5).
 __global__ void k_table_rehash(const unsigned long long* __restrict__ src, int64_t src_cap, PairTable dst) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < src_cap; i += (int64_t)gridDim.x * blockDim.x) {
         unsigned long long k = src[i];
