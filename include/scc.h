@@ -160,24 +160,31 @@ SCC_API int reach_multi(scc_handle h, const int32_t* sources, int32_t k, int32_t
                 void* stream);
 
 /*
- * reach_multi without device allocation. The paper has no counterpart: this
- * entry point exists for callers that cannot allocate device memory at the
- * point of the call -- code running while a stream is being captured into a
- * CUDA graph, latency-critical loops that forbid allocator calls, and hosts
- * whose device memory belongs to their own allocator. It computes exactly what
- * reach_multi computes, with the same kernels, and calls no allocating routine:
- * the search's working memory comes from one fixed device array of 32 MiB that
- * the library keeps on every device it has run on, until the process exits.
+ * reach_multi without device allocation. The paper has no counterpart. Some
+ * callers may not call cudaMalloc, or any routine that allocates device
+ * memory, at the point where they need a reachability result: latency-critical
+ * loops that forbid allocator calls (an allocation can block or synchronise
+ * the device), and hosts whose device memory belongs to their own allocator (a
+ * framework's caching allocator or a fixed arena), where an allocation by a
+ * library would bypass the owner's accounting. This entry point computes
+ * exactly what reach_multi computes, with the same engine kernel, and
+ * allocates nothing: the caller passes the sources and the output, and the
+ * search's working memory comes from one fixed device array of 32 MiB that the
+ * library keeps on every device it has run on, until the process exits.
  *   sources  DEVICE int32[k], 1 <= k <= 64, each in [0, n).
  *   out      DEVICE uint64[n], written. (Host pointers are rejected.)
  * Returns SCC_ERR_INVALID_ARG when the graph's working space does not fit the
- * array (about 500 thousand vertices for sparse graphs), SCC_ERR_CAPACITY when a
- * search needs more frontier space than the array holds.
+ * array (about 500 thousand vertices for sparse graphs) or a source is out of
+ * range, SCC_ERR_CAPACITY when a search needs more frontier space than the
+ * array holds.
  * Every call shares the array and finds the previous call's contents in it, so
- * a call resets what must start empty; calls whose work overlaps on the GPU
+ * a call clears what must start empty; calls whose work overlaps on the GPU
  * (for instance on two streams) race on it and must be serialised by the
- * caller. The first call on a device looks the array's device address up once;
- * make that first call before any stream capture. Synchronises `stream`.
+ * caller. The first call on a device looks the array's device address up, with
+ * that device current, and keeps it for later calls; make that first call
+ * before any stream capture. A cudaDeviceReset of the device discards the
+ * array, so the entry point must not be called on that device after one.
+ * Synchronises `stream`.
  */
 SCC_API int reach_multi_noalloc(scc_handle h, const int32_t* sources, int32_t k, int32_t dir, uint64_t* out,
                                 void* stream);

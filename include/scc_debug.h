@@ -106,6 +106,20 @@ SCC_API int scc_debug_pair_table(const uint64_t* keys, int64_t count, int64_t in
 /* Number of kernel launches the library has issued since it was loaded. */
 SCC_API int64_t scc_debug_launch_count(void);
 
+/*
+ * The failure path of the grid barrier that separates the rounds of every
+ * cooperative search (the bounded device wait behind SCC_ERR_TIMEOUT; the paper
+ * has no counterpart). One cooperative launch of two blocks per SM meets at one
+ * grid barrier whose wait is limited to limit_ns (1e3 .. 1e9 ns); block
+ * absent_block (-1: none) returns without arriving, so every other block's
+ * wait runs out and the launch ends with SCC_ERR_TIMEOUT instead of hanging.
+ *   *n_arrived (host) receives the number of blocks whose wait ended because
+ *   every block arrived (all of them with absent_block = -1, none otherwise).
+ * Returns SCC_OK when every block passed, SCC_ERR_TIMEOUT when a wait ran out,
+ * SCC_ERR_INVALID_ARG for a limit out of range or absent_block >= the grid.
+ */
+SCC_API int scc_debug_barrier_timeout(int32_t absent_block, int64_t limit_ns, int32_t* n_arrived, void* stream);
+
 /* Batched SCC (scc_batch.h): for every graph g of the last scc_batch_run,
    out[11g .. 11g + 5] = device globaltimer (ns) at its start and at the end of
    the transpose, the first SCC, the class trimming, the batches and the

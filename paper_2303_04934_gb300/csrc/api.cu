@@ -280,7 +280,7 @@ int reach_multi_wide(scc_graph* h, const int32_t* sources_d, int32_t k, int32_t 
         SCC_CUDA(cudaMemcpyAsync(&bad, h->flags + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
         SCC_CUDA(cudaStreamSynchronize(s));
         if (bad) return SCC_ERR_INVALID_ARG;
-        SCC_TRY(engine_reserve(&h->eb32, 4, ((long long)n + 1024) << attempt, h->cfg.lambda, h->mt, s));
+        SCC_TRY(engine_reserve(&h->eb32, 4, ((long long)n + 1024) << attempt, h->cfg.lambda, h->mt, h->di.num_sms, s));
         EngineRun r;
         int rc = run_mask2(dir == 0 ? h->off : h->toff, dir == 0 ? h->adj : h->tadj, n, sources_d, k, mask2, &h->eb32,
                            opts_of(h), &r, s);
@@ -658,7 +658,7 @@ static int scc_run_impl(scc_graph* h, int32_t* labels_out, cudaStream_t s) {
         // degree. Below kDenseDegree arcs per vertex (lattices, k-NN graphs) the
         // forward and backward searches share the rounds of one launch instead.
         const bool both = (h->cfg.dense == 0 || (double)h->mt < kDenseDegree * (double)n) && n < INT32_MAX - 2;
-        SCC_TRY(engine_reserve(&h->eb32, 4, (both ? 2 * N : N) + 1024, h->cfg.lambda, h->mt, s));
+        SCC_TRY(engine_reserve(&h->eb32, 4, (both ? 2 * N : N) + 1024, h->cfg.lambda, h->mt, h->di.num_sms, s));
         SCC_TRY(launch_prefill_bits(h->label, 0, n, h->bits_f, h->bits_b, s));
         EngineRun r0, r1;
         if (both) {
@@ -766,7 +766,7 @@ static int scc_run_impl(scc_graph* h, int32_t* labels_out, cudaStream_t s) {
                 SCC_TRY(reserve_table(h, 1, tab_alloc, s));
                 // a search holds at most 3/4 of each of the two tables
                 SCC_TRY(engine_reserve(&h->eb64, 8, (long long)(1.5 * (double)tab_alloc) + (1 << 20), h->cfg.lambda,
-                                       h->mt, s));
+                                       h->mt, h->di.num_sms, s));
                 if (fresh) {  // the kernel keeps both tables empty between batches
                     SCC_CUDA(cudaMemsetAsync(h->tab[0], 0xff, (size_t)tab_alloc * 8, s));
                     SCC_CUDA(cudaMemsetAsync(h->tab[1], 0xff, (size_t)tab_alloc * 8, s));
@@ -859,7 +859,7 @@ int reach_multi(scc_handle h, const int32_t* sources, int32_t k, int32_t dir, ui
         SCC_CUDA(cudaMemcpyAsync(&bad, h->flags + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
         SCC_CUDA(cudaStreamSynchronize(s));
         if (bad) return SCC_ERR_INVALID_ARG;
-        SCC_TRY(engine_reserve(&h->eb32, 4, ((long long)n + 1024) << attempt, h->cfg.lambda, h->mt, s));
+        SCC_TRY(engine_reserve(&h->eb32, 4, ((long long)n + 1024) << attempt, h->cfg.lambda, h->mt, h->di.num_sms, s));
         EngineRun r;
         int rc = run_mask(dir == 0 ? h->off : h->toff, dir == 0 ? h->adj : h->tadj, n, dsrc, k, mask, &h->eb32,
                           opts_of(h), &r, s);
@@ -950,7 +950,7 @@ int scc_debug_single_reach(scc_handle h, const int32_t* labels, int32_t src, int
         rc = cuda_err(cudaMemsetAsync(d, 0, (size_t)n, s));  // a finished source reaches nothing
     } else {
         rc = launch_prefill_bits(dl, L, n, h->bits_f, nullptr, s);
-        if (rc == SCC_OK) rc = engine_reserve(&h->eb32, 4, (long long)n + 1024, h->cfg.lambda, h->mt, s);
+        if (rc == SCC_OK) rc = engine_reserve(&h->eb32, 4, (long long)n + 1024, h->cfg.lambda, h->mt, h->di.num_sms, s);
         EngineRun r;
         if (rc == SCC_OK)
             rc = run_single(dir == 0 ? h->off : h->toff, dir == 0 ? h->adj : h->tadj, n, src, h->bits_f,
@@ -1017,7 +1017,7 @@ int scc_debug_multi_reach(scc_handle h, const int32_t* labels, const int32_t* so
         SCC_TRY(reserve_table(h, d, tcap, s));
         SCC_CUDA(cudaMemsetAsync(h->tab[d], 0xff, (size_t)tcap * 8, s));
         long long max_ins = (long long)(0.6 * (double)tcap);
-        SCC_TRY(engine_reserve(&h->eb64, 8, max_ins + (1 << 20), h->cfg.lambda, h->mt, s));
+        SCC_TRY(engine_reserve(&h->eb64, 8, max_ins + (1 << 20), h->cfg.lambda, h->mt, h->di.num_sms, s));
         EngineRun r;
         int rc = run_pairs(d == 0 ? h->off : h->toff, d == 0 ? h->adj : h->tadj, n, h->label, h->sources, kk,
                            h->tab[d], tcap, max_ins, &h->eb64, o, &r, s);
@@ -1054,6 +1054,14 @@ int scc_debug_multi_reach(scc_handle h, const int32_t* labels, const int32_t* so
 }
 
 int64_t scc_debug_launch_count(void) { return launch_count(); }
+
+int scc_debug_barrier_timeout(int32_t absent_block, int64_t limit_ns, int32_t* n_arrived, void* stream) {
+    if (!n_arrived || limit_ns < 1000 || limit_ns > 1000000000ll || absent_block < -1) return SCC_ERR_INVALID_ARG;
+    int c = 0;
+    const int rc = run_barrier_probe(absent_block, limit_ns, &c, (cudaStream_t)stream);
+    *n_arrived = c;
+    return rc;
+}
 
 int scc_debug_hashbag(const int32_t* items, int64_t count, int32_t lambda, int32_t sigma, int32_t* out, int64_t* nout,
                       int32_t* chunks, void* stream) {

@@ -87,7 +87,7 @@ __device__ __forceinline__ long long pow2ceil_d(long long x) {
 
 // The remaining batches of Alg. 1 in one cooperative launch (the loop the file
 // header describes); B.ctl tells the host why it stopped.
-__global__ void __launch_bounds__(256, 2) bgss_kernel(BgssParams B) {
+__global__ void __launch_bounds__(kEngineBlock, 2) bgss_kernel(BgssParams B) {
     __shared__ EngineSmem<PolPair> sm;
     const LocalQueue<uint64_t> q = warp_queue(sm);
     WarpStats ws;
@@ -256,8 +256,9 @@ int run_bgss_device(const BgssArgs& a, BgssResult* res, cudaStream_t st) {
     SCC_CUDA(cudaMemsetAsync(b->ctl, 0, sizeof(EngineCtl), st));
     static int per_sm = -1;
     if (per_sm < 0) {
-        SCC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bgss_kernel, 256, 0));
+        SCC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bgss_kernel, kEngineBlock, 0));
         if (per_sm < 1) return SCC_ERR_CUDA;
+        per_sm = engine_blocks_per_sm(per_sm);
     }
     void* args[] = {(void*)&B};
     cudaEvent_t e0, e1;
@@ -266,7 +267,7 @@ int run_bgss_device(const BgssArgs& a, BgssResult* res, cudaStream_t st) {
     cudaEventRecord(e0, st);
     const int full = per_sm * a.o.num_sms;
     const int grid = a.grid > 0 ? std::min(a.grid, full) : full;
-    cudaError_t le = cudaLaunchCooperativeKernel((const void*)bgss_kernel, dim3(grid), dim3(256), args, 0, st);
+    cudaError_t le = cudaLaunchCooperativeKernel((const void*)bgss_kernel, dim3(grid), dim3(kEngineBlock), args, 0, st);
     count_launch();
     cudaEventRecord(e1, st);
     EngineCtl ec;
@@ -313,11 +314,11 @@ size_t bgss_ctl_bytes() { return sizeof(BgssCtl); }
 
 int bgss_full_grid(int num_sms) {
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bgss_kernel, 256, 0) != cudaSuccess) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bgss_kernel, kEngineBlock, 0) != cudaSuccess) {
         cudaGetLastError();
         return num_sms;
     }
-    return std::max(1, per_sm) * num_sms;
+    return std::max(1, engine_blocks_per_sm(per_sm)) * num_sms;
 }
 
 }  // namespace scc

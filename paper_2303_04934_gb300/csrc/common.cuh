@@ -78,7 +78,7 @@ struct GridBarrier {
 
 constexpr uint64_t kBarrierTimeoutNs = 4000000000ull;  // 4 s
 
-__device__ __forceinline__ bool grid_sync(GridBarrier* b, int* err) {
+__device__ __forceinline__ bool grid_sync_limit(GridBarrier* b, int* err, uint64_t limit_ns) {
     if (gridDim.x == 1) {  // a one-block grid needs no global arrival counter
         __threadfence_block();
         __syncthreads();
@@ -99,7 +99,7 @@ __device__ __forceinline__ bool grid_sync(GridBarrier* b, int* err) {
             uint64_t t0 = globaltimer_ns();
             while (ld_volatile(&b->gen) == g) {
                 __nanosleep(64);
-                if (globaltimer_ns() - t0 > kBarrierTimeoutNs) {
+                if (globaltimer_ns() - t0 > limit_ns) {
                     atomicCAS(err, 0, SCC_ERR_TIMEOUT);
                     ok = 0;
                     break;
@@ -112,6 +112,7 @@ __device__ __forceinline__ bool grid_sync(GridBarrier* b, int* err) {
     __syncthreads();
     return s_ok != 0;
 }
+__device__ __forceinline__ bool grid_sync(GridBarrier* b, int* err) { return grid_sync_limit(b, err, kBarrierTimeoutNs); }
 
 // ---------------------------------------------------------- pivot order --
 // Seeded bijection of [0, N): 4-round balanced Feistel network on the smallest

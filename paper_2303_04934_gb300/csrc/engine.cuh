@@ -44,9 +44,19 @@ constexpr int kHubSeg = 1024;     // arcs of one hub segment
 constexpr int kMaxChunks = 48;
 constexpr int kBagProbe = 16;     // kappa: segment probes before a chunk advance
 constexpr int kTableProbe = 256;  // pair-table probe limit (then: overflow, regrow)
-// bag slots held by partly filled segments: two 32-slot segments for each warp
-// of the largest cooperative grid (4 blocks of 8 warps on each of up to 160 SMs)
-constexpr long long kBagWarpSlots = 2ll * kSeg * 8 * 4 * 160;
+constexpr int kEngineBlock = 256;         // threads of a block of a grid-wide (cooperative) engine launch
+constexpr int kEngineMaxBlocksPerSm = 4;  // cooperative engine grids are clamped to this many blocks per SM
+// Blocks per SM of a cooperative engine launch, given the occupancy the
+// runtime reports for the kernel.
+inline int engine_blocks_per_sm(int occupancy) {
+    return occupancy < kEngineMaxBlocksPerSm ? occupancy : kEngineMaxBlocksPerSm;
+}
+// Bag slots held by partly filled segments: two 32-slot segments for each warp
+// of the largest cooperative grid on num_sms SMs (engine_blocks_per_sm bounds
+// its blocks per SM), reserved beside the items of every bag.
+inline long long bag_warp_slots(int num_sms) {
+    return 2ll * kSeg * (kEngineBlock / kWarp) * kEngineMaxBlocksPerSm * (long long)num_sms;
+}
 
 template <class Item>
 struct Sent;
@@ -815,7 +825,7 @@ __device__ bool engine_search(const EngineParams<typename Pol::Item>& P, Pol& po
 }
 
 template <class Pol>
-__global__ void __launch_bounds__(256, 3) engine_kernel(EngineParams<typename Pol::Item> P, Pol pol_in, DenseParams dp) {
+__global__ void __launch_bounds__(kEngineBlock, 3) engine_kernel(EngineParams<typename Pol::Item> P, Pol pol_in, DenseParams dp) {
     Pol pol = pol_in;
     __shared__ EngineSmem<Pol> sm;
     const LocalQueue<typename Pol::Item> q = warp_queue(sm);

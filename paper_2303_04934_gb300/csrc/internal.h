@@ -249,7 +249,11 @@ struct EngineBuf {
 // Empty both slot arrays (after a search that stopped early).
 int engine_reset_slots(EngineBuf* b, cudaStream_t s);
 // Allocate (or keep, if large enough) buffers for at most `items` items per round.
-int engine_reserve(EngineBuf* b, int item_bytes, long long items, int lambda, int64_t m, cudaStream_t s);
+// One cooperative launch whose blocks meet at a grid barrier with a limit of
+// limit_ns, block `absent` (< 0: none) never arriving; returns the device's
+// error flag (SCC_ERR_TIMEOUT when a wait ran out) and the blocks that passed.
+int run_barrier_probe(int absent, int64_t limit_ns, int* n_arrived, cudaStream_t st);
+int engine_reserve(EngineBuf* b, int item_bytes, long long items, int lambda, int64_t m, int num_sms, cudaStream_t s);
 void engine_release(EngineBuf* b, cudaStream_t s);
 
 struct EngineRun {

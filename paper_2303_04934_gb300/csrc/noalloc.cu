@@ -1,15 +1,16 @@
 // reach_multi_noalloc: multi-source reachability for callers that cannot
 // allocate device memory during the call.
 //
-// Some callers are not allowed to call cudaMalloc (or any allocating routine)
-// at the point where they need a result: code running while a stream is being
-// captured into a CUDA graph, real-time or latency-critical loops that forbid
-// allocator calls, and hosts whose device memory is owned by a custom
-// allocator. This entry point serves them: it takes a graph handle (created
-// earlier) and device buffers for the sources and the result, and it takes its
-// working memory -- the two hash-bag slot arrays, the hub lists and the control
-// block of the reachability engine -- from one fixed, file-scope device array
-// instead of allocating. It launches the same engine kernel as reach_multi.
+// Some callers may not call cudaMalloc (or any allocating routine) at the
+// point where they need a result: latency-critical loops that forbid allocator
+// calls, because an allocation can block or synchronise the device, and hosts
+// whose device memory is owned by their own allocator, where a library's
+// allocation would bypass that allocator's accounting. This entry point serves
+// them: it takes a graph handle (created earlier) and device buffers for the
+// sources and the result, and it takes its working memory -- the two hash-bag
+// slot arrays, the hub lists and the control block of the reachability engine
+// -- from one fixed, file-scope device array instead of allocating. It
+// launches the same engine kernel as reach_multi.
 //
 // The array is kNoAllocScratchBytes (32 MiB) per device and lives as long as
 // the library is loaded on that device. Every call shares it and it keeps the
@@ -52,9 +53,9 @@ size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 // Carve the engine buffers for vertex items out of the scratch array; returns
 // the bytes needed (the layout is only written when base != nullptr).
-size_t carve(unsigned char* base, int32_t n, int64_t mt, int lambda, EngineBuf* b, int** bad) {
+size_t carve(unsigned char* base, int32_t n, int64_t mt, int lambda, int num_sms, EngineBuf* b, int** bad) {
     long long items = std::max<long long>(2ll * n + 1024, lambda);
-    long long nslots = (std::max<long long>(4 * items, 4ll * lambda) + kBagWarpSlots + kSeg - 1) / kSeg * kSeg;
+    long long nslots = (std::max<long long>(4 * items, 4ll * lambda) + bag_warp_slots(num_sms) + kSeg - 1) / kSeg * kSeg;
     int hub_cap = (int)std::min<long long>(items, 8192);
     long long segmap_cap = 2 * (mt / kHubSeg) + hub_cap + 1024;
     size_t off = 0;
@@ -106,12 +107,12 @@ size_t carve(unsigned char* base, int32_t n, int64_t mt, int lambda, EngineBuf* 
 int reach_multi_noalloc_impl(const int32_t* off, const int32_t* adj, int32_t n, int64_t mt, int lambda,
                              const EngineOpts& o, const int32_t* sources, int32_t k, uint64_t* out,
                              cudaStream_t s) {
-    if (carve(nullptr, n, mt, lambda, nullptr, nullptr) > kNoAllocScratchBytes) return SCC_ERR_INVALID_ARG;
+    if (carve(nullptr, n, mt, lambda, o.num_sms, nullptr, nullptr) > kNoAllocScratchBytes) return SCC_ERR_INVALID_ARG;
     unsigned char* base = nullptr;
     SCC_TRY(scratch_address(&base));
     EngineBuf b;
     int* bad = nullptr;
-    carve(base, n, mt, lambda, &b, &bad);
+    carve(base, n, mt, lambda, o.num_sms, &b, &bad);
     // what must start empty: the bag, the control block, the result and the flag
     for (int j = 0; j < 2; ++j) SCC_CUDA(cudaMemsetAsync(b.slots[j], 0xff, (size_t)b.nslots * 4, s));
     SCC_CUDA(cudaMemsetAsync(b.ctl, 0, sizeof(EngineCtl), s));

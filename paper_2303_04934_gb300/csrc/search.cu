@@ -5,6 +5,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <vector>
 
 #include "common.cuh"
 #include "engine.cuh"
@@ -13,8 +14,6 @@
 namespace scc {
 
 namespace {
-
-constexpr int kEngineBlock = 256;
 
 // The initial multi-reachability items of a batch: the pair (s, s) of every
 // source (Alg. 1: each source reaches itself).
@@ -32,7 +31,7 @@ int coop_grid(int num_sms, int* grid) {
         int per_sm = 0;
         SCC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, engine_kernel<Pol>, kEngineBlock, 0));
         if (per_sm < 1) return SCC_ERR_CUDA;
-        cached = per_sm;
+        cached = engine_blocks_per_sm(per_sm);
     }
     *grid = cached * num_sms;
     return SCC_OK;
@@ -142,11 +141,11 @@ int engine_reset_slots(EngineBuf* b, cudaStream_t st) {
     return SCC_OK;
 }
 
-int engine_reserve(EngineBuf* b, int item_bytes, long long items, int lambda, int64_t m, cudaStream_t s) {
+int engine_reserve(EngineBuf* b, int item_bytes, long long items, int lambda, int64_t m, int num_sms, cudaStream_t s) {
     if (items < 1) items = 1;
     // every warp that pushes holds a partly filled 32-slot segment, so the bag
     // needs room for two segments per warp of the largest grid besides the items
-    long long need_slots = std::max<long long>(4 * items, 4ll * lambda) + kBagWarpSlots;
+    long long need_slots = std::max<long long>(4 * items, 4ll * lambda) + bag_warp_slots(num_sms);
     need_slots = (need_slots + kSeg - 1) / kSeg * kSeg;
     if (b->slots[0] && b->item_bytes == item_bytes && b->nslots >= need_slots && b->lambda == lambda &&
         b->items >= items)
@@ -316,7 +315,7 @@ struct BagOnlyParams {
 // The hash bag alone (Sec. 3.3): every warp inserts a strided share of the items
 // (Insert), one grid barrier, then ExtractAll compacts the bag into `out`; a
 // test hook.
-__global__ void __launch_bounds__(256) k_bag_only(BagOnlyParams P, const int32_t* __restrict__ items, long long count,
+__global__ void __launch_bounds__(kEngineBlock) k_bag_only(BagOnlyParams P, const int32_t* __restrict__ items, long long count,
                                                   int32_t* out) {
     const int lane = lane_id();
     const uint32_t wid = (uint32_t)(blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5));
@@ -352,7 +351,49 @@ __global__ void __launch_bounds__(256) k_bag_only(BagOnlyParams P, const int32_t
     if (blockIdx.x == 0 && threadIdx.x == 0) P.ctl->ring[1].nhub = r;
 }
 
+// The grid barrier's failure path: every block but `absent` waits at one grid
+// barrier with a limit of limit_ns; block `absent` (if any) returns without
+// arriving, so the others' waits run out, record SCC_ERR_TIMEOUT in *err and
+// return. arrived[b] = 1 for a block whose wait ended because all arrived.
+__global__ void k_barrier_probe(GridBarrier* bar, int* err, int absent, unsigned long long limit_ns, int* arrived) {
+    if ((int)blockIdx.x == absent) return;
+    const bool ok = grid_sync_limit(bar, err, limit_ns);
+    if (threadIdx.x == 0) arrived[blockIdx.x] = ok ? 1 : 0;
+}
+
 }  // namespace
+
+int run_barrier_probe(int absent, int64_t limit_ns, int* n_arrived, cudaStream_t st) {
+    DeviceInfo di;
+    SCC_TRY(device_info(&di));
+    int per_sm = 0;
+    SCC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_barrier_probe, 32, 0));
+    const int grid = std::max(1, std::min(per_sm, 2)) * di.num_sms;
+    if (absent >= grid) return SCC_ERR_INVALID_ARG;
+    Scratch tmp(st);
+    GridBarrier* bar = nullptr;
+    int* err = nullptr;
+    int* arrived = nullptr;
+    SCC_TRY(tmp.alloc(&bar, 1));
+    SCC_TRY(tmp.alloc(&err, 1));
+    SCC_TRY(tmp.alloc(&arrived, (size_t)grid));
+    SCC_CUDA(cudaMemsetAsync(bar, 0, sizeof(GridBarrier), st));
+    SCC_CUDA(cudaMemsetAsync(err, 0, sizeof(int), st));
+    SCC_CUDA(cudaMemsetAsync(arrived, 0, sizeof(int) * (size_t)grid, st));
+    unsigned long long lim = (unsigned long long)limit_ns;
+    void* args[] = {(void*)&bar, (void*)&err, (void*)&absent, (void*)&lim, (void*)&arrived};
+    SCC_CUDA(cudaLaunchCooperativeKernel((const void*)k_barrier_probe, dim3(grid), dim3(32), args, 0, st));
+    count_launch();
+    std::vector<int> h((size_t)grid);
+    int herr = 0;
+    SCC_CUDA(cudaMemcpyAsync(h.data(), arrived, sizeof(int) * (size_t)grid, cudaMemcpyDeviceToHost, st));
+    SCC_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    SCC_CUDA(cudaStreamSynchronize(st));
+    int c = 0;
+    for (int x : h) c += x;
+    *n_arrived = c;
+    return herr;
+}
 
 int run_bag_only(const int32_t* items, int64_t count, int lambda, int sigma, int32_t* out, int64_t* nout,
                  int* chunks, cudaStream_t st) {
@@ -361,17 +402,17 @@ int run_bag_only(const int32_t* items, int64_t count, int lambda, int sigma, int
     BagOnlyParams P;
     P.lambda = lambda;
     P.sigma = sigma;
-    P.nslots = std::max<long long>(4 * count, 4ll * lambda);
+    P.nslots = (std::max<long long>(4 * count, 4ll * lambda) + bag_warp_slots(di.num_sms) + kSeg - 1) / kSeg * kSeg;
     Scratch tmp(st);
     SCC_TRY(tmp.alloc(&P.slots, (size_t)P.nslots));
     SCC_TRY(tmp.alloc(&P.ctl, 1));
     SCC_CUDA(cudaMemsetAsync(P.slots, 0xff, (size_t)P.nslots * 4, st));
     SCC_CUDA(cudaMemsetAsync(P.ctl, 0, sizeof(EngineCtl), st));
     int per_sm = 0;
-    SCC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bag_only, 256, 0));
-    int grid = std::max(1, per_sm) * di.num_sms;
+    SCC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bag_only, kEngineBlock, 0));
+    int grid = std::max(1, engine_blocks_per_sm(per_sm)) * di.num_sms;
     void* args[] = {(void*)&P, (void*)&items, (void*)&count, (void*)&out};
-    int rc = cuda_err(cudaLaunchCooperativeKernel((const void*)k_bag_only, dim3(grid), dim3(256), args, 0, st));
+    int rc = cuda_err(cudaLaunchCooperativeKernel((const void*)k_bag_only, dim3(grid), dim3(kEngineBlock), args, 0, st));
     count_launch();
     EngineCtl h;
     memset(&h, 0, sizeof(h));

@@ -32,6 +32,7 @@ EXPORTED = [
     "scc_run", "reach_multi", "reach_multi_noalloc", "scc_get_stats",
     "scc_graph_info", "scc_debug_csr", "scc_debug_trim", "scc_debug_pivot_order", "scc_debug_single_reach",
     "scc_debug_multi_reach", "scc_debug_reach_multi_wide", "scc_debug_hashbag", "scc_debug_pair_table", "scc_debug_launch_count",
+    "scc_debug_barrier_timeout",
     "scc_batch_config_default", "scc_batch_create", "scc_batch_destroy", "scc_batch_set_config",
     "scc_batch_get_config", "scc_batch_run", "scc_batch_autotune", "scc_batch_get_stats",
     "scc_debug_batch_times", "scc_debug_batch_groups", "scc_debug_serve_admission", "scc_debug_serve_unit",
@@ -146,6 +147,7 @@ def load() -> ctypes.CDLL:
         "scc_debug_hashbag": ([vp, i64, i32, i32, vp, P(i64), P(i32), vp], ctypes.c_int),
         "scc_debug_pair_table": ([vp, i64, i64, vp, P(i64), P(i32), vp], ctypes.c_int),
         "scc_debug_launch_count": ([], ctypes.c_int64),
+        "scc_debug_barrier_timeout": ([i32, i64, P(i32), vp], ctypes.c_int),
         "scc_batch_config_default": ([P(scc_batch_config)], ctypes.c_int),
         "scc_batch_create": ([i32, vp, vp, vp, vp, vp, P(vp)], ctypes.c_int),
         "scc_batch_destroy": ([vp], ctypes.c_int),
@@ -581,6 +583,15 @@ def scc_debug_pair_table(keys, count: int, init_cap: int, out, stream=None):
 
 def scc_debug_launch_count() -> int:
     return int(load().scc_debug_launch_count())
+
+
+def scc_debug_barrier_timeout(absent_block: int, limit_ns: int, stream=None) -> tuple[int, int]:
+    """(return code, blocks that passed) of one grid barrier with a limited wait
+    where block ``absent_block`` (-1: none) never arrives; the code is returned,
+    not raised, since SCC_ERR_TIMEOUT is the expected outcome of a test."""
+    arrived = ctypes.c_int32()
+    rc = load().scc_debug_barrier_timeout(absent_block, limit_ns, ctypes.byref(arrived), _stream(stream))
+    return int(rc), arrived.value
 
 
 # ------------------------------------------------------------- convenience --

@@ -67,6 +67,9 @@ def test_null_handles_and_bad_arguments_rejected_on_the_host(lib):
         ("scc_debug_single_reach", (None, None, 0, 0, None, None)),
         ("scc_debug_multi_reach", (None, None, None, 1, 0, None, 0, ctypes.byref(i64), 0, None)),
         ("scc_debug_reach_multi_wide", (None, None, 1, 0, None, None)),
+        ("scc_debug_barrier_timeout", (-1, 0, ctypes.byref(i32), None)),
+        ("scc_debug_barrier_timeout", (-1, 10**6, None, None)),
+        ("scc_debug_barrier_timeout", (-2, 10**6, ctypes.byref(i32), None)),
         ("scc_batch_create", (-1, None, None, None, None, None, None)),
         ("scc_batch_set_config", (None, None)), ("scc_batch_get_config", (None, None)),
         ("scc_batch_run", (None, None, None)), ("scc_batch_autotune", (None, 0, None, None, None)),
