@@ -54,7 +54,7 @@ static_assert(kMaxBuckets <= kBlkA, "bucket scan uses one thread per bucket");
 constexpr int kChunk = 16;              // consecutive arcs per thread per step
 constexpr int kStep = kBlkA * kChunk;   // arcs per block step (8192) = partition tile
 constexpr int kRowsCap = 4096;          // row offsets of one step staged in shared memory
-constexpr int kBlkS = 1024;                    // split pass
+constexpr int kBlkS = 512;                     // split pass (two blocks per SM)
 constexpr int kSplitTile = kBlkS * 8;           // arcs per split tile
 constexpr int kBlkR = 512;                      // rows pass
 constexpr int kWinArcs = 16384;                 // rows staged in shared memory (64 KB)
@@ -383,7 +383,7 @@ __global__ void __launch_bounds__(1024) k_fine_scan(const unsigned long long* __
 
 // A2. partition: per 8k-arc tile, a shared-memory counting sort by bucket,
 // one global reservation per non-empty bucket, then a coalesced write-out.
-__global__ void __launch_bounds__(kBlkA) k_bucket_part(const int32_t* __restrict__ off, const int32_t* __restrict__ adj,
+__global__ void __launch_bounds__(kBlkA, 2) k_bucket_part(const int32_t* __restrict__ off, const int32_t* __restrict__ adj,
                                                        const int32_t* __restrict__ trow, int32_t n, int64_t a_lo,
                                                        int64_t a_hi, int shift, int nb,
                                                        unsigned long long* cursor, int32_t* out_u, uint16_t* out_lv,
@@ -393,28 +393,28 @@ __global__ void __launch_bounds__(kBlkA) k_bucket_part(const int32_t* __restrict
     __shared__ int32_t s_off[kRowsCap];
     __shared__ unsigned int s_cnt[kMaxBuckets];
     __shared__ unsigned int s_start[kMaxBuckets];
-    __shared__ unsigned long long s_gbase[kMaxBuckets];
-    extern __shared__ int32_t s_stage[];  // the sorted tile: u[kStep], v[kStep]
-    int32_t* s_u = s_stage;
-    int32_t* s_v = s_stage + kStep;
+    __shared__ int s_disp[kMaxBuckets];  // staged position -> output position, per bucket
+    extern __shared__ uint2 s_stage[];    // the sorted tile: (u, v)[kStep]
     __shared__ unsigned int s_wsum[kBlkA / 32];
     __shared__ unsigned int s_total;
     for (int64_t t0 = a_lo + (int64_t)blockIdx.x * kStep; t0 < a_hi; t0 += (int64_t)gridDim.x * kStep) {
         const int64_t t1 = min(t0 + (int64_t)kStep, a_hi);
         for (int i = threadIdx.x; i < nb; i += blockDim.x) s_cnt[i] = 0;
         __syncthreads();
-        // ranks within (tile, bucket), kept per thread
-        unsigned int rk[kChunk];
+        // ranks within (tile, bucket), kept per thread two to a word (< kStep)
+        unsigned int rk[kChunk / 2];
         int uu[kChunk], vv[kChunk];
 #pragma unroll
         for (int q = 0; q < kChunk; ++q) vv[q] = -1;
+#pragma unroll
+        for (int q = 0; q < kChunk / 2; ++q) rk[q] = 0;
         // every arc is placed (the histogram counted self-loops too); a self-loop
         // is also counted per row, and any self-loop makes the caller rebuild
         // the CSR without them and start over
         for_step_arcs(off, adj, n, t0, t1, trow, s_off, [&](int q, int u, int v) {
             uu[q] = u;
             vv[q] = v;
-            rk[q] = atomicAdd(&s_cnt[v >> shift], 1u);
+            rk[q >> 1] |= atomicAdd(&s_cnt[v >> shift], 1u) << (16 * (q & 1));
             if (u == v && selfrow != nullptr) {  // without selfrow, self-loops are kept
                 atomicAdd(&selfrow[u], 1);
                 atomicAdd(nself, 1ull);
@@ -442,22 +442,21 @@ __global__ void __launch_bounds__(kBlkA) k_bucket_part(const int32_t* __restrict
             // stage the tile sorted by bucket
 #pragma unroll
             for (int q = 0; q < kChunk; ++q)
-                if (vv[q] >= 0) {
-                    const unsigned int j = s_start[vv[q] >> shift] + rk[q];
-                    s_u[j] = uu[q];
-                    s_v[j] = vv[q];
-                }
-            if (i < nb) s_gbase[i] = g;
+                if (vv[q] >= 0)
+                    s_stage[s_start[vv[q] >> shift] + ((rk[q >> 1] >> (16 * (q & 1))) & 0xffffu)] =
+                        make_uint2((uint32_t)uu[q], (uint32_t)vv[q]);
+            // positions fit 32 bits (m <= INT32_MAX): one displacement per bucket
+            if (i < nb) s_disp[i] = (int)((long long)g - (long long)s_start[i]);
             __syncthreads();
         }
-        const unsigned int total = s_total;
-        for (unsigned int j = threadIdx.x; j < total; j += blockDim.x) {
-            const int v = s_v[j];
-            const int b = v >> shift;
-            const unsigned long long pos = s_gbase[b] + (j - s_start[b]);
-            if (pos < mt) {
-                out_u[pos] = s_u[j];
-                out_lv[pos] = (uint16_t)(v & ((1 << shift) - 1));  // the target within its bucket
+        const int total = (int)s_total;
+        const unsigned int lmask = (1u << shift) - 1u;
+        for (int j = threadIdx.x; j < total; j += kBlkA) {
+            const uint2 x = s_stage[j];
+            const int pos = s_disp[x.y >> shift] + j;
+            if ((unsigned long long)(unsigned int)pos < mt) {
+                out_u[pos] = (int32_t)x.x;
+                out_lv[pos] = (uint16_t)(x.y & lmask);  // the target within its bucket
             } else {
                 atomicExch(err, SCC_ERR_INTERNAL);
             }
@@ -509,7 +508,7 @@ __device__ __forceinline__ SplitLoad split_load(const int32_t* __restrict__ uu, 
     return L;
 }
 
-__global__ void __launch_bounds__(kBlkS, 1) k_bucket_split(const int32_t* __restrict__ uu,
+__global__ void __launch_bounds__(kBlkS, 2) k_bucket_split(const int32_t* __restrict__ uu,
                                                            const uint16_t* __restrict__ lvv,
                                                            const unsigned long long* __restrict__ start,
                                                            const unsigned long long* __restrict__ seg_start,
@@ -520,9 +519,9 @@ __global__ void __launch_bounds__(kBlkS, 1) k_bucket_split(const int32_t* __rest
                                                            uint16_t* lv2, int* err) {
     __shared__ unsigned int s_tcnt[1 << kSubLog];
     __shared__ unsigned int s_tstart[1 << kSubLog];
-    __shared__ unsigned long long s_gb[1 << kSubLog];
-    extern __shared__ int32_t s_u[];                                // [kSplitTile]
-    uint16_t* s_lv = reinterpret_cast<uint16_t*>(s_u + kSplitTile);  // [kSplitTile]
+    __shared__ int s_disp[1 << kSubLog];           // staged position -> output position, per sub-bucket
+    __shared__ unsigned int s_end[1 << kSubLog];   // end of each sub-bucket's range
+    extern __shared__ uint2 s_st[];                // [kSplitTile] (u, local target)
     const int S = 1 << sublog;
     const unsigned int lmask = (1u << sb) - 1u;
     const long long ntiles = (long long)tile_base[nseg];
@@ -533,9 +532,12 @@ __global__ void __launch_bounds__(kBlkS, 1) k_bucket_split(const int32_t* __rest
         const long long tn = t + gridDim.x;
         SplitLoad nxt;
         if (tn < ntiles) nxt = split_load(uu, lvv, seg_start, seg_len, tile_base, tile_seg, nb, tn);
-        if (threadIdx.x < (unsigned)S) s_tcnt[threadIdx.x] = 0;
-        __syncthreads();
         const size_t f0 = (size_t)cur.b << sublog;
+        if (threadIdx.x < (unsigned)S) {
+            s_tcnt[threadIdx.x] = 0;
+            s_end[threadIdx.x] = (unsigned int)__ldg(&start[f0 + threadIdx.x + 1]);
+        }
+        __syncthreads();
         unsigned int lv[8];
         unpack8(cur.lv, lv);
         unsigned int rk[8];
@@ -563,21 +565,18 @@ __global__ void __launch_bounds__(kBlkS, 1) k_bucket_split(const int32_t* __rest
         const int u8[8] = {cur.ua.x, cur.ua.y, cur.ua.z, cur.ua.w, cur.ub.x, cur.ub.y, cur.ub.z, cur.ub.w};
 #pragma unroll
         for (int j = 0; j < 8; ++j)
-            if (rk[j] != ~0u) {
-                const unsigned int q = s_tstart[lv[j] >> sb] + rk[j];
-                s_u[q] = u8[j];
-                s_lv[q] = (uint16_t)lv[j];
-            }
-        if (x) s_gb[threadIdx.x] = g;
+            if (rk[j] != ~0u) s_st[s_tstart[lv[j] >> sb] + rk[j]] = make_uint2((uint32_t)u8[j], lv[j]);
+        // positions fit 32 bits (m <= INT32_MAX): one displacement per sub-bucket
+        if (x) s_disp[threadIdx.x] = (int)((long long)g - (long long)s_tstart[threadIdx.x]);
         __syncthreads();
-        const unsigned int total = s_tstart[S - 1] + s_tcnt[S - 1];
-        for (unsigned int q = threadIdx.x; q < total; q += blockDim.x) {
-            const unsigned int lvq = s_lv[q];
-            const unsigned int sub = lvq >> sb;
-            const unsigned long long pos = s_gb[sub] + (q - s_tstart[sub]);
-            if (pos < __ldg(&start[f0 + sub + 1])) {
-                u2[pos] = s_u[q];
-                lv2[pos] = (uint16_t)(lvq & lmask);
+        const int total = (int)(s_tstart[S - 1] + s_tcnt[S - 1]);
+        for (int q = threadIdx.x; q < total; q += kBlkS) {
+            const uint2 y = s_st[q];
+            const unsigned int sub = y.y >> sb;
+            const unsigned int pos = (unsigned int)(s_disp[sub] + q);
+            if (pos < s_end[sub]) {
+                u2[pos] = (int32_t)y.x;
+                lv2[pos] = (uint16_t)(y.y & lmask);
             } else {
                 atomicExch(err, SCC_ERR_INTERNAL);
             }
@@ -911,7 +910,7 @@ int launch_transpose_rest(int32_t n, int64_t mt, int shift, int K, const unsigne
         }
     }
     int per_sm = 0;
-    const size_t split_smem = (size_t)kSplitTile * (sizeof(int32_t) + sizeof(uint16_t));
+    const size_t split_smem = (size_t)kSplitTile * sizeof(uint2);
     SCC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bucket_split, kBlkS, split_smem));
     if (ev) cudaEventRecord(ev[0], s);
     if (mt > 0) {  // the tile count is read on the device; spare blocks return at once
@@ -991,7 +990,7 @@ int transpose_set_attributes_impl() {
     SCC_CUDA(cudaFuncSetAttribute(k_bucket_part, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   2 * kStep * (int)sizeof(int32_t)));
     SCC_CUDA(cudaFuncSetAttribute(k_bucket_split, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)((size_t)kSplitTile * (sizeof(int32_t) + sizeof(uint16_t)))));
+                                  (int)((size_t)kSplitTile * sizeof(uint2))));
     SCC_CUDA(cudaFuncSetAttribute(k_sub_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rows_smem_bytes()));
     return SCC_OK;
 }
