@@ -584,6 +584,229 @@ def run_serve(args, spec):
     return 0
 
 
+# ------------------------------------------------------------------ extras --
+# The default run (R-MAT 24 headline, one GPU) also measures the other
+# configurations in compact form, each beside its CPU oracle: the 3D torus,
+# the k-NN graph and the small 2D torus (plain per-graph SCC), the batch of
+# 4,096 graphs, and the served trace at its offered rate and at loads the
+# server sustains.
+def _extra_graph(name, scc, torch, stream, steps, warmup, cpu):
+    spec = WORKLOADS[name]
+    t_gen = time.perf_counter()
+    g = make_graph(spec)
+    t_gen = time.perf_counter() - t_gen
+    off_d = torch.from_numpy(g.offsets).to("cuda")
+    adj_d = torch.from_numpy(g.targets).to("cuda")
+    lab = torch.empty(max(g.n, 1), dtype=torch.int32, device="cuda")
+    torch.cuda.synchronize()
+
+    def step():
+        h = scc.scc_graph_create(g.n, g.m, off_d, adj_d, stream)
+        try:
+            scc.scc_run(h, lab, stream)
+            return scc.scc_get_stats(h)
+        finally:
+            scc.scc_graph_destroy(h)
+
+    with torch.cuda.stream(stream):
+        for _ in range(warmup):
+            step()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    sts = []
+    with torch.cuda.stream(stream):
+        ev0.record(stream)
+        for _ in range(steps):
+            sts.append(step())
+        ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1) / steps
+    mean = lambda k: sum(st[k] for st in sts) / len(sts)
+    out = {"workload": workload_name(spec, g), "n": g.n, "m": g.m, "seed": spec["seed"], "steps": steps,
+           "warmup": warmup, "ms_per_step": ms, "edges_per_s": g.m / (ms / 1e3),
+           "create_ms": mean("ms_create"),
+           "run_ms": {k: mean(k) for k in ("ms_trim", "ms_first_scc", "ms_class_trim", "ms_multi_search", "ms_label")},
+           "rounds": sts[-1]["search_rounds"], "batches": sts[-1]["batches"], "tau": sts[-1]["tau"],
+           "step": "scc_graph_create + scc_run + scc_graph_destroy, inputs resident in device memory",
+           "gen_seconds": t_gen}
+    if spec["kind"] == "torus" and spec["dims"] == 2:
+        out["note"] = "L2-resident (about 1.3 MB of CSR): a bandwidth fraction is not meaningful"
+    if cpu:
+        tc = time_oracle(g)
+        out["cpu_baseline"] = {"value": g.m / tc, "unit": UNIT, "cores": 1, "kind": "oracle",
+                               "sample": "the whole graph, 1 run", "seconds": tc}
+        out["gpu_over_oracle"] = (g.m / (ms / 1e3)) / (g.m / tc)
+    del off_d, adj_d, lab
+    return out
+
+
+def _extra_batch(scc, torch, stream, steps, warmup, cpu):
+    from paper_2303_04934_gb300 import graphgen as gg
+    import oracle
+    spec = WORKLOADS["batch4096"]
+    t_gen = time.perf_counter()
+    p = gg.mixed_batch(spec["G"], spec["n_lo"], spec["n_hi"], seed=spec["seed"])
+    t_gen = time.perf_counter() - t_gen
+    G, nv, na = p.G, int(p.vbase[-1]), int(p.ebase[-1])
+    sizes = np.diff(p.ebase) + np.diff(p.vbase)
+    order = np.argsort(-sizes, kind="stable")
+    d = [torch.from_numpy(a).to("cuda") for a in (p.vbase, p.ebase, p.offsets, p.targets)]
+    torch.cuda.synchronize()
+    h = scc.scc_batch_create(G, d[0], d[1], d[2], d[3], stream)
+    try:
+        t_tune = time.perf_counter()
+        best, ms_t = scc.scc_batch_autotune(h, sample=max(32, G // 16), stream=stream)
+        t_tune = time.perf_counter() - t_tune
+        tuned = {"tau": best.tau, "block": best.block, "lambda": best.lambda_, "sample_ms": ms_t,
+                 "seconds": t_tune}
+        cfg = scc.scc_batch_get_config(h)
+        labels_d = torch.empty(max(nv, 1), dtype=torch.int32, device="cuda")
+        with torch.cuda.stream(stream):
+            for _ in range(warmup):
+                scc.scc_batch_run(h, labels_d, stream)
+        torch.cuda.synchronize()
+        launches0 = scc.scc_debug_launch_count()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            ev0.record(stream)
+            for _ in range(steps):
+                scc.scc_batch_run(h, labels_d, stream)
+            ev1.record(stream)
+        torch.cuda.synchronize()
+        launches = scc.scc_debug_launch_count() - launches0
+        ms = ev0.elapsed_time(ev1) / steps
+        st = scc.scc_batch_get_stats(h)
+        tm = scc.scc_debug_batch_times(h, G).astype(np.int64)
+        dur = (tm[:, 5] - tm[:, 0]) / 1e6
+        span = (tm[:, 5].max() - tm[:, 0].min()) / 1e6
+        busy = np.bincount(tm[:, 6], weights=dur, minlength=st["blocks"])
+        labels_h = labels_d.cpu().numpy()
+    finally:
+        scc.scc_batch_destroy(h)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    alg = 20 * na + 24 * nv
+    out = {"workload": f"batch_G{G}_n{spec['n_lo']}-{spec['n_hi']}_torus2d-rmat8", "graphs": G, "vertices": nv,
+           "arcs": na, "seed": spec["seed"], "steps": steps, "warmup": warmup, "ms_per_step": ms,
+           "graphs_per_s": G / (ms / 1e3), "edges_per_s": na / (ms / 1e3), "gpu_launches_per_step": launches / steps,
+           "config": {"tau": cfg.tau, "block": cfg.block, "lambda": cfg.lambda_, "beta": cfg.beta,
+                      "blocks": st["blocks"], "workspace_gb": st["workspace_bytes"] / 2**30},
+           "autotuned": tuned,
+           "roofline": {"bound": "hbm", "kernel": "k_batch_scc (whole replay with the G^T passes)",
+                        "achieved": alg / (ms / 1e3) / 1e9, "peak": hbm_peak, "unit": "GB/s",
+                        "frac": alg / (ms / 1e3) / 1e9 / hbm_peak, "algorithmic_bytes_per_launch": alg,
+                        "bytes_formula": "20 B per arc + 24 B per vertex (build G^T, read G and G^T once, write labels)"},
+           "span_ms": span, "mean_block_ms": float(busy.mean()), "busiest_block_ms": float(busy.max()),
+           "span_over_mean_block": span / max(float(busy.mean()), 1e-9),
+           "step": "scc_batch_run (CUDA graph replay of the persistent launch), inputs resident in device memory",
+           "gen_seconds": t_gen}
+    # the plain per-graph path on a sample spread over the sizes, scaled
+    sample = _stratified(order, 64)
+    tot = 0.0
+    for gi in sample:
+        gph = p.graph(gi)
+        if gph.n == 0:
+            continue
+        od = torch.from_numpy(np.ascontiguousarray(gph.offsets)).to("cuda")
+        ad = torch.from_numpy(np.ascontiguousarray(gph.targets)).to("cuda")
+        lab = torch.empty(gph.n, dtype=torch.int32, device="cuda")
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            for rep in range(2):  # the first call warms this size up
+                if rep == 1:
+                    e0.record(stream)
+                hh = scc.scc_graph_create(gph.n, gph.m, od, ad, stream)
+                scc.scc_run(hh, lab, stream)
+                scc.scc_graph_destroy(hh)
+            e1.record(stream)
+        torch.cuda.synchronize()
+        tot += e0.elapsed_time(e1)
+    est_ms = tot * G / len(sample)
+    out["plain_per_graph"] = {"graphs_per_s": G / (est_ms / 1e3), "edges_per_s": na / (est_ms / 1e3),
+                              "ms_per_batch_est": est_ms, "sample_graphs": len(sample)}
+    out["speedup_vs_plain"] = out["graphs_per_s"] / out["plain_per_graph"]["graphs_per_s"]
+    if cpu:
+        import concurrent.futures as cf
+        csample = _stratified(order, max(16, G // 16))
+        cores = os.cpu_count() or 1
+        res = {}
+
+        def one(gi):
+            hg = p.graph(gi)
+            res[gi] = oracle.scc_labels(hg.n, hg.offsets, hg.targets)[0]
+
+        t0 = time.perf_counter()
+        with cf.ThreadPoolExecutor(max_workers=cores) as ex:
+            list(ex.map(one, csample))
+        tc = time.perf_counter() - t0
+        na_s = int(sum(p.ebase[g + 1] - p.ebase[g] for g in csample))
+        out["cpu_baseline"] = {"value": na_s / tc, "unit": UNIT, "cores": cores, "kind": "oracle",
+                               "sample": f"{len(csample)} of the {G} graphs spread over the size range, one graph "
+                                         "per thread", "seconds": tc}
+        out["gpu_over_oracle"] = out["edges_per_s"] / out["cpu_baseline"]["value"]
+        # the same sampled graphs' labels from the timed replays against the oracle's
+        out["labels_checked_graphs"] = len(csample)
+        out["labels_equal_oracle"] = bool(all(np.array_equal(p.labels_of(labels_h, g), res[g]) for g in csample))
+    del d
+    return out
+
+
+def _extra_serve(scc, torch, sweep=(0.25, 0.5, 0.9), sweep_seconds=2.0):
+    spec = dict(WORKLOADS["serve"])
+    t_gen = time.perf_counter()
+    pool = _serve_pool(spec["pool"], spec["n_lo"], spec["n_hi"], spec["seed"])
+    resident = _serve_pool(spec["resident"], spec["n_lo"], spec["n_hi"], spec["seed"] + 1)
+    t_gen = time.perf_counter() - t_gen
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
+    pool_h = [(g, (pin(g.offsets), pin(g.targets))) for g in pool]
+    res_h = [(pin(g.offsets), pin(g.targets)) for g in resident]
+    cfg = scc.scc_server_config_default()
+    cfg.mem_cap_bytes = int(spec["cap"])
+    plain_cfg = scc.scc_server_config_default()
+    plain_cfg.mem_cap_bytes = int(spec["cap"])
+    plain_cfg.batch_vertices = 0
+    plain_cfg.merge_reach = 0
+    plain_cfg.prefetch = 0
+
+    def both(trace):
+        r = {}
+        for name, c in (("server", cfg), ("plain", plain_cfg)):
+            st, wall, _ = _serve_once(scc, c, pool_h, res_h, resident, trace)
+            n_scc = sum(1 for q in trace if q[1] == 0)
+            r[name] = {"wall_s": wall, "requests_per_s": len(trace) / wall, "graphs_per_s": n_scc / wall,
+                       "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "scc_p99_ms": st["scc_p99_ms"],
+                       "reach_p99_ms": st["reach_p99_ms"], "failed": st["failed"]}
+        return r
+
+    trace = _serve_trace(spec, pool, resident, spec["seed"] + 2)
+    full = both(trace)
+    out = {"workload": f"serve_poisson{int(spec['rate'])}_{spec['seconds']}s_scc{spec['scc_frac']}",
+           "requests": len(trace), "scc_requests": sum(1 for q in trace if q[1] == 0),
+           "mem_cap_gb": spec["cap"] / 1e9, "offered_rate": spec["rate"], "at_offered_rate": full,
+           "speedup_vs_plain": {"graphs_per_s": full["server"]["graphs_per_s"] / full["plain"]["graphs_per_s"],
+                                "p99": full["plain"]["p99_ms"] / max(full["server"]["p99_ms"], 1e-9)},
+           "gen_seconds": t_gen}
+    sat = full["server"]["requests_per_s"]  # what the server completes when offered more than it can take
+    out["saturation_requests_per_s"] = sat
+    loads = []
+    for i, frac in enumerate(sweep):
+        sp = dict(spec)
+        sp["rate"] = frac * sat
+        sp["seconds"] = sweep_seconds
+        tr = _serve_trace(sp, pool, resident, spec["seed"] + 10 + i)
+        r = both(tr)
+        loads.append({"fraction_of_saturation": frac, "offered_rate": sp["rate"], "requests": len(tr), **r})
+    out["below_saturation"] = loads
+    out["note"] = ("every request is host in, host out; at the offered 2,000 requests/s both servers are "
+                   "overloaded, so their latencies there are queueing delays; the loads below saturation are "
+                   "fractions of the rate the continuous-batching server completes when overloaded")
+    return out
+
+
 # ------------------------------------------------------------------- ours --
 def main():
     ap = argparse.ArgumentParser()
@@ -607,6 +830,8 @@ def main():
     ap.add_argument("--batch-bps", type=int, default=None, help="batch workloads: blocks per SM (0 = auto)")
     ap.add_argument("--serve-seconds", type=float, default=None, help="serve workload: trace length")
     ap.add_argument("--serve-rate", type=float, default=None, help="serve workload: arrivals per second")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="default workload: skip the other configurations measured beside the headline")
     args = ap.parse_args()
     spec = dict(WORKLOADS[args.workload])
     if spec["kind"] == "batch":
@@ -744,6 +969,16 @@ def main():
                 traffic = rec["bytes_per_launch"]
     except Exception:
         traffic = None
+    # the transpose build (a1) as one unit: G read twice and G^T written once,
+    # 2 (4m + 4n) + (4m + 4n) = 12m + 12n bytes, over the four passes' time
+    a1_ms = sum(s["ms_transpose_hist"] + s["ms_transpose_part"] + s["ms_transpose_split"] + s["ms_transpose_rows"]
+                for s in stats) / len(stats)
+    a1_bytes = 12 * m + 12 * n
+    a1 = {"ms_per_step": a1_ms, "algorithmic_bytes": a1_bytes, "bytes_formula": "12m + 12n (G read twice, G^T written once)",
+          "achieved_gbs": a1_bytes / (a1_ms / 1e3) / 1e9 if a1_ms > 0 else None,
+          "frac": (a1_bytes / (a1_ms / 1e3) / 1e9 / hbm_peak) if a1_ms > 0 else None,
+          "passes_ms": {k: sum(s[k] for s in stats) / len(stats) for k in
+                        ("ms_transpose_hist", "ms_transpose_part", "ms_transpose_split", "ms_transpose_rows")}}
     roofline = {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": hbm_peak,
                 "peak_source": peak_src, "unit": "GB/s", "frac": achieved / hbm_peak, "traffic": traffic,
                 "algorithmic_bytes_per_launch": kbytes / max(1, klaunch),
@@ -797,7 +1032,7 @@ def main():
                        "tau": cfg.tau or last["tau"], "tau_auto": cfg.tau == 0, "seeds": cfg.seeds,
                        "beta": cfg.beta, "lambda": cfg.lambda_,
                        "step": "scc_graph_create + scc_run + scc_graph_destroy"},
-            "e2e": e2e, "roofline": roofline, "cpu_baseline": cpu, "gpu_launches": launches,
+            "e2e": e2e, "roofline": roofline, "a1_transpose": a1, "cpu_baseline": cpu, "gpu_launches": launches,
             "clocks": clk}
     # one extra step with the three calls timed separately (outside the timed
     # region): the SCC computation alone (scc_run on a built graph) as a rate too
@@ -820,6 +1055,19 @@ def main():
     if args.verbose:
         line["breakdown_last_step"] = last
         line["gen_seconds"] = t_gen
+    if (rank == 0 and world == 1 and not args.no_extras and args.workload == "rmat24" and not args.rmat_scale
+            and not args.rmat_ef):
+        t_x = time.perf_counter()
+        del off_d, adj_d, labels_d
+        torch.cuda.synchronize()
+        cpu_x = not args.no_cpu_baseline
+        line["workloads"] = {nm: _extra_graph(nm, scc, torch, stream, 5, 3, cpu_x)
+                             for nm in ("torus3d256", "knn8m", "torus2d256")}
+        torch.cuda.empty_cache()
+        line["batched"] = _extra_batch(scc, torch, stream, 3, 3, cpu_x)
+        torch.cuda.empty_cache()
+        line["served"] = _extra_serve(scc, torch)
+        line["extras_seconds"] = time.perf_counter() - t_x
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:
