@@ -6,7 +6,8 @@ reference leg may import this package. It shares no code with the CUDA path
 
 * :mod:`oracle.scc_oracle` (``scc_oracle.c``, plain C): iterative Tarjan, the
   transpose, trimming, class-restricted single/multi reachability, plain
-  multi-source reachability masks, the seeded pivot order and batch bounds.
+  multi-source reachability masks, the seeded pivot order and batch bounds, and
+  connected components of the undirected graph under the arcs (Sec. 5.1).
 * :mod:`oracle.definition` (numpy): the definitions written out through the
   transitive closure, for tiny graphs -- the pins of the C oracle.
 * :mod:`oracle.invariants` (numpy): properties every correct SCC labelling has.
@@ -61,10 +62,11 @@ def _load():
             lib.or_reach_mask.argtypes = [i64, vp, vp, vp, i64, vp]
             lib.or_pivot_order.argtypes = [i64, vp, u64, vp]
             lib.or_batch_bounds.argtypes = [i64, dbl, vp, i64]
+            lib.or_cc_labels.argtypes = [i64, vp, vp, vp]
             lib.or_mix64.argtypes = [u64]
             lib.or_mix64.restype = u64
             for f in ("or_scc_tarjan", "or_transpose", "or_trim", "or_reach_set", "or_multi_reach",
-                      "or_reach_mask", "or_pivot_order", "or_batch_bounds"):
+                      "or_reach_mask", "or_pivot_order", "or_batch_bounds", "or_cc_labels"):
                 getattr(lib, f).restype = i64
             _lib = lib
     return _lib
@@ -89,6 +91,19 @@ def scc_labels(n: int, offsets, targets):
     c = _load().or_scc_tarjan(n, po, pa, lab.ctypes.data)
     if c < 0:
         raise MemoryError("oracle: Tarjan allocation failed")
+    return lab[:n], int(c)
+
+
+def cc_labels(n: int, offsets, targets):
+    """Connected components of the undirected graph under the arcs (Sec. 5.1,
+    Alg. 4 output; the paper symmetrises directed inputs): ``label[v]`` =
+    smallest vertex id of v's component, by a sequential union-find. Returns
+    (labels int32[n], #components)."""
+    off, po, adj, pa = _csr(offsets, targets)
+    lab = np.empty(max(n, 1), np.int32)
+    c = _load().or_cc_labels(n, po, pa, lab.ctypes.data)
+    if c < 0:
+        raise MemoryError("oracle: union-find allocation failed")
     return lab[:n], int(c)
 
 

@@ -8,6 +8,9 @@ straight from its definition.
   to v; Sec. 1 notation).
 * SCC label (Sec. 1 problem statement, canonical minimum):
   ``label[v] = min{u : u ~> v and v ~> u}``.
+* Connected component label (Sec. 5.1, connectivity on the symmetrised graph):
+  ``label[v] = min{u : u and v joined by a path of arcs taken in either
+  direction}``.
 * Forward reachability pairs (Sec. 2): ``{(v, s) : s in S, s ~> v}``; backward:
   the same on the transpose. Inside a label class (Alg. 1, MultiReach skips an
   arc (u, v) with L(u) != L(v)) the closure is taken over the subgraph whose arcs
@@ -84,3 +87,14 @@ def reach_mask(n: int, edges, sources, backward: bool = False) -> np.ndarray:
     for j, s in enumerate(sources):
         out[r[s]] |= np.uint64(1) << np.uint64(j)
     return out
+
+
+def cc_labels(n: int, edges) -> np.ndarray:
+    """label[v] = min{u : u and v are joined by a path of arcs, each taken in
+    either direction} (closure of A | A^T)."""
+    a = adjacency(n, edges)
+    r = closure_of(a | a.T)
+    lab = np.empty(n, np.int32)
+    for v in range(n):
+        lab[v] = int(np.flatnonzero(r[:, v])[0])
+    return lab

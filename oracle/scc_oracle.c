@@ -23,6 +23,10 @@
  *   or_pivot_order     the seeded pivot permutation (Feistel network with cycle
  *                      walking) and or_batch_bounds the prefix-doubling batch
  *                      bounds (Alg. 1; Sec. 2 "The BGSS Algorithm", beta > 1).
+ *   or_cc_labels       connected components of the undirected graph under the
+ *                      arcs, label = smallest vertex id of the component: what
+ *                      the connectivity algorithm of Sec. 5.1 (Alg. 4, LDD-UF-JTB)
+ *                      computes, by its plain definition (sequential union-find).
  *
  * Parity pins (tests/test_oracle_*.py): brute-force transitive closure on every
  * digraph with n <= 4 and on random digraphs, closed forms (cycles, chains,
@@ -305,4 +309,43 @@ OR_API int64_t or_batch_bounds(int64_t N, double beta, int64_t* bounds, int64_t 
         x *= beta;
     }
     return nb;
+}
+
+/* ------------------------------------------------- connected components ---- */
+/*
+ * Connectivity (Sec. 5.1, Alg. 4 output): the components of the undirected
+ * graph in which every arc (u, v) of the CSR joins u and v (the paper
+ * symmetrises directed inputs for connectivity). A sequential union-find over
+ * the arcs: a union hooks the larger root under the smaller one, so the root of
+ * a component is its smallest vertex id; finds halve the path. Writes
+ * label[v] = smallest vertex id of v's component; returns the number of
+ * components (-1 if memory could not be allocated).
+ */
+static int32_t uf_find(int32_t* parent, int32_t x) {
+    while (parent[x] != x) {
+        parent[x] = parent[parent[x]];
+        x = parent[x];
+    }
+    return x;
+}
+
+OR_API int64_t or_cc_labels(int64_t n, const int32_t* off, const int32_t* adj, int32_t* label) {
+    if (n == 0) return 0;
+    int32_t* parent = (int32_t*)malloc(sizeof(int32_t) * (size_t)n);
+    if (!parent) return -1;
+    for (int64_t v = 0; v < n; ++v) parent[v] = (int32_t)v;
+    for (int64_t u = 0; u < n; ++u)
+        for (int64_t e = off[u]; e < off[u + 1]; ++e) {
+            int32_t a = uf_find(parent, (int32_t)u), b = uf_find(parent, adj[e]);
+            if (a == b) continue;
+            if (a < b) parent[b] = a;
+            else parent[a] = b;
+        }
+    int64_t comps = 0;
+    for (int64_t v = 0; v < n; ++v) {
+        label[v] = uf_find(parent, (int32_t)v);
+        if (label[v] == (int32_t)v) ++comps;
+    }
+    free(parent);
+    return comps;
 }
