@@ -299,7 +299,7 @@ def run_batch(args, spec):
             c.tau = args.tau
         scc.scc_batch_set_config(h, c)
     if args.autotune:
-        best, ms_t = scc.scc_batch_autotune(h, sample=max(32, G // 16), stream=stream)
+        best, ms_t = scc.scc_batch_autotune(h, sample=min(64, G), stream=stream)
         tuned = {"tau": best.tau, "block": best.block, "lambda": best.lambda_, "sample_ms": ms_t}
     cfg = scc.scc_batch_get_config(h)
     labels_d = torch.empty(max(nv, 1), dtype=torch.int32, device="cuda")
@@ -631,12 +631,79 @@ def _extra_graph(name, scc, torch, stream, steps, warmup, cpu):
            "gen_seconds": t_gen}
     if spec["kind"] == "torus" and spec["dims"] == 2:
         out["note"] = "L2-resident (about 1.3 MB of CSR): a bandwidth fraction is not meaningful"
+    out["connectivity"] = _measure_cc(g, off_d, adj_d, scc, torch, stream, 5, 2, cpu)
+    if spec["kind"] == "knn":
+        # the hash bag of Sec. 3.3 (sampled, sigma = 50) against a reservation bag
+        # (sigma = 0: one counter hands out segments), on the multi-reachability
+        # heavy graph; scc_run alone on a built graph
+        abl = {}
+        h = scc.scc_graph_create(g.n, g.m, off_d, adj_d, stream)
+        try:
+            for name, sig in (("sampled_sigma50", 50), ("reservation", 0)):
+                c = scc.scc_config_default()
+                c.sigma = sig
+                scc.scc_set_config(h, c)
+                ts = []
+                for rep in range(3):
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    with torch.cuda.stream(stream):
+                        e0.record(stream)
+                        scc.scc_run(h, lab, stream)
+                        e1.record(stream)
+                    torch.cuda.synchronize()
+                    if rep:
+                        ts.append(e0.elapsed_time(e1))
+                st = scc.scc_get_stats(h)
+                abl[name] = {"scc_run_ms": sum(ts) / len(ts), "rounds": st["search_rounds"],
+                             "ms_multi_search": st["ms_multi_search"], "pairs": st["pairs"]}
+        finally:
+            scc.scc_graph_destroy(h)
+        out["bag_ablation"] = abl
     if cpu:
         tc = time_oracle(g)
         out["cpu_baseline"] = {"value": g.m / tc, "unit": UNIT, "cores": 1, "kind": "oracle",
                                "sample": "the whole graph, 1 run", "seconds": tc}
         out["gpu_over_oracle"] = (g.m / (ms / 1e3)) / (g.m / tc)
     del off_d, adj_d, lab
+    return out
+
+
+def _measure_cc(g, off_d, adj_d, scc, torch, stream, steps, warmup, cpu):
+    """Connected components (cc_run: LDD-UF-JTB with VGC and the hash bag,
+    Sec. 5.1) of the undirected graph under the arcs, on a built graph: the
+    labels checked against the oracle's union-find, both timed."""
+    import oracle
+    lab = torch.empty(max(g.n, 1), dtype=torch.int32, device="cuda")
+    h = scc.scc_graph_create(g.n, g.m, off_d, adj_d, stream)
+    try:
+        with torch.cuda.stream(stream):
+            for _ in range(warmup):
+                scc.cc_run(h, lab, stream)
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            ev0.record(stream)
+            for _ in range(steps):
+                scc.cc_run(h, lab, stream)
+            ev1.record(stream)
+        torch.cuda.synchronize()
+        st = scc.cc_get_stats(h)
+    finally:
+        scc.scc_graph_destroy(h)
+    ms = ev0.elapsed_time(ev1) / steps
+    out = {"ms_per_run": ms, "edges_per_s": g.m / (ms / 1e3), "steps": steps, "warmup": warmup,
+           "components": st["components"], "clusters": st["clusters"], "ldd_rounds": st["ldd_rounds"],
+           "ldd_batches": st["ldd_batches"], "cross_arcs": st["cross_arcs"],
+           "ms_split": {k: st[k] for k in ("ms_ldd", "ms_union", "ms_label")},
+           "step": "cc_run on a built graph (symmetric CSR kept from the warm-up)"}
+    if cpu:
+        t0 = time.perf_counter()
+        want, ncc = oracle.cc_labels(g.n, g.offsets, g.targets)
+        tc = time.perf_counter() - t0
+        out["labels_equal_oracle"] = bool(np.array_equal(lab.cpu().numpy()[:g.n], want))
+        out["cpu_baseline"] = {"value": g.m / tc, "unit": UNIT, "cores": 1, "kind": "oracle",
+                               "sample": "the whole graph, 1 run (sequential union-find)", "seconds": tc}
+    del lab
     return out
 
 
@@ -655,7 +722,7 @@ def _extra_batch(scc, torch, stream, steps, warmup, cpu):
     h = scc.scc_batch_create(G, d[0], d[1], d[2], d[3], stream)
     try:
         t_tune = time.perf_counter()
-        best, ms_t = scc.scc_batch_autotune(h, sample=max(32, G // 16), stream=stream)
+        best, ms_t = scc.scc_batch_autotune(h, sample=min(64, G), stream=stream)
         t_tune = time.perf_counter() - t_tune
         tuned = {"tau": best.tau, "block": best.block, "lambda": best.lambda_, "sample_ms": ms_t,
                  "seconds": t_tune}
@@ -1050,6 +1117,27 @@ def main():
         torch.cuda.synchronize()
     t_run = evs[1].elapsed_time(evs[2])
     line["split_ms"] = {"create": evs[0].elapsed_time(evs[1]), "run": t_run, "destroy": evs[2].elapsed_time(evs[3])}
+    # the whole run's algorithmic bytes (counted from the run's own counters):
+    # 4 B target + 4 B label or visited word per arc examined, 8 B row offsets
+    # per item expanded, 16 B per pair inserted (table slot + bag slot), 20 B per
+    # active vertex per labelling (the first SCC's over the untrimmed vertices,
+    # then one per multi-reachability batch); the step adds the transpose
+    # build's 12m + 12n
+    E = last["engine_arcs"] + last["multi_arcs"]
+    P = last["engine_items"] + last["multi_items"]
+    I = last["pairs"]
+    act = (n - last["n_trimmed"]) + last["multi_active_sum"]
+    run_bytes = 8 * E + 8 * P + 16 * I + 20 * act
+    line["run_roofline"] = {
+        "bound": "hbm", "bytes_formula": "8 E + 8 P + 16 I + 20 sum(active per labelling)",
+        "E_arcs": E, "P_items": P, "I_pairs": I, "active_labelled": act, "algorithmic_bytes": run_bytes,
+        "scc_run_ms": t_run, "achieved_gbs": run_bytes / (t_run / 1e3) / 1e9 if t_run > 0 else None,
+        "frac": run_bytes / (t_run / 1e3) / 1e9 / hbm_peak if t_run > 0 else None, "peak": hbm_peak,
+        "step_bytes": run_bytes + a1_bytes, "step_ms": ms / args.steps,
+        "step_achieved_gbs": (run_bytes + a1_bytes) / (ms / args.steps / 1e3) / 1e9,
+        "step_frac": (run_bytes + a1_bytes) / (ms / args.steps / 1e3) / 1e9 / hbm_peak,
+        "lower_bound_bytes": 8 * m + 12 * n,
+        "lower_bound_note": "read G and G^T once and write the labels: no SCC method moves fewer bytes"}
     line["scc_run_only"] = {"ms": t_run, "edges_per_s": m / (t_run / 1e3) if t_run > 0 else None,
                             "note": "one scc_run on a built graph (the step also builds and frees it)"}
     if args.verbose:
@@ -1058,6 +1146,7 @@ def main():
     if (rank == 0 and world == 1 and not args.no_extras and args.workload == "rmat24" and not args.rmat_scale
             and not args.rmat_ef):
         t_x = time.perf_counter()
+        line["connectivity"] = _measure_cc(g, off_d, adj_d, scc, torch, stream, 5, 2, not args.no_cpu_baseline)
         del off_d, adj_d, labels_d
         torch.cuda.synchronize()
         cpu_x = not args.no_cpu_baseline

@@ -80,7 +80,9 @@ SCC_API const char* scc_error_string(int code);
  *   lambda      first hash-bag chunk size in slots, a power of two in [1024, 2^24]
  *               (Sec. 3.3; chunks grow lambda, 2*lambda, ...). Default 16384.
  *   sigma       hash-bag samples per chunk before it is declared full (Sec. 3.3),
- *               1..2^20, default 50.
+ *               1..2^20, default 50; 0 replaces the sampled hash bag by a
+ *               reservation bag (one counter hands out 32-slot segments in
+ *               order) as the comparison point of the paper's bag design.
  *   block       threads per block of the search kernels (256; other values are
  *               rejected with SCC_ERR_INVALID_ARG).
  *   seeds       frontier items one warp takes per task, 1..32 (default 32).
@@ -225,9 +227,43 @@ typedef struct scc_stats {
     int64_t multi_items;       /* items expanded */
     int32_t tau;               /* the VGC edge budget used (config tau, or the automatic one) */
     double ms_transpose_split; /* transpose: buckets cut into sub-buckets (ms_transpose_rows: their rows) */
+    int64_t multi_active_sum;  /* active vertices summed over the multi-reachability batches */
 } scc_stats;
 
 SCC_API int scc_get_stats(scc_handle h, scc_stats* out);
+
+/* ---------------------------------------------------------- connectivity ---- */
+/*
+ * Connected components (Sec. 5.1, Alg. 4: LDD-UF-JTB, with the hash bag and
+ * VGC applied to the low-diameter decomposition) of the undirected graph under
+ * the arcs of h: u and v are in one component iff a path joins them when every
+ * arc may be taken in either direction (the paper symmetrises directed inputs
+ * for connectivity; for a directed graph these are its weakly connected
+ * components). labels_out[v] = the smallest vertex id of v's component.
+ *   labels_out  host or device int32[n], written.
+ * The first call on h builds the symmetric CSR (each vertex's out-arcs then
+ * its in-arcs, 2 m_t entries) and keeps it with the handle until it is
+ * destroyed. The decomposition takes its centres from h's seeded order in
+ * batches growing by a factor 1.2 (the paper's choice); the result does not
+ * depend on the seed. Returns SCC_ERR_INTERNAL if a bounded union-find loop
+ * ran out (never expected). Synchronises `stream` before returning.
+ */
+SCC_API int cc_run(scc_handle h, int32_t* labels_out, void* stream);
+
+/* Counters of the last cc_run on h (times in milliseconds, CUDA events on the
+   stream of the call). */
+typedef struct scc_cc_stats {
+    int32_t components;   /* connected components found */
+    int32_t clusters;     /* clusters of the low-diameter decomposition (centres) */
+    int32_t ldd_rounds;   /* rounds of the decomposition's search */
+    int32_t ldd_batches;  /* batches of candidate centres */
+    int64_t ldd_arcs;     /* arcs examined by the decomposition's search */
+    int64_t cross_arcs;   /* arcs of G joining two clusters (the union-find's work) */
+    double ms_sym;        /* building the symmetric CSR (0 when it was kept from an earlier call) */
+    double ms_ldd, ms_union, ms_label, ms_total;
+} scc_cc_stats;
+
+SCC_API int cc_get_stats(scc_handle h, scc_cc_stats* out);
 
 #ifdef __cplusplus
 }

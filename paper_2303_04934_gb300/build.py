@@ -19,7 +19,8 @@ CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_lib")
 SO_NAME = "libscc_gb300.so"
 SO_PATH = os.path.join(OUT_DIR, SO_NAME)
-SOURCES = ["api.cu", "steps.cu", "search.cu", "transpose.cu", "bgss.cu", "noalloc.cu", "batch.cu", "serve.cu"]
+SOURCES = ["api.cu", "steps.cu", "search.cu", "transpose.cu", "bgss.cu", "noalloc.cu", "batch.cu", "serve.cu",
+           "cc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

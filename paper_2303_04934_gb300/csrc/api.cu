@@ -54,6 +54,10 @@ struct scc_graph {
     EngineBuf eb32, eb64;
     scc_stats stats;
     double create_ms[5] = {0, 0, 0, 0, 0};  // total, histogram, partition, rows, split
+    // connectivity: the symmetric CSR (built on the first cc_run) and its stats
+    int32_t* soff = nullptr;
+    int32_t* sadj = nullptr;
+    scc_cc_stats cc_stats;
 };
 
 namespace scc {
@@ -178,7 +182,7 @@ int valid_config(const scc_config* c) {
     if (c->tau < 0 || c->tau > (1 << 20)) return SCC_ERR_INVALID_ARG;
     if (!(c->beta > 1.0 && c->beta <= 64.0)) return SCC_ERR_INVALID_ARG;
     if (c->lambda < 1024 || c->lambda > (1 << 24) || (c->lambda & (c->lambda - 1))) return SCC_ERR_INVALID_ARG;
-    if (c->sigma < 1 || c->sigma > (1 << 20)) return SCC_ERR_INVALID_ARG;
+    if (c->sigma < 0 || c->sigma > (1 << 20)) return SCC_ERR_INVALID_ARG;
     if (c->block != 256) return SCC_ERR_INVALID_ARG;
     if (c->seeds < 1 || c->seeds > 32) return SCC_ERR_INVALID_ARG;
     if (c->dense < 0 || c->dense > 1024) return SCC_ERR_INVALID_ARG;
@@ -546,6 +550,8 @@ static void graph_free(scc_graph* h, cudaStream_t s) {
     dfree(h->rem_v, s);
     engine_release(&h->eb32, s);
     engine_release(&h->eb64, s);
+    dfree(h->soff, s);
+    dfree(h->sadj, s);
 }
 
 int scc_graph_create(int32_t n, int64_t m, const int32_t* offsets, const int32_t* targets, void* stream,
@@ -783,6 +789,7 @@ static int scc_run_impl(scc_graph* h, int32_t* labels_out, cudaStream_t s) {
                 st.batches += r.batches;
                 st.search_rounds += r.rounds;
                 st.pairs += (int64_t)r.pairs;
+                st.multi_active_sum += (int64_t)r.active_sum;
                 st.engine_inserted += (int64_t)r.pairs;
                 st.multi_launches++;
                 st.multi_arcs += (int64_t)r.edges;
@@ -881,6 +888,119 @@ int reach_multi_noalloc(scc_handle h, const int32_t* sources, int32_t k, int32_t
     cudaStream_t s = (cudaStream_t)stream;
     return reach_multi_noalloc_impl(dir == 0 ? h->off : h->toff, dir == 0 ? h->adj : h->tadj, h->n, h->mt,
                                     h->cfg.lambda, opts_of(h), sources, k, out, s);
+}
+
+// ----------------------------------------------------------- connectivity --
+// Connected components of the undirected graph under G's arcs (Sec. 5.1,
+// Alg. 4 LDD-UF-JTB with VGC and the hash bag; steps in cc.cu).
+static constexpr double kLddBeta = 1.2;  // batch growth of the decomposition (Sec. 5.1)
+
+static int cc_run_impl(scc_graph* h, int32_t* labels_out, cudaStream_t s) {
+    const int32_t n = h->n;
+    scc_cc_stats& st = h->cc_stats;
+    memset(&st, 0, sizeof(st));
+    if (n == 0) return SCC_OK;
+    const int num_sms = h->di.num_sms;
+    EvTimer tt(s);
+    tt.start();
+    EvTimer t(s);
+    // the symmetric CSR, kept with the handle
+    t.start();
+    if (!h->soff) {
+        int32_t *so = nullptr, *sa = nullptr;
+        SCC_TRY(dalloc_t(&so, (size_t)n + 1, s));
+        if (dalloc_t(&sa, (size_t)std::max<int64_t>(2 * h->mt, 1), s) != SCC_OK) {
+            dfree(so, s);
+            return SCC_ERR_OOM;
+        }
+        h->soff = so;
+        h->sadj = sa;
+        SCC_TRY(launch_sym_csr(h->off, h->adj, h->toff, h->tadj, n, h->soff, h->sadj, num_sms, s));
+    }
+    st.ms_sym = t.stop();
+    // the seeded order of all vertices and its batches
+    Scratch tmp(s);
+    int32_t *order = nullptr, *center = nullptr, *parent = nullptr, *root = nullptr, *mn = nullptr, *out = nullptr;
+    long long* bounds_d = nullptr;
+    unsigned long long* counters = nullptr;
+    int* err = nullptr;
+    SCC_TRY(tmp.alloc(&order, (size_t)n));
+    SCC_TRY(tmp.alloc(&center, (size_t)n));
+    SCC_TRY(tmp.alloc(&parent, (size_t)n));
+    SCC_TRY(tmp.alloc(&root, (size_t)n));
+    SCC_TRY(tmp.alloc(&mn, (size_t)n));
+    SCC_TRY(tmp.alloc(&counters, 4));
+    SCC_TRY(tmp.alloc(&err, 1));
+    const bool dev_out = is_device_ptr(labels_out);
+    if (dev_out) out = labels_out;
+    else SCC_TRY(tmp.alloc(&out, (size_t)n));
+    SCC_CUDA(cudaMemsetAsync(counters, 0, 4 * sizeof(unsigned long long), s));
+    SCC_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
+    std::vector<long long> bounds{0};
+    {
+        double x = 1.0;
+        long long pos = 0;
+        while (pos < n) {
+            long long sz;
+            if (x >= (double)n) sz = n;
+            else {
+                sz = (long long)x;
+                if ((double)sz < x) ++sz;
+            }
+            if (sz < 1) sz = 1;
+            pos = ((long long)n - pos < sz) ? (long long)n : pos + sz;
+            bounds.push_back(pos);
+            x *= kLddBeta;
+        }
+    }
+    const int nb = (int)bounds.size() - 1;
+    SCC_TRY(tmp.alloc(&bounds_d, bounds.size()));
+    SCC_CUDA(cudaMemcpyAsync(bounds_d, bounds.data(), sizeof(long long) * bounds.size(), cudaMemcpyHostToDevice, s));
+    // ---- LDD (Alg. 4 function LDD)
+    t.start();
+    SCC_TRY(launch_iota(n, root, num_sms, s));  // the identity list, permuted into the order
+    SCC_TRY(launch_pivot_order(root, (int64_t)n, h->cfg.seed, order, s));
+    SCC_TRY(launch_ldd_setup(order, bounds[1], n, center, num_sms, s));
+    SCC_TRY(engine_reserve(&h->eb32, 4, (long long)n + 1024, h->cfg.lambda, 2 * h->mt, num_sms, s));
+    EngineOpts o = opts_of(h);
+    EngineRun r;
+    SCC_TRY(run_ldd(h->soff, h->sadj, n, order, bounds_d, bounds[1], nb, center, &h->eb32, o, &r, s));
+    st.ms_ldd = t.stop();
+    st.ldd_rounds = r.rounds;
+    st.ldd_batches = nb;
+    st.ldd_arcs = (int64_t)r.edges;
+    // ---- union-find over the cross arcs (Alg. 4 Union), then the labels
+    CreateEvents ev;
+    cudaEventRecord(ev.e[0], s);
+    SCC_TRY(launch_cc_union_label(h->off, h->adj, n, center, parent, root, mn, out, counters, err, num_sms, s,
+                                  &ev.e[1]));
+    if (!dev_out) SCC_TRY(from_device(labels_out, out, sizeof(int32_t) * (size_t)n, s));
+    unsigned long long hc[4];
+    int herr = 0;
+    SCC_CUDA(cudaMemcpyAsync(hc, counters, sizeof(hc), cudaMemcpyDeviceToHost, s));
+    SCC_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    SCC_CUDA(cudaStreamSynchronize(s));
+    if (herr) return herr;
+    st.cross_arcs = (int64_t)hc[0];
+    st.clusters = (int32_t)hc[1];
+    st.components = (int32_t)hc[2];
+    st.ms_union = ev.ms(1, 2);
+    st.ms_label = ev.ms(2, 3);
+    st.ms_total = tt.stop();
+    return SCC_OK;
+}
+
+int cc_run(scc_handle h, int32_t* labels_out, void* stream) {
+    if (!h || (h->n > 0 && !labels_out)) return SCC_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    h->last = s;
+    return cc_run_impl(h, labels_out, s);
+}
+
+int cc_get_stats(scc_handle h, scc_cc_stats* out) {
+    if (!h || !out) return SCC_ERR_INVALID_ARG;
+    *out = h->cc_stats;
+    return SCC_OK;
 }
 
 // ------------------------------------------------------------ debug hooks --

@@ -37,6 +37,7 @@ struct BgssCtl {
     int rounds;
     unsigned long long edges;
     unsigned long long items;
+    unsigned long long active_sum;  // active vertices summed over the batches run
 };
 
 namespace {
@@ -124,6 +125,7 @@ __global__ void __launch_bounds__(kEngineBlock, 2) bgss_kernel(BgssParams B) {
         const int k = ld_volatile(&bc->k[kb]);
         const long long b_active = B.N - (long long)ld_volatile(&bc->ndone);
         if (b_active <= 0) break;
+        if (gtid == 0) bc->active_sum += (unsigned long long)b_active;
         if (b_active < B.shrink_below) {
             status = 2;
             stop_batch = i;
@@ -290,6 +292,7 @@ int run_bgss_device(const BgssArgs& a, BgssResult* res, cudaStream_t st) {
     res->a_prev[0] = h.a[0];
     res->a_prev[1] = h.a[1];
     res->pairs = h.pairs;
+    res->active_sum = h.active_sum;
     res->batches = h.batches;
     res->rounds = h.rounds;
     res->edges = h.edges;

@@ -72,6 +72,7 @@ struct Sent<uint64_t> {
 struct BagCtl {
     int r;                   // current chunk
     int sample[kMaxChunks];  // sampled segment claims per chunk
+    unsigned long long tail; // reservation bag (sigma = 0): next free slot
 };
 
 // Per-round state, a ring of three indexed by the global round number g: round
@@ -215,9 +216,24 @@ struct SegState {
 };
 
 // Claim a free segment of the current chunk (lane 0 only). Returns slot index or
-// -1 (bag exhausted: error recorded).
+// -1 (bag exhausted: error recorded). With sigma = 0 the bag is a reservation
+// bag instead (the comparison point of the sampled design): one counter hands
+// out segments in order, and the chunk index only records how far the slots
+// were used, so that the next round's ForAll reads the same prefix.
 template <class Item>
 __device__ long long bag_claim(const BagRef<Item>& b, uint32_t wid, uint32_t round, uint32_t& seq) {
+    if (b.sigma == 0) {
+        const long long idx = (long long)atomicAdd(&b.bc->tail, (unsigned long long)kSeg);
+        if (idx + kSeg > b.nslots) {
+            atomicCAS(b.err, 0, SCC_ERR_CAPACITY);
+            return -1;
+        }
+        int j = 0;
+        while (j + 1 < kMaxChunks && chunk_end(b.lambda, j, b.nslots) < idx + kSeg) ++j;
+        if (j > ld_volatile(&b.bc->r)) atomicMax(&b.bc->r, j);
+        if (j > ld_volatile(b.max_chunk)) atomicMax(b.max_chunk, j);
+        return idx;
+    }
     for (int attempt = 0; attempt < 4 * kMaxChunks; ++attempt) {
         const int r = ld_volatile(&b.bc->r);
         const long long cb = chunk_begin(b.lambda, r);
@@ -511,6 +527,7 @@ __device__ bool engine_search(const EngineParams<typename Pol::Item>& P, Pol& po
             RoundCtl& nx = ctl->ring[(gr + 1) % 3];
             nx.bag.r = 0;
             for (int j = 0; j < kMaxChunks; ++j) nx.bag.sample[j] = 0;
+            nx.bag.tail = 0;
             nx.items = 0;
             nx.hubseg = 0;
             nx.work = 0;
@@ -782,6 +799,10 @@ __device__ bool engine_search(const EngineParams<typename Pol::Item>& P, Pol& po
                 if constexpr (Pol::kCountInserts) pol.flush(sc);
             }
             if constexpr (Pol::kCountInserts) pol.flush(sc);
+            // policies that add sources while the search runs (the batches of
+            // the low-diameter decomposition, Alg. 4) push them into this
+            // round's bag: they join the next round's frontier
+            if constexpr (Pol::kInject) pol.inject(i, out, st, wid, nwarps, gr, pushed);
         }
         if (lane == 0 && pushed) atomicAdd((unsigned long long*)&cur.items, pushed);
         if (!S::sync(&ctl->bar, &ctl->err)) return false;
@@ -801,7 +822,12 @@ __device__ bool engine_search(const EngineParams<typename Pol::Item>& P, Pol& po
             why = 1;
             break;
         }
-        if (ld_volatile(&cur.items) == 0 && ld_volatile(&cur.nhub) == 0) break;
+        if (ld_volatile(&cur.items) == 0 && ld_volatile(&cur.nhub) == 0) {
+            if constexpr (Pol::kInject) {
+                if (pol.more(i)) continue;  // an empty frontier, but batches of sources remain
+            }
+            break;
+        }
     }
     // for readers after the launch (the caller inside the launch uses `why`)
     if (S::block() == 0 && threadIdx.x == 0) {
@@ -851,6 +877,7 @@ struct PolSingle {
     static constexpr bool kCtxInQueue = false;
     using Ctx = uint64_t;  // the per-item value an arc test reads
     static constexpr bool kTwoGraphs = false;
+    static constexpr bool kInject = false;
     static constexpr const char* kName = "single-reach";
     uint32_t* bits;
     __device__ __forceinline__ int vertex(Item it) const { return (int)it; }
@@ -881,6 +908,7 @@ struct PolSingleBoth {
     static constexpr bool kCtxInQueue = false;
     using Ctx = uint64_t;  // the per-item value an arc test reads
     static constexpr bool kTwoGraphs = true;
+    static constexpr bool kInject = false;
     static constexpr const char* kName = "single-reach-both";
     static constexpr uint32_t kDir = 1u << 31;
     uint32_t* bits[2];
@@ -955,6 +983,7 @@ struct PolPair {
     static constexpr bool kCtxInQueue = true;
     using Ctx = uint64_t;  // the per-item value an arc test reads
     static constexpr bool kTwoGraphs = true;
+    static constexpr bool kInject = false;
     static constexpr const char* kName = "multi-reach";
     static constexpr uint64_t kDir = 1ull << 63;
     const int32_t* label;
@@ -1028,6 +1057,7 @@ struct PolMask {
     static constexpr bool kCtxInQueue = false;
     using Ctx = uint64_t;  // the per-item value an arc test reads
     static constexpr bool kTwoGraphs = false;
+    static constexpr bool kInject = false;
     static constexpr const char* kName = "mask-reach";
     unsigned long long* mask;
     bool test_first;  // read the target's mask before the atomic (high-degree graphs)
@@ -1062,6 +1092,7 @@ struct PolMask2 {
     static constexpr bool kCtxInQueue = false;
     using Ctx = Mask128;
     static constexpr bool kTwoGraphs = false;
+    static constexpr bool kInject = false;
     static constexpr const char* kName = "mask-reach-128";
     unsigned long long* mask;
     bool test_first;  // read the target's words before the atomics (high-degree graphs)
@@ -1077,6 +1108,56 @@ struct PolMask2 {
         const unsigned long long o1 = mu.hi ? atomicOr(&tw[1], mu.hi) : 0ull;
         child = (Item)w;
         return ((mu.lo & ~o0) | (mu.hi & ~o1)) != 0;
+    }
+};
+
+// Low-diameter decomposition (Sec. 5.1, Alg. 4 function LDD) on the symmetric
+// graph: vertex items; an arc (u, w) claims an unvisited w for u's centre
+// (center[w] = center[u] by CAS from -1: Alg. 4 "visit[u] <- true, L(u) <-
+// L(v)"). The centre travels with an item in the local queue; an item read
+// from the bag takes it from center[]. With VGC a round explores up to tau
+// arcs from an item instead of one BFS level (reachability, not BFS order, is
+// what the decomposition needs; Sec. 5.1). At the end of round i the unvisited
+// vertices of batch i + 1 of the seeded order become centres of their own and
+// join the frontier (Alg. 4, F = F' + B_i); the search ends when the frontier
+// is empty and no batch is left.
+struct PolLdd {
+    using Item = uint32_t;
+    static constexpr int kQueue = 256;
+    static constexpr bool kCountInserts = false;
+    static constexpr bool kDense = false;
+    static constexpr bool kCtxInQueue = true;
+    using Ctx = uint64_t;  // the centre of the item's cluster
+    static constexpr bool kTwoGraphs = false;
+    static constexpr bool kInject = true;
+    static constexpr const char* kName = "ldd";
+    int32_t* center;          // -1: not yet claimed
+    const int32_t* order;     // seeded order of all vertices
+    const long long* bounds;  // batch i = order[bounds[i] .. bounds[i + 1])
+    int nbatches;
+    __device__ __forceinline__ int vertex(Item it) const { return (int)it; }
+    __device__ __forceinline__ uint64_t ctx(Item it) const { return (uint64_t)(uint32_t)ld_volatile(&center[it]); }
+    __device__ __forceinline__ int32_t load_ctx(Item it) const { return ld_volatile(&center[it]); }
+    __device__ __forceinline__ bool seed(Item) const { return true; }  // items are claimed when pushed
+    __device__ __forceinline__ bool visit(Item, uint64_t c, int w, Item& child) const {
+        if (ld_volatile(&center[w]) >= 0) return false;
+        child = (Item)w;
+        return atomicCAS(&center[w], -1, (int32_t)(uint32_t)c) == -1;
+    }
+    __device__ __forceinline__ bool more(uint32_t i) const { return (long long)i + 2 < (long long)nbatches; }
+    // warp-collective: the unvisited vertices of batch i + 1 claim themselves
+    // and go into this round's bag
+    __device__ __forceinline__ void inject(uint32_t i, const BagRef<Item>& out, SegState& st, uint32_t wid,
+                                           uint32_t nwarps, uint32_t round, unsigned long long& pushed) const {
+        if ((long long)i + 1 >= (long long)nbatches) return;
+        const long long p0 = bounds[i + 1], p1 = bounds[i + 2];
+        const int lane = lane_id();
+        for (long long p = p0 + (long long)wid * 32; p < p1; p += (long long)nwarps * 32) {
+            const long long q = p + lane;
+            const int v = q < p1 ? order[q] : -1;
+            const bool claim = v >= 0 && ld_volatile(&center[v]) < 0 && atomicCAS(&center[v], -1, v) == -1;
+            pushed += bag_push<Item>(out, st, claim, (Item)(claim ? v : 0), wid, round);
+        }
     }
 };
 

@@ -344,6 +344,7 @@ struct BgssResult {
     int batches = 0;
     int rounds = 0;
     unsigned long long edges = 0, items = 0;
+    unsigned long long active_sum = 0;  // active vertices summed over the launch's batches
 };
 size_t bgss_ctl_bytes();
 int bgss_full_grid(int num_sms);
@@ -367,6 +368,27 @@ int batch_runner_enqueue(BatchRunner* r, int32_t G, const long long* vbase, cons
                          int32_t* out, cudaStream_t s);
 
 // Mask reachability on fixed buffers (no allocation, no events).
+// Low-diameter decomposition (Sec. 5.1, Alg. 4) on the symmetric CSR: batch i
+// of the seeded order is order[bounds_d[i] .. bounds_d[i + 1]) (nbatches
+// batches; the first, of `first` vertices, already centres itself in
+// center[]); on return center[v] is the centre of v's cluster.
+int run_ldd(const int32_t* soff, const int32_t* sadj, int32_t n, const int32_t* order, const long long* bounds_d,
+            long long first, int nbatches, int32_t* center, EngineBuf* b, const EngineOpts& o, EngineRun* out,
+            cudaStream_t st);
+// Connectivity steps (cc.cu): the symmetric CSR (soff[v] = off[v] + toff[v],
+// row v = row v of G then row v of G^T); center[] = -1 with the first `first`
+// vertices of order centring themselves; then union-find over the arcs of G
+// joining two clusters and out[v] = the smallest vertex id of v's component
+// (counters[0] += cross arcs, counters[1] += centres, counters[2] += components;
+// err: a bounded union-find loop ran out). launch_iota: a[v] = v. Events ev[0..2]: after the union-find set-up, after the
+// unions, after the labels.
+int launch_sym_csr(const int32_t* off, const int32_t* adj, const int32_t* toff, const int32_t* tadj, int32_t n,
+                   int32_t* soff, int32_t* sadj, int num_sms, cudaStream_t s);
+int launch_iota(int32_t n, int32_t* a, int num_sms, cudaStream_t s);
+int launch_ldd_setup(const int32_t* order, long long first, int32_t n, int32_t* center, int num_sms, cudaStream_t s);
+int launch_cc_union_label(const int32_t* off, const int32_t* adj, int32_t n, const int32_t* center, int32_t* parent,
+                          int32_t* root, int32_t* mn, int32_t* out, unsigned long long* counters, int* err,
+                          int num_sms, cudaStream_t s, cudaEvent_t* ev);
 int run_mask_fixed(const int32_t* off, const int32_t* adj, int32_t n, const int32_t* sources, int32_t k,
                    unsigned long long* mask, const EngineBuf* b, const EngineOpts& o, EngineRun* out,
                    cudaStream_t st);

@@ -54,7 +54,7 @@ static_assert(kMaxBuckets <= kBlkA, "bucket scan uses one thread per bucket");
 constexpr int kChunk = 16;              // consecutive arcs per thread per step
 constexpr int kStep = kBlkA * kChunk;   // arcs per block step (8192) = partition tile
 constexpr int kRowsCap = 4096;          // row offsets of one step staged in shared memory
-constexpr int kBlkS = 512;                     // split pass (two blocks per SM)
+constexpr int kBlkS = 256;                     // split pass (four blocks per SM)
 constexpr int kSplitTile = kBlkS * 8;           // arcs per split tile
 constexpr int kBlkR = 512;                      // rows pass
 constexpr int kWinArcs = 16384;                 // rows staged in shared memory (64 KB)
@@ -508,7 +508,7 @@ __device__ __forceinline__ SplitLoad split_load(const int32_t* __restrict__ uu, 
     return L;
 }
 
-__global__ void __launch_bounds__(kBlkS, 2) k_bucket_split(const int32_t* __restrict__ uu,
+__global__ void __launch_bounds__(kBlkS, 4) k_bucket_split(const int32_t* __restrict__ uu,
                                                            const uint16_t* __restrict__ lvv,
                                                            const unsigned long long* __restrict__ start,
                                                            const unsigned long long* __restrict__ seg_start,

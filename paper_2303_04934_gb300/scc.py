@@ -29,7 +29,7 @@ SCC_ERR_INTERNAL = -6
 #: every symbol the headers declare (checked by tests/test_abi_symbols.py)
 EXPORTED = [
     "scc_error_string", "scc_config_default", "scc_graph_create", "scc_graph_destroy", "scc_set_config",
-    "scc_run", "reach_multi", "reach_multi_noalloc", "scc_get_stats",
+    "scc_run", "reach_multi", "reach_multi_noalloc", "scc_get_stats", "cc_run", "cc_get_stats",
     "scc_graph_info", "scc_debug_csr", "scc_debug_trim", "scc_debug_pivot_order", "scc_debug_single_reach",
     "scc_debug_multi_reach", "scc_debug_reach_multi_wide", "scc_debug_hashbag", "scc_debug_pair_table", "scc_debug_launch_count",
     "scc_debug_barrier_timeout",
@@ -59,7 +59,18 @@ class scc_stats(ctypes.Structure):
                 ("ms_transpose_rows", ctypes.c_double), ("n_class_trimmed", ctypes.c_int32),
                 ("class_trim_passes", ctypes.c_int32), ("ms_class_trim", ctypes.c_double),
                 ("multi_launches", ctypes.c_int32), ("multi_arcs", ctypes.c_int64), ("multi_items", ctypes.c_int64),
-                ("tau", ctypes.c_int32), ("ms_transpose_split", ctypes.c_double)]
+                ("tau", ctypes.c_int32), ("ms_transpose_split", ctypes.c_double),
+                ("multi_active_sum", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class scc_cc_stats(ctypes.Structure):
+    _fields_ = [("components", ctypes.c_int32), ("clusters", ctypes.c_int32), ("ldd_rounds", ctypes.c_int32),
+                ("ldd_batches", ctypes.c_int32), ("ldd_arcs", ctypes.c_int64), ("cross_arcs", ctypes.c_int64),
+                ("ms_sym", ctypes.c_double), ("ms_ldd", ctypes.c_double), ("ms_union", ctypes.c_double),
+                ("ms_label", ctypes.c_double), ("ms_total", ctypes.c_double)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -137,6 +148,8 @@ def load() -> ctypes.CDLL:
         "reach_multi": ([vp, vp, i32, i32, vp, vp], ctypes.c_int),
         "reach_multi_noalloc": ([vp, vp, i32, i32, vp, vp], ctypes.c_int),
         "scc_get_stats": ([vp, P(scc_stats)], ctypes.c_int),
+        "cc_run": ([vp, vp, vp], ctypes.c_int),
+        "cc_get_stats": ([vp, P(scc_cc_stats)], ctypes.c_int),
         "scc_graph_info": ([vp, P(i32), P(i64), P(i64)], ctypes.c_int),
         "scc_debug_csr": ([vp, i32, vp, vp, vp], ctypes.c_int),
         "scc_debug_trim": ([vp, vp, vp], ctypes.c_int),
@@ -272,6 +285,17 @@ def scc_set_config(h, cfg: scc_config) -> None:
 def scc_run(h, labels_out, stream=None) -> None:
     n = scc_graph_info(h)[0]
     _check(load().scc_run(h, _arr(labels_out, "scc_run labels_out", I32, n), _stream(stream)), "scc_run")
+
+
+def cc_run(h, labels_out, stream=None) -> None:
+    n = scc_graph_info(h)[0]
+    _check(load().cc_run(h, _arr(labels_out, "cc_run labels_out", I32, n), _stream(stream)), "cc_run")
+
+
+def cc_get_stats(h) -> dict:
+    s = scc_cc_stats()
+    _check(load().cc_get_stats(h, ctypes.byref(s)), "cc_get_stats")
+    return s.as_dict()
 
 
 def reach_multi(h, sources, k: int, dir: int, out, stream=None) -> None:

@@ -61,6 +61,7 @@ def test_null_handles_and_bad_arguments_rejected_on_the_host(lib):
     i32, i64, dbl = ctypes.c_int32(), ctypes.c_int64(), ctypes.c_double()
     for name, args in [
         ("scc_get_stats", (None, None)), ("scc_graph_info", (None, None, None, None)),
+        ("cc_run", (None, None, None)), ("cc_get_stats", (None, None)),
         ("reach_multi_noalloc", (None, None, 1, 0, None, None)),
         ("scc_debug_csr", (None, 0, None, None, None)), ("scc_debug_trim", (None, None, None)),
         ("scc_debug_pivot_order", (None, None, ctypes.byref(i32), None)),
