@@ -612,19 +612,20 @@ def _extra_graph(name, scc, torch, stream, steps, warmup, cpu):
         for _ in range(warmup):
             step()
     torch.cuda.synchronize()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
     sts = []
     with torch.cuda.stream(stream):
-        ev0.record(stream)
-        for _ in range(steps):
+        evs[0].record(stream)
+        for i in range(steps):
             sts.append(step())
-        ev1.record(stream)
+            evs[i + 1].record(stream)
     torch.cuda.synchronize()
-    ms = ev0.elapsed_time(ev1) / steps
+    ms = evs[0].elapsed_time(evs[-1]) / steps
+    step_ms = [evs[i].elapsed_time(evs[i + 1]) for i in range(steps)]
     mean = lambda k: sum(st[k] for st in sts) / len(sts)
     out = {"workload": workload_name(spec, g), "n": g.n, "m": g.m, "seed": spec["seed"], "steps": steps,
            "warmup": warmup, "ms_per_step": ms, "edges_per_s": g.m / (ms / 1e3),
-           "create_ms": mean("ms_create"),
+           "create_ms": mean("ms_create"), "step_ms": step_ms,
            "run_ms": {k: mean(k) for k in ("ms_trim", "ms_first_scc", "ms_class_trim", "ms_multi_search", "ms_label")},
            "rounds": sts[-1]["search_rounds"], "batches": sts[-1]["batches"], "tau": sts[-1]["tau"],
            "step": "scc_graph_create + scc_run + scc_graph_destroy, inputs resident in device memory",

@@ -6,8 +6,9 @@ reference leg may import this package. It shares no code with the CUDA path
 
 * :mod:`oracle.scc_oracle` (``scc_oracle.c``, plain C): iterative Tarjan, the
   transpose, trimming, class-restricted single/multi reachability, plain
-  multi-source reachability masks, the seeded pivot order and batch bounds, and
-  connected components of the undirected graph under the arcs (Sec. 5.1).
+  multi-source reachability masks, the seeded pivot order and batch bounds,
+  connected components of the undirected graph under the arcs (Sec. 5.1) and
+  its least-element lists for a vertex order (Sec. 5.2).
 * :mod:`oracle.definition` (numpy): the definitions written out through the
   transitive closure, for tiny graphs -- the pins of the C oracle.
 * :mod:`oracle.invariants` (numpy): properties every correct SCC labelling has.
@@ -63,10 +64,11 @@ def _load():
             lib.or_pivot_order.argtypes = [i64, vp, u64, vp]
             lib.or_batch_bounds.argtypes = [i64, dbl, vp, i64]
             lib.or_cc_labels.argtypes = [i64, vp, vp, vp]
+            lib.or_le_lists.argtypes = [i64, vp, vp, vp, vp, vp, vp, i64]
             lib.or_mix64.argtypes = [u64]
             lib.or_mix64.restype = u64
             for f in ("or_scc_tarjan", "or_transpose", "or_trim", "or_reach_set", "or_multi_reach",
-                      "or_reach_mask", "or_pivot_order", "or_batch_bounds", "or_cc_labels"):
+                      "or_reach_mask", "or_pivot_order", "or_batch_bounds", "or_cc_labels", "or_le_lists"):
                 getattr(lib, f).restype = i64
             _lib = lib
     return _lib
@@ -105,6 +107,26 @@ def cc_labels(n: int, offsets, targets):
     if c < 0:
         raise MemoryError("oracle: union-find allocation failed")
     return lab[:n], int(c)
+
+
+def le_lists(n: int, offsets, targets, order):
+    """Least-element lists (Sec. 5.2) of the undirected graph under the arcs for
+    the vertex order ``order``: returns (le_off int64[n+1], le_src int32[],
+    le_dist int32[]) with L(u) = le_src[le_off[u]:le_off[u+1]] in source order
+    (distances strictly decreasing), by the sequential pruned BFS."""
+    off, po, adj, pa = _csr(offsets, targets)
+    o, pord = _c(order if len(order) else np.zeros(1, np.int32), np.int32)
+    le_off = np.zeros(n + 1, np.int64)
+    cap = 4 * n + 16
+    while True:
+        src = np.empty(max(cap, 1), np.int32)
+        dst = np.empty(max(cap, 1), np.int32)
+        t = _load().or_le_lists(n, po, pa, pord, le_off.ctypes.data, src.ctypes.data, dst.ctypes.data, cap)
+        if t < 0:
+            raise MemoryError("oracle: LE-lists allocation failed")
+        if t <= cap:
+            return le_off, src[:t], dst[:t]
+        cap = t
 
 
 def transpose(n: int, offsets, targets):

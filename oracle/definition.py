@@ -11,6 +11,8 @@ straight from its definition.
 * Connected component label (Sec. 5.1, connectivity on the symmetrised graph):
   ``label[v] = min{u : u and v joined by a path of arcs taken in either
   direction}``.
+* Least-element list (Sec. 5.2, unweighted, undirected graph under the arcs):
+  source ``order[j]`` is in L(v) iff ``d(v, order[j]) < min_{k<j} d(v, order[k])``.
 * Forward reachability pairs (Sec. 2): ``{(v, s) : s in S, s ~> v}``; backward:
   the same on the transpose. Inside a label class (Alg. 1, MultiReach skips an
   arc (u, v) with L(u) != L(v)) the closure is taken over the subgraph whose arcs
@@ -98,3 +100,39 @@ def cc_labels(n: int, edges) -> np.ndarray:
     for v in range(n):
         lab[v] = int(np.flatnonzero(r[:, v])[0])
     return lab
+
+
+def bfs_distances(n: int, edges) -> np.ndarray:
+    """All-pairs hop distances of the undirected graph under the arcs (-1: unreachable)."""
+    a = adjacency(n, edges)
+    a = a | a.T
+    dist = np.full((n, n), -1, np.int64)
+    for s in range(n):
+        dist[s, s] = 0
+        frontier, d = [s], 0
+        while frontier:
+            d += 1
+            nxt = []
+            for u in frontier:
+                for w in np.flatnonzero(a[u]):
+                    if dist[s, w] < 0:
+                        dist[s, w] = d
+                        nxt.append(int(w))
+            frontier = nxt
+    return dist
+
+
+def le_lists(n: int, edges, order):
+    """[[(source, distance), ...] for each v]: order[j] with d(v, order[j])
+    smaller than every earlier source's distance, in source order."""
+    dist = bfs_distances(n, edges)
+    out = []
+    for v in range(n):
+        best, lst = None, []
+        for s in order:
+            d = dist[v, s]
+            if d >= 0 and (best is None or d < best):
+                lst.append((int(s), int(d)))
+                best = d
+        out.append(lst)
+    return out

@@ -27,6 +27,10 @@
  *                      arcs, label = smallest vertex id of the component: what
  *                      the connectivity algorithm of Sec. 5.1 (Alg. 4, LDD-UF-JTB)
  *                      computes, by its plain definition (sequential union-find).
+ *   or_le_lists        least-element lists of the undirected graph under the arcs
+ *                      for a given vertex order (Sec. 5.2): the sequential
+ *                      pruned BFS, one source at a time in order (the batches of
+ *                      Alg. 5 with one source each).
  *
  * Parity pins (tests/test_oracle_*.py): brute-force transitive closure on every
  * digraph with n <= 4 and on random digraphs, closed forms (cycles, chains,
@@ -348,4 +352,111 @@ OR_API int64_t or_cc_labels(int64_t n, const int32_t* off, const int32_t* adj, i
     }
     free(parent);
     return comps;
+}
+
+/* ---------------------------------------------------- least-element lists ---- */
+/*
+ * LE-lists (Sec. 5.2) of the undirected graph in which every arc (u, v) joins u
+ * and v, for the vertex order order[0..n): source order[j] is in L(u) iff its
+ * BFS distance d to u is smaller than the distance from u to every earlier
+ * source. Sources are taken one at a time in order; a BFS from s expands a
+ * vertex u first reached at distance d only if d < delta(u) (the smallest
+ * distance from u to an earlier source), and then appends (s, d) to L(u) and
+ * sets delta(u) = d -- Alg. 5 with batches of one source. Each list is in
+ * source order, so its distances strictly decrease.
+ * Output in CSR form: le_off[n + 1], entries le_src / le_dist (cap of them).
+ * Returns the number of entries (written only if it is at most cap), or -1 if
+ * memory could not be allocated.
+ */
+OR_API int64_t or_le_lists(int64_t n, const int32_t* off, const int32_t* adj, const int32_t* order, int64_t* le_off,
+                           int32_t* le_src, int32_t* le_dist, int64_t cap) {
+    if (n == 0) {
+        le_off[0] = 0;
+        return 0;
+    }
+    int64_t m = off[n];
+    /* symmetric adjacency: out-arcs and in-arcs of every vertex */
+    int64_t* so = (int64_t*)calloc((size_t)n + 1, sizeof(int64_t));
+    int32_t* sa = (int32_t*)malloc(sizeof(int32_t) * (size_t)(2 * m > 0 ? 2 * m : 1));
+    int64_t* fill = (int64_t*)malloc(sizeof(int64_t) * (size_t)n);
+    int32_t* delta = (int32_t*)malloc(sizeof(int32_t) * (size_t)n);
+    int32_t* dist = (int32_t*)malloc(sizeof(int32_t) * (size_t)n);
+    int64_t* stamp = (int64_t*)malloc(sizeof(int64_t) * (size_t)n);
+    int32_t* queue = (int32_t*)malloc(sizeof(int32_t) * (size_t)n);
+    int64_t tcap = 4 * n + 16, tn = 0;
+    int32_t* tu = (int32_t*)malloc(sizeof(int32_t) * (size_t)tcap);
+    int32_t* ts = (int32_t*)malloc(sizeof(int32_t) * (size_t)tcap);
+    int32_t* td = (int32_t*)malloc(sizeof(int32_t) * (size_t)tcap);
+    int64_t ret = -1;
+    if (!so || !sa || !fill || !delta || !dist || !stamp || !queue || !tu || !ts || !td) goto done;
+    for (int64_t u = 0; u < n; ++u)
+        for (int64_t e = off[u]; e < off[u + 1]; ++e) {
+            ++so[u + 1];
+            ++so[adj[e] + 1];
+        }
+    for (int64_t u = 0; u < n; ++u) so[u + 1] += so[u];
+    for (int64_t u = 0; u < n; ++u) fill[u] = so[u];
+    for (int64_t u = 0; u < n; ++u)
+        for (int64_t e = off[u]; e < off[u + 1]; ++e) {
+            sa[fill[u]++] = adj[e];
+            sa[fill[adj[e]]++] = (int32_t)u;
+        }
+    for (int64_t u = 0; u < n; ++u) {
+        delta[u] = INT32_MAX;
+        stamp[u] = -1;
+    }
+    for (int64_t j = 0; j < n; ++j) {
+        int32_t s = order[j];
+        int64_t qh = 0, qt = 0;
+        queue[qt++] = s;
+        stamp[s] = j;
+        dist[s] = 0;
+        while (qh < qt) {
+            int32_t u = queue[qh++];
+            int32_t d = dist[u];
+            if (d >= delta[u]) continue; /* an earlier source is as close: pruned */
+            delta[u] = d;
+            if (tn == tcap) {
+                int64_t nc = 2 * tcap;
+                int32_t* a = (int32_t*)realloc(tu, sizeof(int32_t) * (size_t)nc);
+                if (!a) goto done;
+                tu = a;
+                a = (int32_t*)realloc(ts, sizeof(int32_t) * (size_t)nc);
+                if (!a) goto done;
+                ts = a;
+                a = (int32_t*)realloc(td, sizeof(int32_t) * (size_t)nc);
+                if (!a) goto done;
+                td = a;
+                tcap = nc;
+            }
+            tu[tn] = u;
+            ts[tn] = s;
+            td[tn] = d;
+            ++tn;
+            for (int64_t e = so[u]; e < so[u + 1]; ++e) {
+                int32_t w = sa[e];
+                if (stamp[w] == j) continue;
+                stamp[w] = j;
+                dist[w] = d + 1;
+                queue[qt++] = w;
+            }
+        }
+    }
+    ret = tn;
+    if (tn <= cap) {
+        /* group by vertex, keeping the order in which entries were found */
+        for (int64_t u = 0; u <= n; ++u) le_off[u] = 0;
+        for (int64_t i = 0; i < tn; ++i) ++le_off[tu[i] + 1];
+        for (int64_t u = 0; u < n; ++u) le_off[u + 1] += le_off[u];
+        for (int64_t u = 0; u < n; ++u) fill[u] = le_off[u];
+        for (int64_t i = 0; i < tn; ++i) {
+            int64_t p = fill[tu[i]]++;
+            le_src[p] = ts[i];
+            le_dist[p] = td[i];
+        }
+    }
+done:
+    free(so); free(sa); free(fill); free(delta); free(dist); free(stamp); free(queue);
+    free(tu); free(ts); free(td);
+    return ret;
 }

@@ -80,7 +80,8 @@ def test_medium_graphs(make):
 
 @pytest.mark.parametrize("kw", [dict(tau=1), dict(tau=16, seeds=1), dict(tau=4096), dict(beta=2.0),
                                 dict(beta=1.1), dict(lam=1024, sigma=8), dict(seed=12345), dict(seeds=4),
-                                dict(dense=0), dict(dense=3), dict(dense=200)])
+                                dict(dense=0), dict(dense=3), dict(dense=200), dict(sigma=0),
+                                dict(sigma=0, lam=1024, tau=16)])
 def test_configuration_does_not_change_labels(kw):
     # the R-MAT graph with edge factor 16 takes the dense path (average degree >= 8)
     for g in (gg.torus(2, 64, 0.5, seed=31), gg.rmat(13, 8, seed=32), gg.knn(20000, 5, seed=33),
