@@ -265,6 +265,43 @@ typedef struct scc_cc_stats {
 
 SCC_API int cc_get_stats(scc_handle h, scc_cc_stats* out);
 
+/* --------------------------------------------------- least-element lists ---- */
+/*
+ * Least-element lists (Sec. 5.2, Alg. 5: the BGSS LE-lists algorithm with the
+ * frontier of each level kept packed and a hash table of visited
+ * (vertex, source) pairs) of the undirected graph under the arcs of h,
+ * unweighted: for the vertex order order[0..n) (the seeded permutation of h's
+ * pivot seed over all vertices), source order[j] is in L(v) iff its hop
+ * distance to v is smaller than the distance from v to every earlier source.
+ * L(v) lists those sources in order; their distances strictly decrease and
+ * the last entry is v itself at distance 0.
+ * le_lists_run computes the lists and keeps them with the handle (replacing
+ * earlier ones); *total (host) receives the number of entries. The first call
+ * on h builds the symmetric CSR that cc_run also uses. Synchronises `stream`.
+ */
+SCC_API int le_lists_run(scc_handle h, int64_t* total, void* stream);
+/*
+ * Copies the lists of the last le_lists_run out:
+ *   order            host or device int32[n]: the vertex order used.
+ *   le_off           host or device int64[n + 1]: L(v) = entries le_off[v] .. le_off[v+1] - 1.
+ *   le_src, le_dist  host or device int32[total]: each entry's source and distance.
+ * SCC_ERR_INVALID_ARG if no lists were computed. Synchronises `stream`.
+ */
+SCC_API int le_lists_get(scc_handle h, int32_t* order, int64_t* le_off, int32_t* le_src, int32_t* le_dist,
+                         void* stream);
+
+/* Counters of the last le_lists_run on h. */
+typedef struct scc_le_stats {
+    int64_t entries;     /* entries of all lists */
+    int64_t candidates;  /* (vertex, source) pairs found before the per-vertex filter */
+    int64_t arcs;        /* arcs examined by the multi-source BFS */
+    int32_t levels;      /* BFS levels run, all batches */
+    int32_t launches;    /* cooperative launches (more than one when a buffer had to grow) */
+    double ms_total;
+} scc_le_stats;
+
+SCC_API int le_get_stats(scc_handle h, scc_le_stats* out);
+
 #ifdef __cplusplus
 }
 #endif

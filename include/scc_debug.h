@@ -120,6 +120,15 @@ SCC_API int64_t scc_debug_launch_count(void);
  */
 SCC_API int scc_debug_barrier_timeout(int32_t absent_block, int64_t limit_ns, int32_t* n_arrived, void* stream);
 
+/*
+ * le_lists_run (scc.h; Sec. 5.2, Alg. 5) starting from a visited-pair table of
+ * init_cap slots (rounded up to a power of two, at least 1024) and a candidate
+ * log of init_log entries instead of the sizes taken from n, so that tests can
+ * make both grow (a batch that overflows either is run again after the buffer
+ * doubles). The lists are kept with the handle as by le_lists_run.
+ */
+SCC_API int scc_debug_le_lists(scc_handle h, int64_t init_cap, int64_t init_log, int64_t* total, void* stream);
+
 /* Batched SCC (scc_batch.h): for every graph g of the last scc_batch_run,
    out[11g .. 11g + 5] = device globaltimer (ns) at its start and at the end of
    the transpose, the first SCC, the class trimming, the batches and the
@@ -164,11 +173,13 @@ SCC_API int scc_debug_serve_admission(int32_t count, const int64_t* need, const 
  * number: a reachability query with every later query on the same graph and
  * direction while the sources stay within 128 (merge_reach != 0; otherwise
  * request 0 alone); a small SCC request with the next small ones, batch_graphs
- * at most; a larger SCC request alone. count = 0 gives an empty unit.
+ * at most, when at least batch_min small SCC requests are admitted (with fewer,
+ * request 0 alone, for the full-GPU path); a larger SCC request alone.
+ * count = 0 gives an empty unit.
  */
 SCC_API int scc_debug_serve_unit(int32_t count, const int32_t* kind, const int32_t* small, const int32_t* graph,
                                  const int32_t* dir, const int32_t* nsrc, int32_t merge_reach, int32_t batch_graphs,
-                                 int32_t* unit, int32_t* nunit);
+                                 int32_t batch_min, int32_t* unit, int32_t* nunit);
 
 #ifdef __cplusplus
 }

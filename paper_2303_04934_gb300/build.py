@@ -20,7 +20,7 @@ OUT_DIR = os.path.join(HERE, "_lib")
 SO_NAME = "libscc_gb300.so"
 SO_PATH = os.path.join(OUT_DIR, SO_NAME)
 SOURCES = ["api.cu", "steps.cu", "search.cu", "transpose.cu", "bgss.cu", "noalloc.cu", "batch.cu", "serve.cu",
-           "cc.cu"]
+           "cc.cu", "lelists.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -58,6 +58,13 @@ struct scc_graph {
     int32_t* soff = nullptr;
     int32_t* sadj = nullptr;
     scc_cc_stats cc_stats;
+    // least-element lists of the last le_lists_run
+    int32_t* le_order = nullptr;
+    int64_t* le_off = nullptr;
+    int32_t* le_src = nullptr;
+    int32_t* le_dist = nullptr;
+    long long le_total = -1;  // -1: none computed
+    scc_le_stats le_stats;
 };
 
 namespace scc {
@@ -552,6 +559,10 @@ static void graph_free(scc_graph* h, cudaStream_t s) {
     engine_release(&h->eb64, s);
     dfree(h->soff, s);
     dfree(h->sadj, s);
+    dfree(h->le_order, s);
+    dfree(h->le_off, s);
+    dfree(h->le_src, s);
+    dfree(h->le_dist, s);
 }
 
 int scc_graph_create(int32_t n, int64_t m, const int32_t* offsets, const int32_t* targets, void* stream,
@@ -895,6 +906,28 @@ int reach_multi_noalloc(scc_handle h, const int32_t* sources, int32_t k, int32_t
 // Alg. 4 LDD-UF-JTB with VGC and the hash bag; steps in cc.cu).
 static constexpr double kLddBeta = 1.2;  // batch growth of the decomposition (Sec. 5.1)
 
+// The symmetric CSR of h (row v = row v of G, then row v of G^T), built on the
+// first call and kept with the handle.
+static int ensure_sym(scc_graph* h, cudaStream_t s) {
+    if (h->soff) return SCC_OK;
+    const int32_t n = h->n;
+    int32_t *so = nullptr, *sa = nullptr;
+    SCC_TRY(dalloc_t(&so, (size_t)n + 1, s));
+    if (dalloc_t(&sa, (size_t)std::max<int64_t>(2 * h->mt, 1), s) != SCC_OK) {
+        dfree(so, s);
+        return SCC_ERR_OOM;
+    }
+    const int rc = launch_sym_csr(h->off, h->adj, h->toff, h->tadj, n, so, sa, h->di.num_sms, s);
+    if (rc != SCC_OK) {
+        dfree(so, s);
+        dfree(sa, s);
+        return rc;
+    }
+    h->soff = so;
+    h->sadj = sa;
+    return SCC_OK;
+}
+
 static int cc_run_impl(scc_graph* h, int32_t* labels_out, cudaStream_t s) {
     const int32_t n = h->n;
     scc_cc_stats& st = h->cc_stats;
@@ -906,17 +939,7 @@ static int cc_run_impl(scc_graph* h, int32_t* labels_out, cudaStream_t s) {
     EvTimer t(s);
     // the symmetric CSR, kept with the handle
     t.start();
-    if (!h->soff) {
-        int32_t *so = nullptr, *sa = nullptr;
-        SCC_TRY(dalloc_t(&so, (size_t)n + 1, s));
-        if (dalloc_t(&sa, (size_t)std::max<int64_t>(2 * h->mt, 1), s) != SCC_OK) {
-            dfree(so, s);
-            return SCC_ERR_OOM;
-        }
-        h->soff = so;
-        h->sadj = sa;
-        SCC_TRY(launch_sym_csr(h->off, h->adj, h->toff, h->tadj, n, h->soff, h->sadj, num_sms, s));
-    }
+    SCC_TRY(ensure_sym(h, s));
     st.ms_sym = t.stop();
     // the seeded order of all vertices and its batches
     Scratch tmp(s);
@@ -960,11 +983,20 @@ static int cc_run_impl(scc_graph* h, int32_t* labels_out, cudaStream_t s) {
     t.start();
     SCC_TRY(launch_iota(n, root, num_sms, s));  // the identity list, permuted into the order
     SCC_TRY(launch_pivot_order(root, (int64_t)n, h->cfg.seed, order, s));
-    SCC_TRY(launch_ldd_setup(order, bounds[1], n, center, num_sms, s));
+    // the visited bitmap and the two frontier bitmaps of the bottom-up rounds
+    const size_t nw = ((size_t)n + 31) / 32;
+    uint32_t *vbits = nullptr, *fbits = nullptr;
+    SCC_TRY(tmp.alloc(&vbits, nw));
+    SCC_TRY(tmp.alloc(&fbits, 2 * nw));
+    SCC_CUDA(cudaMemsetAsync(fbits, 0, sizeof(uint32_t) * 2 * nw, s));
+    SCC_TRY(launch_ldd_setup(order, bounds[1], n, center, vbits, num_sms, s));
     SCC_TRY(engine_reserve(&h->eb32, 4, (long long)n + 1024, h->cfg.lambda, 2 * h->mt, num_sms, s));
     EngineOpts o = opts_of(h);
     EngineRun r;
-    SCC_TRY(run_ldd(h->soff, h->sadj, n, order, bounds_d, bounds[1], nb, center, &h->eb32, o, &r, s));
+    // bottom-up rounds when the frontier is large, as for the first SCC's searches
+    const int frac_inv = h->cfg.dense == 1 ? 20 : h->cfg.dense;
+    SCC_TRY(run_ldd(h->soff, h->sadj, n, order, bounds_d, bounds[1], nb, center, vbits, fbits, frac_inv, &h->eb32, o,
+                    &r, s));
     st.ms_ldd = t.stop();
     st.ldd_rounds = r.rounds;
     st.ldd_batches = nb;
@@ -972,8 +1004,13 @@ static int cc_run_impl(scc_graph* h, int32_t* labels_out, cudaStream_t s) {
     // ---- union-find over the cross arcs (Alg. 4 Union), then the labels
     CreateEvents ev;
     cudaEventRecord(ev.e[0], s);
-    SCC_TRY(launch_cc_union_label(h->off, h->adj, n, center, parent, root, mn, out, counters, err, num_sms, s,
-                                  &ev.e[1]));
+    const long long big_cap = (long long)(h->mt / 2048) + 1;
+    int32_t* big = nullptr;
+    long long* bpre = nullptr;
+    SCC_TRY(tmp.alloc(&big, (size_t)big_cap));
+    SCC_TRY(tmp.alloc(&bpre, (size_t)big_cap + 1));
+    SCC_TRY(launch_cc_union_label(h->off, h->adj, n, center, parent, root, mn, out, counters, big, bpre, big_cap, err,
+                                  num_sms, s, &ev.e[1]));
     if (!dev_out) SCC_TRY(from_device(labels_out, out, sizeof(int32_t) * (size_t)n, s));
     unsigned long long hc[4];
     int herr = 0;
@@ -1000,6 +1037,95 @@ int cc_run(scc_handle h, int32_t* labels_out, void* stream) {
 int cc_get_stats(scc_handle h, scc_cc_stats* out) {
     if (!h || !out) return SCC_ERR_INVALID_ARG;
     *out = h->cc_stats;
+    return SCC_OK;
+}
+
+// ---------------------------------------------------- least-element lists --
+// LE-lists (Sec. 5.2, Alg. 5) of the undirected graph under G's arcs for the
+// handle's seeded vertex order (steps in lelists.cu).
+static int le_lists_impl(scc_graph* h, int64_t* total, cudaStream_t s, long long init_cap = 0,
+                         long long init_log = 0) {
+    const int32_t n = h->n;
+    scc_le_stats& st = h->le_stats;
+    memset(&st, 0, sizeof(st));
+    dfree(h->le_off, s);
+    dfree(h->le_src, s);
+    dfree(h->le_dist, s);
+    h->le_off = nullptr;
+    h->le_src = h->le_dist = nullptr;
+    h->le_total = -1;
+    EvTimer t(s);
+    t.start();
+    SCC_TRY(ensure_sym(h, s));
+    if (!h->le_order) SCC_TRY(dalloc_t(&h->le_order, (size_t)std::max(n, 1), s));
+    if (n > 0) {
+        Scratch tmp(s);
+        int32_t* iota = nullptr;
+        SCC_TRY(tmp.alloc(&iota, (size_t)n));
+        SCC_TRY(launch_iota(n, iota, h->di.num_sms, s));
+        SCC_TRY(launch_pivot_order(iota, (int64_t)n, h->cfg.seed, h->le_order, s));
+    }
+    LeResult r;
+    const int rc = le_lists_compute(h->soff, h->sadj, n, h->le_order, h->di.num_sms, &r, s, init_cap, init_log);
+    if (rc != SCC_OK) {
+        dfree(r.off, s);
+        dfree(r.src, s);
+        dfree(r.dist, s);
+        return rc;
+    }
+    h->le_off = r.off;
+    h->le_src = r.src;
+    h->le_dist = r.dist;
+    h->le_total = r.total;
+    st.entries = r.total;
+    st.candidates = r.candidates;
+    st.levels = r.levels;
+    st.launches = r.launches;
+    st.arcs = r.edges;
+    st.ms_total = t.stop();
+    *total = r.total;
+    return SCC_OK;
+}
+
+int le_lists_run(scc_handle h, int64_t* total, void* stream) {
+    if (!h || !total) return SCC_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    h->last = s;
+    *total = 0;
+    return le_lists_impl(h, total, s);
+}
+
+int le_lists_get(scc_handle h, int32_t* order, int64_t* le_off, int32_t* le_src, int32_t* le_dist, void* stream) {
+    if (!h || h->le_total < 0) return SCC_ERR_INVALID_ARG;
+    if ((h->n > 0 && (!order || !le_off)) || (h->le_total > 0 && (!le_src || !le_dist))) return SCC_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int32_t n = h->n;
+    if (n > 0) {
+        SCC_CUDA(cudaMemcpyAsync(order, h->le_order, sizeof(int32_t) * (size_t)n, cudaMemcpyDefault, s));
+        SCC_CUDA(cudaMemcpyAsync(le_off, h->le_off, sizeof(int64_t) * ((size_t)n + 1), cudaMemcpyDefault, s));
+    } else if (le_off) {
+        const int64_t z = 0;
+        SCC_CUDA(cudaMemcpyAsync(le_off, &z, sizeof(z), cudaMemcpyDefault, s));
+    }
+    if (h->le_total > 0) {
+        SCC_CUDA(cudaMemcpyAsync(le_src, h->le_src, sizeof(int32_t) * (size_t)h->le_total, cudaMemcpyDefault, s));
+        SCC_CUDA(cudaMemcpyAsync(le_dist, h->le_dist, sizeof(int32_t) * (size_t)h->le_total, cudaMemcpyDefault, s));
+    }
+    SCC_CUDA(cudaStreamSynchronize(s));
+    return SCC_OK;
+}
+
+int scc_debug_le_lists(scc_handle h, int64_t init_cap, int64_t init_log, int64_t* total, void* stream) {
+    if (!h || !total || init_cap < 1 || init_log < 1) return SCC_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    h->last = s;
+    *total = 0;
+    return le_lists_impl(h, total, s, init_cap, init_log);
+}
+
+int le_get_stats(scc_handle h, scc_le_stats* out) {
+    if (!h || !out) return SCC_ERR_INVALID_ARG;
+    *out = h->le_stats;
     return SCC_OK;
 }
 

@@ -565,25 +565,30 @@ __device__ bool engine_search(const EngineParams<typename Pol::Item>& P, Pol& po
             if constexpr (Pol::kDense) {
                 // ---- dense round: frontier bitmap, then bottom-up over unvisited
                 // vertices. After a dense round the bitmap is ready (that round
-                // wrote its new vertices into it, and into no bag); after a
-                // sparse one it is built from the input bag (read and reset)
-                // and last round's hubs.
+                // wrote the vertices it found into it); the input bag (read and
+                // reset) adds what the last round pushed: all of its items after
+                // a sparse round, the sources a policy added after a dense one;
+                // after a sparse round last round's hubs are added too.
                 uint32_t* fb = dp->fbits[par];
                 uint32_t* nfb = dp->fbits[ipar];  // the next round's frontier (cleared above)
-                if (!prev_dense) {
-                    for (long long j = gtid; j < in_end; j += gstride) {
-                        const Item x = in_slots[j];
-                        if (x == Sent<Item>::empty) continue;
-                        in_slots[j] = Sent<Item>::empty;
-                        if (x == Sent<Item>::claimed) continue;
-                        const int v = pol.vertex(x);
-                        atomicOr(&fb[v >> 5], 1u << (v & 31));
-                    }
+                for (long long j = gtid; j < in_end; j += gstride) {
+                    const Item x = in_slots[j];
+                    if (x == Sent<Item>::empty) continue;
+                    in_slots[j] = Sent<Item>::empty;
+                    if (x == Sent<Item>::claimed) continue;
+                    const int v = pol.vertex(x);
+                    atomicOr(&fb[v >> 5], 1u << (v & 31));
+                }
+                if (!prev_dense)
                     for (long long j = gtid; j < fr_hubs; j += gstride) {
                         const int v = pol.vertex(P.hub_item[ipar][j]);
                         atomicOr(&fb[v >> 5], 1u << (v & 31));
                     }
-                }
+                // sources added by the policy go into this round's bag (the next
+                // round's input, as in a sparse round); they are visited before
+                // the bottom-up below reads the visited words, so it leaves them
+                // alone and its stores of whole words keep their bits
+                if constexpr (Pol::kInject) pol.inject(i, out, st, wid, nwarps, gr, pushed);
                 if (!S::sync(&ctl->bar, &ctl->err)) return false;
                 const long long nw = ((long long)P.n + 31) / 32;
                 // each warp takes 32 consecutive words at a time (one coalesced
@@ -651,14 +656,19 @@ __device__ bool engine_search(const EngineParams<typename Pol::Item>& P, Pol& po
 #pragma unroll
                         for (int k = 0; k < kDV; ++k) {
                             bool f = false;
+                            int par_u = -1;
 #pragma unroll
                             for (int a = 0; a < 2; ++a)
                                 if (!f && u[k][a] >= 0) {
                                     ++scanned;
                                     f = (fw[k][a] >> (u[k][a] & 31)) & 1u;
+                                    if (f) par_u = u[k][a];
                                 }
                             e[k] += 2;
-                            if (f) atomicOr(&s_found[(vv[k] >> 5) - w0], 1u << (vv[k] & 31));
+                            if (f) {
+                                atomicOr(&s_found[(vv[k] >> 5) - w0], 1u << (vv[k] & 31));
+                                pol.adopt(vv[k], par_u);  // the vertex takes what its frontier neighbour carries
+                            }
                             if (f || e[k] >= e1[k]) vv[k] = -1;
                         }
                     }
@@ -892,6 +902,7 @@ struct PolSingle {
         child = (Item)w;
         return (atomicOr(&bits[w >> 5], b) & b) == 0;
     }
+    __device__ __forceinline__ void adopt(int, int) const {}
 };
 
 // Forward and backward single-reachability from the same source in one search
@@ -1125,13 +1136,15 @@ struct PolLdd {
     using Item = uint32_t;
     static constexpr int kQueue = 256;
     static constexpr bool kCountInserts = false;
-    static constexpr bool kDense = false;
+    static constexpr bool kDense = true;
     static constexpr bool kCtxInQueue = true;
     using Ctx = uint64_t;  // the centre of the item's cluster
     static constexpr bool kTwoGraphs = false;
     static constexpr bool kInject = true;
     static constexpr const char* kName = "ldd";
     int32_t* center;          // -1: not yet claimed
+    uint32_t* bits;           // claimed vertices (bits past n set), for dense rounds
+    const int32_t* off;       // the symmetric CSR's offsets
     const int32_t* order;     // seeded order of all vertices
     const long long* bounds;  // batch i = order[bounds[i] .. bounds[i + 1])
     int nbatches;
@@ -1139,14 +1152,24 @@ struct PolLdd {
     __device__ __forceinline__ uint64_t ctx(Item it) const { return (uint64_t)(uint32_t)ld_volatile(&center[it]); }
     __device__ __forceinline__ int32_t load_ctx(Item it) const { return ld_volatile(&center[it]); }
     __device__ __forceinline__ bool seed(Item) const { return true; }  // items are claimed when pushed
-    __device__ __forceinline__ bool visit(Item, uint64_t c, int w, Item& child) const {
-        if (ld_volatile(&center[w]) >= 0) return false;
-        child = (Item)w;
-        return atomicCAS(&center[w], -1, (int32_t)(uint32_t)c) == -1;
+    // a claim is the CAS on the centre; its winner also marks the vertex visited
+    __device__ __forceinline__ bool claim(int w, int32_t c) const {
+        if (ld_volatile(&center[w]) >= 0 || atomicCAS(&center[w], -1, c) != -1) return false;
+        atomicOr(&bits[w >> 5], 1u << (w & 31));
+        return true;
     }
+    __device__ __forceinline__ bool visit(Item, uint64_t c, int w, Item& child) const {
+        child = (Item)w;
+        return claim(w, (int32_t)(uint32_t)c);
+    }
+    // dense rounds (the graph is symmetric: a vertex's in-arcs are its arcs):
+    // an unvisited vertex with a neighbour in the frontier joins that
+    // neighbour's cluster, whose centre was settled in an earlier round
+    __device__ __forceinline__ void adopt(int v, int u) const { center[v] = ld_volatile(&center[u]); }
     __device__ __forceinline__ bool more(uint32_t i) const { return (long long)i + 2 < (long long)nbatches; }
     // warp-collective: the unvisited vertices of batch i + 1 claim themselves
-    // and go into this round's bag
+    // and go into this round's bag (an isolated one is a cluster of its own
+    // with nothing to expand: it is claimed but not pushed)
     __device__ __forceinline__ void inject(uint32_t i, const BagRef<Item>& out, SegState& st, uint32_t wid,
                                            uint32_t nwarps, uint32_t round, unsigned long long& pushed) const {
         if ((long long)i + 1 >= (long long)nbatches) return;
@@ -1155,8 +1178,8 @@ struct PolLdd {
         for (long long p = p0 + (long long)wid * 32; p < p1; p += (long long)nwarps * 32) {
             const long long q = p + lane;
             const int v = q < p1 ? order[q] : -1;
-            const bool claim = v >= 0 && ld_volatile(&center[v]) < 0 && atomicCAS(&center[v], -1, v) == -1;
-            pushed += bag_push<Item>(out, st, claim, (Item)(claim ? v : 0), wid, round);
+            const bool push = v >= 0 && claim(v, v) && off[v + 1] > off[v];
+            pushed += bag_push<Item>(out, st, push, (Item)(push ? v : 0), wid, round);
         }
     }
 };

@@ -55,9 +55,15 @@ class Scratch {
     template <class T>
     int alloc(T** p, size_t count) {
         *p = nullptr;
-        if (n_ == kMax) return SCC_ERR_INTERNAL;
+        int slot = -1;  // a slot freed by release or keep, else a new one
+        for (int i = 0; i < n_ && slot < 0; ++i)
+            if (!p_[i]) slot = i;
+        if (slot < 0) {
+            if (n_ == kMax) return SCC_ERR_INTERNAL;
+            slot = n_++;
+        }
         const int rc = dalloc_t(p, count, s_);
-        if (rc == SCC_OK) p_[n_++] = *p;
+        if (rc == SCC_OK) p_[slot] = *p;
         return rc;
     }
     void release(const void* p) {
@@ -73,7 +79,7 @@ class Scratch {
     }
 
   private:
-    static constexpr int kMax = 32;
+    static constexpr int kMax = 48;
     cudaStream_t s_;
     void* p_[kMax] = {};
     int n_ = 0;
@@ -370,11 +376,14 @@ int batch_runner_enqueue(BatchRunner* r, int32_t G, const long long* vbase, cons
 // Mask reachability on fixed buffers (no allocation, no events).
 // Low-diameter decomposition (Sec. 5.1, Alg. 4) on the symmetric CSR: batch i
 // of the seeded order is order[bounds_d[i] .. bounds_d[i + 1]) (nbatches
-// batches; the first, of `first` vertices, already centres itself in
-// center[]); on return center[v] is the centre of v's cluster.
+// batches; the first, of `first` vertices, already centres itself in center[]
+// and in the visited bitmap `bits`, whose bits past n are set); on return
+// center[v] is the centre of v's cluster. fbits: two zeroed frontier bitmaps
+// of ceil(n / 32) words (zero again on return); a round whose frontier holds
+// n / frac_inv vertices or more runs bottom-up (frac_inv = 0: never).
 int run_ldd(const int32_t* soff, const int32_t* sadj, int32_t n, const int32_t* order, const long long* bounds_d,
-            long long first, int nbatches, int32_t* center, EngineBuf* b, const EngineOpts& o, EngineRun* out,
-            cudaStream_t st);
+            long long first, int nbatches, int32_t* center, uint32_t* bits, uint32_t* fbits, int frac_inv,
+            EngineBuf* b, const EngineOpts& o, EngineRun* out, cudaStream_t st);
 // Connectivity steps (cc.cu): the symmetric CSR (soff[v] = off[v] + toff[v],
 // row v = row v of G then row v of G^T); center[] = -1 with the first `first`
 // vertices of order centring themselves; then union-find over the arcs of G
@@ -385,10 +394,29 @@ int run_ldd(const int32_t* soff, const int32_t* sadj, int32_t n, const int32_t* 
 int launch_sym_csr(const int32_t* off, const int32_t* adj, const int32_t* toff, const int32_t* tadj, int32_t n,
                    int32_t* soff, int32_t* sadj, int num_sms, cudaStream_t s);
 int launch_iota(int32_t n, int32_t* a, int num_sms, cudaStream_t s);
-int launch_ldd_setup(const int32_t* order, long long first, int32_t n, int32_t* center, int num_sms, cudaStream_t s);
+int launch_ldd_setup(const int32_t* order, long long first, int32_t n, int32_t* center, uint32_t* bits, int num_sms,
+                     cudaStream_t s);
+// counters: [0] cross arcs [1] clusters [2] components [3] rows spread over the
+// grid (big: big_cap >= m / 2048 + 1 entries, bpre: big_cap + 1)
 int launch_cc_union_label(const int32_t* off, const int32_t* adj, int32_t n, const int32_t* center, int32_t* parent,
-                          int32_t* root, int32_t* mn, int32_t* out, unsigned long long* counters, int* err,
-                          int num_sms, cudaStream_t s, cudaEvent_t* ev);
+                          int32_t* root, int32_t* mn, int32_t* out, unsigned long long* counters, int32_t* big,
+                          long long* bpre, long long big_cap, int* err, int num_sms, cudaStream_t s,
+                          cudaEvent_t* ev);
+// Least-element lists (lelists.cu, Sec. 5.2 Alg. 5) of the symmetric CSR for
+// the vertex order `order`: on success res->off (int64[n+1]), res->src and
+// res->dist (int32[total]) are device allocations the caller frees (dfree);
+// candidates = pairs logged before the per-vertex filter.
+struct LeResult {
+    int64_t* off = nullptr;
+    int32_t* src = nullptr;
+    int32_t* dist = nullptr;
+    long long total = 0, candidates = 0, edges = 0;
+    int levels = 0, launches = 0;
+};
+// init_cap / init_log > 0: the first table capacity and log length (tests of
+// the growth path); 0: sized from n.
+int le_lists_compute(const int32_t* soff, const int32_t* sadj, int32_t n, const int32_t* order, int num_sms,
+                     LeResult* res, cudaStream_t s, long long init_cap = 0, long long init_log = 0);
 int run_mask_fixed(const int32_t* off, const int32_t* adj, int32_t n, const int32_t* sources, int32_t k,
                    unsigned long long* mask, const EngineBuf* b, const EngineOpts& o, EngineRun* out,
                    cudaStream_t st);

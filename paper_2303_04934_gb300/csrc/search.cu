@@ -223,17 +223,22 @@ int run_single_both(const int32_t* off, const int32_t* adj, const int32_t* toff,
 }
 
 int run_ldd(const int32_t* soff, const int32_t* sadj, int32_t n, const int32_t* order, const long long* bounds_d,
-            long long first, int nbatches, int32_t* center, EngineBuf* b, const EngineOpts& o, EngineRun* out,
-            cudaStream_t st) {
+            long long first, int nbatches, int32_t* center, uint32_t* bits, uint32_t* fbits, int frac_inv,
+            EngineBuf* b, const EngineOpts& o, EngineRun* out, cudaStream_t st) {
     auto P = make_engine_params<uint32_t>(soff, sadj, n, b, o);
     P.init = reinterpret_cast<const uint32_t*>(order);  // the first batch, claimed before the launch
     P.ninit = first;
     PolLdd pol;
     pol.center = center;
+    pol.bits = bits;
+    pol.off = soff;
     pol.order = order;
     pol.bounds = bounds_d;
     pol.nbatches = nbatches;
-    int rc = launch_engine(P, pol, o, out, st);
+    // the graph is symmetric: it is its own reverse for the bottom-up rounds
+    const long long nw = ((long long)n + 31) / 32;
+    DenseParams dp{soff, sadj, {fbits, fbits + nw}, (long long)n, frac_inv};
+    int rc = launch_engine(P, pol, o, out, st, dp);
     if (rc != SCC_OK || out->err) SCC_TRY(engine_reset_slots(b, st));
     SCC_TRY(rc);
     return out->err ? out->err : SCC_OK;

@@ -30,9 +30,10 @@ SCC_ERR_INTERNAL = -6
 EXPORTED = [
     "scc_error_string", "scc_config_default", "scc_graph_create", "scc_graph_destroy", "scc_set_config",
     "scc_run", "reach_multi", "reach_multi_noalloc", "scc_get_stats", "cc_run", "cc_get_stats",
+    "le_lists_run", "le_lists_get", "le_get_stats",
     "scc_graph_info", "scc_debug_csr", "scc_debug_trim", "scc_debug_pivot_order", "scc_debug_single_reach",
     "scc_debug_multi_reach", "scc_debug_reach_multi_wide", "scc_debug_hashbag", "scc_debug_pair_table", "scc_debug_launch_count",
-    "scc_debug_barrier_timeout",
+    "scc_debug_barrier_timeout", "scc_debug_le_lists",
     "scc_batch_config_default", "scc_batch_create", "scc_batch_destroy", "scc_batch_set_config",
     "scc_batch_get_config", "scc_batch_run", "scc_batch_autotune", "scc_batch_get_stats",
     "scc_debug_batch_times", "scc_debug_batch_groups", "scc_debug_serve_admission", "scc_debug_serve_unit",
@@ -76,6 +77,14 @@ class scc_cc_stats(ctypes.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+class scc_le_stats(ctypes.Structure):
+    _fields_ = [("entries", ctypes.c_int64), ("candidates", ctypes.c_int64), ("arcs", ctypes.c_int64),
+                ("levels", ctypes.c_int32), ("launches", ctypes.c_int32), ("ms_total", ctypes.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
 class scc_batch_config(ctypes.Structure):
     _fields_ = [("tau", ctypes.c_int32), ("block", ctypes.c_int32), ("lambda_", ctypes.c_int32),
                 ("sigma", ctypes.c_int32), ("seeds", ctypes.c_int32), ("beta", ctypes.c_double),
@@ -98,7 +107,7 @@ class scc_batch_stats(ctypes.Structure):
 class scc_server_config(ctypes.Structure):
     _fields_ = [("mem_cap_bytes", ctypes.c_int64), ("batch_vertices", ctypes.c_int32),
                 ("batch_graphs", ctypes.c_int32), ("merge_reach", ctypes.c_int32), ("prefetch", ctypes.c_int32),
-                ("max_bypass_ms", ctypes.c_double)]
+                ("max_bypass_ms", ctypes.c_double), ("batch_min", ctypes.c_int32)]
 
 
 class scc_server_stats(ctypes.Structure):
@@ -150,6 +159,9 @@ def load() -> ctypes.CDLL:
         "scc_get_stats": ([vp, P(scc_stats)], ctypes.c_int),
         "cc_run": ([vp, vp, vp], ctypes.c_int),
         "cc_get_stats": ([vp, P(scc_cc_stats)], ctypes.c_int),
+        "le_lists_run": ([vp, P(i64), vp], ctypes.c_int),
+        "le_lists_get": ([vp, vp, vp, vp, vp, vp], ctypes.c_int),
+        "le_get_stats": ([vp, P(scc_le_stats)], ctypes.c_int),
         "scc_graph_info": ([vp, P(i32), P(i64), P(i64)], ctypes.c_int),
         "scc_debug_csr": ([vp, i32, vp, vp, vp], ctypes.c_int),
         "scc_debug_trim": ([vp, vp, vp], ctypes.c_int),
@@ -161,6 +173,7 @@ def load() -> ctypes.CDLL:
         "scc_debug_pair_table": ([vp, i64, i64, vp, P(i64), P(i32), vp], ctypes.c_int),
         "scc_debug_launch_count": ([], ctypes.c_int64),
         "scc_debug_barrier_timeout": ([i32, i64, P(i32), vp], ctypes.c_int),
+        "scc_debug_le_lists": ([vp, i64, i64, P(i64), vp], ctypes.c_int),
         "scc_batch_config_default": ([P(scc_batch_config)], ctypes.c_int),
         "scc_batch_create": ([i32, vp, vp, vp, vp, vp, P(vp)], ctypes.c_int),
         "scc_batch_destroy": ([vp], ctypes.c_int),
@@ -172,7 +185,7 @@ def load() -> ctypes.CDLL:
         "scc_debug_batch_times": ([vp, vp], ctypes.c_int),
         "scc_debug_batch_groups": ([i32, vp, vp, i64, i64, vp, P(i32)], ctypes.c_int),
         "scc_debug_serve_admission": ([i32, vp, vp, i64, i64, ctypes.c_double, vp, P(i32)], ctypes.c_int),
-        "scc_debug_serve_unit": ([i32, vp, vp, vp, vp, vp, i32, i32, vp, P(i32)], ctypes.c_int),
+        "scc_debug_serve_unit": ([i32, vp, vp, vp, vp, vp, i32, i32, i32, vp, P(i32)], ctypes.c_int),
         "scc_server_config_default": ([P(scc_server_config)], ctypes.c_int),
         "scc_server_create": ([P(scc_server_config), P(vp)], ctypes.c_int),
         "scc_server_destroy": ([vp], ctypes.c_int),
@@ -298,6 +311,34 @@ def cc_get_stats(h) -> dict:
     return s.as_dict()
 
 
+def le_lists_run(h, stream=None) -> int:
+    """Computes the handle's least-element lists; returns the number of entries."""
+    total = ctypes.c_int64()
+    _check(load().le_lists_run(h, ctypes.byref(total), _stream(stream)), "le_lists_run")
+    return total.value
+
+
+def le_lists_get(h, order, le_off, le_src, le_dist, total: int, stream=None) -> None:
+    n = scc_graph_info(h)[0]
+    what = "le_lists_get"
+    _check(load().le_lists_get(h, _arr(order, what + " order", I32, n), _arr(le_off, what + " le_off", I64, n + 1),
+                               _arr(le_src, what + " le_src", I32, total), _arr(le_dist, what + " le_dist", I32, total),
+                               _stream(stream)), what)
+
+
+def scc_debug_le_lists(h, init_cap: int, init_log: int, stream=None) -> int:
+    total = ctypes.c_int64()
+    _check(load().scc_debug_le_lists(h, init_cap, init_log, ctypes.byref(total), _stream(stream)),
+           "scc_debug_le_lists")
+    return total.value
+
+
+def le_get_stats(h) -> dict:
+    s = scc_le_stats()
+    _check(load().le_get_stats(h, ctypes.byref(s)), "le_get_stats")
+    return s.as_dict()
+
+
 def reach_multi(h, sources, k: int, dir: int, out, stream=None) -> None:
     n = scc_graph_info(h)[0]
     ps = _arr(sources, "reach_multi sources", I32, k)
@@ -406,7 +447,8 @@ def scc_debug_serve_admission(need, waited_ms, in_use: int, cap: int, max_bypass
     return out[:na.value].tolist()
 
 
-def scc_debug_serve_unit(kind, small, graph, dir, nsrc, merge_reach: bool = True, batch_graphs: int = 512) -> list:
+def scc_debug_serve_unit(kind, small, graph, dir, nsrc, merge_reach: bool = True, batch_graphs: int = 512,
+                         batch_min: int = 1) -> list:
     """Indices of the admitted requests (arrival order) that join the unit of
     the oldest one (host only)."""
     cols = [np.ascontiguousarray(c, dtype=np.int32) for c in (kind, small, graph, dir, nsrc)]
@@ -416,7 +458,7 @@ def scc_debug_serve_unit(kind, small, graph, dir, nsrc, merge_reach: bool = True
     out = np.zeros(max(count, 1), np.int32)
     nu = ctypes.c_int32()
     _check(load().scc_debug_serve_unit(count, *[_ptr(c) for c in cols], int(bool(merge_reach)), batch_graphs,
-                                       _ptr(out), ctypes.byref(nu)), "scc_debug_serve_unit")
+                                       batch_min, _ptr(out), ctypes.byref(nu)), "scc_debug_serve_unit")
     return out[:nu.value].tolist()
 
 

@@ -13,7 +13,7 @@ from paper_2303_04934_gb300 import scc
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 HEADERS = ["scc.h", "scc_batch.h", "scc_serve.h", "scc_debug.h"]
-STRUCTS = [scc.scc_config, scc.scc_stats, scc.scc_cc_stats, scc.scc_batch_config, scc.scc_batch_stats, scc.scc_server_config,
+STRUCTS = [scc.scc_config, scc.scc_stats, scc.scc_cc_stats, scc.scc_le_stats, scc.scc_batch_config, scc.scc_batch_stats, scc.scc_server_config,
            scc.scc_server_stats]
 
 

@@ -62,6 +62,8 @@ def test_null_handles_and_bad_arguments_rejected_on_the_host(lib):
     for name, args in [
         ("scc_get_stats", (None, None)), ("scc_graph_info", (None, None, None, None)),
         ("cc_run", (None, None, None)), ("cc_get_stats", (None, None)),
+        ("le_lists_run", (None, None, None)), ("le_lists_get", (None, None, None, None, None, None)),
+        ("le_get_stats", (None, None)), ("scc_debug_le_lists", (None, 1, 1, None, None)),
         ("reach_multi_noalloc", (None, None, 1, 0, None, None)),
         ("scc_debug_csr", (None, 0, None, None, None)), ("scc_debug_trim", (None, None, None)),
         ("scc_debug_pivot_order", (None, None, ctypes.byref(i32), None)),
