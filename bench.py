@@ -708,6 +708,50 @@ def _measure_cc(g, off_d, adj_d, scc, torch, stream, steps, warmup, cpu):
     return out
 
 
+def _measure_le(g, scc, torch, stream, steps, cpu):
+    """Least-element lists (le_lists_run: Alg. 5, Sec. 5.2) of the undirected
+    graph under the arcs for the handle's seeded order, timed on a built graph;
+    the lists checked against the oracle's sequential pruned BFS (same order)."""
+    import oracle
+    off_d = torch.from_numpy(g.offsets).to("cuda")
+    adj_d = torch.from_numpy(g.targets).to("cuda")
+    h = scc.scc_graph_create(g.n, g.m, off_d, adj_d, stream)
+    try:
+        total = scc.le_lists_run(h, stream)  # warm-up (and the symmetric CSR)
+        ts = []
+        for _ in range(steps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            with torch.cuda.stream(stream):
+                e0.record(stream)
+                total = scc.le_lists_run(h, stream)
+                e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        st = scc.le_get_stats(h)
+        order = np.empty(g.n, np.int32)
+        off = np.empty(g.n + 1, np.int64)
+        src = np.empty(max(total, 1), np.int32)
+        dist = np.empty(max(total, 1), np.int32)
+        scc.le_lists_get(h, order, off, src, dist, total, stream)
+    finally:
+        scc.scc_graph_destroy(h)
+    ms = sum(ts) / len(ts)
+    out = {"workload": g.name, "n": g.n, "m": g.m, "ms_per_run": ms, "edges_per_s": g.m / (ms / 1e3),
+           "entries": total, "mean_list_length": total / max(g.n, 1), "candidates": st["candidates"],
+           "bfs_levels": st["levels"], "arcs_examined": st["arcs"], "launches": st["launches"], "steps": steps,
+           "step": "le_lists_run on a built graph (symmetric CSR kept from the warm-up)"}
+    if cpu:
+        t0 = time.perf_counter()
+        w_off, w_src, w_dist = oracle.le_lists(g.n, g.offsets, g.targets, order)
+        tc = time.perf_counter() - t0
+        out["lists_equal_oracle"] = bool(np.array_equal(off, w_off) and np.array_equal(src[:total], w_src)
+                                         and np.array_equal(dist[:total], w_dist))
+        out["cpu_baseline"] = {"value": g.m / tc, "unit": UNIT, "cores": 1, "kind": "oracle",
+                               "sample": "the whole graph, 1 run (sequential pruned BFS, same order)", "seconds": tc}
+    del off_d, adj_d
+    return out
+
+
 def _extra_batch(scc, torch, stream, steps, warmup, cpu):
     from paper_2303_04934_gb300 import graphgen as gg
     import oracle
@@ -723,7 +767,7 @@ def _extra_batch(scc, torch, stream, steps, warmup, cpu):
     h = scc.scc_batch_create(G, d[0], d[1], d[2], d[3], stream)
     try:
         t_tune = time.perf_counter()
-        best, ms_t = scc.scc_batch_autotune(h, sample=min(64, G), stream=stream)
+        best, ms_t = scc.scc_batch_autotune(h, sample=min(16, G), stream=stream)
         t_tune = time.perf_counter() - t_tune
         tuned = {"tau": best.tau, "block": best.block, "lambda": best.lambda_, "sample_ms": ms_t,
                  "seconds": t_tune}
@@ -1153,6 +1197,9 @@ def main():
         cpu_x = not args.no_cpu_baseline
         line["workloads"] = {nm: _extra_graph(nm, scc, torch, stream, 5, 3, cpu_x)
                              for nm in ("torus3d256", "knn8m", "torus2d256")}
+        from paper_2303_04934_gb300 import graphgen as gg
+        line["lelists"] = [_measure_le(gx, scc, torch, stream, 3, cpu_x)
+                           for gx in (gg.rmat(20, 16, seed=0x5CC01), gg.torus(3, 64, 0.3, seed=0x5CC02))]
         torch.cuda.empty_cache()
         line["batched"] = _extra_batch(scc, torch, stream, 3, 3, cpu_x)
         torch.cuda.empty_cache()

@@ -48,6 +48,11 @@ typedef struct scc_server_config {
                                (default 1); 0: upload each request's input when its unit runs */
     double max_bypass_ms;   /* a waiting request stops later ones from passing it after this
                                long (default 50) */
+    int32_t batch_min;      /* a batched launch needs at least this many small SCC requests
+                               admitted (default 4, at most batch_graphs); with fewer, the
+                               oldest runs alone on the full-GPU path, which finishes one graph
+                               sooner than one block of the batched kernel does (1: every
+                               small request goes to a batched launch) */
 } scc_server_config;
 
 SCC_API int scc_server_config_default(scc_server_config* cfg);

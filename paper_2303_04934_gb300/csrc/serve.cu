@@ -86,9 +86,11 @@ struct UnitItem {
 // The unit of the oldest admitted request q[0], as increasing indices into q:
 // a reachability query with every later query on the same graph and direction
 // while the sources stay within kMaxMergedSources (merge_reach; otherwise q[0]
-// alone); a small SCC request with the next small ones, batch_graphs at most;
-// a larger SCC request alone.
-std::vector<size_t> unit_select(const std::vector<UnitItem>& q, bool merge_reach, int batch_graphs) {
+// alone); a small SCC request with the next small ones, batch_graphs at most,
+// when at least batch_min small SCC requests are admitted (with fewer, q[0]
+// alone: it runs on the full-GPU path, which is faster for one graph than one
+// block of the batched kernel); a larger SCC request alone.
+std::vector<size_t> unit_select(const std::vector<UnitItem>& q, bool merge_reach, int batch_graphs, int batch_min) {
     std::vector<size_t> u;
     if (q.empty()) return u;
     const UnitItem& h = q[0];
@@ -104,8 +106,14 @@ std::vector<size_t> unit_select(const std::vector<UnitItem>& q, bool merge_reach
             if (!merge_reach) break;
         }
     } else if (h.small) {
-        for (size_t i = 0; i < q.size() && (int)u.size() < std::max(1, batch_graphs); ++i)
-            if (q[i].kind == 0 && q[i].small) u.push_back(i);
+        int smalls = 0;
+        for (const UnitItem& r : q) smalls += r.kind == 0 && r.small;
+        if (smalls < std::max(1, batch_min)) {
+            u.push_back(0);
+        } else {
+            for (size_t i = 0; i < q.size() && (int)u.size() < std::max(1, batch_graphs); ++i)
+                if (q[i].kind == 0 && q[i].small) u.push_back(i);
+        }
     } else {
         u.push_back(0);
     }
@@ -473,7 +481,8 @@ void run_unit(scc_server* S) {
     q.reserve(S->admitted.size());
     for (const ReqPtr& r : S->admitted)
         q.push_back({r->kind, is_small(S, *r), r->graph, r->dir, (int32_t)r->src.size()});
-    const std::vector<size_t> pick = unit_select(q, S->cfg.merge_reach != 0, S->cfg.batch_graphs);
+    const std::vector<size_t> pick =
+        unit_select(q, S->cfg.merge_reach != 0, S->cfg.batch_graphs, S->cfg.batch_min);
     std::vector<ReqPtr> u;
     take_indices(S->admitted, pick, u);
     const auto t0 = Clock::now();
@@ -481,7 +490,7 @@ void run_unit(scc_server* S) {
     if (q[0].kind == 1) {
         run_reach(S, u);
         busy = &S->st.busy_reach_ms;
-    } else if (q[0].small) {
+    } else if (q[0].small && (int)pick.size() >= std::max(1, S->cfg.batch_min)) {
         run_batched(S, u);
         busy = &S->st.busy_batched_ms;
     } else {
@@ -554,6 +563,7 @@ SCC_API int scc_server_config_default(scc_server_config* cfg) {
     cfg->merge_reach = 1;
     cfg->prefetch = 1;
     cfg->max_bypass_ms = 50.0;
+    cfg->batch_min = 4;
     return SCC_OK;
 }
 
@@ -563,7 +573,8 @@ SCC_API int scc_server_create(const scc_server_config* cfg, scc_server_handle* o
     scc_server_config c;
     if (cfg) c = *cfg;
     else scc_server_config_default(&c);
-    if (c.mem_cap_bytes <= 0 || c.batch_vertices < 0 || c.batch_graphs < 1 || !(c.max_bypass_ms >= 0))
+    if (c.mem_cap_bytes <= 0 || c.batch_vertices < 0 || c.batch_graphs < 1 || !(c.max_bypass_ms >= 0) ||
+        c.batch_min < 1 || c.batch_min > c.batch_graphs)
         return SCC_ERR_INVALID_ARG;
     scc_server* S = new (std::nothrow) scc_server();
     if (!S) return SCC_ERR_OOM;
@@ -783,7 +794,7 @@ SCC_API int scc_debug_serve_admission(int32_t count, const int64_t* need, const 
 
 SCC_API int scc_debug_serve_unit(int32_t count, const int32_t* kind, const int32_t* small, const int32_t* graph,
                                  const int32_t* dir, const int32_t* nsrc, int32_t merge_reach, int32_t batch_graphs,
-                                 int32_t* unit, int32_t* nunit) {
+                                 int32_t batch_min, int32_t* unit, int32_t* nunit) {
     if (count < 0 || !nunit || (count > 0 && (!kind || !small || !graph || !dir || !nsrc || !unit)))
         return SCC_ERR_INVALID_ARG;
     std::vector<UnitItem> q((size_t)count);
@@ -791,7 +802,7 @@ SCC_API int scc_debug_serve_unit(int32_t count, const int32_t* kind, const int32
         if ((kind[i] != 0 && kind[i] != 1) || nsrc[i] < 0) return SCC_ERR_INVALID_ARG;
         q[i] = {kind[i], kind[i] == 0 && small[i] != 0, graph[i], dir[i], nsrc[i]};
     }
-    const std::vector<size_t> u = unit_select(q, merge_reach != 0, batch_graphs);
+    const std::vector<size_t> u = unit_select(q, merge_reach != 0, batch_graphs, batch_min);
     for (size_t j = 0; j < u.size(); ++j) unit[j] = (int32_t)u[j];
     *nunit = (int32_t)u.size();
     return SCC_OK;

@@ -23,7 +23,7 @@ def _admission_model(need, waited, in_use, cap, max_bypass):
     return taken
 
 
-def _unit_model(kind, small, graph, dir_, nsrc, merge, batch_graphs):
+def _unit_model(kind, small, graph, dir_, nsrc, merge, batch_graphs, batch_min=1):
     if not kind:
         return []
     if kind[0] == 1:
@@ -37,7 +37,8 @@ def _unit_model(kind, small, graph, dir_, nsrc, merge, batch_graphs):
                 break
         return out
     if small[0]:
-        return [i for i in range(len(kind)) if kind[i] == 0 and small[i]][:batch_graphs]
+        smalls = [i for i in range(len(kind)) if kind[i] == 0 and small[i]]
+        return smalls[:batch_graphs] if len(smalls) >= batch_min else [0]
     return [0]
 
 
@@ -96,6 +97,13 @@ def test_unit_hand_cases():
     assert f([], [], [], [], []) == []
 
 
+def test_unit_needs_batch_min_small_requests_for_a_batched_launch():
+    f = scc.scc_debug_serve_unit
+    kind, small, z = [0, 0, 1, 0], [1, 1, 0, 1], [0, 0, 0, 0]
+    assert f(kind, small, z, z, [0, 0, 5, 0], batch_min=3) == [0, 1, 3]
+    assert f(kind, small, z, z, [0, 0, 5, 0], batch_min=4) == [0]  # too few: the oldest alone
+
+
 @pytest.mark.parametrize("merge", [True, False])
 def test_unit_random_queues_match_the_rule(merge):
     rng = np.random.default_rng(0x0417 + merge)
@@ -107,7 +115,9 @@ def test_unit_random_queues_match_the_rule(merge):
         dir_ = rng.integers(0, 2, count)
         nsrc = rng.integers(1, 65, count) * (kind == 1)
         bg = int(rng.integers(1, 8))
-        want = _unit_model(kind.tolist(), small.tolist(), graph.tolist(), dir_.tolist(), nsrc.tolist(), merge, bg)
-        got = scc.scc_debug_serve_unit(kind, small, graph, dir_, nsrc, merge_reach=merge, batch_graphs=bg)
+        bm = int(rng.integers(1, bg + 1))
+        want = _unit_model(kind.tolist(), small.tolist(), graph.tolist(), dir_.tolist(), nsrc.tolist(), merge, bg, bm)
+        got = scc.scc_debug_serve_unit(kind, small, graph, dir_, nsrc, merge_reach=merge, batch_graphs=bg,
+                                       batch_min=bm)
         assert got == want, trial
         assert got[0] == 0 and got == sorted(set(got))
