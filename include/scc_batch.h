@@ -97,12 +97,16 @@ SCC_API int scc_batch_get_config(scc_batch_handle h, scc_batch_config* cfg);
 SCC_API int scc_batch_run(scc_batch_handle h, int32_t* labels_out, void* stream);
 
 /*
- * Autotuner: times the batched kernel on a sample of about `sample` graphs
- * (spread over the size range; all graphs when sample <= 0 or >= G) for every
- * configuration of the grid tau in {16, 64, 256, 1024, 4096} x block in
- * {128, 256, 512} x lambda in {256, 1024, 4096, 16384}, keeps the fastest in
- * the handle and returns it (and its time in milliseconds) when the pointers
- * are not NULL.
+ * Autotuner: runs the batched kernel on a sample of about `sample` graphs
+ * (spread over the size range; all graphs when sample <= 0 or >= G) for the
+ * handle's configuration and for every configuration of the grid tau in
+ * {16, 64, 256, 1024, 4096} x block in {128, 256, 512} x lambda in
+ * {256, 1024, 4096, 16384}. It scores each by the sample's total block time
+ * (the sum over the sampled graphs of the time a block spent on each, which is
+ * what a full batch's time follows), keeps the best in the handle if it beats
+ * the handle's configuration by more than 3% (the handle's otherwise), and
+ * returns it and the sample's launch time in milliseconds when the pointers
+ * are not NULL. Synchronises `stream`.
  */
 SCC_API int scc_batch_autotune(scc_batch_handle h, int32_t sample, void* stream, scc_batch_config* best,
                                double* best_ms);

@@ -1373,30 +1373,55 @@ SCC_API int scc_batch_autotune(scc_batch_handle h, int32_t sample, void* stream_
     const int taus[] = {16, 64, 256, 1024, 4096};
     const int blocks[] = {128, 256, 512};
     const int lambdas[] = {256, 1024, 4096, 16384};
+    // The objective is the sample's total block time (every sampled graph
+    // runs on its own block, from the kernel's per-graph clock), not the
+    // launch's span: a sample smaller than the grid finishes when its largest
+    // graph does, while a full batch's time is its total work spread over the
+    // blocks. The configuration in the handle stays unless another one cuts
+    // that work by more than 3%.
+    std::vector<unsigned long long> tms((size_t)kTimeWords * h->G);
+    auto measure = [&](const scc_batch_config& c, double* work, double* span) -> int {
+        SCC_TRY(scc_batch_set_config(h, &c));
+        double ms = 0;
+        SCC_TRY(run_order(h, dsub, (int)sub.size(), h->labels, stream, &ms));  // warm-up (and capture)
+        SCC_TRY(run_order(h, dsub, (int)sub.size(), h->labels, stream, span));
+        SCC_CUDA(cudaMemcpyAsync(tms.data(), h->times, sizeof(unsigned long long) * tms.size(),
+                                 cudaMemcpyDeviceToHost, stream));
+        SCC_CUDA(cudaStreamSynchronize(stream));
+        double w = 0;
+        for (int32_t g : sub) {
+            const unsigned long long* t = &tms[(size_t)kTimeWords * g];
+            w += t[5] > t[0] ? 1e-6 * (double)(t[5] - t[0]) : 0.0;
+        }
+        *work = w;
+        return SCC_OK;
+    };
     scc_batch_config bc = base;
-    double bms = 1e300;
-    int rc = SCC_OK;
+    double bwork = 1e300, bms = 0, base_work = 0, base_ms = 0;
+    int rc = measure(base, &base_work, &base_ms);
     for (int blk : blocks) {
+        if (rc != SCC_OK) break;
         for (int lam : lambdas) {
+            if (rc != SCC_OK) break;
             for (int tau : taus) {
                 scc_batch_config c = base;
                 c.block = blk;
                 c.lambda = lam;
                 c.tau = tau;
-                rc = scc_batch_set_config(h, &c);
+                double work = 0, ms2 = 0;
+                rc = measure(c, &work, &ms2);
                 if (rc != SCC_OK) break;
-                double ms = 0, ms2 = 0;
-                rc = run_order(h, dsub, (int)sub.size(), h->labels, stream, &ms);  // warm-up (and capture)
-                if (rc == SCC_OK) rc = run_order(h, dsub, (int)sub.size(), h->labels, stream, &ms2);
-                if (rc != SCC_OK) break;
-                if (ms2 < bms) {
+                if (work < bwork) {
+                    bwork = work;
                     bms = ms2;
                     bc = c;
                 }
             }
-            if (rc != SCC_OK) break;
         }
-        if (rc != SCC_OK) break;
+    }
+    if (rc == SCC_OK && !(bwork < 0.97 * base_work)) {
+        bc = base;
+        bms = base_ms;
     }
     tmp.release(dsub);
     cudaStreamSynchronize(stream);
