@@ -231,6 +231,7 @@ DenseOpts dense_opts(const scc_graph* h, int dir, long long n_active) {
     d.fbits[1] = h->fbits + nw;
     d.n_active = n_active;
     d.frac_inv = h->cfg.dense == 1 ? 20 : h->cfg.dense;
+    d.m_active = (long long)h->mt;
     return d;
 }
 
@@ -995,8 +996,8 @@ static int cc_run_impl(scc_graph* h, int32_t* labels_out, cudaStream_t s) {
     EngineRun r;
     // bottom-up rounds when the frontier is large, as for the first SCC's searches
     const int frac_inv = h->cfg.dense == 1 ? 20 : h->cfg.dense;
-    SCC_TRY(run_ldd(h->soff, h->sadj, n, order, bounds_d, bounds[1], nb, center, vbits, fbits, frac_inv, &h->eb32, o,
-                    &r, s));
+    SCC_TRY(run_ldd(h->soff, h->sadj, n, 2 * (long long)h->mt, order, bounds_d, bounds[1], nb, center, vbits, fbits,
+                    frac_inv, &h->eb32, o, &r, s));
     st.ms_ldd = t.stop();
     st.ldd_rounds = r.rounds;
     st.ldd_batches = nb;

@@ -91,6 +91,7 @@ struct RoundCtl {
     int overflow;      // a pair table went over its load or probe limit
     int err;           // first error of the round (SCC_ERR_*: the bag is full)
     int pad;
+    long long arcs;    // arcs of the items this round pushed or set aside (of those whose degree it loaded)
 };
 
 // Per-search state, a ring of three indexed by the search index: search s
@@ -339,7 +340,7 @@ __device__ __forceinline__ void expand_batch(const EngineParams<typename Pol::It
                                              const BagRef<typename Pol::Item>& out, SegState& st, uint32_t wid,
                                              uint32_t round, const LocalQueue<typename Pol::Item>& q, uint32_t& qh, uint32_t& qt,
                                              int& t, bool seeds_phase, int max_take, int hub_thr, WarpStats& ws,
-                                             unsigned long long& pushed) {
+                                             unsigned long long& pushed, unsigned long long& parcs) {
     using Item = typename Pol::Item;
     constexpr uint32_t QM = Pol::kQueue - 1;
     const int lane = lane_id();
@@ -436,6 +437,7 @@ __device__ __forceinline__ void expand_batch(const EngineParams<typename Pol::It
                 }
                 const int nq = cnt < room ? cnt : room;
                 pushed += bag_push<Item>(out, st, nw[u] && !toq, child[u], wid, round);
+                if (nw[u] && !toq) parcs += (unsigned long long)(re[u] - rb[u]);
                 qt += nq;
             }
         }
@@ -449,13 +451,16 @@ __device__ __forceinline__ void expand_batch(const EngineParams<typename Pol::It
 // Dense (bottom-up) rounds of a single-reachability search (Sec. 4.2): every
 // unvisited vertex of the class scans its in-arcs (the reverse CSR) and stops at
 // the first one whose tail is in the current frontier. Used when the frontier
-// holds at least n_active / frac_inv items.
+// holds at least n_active / frac_inv items, or when its items' arcs number at
+// least m_active / frac_inv (a few hubs can claim much of the graph in one
+// round; their arcs, not their count, set a top-down round's cost).
 struct DenseParams {
     const int32_t* roff;  // reverse CSR (G^T for a forward search, G for a backward one)
     const int32_t* radj;
     uint32_t* fbits[2];   // frontier bitmaps (alternating), ceil(n/32) words each, zero between searches
     long long n_active;   // vertices of the class
     int frac_inv;         // 0 = never dense
+    long long m_active;   // arcs of the graph searched (0: the arcs test is off)
 };
 
 // The initial items of a search: an explicit list (or, for pair searches,
@@ -534,6 +539,7 @@ __device__ bool engine_search(const EngineParams<typename Pol::Item>& P, Pol& po
             nx.nhub = 0;
             nx.overflow = 0;
             nx.err = 0;
+            nx.arcs = 0;
             if (i == 0) {
                 SearchCtl& other = ctl->search[(si + 1) % 3];
                 other.overflow = 0;
@@ -546,14 +552,15 @@ __device__ bool engine_search(const EngineParams<typename Pol::Item>& P, Pol& po
         if constexpr (Pol::kCountInserts) pol.overflow = &cur.overflow;
         Item* const in_slots = P.slots[ipar];
         SegState st{-1, 0, (uint32_t)(wid * 2654435761u) ^ gr};
-        unsigned long long pushed = 0;
+        unsigned long long pushed = 0, parcs = 0;
         long long in_end = i == 0 ? 0 : chunk_end(P.lambda, ld_volatile(&prev.bag.r), P.nslots);
         const long long fr_items = i == 0 ? ninit : ld_volatile(&prev.items);
         const int fr_hubs = i == 0 ? 0 : min(ld_volatile(&prev.nhub), P.hub_cap);
         bool dense = false;
         if constexpr (Pol::kDense) {
             dense = i > 0 && dp != nullptr && dp->frac_inv > 0 &&
-                    (long long)(fr_items + fr_hubs) * (long long)dp->frac_inv >= dp->n_active;
+                    ((long long)(fr_items + fr_hubs) * (long long)dp->frac_inv >= dp->n_active ||
+                     (dp->m_active > 0 && ld_volatile(&prev.arcs) * (long long)dp->frac_inv >= dp->m_active));
             if (prev_dense) {  // the bitmap of the previous (dense) round
                 uint32_t* old = dp->fbits[ipar];
                 const long long nw = ((long long)P.n + 31) / 32;
@@ -782,7 +789,10 @@ __device__ bool engine_search(const EngineParams<typename Pol::Item>& P, Pol& po
                     b0 = S::ld(&O[v]);
                     dg = S::ld(&O[v + 1]) - b0;
                     if constexpr (Pol::kCtxInQueue) cx0 = pol.load_ctx(it);
-                    if (dg > hub_thr && reserve_hub(P, cur, par, it, b0, dg)) has = false;
+                    if (dg > hub_thr && reserve_hub(P, cur, par, it, b0, dg)) {
+                        has = false;
+                        parcs += (unsigned long long)dg;
+                    }
                 }
                 const uint32_t m = __ballot_sync(kFull, has);
                 if (m == 0) continue;
@@ -795,13 +805,16 @@ __device__ bool engine_search(const EngineParams<typename Pol::Item>& P, Pol& po
                 __syncwarp();
                 uint32_t qh = 0, qt = (uint32_t)__popc(m);
                 int t = 0;
-                expand_batch<Pol, S>(P, pol, out, st, wid, gr, q, qh, qt, t, true, P.seeds, hub_thr, ws, pushed);
+                expand_batch<Pol, S>(P, pol, out, st, wid, gr, q, qh, qt, t, true, P.seeds, hub_thr, ws, pushed,
+                                     parcs);
                 while (qt != qh && t < P.tau)
-                    expand_batch<Pol, S>(P, pol, out, st, wid, gr, q, qh, qt, t, false, 32, hub_thr, ws, pushed);
+                    expand_batch<Pol, S>(P, pol, out, st, wid, gr, q, qh, qt, t, false, 32, hub_thr, ws, pushed,
+                                         parcs);
                 // budget spent: flush what is left in the local queue
                 while (qt != qh) {
                     const int nrem = (int)min(32u, qt - qh);
                     const Item x = lane < nrem ? q.it[(qh + lane) & QM] : Sent<Item>::empty;
+                    if (lane < nrem) parcs += (unsigned long long)q.rg[(qh + lane) & QM].y;
                     qh += nrem;
                     pushed += bag_push<Item>(out, st, lane < nrem, x, wid, gr);
                 }
@@ -815,6 +828,10 @@ __device__ bool engine_search(const EngineParams<typename Pol::Item>& P, Pol& po
             if constexpr (Pol::kInject) pol.inject(i, out, st, wid, nwarps, gr, pushed);
         }
         if (lane == 0 && pushed) atomicAdd((unsigned long long*)&cur.items, pushed);
+        if constexpr (Pol::kDense) {
+            for (int d = 16; d >= 1; d >>= 1) parcs += __shfl_xor_sync(kFull, parcs, d);
+            if (lane == 0 && parcs) atomicAdd((unsigned long long*)&cur.arcs, parcs);
+        }
         if (!S::sync(&ctl->bar, &ctl->err)) return false;
         if (gr < (uint32_t)kTraceRounds && S::block() == 0 && threadIdx.x == 0) {
             ctl->t_end[gr] = globaltimer_ns();

@@ -285,14 +285,15 @@ struct EngineOpts {
 };
 
 // Dense-round inputs of a single-reachability search (Sec. 4.2 dense mode):
-// the reverse CSR, a zeroed frontier bitmap and the class size; frac_inv = 0
-// disables dense rounds.
+// the reverse CSR, a zeroed frontier bitmap, the class size and the graph's
+// arcs; frac_inv = 0 disables dense rounds.
 struct DenseOpts {
     const int32_t* roff = nullptr;
     const int32_t* radj = nullptr;
     uint32_t* fbits[2] = {nullptr, nullptr};
     long long n_active = 0;
     int frac_inv = 0;
+    long long m_active = 0;
 };
 // Single reachability from `s` over (off, adj) with the bitmap (already prefilled).
 // Forward (off/adj, marks bits_f) and backward (toff/tadj, marks bits_b)
@@ -380,10 +381,11 @@ int batch_runner_enqueue(BatchRunner* r, int32_t G, const long long* vbase, cons
 // and in the visited bitmap `bits`, whose bits past n are set); on return
 // center[v] is the centre of v's cluster. fbits: two zeroed frontier bitmaps
 // of ceil(n / 32) words (zero again on return); a round whose frontier holds
-// n / frac_inv vertices or more runs bottom-up (frac_inv = 0: never).
-int run_ldd(const int32_t* soff, const int32_t* sadj, int32_t n, const int32_t* order, const long long* bounds_d,
-            long long first, int nbatches, int32_t* center, uint32_t* bits, uint32_t* fbits, int frac_inv,
-            EngineBuf* b, const EngineOpts& o, EngineRun* out, cudaStream_t st);
+// n / frac_inv vertices, or arcs numbering soff_arcs / frac_inv, or more runs
+// bottom-up (frac_inv = 0: never).
+int run_ldd(const int32_t* soff, const int32_t* sadj, int32_t n, long long soff_arcs, const int32_t* order,
+            const long long* bounds_d, long long first, int nbatches, int32_t* center, uint32_t* bits, uint32_t* fbits,
+            int frac_inv, EngineBuf* b, const EngineOpts& o, EngineRun* out, cudaStream_t st);
 // Connectivity steps (cc.cu): the symmetric CSR (soff[v] = off[v] + toff[v],
 // row v = row v of G then row v of G^T); center[] = -1 with the first `first`
 // vertices of order centring themselves; then union-find over the arcs of G

@@ -193,7 +193,7 @@ int run_single(const int32_t* off, const int32_t* adj, int32_t n, int32_t s, uin
     P.init = reinterpret_cast<const uint32_t*>(b->init);
     P.ninit = 1;
     PolSingle pol{bits};
-    DenseParams dp{dn.roff, dn.radj, {dn.fbits[0], dn.fbits[1]}, dn.n_active, dn.frac_inv};
+    DenseParams dp{dn.roff, dn.radj, {dn.fbits[0], dn.fbits[1]}, dn.n_active, dn.frac_inv, dn.m_active};
     int rc = launch_engine(P, pol, o, out, st, dp);
     if (rc != SCC_OK || out->err) SCC_TRY(engine_reset_slots(b, st));
     SCC_TRY(rc);
@@ -222,9 +222,9 @@ int run_single_both(const int32_t* off, const int32_t* adj, const int32_t* toff,
     return out->err ? out->err : SCC_OK;
 }
 
-int run_ldd(const int32_t* soff, const int32_t* sadj, int32_t n, const int32_t* order, const long long* bounds_d,
-            long long first, int nbatches, int32_t* center, uint32_t* bits, uint32_t* fbits, int frac_inv,
-            EngineBuf* b, const EngineOpts& o, EngineRun* out, cudaStream_t st) {
+int run_ldd(const int32_t* soff, const int32_t* sadj, int32_t n, long long soff_arcs, const int32_t* order,
+            const long long* bounds_d, long long first, int nbatches, int32_t* center, uint32_t* bits, uint32_t* fbits,
+            int frac_inv, EngineBuf* b, const EngineOpts& o, EngineRun* out, cudaStream_t st) {
     auto P = make_engine_params<uint32_t>(soff, sadj, n, b, o);
     P.init = reinterpret_cast<const uint32_t*>(order);  // the first batch, claimed before the launch
     P.ninit = first;
@@ -237,7 +237,7 @@ int run_ldd(const int32_t* soff, const int32_t* sadj, int32_t n, const int32_t* 
     pol.nbatches = nbatches;
     // the graph is symmetric: it is its own reverse for the bottom-up rounds
     const long long nw = ((long long)n + 31) / 32;
-    DenseParams dp{soff, sadj, {fbits, fbits + nw}, (long long)n, frac_inv};
+    DenseParams dp{soff, sadj, {fbits, fbits + nw}, (long long)n, frac_inv, soff_arcs};
     int rc = launch_engine(P, pol, o, out, st, dp);
     if (rc != SCC_OK || out->err) SCC_TRY(engine_reset_slots(b, st));
     SCC_TRY(rc);
