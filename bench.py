@@ -348,11 +348,7 @@ def run_batch(args, spec):
     # building G^T (read the targets twice, write them once, 12 B per arc, + 12 B
     # per vertex of offsets) + reading G and G^T once and writing the labels
     # (8 B per arc + 12 B per vertex)
-    peaks = {}
-    try:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    except Exception:
-        pass
+    peaks = _read_peaks()
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
     alg = 20 * na + 24 * nv
     achieved = alg / (ms / args.steps / 1e3) / 1e9
@@ -590,6 +586,14 @@ def run_serve(args, spec):
 # the k-NN graph and the small 2D torus (plain per-graph SCC), the batch of
 # 4,096 graphs, and the served trace at its offered rate and at loads the
 # server sustains.
+def _read_peaks():
+    """The measured peaks of this machine (MEASURED_PEAKS.json), or {}."""
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
 def _extra_graph(name, scc, torch, stream, steps, warmup, cpu):
     spec = WORKLOADS[name]
     t_gen = time.perf_counter()
@@ -632,6 +636,24 @@ def _extra_graph(name, scc, torch, stream, steps, warmup, cpu):
            "gen_seconds": t_gen}
     if spec["kind"] == "torus" and spec["dims"] == 2:
         out["note"] = "L2-resident (about 1.3 MB of CSR): a bandwidth fraction is not meaningful"
+    # the run's algorithmic bytes, counted as for the benchmark graph (8 B per
+    # arc examined, 8 B per item expanded, 16 B per pair inserted, 20 B per
+    # active vertex per labelling), over the run's mean time (create excluded)
+    last = sts[-1]
+    E = last["engine_arcs"] + last["multi_arcs"]
+    P = last["engine_items"] + last["multi_items"]
+    I = last["pairs"]
+    act = (g.n - last["n_trimmed"]) + last["multi_active_sum"]
+    run_bytes = 8 * E + 8 * P + 16 * I + 20 * act
+    run_ms = sum(out["run_ms"].values())
+    peak = float(_read_peaks().get("hbm_gbs", 6800.0))
+    out["run_roofline"] = {"bound": "hbm", "bytes_formula": "8 E + 8 P + 16 I + 20 sum(active per labelling)",
+                           "E_arcs": E, "P_items": P, "I_pairs": I, "active_labelled": act,
+                           "algorithmic_bytes": run_bytes, "run_ms": run_ms,
+                           "achieved_gbs": run_bytes / (run_ms / 1e3) / 1e9 if run_ms > 0 else None,
+                           "frac": run_bytes / (run_ms / 1e3) / 1e9 / peak if run_ms > 0 else None, "peak": peak,
+                           "rounds": last["search_rounds"],
+                           "note": "latency-bound rounds: the time follows the rounds, not the bytes"}
     out["connectivity"] = _measure_cc(g, off_d, adj_d, scc, torch, stream, 5, 2, cpu)
     if spec["kind"] == "knn":
         # the hash bag of Sec. 3.3 (sampled, sigma = 50) against a reservation bag
@@ -795,11 +817,7 @@ def _extra_batch(scc, torch, stream, steps, warmup, cpu):
         labels_h = labels_d.cpu().numpy()
     finally:
         scc.scc_batch_destroy(h)
-    peaks = {}
-    try:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    except Exception:
-        pass
+    peaks = _read_peaks()
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
     alg = 20 * na + 24 * nv
     out = {"workload": f"batch_G{G}_n{spec['n_lo']}-{spec['n_hi']}_torus2d-rmat8", "graphs": G, "vertices": nv,
@@ -1043,11 +1061,7 @@ def main():
     #   multi-reachability batch loop: 8 B per arc examined (target + label),
     #     8 B row offsets per item expanded, 16 B per pair inserted (table
     #     slot + bag slot).
-    peaks = {}
-    try:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    except Exception:
-        pass
+    peaks = _read_peaks()
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
     peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
     mt = m  # generated graphs have no self-loops
