@@ -763,6 +763,7 @@ static int scc_run_impl(scc_graph* h, int32_t* labels_out, cudaStream_t s) {
             a.bgss_ctl = h->bgss_ctl;
             a.ndone = hc[1];
             a.a_prev[0] = a.a_prev[1] = 0;
+            a.ka_prev = 0;
             a.o = o;
             // Grid sized to the active vertices (about 2k per block, at least 16
             // blocks): small remainders run on fewer blocks, whose barriers cost
@@ -813,6 +814,7 @@ static int scc_run_impl(scc_graph* h, int32_t* labels_out, cudaStream_t s) {
                     a.ndone = r.ndone;
                     a.a_prev[0] = r.a_prev[0];
                     a.a_prev[1] = r.a_prev[1];
+                    a.ka_prev = r.ka_prev;
                     a.first_min_cap = 0;
                     plan(N - (int64_t)r.ndone);
                     continue;
@@ -825,6 +827,7 @@ static int scc_run_impl(scc_graph* h, int32_t* labels_out, cudaStream_t s) {
                 a.ndone = r.ndone;
                 a.a_prev[0] = r.a_prev[0];
                 a.a_prev[1] = r.a_prev[1];
+                a.ka_prev = r.ka_prev;
             }
         }
         if ((int64_t)hc[1] != N) return SCC_ERR_INTERNAL;  // every active vertex must be finished

@@ -444,6 +444,7 @@ __device__ bool scc_one_graph(const BatchArgs& A, Ws& W, int g, BlockShared& sh,
     long long lo = 1;
     double width = A.beta;
     long long a_prev[2] = {0, 0};
+    long long k_prev = 0;     // sources of the batch whose pairs a_prev holds
     long long cap_floor = 0;  // table size forced by a retried batch
     while (lo < (long long)na && active > 0) {
         long long hi = width >= (double)na ? (long long)na : min((long long)na, lo + (long long)ceil(width));
@@ -459,10 +460,13 @@ __device__ bool scc_one_graph(const BatchArgs& A, Ws& W, int g, BlockShared& sh,
             const long long k = sh.count;
             __syncthreads();
             if (k == 0) break;
-            // table sizes (Sec. 4.5 heuristic, capped by the slice)
+            // table sizes (Sec. 4.5 heuristic, capped by the slice; the previous
+            // batch's pairs scaled by the ratio of the sources, as batches grow)
             long long cap[2];
+            const double grow_k = k_prev > 0 ? (double)k / (double)k_prev : 1.0;
             for (int d = 0; d < 2; ++d) {
-                long long want = max((long long)ceil(0.3 * (double)active), (long long)ceil(1.5 * (double)a_prev[d]));
+                long long want = max((long long)ceil(0.3 * (double)active),
+                                     (long long)ceil(1.5 * (double)a_prev[d] * grow_k));
                 want = max(want, k);
                 long long c2 = kBatchMinTable;
                 while (c2 < 2 * want && c2 < A.D.tcap) c2 <<= 1;
@@ -534,6 +538,7 @@ __device__ bool scc_one_graph(const BatchArgs& A, Ws& W, int g, BlockShared& sh,
             active -= (long long)block_sum(c, sh);
             a_prev[0] = pairs0;
             a_prev[1] = pairs1;
+            k_prev = k;
             cap_floor = 0;
             ++n_batch;
             break;

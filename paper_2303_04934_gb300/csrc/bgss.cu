@@ -31,6 +31,7 @@ struct BgssCtl {
     long long need_cap;
     unsigned long long ndone;   // finished vertices so far (first SCC included)
     unsigned long long a[2];    // pairs of the previous batch, per direction
+    int ka;                     // that batch's sources (0: unknown)
     int k[2];                   // sources of the batch (double-buffered)
     unsigned long long pairs;   // statistics
     int batches;
@@ -134,11 +135,15 @@ __global__ void __launch_bounds__(kEngineBlock, 2) bgss_kernel(BgssParams B) {
         if (k == 0) continue;
         // ---- pair-table sizes (Sec. 4.5): the expected pairs max(0.3 b, 1.5 a) (at
         // least k) at load factor 1/2, rounded up to a power of two; a batch
-        // resumed after an overflow keeps the grown size
+        // resumed after an overflow keeps the grown size. a is the previous
+        // batch's pairs scaled by the ratio of this batch's sources to that
+        // batch's: batches grow by beta, and their pairs with them
         long long cap[2];
+        const int ka = ld_volatile(&bc->ka);
+        const double grow_k = ka > 0 ? (double)k / (double)ka : 1.0;
         for (int d = 0; d < 2; ++d) {
-            const long long a = (long long)ld_volatile(&bc->a[d]);
-            long long want = max((long long)ceil(0.3 * (double)b_active), (long long)ceil(1.5 * (double)a));
+            const double a = (double)ld_volatile(&bc->a[d]) * grow_k;
+            long long want = max((long long)ceil(0.3 * (double)b_active), (long long)ceil(1.5 * a));
             want = max(want, (long long)k);
             cap[d] = max(1024ll, pow2ceil_d(2 * want));
             if (i == B.first) cap[d] = max(cap[d], B.first_min_cap);
@@ -202,6 +207,7 @@ __global__ void __launch_bounds__(kEngineBlock, 2) bgss_kernel(BgssParams B) {
         if (gtid == 0) {
             bc->a[0] = (unsigned long long)pairs[0];
             bc->a[1] = (unsigned long long)pairs[1];
+            bc->ka = k;
             bc->pairs += (unsigned long long)(pairs[0] + pairs[1]);
             bc->batches += 1;
         }
@@ -253,6 +259,7 @@ int run_bgss_device(const BgssArgs& a, BgssResult* res, cudaStream_t st) {
     h.ndone = a.ndone;
     h.a[0] = a.a_prev[0];
     h.a[1] = a.a_prev[1];
+    h.ka = a.ka_prev;
     B.bc = dbc;
     SCC_CUDA(cudaMemcpyAsync(dbc, &h, sizeof(h), cudaMemcpyHostToDevice, st));
     SCC_CUDA(cudaMemsetAsync(b->ctl, 0, sizeof(EngineCtl), st));
@@ -291,6 +298,7 @@ int run_bgss_device(const BgssArgs& a, BgssResult* res, cudaStream_t st) {
     res->ndone = h.ndone;
     res->a_prev[0] = h.a[0];
     res->a_prev[1] = h.a[1];
+    res->ka_prev = h.ka;
     res->pairs = h.pairs;
     res->active_sum = h.active_sum;
     res->batches = h.batches;

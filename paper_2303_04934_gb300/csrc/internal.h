@@ -338,6 +338,7 @@ struct BgssArgs {
     void* bgss_ctl;  // device, bgss_ctl_bytes()
     unsigned long long ndone;
     unsigned long long a_prev[2];
+    int ka_prev = 0;  // sources of the batch whose pairs a_prev holds (0: unknown)
     EngineOpts o;
 };
 struct BgssResult {
@@ -347,6 +348,7 @@ struct BgssResult {
     long long need_cap = 0;
     unsigned long long ndone = 0;
     unsigned long long a_prev[2] = {0, 0};
+    int ka_prev = 0;
     unsigned long long pairs = 0;
     int batches = 0;
     int rounds = 0;
