@@ -91,6 +91,11 @@ SCC_API const char* scc_error_string(int code);
  *               holds 1/20 of the searched class (the default); k in [2, 1024]:
  *               once it holds 1/k of it.
  *   seed        seed of the pivot permutation (default 0x5CC00).
+ *   ldd_beta    growth factor of the centre batches of cc_run's low-diameter
+ *               decomposition, in (1, 64] (Sec. 5.1 uses 1.2). Default 2: each
+ *               batch adds a round whose time on the GPU is mostly barrier and
+ *               memory latency, so fewer and larger batches are faster here
+ *               (R-MAT 24: 83 -> 24 rounds); the components do not change.
  * Out-of-range values are rejected with SCC_ERR_INVALID_ARG.
  */
 typedef struct scc_config {
@@ -102,6 +107,7 @@ typedef struct scc_config {
     int32_t seeds;
     int32_t dense;
     uint64_t seed;
+    double ldd_beta;
 } scc_config;
 
 /* Fill *cfg with the defaults listed above. */
@@ -244,8 +250,8 @@ SCC_API int scc_get_stats(scc_handle h, scc_stats* out);
  * The first call on h builds the symmetric CSR (each vertex's out-arcs then
  * its in-arcs, 2 m_t entries) and keeps it with the handle until it is
  * destroyed. The decomposition takes its centres from h's seeded order in
- * batches growing by a factor 1.2 (the paper's choice); the result does not
- * depend on the seed. Returns SCC_ERR_INTERNAL if a bounded union-find loop
+ * batches growing by the configuration's ldd_beta (default 2; the paper's
+ * choice is 1.2); the result depends on neither the seed nor ldd_beta. Returns SCC_ERR_INTERNAL if a bounded union-find loop
  * ran out (never expected). Synchronises `stream` before returning.
  */
 SCC_API int cc_run(scc_handle h, int32_t* labels_out, void* stream);

@@ -193,6 +193,7 @@ int valid_config(const scc_config* c) {
     if (c->block != 256) return SCC_ERR_INVALID_ARG;
     if (c->seeds < 1 || c->seeds > 32) return SCC_ERR_INVALID_ARG;
     if (c->dense < 0 || c->dense > 1024) return SCC_ERR_INVALID_ARG;
+    if (!(c->ldd_beta > 1.0 && c->ldd_beta <= 64.0)) return SCC_ERR_INVALID_ARG;
     return SCC_OK;
 }
 
@@ -328,6 +329,7 @@ int scc_config_default(scc_config* cfg) {
     cfg->seeds = 32;
     cfg->dense = 1;
     cfg->seed = 0x5CC00ull;
+    cfg->ldd_beta = 2.0;
     return SCC_OK;
 }
 
@@ -908,7 +910,6 @@ int reach_multi_noalloc(scc_handle h, const int32_t* sources, int32_t k, int32_t
 // ----------------------------------------------------------- connectivity --
 // Connected components of the undirected graph under G's arcs (Sec. 5.1,
 // Alg. 4 LDD-UF-JTB with VGC and the hash bag; steps in cc.cu).
-static constexpr double kLddBeta = 1.2;  // batch growth of the decomposition (Sec. 5.1)
 
 // The symmetric CSR of h (row v = row v of G, then row v of G^T), built on the
 // first call and kept with the handle.
@@ -977,7 +978,7 @@ static int cc_run_impl(scc_graph* h, int32_t* labels_out, cudaStream_t s) {
             if (sz < 1) sz = 1;
             pos = ((long long)n - pos < sz) ? (long long)n : pos + sz;
             bounds.push_back(pos);
-            x *= kLddBeta;
+            x *= h->cfg.ldd_beta;
         }
     }
     const int nb = (int)bounds.size() - 1;

@@ -5,7 +5,8 @@
 //      symmetrises directed inputs for connectivity). Its offsets are
 //      off[v] + toff[v], so only the rows are copied.
 //   2. LDD (Alg. 4 function LDD): a seeded order of all vertices cut into
-//      batches growing by a factor beta (1.2, the paper's choice); the first
+//      batches growing by the factor scc_config.ldd_beta (default 2; the
+//      paper's choice is 1.2, fewer batches mean fewer rounds here); the first
 //      batch claims itself, then one search of the VGC engine (PolLdd) runs
 //      rounds in which every frontier item claims unvisited neighbours for its
 //      centre, and at the end of round i the unvisited vertices of batch i + 1

@@ -46,7 +46,7 @@ EXPORTED = [
 class scc_config(ctypes.Structure):
     _fields_ = [("tau", ctypes.c_int32), ("beta", ctypes.c_double), ("lambda_", ctypes.c_int32),
                 ("sigma", ctypes.c_int32), ("block", ctypes.c_int32), ("seeds", ctypes.c_int32),
-                ("dense", ctypes.c_int32), ("seed", ctypes.c_uint64)]
+                ("dense", ctypes.c_int32), ("seed", ctypes.c_uint64), ("ldd_beta", ctypes.c_double)]
 
 
 class scc_stats(ctypes.Structure):

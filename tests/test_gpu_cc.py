@@ -91,3 +91,18 @@ def test_component_labels_refined_by_scc_labels():
         cc = _cc(G)
         lab = lab.cpu().numpy()
     assert np.array_equal(cc[lab], cc)
+
+
+@pytest.mark.parametrize("ldd_beta", [1.2, 2.0, 8.0])
+def test_labels_do_not_depend_on_the_batch_growth(ldd_beta):
+    """The decomposition's batch growth (the paper's 1.2, the default 2, a
+    coarse 8) changes the clusters, never the components."""
+    c = scc.scc_config_default()
+    c.ldd_beta = ldd_beta
+    for g in (gg.rmat(15, 8, seed=51), gg.torus(2, 120, 0.3, seed=52), gg.knn(50_000, 4, seed=53)):
+        want, ncc = oracle.cc_labels(g.n, g.offsets, g.targets)
+        with make_graph(g, config=c) as G:
+            got = _cc(G)
+            st = scc.cc_get_stats(G.h)
+        assert np.array_equal(got, want), (g.name, ldd_beta)
+        assert st["components"] == ncc
