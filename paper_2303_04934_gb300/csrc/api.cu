@@ -1009,13 +1009,15 @@ static int cc_run_impl(scc_graph* h, int32_t* labels_out, cudaStream_t s) {
     // ---- union-find over the cross arcs (Alg. 4 Union), then the labels
     CreateEvents ev;
     cudaEventRecord(ev.e[0], s);
-    const long long big_cap = (long long)(h->mt / 2048) + 1;
-    int32_t* big = nullptr;
-    long long* bpre = nullptr;
+    const long long big_cap = (long long)(h->mt / 33) + 1;  // rows of more than 32 arcs
+    int32_t *big = nullptr, *bdeg = nullptr, *bpre = nullptr;
+    unsigned char* stmp = nullptr;
     SCC_TRY(tmp.alloc(&big, (size_t)big_cap));
+    SCC_TRY(tmp.alloc(&bdeg, (size_t)big_cap));
     SCC_TRY(tmp.alloc(&bpre, (size_t)big_cap + 1));
-    SCC_TRY(launch_cc_union_label(h->off, h->adj, n, center, parent, root, mn, out, counters, big, bpre, big_cap, err,
-                                  num_sms, s, &ev.e[1]));
+    SCC_TRY(tmp.alloc(&stmp, scan_tmp_bytes(big_cap)));
+    SCC_TRY(launch_cc_union_label(h->off, h->adj, n, center, parent, root, mn, out, counters, big, bdeg, bpre, stmp,
+                                  big_cap, err, num_sms, s, &ev.e[1]));
     if (!dev_out) SCC_TRY(from_device(labels_out, out, sizeof(int32_t) * (size_t)n, s));
     unsigned long long hc[4];
     int herr = 0;

@@ -34,7 +34,7 @@ namespace {
 
 constexpr int kBlk = 256;
 constexpr int kUfLimit = 1 << 20;  // steps of one find or union before it reports an error
-constexpr int kBigRow = 2048;      // rows with more arcs are split over the whole grid
+constexpr int kSmallRow = 32;      // rows with more arcs go to the flat pass (k_uf_flat)
 
 inline int grid_for(int64_t work, int per_block, int cap) {
     int64_t g = (work + per_block - 1) / per_block;
@@ -125,164 +125,152 @@ __global__ void k_uf_init(int32_t n, int32_t* parent, int32_t* mn) {
 
 // Arcs of G whose endpoints lie in different clusters join the clusters'
 // centres (every edge of the undirected graph is an arc of G). A thread takes
-// one row and walks its arcs; rows of more than 32 arcs are walked by the
-// whole warp, one after another; rows of more than kBigRow arcs go to a list
-// (at most m / kBigRow of them) whose arcs k_uf_big spreads evenly over the
-// whole grid, so no warp walks a hub's row alone.
-// After the decomposition most such arcs repeat a pair that is already joined
-// (a few clusters per component, many arcs between them), and every union on
-// the same pair would contend for the same few parent words: a row skips the
-// centre it joined last, a warp on a hub row elects one lane per distinct
-// centre, and a read-only peek at both sets skips pairs already joined.
-__device__ __forceinline__ void uf_warp_arcs(const int32_t* __restrict__ adj, const int32_t* __restrict__ center,
-                                             int32_t* parent, int32_t cu, long long b0, long long b1, long long step,
-                                             unsigned long long& c, int* err) {
-    const int lane = lane_id();
-    for (long long e0 = b0; e0 < b1; e0 += step) {  // warp-uniform
-        const long long e = e0 + lane;
-        int32_t cw = e < b1 ? center[adj[e]] : cu;
-        if (cw < 0) {  // every vertex has a centre after the decomposition
-            atomicCAS(err, 0, SCC_ERR_INTERNAL);
-            cw = cu;
-        }
-        const bool x = cw != cu;
-        c += x;
-        const uint32_t peers = __match_any_sync(kFull, x ? cw : -1);
-        if (x && __ffs(peers) - 1 == lane && uf_peek(parent, cu) != uf_peek(parent, cw)) uf_union(parent, cu, cw, err);
-    }
-}
-
+// one row of at most kSmallRow arcs and walks it, four arcs at a time; longer
+// rows go to a list (row, degree) whose arcs k_uf_flat spreads evenly over the
+// whole grid. After the decomposition most cross arcs repeat a pair that is
+// already joined (a few clusters per component, many arcs between them), and
+// every union on the same pair would contend for the same few parent words:
+// a row skips the centre it joined last, a warp elects one lane per distinct
+// pair, and a read-only peek at both sets skips pairs already joined.
 __global__ void k_uf_arcs(const int32_t* __restrict__ off, const int32_t* __restrict__ adj, int32_t n,
                           const int32_t* __restrict__ center, int32_t* parent, unsigned long long* cross,
-                          int32_t* big, unsigned long long* nbig, long long big_cap, int* err) {
-    const int lane = lane_id();
+                          int32_t* big, int32_t* bdeg, unsigned long long* nbig, long long big_cap, int* err) {
     const long long gtid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long gstride = (long long)gridDim.x * blockDim.x;
     unsigned long long c = 0;
-    for (long long base = gtid - lane; base < n; base += gstride) {  // warp-uniform
-        const long long u = base + lane;
-        int a0 = 0, a1 = 0;
-        int32_t cu = 0;
-        if (u < n) {
-            a0 = off[u];
-            a1 = off[u + 1];
-            if (a1 > a0) cu = center[u];
-            if ((uint32_t)cu >= (uint32_t)n) {  // every vertex has a centre after the decomposition
-                atomicCAS(err, 0, SCC_ERR_INTERNAL);
-                a1 = a0;
-                cu = 0;
-            }
-        }
-        if (a1 - a0 > kBigRow) {
+    for (long long u = gtid; u < n; u += gstride) {
+        const int a0 = off[u], a1 = off[u + 1];
+        if (a1 == a0) continue;
+        if (a1 - a0 > kSmallRow) {
             const unsigned long long k = atomicAdd(nbig, 1ull);
-            if ((long long)k < big_cap) big[k] = (int32_t)u;
-            else atomicExch(err, SCC_ERR_INTERNAL);  // cannot happen: big_cap >= m / kBigRow + 1
-            a1 = a0;
+            if ((long long)k < big_cap) {
+                big[k] = (int32_t)u;
+                bdeg[k] = a1 - a0;
+            } else {
+                atomicExch(err, SCC_ERR_INTERNAL);  // cannot happen: big_cap >= m / (kSmallRow + 1) + 1
+            }
+            continue;
         }
-        const bool big = a1 - a0 > 32;
-        if (!big) {
-            int32_t last = cu;
-            for (int e = a0; e < a1; ++e) {
-                const int32_t cw = center[adj[e]];
-                if ((uint32_t)cw >= (uint32_t)n) {
+        const int32_t cu = center[u];
+        if ((uint32_t)cu >= (uint32_t)n) {  // every vertex has a centre after the decomposition
+            atomicCAS(err, 0, SCC_ERR_INTERNAL);
+            continue;
+        }
+        // four arcs at a time: their targets, then the targets' centres, as
+        // independent loads
+        int32_t last = cu;
+        for (int e0 = a0; e0 < a1; e0 += 4) {
+            int32_t w[4], cw[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) w[j] = e0 + j < a1 ? adj[e0 + j] : -1;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) cw[j] = w[j] >= 0 ? center[w[j]] : cu;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                if ((uint32_t)cw[j] >= (uint32_t)n) {
                     atomicCAS(err, 0, SCC_ERR_INTERNAL);
                     continue;
                 }
-                if (cw != cu) {
+                if (cw[j] != cu) {
                     ++c;
-                    if (cw != last) {
-                        last = cw;
-                        if (uf_peek(parent, cu) != uf_peek(parent, cw)) uf_union(parent, cu, cw, err);
+                    if (cw[j] != last) {
+                        last = cw[j];
+                        if (uf_peek(parent, cu) != uf_peek(parent, cw[j])) uf_union(parent, cu, cw[j], err);
                     }
                 }
             }
         }
-        uint32_t m = __ballot_sync(kFull, big);
-        while (m) {
-            const int j = __ffs(m) - 1;
-            m &= m - 1;
-            const int32_t bu = __shfl_sync(kFull, cu, j);
-            const int b0 = __shfl_sync(kFull, a0, j), b1 = __shfl_sync(kFull, a1, j);
-            uf_warp_arcs(adj, center, parent, bu, b0, b1, 32, c, err);
-        }
     }
     for (int d = 16; d >= 1; d >>= 1) c += __shfl_xor_sync(kFull, c, d);
-    if (lane == 0 && c) atomicAdd(cross, c);
+    if (lane_id() == 0 && c) atomicAdd(cross, c);
 }
 
-// Offsets of the rows k_uf_arcs left in one flat range: bpre[i] = arcs of
-// big[0 .. i) (one block; at most m / kBigRow + 1 rows).
-__global__ void __launch_bounds__(1024) k_big_scan(const int32_t* __restrict__ off, const int32_t* __restrict__ big,
-                                                   const unsigned long long* nbig, long long big_cap, long long* bpre) {
-    __shared__ long long s_part[32];
-    const long long nb = min((long long)*nbig, big_cap);
-    const long long per = (nb + blockDim.x - 1) / blockDim.x;
-    const long long i0 = (long long)threadIdx.x * per, i1 = min(i0 + per, nb);
-    long long sum = 0;
-    for (long long i = i0; i < i1; ++i) sum += (long long)(off[big[i] + 1] - off[big[i]]);
-    // exclusive scan of the threads' sums
-    long long incl = sum;
-    for (int d = 1; d < 32; d <<= 1) {
-        const long long y = __shfl_up_sync(kFull, incl, d);
-        if (lane_id() >= d) incl += y;
-    }
-    if (lane_id() == 31) s_part[threadIdx.x >> 5] = incl;
-    __syncthreads();
-    if (threadIdx.x < 32) {
-        long long x = threadIdx.x < (blockDim.x >> 5) ? s_part[threadIdx.x] : 0;
-        long long y = x;
-        for (int d = 1; d < 32; d <<= 1) {
-            const long long z = __shfl_up_sync(kFull, y, d);
-            if (lane_id() >= d) y += z;
-        }
-        s_part[threadIdx.x] = y - x;
-    }
-    __syncthreads();
-    long long run = s_part[threadIdx.x >> 5] + incl - sum;
-    for (long long i = i0; i < i1; ++i) {
-        bpre[i] = run;
-        run += (long long)(off[big[i] + 1] - off[big[i]]);
-    }
-    if (i1 == nb && i0 <= nb) bpre[nb] = run;  // the thread holding the last row (or the first, for none)
-}
-
-// The arcs of the rows k_uf_arcs left, as one flat range cut into 32-arc
-// chunks shared by all warps of the grid; each lane finds its row among the
-// big rows by a binary search over bpre.
-__global__ void k_uf_big(const int32_t* __restrict__ off, const int32_t* __restrict__ adj,
-                         const int32_t* __restrict__ center, int32_t* parent, unsigned long long* cross,
-                         const int32_t* __restrict__ big, const unsigned long long* nbig, long long big_cap,
-                         const long long* __restrict__ bpre, int32_t n, int* err) {
+// The arcs of the listed rows as one flat range (row k of the list covers
+// [bpre[k], bpre[k + 1])) cut into 32-arc chunks; each warp takes a contiguous
+// run of chunks and walks the rows forward. A chunk meets at most two rows
+// (every listed row has more than 32 arcs), so a lane's row is the warp's
+// current row or the next one, whose start in the flat range, arc base and
+// centre the warp keeps in registers: a chunk costs a coalesced read of its
+// targets and a gather of their centres.
+__global__ void k_uf_flat(const int32_t* __restrict__ off, const int32_t* __restrict__ adj,
+                          const int32_t* __restrict__ center, int32_t* parent, unsigned long long* cross,
+                          const int32_t* __restrict__ big, const unsigned long long* nbig, long long big_cap,
+                          const int32_t* __restrict__ bpre, int32_t n, int* err) {
     const int lane = lane_id();
     const long long wid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
     const long long nb = min((long long)*nbig, big_cap);
-    const long long total = nb > 0 ? bpre[nb] : 0;
     unsigned long long c = 0;
-    for (long long f0 = wid * 32; f0 < total; f0 += nw * 32) {  // warp-uniform
-        const long long f = f0 + lane;
-        int32_t cu = 0, cw = 0;
-        bool x = false;
-        if (f < total) {
-            long long lo = 0, hi = nb - 1;  // the last row with bpre <= f
-            while (lo < hi) {
-                const long long mid = (lo + hi + 1) >> 1;
-                if (bpre[mid] <= f) lo = mid;
-                else hi = mid - 1;
-            }
-            const int32_t u = big[lo];
-            cu = center[u];
-            cw = center[adj[(long long)off[u] + (f - bpre[lo])]];
-            if ((uint32_t)cu >= (uint32_t)n || (uint32_t)cw >= (uint32_t)n) {  // every vertex has a centre
-                atomicCAS(err, 0, SCC_ERR_INTERNAL);
-                cw = cu;
-            }
-            x = cw != cu;
+    const long long total = nb > 0 ? (long long)bpre[nb] : 0;
+    const long long nch = (total + 31) / 32;
+    const long long per = (nch + nw - 1) / nw;
+    const long long ch0 = wid * per, ch1 = min(ch0 + per, nch);
+    if (ch0 < ch1) {  // warp-uniform
+        // the row of the run's first arc: the last k with bpre[k] <= 32 ch0
+        long long lo = 0, hi = nb - 1;
+        while (lo < hi) {
+            const long long mid = (lo + hi + 1) >> 1;
+            if ((long long)bpre[mid] <= ch0 * 32) lo = mid;
+            else hi = mid - 1;
         }
-        c += x;
-        const unsigned long long key = x ? ((unsigned long long)(uint32_t)cu << 32 | (uint32_t)cw) : ~0ull;
-        const uint32_t peers = __match_any_sync(kFull, key);
-        if (x && __ffs(peers) - 1 == lane && uf_peek(parent, cu) != uf_peek(parent, cw)) uf_union(parent, cu, cw, err);
+        long long r = lo;
+        // rows r and r + 1: start in the flat range, arc base (off[u] - start), centre
+        auto row = [&](long long k, long long& st, long long& base, int32_t& cu) {
+            if (k < nb) {
+                const int32_t u = big[k];
+                st = bpre[k];
+                base = (long long)off[u] - st;
+                cu = center[u];
+            } else {
+                st = total;
+                base = 0;
+                cu = 0;
+            }
+        };
+        long long s0, b0, s1, b1;
+        int32_t c0, c1;
+        row(r, s0, b0, c0);
+        row(r + 1, s1, b1, c1);
+        int32_t lcu = -1, lcw = -1;  // the pair this lane joined last
+        // two chunks a step: both targets, then both centres, as independent loads
+        for (long long ch = ch0; ch < ch1; ch += 2) {
+            int32_t cu[2], w[2], cw[2];
+#pragma unroll
+            for (int t = 0; t < 2; ++t) {
+                const long long f0 = (ch + t) * 32;
+                while (f0 >= s1 && r + 1 < nb) {  // at most once a chunk: every listed row has more than 32 arcs
+                    ++r;
+                    s0 = s1;
+                    b0 = b1;
+                    c0 = c1;
+                    row(r + 1, s1, b1, c1);
+                }
+                const long long f = f0 + lane;
+                const bool in = ch + t < ch1 && f < total;
+                const bool nx = f >= s1;
+                cu[t] = nx ? c1 : c0;
+                w[t] = in ? adj[f + (nx ? b1 : b0)] : -1;
+            }
+#pragma unroll
+            for (int t = 0; t < 2; ++t) cw[t] = w[t] >= 0 ? center[w[t]] : cu[t];
+#pragma unroll
+            for (int t = 0; t < 2; ++t) {
+                if (w[t] >= 0 && ((uint32_t)cu[t] >= (uint32_t)n || (uint32_t)cw[t] >= (uint32_t)n)) {
+                    atomicCAS(err, 0, SCC_ERR_INTERNAL);  // every vertex has a centre
+                    cw[t] = cu[t];
+                }
+                const bool x = w[t] >= 0 && cw[t] != cu[t];
+                c += x;
+                const unsigned long long key =
+                    x ? ((unsigned long long)(uint32_t)cu[t] << 32 | (uint32_t)cw[t]) : ~0ull;
+                const uint32_t peers = __match_any_sync(kFull, key);
+                if (x && __ffs(peers) - 1 == lane && !(cu[t] == lcu && cw[t] == lcw)) {
+                    lcu = cu[t];
+                    lcw = cw[t];
+                    if (uf_peek(parent, cu[t]) != uf_peek(parent, cw[t])) uf_union(parent, cu[t], cw[t], err);
+                }
+            }
+        }
     }
     for (int d = 16; d >= 1; d >>= 1) c += __shfl_xor_sync(kFull, c, d);
     if (lane == 0 && c) atomicAdd(cross, c);
@@ -355,19 +343,19 @@ int launch_ldd_setup(const int32_t* order, long long first, int32_t n, int32_t* 
 
 int launch_cc_union_label(const int32_t* off, const int32_t* adj, int32_t n, const int32_t* center, int32_t* parent,
                           int32_t* root, int32_t* mn, int32_t* out, unsigned long long* counters, int32_t* big,
-                          long long* bpre, long long big_cap, int* err, int num_sms, cudaStream_t s,
-                          cudaEvent_t* ev) {
+                          int32_t* bdeg, int32_t* bpre, void* scan_tmp, long long big_cap, int* err, int num_sms,
+                          cudaStream_t s, cudaEvent_t* ev) {
     const int g = grid_for(n, kBlk * 4, num_sms * 16);
     k_uf_init<<<g, kBlk, 0, s>>>(n, parent, mn);
     SCC_LAUNCH();
+    SCC_CUDA(cudaMemsetAsync(bdeg, 0, sizeof(int32_t) * (size_t)big_cap, s));
     if (ev) cudaEventRecord(ev[0], s);
-    k_uf_arcs<<<grid_for(n, kBlk * 4, num_sms * 16), kBlk, 0, s>>>(off, adj, n, center, parent, &counters[0], big,
+    k_uf_arcs<<<grid_for(n, kBlk * 4, num_sms * 16), kBlk, 0, s>>>(off, adj, n, center, parent, &counters[0], big, bdeg,
                                                                    &counters[3], big_cap, err);
     SCC_LAUNCH();
-    k_big_scan<<<1, 1024, 0, s>>>(off, big, &counters[3], big_cap, bpre);
-    SCC_LAUNCH();
-    k_uf_big<<<num_sms * 8, kBlk, 0, s>>>(off, adj, center, parent, &counters[0], big, &counters[3], big_cap, bpre, n,
-                                          err);
+    SCC_TRY(launch_scan(bdeg, bpre, big_cap, scan_tmp, s));  // the listed rows' places in the flat range
+    k_uf_flat<<<num_sms * 8, kBlk, 0, s>>>(off, adj, center, parent, &counters[0], big, &counters[3], big_cap, bpre, n,
+                                           err);
     SCC_LAUNCH();
     if (ev) cudaEventRecord(ev[1], s);
     k_uf_roots<<<g, kBlk, 0, s>>>(n, center, parent, root, mn, err);

@@ -400,12 +400,13 @@ int launch_sym_csr(const int32_t* off, const int32_t* adj, const int32_t* toff, 
 int launch_iota(int32_t n, int32_t* a, int num_sms, cudaStream_t s);
 int launch_ldd_setup(const int32_t* order, long long first, int32_t n, int32_t* center, uint32_t* bits, int num_sms,
                      cudaStream_t s);
-// counters: [0] cross arcs [1] clusters [2] components [3] rows spread over the
-// grid (big: big_cap >= m / 2048 + 1 entries, bpre: big_cap + 1)
+// counters: [0] cross arcs [1] clusters [2] components [3] rows of more than 32
+// arcs (big, bdeg: big_cap >= m / 33 + 1 entries; bpre: big_cap + 1; scan_tmp:
+// scan_tmp_bytes(big_cap))
 int launch_cc_union_label(const int32_t* off, const int32_t* adj, int32_t n, const int32_t* center, int32_t* parent,
                           int32_t* root, int32_t* mn, int32_t* out, unsigned long long* counters, int32_t* big,
-                          long long* bpre, long long big_cap, int* err, int num_sms, cudaStream_t s,
-                          cudaEvent_t* ev);
+                          int32_t* bdeg, int32_t* bpre, void* scan_tmp, long long big_cap, int* err, int num_sms,
+                          cudaStream_t s, cudaEvent_t* ev);
 // Least-element lists (lelists.cu, Sec. 5.2 Alg. 5) of the symmetric CSR for
 // the vertex order `order`: on success res->off (int64[n+1]), res->src and
 // res->dist (int32[total]) are device allocations the caller frees (dfree);
