@@ -368,16 +368,18 @@ __global__ void __launch_bounds__(1024) k_fine_scan(const unsigned long long* __
         tb += tiles_of(g);
     }
     if (threadIdx.x == 0) tile_base[ns] = ntot;
-    __syncthreads();
-    // segment of every tile: the last g with tile_base[g] <= t (all threads)
-    for (unsigned long long t = threadIdx.x; t < ntot; t += blockDim.x) {
-        int lo = 0, hi = ns;
-        while (hi - lo > 1) {
-            const int mid = (lo + hi) >> 1;
-            if (tile_base[mid] <= t) lo = mid;
-            else hi = mid;
-        }
-        tile_seg[t] = lo;
+}
+
+// The segment of every split tile: a warp per segment fills its run of
+// tile_seg (tile_base written by k_fine_scan; runs past tile_cap are cut).
+__global__ void k_tile_seg(const unsigned long long* __restrict__ tile_base, int ns, long long tile_cap,
+                           int32_t* tile_seg) {
+    const int lane = lane_id();
+    const long long w0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long g = w0; g < ns; g += nw) {
+        const long long t0 = (long long)tile_base[g], t1 = min((long long)tile_base[g + 1], tile_cap);
+        for (long long t = t0 + lane; t < t1; t += 32) tile_seg[t] = (int32_t)g;
     }
 }
 
@@ -897,8 +899,12 @@ int launch_transpose_rest(int32_t n, int64_t mt, int shift, int K, const unsigne
         return SCC_OK;
     }
     SCC_TRY(ensure_attributes());
+    const long long tile_cap = (long long)transpose_split_tiles(mt, n, shift, K);
     k_fine_scan<<<1, 1024, 0, s>>>(hist, K, nf, nb, T.start, T.gcur, order_tmp, T.seg_start, T.seg_len, T.tile_base,
-                                   tile_tmp, (long long)transpose_split_tiles(mt, n, shift, K), T.counters, err);
+                                   tile_tmp, tile_cap, T.counters, err);
+    SCC_LAUNCH();
+    k_tile_seg<<<std::max(1, std::min(num_sms * 4, (K * nb + 7) / 8)), 256, 0, s>>>(T.tile_base, K * nb, tile_cap,
+                                                                                    tile_tmp);
     SCC_LAUNCH();
     if (nself != nullptr) {
         unsigned long long hself = 0;
