@@ -49,8 +49,11 @@ extern "C" {
 
 /*
  * Tunables of the batched kernel (results never depend on them). Defaults:
- * tau 512, block 512, lambda 256, sigma 50, seeds 32, beta 2, blocks_per_sm 0.
- *   tau     VGC edge budget of a warp's local search (Sec. 3.2), 1..65536.
+ * tau 0, block 512, lambda 256, sigma 50, seeds 32, beta 2, blocks_per_sm 0.
+ *   tau     VGC edge budget of a warp's local search (Sec. 3.2), 1..65536, or 0
+ *           (the default): chosen per graph, 128 for a graph with at least 8
+ *           arcs per vertex or a row of at least 16 times the mean degree
+ *           (hubs), 2048 otherwise (lattices, k-NN-like graphs).
  *   block   threads per block, 128, 256 or 512 (one block runs one graph).
  *   lambda  first hash-bag chunk, a power of two in [256, 65536] (Sec. 3.3).
  *           Every round of a search reads at least the first chunk, and one

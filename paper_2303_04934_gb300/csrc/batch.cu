@@ -217,6 +217,19 @@ struct BlockShared {
     unsigned long long acc;
 };
 
+// Maximum over the block (every thread gets it).
+__device__ unsigned long long block_max(unsigned long long x, BlockShared& sh) {
+    for (int d = 16; d >= 1; d >>= 1) x = max(x, __shfl_xor_sync(kFull, x, d));
+    __syncthreads();
+    if (threadIdx.x == 0) sh.acc = 0;
+    __syncthreads();
+    if (lane_id() == 0 && x) atomicMax(&sh.acc, x);
+    __syncthreads();
+    const unsigned long long t = sh.acc;
+    __syncthreads();
+    return t;
+}
+
 // Sum over the block (every thread gets the total).
 __device__ unsigned long long block_sum(unsigned long long x, BlockShared& sh) {
     for (int d = 16; d >= 1; d >>= 1) x += __shfl_xor_sync(kFull, x, d);
@@ -337,8 +350,9 @@ __device__ bool scc_one_graph(const BatchArgs& A, Ws& W, int g, BlockShared& sh,
 
     mark(1);
     // ---- 2. trimming; 3. active list (ordered) for the pivot permutation
-    unsigned long long na = 0;
+    unsigned long long na = 0, maxdeg = 0;
     for (int v = tid; v < n; v += nt) {
+        maxdeg = max(maxdeg, (unsigned long long)(off[v + 1] - off[v]));
         const bool t = off[v + 1] == off[v] || W.toff[v + 1] == W.toff[v];
         W.label[v] = t ? kDone : 0;
         W.rep[v] = v;
@@ -347,6 +361,13 @@ __device__ bool scc_one_graph(const BatchArgs& A, Ws& W, int g, BlockShared& sh,
     }
     __syncthreads();
     na = block_sum(na, sh);
+    // the graph's VGC budget: the configured tau, or (tau = 0) 128 for a graph
+    // with 8 arcs a vertex or more or with a row of 16 times the mean degree
+    // or more (hubs: a round lasts as long as its longest local search, which
+    // grows fastest where degrees are high or skewed), 2048 otherwise
+    maxdeg = block_max(maxdeg, sh);
+    const int tau_g = A.tau > 0 ? A.tau
+                                : ((m >= 8ll * n || (long long)maxdeg * n >= 16ll * max(m, 1ll)) ? 128 : 2048);
     if (na > 0) {
         block_exclusive_scan(W.cnt, n, sh);
         for (int v = tid; v < n; v += nt)
@@ -374,6 +395,7 @@ __device__ bool scc_one_graph(const BatchArgs& A, Ws& W, int g, BlockShared& sh,
         {
             // forward (G) and backward (G^T) searches in the same rounds
             EngineParams<uint32_t> P = W.P32;
+            P.tau = P.hub_thr = tau_g;
             P.off = off;
             P.adj = adj;
             P.off2 = W.toff;
@@ -473,6 +495,7 @@ __device__ bool scc_one_graph(const BatchArgs& A, Ws& W, int g, BlockShared& sh,
                 cap[d] = min(max(c2, cap_floor), A.D.tcap);
             }
             EngineParams<uint64_t> P = W.P64;
+            P.tau = P.hub_thr = tau_g;
             P.off = off;
             P.adj = adj;
             P.off2 = W.toff;
@@ -810,7 +833,7 @@ namespace {
 
 bool valid_config(const scc_batch_config* c) {
     if (!c) return false;
-    if (c->tau < 1 || c->tau > 65536) return false;
+    if (c->tau < 0 || c->tau > 65536) return false;
     if (c->block != 128 && c->block != 256 && c->block != 512) return false;
     if (c->lambda < 256 || c->lambda > 65536 || (c->lambda & (c->lambda - 1))) return false;
     if (c->sigma < 1 || c->seeds < 1 || c->seeds > 32) return false;
@@ -1279,7 +1302,7 @@ extern "C" {
 
 SCC_API int scc_batch_config_default(scc_batch_config* cfg) {
     if (!cfg) return SCC_ERR_INVALID_ARG;
-    cfg->tau = 512;
+    cfg->tau = 0;
     cfg->block = 512;
     cfg->lambda = 256;
     cfg->sigma = 50;
