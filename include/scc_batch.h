@@ -8,7 +8,10 @@
  * forward and backward single-reachability, prefix-doubling batches of
  * multi-reachability with VGC local searches and a hash-bag frontier, the
  * labelling step of Alg. 1, and the canonical minimum label -- on every graph
- * of a batch. There is no counterpart in the paper: batching is how a serving
+ * of a batch. On a graph of high or skewed degree (at least 8 arcs per vertex,
+ * or a row of at least 16 times the mean degree) the first SCC runs its forward
+ * and backward searches one after the other with the dense rounds of Sec. 4.2;
+ * on the others both directions share each round. There is no counterpart in the paper: batching is how a serving
  * system amortises launches over thousands of small graphs.
  *
  * Execution: one persistent kernel; each thread block takes the next graph from

@@ -56,7 +56,7 @@ constexpr int kTimeWords = 11;
 // ------------------------------------------------------------ working memory --
 // Byte offsets of a block's arrays inside its slice (all 256-byte aligned).
 struct WsLayout {
-    size_t toff, tadj, cnt, label, rep, act, src, fmax, bmax, hit, bits_f, bits_b, tab0, tab1, slots0, slots1,
+    size_t toff, tadj, cnt, label, rep, act, src, fmax, bmax, hit, bits_f, bits_b, fb0, fb1, tab0, tab1, slots0, slots1,
         hub_item0, hub_item1, hub_beg0, hub_beg1, hub_deg0, hub_deg1, hub_sb0, hub_sb1, segmap0, segmap1, ctl,
         tag, bytes;
 };
@@ -93,6 +93,8 @@ WsLayout make_layout(const BatchDims& d) {
     L.hit = take(8 * n1);
     L.bits_f = take(4 * words);
     L.bits_b = take(4 * words);
+    L.fb0 = take(4 * words);
+    L.fb1 = take(4 * words);
     L.tab0 = take(8 * (size_t)d.tcap);
     L.tab1 = take(8 * (size_t)d.tcap);
     L.slots0 = take(8 * (size_t)d.nslots);
@@ -146,6 +148,7 @@ struct Ws {
     int32_t *toff_slice, *tadj_slice;  // the slice's own G^T arrays
     unsigned long long *fmax, *bmax, *hit;
     uint32_t *bits_f, *bits_b;
+    uint32_t *fb0, *fb1;  // frontier bitmaps of the dense (bottom-up) rounds
     unsigned long long *tab0, *tab1;
     uint32_t* tag;  // the block's labelling-tag counter, kept across launches
     EngineParams<uint32_t> P32;
@@ -172,6 +175,8 @@ __device__ void bind_ws(const BatchArgs& A, Ws& W) {
     W.hit = at<unsigned long long>(b, L.hit);
     W.bits_f = at<uint32_t>(b, L.bits_f);
     W.bits_b = at<uint32_t>(b, L.bits_b);
+    W.fb0 = at<uint32_t>(b, L.fb0);
+    W.fb1 = at<uint32_t>(b, L.fb1);
     W.tab0 = at<unsigned long long>(b, L.tab0);
     W.tab1 = at<unsigned long long>(b, L.tab1);
     W.tag = at<uint32_t>(b, L.tag);
@@ -298,6 +303,10 @@ struct InitPivotBoth {
     uint32_t v;
     __device__ __forceinline__ uint32_t operator()(long long i) const { return i ? (v | PolSingleBoth::kDir) : v; }
 };
+struct InitPivot {
+    uint32_t v;
+    __device__ __forceinline__ uint32_t operator()(long long) const { return v; }
+};
 
 // ------------------------------------------------------------ one graph --
 // Returns false after an error (recorded in *A.err): the block stops.
@@ -366,8 +375,8 @@ __device__ bool scc_one_graph(const BatchArgs& A, Ws& W, int g, BlockShared& sh,
     // or more (hubs: a round lasts as long as its longest local search, which
     // grows fastest where degrees are high or skewed), 2048 otherwise
     maxdeg = block_max(maxdeg, sh);
-    const int tau_g = A.tau > 0 ? A.tau
-                                : ((m >= 8ll * n || (long long)maxdeg * n >= 16ll * max(m, 1ll)) ? 128 : 2048);
+    const bool hubby = m >= 8ll * n || (long long)maxdeg * n >= 16ll * max(m, 1ll);
+    const int tau_g = A.tau > 0 ? A.tau : (hubby ? 128 : 2048);
     if (na > 0) {
         block_exclusive_scan(W.cnt, n, sh);
         for (int v = tid; v < n; v += nt)
@@ -392,7 +401,37 @@ __device__ bool scc_one_graph(const BatchArgs& A, Ws& W, int g, BlockShared& sh,
             W.bits_b[w] = m0;
         }
         __syncthreads();
-        {
+        if (hubby) {
+            // a graph of high or skewed degree (a few rounds hold most of the
+            // class): forward and backward searches one after the other, each
+            // with dense (bottom-up) rounds once its frontier holds 1/20 of the
+            // class or of the arcs (Sec. 4.2)
+            for (int w = tid; w < words; w += nt) {
+                W.fb0[w] = 0;
+                W.fb1[w] = 0;
+            }
+            __syncthreads();
+            for (int d = 0; d < 2; ++d) {
+                EngineParams<uint32_t> P = W.P32;
+                P.tau = P.hub_thr = tau_g;
+                P.off = d == 0 ? off : W.toff;
+                P.adj = d == 0 ? adj : W.tadj;
+                P.n = n;
+                DenseParams dp{d == 0 ? W.toff : off, d == 0 ? W.tadj : adj, {W.fb0, W.fb1}, (long long)na, 20, m};
+                PolSingle pol;
+                pol.bits = d == 0 ? W.bits_f : W.bits_b;
+                WarpStats ws;
+                int why = 0;
+                if (!engine_search<PolSingle, InitPivot, CtaScope>(P, pol, InitPivot{(uint32_t)p0}, 1, &dp, q32, ws,
+                                                                   gr, si, why))
+                    return false;
+                ++si;
+                if (why != 0) {  // the hash bag is sized so that this never happens
+                    if (tid == 0) atomicCAS(A.err, 0, why < 0 ? why : SCC_ERR_INTERNAL);
+                    return false;
+                }
+            }
+        } else {
             // forward (G) and backward (G^T) searches in the same rounds
             EngineParams<uint32_t> P = W.P32;
             P.tau = P.hub_thr = tau_g;
