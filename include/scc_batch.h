@@ -8,11 +8,20 @@
  * forward and backward single-reachability, prefix-doubling batches of
  * multi-reachability with VGC local searches and a hash-bag frontier, the
  * labelling step of Alg. 1, and the canonical minimum label -- on every graph
- * of a batch. On a graph of high or skewed degree (at least 8 arcs per vertex,
- * or a row of at least 16 times the mean degree) the first SCC runs its forward
- * and backward searches one after the other with the dense rounds of Sec. 4.2;
- * on the others both directions share each round. There is no counterpart in the paper: batching is how a serving
+ * of a batch. There is no counterpart in the paper: batching is how a serving
  * system amortises launches over thousands of small graphs.
+ *
+ * Single-pivot steps: the next pivots of the order take the first pivot's
+ * single-reachability step too, while the last such step left at least 1/8
+ * of the active vertices reached one way only (at most 8 steps); and the
+ * sources of a batch of at most 16 that overflows its pair tables are taken
+ * one such step each. Sources that reach much of the graph (a pivot that
+ * missed a giant SCC) cost one bitmap search each this way, not pair-table
+ * searches that fill up and rerun. On a graph of high or skewed degree (at
+ * least 8 arcs per vertex, or a row of at least 16 times the mean degree) a
+ * step runs its forward and backward searches one after the other with the
+ * dense rounds of Sec. 4.2; on the others both directions share each round.
+ * The labels never depend on these choices.
  *
  * Execution: one persistent kernel; each thread block takes the next graph from
  * a device work queue (largest graphs first) and runs its whole SCC alone, with

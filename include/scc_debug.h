@@ -131,10 +131,12 @@ SCC_API int scc_debug_le_lists(scc_handle h, int64_t init_cap, int64_t init_log,
 
 /* Batched SCC (scc_batch.h): for every graph g of the last scc_batch_run,
    out[11g .. 11g + 5] = device globaltimer (ns) at its start and at the end of
-   the transpose, the first SCC, the class trimming, the batches and the
-   labels; out[11g + 6] = the block that ran it; out[11g + 7 .. 11g + 10] =
-   engine rounds of its batches, pair searches, pair searches rerun after a
-   table or the bag filled up, batches labelled. out: host uint64[11 * G]. */
+   the transpose, the single-pivot steps, the class trimming, the batches and
+   the labels; out[11g + 6] = the block that ran it; out[11g + 7 .. 11g + 10]
+   = engine rounds of its batches, pair searches, pair searches that stopped
+   because a table or the bag filled up (the batch then reruns or takes its
+   sources one single-pivot step each), batches labelled. out: host
+   uint64[11 * G]. */
 SCC_API int scc_debug_batch_times(struct scc_batch* h, uint64_t* out);
 
 /*

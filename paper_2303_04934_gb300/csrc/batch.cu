@@ -47,6 +47,8 @@ namespace {
 
 constexpr int kBatchMaxBlock = 512;
 constexpr int kBatchTrimPasses = 4;
+constexpr int kBatchSingleSteps = 8;  // single-pivot steps before the batches, at most
+constexpr long long kBatchSingleFallback = 16;  // an overflowing batch this small runs as single steps
 constexpr long long kBatchMinTable = 1024;
 // per-graph record: start, transpose done, first SCC done, class trimming done,
 // batches done, end (globaltimer ns); block; engine rounds, pair searches, pair
@@ -308,6 +310,108 @@ struct InitPivot {
     __device__ __forceinline__ uint32_t operator()(long long) const { return v; }
 };
 
+// One single-pivot step (Sec. 4.2): forward and backward single-reachability
+// from pivot p inside its class, then the labelling of Alg. 1 for that class:
+// reached both ways -> p's SCC; one way -> a new class (old class, p or none,
+// p or none). *c = vertices finished, *r = vertices moved to a new class. Kept
+// out of line: its register use stays apart from the batch loop's. Returns
+// false after an error (recorded in *A.err).
+__device__ __noinline__ bool single_step(const BatchArgs& A, Ws& W, BlockShared& sh, const LocalQueue<uint32_t>& q32,
+                                         uint32_t& gr, uint32_t& si, const int32_t* off, const int32_t* adj, int n,
+                                         long long m, int tau_g, bool hubby, int p, unsigned long long* c_out,
+                                         unsigned long long* r_out) {
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int words = (n + 31) / 32;
+    const int wid = tid >> 5, nwarps = nt >> 5, lane = tid & 31;
+    const int32_t Lp = W.label[p];
+    // vertices outside the pivot's class are pre-visited (one coalesced label
+    // load per 32 vertices and a ballot per bitmap word)
+    unsigned long long ncls = 0;
+    for (int w0 = wid * 32; w0 < words; w0 += nwarps * 32) {
+        uint32_t mine = 0;
+        for (int j = 0; j < 32 && w0 + j < words; ++j) {
+            const int v = (w0 + j) * 32 + lane;
+            const uint32_t msk = __ballot_sync(kFull, v >= n || W.label[v] != Lp);
+            if (lane == j) mine = msk;
+        }
+        if (w0 + lane < words) {
+            W.bits_f[w0 + lane] = mine;
+            W.bits_b[w0 + lane] = mine;
+            ncls += (unsigned long long)__popc(~mine);
+        }
+    }
+    ncls = block_sum(ncls, sh);
+    if (hubby) {
+        // a graph of high or skewed degree (a few rounds hold most of the
+        // class): forward and backward searches one after the other, each
+        // with dense (bottom-up) rounds once its frontier holds 1/20 of the
+        // class or of the arcs (Sec. 4.2)
+        for (int w = tid; w < words; w += nt) {
+            W.fb0[w] = 0;
+            W.fb1[w] = 0;
+        }
+        __syncthreads();
+        for (int d = 0; d < 2; ++d) {
+            EngineParams<uint32_t> P = W.P32;
+            P.tau = P.hub_thr = tau_g;
+            P.off = d == 0 ? off : W.toff;
+            P.adj = d == 0 ? adj : W.tadj;
+            P.n = n;
+            DenseParams dp{d == 0 ? W.toff : off, d == 0 ? W.tadj : adj, {W.fb0, W.fb1}, (long long)ncls, 20, m};
+            PolSingle pol;
+            pol.bits = d == 0 ? W.bits_f : W.bits_b;
+            WarpStats ws;
+            int why = 0;
+            if (!engine_search<PolSingle, InitPivot, CtaScope>(P, pol, InitPivot{(uint32_t)p}, 1, &dp, q32, ws,
+                                                               gr, si, why))
+                return false;
+            ++si;
+            if (why != 0) {  // the hash bag is sized so that this never happens
+                if (tid == 0) atomicCAS(A.err, 0, why < 0 ? why : SCC_ERR_INTERNAL);
+                return false;
+            }
+        }
+    } else {
+        // forward (G) and backward (G^T) searches in the same rounds
+        EngineParams<uint32_t> P = W.P32;
+        P.tau = P.hub_thr = tau_g;
+        P.off = off;
+        P.adj = adj;
+        P.off2 = W.toff;
+        P.adj2 = W.tadj;
+        P.n = n;
+        PolSingleBoth pol;
+        pol.bits[0] = W.bits_f;
+        pol.bits[1] = W.bits_b;
+        WarpStats ws;
+        int why = 0;
+        const InitPivotBoth init{(uint32_t)p};
+        if (!engine_search<PolSingleBoth, InitPivotBoth, CtaScope>(P, pol, init, 2, nullptr, q32, ws, gr, si, why))
+            return false;
+        ++si;
+        if (why != 0) {  // the hash bag is sized so that this never happens
+            if (tid == 0) atomicCAS(A.err, 0, why < 0 ? why : SCC_ERR_INTERNAL);
+            return false;
+        }
+    }
+    unsigned long long c = 0, r = 0;
+    for (int v = tid; v < n; v += nt) {
+        if (W.label[v] != Lp) continue;
+        const bool f = (W.bits_f[v >> 5] >> (v & 31)) & 1u, b = (W.bits_b[v >> 5] >> (v & 31)) & 1u;
+        if (f && b) {
+            W.label[v] = kDone;
+            W.rep[v] = p;
+            ++c;
+        } else if (f || b) {
+            W.label[v] = class_hash(Lp, f ? p : -1, b ? p : -1);
+            ++r;
+        }
+    }
+    *c_out = block_sum(c, sh);
+    *r_out = block_sum(r, sh);
+    return true;
+}
+
 // ------------------------------------------------------------ one graph --
 // Returns false after an error (recorded in *A.err): the block stops.
 __device__ bool scc_one_graph(const BatchArgs& A, Ws& W, int g, BlockShared& sh,
@@ -387,86 +491,32 @@ __device__ bool scc_one_graph(const BatchArgs& A, Ws& W, int g, BlockShared& sh,
     Feistel perm;
     perm.init(A.seed, (uint64_t)max(na, 1ull));
 
-    // ---- 4. the first SCC from the first pivot
-    if (na > 0) {
-        const int p0 = W.act[perm.perm(0, na)];
-        const int words = (n + 31) / 32;
-        for (int w = tid; w < words; w += nt) {
-            uint32_t m0 = 0;
-            for (int j = 0; j < 32; ++j) {
-                const int v = w * 32 + j;
-                if (v >= n || W.label[v] < 0) m0 |= 1u << j;  // outside the class: pre-visited
-            }
-            W.bits_f[w] = m0;
-            W.bits_b[w] = m0;
-        }
-        __syncthreads();
-        if (hubby) {
-            // a graph of high or skewed degree (a few rounds hold most of the
-            // class): forward and backward searches one after the other, each
-            // with dense (bottom-up) rounds once its frontier holds 1/20 of the
-            // class or of the arcs (Sec. 4.2)
-            for (int w = tid; w < words; w += nt) {
-                W.fb0[w] = 0;
-                W.fb1[w] = 0;
-            }
-            __syncthreads();
-            for (int d = 0; d < 2; ++d) {
-                EngineParams<uint32_t> P = W.P32;
-                P.tau = P.hub_thr = tau_g;
-                P.off = d == 0 ? off : W.toff;
-                P.adj = d == 0 ? adj : W.tadj;
-                P.n = n;
-                DenseParams dp{d == 0 ? W.toff : off, d == 0 ? W.tadj : adj, {W.fb0, W.fb1}, (long long)na, 20, m};
-                PolSingle pol;
-                pol.bits = d == 0 ? W.bits_f : W.bits_b;
-                WarpStats ws;
-                int why = 0;
-                if (!engine_search<PolSingle, InitPivot, CtaScope>(P, pol, InitPivot{(uint32_t)p0}, 1, &dp, q32, ws,
-                                                                   gr, si, why))
-                    return false;
-                ++si;
-                if (why != 0) {  // the hash bag is sized so that this never happens
-                    if (tid == 0) atomicCAS(A.err, 0, why < 0 ? why : SCC_ERR_INTERNAL);
-                    return false;
-                }
-            }
-        } else {
-            // forward (G) and backward (G^T) searches in the same rounds
-            EngineParams<uint32_t> P = W.P32;
-            P.tau = P.hub_thr = tau_g;
-            P.off = off;
-            P.adj = adj;
-            P.off2 = W.toff;
-            P.adj2 = W.tadj;
-            P.n = n;
-            PolSingleBoth pol;
-            pol.bits[0] = W.bits_f;
-            pol.bits[1] = W.bits_b;
-            WarpStats ws;
-            int why = 0;
-            const InitPivotBoth init{(uint32_t)p0};
-            if (!engine_search<PolSingleBoth, InitPivotBoth, CtaScope>(P, pol, init, 2, nullptr, q32, ws, gr, si, why))
-                return false;
-            ++si;
-            if (why != 0) {  // the hash bag is sized so that this never happens
-                if (tid == 0) atomicCAS(A.err, 0, why < 0 ? why : SCC_ERR_INTERNAL);
-                return false;
+    // ---- 4. single-pivot steps (Sec. 4.2): the first pivot's SCC by a forward
+    // and a backward single-reachability search inside its class. The next
+    // pivots of the order take the same step while the last one left a large
+    // remainder reached but not finished (at least 1/8 of the active
+    // vertices), at most kBatchSingleSteps of them. Sources whose reach is
+    // much of the graph are covered far more cheaply by one bitmap search
+    // each than by a batch's pair tables (so a small batch that overflows its
+    // tables takes the same steps, below). The batches start after the
+    // positions these steps took.
+    long long pos = 0;  // pivot positions taken
+    for (int step = 0; step < kBatchSingleSteps && pos < (long long)na && active > 0; ++step) {
+        int p = -1;  // the next unfinished pivot (every thread walks the same positions)
+        while (pos < (long long)na) {
+            const int v = W.act[perm.perm((uint64_t)pos, na)];
+            ++pos;
+            if (W.label[v] >= 0) {
+                p = v;
+                break;
             }
         }
-        unsigned long long c = 0;
-        for (int v = tid; v < n; v += nt) {
-            if (W.label[v] != 0) continue;
-            const bool f = (W.bits_f[v >> 5] >> (v & 31)) & 1u, b = (W.bits_b[v >> 5] >> (v & 31)) & 1u;
-            if (f && b) {
-                W.label[v] = kDone;
-                W.rep[v] = p0;
-                ++c;
-            } else if (f || b) {
-                W.label[v] = class_hash(0, f ? p0 : -1, b ? p0 : -1);
-            }
-        }
-        active -= (long long)block_sum(c, sh);
+        if (p < 0) break;
+        unsigned long long c = 0, r = 0;
+        if (!single_step(A, W, sh, q32, gr, si, off, adj, n, m, tau_g, hubby, p, &c, &r)) return false;
+        const long long before = active;
+        active -= (long long)c;
+        if ((long long)r * 8 < before) break;
     }
 
     mark(2);
@@ -502,7 +552,7 @@ __device__ bool scc_one_graph(const BatchArgs& A, Ws& W, int g, BlockShared& sh,
     const uint32_t gr_batches = gr;
     unsigned long long n_search = 0, n_retry = 0, n_batch = 0;
     // ---- 6. prefix-doubling batches over the pivot order
-    long long lo = 1;
+    long long lo = pos;
     double width = A.beta;
     long long a_prev[2] = {0, 0};
     long long k_prev = 0;     // sources of the batch whose pairs a_prev holds
@@ -567,8 +617,9 @@ __device__ bool scc_one_graph(const BatchArgs& A, Ws& W, int g, BlockShared& sh,
             }
             if (why == 1 || why == SCC_ERR_CAPACITY) {  // a table or the hash bag is full
                 // the search stopped early: empty both tables and the used part of
-                // both hash-bag slot arrays, then grow the tables or, at full
-                // size, halve the batch
+                // both hash-bag slot arrays, then take a small batch's sources
+                // one at a time, or grow the tables or, at full size, halve the
+                // batch
                 for (long long i = tid; i < cap[0]; i += nt) W.tab0[i] = ~0ull;
                 for (long long i = tid; i < cap[1]; i += nt) W.tab1[i] = ~0ull;
                 const long long used = chunk_end(A.lambda, ld_volatile(&W.P64.ctl->max_chunk), A.D.nslots);
@@ -577,6 +628,21 @@ __device__ bool scc_one_graph(const BatchArgs& A, Ws& W, int g, BlockShared& sh,
                     W.P64.slots[1][i] = ~0ull;
                 }
                 __syncthreads();
+                ++n_retry;
+                if (k <= kBatchSingleFallback) {
+                    // a few sources whose reach fills a table: a single-pivot
+                    // step each (bitmaps, not pairs), and the batch is done
+                    for (long long j = 0; j < k; ++j) {
+                        const int sj = W.src[j];
+                        if (W.label[sj] < 0) continue;  // finished by an earlier step
+                        unsigned long long c1 = 0, r1 = 0;
+                        if (!single_step(A, W, sh, q32, gr, si, off, adj, n, m, tau_g, hubby, sj, &c1, &r1))
+                            return false;
+                        active -= (long long)c1;
+                    }
+                    cap_floor = 0;
+                    break;
+                }
                 const long long c = max(cap[0], cap[1]);
                 if (why == 1 && c < A.D.tcap) {
                     cap_floor = 2 * c;
@@ -586,7 +652,6 @@ __device__ bool scc_one_graph(const BatchArgs& A, Ws& W, int g, BlockShared& sh,
                     if (tid == 0) atomicCAS(A.err, 0, SCC_ERR_CAPACITY);
                     return false;
                 }
-                ++n_retry;
                 continue;
             }
             // labelling (Alg. 1; Sec. 4.4), which also empties both tables

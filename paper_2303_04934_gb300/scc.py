@@ -413,8 +413,8 @@ def scc_batch_get_stats(h) -> dict:
 
 def scc_debug_batch_times(h, G: int) -> np.ndarray:
     """(G, 11) uint64 per graph of the last run: globaltimer ns at its start and
-    after the transpose, first SCC, class trimming, batches and labels; block;
-    batch rounds, pair searches, reruns, batches."""
+    after the transpose, single-pivot steps, class trimming, batches and
+    labels; block; batch rounds, pair searches, reruns, batches."""
     out = np.zeros(11 * max(G, 1), np.uint64)
     _check(load().scc_debug_batch_times(h, _ptr(out)), "scc_debug_batch_times")
     return out[:11 * G].reshape(G, 11)

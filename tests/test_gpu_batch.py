@@ -184,3 +184,39 @@ def test_batch_empty():
     h = scc.scc_batch_create(0, p.vbase, p.ebase, p.offsets, p.targets)
     scc.scc_batch_run(h, np.zeros(1, np.int32))
     scc.scc_batch_destroy(h)
+
+
+def _cycle_chain(L: int, k: int, seed: int, name: str):
+    """L k-cliques in a line (clique c -> clique c+1 by one arc), vertex ids
+    shuffled: L SCCs, each reaching every clique after it, so a few sources
+    fill a batch's pair tables."""
+    rng = np.random.default_rng(seed)
+    p = rng.permutation(L * k)
+    e = []
+    for c in range(L):
+        e += [(int(p[k * c + x]), int(p[k * c + y])) for x in range(k) for y in range(k) if x != y]
+        if c + 1 < L:
+            e.append((int(p[k * c + k - 1]), int(p[k * c + k])))
+    return gg.from_edges(L * k, e, name=name)
+
+
+def test_batch_overflowing_batches_take_single_pivot_steps():
+    """Chains of SCCs where every source reaches a long stretch of the chain:
+    batches overflow their pair tables, small ones are then taken one pivot at
+    a time and larger ones rerun with bigger tables or fewer sources. Labels
+    match the oracle, on the lattice-like path (2-cycles) and on the dense one
+    (10-cliques: 9 arcs per vertex, forward and backward searches apart)."""
+    import torch
+    ensure_lib()
+    gs = [_cycle_chain(3000, 2, 960, "chain2x3000"), _cycle_chain(50000, 2, 961, "chain2x50000"),
+          _cycle_chain(2000, 10, 962, "chain10x2000")]
+    p = gg.pack(gs)
+    with scc.SccBatch(p) as B:
+        out = B.labels()
+        torch.cuda.synchronize()
+        lab = out.cpu().numpy()
+        t = scc.scc_debug_batch_times(B.h, p.G)
+    for g in range(p.G):
+        want, _ = oracle.scc_labels(p.graph(g).n, p.graph(g).offsets, p.graph(g).targets)
+        assert np.array_equal(p.labels_of(lab, g), want), p.names[g]
+    assert t[1, 9] > 0, "the long chain reran a batch"
