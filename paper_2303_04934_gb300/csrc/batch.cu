@@ -835,29 +835,61 @@ __device__ __forceinline__ int last_le(const long long* __restrict__ a, int lo, 
     return lo;
 }
 
-// The group's CSR: offsets from its first arc, targets from its first vertex.
+// Elements [0, cnt) of a group (its vertices or arcs; global index base + i):
+// a warp takes one contiguous run of 512-element chunks, lane l the elements
+// l, l + 32, ... of a chunk (loads and stores coalesce). Per chunk, first the
+// graph g of each of the lane's 16 elements (bnd = vbase or ebase: the graphs'
+// first elements; one search for the run's first element, then the graph only
+// walks forward, in L1-resident reads), then the 16 loads ld(i, g), all in
+// flight together, then the 16 stores st(i, g, value).
+template <class Ld, class St>
+__device__ __forceinline__ void for_group_elems(const long long* __restrict__ bnd, int g0, int g1, long long base,
+                                                long long cnt, Ld ld, St st) {
+    const int lane = threadIdx.x & 31;
+    const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    const long long per = ((cnt + nwarps - 1) / nwarps + 511) / 512 * 512;
+    const long long lo = warp * per, hi = min(cnt, lo + per);
+    if (lo >= hi) return;  // warp-uniform
+    int g = lane == 0 ? last_le(bnd, g0, g1, base + lo) : 0;
+    g = __shfl_sync(kFull, g, 0);
+    for (long long c0 = lo; c0 < hi; c0 += 512) {
+        int gk[16];
+        int32_t v[16];
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+            const long long i = c0 + k * 32 + lane;
+            if (i < hi)
+                while (g + 1 < g1 && bnd[g + 1] <= base + i) ++g;
+            gk[k] = g;
+        }
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+            const long long i = c0 + k * 32 + lane;
+            v[k] = i < hi ? ld(i, gk[k]) : 0;
+        }
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+            const long long i = c0 + k * 32 + lane;
+            if (i < hi) st(i, gk[k], v[k]);
+        }
+        g = (int)__reduce_max_sync(kFull, (unsigned)g);  // the graph of the chunk's last element
+    }
+}
+
+// The group's CSR: offsets from its first arc, targets from its first vertex
+// (graph g's local row offsets start at offsets[vbase[g] + g]).
 __global__ void k_group_csr(const long long* __restrict__ vbase, const long long* __restrict__ ebase,
                             const int32_t* __restrict__ offsets, const int32_t* __restrict__ targets, int g0, int g1,
-                            long long v0, long long e0, long long ng, long long mg, int32_t* goff, int32_t* gadj) {
-    const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long i0 = 16 * tid; i0 < ng; i0 += 16 * stride) {
-        const long long i1 = min(i0 + 16, ng);
-        int g = last_le(vbase, g0, g1, v0 + i0);
-        for (long long i = i0; i < i1; ++i) {
-            while (g + 1 < g1 && vbase[g + 1] <= v0 + i) ++g;
-            goff[i] = offsets[vbase[g] + g + (v0 + i - vbase[g])] + (int32_t)(ebase[g] - e0);
-        }
-    }
-    if (tid == 0) goff[ng] = (int32_t)mg;
-    for (long long j0 = 16 * tid; j0 < mg; j0 += 16 * stride) {
-        const long long j1 = min(j0 + 16, mg);
-        int g = last_le(ebase, g0, g1, e0 + j0);
-        for (long long j = j0; j < j1; ++j) {
-            while (g + 1 < g1 && ebase[g + 1] <= e0 + j) ++g;
-            gadj[j] = targets[e0 + j] + (int32_t)(vbase[g] - v0);
-        }
-    }
+                            long long v0, long long e0, long long ng, long long mg, int32_t* __restrict__ goff,
+                            int32_t* __restrict__ gadj) {
+    for_group_elems(
+        vbase, g0, g1, v0, ng, [&](long long i, int g) { return offsets[v0 + i + g] + (int32_t)(ebase[g] - e0); },
+        [&](long long i, int, int32_t x) { goff[i] = x; });
+    if (blockIdx.x == 0 && threadIdx.x == 0) goff[ng] = (int32_t)mg;
+    for_group_elems(
+        ebase, g0, g1, e0, mg, [&](long long j, int g) { return targets[e0 + j] + (int32_t)(vbase[g] - v0); },
+        [&](long long j, int, int32_t x) { gadj[j] = x; });
 }
 
 // The group's G^T back to per-graph local form, packed like the input:
@@ -865,26 +897,16 @@ __global__ void k_group_csr(const long long* __restrict__ vbase, const long long
 // its first vertex (in place: the group's G^T arcs are gt_adj[e0 ..)).
 __global__ void k_group_localize(const long long* __restrict__ vbase, const long long* __restrict__ ebase, int g0,
                                  int g1, long long v0, long long e0, long long ng, long long mg,
-                                 const int32_t* __restrict__ gtoff, int32_t* gt_off, int32_t* gt_adj) {
+                                 const int32_t* __restrict__ gtoff, int32_t* __restrict__ gt_off, int32_t* gt_adj) {
     const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long i0 = 16 * tid; i0 < ng; i0 += 16 * stride) {
-        const long long i1 = min(i0 + 16, ng);
-        int g = last_le(vbase, g0, g1, v0 + i0);
-        for (long long i = i0; i < i1; ++i) {
-            while (g + 1 < g1 && vbase[g + 1] <= v0 + i) ++g;
-            gt_off[vbase[g] + g + (v0 + i - vbase[g])] = gtoff[i] - (int32_t)(ebase[g] - e0);
-        }
-    }
+    for_group_elems(
+        vbase, g0, g1, v0, ng, [&](long long i, int g) { return gtoff[i] - (int32_t)(ebase[g] - e0); },
+        [&](long long i, int g, int32_t x) { gt_off[v0 + i + g] = x; });
     for (long long g = g0 + tid; g < g1; g += stride) gt_off[vbase[g + 1] + g] = (int32_t)(ebase[g + 1] - ebase[g]);
-    for (long long j0 = 16 * tid; j0 < mg; j0 += 16 * stride) {
-        const long long j1 = min(j0 + 16, mg);
-        int g = last_le(ebase, g0, g1, e0 + j0);
-        for (long long j = j0; j < j1; ++j) {
-            while (g + 1 < g1 && ebase[g + 1] <= e0 + j) ++g;
-            gt_adj[e0 + j] -= (int32_t)(vbase[g] - v0);
-        }
-    }
+    for_group_elems(
+        ebase, g0, g1, e0, mg, [&](long long j, int g) { return gt_adj[e0 + j] - (int32_t)(vbase[g] - v0); },
+        [&](long long j, int, int32_t x) { gt_adj[e0 + j] = x; });
 }
 
 }  // namespace
