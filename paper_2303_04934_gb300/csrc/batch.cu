@@ -49,6 +49,7 @@ constexpr int kBatchMaxBlock = 512;
 constexpr int kBatchTrimPasses = 4;
 constexpr int kBatchSingleSteps = 8;  // single-pivot steps before the batches, at most
 constexpr long long kBatchSingleFallback = 16;  // an overflowing batch this small runs as single steps
+constexpr int kVU = 4;  // vertices per thread per pass of a block's vertex loops
 constexpr long long kBatchMinTable = 1024;
 // per-graph record: start, transpose done, first SCC done, class trimming done,
 // batches done, end (globaltimer ns); block; engine rounds, pair searches, pair
@@ -325,12 +326,14 @@ __device__ __noinline__ bool single_step(const BatchArgs& A, Ws& W, BlockShared&
     const int wid = tid >> 5, nwarps = nt >> 5, lane = tid & 31;
     const int32_t Lp = W.label[p];
     // vertices outside the pivot's class are pre-visited (one coalesced label
-    // load per 32 vertices and a ballot per bitmap word)
+    // load per 32 vertices and a ballot per bitmap word; a fixed trip count,
+    // so the loads of several words are in flight together)
     unsigned long long ncls = 0;
     for (int w0 = wid * 32; w0 < words; w0 += nwarps * 32) {
         uint32_t mine = 0;
-        for (int j = 0; j < 32 && w0 + j < words; ++j) {
-            const int v = (w0 + j) * 32 + lane;
+#pragma unroll 8
+        for (int j = 0; j < 32; ++j) {
+            const int v = (w0 + j) * 32 + lane;  // v >= n past the last word
             const uint32_t msk = __ballot_sync(kFull, v >= n || W.label[v] != Lp);
             if (lane == j) mine = msk;
         }
@@ -394,17 +397,36 @@ __device__ __noinline__ bool single_step(const BatchArgs& A, Ws& W, BlockShared&
             return false;
         }
     }
+    // four vertices per thread per pass, their loads issued before any store
     unsigned long long c = 0, r = 0;
-    for (int v = tid; v < n; v += nt) {
-        if (W.label[v] != Lp) continue;
-        const bool f = (W.bits_f[v >> 5] >> (v & 31)) & 1u, b = (W.bits_b[v >> 5] >> (v & 31)) & 1u;
-        if (f && b) {
-            W.label[v] = kDone;
-            W.rep[v] = p;
-            ++c;
-        } else if (f || b) {
-            W.label[v] = class_hash(Lp, f ? p : -1, b ? p : -1);
-            ++r;
+    constexpr int U = 4;
+    for (int v0 = tid; v0 < n; v0 += U * nt) {
+        int32_t L[U];
+        uint32_t wf[U], wb[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int v = v0 + u * nt;
+            L[u] = v < n ? W.label[v] : kDone;
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int v = v0 + u * nt;
+            wf[u] = L[u] == Lp ? W.bits_f[v >> 5] : 0u;
+            wb[u] = L[u] == Lp ? W.bits_b[v >> 5] : 0u;
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            if (L[u] != Lp) continue;
+            const int v = v0 + u * nt;
+            const bool f = (wf[u] >> (v & 31)) & 1u, b = (wb[u] >> (v & 31)) & 1u;
+            if (f && b) {
+                W.label[v] = kDone;
+                W.rep[v] = p;
+                ++c;
+            } else if (f || b) {
+                W.label[v] = class_hash(Lp, f ? p : -1, b ? p : -1);
+                ++r;
+            }
         }
     }
     *c_out = block_sum(c, sh);
@@ -463,14 +485,31 @@ __device__ bool scc_one_graph(const BatchArgs& A, Ws& W, int g, BlockShared& sh,
 
     mark(1);
     // ---- 2. trimming; 3. active list (ordered) for the pivot permutation
+    // (the vertex passes of a block take kVU vertices per thread per pass, all
+    // their loads issued before any store: one memory latency per pass, not
+    // one per vertex)
     unsigned long long na = 0, maxdeg = 0;
-    for (int v = tid; v < n; v += nt) {
-        maxdeg = max(maxdeg, (unsigned long long)(off[v + 1] - off[v]));
-        const bool t = off[v + 1] == off[v] || W.toff[v + 1] == W.toff[v];
-        W.label[v] = t ? kDone : 0;
-        W.rep[v] = v;
-        W.cnt[v] = t ? 0 : 1;
-        na += t ? 0 : 1;
+    for (int v0 = tid; v0 < n; v0 += kVU * nt) {
+        int32_t o0[kVU], o1[kVU], t0[kVU], t1[kVU];
+#pragma unroll
+        for (int u = 0; u < kVU; ++u) {
+            const int v = min(v0 + u * nt, n - 1);
+            o0[u] = off[v];
+            o1[u] = off[v + 1];
+            t0[u] = W.toff[v];
+            t1[u] = W.toff[v + 1];
+        }
+#pragma unroll
+        for (int u = 0; u < kVU; ++u) {
+            const int v = v0 + u * nt;
+            if (v >= n) break;
+            maxdeg = max(maxdeg, (unsigned long long)(o1[u] - o0[u]));
+            const bool t = o1[u] == o0[u] || t1[u] == t0[u];
+            W.label[v] = t ? kDone : 0;
+            W.rep[v] = v;
+            W.cnt[v] = t ? 0 : 1;
+            na += t ? 0 : 1;
+        }
     }
     __syncthreads();
     na = block_sum(na, sh);
@@ -483,8 +522,18 @@ __device__ bool scc_one_graph(const BatchArgs& A, Ws& W, int g, BlockShared& sh,
     const int tau_g = A.tau > 0 ? A.tau : (hubby ? 128 : 2048);
     if (na > 0) {
         block_exclusive_scan(W.cnt, n, sh);
-        for (int v = tid; v < n; v += nt)
-            if (W.label[v] == 0) W.act[W.cnt[v]] = v;
+        for (int v0 = tid; v0 < n; v0 += kVU * nt) {
+            int32_t L[kVU], C[kVU];
+#pragma unroll
+            for (int u = 0; u < kVU; ++u) {
+                const int v = min(v0 + u * nt, n - 1);
+                L[u] = W.label[v];
+                C[u] = W.cnt[v];
+            }
+#pragma unroll
+            for (int u = 0; u < kVU; ++u)
+                if (v0 + u * nt < n && L[u] == 0) W.act[C[u]] = v0 + u * nt;
+        }
     }
     __syncthreads();
     long long active = (long long)na;
@@ -563,14 +612,33 @@ __device__ bool scc_one_graph(const BatchArgs& A, Ws& W, int g, BlockShared& sh,
             // sources: the still-active vertices at positions [lo, hi)
             if (tid == 0) sh.count = 0;
             __syncthreads();
-            for (long long p = lo + tid; p < hi; p += nt) {
-                const int v = W.act[perm.perm((uint64_t)p, na)];
-                if (ld_volatile(&W.label[v]) >= 0) W.src[atomicAdd((unsigned long long*)&sh.count, 1ull)] = v;
+            for (long long p0 = lo + tid; p0 < hi; p0 += kVU * nt) {
+                int vv[kVU], L[kVU];
+#pragma unroll
+                for (int u = 0; u < kVU; ++u) {
+                    const long long p = p0 + (long long)u * nt;
+                    vv[u] = p < hi ? W.act[perm.perm((uint64_t)p, na)] : -1;
+                }
+#pragma unroll
+                for (int u = 0; u < kVU; ++u) L[u] = vv[u] >= 0 ? ld_volatile(&W.label[vv[u]]) : -1;
+#pragma unroll
+                for (int u = 0; u < kVU; ++u)
+                    if (L[u] >= 0) W.src[atomicAdd((unsigned long long*)&sh.count, 1ull)] = vv[u];
             }
             __syncthreads();
             const long long k = sh.count;
             __syncthreads();
             if (k == 0) break;
+            if (k == 1) {
+                // one source: the single-pivot step is the same search, with
+                // bitmaps in place of pair tables
+                unsigned long long c1 = 0, r1 = 0;
+                if (!single_step(A, W, sh, q32, gr, si, off, adj, n, m, tau_g, hubby, W.src[0], &c1, &r1))
+                    return false;
+                active -= (long long)c1;
+                ++n_batch;
+                break;
+            }
             // table sizes (Sec. 4.5 heuristic, capped by the slice; the previous
             // batch's pairs scaled by the ratio of the sources, as batches grow)
             long long cap[2];
@@ -684,9 +752,25 @@ __device__ bool scc_one_graph(const BatchArgs& A, Ws& W, int g, BlockShared& sh,
     // ---- 7. canonical labels: the smallest vertex of each SCC (by its rep)
     for (int v = tid; v < n; v += nt) W.cnt[v] = INT_MAX;
     __syncthreads();
-    for (int v = tid; v < n; v += nt) atomicMin(&W.cnt[W.rep[v]], v);
+    for (int v0 = tid; v0 < n; v0 += kVU * nt) {
+        int32_t R[kVU];
+#pragma unroll
+        for (int u = 0; u < kVU; ++u) R[u] = W.rep[min(v0 + u * nt, n - 1)];
+#pragma unroll
+        for (int u = 0; u < kVU; ++u)
+            if (v0 + u * nt < n) atomicMin(&W.cnt[R[u]], v0 + u * nt);
+    }
     __syncthreads();
-    for (int v = tid; v < n; v += nt) out[v] = W.cnt[W.rep[v]];
+    for (int v0 = tid; v0 < n; v0 += kVU * nt) {
+        int32_t R[kVU], M[kVU];
+#pragma unroll
+        for (int u = 0; u < kVU; ++u) R[u] = W.rep[min(v0 + u * nt, n - 1)];
+#pragma unroll
+        for (int u = 0; u < kVU; ++u) M[u] = W.cnt[R[u]];
+#pragma unroll
+        for (int u = 0; u < kVU; ++u)
+            if (v0 + u * nt < n) out[v0 + u * nt] = M[u];
+    }
     __syncthreads();
     return true;
 }
