@@ -61,12 +61,14 @@ extern "C" {
 
 /*
  * Tunables of the batched kernel (results never depend on them). Defaults:
- * tau 0, block 512, lambda 256, sigma 50, seeds 32, beta 2, blocks_per_sm 0.
+ * tau 0, block 1024, lambda 256, sigma 50, seeds 32, beta 2, blocks_per_sm 0.
  *   tau     VGC edge budget of a warp's local search (Sec. 3.2), 1..65536, or 0
  *           (the default): chosen per graph, 128 for a graph with at least 8
  *           arcs per vertex or a row of at least 16 times the mean degree
  *           (hubs), 2048 otherwise (lattices, k-NN-like graphs).
- *   block   threads per block, 128, 256 or 512 (one block runs one graph).
+ *   block   threads per block, 128, 256, 512 or 1024 (one block runs one
+ *           graph; the kernel takes 64 registers a thread, one SM holds
+ *           1,024 threads).
  *   lambda  first hash-bag chunk, a power of two in [256, 65536] (Sec. 3.3).
  *           Every round of a search reads at least the first chunk, and one
  *           block's rounds are short, so the default is the smallest, 256.
@@ -115,10 +117,11 @@ SCC_API int scc_batch_run(scc_batch_handle h, int32_t* labels_out, void* stream)
  * Autotuner: runs the batched kernel on a sample of about `sample` graphs
  * (spread over the size range; all graphs when sample <= 0 or >= G) for the
  * handle's configuration and for every configuration of the grid tau in
- * {16, 64, 256, 1024, 4096} x block in {128, 256, 512} x lambda in
+ * {16, 64, 256, 1024, 4096} x block in {128, 256, 512, 1024} x lambda in
  * {256, 1024, 4096, 16384}. It scores each by the sample's total block time
- * (the sum over the sampled graphs of the time a block spent on each, which is
- * what a full batch's time follows), keeps the best in the handle if it beats
+ * (the sum over the sampled graphs of the time a block spent on each) over the
+ * number of blocks the launch keeps resident, which is what a full batch's
+ * time follows, keeps the best in the handle if it beats
  * the handle's configuration by more than 3% (the handle's otherwise), and
  * returns it and the sample's launch time in milliseconds when the pointers
  * are not NULL. Synchronises `stream`.

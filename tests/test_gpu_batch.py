@@ -126,7 +126,7 @@ def test_batch_mixed_generator_and_autotune():
         best, ms = scc.scc_batch_autotune(B.h, sample=6)
         # the tuner keeps the handle's configuration unless a grid point beats it
         kept = (best.tau, best.block, best.lambda_) == (start.tau, start.block, start.lambda_)
-        assert ms > 0 and (kept or (best.block in (128, 256, 512) and best.tau in (16, 64, 256, 1024, 4096)
+        assert ms > 0 and (kept or (best.block in (128, 256, 512, 1024) and best.tau in (16, 64, 256, 1024, 4096)
                                     and best.lambda_ in (256, 1024, 4096, 16384)))
         got = scc.scc_batch_get_config(B.h)
         assert (got.tau, got.block, got.lambda_) == (best.tau, best.block, best.lambda_)
