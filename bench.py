@@ -1119,7 +1119,7 @@ def main():
         off_h = torch.from_numpy(g.offsets).pin_memory()
         adj_h = torch.from_numpy(g.targets).pin_memory()
         lab_h = torch.empty(n, dtype=torch.int32).pin_memory()
-        k2 = max(1, min(args.steps, 3))
+        k2 = max(1, min(args.steps, 10))  # whole-step wall time over up to 10 steps: one host hiccup moves it less
         with torch.cuda.stream(stream):
             step(off_h, adj_h, lab_h)
             torch.cuda.synchronize()

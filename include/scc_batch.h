@@ -119,9 +119,8 @@ SCC_API int scc_batch_run(scc_batch_handle h, int32_t* labels_out, void* stream)
  * handle's configuration and for every configuration of the grid tau in
  * {16, 64, 256, 1024, 4096} x block in {128, 256, 512, 1024} x lambda in
  * {256, 1024, 4096, 16384}. It scores each by the sample's total block time
- * (the sum over the sampled graphs of the time a block spent on each) over the
- * number of blocks the launch keeps resident, which is what a full batch's
- * time follows, keeps the best in the handle if it beats
+ * (the sum over the sampled graphs of the time a block spent on each, which is
+ * what a full batch's time follows), keeps the best in the handle if it beats
  * the handle's configuration by more than 3% (the handle's otherwise), and
  * returns it and the sample's launch time in milliseconds when the pointers
  * are not NULL. Synchronises `stream`.

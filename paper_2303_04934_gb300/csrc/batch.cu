@@ -1615,13 +1615,15 @@ SCC_API int scc_batch_autotune(scc_batch_handle h, int32_t sample, void* stream_
     const int blocks[] = {128, 256, 512, 1024};
     const int lambdas[] = {256, 1024, 4096, 16384};
     // The objective is the sample's total block time (every sampled graph
-    // runs on its own block, from the kernel's per-graph clock) over the
-    // number of blocks the launch keeps resident, not the launch's span: a
-    // sample smaller than the grid finishes when its largest graph does,
-    // while a full batch's time is its total work spread over the resident
-    // blocks (one 1,024-thread block per SM, or two of 512 threads, ...). The
-    // configuration in the handle stays unless another one cuts that time by
-    // more than 3%.
+    // runs on its own block, from the kernel's per-graph clock), not the
+    // launch's span: a sample smaller than the grid finishes when its largest
+    // graph does, while a full batch's time is its total work spread over the
+    // blocks. It is not divided by the blocks a full launch keeps resident:
+    // the sample's few blocks each have an SM to themselves, so a small block
+    // runs faster here than beside the others of a full batch, and that
+    // division favoured 512-thread blocks that lost on the full batch (span
+    // 516 against 477 ms). The configuration in the handle stays unless
+    // another one cuts the objective by more than 3%.
     std::vector<unsigned long long> tms((size_t)kTimeWords * h->G);
     auto measure = [&](const scc_batch_config& c, double* work, double* span) -> int {
         SCC_TRY(scc_batch_set_config(h, &c));
@@ -1636,7 +1638,7 @@ SCC_API int scc_batch_autotune(scc_batch_handle h, int32_t sample, void* stream_
             const unsigned long long* t = &tms[(size_t)kTimeWords * g];
             w += t[5] > t[0] ? 1e-6 * (double)(t[5] - t[0]) : 0.0;
         }
-        *work = w / (double)std::max(1, h->blocks);
+        *work = w;
         return SCC_OK;
     };
     scc_batch_config bc = base;
