@@ -188,11 +188,9 @@ SCC_API int reach_multi(scc_handle h, const int32_t* sources, int32_t k, int32_t
  * Every call shares the array and finds the previous call's contents in it, so
  * a call clears what must start empty; calls whose work overlaps on the GPU
  * (for instance on two streams) race on it and must be serialised by the
- * caller. The first call on a device looks the array's device address up, with
- * that device current, and keeps it for later calls; make that first call
- * before any stream capture. A cudaDeviceReset of the device discards the
- * array, so the entry point must not be called on that device after one.
- * Synchronises `stream`.
+ * caller. Every call looks the array's device address up on the current
+ * device (after a cudaDeviceReset the array is a new one, zeroed, and the
+ * handles made before the reset are gone). Synchronises `stream`.
  */
 SCC_API int reach_multi_noalloc(scc_handle h, const int32_t* sources, int32_t k, int32_t dir, uint64_t* out,
                                 void* stream);

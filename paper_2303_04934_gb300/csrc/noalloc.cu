@@ -17,7 +17,6 @@
 // previous call's contents, so each call resets what must start empty; two
 // calls whose work overlaps on the GPU (for instance on two streams) race on it.
 #include <cstring>
-#include <mutex>
 
 #include "../../include/scc.h"
 #include "common.cuh"
@@ -31,21 +30,15 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratch
 
 namespace {
 
-// Device address of the scratch array on the current device, looked up once per
-// device (host code must not use the symbol's host-side name as a pointer).
+// Device address of the scratch array on the current device, looked up on every
+// call (host code must not use the symbol's host-side name as a pointer). A
+// cached address would go stale when the module is loaded again after a
+// cudaDeviceReset or a new primary context; the lookup is no stream operation
+// and costs microseconds.
 int scratch_address(unsigned char** out) {
-    static std::mutex mu;
-    static unsigned char* addr[64] = {};
-    int dev = 0;
-    SCC_CUDA(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= 64) return SCC_ERR_CUDA;
-    std::lock_guard<std::mutex> lk(mu);
-    if (!addr[dev]) {
-        void* p = nullptr;
-        SCC_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
-        addr[dev] = static_cast<unsigned char*>(p);
-    }
-    *out = addr[dev];
+    void* p = nullptr;
+    SCC_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+    *out = static_cast<unsigned char*>(p);
     return SCC_OK;
 }
 
