@@ -92,10 +92,11 @@ __device__ __forceinline__ void for_step_arcs(const int32_t* __restrict__ off, c
         const int64_t e1 = min(e0 + (int64_t)kChunk, s1);
         int r;
         if (sm) {
+            const int ei = (int)e0;  // offsets fit 32 bits (m <= INT32_MAX)
             int lo = 0, hi = cnt - 2;
             while (lo < hi) {
                 int mid = (lo + hi + 1) >> 1;
-                if ((int64_t)s_off[mid] <= e0) lo = mid;
+                if (s_off[mid] <= ei) lo = mid;
                 else hi = mid - 1;
             }
             r = lo;  // relative row
@@ -117,18 +118,28 @@ __device__ __forceinline__ void for_step_arcs(const int32_t* __restrict__ off, c
 #pragma unroll
             for (int q = 0; q < kChunk; ++q) a[q] = (e0 + q < e1) ? __ldg(&adj[e0 + q]) : 0;
         }
+        if (sm) {
+            // offsets fit 32 bits (m <= INT32_MAX); the next row's start stays in
+            // a register, so an arc costs one compare unless its row changes
+            const int ei0 = (int)e0, ne = (int)(e1 - e0);
+            int nxt = s_off[r + 1];
 #pragma unroll
-        for (int q = 0; q < kChunk; ++q) {
-            const int64_t e = e0 + q;
-            if (e < e1) {
-                // advance to the row containing e
-                // (bounded by the staged rows: r0..r1 always contain e)
-                if (sm) {
-                    while (r + 1 < cnt - 1 && (int64_t)s_off[r + 1] <= e) ++r;
-                } else {
-                    while (r0 + r + 1 <= r1 && (int64_t)__ldg(&off[r0 + r + 1]) <= e) ++r;
+            for (int q = 0; q < kChunk; ++q) {
+                if (q < ne) {
+                    while (r + 1 < cnt - 1 && nxt <= ei0 + q) nxt = s_off[++r + 1];
+                    f(q, r0 + r, a[q]);
                 }
-                f(q, r0 + r, a[q]);
+            }
+        } else {
+#pragma unroll
+            for (int q = 0; q < kChunk; ++q) {
+                const int64_t e = e0 + q;
+                if (e < e1) {
+                    // advance to the row containing e
+                    // (bounded by the rows r0..r1, which always contain e)
+                    while (r0 + r + 1 <= r1 && (int64_t)__ldg(&off[r0 + r + 1]) <= e) ++r;
+                    f(q, r0 + r, a[q]);
+                }
             }
         }
     }
@@ -456,7 +467,7 @@ __global__ void __launch_bounds__(kBlkA, 2) k_bucket_part(const int32_t* __restr
         for (int j = threadIdx.x; j < total; j += kBlkA) {
             const uint2 x = s_stage[j];
             const int pos = s_disp[x.y >> shift] + j;
-            if ((unsigned long long)(unsigned int)pos < mt) {
+            if ((unsigned int)pos < (unsigned int)mt) {  // mt <= INT32_MAX
                 out_u[pos] = (int32_t)x.x;
                 out_lv[pos] = (uint16_t)(x.y & lmask);  // the target within its bucket
             } else {
