@@ -13,15 +13,22 @@
 //      in-degree counts, a block scan, placement.
 //   2. Trimming (Sec. 4.1): vertices without in- or out-arcs are singletons.
 //   3. The pivot order: a seeded Feistel permutation of the active vertices.
-//   4. The first SCC (Sec. 4.2): forward and backward single-reachability from
-//      the first pivot in the same rounds (vertex items with a direction bit),
-//      the VGC engine with visited bitmaps.
-//   5. Trimming inside the three classes the first SCC leaves.
-//   6. Prefix-doubling batches (Alg. 1): forward and backward multi-
-//      reachability sharing the rounds of one search (pair items with a
-//      direction bit, Sec. 4.3 pair tables), then the labelling step of Alg. 1
-//      (labels.cuh). A batch whose pairs outgrow its tables is rerun with
-//      larger tables, or -- at the largest size -- with half of its sources.
+//   4. Single-pivot steps (Sec. 4.2): the first pivot's SCC by forward and
+//      backward single-reachability with visited bitmaps -- in the same rounds
+//      (vertex items with a direction bit), or, on a graph of high or skewed
+//      degree, one after the other with dense (bottom-up) rounds -- then the
+//      labelling of Alg. 1 for its class. The next pivots take the same step
+//      while a step leaves at least 1/8 of the active vertices reached one way
+//      only (a pivot that missed a giant SCC), at most kBatchSingleSteps times.
+//   5. Trimming inside the classes the steps leave.
+//   6. Prefix-doubling batches (Alg. 1) over the rest of the pivot order:
+//      forward and backward multi-reachability sharing the rounds of one
+//      search (pair items with a direction bit, Sec. 4.3 pair tables), then the
+//      labelling step of Alg. 1 (labels.cuh). A batch of one source takes a
+//      single-pivot step; a batch of at most kBatchSingleFallback sources whose
+//      pairs overflow its tables takes one step per source; a larger one is
+//      rerun with larger tables, or -- at the largest size -- with half of its
+//      sources.
 //   7. The canonical label: the smallest vertex id of each SCC.
 //
 // The working memory of a block (transpose, labels, tables, hash bag, engine
