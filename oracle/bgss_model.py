@@ -19,7 +19,13 @@ readings the CUDA path implements reach the exact SCC partition:
   labelled by the largest such source (Sec. 4.4); every other reached vertex
   moves to the class (old class, largest forward source, largest backward
   source);
-* the output label of a vertex is the smallest vertex id of its SCC.
+* the output label of a vertex is the smallest vertex id of its SCC;
+* optionally, the batched kernel's cut of the order (the library's reading
+  r17): further batches of one pivot after the first while a step leaves at
+  least 1/8 of the active vertices reached one way only, the batches of Alg. 1
+  after the positions those steps took, and a batch of at most
+  ``single_fallback`` sources whose pairs in one direction exceed ``pair_cap``
+  taken one pivot at a time (on the GPU: a batch whose pair tables overflow).
 """
 from __future__ import annotations
 
@@ -46,11 +52,34 @@ def _reach(adj, s, cls, done):
     return seen
 
 
-def bgss_labels(n: int, offsets, targets, beta: float = 2.0, seed: int = 0x5CC00, class_trim: bool = True):
+def _single_step(out, inn, p, cls, done, rep):
+    """One single-pivot step inside p's class: reached both ways -> p's SCC,
+    one way -> class (old class, p or none, p or none). Returns (finished,
+    reached one way only)."""
+    f = _reach(out, p, cls, done)
+    b = _reach(inn, p, cls, done)
+    fin = one = 0
+    for v in f | b:
+        if v in f and v in b:
+            done[v] = True
+            rep[v] = p
+            fin += 1
+        else:
+            cls[v] = (cls[v], p if v in f else NONE, p if v in b else NONE)
+            one += 1
+    return fin, one
+
+
+def bgss_labels(n: int, offsets, targets, beta: float = 2.0, seed: int = 0x5CC00, class_trim: bool = True,
+                single_steps: int = 0, single_fallback: int = 0, pair_cap: int = 0):
     """SCC labels (smallest vertex id of each SCC) by the model of Alg. 1.
 
-    Returns (labels, stats) with stats = dict(n_trimmed, first_scc_size,
-    n_class_trimmed, batches)."""
+    ``single_steps`` > 0 selects the batched kernel's cut of the pivot order
+    (at most that many single-pivot steps in all before the batches), with
+    ``single_fallback`` / ``pair_cap`` its per-source fallback for small
+    batches; 0 keeps the paper's cut. Returns (labels, stats) with stats =
+    dict(n_trimmed, first_scc_size, n_class_trimmed, batches, single_steps,
+    fallback_batches)."""
     off = np.asarray(offsets, dtype=np.int64)
     tg = np.asarray(targets, dtype=np.int64)
     out = [[] for _ in range(n)]
@@ -63,7 +92,7 @@ def bgss_labels(n: int, offsets, targets, beta: float = 2.0, seed: int = 0x5CC00
     rep = list(range(n))       # SCC representative of finished vertices
     done = [False] * n
     cls = [0] * n              # class of unfinished vertices (a tuple after the first split)
-    stats = dict(n_trimmed=0, first_scc_size=0, n_class_trimmed=0, batches=0)
+    stats = dict(n_trimmed=0, first_scc_size=0, n_class_trimmed=0, batches=0, single_steps=0, fallback_batches=0)
 
     # trimming once (Sec. 4.1)
     for v in range(n):
@@ -87,6 +116,22 @@ def bgss_labels(n: int, offsets, targets, beta: float = 2.0, seed: int = 0x5CC00
             if not done[v]:
                 cls[v] = (cls[v], s0 if v in f else NONE, s0 if v in b else NONE)
         stats["batches"] = 1
+        stats["single_steps"] = 1
+        pos = 1  # pivot positions taken
+        if single_steps > 0:
+            # further steps while the last one left at least 1/8 of the active
+            # vertices reached one way only (the first step's count included)
+            active_before = len(order)
+            one = len((f | b) - (f & b))
+            while stats["single_steps"] < single_steps and 8 * one >= active_before and pos < len(order):
+                while pos < len(order) and done[order[pos]]:
+                    pos += 1
+                if pos == len(order):
+                    break
+                active_before = sum(1 for v in range(n) if not done[v])
+                _, one = _single_step(out, inn, order[pos], cls, done, rep)
+                pos += 1
+                stats["single_steps"] += 1
 
         # trimming inside the classes, in passes while one still finishes a vertex
         while class_trim:
@@ -99,9 +144,20 @@ def bgss_labels(n: int, offsets, targets, beta: float = 2.0, seed: int = 0x5CC00
             if not fin:
                 break
 
-    # prefix-doubling batches (Alg. 1; Sec. 4.3-4.4); batch 0 was the first SCC
-    for i in range(1, len(bounds) - 1):
-        srcs = [s for s in order[bounds[i]:bounds[i + 1]] if not done[s]]
+    # prefix-doubling batches (Alg. 1; Sec. 4.3-4.4); batch 0 was the first SCC.
+    # The batched kernel's cut starts after the single-pivot steps' positions
+    # with widths beta, beta^2, ... (ceil of each)
+    if single_steps > 0 and order:
+        cut = [pos]
+        width = beta
+        while cut[-1] < len(order):
+            cut.append(min(len(order), cut[-1] + int(np.ceil(width))))
+            width *= beta
+        ranges = list(zip(cut[:-1], cut[1:]))
+    else:
+        ranges = [(bounds[i], bounds[i + 1]) for i in range(1, len(bounds) - 1)]
+    for lo, hi in ranges:
+        srcs = [s for s in order[lo:hi] if not done[s]]
         if not srcs:
             continue
         stats["batches"] += 1
@@ -110,6 +166,15 @@ def bgss_labels(n: int, offsets, targets, beta: float = 2.0, seed: int = 0x5CC00
         hit = [NONE] * n
         fwd = {s: _reach(out, s, cls, done) for s in srcs}
         bwd = {s: _reach(inn, s, cls, done) for s in srcs}
+        if (single_fallback and len(srcs) <= single_fallback and
+                max(sum(len(x) for x in fwd.values()), sum(len(x) for x in bwd.values())) > pair_cap):
+            # the batch's pairs overflow: one single-pivot step per source, in order
+            stats["fallback_batches"] += 1
+            for s_ in srcs:
+                if not done[s_]:
+                    _single_step(out, inn, s_, cls, done, rep)
+                    stats["single_steps"] += 1
+            continue
         for s in srcs:
             for v in fwd[s]:
                 fmax[v] = max(fmax[v], s)

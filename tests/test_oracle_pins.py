@@ -243,6 +243,41 @@ def test_bgss_model_reaches_the_scc_partition():
         assert st["n_trimmed"] == int(oracle.trim(n, g.offsets, g.targets).sum())
 
 
+def test_bgss_model_with_the_batched_kernels_cut_reaches_the_scc_partition():
+    """Reading r17 (the batched kernel's cut of the pivot order: further
+    single-pivot steps while a step leaves 1/8 of the active vertices reached
+    one way only, batches after those positions, and a small batch whose pairs
+    pass a cap taken one pivot at a time) still gives Tarjan's labels: on every
+    digraph with 3 vertices, on random digraphs and on tori, R-MAT and k-NN
+    graphs, with pair caps small enough that the per-source fallback runs."""
+    from oracle.bgss_model import bgss_labels
+    r17 = dict(single_steps=8, single_fallback=16)
+    for edges in _all_digraphs(3, True):
+        off, adj = _csr(3, edges)
+        lab, _ = bgss_labels(3, off, adj, pair_cap=1, **r17)
+        assert np.array_equal(lab, oracle.scc_labels(3, off, adj)[0]), edges
+    rng = np.random.default_rng(0xB617)
+    steps = fallbacks = 0
+    for trial in range(300):
+        n = int(rng.integers(1, 61))
+        g = gg.gnp(n, float(rng.choice([0.02, 0.05, 0.1, 0.3])), seed=9400 + trial, allow_self=trial % 4 == 0)
+        want, _ = oracle.scc_labels(n, g.offsets, g.targets)
+        lab, st = bgss_labels(n, g.offsets, g.targets, beta=float(rng.choice([1.5, 2.0, 3.0])),
+                              seed=int(rng.integers(1 << 62)), pair_cap=int(rng.integers(0, 40)), **r17)
+        assert np.array_equal(lab, want), (trial, n)
+        steps += st["single_steps"] - 1
+        fallbacks += st["fallback_batches"]
+    for g in (gg.torus(2, 16, 0.5, seed=3), gg.torus(3, 6, 0.4, seed=4), gg.rmat(9, 4, seed=5),
+              gg.knn(400, 3, seed=6)):
+        want, _ = oracle.scc_labels(g.n, g.offsets, g.targets)
+        for cap in (0, 8, 64):
+            lab, st = bgss_labels(g.n, g.offsets, g.targets, pair_cap=cap, **r17)
+            assert np.array_equal(lab, want), (g.n, cap)
+            steps += st["single_steps"] - 1
+            fallbacks += st["fallback_batches"]
+    assert steps > 0 and fallbacks > 0  # both parts of the reading ran
+
+
 @pytest.mark.parametrize("make", [lambda: gg.torus(2, 16, 0.5, seed=3), lambda: gg.torus(3, 6, 0.4, seed=4),
                                   lambda: gg.rmat(9, 4, seed=5), lambda: gg.knn(400, 3, seed=6)])
 def test_bgss_model_on_structured_graphs(make):
