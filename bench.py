@@ -241,8 +241,13 @@ def run_batch(args, spec):
     sizes = np.diff(p.ebase) + np.diff(p.vbase)
     order = np.argsort(-sizes, kind="stable")
     wname = f"batch_G{G}_n{spec['n_lo']}-{spec['n_hi']}_torus2d-rmat8"
+    # a replay reads the packed CSR and writes (then reads) its G^T, as large again
+    csr_bytes = 4 * (nv + G) + 4 * na
+    l2_note = (f"inputs larger than L2 (packed CSR {csr_bytes / 1e9:.2f} GB and its G^T as much again, "
+               f"against a 129 MB L2)" if 2 * csr_bytes > 129e6 else
+               f"inputs smaller than L2 (packed CSR {csr_bytes / 1e6:.0f} MB): replays may find them in L2")
     config = {"workload": wname, "graphs": G, "vertices": nv, "arcs": na, "seed": spec["seed"],
-              "parallelism": f"replicas{world}", "l2": "inputs larger than L2 (packed CSR > 4 GB)"}
+              "parallelism": f"replicas{world}", "l2": l2_note}
 
     if args.impl == "reference":
         if rank != 0:
